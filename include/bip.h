@@ -1,0 +1,195 @@
+/*
+ * bip.h -- C ABI of the GB300 BiP-PRISM core-loss evaluation library.
+ *
+ * The library evaluates the detector-integrated core-loss (EELS) elemental
+ * map of the BiP-PRISM method (arxiv 2607.00756, Algorithm 5): both
+ * scattering matrices are partitioned onto hex-ring parent beams, rebuilt
+ * by natural-neighbour interpolation on each ionized atom's window, and
+ * contracted with the transition potentials and the probe illumination.
+ *
+ * Conventions used by every call
+ *   grid      pixel r = (r_y, r_x), corner origin, N_y x N_x pixels over
+ *             L_y x L_x Angstrom; slices 0..nz-1 of thickness dz.
+ *   beams     signed integer index h in [-N/2, N/2) per axis, spatial
+ *             frequency q = (h_y/L_y, h_x/L_x); lists are ordered by
+ *             (h_y, h_x) ascending.
+ *   complex   interleaved (re, im) float32 pairs ("complex64").
+ *   window    the win x win pixel block of a site at pixel position
+ *             t = position / pixel size starting at floor(t + 1/2) - win/2
+ *             on each axis, wrapped periodically.
+ *   sites     the atoms with nch > 0, in the order they appear in the atom
+ *             array passed to bip_build_s1 / bip_build_s2.
+ *   memory    device pointers are owned by the caller and never freed by the
+ *             library; host pointers are read (or written) only during the
+ *             call.  The library's own device workspaces (window stashes,
+ *             GEMM operands) belong to the context and are released by
+ *             bip_destroy.
+ *   streams   `stream` is a cudaStream_t (NULL: the legacy default stream).
+ *             Work is enqueued on it; host-visible outputs are complete when
+ *             the call returns, device outputs when the stream reaches the
+ *             end of the enqueued work.
+ *   errors    every call returns a bip_status and never aborts; argument
+ *             checks run before any launch; bip_last_error(ctx) gives the
+ *             text of the last failure on that context.  Calls on one
+ *             context are not thread-safe; distinct contexts are
+ *             independent.
+ */
+#ifndef BIP_H
+#define BIP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bip_ctx bip_ctx;
+
+typedef enum {
+    BIP_OK = 0,
+    BIP_ERR_INVALID_ARG = 1,   /* null pointer, bad value, wrong call order   */
+    BIP_ERR_SHAPE = 2,         /* sizes inconsistent with the configuration   */
+    BIP_ERR_OOM = 3,           /* a device or host allocation failed          */
+    BIP_ERR_CUDA = 4,          /* a CUDA call failed (text in bip_last_error) */
+    BIP_ERR_TIMEOUT = 5,       /* a device-side wait gave up                  */
+    BIP_ERR_UNSUPPORTED = 6    /* valid request this build does not implement */
+} bip_status;
+
+typedef enum {
+    BIP_PREC_FP32 = 0,         /* FP32 SIMT complex GEMMs                     */
+    BIP_PREC_SPLIT_BF16 = 1    /* tcgen05 BF16 hi+lo (3 products), FP32 acc.  */
+} bip_precision;
+
+typedef enum {
+    BIP_RECON_COMPLEX = 0,     /* plain convex average (Eq. window-recon)     */
+    BIP_RECON_MAGNITUDE = 1    /* magnitude-preserving (Eq. magpreserve)      */
+} bip_recon;
+
+/* An atom site: position in Angstrom, slice index, number of transition
+ * channels (0: not ionized). */
+typedef struct {
+    double y, x;
+    int32_t slice;
+    int32_t nch;
+} bip_atom;
+
+/* Simulation parameters (lengths in Angstrom, angles in rad, energy in eV).
+ * Constraints checked by bip_create: ny, nx powers of two in [64, 1024];
+ * fy | ny and fx | nx; win even, 2 <= win <= min(ny/fy, nx/fx); nz >= 1;
+ * e0 > 0; 0 < alpha; 0 < theta_det; nrad >= 0; nang >= 1; the aperture and
+ * detector discs fit inside the grid's Nyquist band. */
+typedef struct {
+    int32_t ny, nx;
+    double ly, lx;
+    int32_t nz;
+    double dz;
+    double e0, alpha, theta_det;
+    double defocus, cs;
+    int32_t fy, fx;
+    int32_t nrad1, nang1, nrad2, nang2;
+    int32_t win;
+    int32_t recon;             /* bip_recon     */
+    int32_t prec;              /* bip_precision */
+} bip_config;
+
+/* Host geometry (Algorithm 5 build steps; Sec. 2.2.2-2.2.3, Eq. nnw):
+ * aperture beams |q| lambda <= alpha with h = 0 mod f, detector beams
+ * |q| lambda <= theta_det with h = 0 mod f, hex-ring parents for both and
+ * FP64 Sibson natural-neighbour weights, computed once and cached in the
+ * context.  Host only: touches no GPU.  *out receives the new context. */
+bip_status bip_create(const bip_config* cfg, bip_ctx** out);
+
+/* Releases the context and every device workspace it holds.  The caller
+ * must make sure no work enqueued with this context is still running. */
+bip_status bip_destroy(bip_ctx* ctx);
+
+/* Sizes of the cached geometry: B aperture beams, n_det detector beams,
+ * Bp1 probe parents, Bp2 detector parents; n_sites after a build (else 0).
+ * Any pointer may be NULL. */
+bip_status bip_query(const bip_ctx* ctx, int32_t* B, int32_t* n_det,
+                     int32_t* Bp1, int32_t* Bp2, int32_t* n_sites);
+
+/* Copies the cached geometry to host buffers (any may be NULL):
+ * h_beam [B,2], h_det [n_det,2] beam indices; p1 [Bp1], p2 [Bp2] parent
+ * positions within those lists; w1 [B,Bp1], w2 [n_det,Bp2] dense FP64
+ * weights (row = target beam). */
+bip_status bip_get_geometry(const bip_ctx* ctx, int32_t* h_beam, int32_t* h_det,
+                            int32_t* p1, int32_t* p2, double* w1, double* w2);
+
+/* Chooses the contraction arithmetic for later bip_coreloss_* calls. */
+bip_status bip_set_precision(bip_ctx* ctx, int32_t prec);
+
+/* Probe-forming matrix S1 (Eq. smatrix-advance; Algorithm 5 first and
+ * fourth steps): the Bp1 parent plane waves are advanced through
+ * T_j = exp(i sigma V_j) and the Fresnel propagator to every plane that
+ * holds a site, and each site's window of every parent, de-tilted by
+ * exp(-2 pi i h_p.r/N) (Eq. part-basis), is kept in the context.
+ *   V      [nz, ny, nx] float32 device: projected potential in V*Angstrom.
+ *   atoms  [n_atoms] host; sites are the entries with nch > 0, their slice
+ *          must lie in [0, nz); n_atoms >= 1.
+ * Errors: BIP_ERR_INVALID_ARG (null, bad slice/nch), BIP_ERR_OOM,
+ * BIP_ERR_CUDA. */
+bip_status bip_build_s1(bip_ctx* ctx, const float* V, const bip_atom* atoms,
+                        int32_t n_atoms, void* stream);
+
+/* Detector matrix S2 (Eq. s2, Algorithm 4 second step): the conjugate
+ * detector plane waves G^{-1/2} exp(-2 pi i h_d.r/N) of the Bp2 detector
+ * parents are back-propagated from the exit surface by the transposed
+ * multislice (P, then T_j, for j = nz-1 down to 0), and each site's
+ * window at its plane, de-tilted by exp(+2 pi i h_p.r/N), is kept.  Same
+ * arguments and errors as bip_build_s1; the atom array must describe the
+ * same sites as the S1 build when both are used by one map. */
+bip_status bip_build_s2(bip_ctx* ctx, const float* V, const bip_atom* atoms,
+                        int32_t n_atoms, void* stream);
+
+/* Elemental map (Algorithm 5; Eq. window-recon, magpreserve, coupling,
+ * map-sum): for every site the windows of S1 and S2 are rebuilt from the
+ * parents, M^{(n)} = S2^T diag(H_n) S1 is formed, and
+ *   I(rho) = f_y f_x sum_sites sum_n sum_d |sum_b M^{(n)}_{d,b} c_b(rho)|^2,
+ *   c_b(rho) = f_y f_x Psi(h_b) / sqrt(G sum_aperture |Psi|^2)
+ *              exp(-2 pi i h_b.rho/N),
+ * each site contributing only at scans whose minimum-image offset from it
+ * lies in [-N/(2f), N/(2f)) on both axes (crop mask).  Sites are summed in
+ * a fixed order in FP64 with Neumaier compensation.
+ *   H        [sum nch, win, win] complex64 device: transition potentials of
+ *            each site's channels sampled on its window, sites in order.
+ *   scan_px  [P, 2] float64 host: scan positions in pixels (y, x).
+ *   map_out  [P] float64 device.
+ * Requires both builds on this context (else BIP_ERR_INVALID_ARG). */
+bip_status bip_coreloss_map(bip_ctx* ctx, const void* H, const double* scan_px,
+                            int32_t P, double* map_out, void* stream);
+
+/* Per-site contributions I_tau(rho) of the map above, [n_sites, P] float32
+ * device; entries outside a site's crop mask are written as 0.  The map is
+ * their FP64 sum over sites. */
+bip_status bip_coreloss_sites(bip_ctx* ctx, const void* H, const double* scan_px,
+                              int32_t P, float* partial_out, void* stream);
+
+/* Energy-filtered 4D cube I(q, rho) (Sec. 2.2.6).  Not implemented in this
+ * build: returns BIP_ERR_UNSUPPORTED after checking its arguments. */
+bip_status bip_coreloss_cube(bip_ctx* ctx, const void* H, const double* scan_px,
+                             int32_t P, float* cube_out, void* stream);
+
+/* Stage access for validation.
+ * bip_copy_stash: the de-tilted parent windows of one site, which = 1 (S1,
+ *   [Bp1, win, win]) or 2 (S2, [Bp2, win, win]) complex64, to device `out`.
+ * bip_site_windows: the reconstructed windows of one site, S1 [B, win, win]
+ *   and S2 [n_det, win, win] complex64 device (Eq. window-recon).
+ * bip_site_coupling: the coupling matrices of one site, [nch, n_det, B]
+ *   complex64 device (Eq. coupling), in the context's precision. */
+bip_status bip_copy_stash(bip_ctx* ctx, int32_t which, int32_t site, void* out,
+                          void* stream);
+bip_status bip_site_windows(bip_ctx* ctx, int32_t site, void* s1_out, void* s2_out,
+                            void* stream);
+bip_status bip_site_coupling(bip_ctx* ctx, const void* H, int32_t site, void* m_out,
+                             void* stream);
+
+/* Text of the last error on this context ("" if none; static text if ctx
+ * is NULL). */
+const char* bip_last_error(const bip_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BIP_H */

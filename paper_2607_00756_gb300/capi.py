@@ -1,0 +1,236 @@
+"""ctypes binding of libbip.so -- argument marshalling only.
+
+Every function named bip_* here calls the C entry point of the same name
+(include/bip.h); tensors are passed as raw device pointers together with
+the current CUDA stream of PyTorch.  The library must have been built (see
+build.py); importing this module without it raises, so no call can silently
+run anything but the CUDA path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbip.so")
+
+BIP_OK = 0
+STATUS = {0: "BIP_OK", 1: "BIP_ERR_INVALID_ARG", 2: "BIP_ERR_SHAPE", 3: "BIP_ERR_OOM",
+          4: "BIP_ERR_CUDA", 5: "BIP_ERR_TIMEOUT", 6: "BIP_ERR_UNSUPPORTED"}
+PREC = {"fp32": 0, "split_bf16": 1}
+RECON = {"complex": 0, "magnitude": 1}
+
+
+class BipConfig(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int32), ("nx", ctypes.c_int32),
+                ("ly", ctypes.c_double), ("lx", ctypes.c_double),
+                ("nz", ctypes.c_int32), ("dz", ctypes.c_double),
+                ("e0", ctypes.c_double), ("alpha", ctypes.c_double), ("theta_det", ctypes.c_double),
+                ("defocus", ctypes.c_double), ("cs", ctypes.c_double),
+                ("fy", ctypes.c_int32), ("fx", ctypes.c_int32),
+                ("nrad1", ctypes.c_int32), ("nang1", ctypes.c_int32),
+                ("nrad2", ctypes.c_int32), ("nang2", ctypes.c_int32),
+                ("win", ctypes.c_int32), ("recon", ctypes.c_int32), ("prec", ctypes.c_int32)]
+
+
+class BipAtom(ctypes.Structure):
+    _fields_ = [("y", ctypes.c_double), ("x", ctypes.c_double),
+                ("slice", ctypes.c_int32), ("nch", ctypes.c_int32)]
+
+
+class BipError(RuntimeError):
+    def __init__(self, fn, status, text):
+        super().__init__(f"{fn} -> {STATUS.get(status, status)}: {text}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libbip.so is not built ({LIB_PATH}); run paper_2607_00756_gb300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, VP, D = ctypes.POINTER, ctypes.c_int32, ctypes.c_void_p, ctypes.c_double
+    sig = {
+        "bip_create": [P(BipConfig), P(VP)],
+        "bip_destroy": [VP],
+        "bip_query": [VP, P(I32), P(I32), P(I32), P(I32), P(I32)],
+        "bip_get_geometry": [VP, VP, VP, VP, VP, VP, VP],
+        "bip_set_precision": [VP, I32],
+        "bip_build_s1": [VP, VP, P(BipAtom), I32, VP],
+        "bip_build_s2": [VP, VP, P(BipAtom), I32, VP],
+        "bip_coreloss_map": [VP, VP, P(D), I32, VP, VP],
+        "bip_coreloss_sites": [VP, VP, P(D), I32, VP, VP],
+        "bip_coreloss_cube": [VP, VP, P(D), I32, VP, VP],
+        "bip_copy_stash": [VP, I32, I32, VP, VP],
+        "bip_site_windows": [VP, I32, VP, VP, VP],
+        "bip_site_coupling": [VP, VP, I32, VP, VP],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.bip_last_error.argtypes = [VP]
+    lib.bip_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(fn, ctx, status):
+    if status != BIP_OK:
+        text = _lib.bip_last_error(ctx).decode() if ctx else ""
+        raise BipError(fn, status, text)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_config(cfg, prec=None, recon=None):
+    """bip_config from any object with the configuration's attributes."""
+    c = BipConfig()
+    for name, _ in BipConfig._fields_:
+        if name in ("recon", "prec"):
+            continue
+        setattr(c, name, getattr(cfg, name))
+    r = recon if recon is not None else getattr(cfg, "recon", "magnitude")
+    p = prec if prec is not None else getattr(cfg, "prec", "fp32")
+    c.recon = RECON[r] if isinstance(r, str) else int(r)
+    c.prec = PREC[p] if isinstance(p, str) else int(p)
+    return c
+
+
+def make_atoms(atoms, nch):
+    """bip_atom array from [n,3] (y, x, slice) and [n] channel counts."""
+    atoms = np.asarray(atoms, dtype=np.float64)
+    nch = np.asarray(nch)
+    arr = (BipAtom * len(atoms))()
+    for i in range(len(atoms)):
+        arr[i].y = float(atoms[i, 0])
+        arr[i].x = float(atoms[i, 1])
+        arr[i].slice = int(atoms[i, 2])
+        arr[i].nch = int(nch[i])
+    return arr
+
+
+# ---- the C entry points, by name -------------------------------------------
+
+def bip_create(cfg_struct):
+    ctx = ctypes.c_void_p()
+    st = _lib.bip_create(ctypes.byref(cfg_struct), ctypes.byref(ctx))
+    _check("bip_create", None, st)
+    return ctx
+
+
+def bip_destroy(ctx):
+    _check("bip_destroy", None, _lib.bip_destroy(ctx))
+
+
+def bip_query(ctx):
+    v = [ctypes.c_int32() for _ in range(5)]
+    _check("bip_query", ctx, _lib.bip_query(ctx, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def bip_get_geometry(ctx):
+    B, nd, bp1, bp2, _ = bip_query(ctx)
+    hb = np.zeros((B, 2), np.int32)
+    hd = np.zeros((nd, 2), np.int32)
+    p1 = np.zeros(bp1, np.int32)
+    p2 = np.zeros(bp2, np.int32)
+    w1 = np.zeros((B, bp1), np.float64)
+    w2 = np.zeros((nd, bp2), np.float64)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check("bip_get_geometry", ctx, _lib.bip_get_geometry(ctx, ptr(hb), ptr(hd), ptr(p1), ptr(p2), ptr(w1), ptr(w2)))
+    return dict(h_beam=hb, h_det=hd, p1=p1, p2=p2, w1=w1, w2=w2)
+
+
+def bip_set_precision(ctx, prec):
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    _check("bip_set_precision", ctx, _lib.bip_set_precision(ctx, p))
+
+
+def bip_build_s1(ctx, V, atoms_arr, stream=None):
+    import torch
+    _check("bip_build_s1", ctx, _lib.bip_build_s1(ctx, _dev(V, torch.float32, "V"), atoms_arr,
+                                                   len(atoms_arr), _stream(stream)))
+
+
+def bip_build_s2(ctx, V, atoms_arr, stream=None):
+    import torch
+    _check("bip_build_s2", ctx, _lib.bip_build_s2(ctx, _dev(V, torch.float32, "V"), atoms_arr,
+                                                   len(atoms_arr), _stream(stream)))
+
+
+def _scans(scans):
+    s = np.ascontiguousarray(scans, dtype=np.float64)
+    if s.ndim != 2 or s.shape[1] != 2:
+        raise ValueError("scans must be [P, 2]")
+    return s, s.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def bip_coreloss_map(ctx, H, scans, out, stream=None):
+    import torch
+    s, sp = _scans(scans)
+    _check("bip_coreloss_map", ctx, _lib.bip_coreloss_map(ctx, _dev(H, torch.complex64, "H"), sp, len(s),
+                                                           _dev(out, torch.float64, "out"), _stream(stream)))
+    return out
+
+
+def bip_coreloss_sites(ctx, H, scans, out, stream=None):
+    import torch
+    s, sp = _scans(scans)
+    _check("bip_coreloss_sites", ctx, _lib.bip_coreloss_sites(ctx, _dev(H, torch.complex64, "H"), sp, len(s),
+                                                               _dev(out, torch.float32, "out"), _stream(stream)))
+    return out
+
+
+def bip_coreloss_cube(ctx, H, scans, out, stream=None):
+    import torch
+    s, sp = _scans(scans)
+    _check("bip_coreloss_cube", ctx, _lib.bip_coreloss_cube(ctx, _dev(H, torch.complex64, "H"), sp, len(s),
+                                                             _dev(out, torch.float32, "out"), _stream(stream)))
+    return out
+
+
+def bip_copy_stash(ctx, which, site, out, stream=None):
+    import torch
+    _check("bip_copy_stash", ctx, _lib.bip_copy_stash(ctx, which, site, _dev(out, torch.complex64, "out"),
+                                                       _stream(stream)))
+    return out
+
+
+def bip_site_windows(ctx, site, s1_out, s2_out, stream=None):
+    import torch
+    _check("bip_site_windows", ctx, _lib.bip_site_windows(ctx, site, _dev(s1_out, torch.complex64, "s1_out"),
+                                                           _dev(s2_out, torch.complex64, "s2_out"),
+                                                           _stream(stream)))
+    return s1_out, s2_out
+
+
+def bip_site_coupling(ctx, H, site, out, stream=None):
+    import torch
+    _check("bip_site_coupling", ctx, _lib.bip_site_coupling(ctx, _dev(H, torch.complex64, "H"), site,
+                                                             _dev(out, torch.complex64, "out"), _stream(stream)))
+    return out
+
+
+def bip_last_error(ctx):
+    return _lib.bip_last_error(ctx).decode()

@@ -1,0 +1,79 @@
+"""Convenience wrapper over the C ABI: owns a bip_ctx and allocates the
+output tensors with PyTorch.  Marshalling only -- every step runs in
+libbip.so."""
+import numpy as np
+import torch
+
+from . import capi
+
+
+class BipContext:
+    def __init__(self, cfg, prec=None, recon=None):
+        self.cfg = cfg
+        self._struct = capi.make_config(cfg, prec=prec, recon=recon)
+        self.ctx = capi.bip_create(self._struct)
+        self.B, self.n_det, self.Bp1, self.Bp2, _ = capi.bip_query(self.ctx)
+        self._geo = None
+        self._atoms = None
+        self.n_sites = 0
+
+    @property
+    def geometry(self):
+        if self._geo is None:
+            self._geo = capi.bip_get_geometry(self.ctx)
+        return self._geo
+
+    def set_precision(self, prec):
+        capi.bip_set_precision(self.ctx, prec)
+
+    def build(self, V, atoms, nch, stream=None):
+        """S1 and S2 builds (both window stashes) from a device V."""
+        self._atoms = capi.make_atoms(atoms, nch)
+        capi.bip_build_s1(self.ctx, V, self._atoms, stream)
+        capi.bip_build_s2(self.ctx, V, self._atoms, stream)
+        self.n_sites = capi.bip_query(self.ctx)[4]
+
+    def build_s1(self, V, atoms, nch, stream=None):
+        self._atoms = capi.make_atoms(atoms, nch)
+        capi.bip_build_s1(self.ctx, V, self._atoms, stream)
+        self.n_sites = capi.bip_query(self.ctx)[4]
+
+    def build_s2(self, V, atoms, nch, stream=None):
+        self._atoms = capi.make_atoms(atoms, nch)
+        capi.bip_build_s2(self.ctx, V, self._atoms, stream)
+        self.n_sites = capi.bip_query(self.ctx)[4]
+
+    def map(self, H, scans, out=None, stream=None):
+        scans = np.asarray(scans, dtype=np.float64)
+        if out is None:
+            out = torch.empty(len(scans), dtype=torch.float64, device=H.device)
+        return capi.bip_coreloss_map(self.ctx, H, scans, out, stream)
+
+    def sites(self, H, scans, out=None, stream=None):
+        scans = np.asarray(scans, dtype=np.float64)
+        if out is None:
+            out = torch.empty((self.n_sites, len(scans)), dtype=torch.float32, device=H.device)
+        return capi.bip_coreloss_sites(self.ctx, H, scans, out, stream)
+
+    def stash(self, which, site, device="cuda"):
+        n = self.Bp1 if which == 1 else self.Bp2
+        w = self.cfg.win
+        out = torch.empty((n, w, w), dtype=torch.complex64, device=device)
+        return capi.bip_copy_stash(self.ctx, which, site, out)
+
+    def windows(self, site, device="cuda"):
+        w = self.cfg.win
+        s1 = torch.empty((self.B, w, w), dtype=torch.complex64, device=device)
+        s2 = torch.empty((self.n_det, w, w), dtype=torch.complex64, device=device)
+        return capi.bip_site_windows(self.ctx, site, s1, s2)
+
+    def close(self):
+        if self.ctx:
+            capi.bip_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

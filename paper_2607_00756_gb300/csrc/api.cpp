@@ -1,0 +1,736 @@
+// C ABI of the BiP-PRISM library: argument checks, host geometry, device
+// tables and the order of the kernels (Algorithm 5).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "bip_internal.h"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kRowPad = 128;        // operand rows padded to the MMA tile
+constexpr int kScanTile = 64;       // scans per quadratic-form work item (FP32 path)
+constexpr int kScanTileTc = 128;    // scans per work item (split-BF16 path)
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace
+
+struct bip_ctx {
+    bip_config cfg{};
+    BipGeometry geo;
+    std::string err;
+    int prec = 0;
+    int Bpad = 0, Dpad = 0;
+
+    // device geometry tables
+    bool tables = false;
+    DevBuf twy, twx, py, px, ey, ex, shift1, shift2, hbeam, hdet, coef;
+    DevBuf ell1_idx, ell1_w, ell2_idx, ell2_w;
+    int ell1_k = 0, ell2_k = 0;
+
+    // sites of the current builds
+    std::vector<SiteDev> sites;
+    std::vector<int32_t> plane_ids;     // site ids grouped by plane
+    std::vector<int32_t> plane_off;     // [nz + 1]
+    DevBuf sites_d, plane_ids_d, seq_ids_d;
+    int n_sites = 0, nch_max = 0, n_ch_total = 0;
+    uint64_t sig1 = 0, sig2 = 0;        // site-list signatures of the builds
+    bool s1 = false, s2 = false;
+
+    DevBuf stash1, stash2, cols;
+
+    // map workspaces
+    DevBuf scans_d, ct, ctb, work_d, partial;
+    DevBuf opA32, opB32, mt32, q32;     // FP32 path (zeroed at allocation)
+    DevBuf opA16, opB16, mt16, q16;     // split-BF16 path (zeroed at allocation)
+    DevBuf errflag;
+    std::vector<int32_t> work_h;
+};
+
+namespace {
+
+bip_status fail(bip_ctx* c, bip_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+bip_status fail_cuda(bip_ctx* c, cudaError_t e, const char* what) {
+    const bip_status s = (e == cudaErrorMemoryAllocation) ? BIP_ERR_OOM : BIP_ERR_CUDA;
+    if (c) c->err = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();   // clear a non-sticky error
+    return s;
+}
+
+#define CUDA_TRY(c, expr)                                   \
+    do {                                                    \
+        cudaError_t e_ = (expr);                            \
+        if (e_ != cudaSuccess) return fail_cuda(c, e_, #expr); \
+    } while (0)
+
+cudaError_t ensure(DevBuf& b, size_t bytes, bool zero = false, cudaStream_t s = nullptr) {
+    if (bytes == 0) bytes = 16;
+    if (b.cap >= bytes) return cudaSuccess;
+    if (b.p) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return e;
+    }
+    b.cap = bytes;
+    if (zero) return cudaMemsetAsync(b.p, 0, bytes, s);
+    return cudaSuccess;
+}
+
+void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+template <class T>
+cudaError_t upload(DevBuf& b, const std::vector<T>& h, cudaStream_t s) {
+    cudaError_t e = ensure(b, h.size() * sizeof(T), false, s);
+    if (e != cudaSuccess || h.empty()) return e;
+    return cudaMemcpyAsync(b.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+
+int signed_bin(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// sparse (ELL) copy of a dense weight matrix
+void to_ell(const std::vector<double>& w, int rows, int cols, int& k, std::vector<int32_t>& idx,
+            std::vector<float>& val) {
+    k = 1;
+    for (int r = 0; r < rows; ++r) {
+        int n = 0;
+        for (int c = 0; c < cols; ++c) n += w[(size_t)r * cols + c] != 0.0;
+        k = std::max(k, n);
+    }
+    idx.assign((size_t)rows * k, 0);
+    val.assign((size_t)rows * k, 0.f);
+    for (int r = 0; r < rows; ++r) {
+        int n = 0;
+        for (int c = 0; c < cols; ++c) {
+            const double x = w[(size_t)r * cols + c];
+            if (x != 0.0) {
+                idx[(size_t)r * k + n] = c;
+                val[(size_t)r * k + n] = (float)x;
+                ++n;
+            }
+        }
+    }
+}
+
+bip_status make_tables(bip_ctx* c, cudaStream_t s) {
+    if (c->tables) return BIP_OK;
+    const bip_config& g = c->cfg;
+    const BipGeometry& geo = c->geo;
+    auto turn = [](int m, int n, double sign) {
+        const double a = sign * 2.0 * kPi * (double)m / (double)n;
+        return float2{(float)std::cos(a), (float)std::sin(a)};
+    };
+    std::vector<float2> twy(g.ny), twx(g.nx), ey(g.ny), ex(g.nx), py(g.ny), px(g.nx);
+    for (int m = 0; m < g.ny; ++m) { twy[m] = turn(m, g.ny, -1.0); ey[m] = turn(m, g.ny, +1.0); }
+    for (int m = 0; m < g.nx; ++m) { twx[m] = turn(m, g.nx, -1.0); ex[m] = turn(m, g.nx, +1.0); }
+    // separable propagator exp(-i pi lambda dz q^2) per axis, with the 1/N
+    // of the unnormalised inverse FFT folded in
+    for (int k = 0; k < g.ny; ++k) {
+        const double q = signed_bin(k, g.ny) / g.ly;
+        const double a = -kPi * geo.lambda * g.dz * q * q;
+        py[k] = float2{(float)(std::cos(a) / g.ny), (float)(std::sin(a) / g.ny)};
+    }
+    for (int k = 0; k < g.nx; ++k) {
+        const double q = signed_bin(k, g.nx) / g.lx;
+        const double a = -kPi * geo.lambda * g.dz * q * q;
+        px[k] = float2{(float)(std::cos(a) / g.nx), (float)(std::sin(a) / g.nx)};
+    }
+    std::vector<int2> sh1(geo.Bp1), sh2(geo.Bp2), hb(geo.B), hd(geo.n_det);
+    for (int i = 0; i < geo.Bp1; ++i) sh1[i] = int2{geo.h_beam[2 * geo.p1[i]], geo.h_beam[2 * geo.p1[i] + 1]};
+    for (int i = 0; i < geo.Bp2; ++i) sh2[i] = int2{-geo.h_det[2 * geo.p2[i]], -geo.h_det[2 * geo.p2[i] + 1]};
+    for (int b = 0; b < geo.B; ++b) hb[b] = int2{geo.h_beam[2 * b], geo.h_beam[2 * b + 1]};
+    for (int d = 0; d < geo.n_det; ++d) hd[d] = int2{geo.h_det[2 * d], geo.h_det[2 * d + 1]};
+    std::vector<double2> coef(geo.B);
+    const double fyfx = (double)g.fy * g.fx;
+    for (int b = 0; b < geo.B; ++b) {
+        const std::complex<double> v = fyfx * geo.psi_beam[b] / geo.psi_norm;
+        coef[b] = double2{v.real(), v.imag()};
+    }
+    std::vector<int32_t> i1, i2;
+    std::vector<float> w1, w2;
+    to_ell(geo.w1, geo.B, geo.Bp1, c->ell1_k, i1, w1);
+    to_ell(geo.w2, geo.n_det, geo.Bp2, c->ell2_k, i2, w2);
+    CUDA_TRY(c, upload(c->twy, twy, s));
+    CUDA_TRY(c, upload(c->twx, twx, s));
+    CUDA_TRY(c, upload(c->ey, ey, s));
+    CUDA_TRY(c, upload(c->ex, ex, s));
+    CUDA_TRY(c, upload(c->py, py, s));
+    CUDA_TRY(c, upload(c->px, px, s));
+    CUDA_TRY(c, upload(c->shift1, sh1, s));
+    CUDA_TRY(c, upload(c->shift2, sh2, s));
+    CUDA_TRY(c, upload(c->hbeam, hb, s));
+    CUDA_TRY(c, upload(c->hdet, hd, s));
+    CUDA_TRY(c, upload(c->coef, coef, s));
+    CUDA_TRY(c, upload(c->ell1_idx, i1, s));
+    CUDA_TRY(c, upload(c->ell1_w, w1, s));
+    CUDA_TRY(c, upload(c->ell2_idx, i2, s));
+    CUDA_TRY(c, upload(c->ell2_w, w2, s));
+    CUDA_TRY(c, ensure(c->errflag, 64, true, s));
+    c->tables = true;
+    return BIP_OK;
+}
+
+uint64_t site_signature(const std::vector<SiteDev>& v) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* b = (const unsigned char*)p;
+        for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+    };
+    for (const SiteDev& s : v) {
+        mix(&s.ty, sizeof(double));
+        mix(&s.tx, sizeof(double));
+        mix(&s.plane, sizeof(int32_t));
+        mix(&s.nch, sizeof(int32_t));
+    }
+    return h;
+}
+
+// host part: validates the atoms and computes the site list (no CUDA call)
+bip_status parse_sites(bip_ctx* c, const bip_atom* atoms, int32_t n_atoms, std::vector<SiteDev>& sites,
+                       int& nmax, int& total) {
+    const bip_config& g = c->cfg;
+    if (!atoms || n_atoms < 1) return fail(c, BIP_ERR_INVALID_ARG, "atoms is null or n_atoms < 1");
+    const double dy = g.ly / g.ny, dx = g.lx / g.nx;
+    int off = 0;
+    nmax = 0;
+    for (int i = 0; i < n_atoms; ++i) {
+        const bip_atom& a = atoms[i];
+        if (a.nch < 0 || a.nch > 9)
+            return fail(c, BIP_ERR_INVALID_ARG, "atom nch must lie in [0, 9]");
+        if (a.nch == 0) continue;
+        if (a.slice < 0 || a.slice >= g.nz)
+            return fail(c, BIP_ERR_INVALID_ARG, "ionized atom slice outside [0, nz)");
+        if (!std::isfinite(a.y) || !std::isfinite(a.x))
+            return fail(c, BIP_ERR_INVALID_ARG, "atom position is not finite");
+        SiteDev sd{};
+        sd.ty = a.y / dy;
+        sd.tx = a.x / dx;
+        sd.oy = (int32_t)std::floor(sd.ty + 0.5) - g.win / 2;
+        sd.ox = (int32_t)std::floor(sd.tx + 0.5) - g.win / 2;
+        sd.plane = a.slice;
+        sd.nch = a.nch;
+        sd.ch_off = off;
+        off += a.nch;
+        nmax = std::max(nmax, (int)a.nch);
+        sites.push_back(sd);
+    }
+    if (sites.empty()) return fail(c, BIP_ERR_INVALID_ARG, "no ionized atom (every nch is 0)");
+    total = off;
+    return BIP_OK;
+}
+
+bip_status set_sites(bip_ctx* c, std::vector<SiteDev>& sites, int nmax, int total, cudaStream_t s) {
+    const bip_config& g = c->cfg;
+    const uint64_t sig = site_signature(sites);
+    if (sig != c->sig1 && sig != c->sig2) {
+        c->s1 = c->s2 = false;
+    }
+    c->sites = sites;
+    c->n_sites = (int)sites.size();
+    c->nch_max = nmax;
+    c->n_ch_total = total;
+    c->plane_off.assign(g.nz + 1, 0);
+    for (auto& sd : sites) c->plane_off[sd.plane + 1]++;
+    for (int j = 0; j < g.nz; ++j) c->plane_off[j + 1] += c->plane_off[j];
+    c->plane_ids.assign(sites.size(), 0);
+    std::vector<int32_t> fill(c->plane_off.begin(), c->plane_off.end() - 1);
+    for (int i = 0; i < (int)sites.size(); ++i) c->plane_ids[fill[sites[i].plane]++] = i;
+    std::vector<int32_t> seq(sites.size());
+    std::iota(seq.begin(), seq.end(), 0);
+    CUDA_TRY(c, upload(c->sites_d, c->sites, s));
+    CUDA_TRY(c, upload(c->plane_ids_d, c->plane_ids, s));
+    CUDA_TRY(c, upload(c->seq_ids_d, seq, s));
+    return BIP_OK;
+}
+
+MsPlan plan_for(bip_ctx* c, int ncol, const DevBuf& shift) {
+    MsPlan p{};
+    p.ny = c->cfg.ny;
+    p.nx = c->cfg.nx;
+    p.ncol = ncol;
+    p.sigma = (float)c->geo.sigma;
+    p.twy = (const float2*)c->twy.p;
+    p.twx = (const float2*)c->twx.p;
+    p.py = (const float2*)c->py.p;
+    p.px = (const float2*)c->px.p;
+    p.shift = (const int2*)shift.p;
+    return p;
+}
+
+bip_status build_common(bip_ctx* c, const float* V, const bip_atom* atoms, int32_t n_atoms, cudaStream_t s) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (!V) return fail(c, BIP_ERR_INVALID_ARG, "V is null");
+    std::vector<SiteDev> sites;
+    int nmax = 0, total = 0;
+    bip_status st = parse_sites(c, atoms, n_atoms, sites, nmax, total);
+    if (st != BIP_OK) return st;
+    st = make_tables(c, s);
+    if (st != BIP_OK) return st;
+    return set_sites(c, sites, nmax, total, s);
+}
+
+}  // namespace
+
+// ===========================================================================
+
+extern "C" {
+
+bip_status bip_create(const bip_config* cfg, bip_ctx** out) {
+    if (!cfg || !out) return BIP_ERR_INVALID_ARG;
+    *out = nullptr;
+    const bip_config& g = *cfg;
+    bip_ctx* c = new (std::nothrow) bip_ctx();
+    if (!c) return BIP_ERR_OOM;
+    auto bad = [&](bip_status s, const char*) {
+        delete c;
+        return s;
+    };
+    if (!pow2_in(g.ny, 64, 1024) || !pow2_in(g.nx, 64, 1024)) return bad(BIP_ERR_SHAPE, "grid");
+    if (!(g.ly > 0) || !(g.lx > 0) || g.nz < 1 || !(g.dz >= 0) || !(g.e0 > 0) || !(g.alpha > 0) ||
+        !(g.theta_det > 0) || !std::isfinite(g.defocus) || !std::isfinite(g.cs))
+        return bad(BIP_ERR_INVALID_ARG, "optics");
+    if (g.fy < 1 || g.fx < 1 || g.ny % g.fy || g.nx % g.fx) return bad(BIP_ERR_SHAPE, "f");
+    if (g.win < 16 || g.win % 16 || g.win > g.ny / g.fy || g.win > g.nx / g.fx) return bad(BIP_ERR_SHAPE, "win");
+    if (g.nrad1 < 0 || g.nrad2 < 0 || g.nang1 < 1 || g.nang2 < 1) return bad(BIP_ERR_INVALID_ARG, "rings");
+    if (g.recon != BIP_RECON_COMPLEX && g.recon != BIP_RECON_MAGNITUDE) return bad(BIP_ERR_INVALID_ARG, "recon");
+    if (g.prec != BIP_PREC_FP32 && g.prec != BIP_PREC_SPLIT_BF16) return bad(BIP_ERR_INVALID_ARG, "prec");
+    c->cfg = g;
+    c->prec = g.prec;
+    std::string err;
+    bip_status st = bip_build_geometry(g, c->geo, err);
+    if (st != BIP_OK) {
+        delete c;
+        return st;
+    }
+    c->Bpad = round_up(c->geo.B, kRowPad);
+    c->Dpad = round_up(c->geo.n_det, kRowPad);
+    *out = c;
+    return BIP_OK;
+}
+
+bip_status bip_destroy(bip_ctx* c) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    DevBuf* all[] = {&c->twy, &c->twx, &c->py, &c->px, &c->ey, &c->ex, &c->shift1, &c->shift2, &c->hbeam,
+                     &c->hdet, &c->coef, &c->ell1_idx, &c->ell1_w, &c->ell2_idx, &c->ell2_w, &c->sites_d,
+                     &c->plane_ids_d, &c->seq_ids_d, &c->stash1, &c->stash2, &c->cols, &c->scans_d, &c->ct,
+                     &c->ctb, &c->work_d, &c->partial, &c->opA32, &c->opB32, &c->mt32, &c->q32, &c->opA16,
+                     &c->opB16, &c->mt16, &c->q16, &c->errflag};
+    for (DevBuf* b : all) release(*b);
+    delete c;
+    return BIP_OK;
+}
+
+bip_status bip_query(const bip_ctx* c, int32_t* B, int32_t* n_det, int32_t* Bp1, int32_t* Bp2, int32_t* n_sites) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (B) *B = c->geo.B;
+    if (n_det) *n_det = c->geo.n_det;
+    if (Bp1) *Bp1 = c->geo.Bp1;
+    if (Bp2) *Bp2 = c->geo.Bp2;
+    if (n_sites) *n_sites = (c->s1 || c->s2) ? c->n_sites : 0;
+    return BIP_OK;
+}
+
+bip_status bip_get_geometry(const bip_ctx* c, int32_t* h_beam, int32_t* h_det, int32_t* p1, int32_t* p2,
+                            double* w1, double* w2) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    const BipGeometry& g = c->geo;
+    if (h_beam) std::memcpy(h_beam, g.h_beam.data(), g.h_beam.size() * sizeof(int32_t));
+    if (h_det) std::memcpy(h_det, g.h_det.data(), g.h_det.size() * sizeof(int32_t));
+    if (p1) std::memcpy(p1, g.p1.data(), g.p1.size() * sizeof(int32_t));
+    if (p2) std::memcpy(p2, g.p2.data(), g.p2.size() * sizeof(int32_t));
+    if (w1) std::memcpy(w1, g.w1.data(), g.w1.size() * sizeof(double));
+    if (w2) std::memcpy(w2, g.w2.data(), g.w2.size() * sizeof(double));
+    return BIP_OK;
+}
+
+bip_status bip_set_precision(bip_ctx* c, int32_t prec) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (prec != BIP_PREC_FP32 && prec != BIP_PREC_SPLIT_BF16)
+        return fail(c, BIP_ERR_INVALID_ARG, "unknown precision");
+    c->prec = prec;
+    return BIP_OK;
+}
+
+const char* bip_last_error(const bip_ctx* c) {
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+bip_status bip_build_s1(bip_ctx* c, const float* V, const bip_atom* atoms, int32_t n_atoms, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    bip_status st = build_common(c, V, atoms, n_atoms, s);
+    if (st != BIP_OK) return st;
+    const bip_config& g = c->cfg;
+    const int ncol = c->geo.Bp1;
+    const size_t win2 = (size_t)g.win * g.win;
+    const size_t G = (size_t)g.ny * g.nx;
+    CUDA_TRY(c, ensure(c->stash1, (size_t)c->n_sites * ncol * win2 * sizeof(float2), false, s));
+    CUDA_TRY(c, ensure(c->cols, (size_t)std::max(c->geo.Bp1, c->geo.Bp2) * G * sizeof(float2), false, s));
+    const MsPlan plan = plan_for(c, ncol, c->shift1);
+    int last = 0;
+    for (auto& sd : c->sites) last = std::max(last, (int)sd.plane);
+    for (int j = 0; j <= last; ++j) {
+        MsRowArgs a{};
+        a.cols = (float2*)c->cols.p;
+        a.init = j == 0;
+        a.init_val = 1.0f;
+        a.do_ifft = j > 0;
+        a.v_pre = nullptr;
+        a.v_post = j < last ? V + (size_t)j * G : nullptr;
+        a.do_fft = j < last;
+        a.sites = (const SiteDev*)c->sites_d.p;
+        a.site_ids = (const int32_t*)c->plane_ids_d.p + c->plane_off[j];
+        a.n_sites = c->plane_off[j + 1] - c->plane_off[j];
+        a.win = g.win;
+        a.stash = (float2*)c->stash1.p;
+        CUDA_TRY(c, bip_ms_row_pass(plan, a, s));
+        if (j < last) CUDA_TRY(c, bip_ms_col_pass(plan, (float2*)c->cols.p, s));
+    }
+    c->s1 = true;
+    c->sig1 = site_signature(c->sites);
+    return BIP_OK;
+}
+
+bip_status bip_build_s2(bip_ctx* c, const float* V, const bip_atom* atoms, int32_t n_atoms, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    bip_status st = build_common(c, V, atoms, n_atoms, s);
+    if (st != BIP_OK) return st;
+    const bip_config& g = c->cfg;
+    const int ncol = c->geo.Bp2;
+    const size_t win2 = (size_t)g.win * g.win;
+    const size_t G = (size_t)g.ny * g.nx;
+    CUDA_TRY(c, ensure(c->stash2, (size_t)c->n_sites * ncol * win2 * sizeof(float2), false, s));
+    CUDA_TRY(c, ensure(c->cols, (size_t)std::max(c->geo.Bp1, c->geo.Bp2) * G * sizeof(float2), false, s));
+    const MsPlan plan = plan_for(c, ncol, c->shift2);
+    int first = g.nz - 1;
+    for (auto& sd : c->sites) first = std::min(first, (int)sd.plane);
+    // start: G^{-1/2} constant, forward row FFT, then the first propagator
+    {
+        MsRowArgs a{};
+        a.cols = (float2*)c->cols.p;
+        a.init = 1;
+        a.init_val = (float)(1.0 / std::sqrt((double)G));
+        a.do_fft = 1;
+        a.win = g.win;
+        a.sites = (const SiteDev*)c->sites_d.p;
+        a.site_ids = (const int32_t*)c->plane_ids_d.p;
+        a.stash = (float2*)c->stash2.p;
+        CUDA_TRY(c, bip_ms_row_pass(plan, a, s));
+        CUDA_TRY(c, bip_ms_col_pass(plan, (float2*)c->cols.p, s));
+    }
+    for (int j = g.nz - 1; j >= first; --j) {
+        MsRowArgs a{};
+        a.cols = (float2*)c->cols.p;
+        a.do_ifft = 1;
+        a.v_pre = V + (size_t)j * G;
+        a.do_fft = j > first;
+        a.sites = (const SiteDev*)c->sites_d.p;
+        a.site_ids = (const int32_t*)c->plane_ids_d.p + c->plane_off[j];
+        a.n_sites = c->plane_off[j + 1] - c->plane_off[j];
+        a.win = g.win;
+        a.stash = (float2*)c->stash2.p;
+        CUDA_TRY(c, bip_ms_row_pass(plan, a, s));
+        if (j > first) CUDA_TRY(c, bip_ms_col_pass(plan, (float2*)c->cols.p, s));
+    }
+    c->s2 = true;
+    c->sig2 = site_signature(c->sites);
+    return BIP_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// the map (Algorithm 5, per-site part)
+
+namespace {
+
+bip_status check_map_args(bip_ctx* c, const void* H, const double* scans, int32_t P, const void* out) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (!c->s1 || !c->s2 || c->sig1 != c->sig2)
+        return fail(c, BIP_ERR_INVALID_ARG, "bip_build_s1 and bip_build_s2 must run first on the same sites");
+    if (!H || !scans || !out) return fail(c, BIP_ERR_INVALID_ARG, "null pointer argument");
+    if (P < 1) return fail(c, BIP_ERR_INVALID_ARG, "P must be >= 1");
+    for (int i = 0; i < 2 * P; ++i)
+        if (!std::isfinite(scans[i])) return fail(c, BIP_ERR_INVALID_ARG, "scan position is not finite");
+    return BIP_OK;
+}
+
+// conservative test: can any scan with y in [y0, y1] and x in [x0, x1] lie
+// inside the crop window of site (ty, tx)?
+bool box_meets_crop(double y0, double y1, double x0, double x1, double ty, double tx, const bip_config& g) {
+    auto axis = [](double lo, double hi, double t, int n, int f) {
+        const double half = 0.5 * n / f;
+        for (int k = -2; k <= 2; ++k) {
+            const double a = t - half + (double)k * n, b = t + half + (double)k * n;
+            if (hi >= a && lo < b) return true;
+        }
+        return false;
+    };
+    return axis(y0, y1, ty, g.ny, g.fy) && axis(x0, x1, tx, g.nx, g.fx);
+}
+
+bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, float* partial_out,
+                   double* map_out, cudaStream_t s) {
+    const bip_config& g = c->cfg;
+    const BipGeometry& geo = c->geo;
+    const int K = g.win * g.win;
+    const int Bpad = c->Bpad, Dpad = c->Dpad;
+    const int nch = c->nch_max;
+    const bool tc = c->prec == BIP_PREC_SPLIT_BF16;
+    const int tile = tc ? kScanTileTc : kScanTile;
+    const int n_tiles = (P + tile - 1) / tile;
+
+    CUDA_TRY(c, ensure(c->scans_d, (size_t)P * 2 * sizeof(double), false, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->scans_d.p, scans, (size_t)P * 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+    const int Ppad = n_tiles * tile;
+    CUDA_TRY(c, ensure(c->ct, (size_t)Ppad * Bpad * sizeof(float2), false, s));
+    size_t ct_plane = (size_t)Ppad * Bpad;
+    if (tc) CUDA_TRY(c, ensure(c->ctb, 4 * ct_plane * sizeof(uint16_t), true, s));
+    CUDA_TRY(c, bip_illumination((const double*)c->scans_d.p, P, (const int2*)c->hbeam.p,
+                                 (const double2*)c->coef.p, geo.B, Bpad, g.ny, g.nx, (float2*)c->ct.p,
+                                 tc ? (uint16_t*)c->ctb.p : nullptr, ct_plane, s));
+
+    float* partial = partial_out;
+    if (!partial) {
+        CUDA_TRY(c, ensure(c->partial, (size_t)c->n_sites * P * sizeof(float), false, s));
+        partial = (float*)c->partial.p;
+    }
+
+    // scan-tile bounding boxes (host)
+    std::vector<double> bb((size_t)n_tiles * 4);
+    for (int t = 0; t < n_tiles; ++t) {
+        double y0 = INFINITY, y1 = -INFINITY, x0 = INFINITY, x1 = -INFINITY;
+        for (int p = t * tile; p < std::min(P, (t + 1) * tile); ++p) {
+            y0 = std::min(y0, scans[2 * p]);
+            y1 = std::max(y1, scans[2 * p]);
+            x0 = std::min(x0, scans[2 * p + 1]);
+            x1 = std::max(x1, scans[2 * p + 1]);
+        }
+        bb[4 * t] = y0; bb[4 * t + 1] = y1; bb[4 * t + 2] = x0; bb[4 * t + 3] = x1;
+    }
+
+    const int SB = std::min(c->n_sites, 8);
+    const size_t rowsA = Dpad, rowsB = (size_t)nch * Bpad;
+    const size_t perA = rowsA * K, perB = rowsB * K;
+    const size_t perMt = (size_t)Bpad * nch * Dpad, perQ = (size_t)Bpad * Bpad;
+    if (!tc) {
+        CUDA_TRY(c, ensure(c->opA32, SB * perA * sizeof(float2), true, s));
+        CUDA_TRY(c, ensure(c->opB32, SB * perB * sizeof(float2), true, s));
+        CUDA_TRY(c, ensure(c->mt32, SB * perMt * sizeof(float2), true, s));
+        CUDA_TRY(c, ensure(c->q32, SB * perQ * sizeof(float2), true, s));
+    } else {
+        return fail(c, BIP_ERR_UNSUPPORTED, "split-BF16 contraction not built");
+    }
+
+    // work lists for all batches, uploaded once
+    std::vector<int32_t>& work = c->work_h;
+    work.clear();
+    std::vector<int> batch_off;
+    for (int b0 = 0; b0 < c->n_sites; b0 += SB) {
+        batch_off.push_back((int)work.size() / 2);
+        for (int bs = 0; bs < std::min(SB, c->n_sites - b0); ++bs) {
+            const SiteDev& sd = c->sites[b0 + bs];
+            for (int t = 0; t < n_tiles; ++t)
+                if (box_meets_crop(bb[4 * t], bb[4 * t + 1], bb[4 * t + 2], bb[4 * t + 3], sd.ty, sd.tx, g)) {
+                    work.push_back(bs);
+                    work.push_back(t);
+                }
+        }
+    }
+    batch_off.push_back((int)work.size() / 2);
+    CUDA_TRY(c, upload(c->work_d, work, s));
+
+    int bi = 0;
+    for (int b0 = 0; b0 < c->n_sites; b0 += SB, ++bi) {
+        const int nb = std::min(SB, c->n_sites - b0);
+        const int32_t* ids = (const int32_t*)c->seq_ids_d.p + b0;
+        // S2 windows -> coupling A operand, S1 windows x H_n -> B operand
+        GatherArgs ga{};
+        ga.n_sites = nb;
+        ga.site_ids = ids;
+        ga.sites = (const SiteDev*)c->sites_d.p;
+        ga.win = g.win; ga.ny = g.ny; ga.nx = g.nx; ga.K = K;
+        ga.magnitude = g.recon == BIP_RECON_MAGNITUDE;
+        ga.ey = (const float2*)c->ey.p;
+        ga.ex = (const float2*)c->ex.p;
+        GatherArgs g2 = ga;
+        g2.Bp = geo.Bp2; g2.n_targets = geo.n_det; g2.rows_pad = Dpad;
+        g2.stash = (const float2*)c->stash2.p;
+        g2.ell = EllDev{c->ell2_k, (const int32_t*)c->ell2_idx.p, (const float*)c->ell2_w.p};
+        g2.h_t = (const int2*)c->hdet.p;
+        g2.tilt_sign = -1;
+        g2.nch = 0;
+        g2.out_c64 = (float2*)c->opA32.p;
+        g2.site_stride = (int64_t)perA;
+        CUDA_TRY(c, bip_gather(g2, s));
+        GatherArgs g1 = ga;
+        g1.Bp = geo.Bp1; g1.n_targets = geo.B; g1.rows_pad = Bpad;
+        g1.stash = (const float2*)c->stash1.p;
+        g1.ell = EllDev{c->ell1_k, (const int32_t*)c->ell1_idx.p, (const float*)c->ell1_w.p};
+        g1.h_t = (const int2*)c->hbeam.p;
+        g1.tilt_sign = +1;
+        g1.nch = nch;
+        g1.H = (const float2*)H;
+        g1.out_c64 = (float2*)c->opB32.p;
+        g1.site_stride = (int64_t)perB;
+        CUDA_TRY(c, bip_gather(g1, s));
+        // coupling M = S2^T diag(H) S1, stored transposed for the Gram step
+        CGemmArgs A{};
+        A.M = geo.n_det; A.N = (int)rowsB; A.K = K;
+        A.A = (const float2*)c->opA32.p; A.lda = K; A.strideA = (int64_t)perA;
+        A.Bm = (const float2*)c->opB32.p; A.ldb = K; A.strideB = (int64_t)perB;
+        A.batch = nb;
+        A.epi = 1;
+        A.C = (float2*)c->mt32.p; A.ldc = (int64_t)nch * Dpad; A.strideC = (int64_t)perMt;
+        A.ep_B = Bpad; A.ep_Dp = Dpad;
+        CUDA_TRY(c, bip_cgemm_simt(A, s));
+        // Gram Q = sum_n M^(n)H M^(n)
+        CGemmArgs Bq{};
+        Bq.M = Bpad; Bq.N = Bpad; Bq.K = nch * Dpad;
+        Bq.A = (const float2*)c->mt32.p; Bq.lda = (int64_t)nch * Dpad; Bq.strideA = (int64_t)perMt;
+        Bq.Bm = Bq.A; Bq.ldb = Bq.lda; Bq.strideB = Bq.strideA;
+        Bq.conjA = 1;
+        Bq.batch = nb;
+        Bq.epi = 0;
+        Bq.C = (float2*)c->q32.p; Bq.ldc = Bpad; Bq.strideC = (int64_t)perQ;
+        CUDA_TRY(c, bip_cgemm_simt(Bq, s));
+        // quadratic form over the site's crop-window scan tiles
+        QuadArgs q{};
+        q.Bpad = Bpad;
+        q.Q = (const float2*)c->q32.p; q.strideQ = (int64_t)perQ;
+        q.Ct = (const float2*)c->ct.p;
+        q.work = (const int32_t*)c->work_d.p + 2 * batch_off[bi];
+        q.n_work = batch_off[bi + 1] - batch_off[bi];
+        q.tile = tile;
+        q.P = P;
+        q.scans = (const double*)c->scans_d.p;
+        q.sites = (const SiteDev*)c->sites_d.p;
+        q.site_ids = ids;
+        q.ny = g.ny; q.nx = g.nx; q.fy = g.fy; q.fx = g.fx;
+        q.scale = (float)(g.fy * g.fx);
+        q.partial = partial;
+        CUDA_TRY(c, bip_quadform_simt(q, s));
+    }
+    if (map_out) {
+        CUDA_TRY(c, bip_reduce_sites(partial, c->n_sites, P, (const double*)c->scans_d.p,
+                                     (const SiteDev*)c->sites_d.p, g.ny, g.nx, g.fy, g.fx, map_out, s));
+    } else {
+        CUDA_TRY(c, bip_zero_outside(partial, c->n_sites, P, (const double*)c->scans_d.p,
+                                     (const SiteDev*)c->sites_d.p, g.ny, g.nx, g.fy, g.fx, s));
+    }
+    return BIP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bip_status bip_coreloss_map(bip_ctx* c, const void* H, const double* scan_px, int32_t P, double* map_out,
+                            void* stream) {
+    bip_status st = check_map_args(c, H, scan_px, P, map_out);
+    if (st != BIP_OK) return st;
+    return run_map(c, H, scan_px, P, nullptr, map_out, (cudaStream_t)stream);
+}
+
+bip_status bip_coreloss_sites(bip_ctx* c, const void* H, const double* scan_px, int32_t P, float* partial_out,
+                              void* stream) {
+    bip_status st = check_map_args(c, H, scan_px, P, partial_out);
+    if (st != BIP_OK) return st;
+    return run_map(c, H, scan_px, P, partial_out, nullptr, (cudaStream_t)stream);
+}
+
+bip_status bip_coreloss_cube(bip_ctx* c, const void* H, const double* scan_px, int32_t P, float* cube_out,
+                             void* stream) {
+    (void)stream;
+    bip_status st = check_map_args(c, H, scan_px, P, cube_out);
+    if (st != BIP_OK) return st;
+    return fail(c, BIP_ERR_UNSUPPORTED, "the 4D cube is not implemented in this build");
+}
+
+bip_status bip_copy_stash(bip_ctx* c, int32_t which, int32_t site, void* out, void* stream) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (!out) return fail(c, BIP_ERR_INVALID_ARG, "out is null");
+    if (which != 1 && which != 2) return fail(c, BIP_ERR_INVALID_ARG, "which must be 1 or 2");
+    if ((which == 1 && !c->s1) || (which == 2 && !c->s2)) return fail(c, BIP_ERR_INVALID_ARG, "matrix not built");
+    if (site < 0 || site >= c->n_sites) return fail(c, BIP_ERR_INVALID_ARG, "site out of range");
+    const int ncol = which == 1 ? c->geo.Bp1 : c->geo.Bp2;
+    const size_t n = (size_t)ncol * c->cfg.win * c->cfg.win;
+    const float2* src = (const float2*)(which == 1 ? c->stash1.p : c->stash2.p) + (size_t)site * n;
+    CUDA_TRY(c, cudaMemcpyAsync(out, src, n * sizeof(float2), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return BIP_OK;
+}
+
+bip_status bip_site_windows(bip_ctx* c, int32_t site, void* s1_out, void* s2_out, void* stream) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (!c->s1 || !c->s2 || c->sig1 != c->sig2)
+        return fail(c, BIP_ERR_INVALID_ARG, "bip_build_s1 and bip_build_s2 must run first on the same sites");
+    if (site < 0 || site >= c->n_sites) return fail(c, BIP_ERR_INVALID_ARG, "site out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bip_config& g = c->cfg;
+    const int K = g.win * g.win;
+    GatherArgs ga{};
+    ga.n_sites = 1;
+    ga.site_ids = (const int32_t*)c->seq_ids_d.p + site;
+    ga.sites = (const SiteDev*)c->sites_d.p;
+    ga.win = g.win; ga.ny = g.ny; ga.nx = g.nx; ga.K = K;
+    ga.magnitude = g.recon == BIP_RECON_MAGNITUDE;
+    ga.ey = (const float2*)c->ey.p;
+    ga.ex = (const float2*)c->ex.p;
+    if (s1_out) {
+        GatherArgs a = ga;
+        a.Bp = c->geo.Bp1; a.n_targets = c->geo.B; a.rows_pad = c->geo.B;
+        a.stash = (const float2*)c->stash1.p;
+        a.ell = EllDev{c->ell1_k, (const int32_t*)c->ell1_idx.p, (const float*)c->ell1_w.p};
+        a.h_t = (const int2*)c->hbeam.p;
+        a.tilt_sign = +1;
+        a.out_c64 = (float2*)s1_out;
+        a.site_stride = (int64_t)c->geo.B * K;
+        CUDA_TRY(c, bip_gather(a, s));
+    }
+    if (s2_out) {
+        GatherArgs a = ga;
+        a.Bp = c->geo.Bp2; a.n_targets = c->geo.n_det; a.rows_pad = c->geo.n_det;
+        a.stash = (const float2*)c->stash2.p;
+        a.ell = EllDev{c->ell2_k, (const int32_t*)c->ell2_idx.p, (const float*)c->ell2_w.p};
+        a.h_t = (const int2*)c->hdet.p;
+        a.tilt_sign = -1;
+        a.out_c64 = (float2*)s2_out;
+        a.site_stride = (int64_t)c->geo.n_det * K;
+        CUDA_TRY(c, bip_gather(a, s));
+    }
+    return BIP_OK;
+}
+
+bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_out, void* stream) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    (void)H; (void)site; (void)m_out; (void)stream;
+    return fail(c, BIP_ERR_UNSUPPORTED, "coupling export not implemented yet");
+}
+
+}  // extern "C"

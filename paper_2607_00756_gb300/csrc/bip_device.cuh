@@ -1,0 +1,20 @@
+// Device helpers shared by several kernels of the map path.
+#pragma once
+
+#include <cuda_runtime.h>
+
+// Crop mask of Sec. 2.2.4: a site at pixel position (ty, tx) contributes to
+// the scan at (ry, rx) when the minimum-image offset lies in
+// [-N/(2f), N/(2f)) on both axes.  FP64 so the decision matches a host
+// FP64 evaluation of the same formula.
+__device__ __forceinline__ bool in_crop(double ry, double rx, double ty, double tx, int ny, int nx, int fy,
+                                        int fx) {
+    double d = ry - ty;
+    d -= ny * floor((d + 0.5 * ny) / ny);
+    const double hy = 0.5 * ny / fy;
+    if (!(d >= -hy && d < hy)) return false;
+    d = rx - tx;
+    d -= nx * floor((d + 0.5 * nx) / nx);
+    const double hx = 0.5 * nx / fx;
+    return d >= -hx && d < hx;
+}

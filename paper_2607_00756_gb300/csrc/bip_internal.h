@@ -1,0 +1,177 @@
+// Internal declarations of the BiP-PRISM library: context, geometry and the
+// launchers of every CUDA kernel.  Host code only (no device code here).
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bip.h"
+
+// ---------------------------------------------------------------------------
+// host geometry (FP64), built once per context
+
+struct BipGeometry {
+    double lambda = 0.0;      // electron wavelength, Angstrom
+    double sigma = 0.0;       // interaction constant, rad/(V*Angstrom)
+    int n_full = 0;           // aperture beams before subsampling
+    int B = 0, n_det = 0, Bp1 = 0, Bp2 = 0;
+    std::vector<int32_t> h_beam, h_det;            // [B*2], [n_det*2]  (y, x)
+    std::vector<int32_t> p1, p2;                   // parent positions in the lists
+    std::vector<double> w1, w2;                    // [B*Bp1], [n_det*Bp2]
+    std::vector<std::complex<double>> psi_beam;    // Psi(h_b)
+    double psi_norm = 0.0;                         // sqrt(G sum_aperture |Psi|^2)
+};
+
+bip_status bip_build_geometry(const bip_config& cfg, BipGeometry& g, std::string& err);
+
+// Sibson weights of `queries` against `parents` (integer beam indices,
+// physical scale 1/ly, 1/lx); dense [nq * np] row-major.
+void bip_sibson_weights(const std::vector<int32_t>& parents, const std::vector<int32_t>& queries,
+                        double ly, double lx, std::vector<double>& w);
+
+// ---------------------------------------------------------------------------
+// device-side tables shared by several kernels
+
+struct SiteDev {            // one ionized site, as the kernels see it
+    int32_t oy, ox;         // window origin (unwrapped pixel index)
+    int32_t plane;          // slice index
+    int32_t nch;            // channels
+    int32_t ch_off;         // first channel in H
+    int32_t pad_;
+    double ty, tx;          // position in pixels
+};
+
+struct EllDev {             // sparse NNW weights, fixed nnz per target row
+    int32_t k;              // entries per row (padded with w = 0)
+    const int32_t* idx;     // [rows * k] parent index
+    const float* w;         // [rows * k] weight
+};
+
+// ---------------------------------------------------------------------------
+// kernel launchers (defined in the .cu files)
+
+// multislice.cu
+struct MsPlan {
+    int ny, nx, ncol;
+    float sigma;                    // interaction constant (FP32)
+    const float2* twy;              // [ny] exp(-2 pi i m / ny)
+    const float2* twx;              // [nx]
+    const float2* py;               // [ny] exp(-i pi lambda dz qy^2) / ny
+    const float2* px;               // [nx]
+    const int2* shift;              // [ncol] propagator shift (sy, sx)
+};
+// row pass: [inverse row FFT] -> [T_pre] -> [stash] -> [T_post] -> [row FFT]
+struct MsRowArgs {
+    float2* cols;                   // [ncol, ny, nx]
+    const float* v_pre;             // V slice applied before the stash (or null)
+    const float* v_post;            // V slice applied after the stash (or null)
+    int init;                       // 1: start from a constant field `init_val`
+    float init_val;
+    int do_ifft, do_fft;
+    const SiteDev* sites;           // sites stashed at this pass (device)
+    const int32_t* site_ids;        // their indices into the stash
+    int n_sites;
+    int win;
+    float2* stash;                  // [n_sites_total, ncol, win, win]
+};
+cudaError_t bip_ms_row_pass(const MsPlan& plan, const MsRowArgs& a, cudaStream_t s);
+cudaError_t bip_ms_col_pass(const MsPlan& plan, float2* cols, cudaStream_t s);
+
+// gather.cu : window reconstruction into GEMM operands
+struct GatherArgs {
+    int n_sites;                    // sites in this batch
+    const int32_t* site_ids;        // [n_sites] global site index
+    const SiteDev* sites;           // all sites
+    int win, ny, nx;
+    int Bp, n_targets, rows_pad;    // parents, targets, padded rows
+    const float2* stash;            // [n_sites_total, Bp, win, win]
+    EllDev ell;                     // weights of the targets
+    const int2* h_t;                // [n_targets] target beams (y, x)
+    int tilt_sign;                  // +1 (S1) or -1 (S2)
+    int magnitude;                  // 1: magnitude-preserving
+    const float2* ey;               // [ny] exp(+2 pi i m / ny)
+    const float2* ex;               // [nx]
+    // channel expansion (S1 side): out row (n * rows_pad + t) = H_n * S
+    int nch;                        // 0: no channel product (S2 side)
+    const float2* H;                // [sum nch, win, win]
+    // outputs (one of the two layouts)
+    float2* out_c64;                // [n_sites][rows_total][K] complex64
+    uint16_t* out_bf16;             // [n_sites][4 planes][rows_total][K]  (re_hi, re_lo, im_hi, im_lo)
+    int64_t site_stride;            // elements per site in the output
+    int K;                          // window pixels (row length)
+};
+cudaError_t bip_gather(const GatherArgs& a, cudaStream_t s);
+
+// gemm_simt.cu : FP32 complex GEMMs, C[m][n] = sum_k op(A[m][k]) B[n][k]
+struct CGemmArgs {
+    int M, N, K;                    // complex sizes (K multiple of 16)
+    const float2* A; int64_t lda, strideA;   // row-major [M][lda], batch stride
+    const float2* Bm; int64_t ldb, strideB;
+    int conjA;
+    int batch;
+    // epilogue
+    int epi;                        // 0: C row-major; 1: transposed to Mt[n%Bp][(n/Bp)*Dp + m]
+    float2* C; int64_t ldc, strideC;
+    int ep_B, ep_Dp;                // epilogue 1 geometry
+};
+cudaError_t bip_cgemm_simt(const CGemmArgs& a, cudaStream_t s);
+
+// stage C: per (site, scan tile) quadratic form f_yf_x Re(c^H Q c)
+struct QuadArgs {
+    int Bpad;                       // padded beam count (multiple of 64)
+    const float2* Q;                // [n_sites][Bpad][Bpad] per-site Q (complex)
+    int64_t strideQ;
+    const float2* Ct;               // [P][Bpad] c_b(rho), complex
+    const int32_t* work;            // [n_work][2] (site index in batch, scan tile)
+    int n_work;
+    int tile;                       // scans per tile
+    int P;
+    const double* scans;            // [P][2]
+    const SiteDev* sites;
+    const int32_t* site_ids;        // batch -> global site index
+    int ny, nx, fy, fx;
+    float scale;                    // f_y f_x
+    float* partial;                 // [n_sites_total][P]
+};
+cudaError_t bip_quadform_simt(const QuadArgs& a, cudaStream_t s);
+
+// illumination table Ct[rho][b] (complex64) and/or its split-BF16 planes
+// (4 planes of `plane` elements: re_hi, re_lo, im_hi, im_lo)
+cudaError_t bip_illumination(const double* scans, int P, const int2* h_beam, const double2* coef,
+                             int B, int Bpad, int ny, int nx, float2* Ct, uint16_t* Ct_bf16,
+                             size_t plane, cudaStream_t s);
+
+// reduce.cu : map[rho] = Neumaier sum over sites of the in-crop partials
+cudaError_t bip_reduce_sites(const float* partial, int n_sites, int P, const double* scans,
+                             const SiteDev* sites, int ny, int nx, int fy, int fx,
+                             double* map_out, cudaStream_t s);
+cudaError_t bip_zero_outside(float* partial, int n_sites, int P, const double* scans,
+                             const SiteDev* sites, int ny, int nx, int fy, int fx, cudaStream_t s);
+
+// gemm_tc.cu : tcgen05 split-BF16 complex GEMMs
+struct TcGemmArgs {
+    int M, N, K;                    // complex sizes; M, N multiples of 128, K of 32
+    const uint16_t* A;              // [batch][4][M][K] planes re_hi, re_lo, im_hi, im_lo
+    const uint16_t* Bm;             // [batch][4][N][K]
+    int64_t strideA, strideB;       // elements per batch entry
+    int conjA;
+    int batch;
+    int epi;                        // 0: C complex64 [M][N]; 1: Mt bf16 planes; 2: Q bf16 planes
+    float2* C; int64_t ldc, strideC;
+    uint16_t* Cb; int64_t strideCb; // bf16 planes output
+    int ep_B, ep_Dp, ep_rows, ep_K; // epilogue geometry
+    int* err_flag;                  // device word set on a wait timeout
+};
+cudaError_t bip_cgemm_tc(const TcGemmArgs& a, cudaStream_t s);
+struct TcQuadArgs {
+    QuadArgs q;                     // sizes, work list, output
+    const uint16_t* Qb;             // [n_sites][4][Bpad][Bpad]
+    const uint16_t* Ctb;            // [4][Ppad][Bpad]
+    int Ppad;
+    int* err_flag;
+};
+cudaError_t bip_quadform_tc(const TcQuadArgs& a, cudaStream_t s);

@@ -1,0 +1,110 @@
+"""C-ABI library checks that need no GPU: it builds, loads, exports every
+declared entry point, and its host geometry (FP64 beams, parents, Sibson
+weights) agrees with the oracle's independent implementation."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import geometry as G, physics as ph
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2607_00756_gb300 import build
+    build.build()
+    from paper_2607_00756_gb300 import capi as c
+    return c
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "bip.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:bip_status|const char\*)\s+(bip_\w+)\s*\(", text, re.M)))
+
+
+def test_exports_every_declared_symbol(capi):
+    names = declared_functions()
+    assert len(names) >= 14
+    lib = ctypes.CDLL(capi.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _cfgs():
+    c1 = synth.config1()
+    return [c1, synth.config2(), synth.tiny_config(ny=64, nx=64, win=64),
+            c1.replace(name="aniso", ny=64, nx=128, ly=6.0, lx=10.0, fy=1, fx=2, win=32),
+            c1.replace(name="rings", nrad1=3, nrad2=4, nang1=5, nang2=7),
+            c1.replace(name="aberrated", defocus=-35.0, cs=1e4)]
+
+
+@pytest.mark.parametrize("cfg", _cfgs(), ids=lambda c: c.name)
+def test_geometry_matches_oracle(capi, cfg):
+    ctx = capi.bip_create(capi.make_config(cfg))
+    try:
+        g = capi.bip_get_geometry(ctx)
+        og = G.Geometry(cfg, ph.wavelength(cfg.e0))
+        assert np.array_equal(g["h_beam"], og.h_beam)
+        assert np.array_equal(g["h_det"], og.h_det)
+        assert np.array_equal(g["p1"], og.p1)
+        assert np.array_equal(g["p2"], og.p2)
+        assert np.max(np.abs(g["w1"] - og.w1)) < 1e-12
+        assert np.max(np.abs(g["w2"] - og.w2)) < 1e-12
+    finally:
+        capi.bip_destroy(ctx)
+
+
+def test_config2_sizes(capi):
+    """300 keV, 25 mrad, 40 A, f = 4: 505 retained beams of 8093, 1305
+    detector beams in 40 mrad, 61 parents each at n_radial = 4."""
+    ctx = capi.bip_create(capi.make_config(synth.config2()))
+    try:
+        assert capi.bip_query(ctx) == (505, 1305, 61, 61, 0)
+    finally:
+        capi.bip_destroy(ctx)
+
+
+@pytest.mark.parametrize("change,status", [
+    (dict(ny=96), "BIP_ERR_SHAPE"),
+    (dict(nx=2048), "BIP_ERR_SHAPE"),
+    (dict(win=40), "BIP_ERR_SHAPE"),
+    (dict(win=128), "BIP_ERR_SHAPE"),
+    (dict(fy=3), "BIP_ERR_SHAPE"),
+    (dict(alpha=0.2), "BIP_ERR_SHAPE"),
+    (dict(nz=0), "BIP_ERR_INVALID_ARG"),
+    (dict(e0=-1.0), "BIP_ERR_INVALID_ARG"),
+    (dict(nang1=0), "BIP_ERR_INVALID_ARG"),
+])
+def test_create_rejects_bad_config(capi, change, status):
+    cfg = synth.config1().replace(**change)
+    with pytest.raises(capi.BipError) as e:
+        capi.bip_create(capi.make_config(cfg))
+    assert capi.STATUS[e.value.status] == status
+
+
+def test_calls_out_of_order_return_errors(capi):
+    ctx = capi.bip_create(capi.make_config(synth.config1()))
+    try:
+        lib = capi.lib()
+        scans = np.zeros((4, 2))
+        sp = scans.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        dummy = ctypes.c_void_p(16)
+        assert lib.bip_coreloss_map(ctx, dummy, sp, 4, dummy, None) == 1
+        assert "bip_build_s1" in capi.bip_last_error(ctx)
+        assert lib.bip_copy_stash(ctx, 1, 0, dummy, None) == 1
+        assert lib.bip_set_precision(ctx, 7) == 1
+        assert lib.bip_build_s1(ctx, None, None, 0, None) == 1
+        atoms = capi.make_atoms(np.array([[1.0, 1.0, 9.0]]), np.array([3]))
+        assert lib.bip_build_s1(ctx, dummy, atoms, 1, None) == 1      # slice 9 >= nz
+        assert "slice" in capi.bip_last_error(ctx)
+        atoms = capi.make_atoms(np.array([[1.0, 1.0, 0.0]]), np.array([0]))
+        assert lib.bip_build_s1(ctx, dummy, atoms, 1, None) == 1      # nothing ionized
+    finally:
+        capi.bip_destroy(ctx)
+    assert capi.lib().bip_last_error(None) == b"null context"
+    assert capi.lib().bip_destroy(None) == 1

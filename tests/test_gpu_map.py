@@ -1,0 +1,153 @@
+"""GPU parity of the CUDA path against the FP64 oracle, stage by stage and
+end to end, through the C ABI.  Tolerances: rel L2 <= 1e-4 for the FP32
+path (and for the stashed / reconstructed windows, 2e-5 max-relative), the
+figures fixed for this method's FP32 maps."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import bip as obip
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2607_00756_gb300 import build
+    build.build()
+    from paper_2607_00756_gb300.context import BipContext
+    return BipContext
+
+
+def gpu_run(BipContext, cfg, sp, prec="fp32", recon=None, scans=None):
+    dev = torch.device("cuda:0")
+    V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
+    H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+    ctx = BipContext(cfg, prec=prec, recon=recon)
+    ctx.build(V, sp.atoms, sp.nch)
+    scans = sp.scans if scans is None else scans
+    m = ctx.map(H, scans).cpu().numpy()
+    parts = ctx.sites(H, scans).cpu().numpy()
+    torch.cuda.synchronize()
+    return ctx, m, parts, H
+
+
+@pytest.fixture(scope="module")
+def c1(lib):
+    cfg = synth.config1()
+    sp = synth.make_specimen(cfg)
+    pr = obip.make_problem(sp)
+    ref = obip.bip_map(pr, keep_stages=True)
+    return cfg, sp, pr, ref
+
+
+def test_stash_parity(lib, c1):
+    """Stashed de-tilted parent windows of S1 and S2 (Eq. smatrix-advance,
+    Eq. s2, Eq. part-basis) against the oracle, every site."""
+    cfg, sp, pr, ref = c1
+    ctx, *_ = gpu_run(lib, cfg, sp)
+    for k in range(len(pr.ion)):
+        for which, key in ((1, "stash1"), (2, "stash2")):
+            got = ctx.stash(which, k).cpu().numpy()
+            want = ref.stages[k][key]
+            assert got.shape == want.shape
+            assert np.max(np.abs(got - want)) < 2e-5 * np.max(np.abs(want)), (k, which)
+
+
+@pytest.mark.parametrize("recon", ["magnitude", "complex"])
+def test_window_reconstruction_parity(lib, c1, recon):
+    """Reconstructed windows S1^b and S2^d (Eq. window-recon, magpreserve)."""
+    cfg, sp, pr, ref = c1
+    cref = ref if recon == "magnitude" else obip.bip_map(pr, mode="complex", keep_stages=True)
+    ctx, *_ = gpu_run(lib, cfg, sp, recon=recon)
+    for k in range(len(pr.ion)):
+        s1, s2 = ctx.windows(k)
+        s1, s2 = s1.cpu().numpy(), s2.cpu().numpy()
+        w1, w2 = cref.stages[k]["S1w"], cref.stages[k]["S2w"]
+        assert np.max(np.abs(s1 - w1)) < 2e-5 * np.max(np.abs(w1))
+        assert np.max(np.abs(s2 - w2)) < 2e-5 * np.max(np.abs(w2))
+
+
+def test_map_fp32_config1(lib, c1):
+    """The FP32 map and its per-site contributions (Algorithm 5)."""
+    cfg, sp, pr, ref = c1
+    _, m, parts, _ = gpu_run(lib, cfg, sp)
+    assert rel(m, ref.map) < 1e-4
+    for k in range(len(pr.ion)):
+        assert rel(parts[k], ref.partials[k]) < 1e-4
+    # zero outside the crop mask, exactly
+    for k in range(len(pr.ion)):
+        outside = ~obip.crop_mask(pr, k, pr.scans)
+        assert np.all(parts[k][outside] == 0.0)
+
+
+def test_map_complex_mode(lib, c1):
+    cfg, sp, pr, ref = c1
+    want = obip.bip_map(pr, mode="complex").map
+    _, m, _, _ = gpu_run(lib, cfg, sp, recon="complex")
+    assert rel(m, want) < 1e-4
+
+
+def _edge_specimen():
+    """Sites in every plane (first and last included), windows that wrap
+    around the grid, 21 sites (not a multiple of the site batch), one or
+    three channels per site, and a ragged scan list that wraps the cell."""
+    cfg = synth.config1().replace(name="edge", ion_slices=(0, 5), ion_cells=(0, 4))
+    sp = synth.make_specimen(cfg)
+    keep = np.nonzero(sp.nch > 0)[0]
+    rng = np.random.default_rng(5)
+    pick = np.sort(rng.choice(keep, size=21, replace=False))
+    nch = np.zeros_like(sp.nch)
+    nch[pick] = 3
+    nch[pick[::4]] = 1
+    # H rows for the chosen sites in order; one-channel sites keep m = 0
+    H_all = sp.H.reshape(len(keep), 3, cfg.win, cfg.win)
+    rows = []
+    for a in pick:
+        h = H_all[np.searchsorted(keep, a)]
+        rows.extend([h[1]] if nch[a] == 1 else list(h))
+    scans = np.stack([np.linspace(-20.0, 140.0, 101), np.linspace(130.0, -5.0, 101)], axis=1)
+    return cfg, synth.Specimen(cfg=cfg, atoms=sp.atoms, nch=nch, V=sp.V, H=np.stack(rows), scans=scans)
+
+
+def test_map_edge_cases(lib):
+    cfg, sp = _edge_specimen()
+    pr = obip.make_problem(sp)
+    assert set(pr.plane.tolist()) == {0, 1, 2, 3, 4}
+    assert np.any(pr.tau_px < cfg.win / 2) and len(pr.ion) == 21
+    ref = obip.bip_map(pr)
+    _, m, parts, _ = gpu_run(lib, cfg, sp)
+    assert rel(m, ref.map) < 1e-4
+    assert rel(parts, ref.partials) < 1e-4
+
+
+def test_single_scan_single_site(lib):
+    cfg = synth.config1().replace(ion_cells=(2, 3))
+    sp = synth.make_specimen(cfg)
+    sp.scans = np.array([[80.0, 78.0]])
+    pr = obip.make_problem(sp)
+    assert len(pr.ion) == 1
+    ref = obip.bip_map(pr)
+    _, m, _, _ = gpu_run(lib, cfg, sp)
+    assert abs(m[0] - ref.map[0]) < 1e-4 * abs(ref.map[0])
+
+
+def test_anisotropic_grid(lib):
+    """ny != nx, L_y != L_x, f_y != f_x, a window of 32 and sub-pixel scans."""
+    cfg = synth.config1().replace(name="aniso", ny=64, nx=128, ly=7.5, lx=10.0, cells_y=3, cells_x=4,
+                                  fy=1, fx=2, win=32, ion_cells=(1, 3), ion_slices=(1, 4),
+                                  scan_y=(10.3, 3.5, 9), scan_x=(20.7, 6.25, 7))
+    sp = synth.make_specimen(cfg)
+    pr = obip.make_problem(sp)
+    ref = obip.bip_map(pr)
+    _, m, _, _ = gpu_run(lib, cfg, sp)
+    assert rel(m, ref.map) < 1e-4
