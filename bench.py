@@ -1,0 +1,472 @@
+#!/usr/bin/env python3
+"""Benchmark of the BiP-PRISM core-loss map on GB300.
+
+Metric: atom x probe core-loss evaluations per second -- (ionized sites x
+scan positions) / time of one whole map evaluation (S1 build + S2 build +
+window reconstruction + coupling + Gram + quadratic form + site sum),
+inputs resident in HBM.  Workload: the 512^2 x 100-slice synthetic crystal
+with 1600 ionized sites (3 channels each) and 128 x 128 scans (config2 in
+synth/configs.py).  The split-BF16 path is the headline; the FP32 path is
+timed beside it and their maps are compared.
+
+Multi-GPU (torchrun): each rank evaluates an independent frozen-phonon
+configuration (its own seeded jitter), so per-GPU work is fixed (weak
+scaling); the maps are averaged over ranks with one all-reduce per step,
+the incoherent frozen-phonon average of the method.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on this machine's host cores (there is no runnable reference
+implementation of the paper).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom×probe core-loss evals/s, mixed vs FP32 path on GB300, at ≤1e-3 rel L2"
+UNIT = "atom×probe evals/s"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# workload
+
+def workload(name, rank):
+    import synth
+    cfg = synth.CONFIGS[name]()
+    if rank:
+        cfg = cfg.replace(seed=rank)          # another frozen-phonon configuration
+    sp = synth.make_specimen(cfg)
+    return cfg, sp
+
+
+def crop_counts(cfg, sp):
+    """Sum over sites of the scans inside each site's crop window."""
+    dy, dx = cfg.ly / cfg.ny, cfg.lx / cfg.nx
+    ion = np.nonzero(sp.nch > 0)[0]
+    ty = sp.atoms[ion, 0] / dy
+    tx = sp.atoms[ion, 1] / dx
+    tot = 0
+    for k in range(len(ion)):
+        ok = np.ones(len(sp.scans), bool)
+        for t, ax, n, f in ((ty[k], 0, cfg.ny, cfg.fy), (tx[k], 1, cfg.nx, cfg.fx)):
+            d = sp.scans[:, ax] - t
+            d = d - n * np.floor((d + 0.5 * n) / n)
+            ok &= (d >= -0.5 * n / f) & (d < 0.5 * n / f)
+        tot += int(ok.sum())
+    return tot
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+def algorithmic(cfg, geo_sizes, n_sites, n_crop, nch):
+    """Per-stage algorithmic work of one step (flops or bytes), the figures
+    the roofline fractions divide."""
+    B, n_det, bp1, bp2 = geo_sizes
+    K = cfg.win * cfg.win
+    G = cfg.ny * cfg.nx
+    cmac_coupling = n_det * nch * B * K * n_sites
+    cmac_gram = B * B * nch * n_det * n_sites
+    cmac_quad = B * B * n_crop
+    return {
+        "coupling": 8.0 * cmac_coupling,        # real flops (complex MAC = 8)
+        "gram": 8.0 * cmac_gram,
+        "quadform": 8.0 * cmac_quad,
+        # multislice: one read + one write of every column per pass
+        "ms_row_bytes": 16.0 * G,               # per column per pass (+ V from L2)
+        "ms_col_bytes": 16.0 * G,
+        "gather_bytes": 8.0 * K * (n_det + nch * B) * n_sites,   # operand writes
+    }
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_2607_00756_gb300 import build as pbuild
+    if rank == 0:
+        pbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2607_00756_gb300 import capi
+    from paper_2607_00756_gb300.context import BipContext
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cfg, sp = workload(args.workload, rank)
+    V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
+    H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+    atoms, nch_a, scans = sp.atoms, sp.nch, sp.scans
+    n_sites = int((nch_a > 0).sum())
+    P = len(scans)
+    nch = int(nch_a.max())
+    n_crop = crop_counts(cfg, sp)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
+    peaks, peak_kind = load_peaks()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    results = {}
+    paths = [p for p in args.paths.split(",") if p]
+    for path in paths:
+        ctx = BipContext(cfg, prec=path)
+        out = torch.empty(P, dtype=torch.float64, device=dev)
+
+        def step():
+            ctx.build(V, atoms, nch_a)
+            ctx.map(H, scans, out=out)
+            if world > 1:
+                torch.distributed.all_reduce(out)
+                out.div_(world)
+
+        try:
+            for _ in range(args.warmup):
+                step()
+        except capi.BipError as e:
+            results[path] = {"error": str(e)}
+            ctx.close()
+            continue
+        torch.cuda.synchronize()
+        barrier()
+        capi.bip_set_profiling(ctx.ctx, 1)
+        times = []
+        stream = torch.cuda.current_stream()
+        with ClockSampler(dev.index) as clk:
+            for _ in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                times.append((e0, e1))
+            torch.cuda.synchronize()
+        barrier()
+        ms = [a.elapsed_time(b) for a, b in times]
+        prof = capi.bip_get_profile(ctx.ctx)
+        capi.bip_set_profiling(ctx.ctx, 0)
+        t_step = sum(ms) / len(ms)
+        if world > 1:
+            t = torch.tensor([t_step], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            t_step = float(t.item())
+        res = {"ms_per_step": t_step, "evals_per_s": world * n_sites * P / (t_step / 1e3),
+               "profile": prof, "clocks": clk.summary(), "map": out.cpu().numpy().copy(),
+               "launches": int(sum(v[1] for v in prof.values()))}
+
+        # end to end through the C ABI with host buffers: H2D of V and H
+        # from pinned memory, the map back to the host, every step
+        if path == paths[0] and args.e2e:
+            Vh = torch.tensor(sp.V, dtype=torch.float32).pin_memory()
+            Hh = torch.tensor(sp.H, dtype=torch.complex64).pin_memory()
+            Vd = torch.empty_like(V)
+            Hd = torch.empty_like(H)
+            host_map = torch.empty(P, dtype=torch.float64).pin_memory()
+
+            def e2e_step():
+                Vd.copy_(Vh, non_blocking=True)
+                Hd.copy_(Hh, non_blocking=True)
+                ctx.build(Vd, atoms, nch_a)
+                ctx.map(Hd, scans, out=out)
+                host_map.copy_(out, non_blocking=True)
+
+            for _ in range(max(1, args.warmup // 2)):
+                e2e_step()
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(args.steps):
+                e2e_step()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            wall = (time.perf_counter() - t0) * 1e3 / args.steps
+            dev_ms = ev0.elapsed_time(ev1) / args.steps
+            t_e2e = max(wall, dev_ms)
+            res["e2e"] = {"value": world * n_sites * P / (t_e2e / 1e3), "unit": UNIT,
+                          "h2d_bytes_per_step": int(Vh.numel() * 4 + Hh.numel() * 8 + P * 16),
+                          "d2h_bytes_per_step": int(P * 8), "ms_per_step": t_e2e}
+        ctx.close()
+        results[path] = res
+
+    return cfg, sp, results, dict(n_sites=n_sites, P=P, nch=nch, n_crop=n_crop, peaks=peaks,
+                                  peak_kind=peak_kind)
+
+
+def roofline(cfg, path, res, info, geo_sizes):
+    """Roofline of the step's dominant kernel, from the live per-stage
+    event timings."""
+    prof = res["profile"]
+    alg = algorithmic(cfg, geo_sizes, info["n_sites"], info["n_crop"], info["nch"])
+    stage, (ms, n) = max(prof.items(), key=lambda kv: kv[1][0])
+    peaks = info["peaks"]
+    steps = None
+    ms_launch = ms / max(n, 1)
+    out = {"kernel": stage, "launches": n, "ms_per_launch": ms_launch}
+    if stage in ("coupling", "gram", "quadform"):
+        flops_step = alg[stage]
+        # per launch: the step's work over the step's launches of this stage
+        per_step_launches = n / res["steps"]
+        per_launch = flops_step / per_step_launches
+        if path == "split_bf16":
+            # three BF16 products per real product (hi*hi + hi*lo + lo*hi)
+            achieved = 3.0 * per_launch / (ms_launch / 1e3) / 1e12
+            peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+            out.update(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s",
+                       peak_source=f"{info['peak_kind']} bf16 sustained")
+        else:
+            achieved = per_launch / (ms_launch / 1e3) / 1e12
+            # FP32 FFMA: 152 SMs x 128 lanes x 2 flop x max SM clock
+            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            out.update(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
+                       peak_source="FP32 FMA: 152 SM x 128 lanes x 2 flop x max SM clock")
+    else:
+        key = {"ms_row": "ms_row_bytes", "ms_col": "ms_col_bytes", "gather": "gather_bytes"}.get(stage)
+        if key in ("ms_row_bytes", "ms_col_bytes"):
+            B, n_det, bp1, bp2 = geo_sizes
+            per_launch = alg[key] * (bp1 + bp2) / 2.0
+        else:
+            per_launch = alg.get(key, 0.0) / max(n / res["steps"], 1)
+        achieved = per_launch / (ms_launch / 1e3) / 1e9
+        out.update(bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
+                   peak_source=f"{info['peak_kind']} copy")
+    out["frac"] = out["achieved"] / out["peak"]
+    out["traffic"] = None
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+
+def oracle_sample(cfg, sp, n_site_sample=2, n_slice_sample=2):
+    """Times the FP64 oracle's own steps on a sample of the workload and
+    extrapolates to one full evaluation: the S1/S2 sweeps over
+    n_slice_sample slices each (all parent columns) scaled to the full
+    sweep lengths, plus reconstruction + coupling + map for n_site_sample
+    sites over all their crop-window scans, scaled to every site."""
+    from oracle import bip as obip, physics as ph
+    pr = obip.make_problem(sp)
+    geo = pr.geo
+    t0 = time.perf_counter()
+    psi = np.stack([ph.plane_wave(h, cfg.ny, cfg.nx, +1) for h in geo.h_p1])
+    for j in range(n_slice_sample):
+        psi = ph.step(psi, pr.T(j), pr.P)
+    x = np.stack([ph.plane_wave(h, cfg.ny, cfg.nx, -1) for h in geo.h_p2])
+    for j in range(cfg.nz - 1, cfg.nz - 1 - n_slice_sample, -1):
+        x = pr.T(j) * ph.propagate(x, pr.P)
+    t_sweep = time.perf_counter() - t0
+    steps_full = (int(pr.plane.max()) ) + (cfg.nz - int(pr.plane.min()))
+    t_build = t_sweep * steps_full / (2.0 * n_slice_sample)
+    C = obip.illumination(pr, geo.h_beam, geo.psi_beam, pr.scans)
+    t1 = time.perf_counter()
+    for k in range(n_site_sample):
+        iy, ix = pr.window_index(k)
+        w1 = psi[:, iy[:, None], ix[None, :]] * obip.window_phase(geo.h_p1, iy, ix, cfg.ny, cfg.nx, -1)
+        w2 = x[:, iy[:, None], ix[None, :]] * obip.window_phase(geo.h_p2, iy, ix, cfg.ny, cfg.nx, +1)
+        S1 = obip.reconstruct(w1, geo.w1, geo.h_beam, iy, ix, cfg.ny, cfg.nx, +1, cfg.recon)
+        S2 = obip.reconstruct(w2, geo.w2, geo.h_det, iy, ix, cfg.ny, cfg.nx, -1, cfg.recon)
+        M = obip.coupling(S2, pr.H[k], S1)
+        obip.site_map(M, C, obip.crop_mask(pr, k, pr.scans), cfg.fy * cfg.fx)
+    t_site = (time.perf_counter() - t1) / n_site_sample
+    n_sites = len(pr.ion)
+    t_full = t_build + n_sites * t_site
+    evals = n_sites * len(pr.scans) / t_full
+    sample = (f"oracle sweeps of {n_slice_sample} of {steps_full} S1+S2 slice steps "
+              f"({geo.p1.size}+{geo.p2.size} parent columns, {cfg.ny}^2) scaled linearly, plus "
+              f"{n_site_sample} of {n_sites} sites (reconstruction, coupling, map over their crop "
+              f"scans) scaled linearly; measured {t_sweep + n_site_sample * t_site:.1f} s")
+    return evals, sample, t_sweep + n_site_sample * t_site
+
+
+def cpu_cores():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        n = max((i.get("num_threads", 1) for i in info), default=os.cpu_count())
+        return int(max(n, os.cpu_count() or 1))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="config2")
+    ap.add_argument("--paths", default="split_bf16,fp32")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu", dest="cpu", action="store_false")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cfg, sp = workload(args.workload, 0)
+        vals = []
+        sample = ""
+        for _ in range(args.warmup):
+            oracle_sample(cfg, sp, 1, 1)
+        for _ in range(args.steps):
+            v, sample, _ = oracle_sample(cfg, sp)
+            vals.append(v)
+        v = statistics.median(vals)
+        n_sites = int((sp.nch > 0).sum())
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": n_sites * len(sp.scans) / v * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config_block(cfg, sp),
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    cfg, sp, results, info = run_gpu(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    paths = [p for p in args.paths.split(",") if p]
+    from paper_2607_00756_gb300 import capi
+    ctx = capi.bip_create(capi.make_config(cfg))
+    geo_sizes = capi.bip_query(ctx)[:4]
+    capi.bip_destroy(ctx)
+    ok = [p for p in paths if "error" not in results[p]]
+    head = ok[0]
+    res = results[head]
+    res["steps"] = args.steps
+    line = {"metric": METRIC, "value": res["evals_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"split_bf16": "bf16x3 (hi+lo) / f32 accumulate", "fp32": "f32"}[head],
+            "data": "synthetic", "config": config_block(cfg, sp)}
+    line["roofline"] = roofline(cfg, head, res, info, geo_sizes)
+    paths_out = {}
+    for p in paths:
+        r = results[p]
+        if "error" in r:
+            paths_out[p] = {"error": r["error"]}
+            continue
+        r["steps"] = args.steps
+        paths_out[p] = {"evals_per_s": r["evals_per_s"], "ms_per_step": r["ms_per_step"],
+                        "stage_ms_per_step": {k: v[0] / args.steps for k, v in r["profile"].items()},
+                        "roofline": roofline(cfg, p, r, info, geo_sizes)}
+    line["paths"] = paths_out
+    if len(ok) > 1:
+        a, b = results[ok[0]]["map"], results[ok[-1]]["map"]
+        line["accuracy"] = {f"{ok[0]}_vs_{ok[-1]}_rel_l2": float(np.linalg.norm(a - b) / np.linalg.norm(b))}
+    line["e2e"] = res.get("e2e")
+    line["gpu_launches"] = res["launches"]
+    line["clocks"] = res["clocks"]
+    if args.cpu and world == 1:
+        v, sample, secs = oracle_sample(cfg, sp)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def config_block(cfg, sp):
+    n_sites = int((sp.nch > 0).sum())
+    return {"workload": f"{cfg.name}: {cfg.ny}x{cfg.nx} grid, {cfg.nz} slices of {cfg.dz} A, "
+                        f"{cfg.e0 / 1e3:.0f} keV, {cfg.alpha * 1e3:.0f} mrad, f={cfg.fy}, "
+                        f"{n_sites} ionized sites x {len(cfg.channels)} channels, "
+                        f"{len(sp.scans)} scans, 0-{cfg.theta_det * 1e3:.0f} mrad detector",
+            "sites": n_sites, "scans": len(sp.scans), "grid": [cfg.ny, cfg.nx], "slices": cfg.nz,
+            "window": cfg.win, "recon": cfg.recon,
+            "l2": "256 MB buffer written between timed steps; working set (6.4 GB stash) >> L2"}
+
+
+if __name__ == "__main__":
+    main()

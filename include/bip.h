@@ -75,7 +75,8 @@ typedef struct {
 
 /* Simulation parameters (lengths in Angstrom, angles in rad, energy in eV).
  * Constraints checked by bip_create: ny, nx powers of two in [64, 1024];
- * fy | ny and fx | nx; win even, 2 <= win <= min(ny/fy, nx/fx); nz >= 1;
+ * fy | ny and fx | nx; win a multiple of 16 with 16 <= win <=
+ * min(ny/fy, nx/fx); nz >= 1;
  * e0 > 0; 0 < alpha; 0 < theta_det; nrad >= 0; nang >= 1; the aperture and
  * detector discs fit inside the grid's Nyquist band. */
 typedef struct {
@@ -183,6 +184,21 @@ bip_status bip_site_windows(bip_ctx* ctx, int32_t site, void* s1_out, void* s2_o
                             void* stream);
 bip_status bip_site_coupling(bip_ctx* ctx, const void* H, int32_t site, void* m_out,
                              void* stream);
+
+/* Per-stage timing of the library's own kernels.  With profiling on, every
+ * launch is bracketed by CUDA events recorded on the stream it runs on;
+ * bip_get_profile waits for them and returns, per stage, the summed device
+ * time in ms and the number of launches since profiling was (re)enabled.
+ * Stages: multislice row pass, multislice column pass, window
+ * reconstruction, coupling GEMM, Gram GEMM, quadratic form, illumination +
+ * site sum.  ms / launches: [BIP_N_STAGES] host arrays (either may be
+ * NULL).  bip_set_profiling(ctx, 1) clears earlier records. */
+enum {
+    BIP_STAGE_MS_ROW = 0, BIP_STAGE_MS_COL = 1, BIP_STAGE_GATHER = 2, BIP_STAGE_COUPLING = 3,
+    BIP_STAGE_GRAM = 4, BIP_STAGE_QUADFORM = 5, BIP_STAGE_REDUCE = 6, BIP_N_STAGES = 7
+};
+bip_status bip_set_profiling(bip_ctx* ctx, int32_t on);
+bip_status bip_get_profile(bip_ctx* ctx, double* ms, int64_t* launches);
 
 /* Text of the last error on this context ("" if none; static text if ctx
  * is NULL). */

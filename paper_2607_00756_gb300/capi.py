@@ -63,6 +63,8 @@ def _load():
         "bip_copy_stash": [VP, I32, I32, VP, VP],
         "bip_site_windows": [VP, I32, VP, VP, VP],
         "bip_site_coupling": [VP, VP, I32, VP, VP],
+        "bip_set_profiling": [VP, I32],
+        "bip_get_profile": [VP, VP, VP],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -230,6 +232,22 @@ def bip_site_coupling(ctx, H, site, out, stream=None):
     _check("bip_site_coupling", ctx, _lib.bip_site_coupling(ctx, _dev(H, torch.complex64, "H"), site,
                                                              _dev(out, torch.complex64, "out"), _stream(stream)))
     return out
+
+
+N_STAGES = 7
+STAGES = ["ms_row", "ms_col", "gather", "coupling", "gram", "quadform", "reduce"]
+
+
+def bip_set_profiling(ctx, on):
+    _check("bip_set_profiling", ctx, _lib.bip_set_profiling(ctx, int(bool(on))))
+
+
+def bip_get_profile(ctx):
+    ms = np.zeros(N_STAGES, np.float64)
+    n = np.zeros(N_STAGES, np.int64)
+    _check("bip_get_profile", ctx, _lib.bip_get_profile(ctx, ms.ctypes.data_as(ctypes.c_void_p),
+                                                         n.ctypes.data_as(ctypes.c_void_p)))
+    return {STAGES[i]: (float(ms[i]), int(n[i])) for i in range(N_STAGES)}
 
 
 def bip_last_error(ctx):

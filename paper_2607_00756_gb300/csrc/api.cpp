@@ -53,6 +53,13 @@ struct bip_ctx {
     DevBuf opA16, opB16, mt16, q16;     // split-BF16 path (zeroed at allocation)
     DevBuf errflag;
     std::vector<int32_t> work_h;
+
+    // per-stage event timing
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_rec;
+    int64_t launches[BIP_N_STAGES] = {0};
 };
 
 namespace {
@@ -73,6 +80,43 @@ bip_status fail_cuda(bip_ctx* c, cudaError_t e, const char* what) {
     do {                                                    \
         cudaError_t e_ = (expr);                            \
         if (e_ != cudaSuccess) return fail_cuda(c, e_, #expr); \
+    } while (0)
+
+// Brackets one launch with events on its stream when profiling is on, and
+// counts it.  Returns the launch's error.
+struct StageTimer {
+    bip_ctx* c;
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEvent_t take() {
+        if (c->ev_used == c->ev_pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            c->ev_pool.push_back(e);
+        }
+        return c->ev_pool[c->ev_used++];
+    }
+    StageTimer(bip_ctx* c_, int st, cudaStream_t s_) : c(c_), stage(st), s(s_) {
+        c->launches[stage]++;
+        if (c->prof) {
+            e0 = take();
+            e1 = take();
+            if (e0) cudaEventRecord(e0, s);
+        }
+    }
+    ~StageTimer() {
+        if (c->prof && e0 && e1) {
+            cudaEventRecord(e1, s);
+            c->ev_rec.push_back({stage, {e0, e1}});
+        }
+    }
+};
+
+#define TIMED(c, stage, s, expr)        \
+    do {                                 \
+        StageTimer t_(c, stage, s);      \
+        CUDA_TRY(c, expr);               \
     } while (0)
 
 cudaError_t ensure(DevBuf& b, size_t bytes, bool zero = false, cudaStream_t s = nullptr) {
@@ -342,6 +386,7 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->ctb, &c->work_d, &c->partial, &c->opA32, &c->opB32, &c->mt32, &c->q32, &c->opA16,
                      &c->opB16, &c->mt16, &c->q16, &c->errflag};
     for (DevBuf* b : all) release(*b);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
     return BIP_OK;
 }
@@ -409,8 +454,8 @@ bip_status bip_build_s1(bip_ctx* c, const float* V, const bip_atom* atoms, int32
         a.n_sites = c->plane_off[j + 1] - c->plane_off[j];
         a.win = g.win;
         a.stash = (float2*)c->stash1.p;
-        CUDA_TRY(c, bip_ms_row_pass(plan, a, s));
-        if (j < last) CUDA_TRY(c, bip_ms_col_pass(plan, (float2*)c->cols.p, s));
+        TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
+        if (j < last) TIMED(c, BIP_STAGE_MS_COL, s, bip_ms_col_pass(plan, (float2*)c->cols.p, s));
     }
     c->s1 = true;
     c->sig1 = site_signature(c->sites);
@@ -441,8 +486,8 @@ bip_status bip_build_s2(bip_ctx* c, const float* V, const bip_atom* atoms, int32
         a.sites = (const SiteDev*)c->sites_d.p;
         a.site_ids = (const int32_t*)c->plane_ids_d.p;
         a.stash = (float2*)c->stash2.p;
-        CUDA_TRY(c, bip_ms_row_pass(plan, a, s));
-        CUDA_TRY(c, bip_ms_col_pass(plan, (float2*)c->cols.p, s));
+        TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
+        TIMED(c, BIP_STAGE_MS_COL, s, bip_ms_col_pass(plan, (float2*)c->cols.p, s));
     }
     for (int j = g.nz - 1; j >= first; --j) {
         MsRowArgs a{};
@@ -455,8 +500,8 @@ bip_status bip_build_s2(bip_ctx* c, const float* V, const bip_atom* atoms, int32
         a.n_sites = c->plane_off[j + 1] - c->plane_off[j];
         a.win = g.win;
         a.stash = (float2*)c->stash2.p;
-        CUDA_TRY(c, bip_ms_row_pass(plan, a, s));
-        if (j > first) CUDA_TRY(c, bip_ms_col_pass(plan, (float2*)c->cols.p, s));
+        TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
+        if (j > first) TIMED(c, BIP_STAGE_MS_COL, s, bip_ms_col_pass(plan, (float2*)c->cols.p, s));
     }
     c->s2 = true;
     c->sig2 = site_signature(c->sites);
@@ -512,7 +557,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     CUDA_TRY(c, ensure(c->ct, (size_t)Ppad * Bpad * sizeof(float2), false, s));
     size_t ct_plane = (size_t)Ppad * Bpad;
     if (tc) CUDA_TRY(c, ensure(c->ctb, 4 * ct_plane * sizeof(uint16_t), true, s));
-    CUDA_TRY(c, bip_illumination((const double*)c->scans_d.p, P, (const int2*)c->hbeam.p,
+    TIMED(c, BIP_STAGE_REDUCE, s, bip_illumination((const double*)c->scans_d.p, P, (const int2*)c->hbeam.p,
                                  (const double2*)c->coef.p, geo.B, Bpad, g.ny, g.nx, (float2*)c->ct.p,
                                  tc ? (uint16_t*)c->ctb.p : nullptr, ct_plane, s));
 
@@ -588,7 +633,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         g2.nch = 0;
         g2.out_c64 = (float2*)c->opA32.p;
         g2.site_stride = (int64_t)perA;
-        CUDA_TRY(c, bip_gather(g2, s));
+        TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g2, s));
         GatherArgs g1 = ga;
         g1.Bp = geo.Bp1; g1.n_targets = geo.B; g1.rows_pad = Bpad;
         g1.stash = (const float2*)c->stash1.p;
@@ -599,7 +644,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         g1.H = (const float2*)H;
         g1.out_c64 = (float2*)c->opB32.p;
         g1.site_stride = (int64_t)perB;
-        CUDA_TRY(c, bip_gather(g1, s));
+        TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g1, s));
         // coupling M = S2^T diag(H) S1, stored transposed for the Gram step
         CGemmArgs A{};
         A.M = geo.n_det; A.N = (int)rowsB; A.K = K;
@@ -609,7 +654,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         A.epi = 1;
         A.C = (float2*)c->mt32.p; A.ldc = (int64_t)nch * Dpad; A.strideC = (int64_t)perMt;
         A.ep_B = Bpad; A.ep_Dp = Dpad;
-        CUDA_TRY(c, bip_cgemm_simt(A, s));
+        TIMED(c, BIP_STAGE_COUPLING, s, bip_cgemm_simt(A, s));
         // Gram Q = sum_n M^(n)H M^(n)
         CGemmArgs Bq{};
         Bq.M = Bpad; Bq.N = Bpad; Bq.K = nch * Dpad;
@@ -619,7 +664,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         Bq.batch = nb;
         Bq.epi = 0;
         Bq.C = (float2*)c->q32.p; Bq.ldc = Bpad; Bq.strideC = (int64_t)perQ;
-        CUDA_TRY(c, bip_cgemm_simt(Bq, s));
+        TIMED(c, BIP_STAGE_GRAM, s, bip_cgemm_simt(Bq, s));
         // quadratic form over the site's crop-window scan tiles
         QuadArgs q{};
         q.Bpad = Bpad;
@@ -635,13 +680,13 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         q.ny = g.ny; q.nx = g.nx; q.fy = g.fy; q.fx = g.fx;
         q.scale = (float)(g.fy * g.fx);
         q.partial = partial;
-        CUDA_TRY(c, bip_quadform_simt(q, s));
+        TIMED(c, BIP_STAGE_QUADFORM, s, bip_quadform_simt(q, s));
     }
     if (map_out) {
-        CUDA_TRY(c, bip_reduce_sites(partial, c->n_sites, P, (const double*)c->scans_d.p,
+        TIMED(c, BIP_STAGE_REDUCE, s, bip_reduce_sites(partial, c->n_sites, P, (const double*)c->scans_d.p,
                                      (const SiteDev*)c->sites_d.p, g.ny, g.nx, g.fy, g.fx, map_out, s));
     } else {
-        CUDA_TRY(c, bip_zero_outside(partial, c->n_sites, P, (const double*)c->scans_d.p,
+        TIMED(c, BIP_STAGE_REDUCE, s, bip_zero_outside(partial, c->n_sites, P, (const double*)c->scans_d.p,
                                      (const SiteDev*)c->sites_d.p, g.ny, g.nx, g.fy, g.fx, s));
     }
     return BIP_OK;
@@ -723,6 +768,31 @@ bip_status bip_site_windows(bip_ctx* c, int32_t site, void* s1_out, void* s2_out
         a.out_c64 = (float2*)s2_out;
         a.site_stride = (int64_t)c->geo.n_det * K;
         CUDA_TRY(c, bip_gather(a, s));
+    }
+    return BIP_OK;
+}
+
+bip_status bip_set_profiling(bip_ctx* c, int32_t on) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    c->prof = on != 0;
+    c->ev_used = 0;
+    c->ev_rec.clear();
+    for (int i = 0; i < BIP_N_STAGES; ++i) c->launches[i] = 0;
+    return BIP_OK;
+}
+
+bip_status bip_get_profile(bip_ctx* c, double* ms, int64_t* launches) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    double acc[BIP_N_STAGES] = {0};
+    for (auto& r : c->ev_rec) {
+        CUDA_TRY(c, cudaEventSynchronize(r.second.second));
+        float t = 0.f;
+        CUDA_TRY(c, cudaEventElapsedTime(&t, r.second.first, r.second.second));
+        acc[r.first] += t;
+    }
+    for (int i = 0; i < BIP_N_STAGES; ++i) {
+        if (ms) ms[i] = acc[i];
+        if (launches) launches[i] = c->launches[i];
     }
     return BIP_OK;
 }
