@@ -200,6 +200,33 @@ enum {
 bip_status bip_set_profiling(bip_ctx* ctx, int32_t on);
 bip_status bip_get_profile(bip_ctx* ctx, double* ms, int64_t* launches);
 
+/* bip_build_s1 for callers that cannot allocate device memory: a host
+ * framework that owns every device allocation through its own pool, a
+ * process whose device-memory budget is fixed up front, or a pipeline that
+ * cannot afford cudaMalloc/cudaFree because they synchronize the device and
+ * would stall its other streams.  (This entry point has no counterpart in
+ * the paper; it is the same S1 build as bip_build_s1.)
+ *
+ * It allocates nothing.  The caller passes the inputs of bip_build_s1 and
+ * the output `stash` [n_sites, Bp1, win, win] complex64 (device): the
+ * de-tilted S1 parent windows of every site, the layout bip_copy_stash
+ * returns per site.  The parent columns and the device tables live in a
+ * static array of 32 MiB inside the library, which every GPU that loads
+ * the library holds until the process exits.  The context only supplies
+ * its host geometry (bip_create allocates no device memory); this call does
+ * not touch the context's own device buffers or mark S1 as built.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device); the driver may place the array in device memory at that moment.
+ * Make that first call before any stream capture.  Requests that
+ * need more than 32 MiB -- Bp1 * ny * nx * 8 bytes of parent columns plus a
+ * few KB of tables and site lists -- return BIP_ERR_SHAPE with the sizes in
+ * bip_last_error.  All calls share the one array and keep the last call's
+ * contents; calls that overlap on the GPU (on different streams, or from
+ * different threads) race and corrupt each other's results. */
+bip_status bip_build_s1_noalloc(bip_ctx* ctx, const float* V, const bip_atom* atoms,
+                                int32_t n_atoms, void* stash, void* stream);
+
 /* Text of the last error on this context ("" if none; static text if ctx
  * is NULL). */
 const char* bip_last_error(const bip_ctx* ctx);

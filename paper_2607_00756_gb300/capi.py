@@ -64,6 +64,7 @@ def _load():
         "bip_site_windows": [VP, I32, VP, VP, VP],
         "bip_site_coupling": [VP, VP, I32, VP, VP],
         "bip_set_profiling": [VP, I32],
+        "bip_build_s1_noalloc": [VP, VP, P(BipAtom), I32, VP, VP],
         "bip_get_profile": [VP, VP, VP],
     }
     for name, args in sig.items():
@@ -186,6 +187,16 @@ def _scans(scans):
     if s.ndim != 2 or s.shape[1] != 2:
         raise ValueError("scans must be [P, 2]")
     return s, s.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def bip_build_s1_noalloc(ctx, V, atoms_arr, stash, stream=None):
+    """S1 build into the caller's `stash` [n_sites, Bp1, win, win] complex64
+    with no device allocation (scratch in the library's static array)."""
+    import torch
+    _check("bip_build_s1_noalloc", ctx,
+           _lib.bip_build_s1_noalloc(ctx, _dev(V, torch.float32, "V"), atoms_arr, len(atoms_arr),
+                                     _dev(stash, torch.complex64, "stash"), _stream(stream)))
+    return stash
 
 
 def bip_coreloss_map(ctx, H, scans, out, stream=None):

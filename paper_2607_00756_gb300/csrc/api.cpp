@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <string>
 
 #include "bip_internal.h"
 
@@ -804,3 +805,118 @@ bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_ou
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// S1 build without any allocation: parent columns and device tables in the
+// library's static scratch array, windows written to the caller's buffer.
+
+extern "C" bip_status bip_build_s1_noalloc(bip_ctx* c, const float* V, const bip_atom* atoms, int32_t n_atoms,
+                                           void* stash, void* stream) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (!V) return fail(c, BIP_ERR_INVALID_ARG, "V is null");
+    if (!stash) return fail(c, BIP_ERR_INVALID_ARG, "stash is null");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bip_config& g = c->cfg;
+    const BipGeometry& geo = c->geo;
+    std::vector<SiteDev> sites;
+    int nmax = 0, total = 0;
+    bip_status st = parse_sites(c, atoms, n_atoms, sites, nmax, total);
+    if (st != BIP_OK) return st;
+    const int ncol = geo.Bp1;
+    const int n = (int)sites.size();
+    const size_t G = (size_t)g.ny * g.nx;
+
+    // layout of the scratch array, every region 256-byte aligned
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t o_cols = 0;
+    const size_t o_twy = o_cols + al((size_t)ncol * G * sizeof(float2));
+    const size_t o_twx = o_twy + al((size_t)g.ny * sizeof(float2));
+    const size_t o_py = o_twx + al((size_t)g.nx * sizeof(float2));
+    const size_t o_px = o_py + al((size_t)g.ny * sizeof(float2));
+    const size_t o_sh = o_px + al((size_t)g.nx * sizeof(float2));
+    const size_t o_sites = o_sh + al((size_t)ncol * sizeof(int2));
+    const size_t o_ids = o_sites + al((size_t)n * sizeof(SiteDev));
+    const size_t need = o_ids + al((size_t)n * sizeof(int32_t));
+    if (need > kNoallocScratchBytes)
+        return fail(c, BIP_ERR_SHAPE,
+                    "bip_build_s1_noalloc needs " + std::to_string(need) + " bytes of scratch (" +
+                        std::to_string(ncol) + " parent columns of " + std::to_string(g.ny) + "x" +
+                        std::to_string(g.nx) + "); the static scratch holds " +
+                        std::to_string(kNoallocScratchBytes) + " bytes");
+
+    void* base = nullptr;
+    CUDA_TRY(c, bip_noalloc_scratch_ptr(&base));
+    unsigned char* sc = (unsigned char*)base;
+
+    // host tables (same definitions as the context's: FP64 then rounded)
+    std::vector<float2> twy(g.ny), twx(g.nx), py(g.ny), px(g.nx);
+    for (int m = 0; m < g.ny; ++m) {
+        const double a = -2.0 * kPi * m / g.ny;
+        twy[m] = float2{(float)std::cos(a), (float)std::sin(a)};
+    }
+    for (int m = 0; m < g.nx; ++m) {
+        const double a = -2.0 * kPi * m / g.nx;
+        twx[m] = float2{(float)std::cos(a), (float)std::sin(a)};
+    }
+    for (int k = 0; k < g.ny; ++k) {
+        const double q = signed_bin(k, g.ny) / g.ly;
+        const double a = -kPi * geo.lambda * g.dz * q * q;
+        py[k] = float2{(float)(std::cos(a) / g.ny), (float)(std::sin(a) / g.ny)};
+    }
+    for (int k = 0; k < g.nx; ++k) {
+        const double q = signed_bin(k, g.nx) / g.lx;
+        const double a = -kPi * geo.lambda * g.dz * q * q;
+        px[k] = float2{(float)(std::cos(a) / g.nx), (float)(std::sin(a) / g.nx)};
+    }
+    std::vector<int2> sh(ncol);
+    for (int i = 0; i < ncol; ++i) sh[i] = int2{geo.h_beam[2 * geo.p1[i]], geo.h_beam[2 * geo.p1[i] + 1]};
+    // sites grouped by plane
+    std::vector<int32_t> off(g.nz + 1, 0), ids(n);
+    for (auto& sd : sites) off[sd.plane + 1]++;
+    for (int j = 0; j < g.nz; ++j) off[j + 1] += off[j];
+    {
+        std::vector<int32_t> fill(off.begin(), off.end() - 1);
+        for (int i = 0; i < n; ++i) ids[fill[sites[i].plane]++] = i;
+    }
+    auto put = [&](size_t o, const void* h, size_t bytes) {
+        return cudaMemcpyAsync(sc + o, h, bytes, cudaMemcpyHostToDevice, s);
+    };
+    CUDA_TRY(c, put(o_twy, twy.data(), twy.size() * sizeof(float2)));
+    CUDA_TRY(c, put(o_twx, twx.data(), twx.size() * sizeof(float2)));
+    CUDA_TRY(c, put(o_py, py.data(), py.size() * sizeof(float2)));
+    CUDA_TRY(c, put(o_px, px.data(), px.size() * sizeof(float2)));
+    CUDA_TRY(c, put(o_sh, sh.data(), sh.size() * sizeof(int2)));
+    CUDA_TRY(c, put(o_sites, sites.data(), sites.size() * sizeof(SiteDev)));
+    CUDA_TRY(c, put(o_ids, ids.data(), ids.size() * sizeof(int32_t)));
+
+    MsPlan plan{};
+    plan.ny = g.ny;
+    plan.nx = g.nx;
+    plan.ncol = ncol;
+    plan.sigma = (float)geo.sigma;
+    plan.twy = (const float2*)(sc + o_twy);
+    plan.twx = (const float2*)(sc + o_twx);
+    plan.py = (const float2*)(sc + o_py);
+    plan.px = (const float2*)(sc + o_px);
+    plan.shift = (const int2*)(sc + o_sh);
+    float2* cols = (float2*)(sc + o_cols);
+    int last = 0;
+    for (auto& sd : sites) last = std::max(last, (int)sd.plane);
+    for (int j = 0; j <= last; ++j) {
+        MsRowArgs a{};
+        a.cols = cols;
+        a.init = j == 0;
+        a.init_val = 1.0f;
+        a.do_ifft = j > 0;
+        a.v_post = j < last ? V + (size_t)j * G : nullptr;
+        a.do_fft = j < last;
+        a.sites = (const SiteDev*)(sc + o_sites);
+        a.site_ids = (const int32_t*)(sc + o_ids) + off[j];
+        a.n_sites = off[j + 1] - off[j];
+        a.win = g.win;
+        a.stash = (float2*)stash;
+        CUDA_TRY(c, bip_ms_row_pass(plan, a, s));
+        if (j < last) CUDA_TRY(c, bip_ms_col_pass(plan, cols, s));
+    }
+    return BIP_OK;
+}

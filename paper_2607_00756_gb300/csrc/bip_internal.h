@@ -175,3 +175,9 @@ struct TcQuadArgs {
     int* err_flag;
 };
 cudaError_t bip_quadform_tc(const TcQuadArgs& a, cudaStream_t s);
+
+// noalloc.cu : the static device scratch used by bip_build_s1_noalloc
+constexpr size_t kNoallocScratchBytes = size_t(32) << 20;   // 32 MiB per GPU
+// Device address of that array on the current device; the first call on a
+// device looks it up (cudaGetSymbolAddress), later calls reuse it.
+cudaError_t bip_noalloc_scratch_ptr(void** ptr);
