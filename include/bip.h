@@ -176,8 +176,10 @@ bip_status bip_coreloss_cube(bip_ctx* ctx, const void* H, const double* scan_px,
  *   [Bp1, win, win]) or 2 (S2, [Bp2, win, win]) complex64, to device `out`.
  * bip_site_windows: the reconstructed windows of one site, S1 [B, win, win]
  *   and S2 [n_det, win, win] complex64 device (Eq. window-recon).
- * bip_site_coupling: the coupling matrices of one site, [nch, n_det, B]
- *   complex64 device (Eq. coupling), in the context's precision. */
+ * bip_site_coupling: the coupling matrices of one site, [nch_max, n_det, B]
+ *   complex64 device (Eq. coupling), nch_max the largest channel count of
+ *   the built sites (missing channels of a site come out zero), computed in
+ *   the context's precision. */
 bip_status bip_copy_stash(bip_ctx* ctx, int32_t which, int32_t site, void* out,
                           void* stream);
 bip_status bip_site_windows(bip_ctx* ctx, int32_t site, void* s1_out, void* s2_out,

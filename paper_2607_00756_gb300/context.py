@@ -29,6 +29,7 @@ class BipContext:
     def build(self, V, atoms, nch, stream=None):
         """S1 and S2 builds (both window stashes) from a device V."""
         self._atoms = capi.make_atoms(atoms, nch)
+        self._nch_max = int(np.max(nch))
         capi.bip_build_s1(self.ctx, V, self._atoms, stream)
         capi.bip_build_s2(self.ctx, V, self._atoms, stream)
         self.n_sites = capi.bip_query(self.ctx)[4]
@@ -66,6 +67,13 @@ class BipContext:
         s1 = torch.empty((self.B, w, w), dtype=torch.complex64, device=device)
         s2 = torch.empty((self.n_det, w, w), dtype=torch.complex64, device=device)
         return capi.bip_site_windows(self.ctx, site, s1, s2)
+
+    def coupling(self, H, site, device="cuda"):
+        """M^(n) of one site, [nch_max, n_det, B] complex64, in the context's
+        precision."""
+        nch = int(max(1, getattr(self, "_nch_max", 0)))
+        out = torch.empty((nch, self.n_det, self.B), dtype=torch.complex64, device=device)
+        return capi.bip_site_coupling(self.ctx, H, site, out)
 
     def close(self):
         if self.ctx:

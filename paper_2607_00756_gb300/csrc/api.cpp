@@ -555,7 +555,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     CUDA_TRY(c, ensure(c->scans_d, (size_t)P * 2 * sizeof(double), false, s));
     CUDA_TRY(c, cudaMemcpyAsync(c->scans_d.p, scans, (size_t)P * 2 * sizeof(double), cudaMemcpyHostToDevice, s));
     const int Ppad = n_tiles * tile;
-    CUDA_TRY(c, ensure(c->ct, (size_t)Ppad * Bpad * sizeof(float2), false, s));
+    CUDA_TRY(c, ensure(c->ct, (size_t)Ppad * Bpad * sizeof(float2), true, s));
     size_t ct_plane = (size_t)Ppad * Bpad;
     if (tc) CUDA_TRY(c, ensure(c->ctb, 4 * ct_plane * sizeof(uint16_t), true, s));
     TIMED(c, BIP_STAGE_REDUCE, s, bip_illumination((const double*)c->scans_d.p, P, (const int2*)c->hbeam.p,
@@ -581,7 +581,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         bb[4 * t] = y0; bb[4 * t + 1] = y1; bb[4 * t + 2] = x0; bb[4 * t + 3] = x1;
     }
 
-    const int SB = std::min(c->n_sites, 8);
+    const int SB = std::min(c->n_sites, tc ? 16 : 8);
     const size_t rowsA = Dpad, rowsB = (size_t)nch * Bpad;
     const size_t perA = rowsA * K, perB = rowsB * K;
     const size_t perMt = (size_t)Bpad * nch * Dpad, perQ = (size_t)Bpad * Bpad;
@@ -591,7 +591,12 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         CUDA_TRY(c, ensure(c->mt32, SB * perMt * sizeof(float2), true, s));
         CUDA_TRY(c, ensure(c->q32, SB * perQ * sizeof(float2), true, s));
     } else {
-        return fail(c, BIP_ERR_UNSUPPORTED, "split-BF16 contraction not built");
+        // four bf16 planes per complex element: 8 bytes, as complex64
+        CUDA_TRY(c, ensure(c->opA16, SB * perA * 8, true, s));
+        CUDA_TRY(c, ensure(c->opB16, SB * perB * 8, true, s));
+        CUDA_TRY(c, ensure(c->mt16, SB * perMt * 8, true, s));
+        CUDA_TRY(c, ensure(c->q16, SB * perQ * 8, true, s));
+        CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
     }
 
     // work lists for all batches, uploaded once
@@ -632,8 +637,13 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         g2.h_t = (const int2*)c->hdet.p;
         g2.tilt_sign = -1;
         g2.nch = 0;
-        g2.out_c64 = (float2*)c->opA32.p;
-        g2.site_stride = (int64_t)perA;
+        if (tc) {
+            g2.out_bf16 = (uint16_t*)c->opA16.p;
+            g2.site_stride = (int64_t)(4 * perA);
+        } else {
+            g2.out_c64 = (float2*)c->opA32.p;
+            g2.site_stride = (int64_t)perA;
+        }
         TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g2, s));
         GatherArgs g1 = ga;
         g1.Bp = geo.Bp1; g1.n_targets = geo.B; g1.rows_pad = Bpad;
@@ -643,9 +653,71 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         g1.tilt_sign = +1;
         g1.nch = nch;
         g1.H = (const float2*)H;
-        g1.out_c64 = (float2*)c->opB32.p;
-        g1.site_stride = (int64_t)perB;
+        if (tc) {
+            g1.out_bf16 = (uint16_t*)c->opB16.p;
+            g1.site_stride = (int64_t)(4 * perB);
+        } else {
+            g1.out_c64 = (float2*)c->opB32.p;
+            g1.site_stride = (int64_t)perB;
+        }
         TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g1, s));
+        if (tc) {
+            // coupling -> Mt planes, Gram -> Q planes, quadratic form -> partials
+            TcArgs A{};
+            A.epi = TC_EPI_MT;
+            A.N = (rowsB % 256 == 0) ? 256 : 128;
+            A.A = TcOperand{c->opA16.p, (int64_t)SB * 4 * (int64_t)rowsA, K, 4 * (int64_t)rowsA, (int64_t)rowsA};
+            A.B = TcOperand{c->opB16.p, (int64_t)SB * 4 * (int64_t)rowsB, K, 4 * (int64_t)rowsB, (int64_t)rowsB};
+            A.kb = K / 32;
+            A.n_sites = nb;
+            A.mt_per = Dpad / 128;
+            A.nt_per = (int)(rowsB / A.N);
+            A.out16 = (uint16_t*)c->mt16.p;
+            A.out_site = 4 * (int64_t)perMt;
+            A.out_plane = (int64_t)perMt;
+            A.out_ld = (int64_t)nch * Dpad;
+            A.ep_B = Bpad;
+            A.ep_Dp = Dpad;
+            A.err = (int*)c->errflag.p;
+            TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(A, s));
+            TcArgs Gq{};
+            Gq.epi = TC_EPI_Q;
+            Gq.N = (Bpad % 256 == 0) ? 256 : 128;
+            Gq.A = TcOperand{c->mt16.p, (int64_t)SB * 4 * Bpad, (int64_t)nch * Dpad, 4 * (int64_t)Bpad, Bpad};
+            Gq.B = Gq.A;
+            Gq.kb = nch * Dpad / 32;
+            Gq.n_sites = nb;
+            Gq.mt_per = Bpad / 128;
+            Gq.nt_per = Bpad / Gq.N;
+            Gq.conjA = 1;
+            Gq.out16 = (uint16_t*)c->q16.p;
+            Gq.out_site = 4 * (int64_t)perQ;
+            Gq.out_plane = (int64_t)perQ;
+            Gq.out_ld = Bpad;
+            Gq.err = (int*)c->errflag.p;
+            TIMED(c, BIP_STAGE_GRAM, s, bip_tc_gemm(Gq, s));
+            TcArgs Qd{};
+            Qd.epi = TC_EPI_QUAD;
+            Qd.N = tile;
+            Qd.A = TcOperand{c->q16.p, (int64_t)SB * 4 * Bpad, Bpad, 4 * (int64_t)Bpad, Bpad};
+            Qd.B = TcOperand{c->ctb.p, 4 * (int64_t)Ppad, Bpad, 0, Ppad};
+            Qd.kb = Bpad / 32;
+            Qd.mt_per = Bpad / 128;
+            Qd.work = (const int32_t*)c->work_d.p + 2 * batch_off[bi];
+            Qd.n_work = batch_off[bi + 1] - batch_off[bi];
+            Qd.ct32 = (const float2*)c->ct.p;
+            Qd.bpad = Bpad;
+            Qd.P = P;
+            Qd.scans = (const double*)c->scans_d.p;
+            Qd.sites = (const SiteDev*)c->sites_d.p;
+            Qd.site_ids = ids;
+            Qd.ny = g.ny; Qd.nx = g.nx; Qd.fy = g.fy; Qd.fx = g.fx;
+            Qd.scale = (float)(g.fy * g.fx);
+            Qd.partial = partial;
+            Qd.err = (int*)c->errflag.p;
+            TIMED(c, BIP_STAGE_QUADFORM, s, bip_tc_gemm(Qd, s));
+            continue;
+        }
         // coupling M = S2^T diag(H) S1, stored transposed for the Gram step
         CGemmArgs A{};
         A.M = geo.n_det; A.N = (int)rowsB; A.K = K;
@@ -682,6 +754,12 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         q.scale = (float)(g.fy * g.fx);
         q.partial = partial;
         TIMED(c, BIP_STAGE_QUADFORM, s, bip_quadform_simt(q, s));
+    }
+    if (tc) {
+        int flag = 0;
+        CUDA_TRY(c, cudaMemcpyAsync(&flag, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        if (flag) return fail(c, BIP_ERR_TIMEOUT, "a tensor-core contraction gave up waiting (device timeout)");
     }
     if (map_out) {
         TIMED(c, BIP_STAGE_REDUCE, s, bip_reduce_sites(partial, c->n_sites, P, (const double*)c->scans_d.p,
@@ -800,8 +878,92 @@ bip_status bip_get_profile(bip_ctx* c, double* ms, int64_t* launches) {
 
 bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_out, void* stream) {
     if (!c) return BIP_ERR_INVALID_ARG;
-    (void)H; (void)site; (void)m_out; (void)stream;
-    return fail(c, BIP_ERR_UNSUPPORTED, "coupling export not implemented yet");
+    if (!c->s1 || !c->s2 || c->sig1 != c->sig2)
+        return fail(c, BIP_ERR_INVALID_ARG, "bip_build_s1 and bip_build_s2 must run first on the same sites");
+    if (!H || !m_out) return fail(c, BIP_ERR_INVALID_ARG, "null pointer argument");
+    if (site < 0 || site >= c->n_sites) return fail(c, BIP_ERR_INVALID_ARG, "site out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bip_config& g = c->cfg;
+    const BipGeometry& geo = c->geo;
+    const int K = g.win * g.win, Bpad = c->Bpad, Dpad = c->Dpad, nch = c->nch_max;
+    const bool tc = c->prec == BIP_PREC_SPLIT_BF16;
+    const size_t perA = (size_t)Dpad * K, perB = (size_t)nch * Bpad * K;
+    const size_t ldc = (size_t)nch * Bpad;
+    DevBuf& opA = tc ? c->opA16 : c->opA32;
+    DevBuf& opB = tc ? c->opB16 : c->opB32;
+    CUDA_TRY(c, ensure(opA, perA * 8, true, s));
+    CUDA_TRY(c, ensure(opB, perB * 8, true, s));
+    CUDA_TRY(c, ensure(c->partial, (size_t)Dpad * ldc * sizeof(float2), false, s));
+    GatherArgs ga{};
+    ga.n_sites = 1;
+    ga.site_ids = (const int32_t*)c->seq_ids_d.p + site;
+    ga.sites = (const SiteDev*)c->sites_d.p;
+    ga.win = g.win; ga.ny = g.ny; ga.nx = g.nx; ga.K = K;
+    ga.magnitude = g.recon == BIP_RECON_MAGNITUDE;
+    ga.ey = (const float2*)c->ey.p;
+    ga.ex = (const float2*)c->ex.p;
+    GatherArgs g2 = ga;
+    g2.Bp = geo.Bp2; g2.n_targets = geo.n_det; g2.rows_pad = Dpad;
+    g2.stash = (const float2*)c->stash2.p;
+    g2.ell = EllDev{c->ell2_k, (const int32_t*)c->ell2_idx.p, (const float*)c->ell2_w.p};
+    g2.h_t = (const int2*)c->hdet.p;
+    g2.tilt_sign = -1;
+    GatherArgs g1 = ga;
+    g1.Bp = geo.Bp1; g1.n_targets = geo.B; g1.rows_pad = Bpad;
+    g1.stash = (const float2*)c->stash1.p;
+    g1.ell = EllDev{c->ell1_k, (const int32_t*)c->ell1_idx.p, (const float*)c->ell1_w.p};
+    g1.h_t = (const int2*)c->hbeam.p;
+    g1.tilt_sign = +1;
+    g1.nch = nch;
+    g1.H = (const float2*)H;
+    if (tc) {
+        g2.out_bf16 = (uint16_t*)opA.p; g2.site_stride = (int64_t)(4 * perA);
+        g1.out_bf16 = (uint16_t*)opB.p; g1.site_stride = (int64_t)(4 * perB);
+    } else {
+        g2.out_c64 = (float2*)opA.p; g2.site_stride = (int64_t)perA;
+        g1.out_c64 = (float2*)opB.p; g1.site_stride = (int64_t)perB;
+    }
+    TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g2, s));
+    TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g1, s));
+    float2* tmp = (float2*)c->partial.p;      // [Dpad][nch * Bpad] complex64
+    if (tc) {
+        CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
+        TcArgs A{};
+        A.epi = TC_EPI_C32;
+        A.N = (ldc % 256 == 0) ? 256 : 128;
+        A.A = TcOperand{opA.p, 4 * (int64_t)Dpad, K, 4 * (int64_t)Dpad, Dpad};
+        A.B = TcOperand{opB.p, 4 * (int64_t)ldc, K, 4 * (int64_t)ldc, (int64_t)ldc};
+        A.kb = K / 32;
+        A.n_sites = 1;
+        A.mt_per = Dpad / 128;
+        A.nt_per = (int)(ldc / A.N);
+        A.out32 = tmp;
+        A.out32_site = 0;
+        A.out32_ld = (int64_t)ldc;
+        A.err = (int*)c->errflag.p;
+        TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(A, s));
+    } else {
+        CGemmArgs A{};
+        A.M = geo.n_det; A.N = (int)ldc; A.K = K;
+        A.A = (const float2*)opA.p; A.lda = K; A.strideA = (int64_t)perA;
+        A.Bm = (const float2*)opB.p; A.ldb = K; A.strideB = (int64_t)perB;
+        A.batch = 1;
+        A.epi = 0;
+        A.C = tmp; A.ldc = (int64_t)ldc; A.strideC = 0;
+        TIMED(c, BIP_STAGE_COUPLING, s, bip_cgemm_simt(A, s));
+    }
+    // [n_det][(ch, b)] -> m_out[ch][n_det][B]
+    for (int ch = 0; ch < nch; ++ch)
+        CUDA_TRY(c, cudaMemcpy2DAsync((float2*)m_out + (size_t)ch * geo.n_det * geo.B, geo.B * sizeof(float2),
+                                      tmp + (size_t)ch * Bpad, ldc * sizeof(float2), geo.B * sizeof(float2),
+                                      geo.n_det, cudaMemcpyDeviceToDevice, s));
+    if (tc) {
+        int flag = 0;
+        CUDA_TRY(c, cudaMemcpyAsync(&flag, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        if (flag) return fail(c, BIP_ERR_TIMEOUT, "a tensor-core contraction gave up waiting (device timeout)");
+    }
+    return BIP_OK;
 }
 
 }  // extern "C"

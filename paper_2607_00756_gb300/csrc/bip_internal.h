@@ -152,29 +152,44 @@ cudaError_t bip_reduce_sites(const float* partial, int n_sites, int P, const dou
 cudaError_t bip_zero_outside(float* partial, int n_sites, int P, const double* scans,
                              const SiteDev* sites, int ny, int nx, int fy, int fx, cudaStream_t s);
 
-// gemm_tc.cu : tcgen05 split-BF16 complex GEMMs
-struct TcGemmArgs {
-    int M, N, K;                    // complex sizes; M, N multiples of 128, K of 32
-    const uint16_t* A;              // [batch][4][M][K] planes re_hi, re_lo, im_hi, im_lo
-    const uint16_t* Bm;             // [batch][4][N][K]
-    int64_t strideA, strideB;       // elements per batch entry
+// gemm_tc.cu : tcgen05 split-BF16 complex contractions.
+// Operands are four bf16 planes (re_hi, re_lo, im_hi, im_lo), K contiguous,
+// seen by TMA as one 2-D tensor [rows][K]; row (site, plane, r) is at
+// site * site_rows + plane * plane_rows + r.
+enum TcEpilogue { TC_EPI_MT = 0, TC_EPI_Q = 1, TC_EPI_C32 = 2, TC_EPI_QUAD = 3 };
+struct TcOperand {
+    const void* base;               // bf16 planes
+    int64_t rows, k;                // tensor extent (k multiple of 32)
+    int64_t site_rows, plane_rows;  // row strides
+};
+struct TcArgs {
+    int epi;                        // TcEpilogue
+    int N;                          // 128 or 256 (tile columns)
+    TcOperand A, B;                 // A tiles of 128 rows, B tiles of N rows
+    int kb;                         // K blocks of 32
+    int n_sites, mt_per, nt_per;    // tiles per site (MT, Q, C32)
     int conjA;
-    int batch;
-    int epi;                        // 0: C complex64 [M][N]; 1: Mt bf16 planes; 2: Q bf16 planes
-    float2* C; int64_t ldc, strideC;
-    uint16_t* Cb; int64_t strideCb; // bf16 planes output
-    int ep_B, ep_Dp, ep_rows, ep_K; // epilogue geometry
-    int* err_flag;                  // device word set on a wait timeout
+    // MT / Q epilogues: bf16 planes out[site][plane][row][ld]
+    uint16_t* out16;
+    int64_t out_site, out_plane, out_ld;
+    int ep_B, ep_Dp;                // MT: column n = (n / ep_B, n % ep_B) -> Mt[b][ch*ep_Dp + m]
+    // C32 epilogue: complex64 out32[site][m][ld]
+    float2* out32;
+    int64_t out32_site, out32_ld;
+    // QUAD epilogue: per (site, scan tile) work items, M tiles looped inside
+    const int32_t* work;            // [n_work][2] (site in batch, scan tile)
+    int n_work;
+    const float2* ct32;             // [Ppad][bpad] c_b(rho)
+    int bpad, P;
+    const double* scans;
+    const SiteDev* sites;
+    const int32_t* site_ids;
+    int ny, nx, fy, fx;
+    float scale;
+    float* partial;                 // [n_sites_total][P]
+    int* err;                       // device flag: set when a wait gives up
 };
-cudaError_t bip_cgemm_tc(const TcGemmArgs& a, cudaStream_t s);
-struct TcQuadArgs {
-    QuadArgs q;                     // sizes, work list, output
-    const uint16_t* Qb;             // [n_sites][4][Bpad][Bpad]
-    const uint16_t* Ctb;            // [4][Ppad][Bpad]
-    int Ppad;
-    int* err_flag;
-};
-cudaError_t bip_quadform_tc(const TcQuadArgs& a, cudaStream_t s);
+cudaError_t bip_tc_gemm(const TcArgs& a, cudaStream_t s);
 
 // noalloc.cu : the static device scratch used by bip_build_s1_noalloc
 constexpr size_t kNoallocScratchBytes = size_t(32) << 20;   // 32 MiB per GPU

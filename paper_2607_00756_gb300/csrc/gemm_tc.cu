@@ -1,0 +1,583 @@
+// Split-BF16 complex contractions on the 5th-generation tensor cores
+// (tcgen05.mma, TMEM accumulators, TMA operand staging).
+//
+// Every complex FP32 operand is stored as four BF16 planes: x = hi + lo with
+// hi = bf16(x), lo = bf16(x - hi), for the real and the imaginary part.  A
+// real product A B is taken as A_hi B_hi + A_hi B_lo + A_lo B_hi (the
+// lo*lo term is below FP32 rounding), accumulated in FP32 in TMEM, and the
+// complex product as
+//   Re += Ar Br -/+ Ai Bi,   Im += Ar Bi +/- Ai Br     (-/+: op(A) = A / conj A)
+// -- twelve MMAs per K step into two accumulators, the signs carried by the
+// instruction descriptor's negate-A bit.
+//
+// Kernel: persistent, one CTA per SM, 192 threads:
+//   warp 0      TMA producer (one elected thread): 4 A planes + 4 B planes
+//               per 32-wide K block into a 64B-swizzled shared stage;
+//   warp 1      TMEM allocator and MMA issuer (one elected thread);
+//   warps 2-5   epilogue: tcgen05.ld of the accumulators, then
+//     MT   : coupling M written transposed as bf16 planes for the Gram step
+//     Q    : Gram matrix written as bf16 planes for the quadratic form
+//     C32  : complex64 row-major copy (validation of the coupling)
+//     QUAD : f_y f_x Re(sum_b conj(c_b) Y_b) reduced over the 128 lanes
+//            of each M tile and over the M tiles of a site's scan tile.
+// Every wait is bounded (a few seconds of %globaltimer); on a timeout the
+// kernel sets *err, stops issuing work, drains what it issued and frees
+// TMEM before returning.
+#include <cuda.h>
+
+#include "bip_device.cuh"
+#include "bip_internal.h"
+
+namespace {
+
+constexpr int kThreads = 192;
+constexpr uint64_t kTimeoutNs = 4000000000ull;   // 4 s per wait
+constexpr uint32_t kTmemCols = 512;
+constexpr int kATile = 128 * 64;                 // one plane: 128 rows x 32 bf16
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---- mbarrier ---------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false on timeout or when another role aborted
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_try(b, parity)) return true;
+    const uint64_t t0 = gtimer();
+    for (uint32_t n = 1;; ++n) {
+        if (mbar_try(b, parity)) return true;
+        if ((n & 255u) == 0) {
+            if (*abort_flag) return false;
+            if (gtimer() - t0 > kTimeoutNs) return false;
+        }
+    }
+}
+
+// ---- TMA ----------------------------------------------------------------------
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---- tcgen05 ----------------------------------------------------------------------
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand tile, rows of 64 bytes (32 bf16), 64-byte swizzle:
+// 8-row groups are 512 bytes apart (stride byte offset); the leading
+// offset is unused for swizzled K-major tiles.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;              // leading byte offset (unused)
+    d |= (uint64_t)(512 >> 4) << 32;     // stride byte offset
+    d |= (uint64_t)1 << 46;              // descriptor version
+    d |= (uint64_t)4 << 61;              // 64-byte swizzle
+    return d;
+}
+// kind::f16 instruction descriptor: BF16 x BF16 -> F32, both K-major
+__host__ __device__ constexpr uint32_t idesc(int M, int N, bool negA) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint16_t bf16_rn(float x) {
+    uint32_t u = __float_as_uint(x);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+__device__ __forceinline__ float bf16_f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
+__device__ __forceinline__ void named_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Work units: (site in batch, M tile, N tile); QUAD: (work item, M tile).
+struct Unit {
+    int bs, mt, nt, w;
+};
+
+template <int EPI>
+struct UnitIter {
+    const TcArgs& p;
+    int total;
+    __device__ UnitIter(const TcArgs& a) : p(a) {
+        total = EPI == TC_EPI_QUAD ? a.n_work * a.mt_per : a.n_sites * a.mt_per * a.nt_per;
+    }
+    // the i-th unit of this CTA (i = 0, 1, ...), false past the end
+    __device__ bool get(int i, Unit& u) const {
+        if (EPI == TC_EPI_QUAD) {
+            const int wi = blockIdx.x + (i / p.mt_per) * gridDim.x;
+            if (wi >= p.n_work) return false;
+            u.w = wi;
+            u.mt = i % p.mt_per;
+            u.bs = p.work[2 * wi];
+            u.nt = p.work[2 * wi + 1];
+            return true;
+        }
+        const int idx = blockIdx.x + i * gridDim.x;
+        if (idx >= total) return false;
+        const int per = p.mt_per * p.nt_per;
+        u.bs = idx / per;
+        const int r = idx % per;
+        u.mt = r / p.nt_per;
+        u.nt = r % p.nt_per;
+        u.w = 0;
+        return true;
+    }
+};
+
+template <int N, int EPI>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const TcArgs p) {
+    constexpr int STAGES = N == 256 ? 2 : 3;
+    constexpr int NACC = N == 256 ? 1 : 2;
+    constexpr int B_TILE = N * 64;
+    constexpr int STAGE = 4 * kATile + 4 * B_TILE;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE);
+    uint64_t* empty = full + STAGES;
+    uint64_t* acc_full = empty + STAGES;
+    uint64_t* acc_empty = acc_full + NACC;
+    uint64_t* drain = acc_empty + NACC;
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    volatile int* ep_ok = abort_flag + 1;                    // epilogue's shared wait result
+    float* red = (float*)(smem + STAGES * STAGE + 256);     // [4][N]
+    float* qacc = red + 4 * N;                               // [N]
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < NACC; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 4);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+    const UnitIter<EPI> it(p);
+
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicExch(p.err, 1);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            int s = 0;
+            uint32_t ph = 0;
+            int issued = 0;
+            Unit u;
+            bool ok = true;
+            for (int i = 0; ok && it.get(i, u); ++i) {
+                const int64_t a0 = (int64_t)u.bs * p.A.site_rows + (int64_t)u.mt * 128;
+                const int64_t b0 = (int64_t)u.bs * p.B.site_rows + (int64_t)u.nt * N;
+                for (int kb = 0; kb < p.kb; ++kb) {
+                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* st = smem + s * STAGE;
+                    mbar_expect_tx(&full[s], STAGE);
+#pragma unroll
+                    for (int pl = 0; pl < 4; ++pl)
+                        tma_2d(st + pl * kATile, &mapA, kb * 32, (int)(a0 + pl * p.A.plane_rows), &full[s]);
+#pragma unroll
+                    for (int pl = 0; pl < 4; ++pl)
+                        tma_2d(st + 4 * kATile + pl * B_TILE, &mapB, kb * 32, (int)(b0 + pl * p.B.plane_rows),
+                               &full[s]);
+                    ++issued;
+                    if (++s == STAGES) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+            }
+            if (!ok) {
+                // let the copies already issued land before the CTA exits
+                for (int k = 0; k < STAGES && k < issued; ++k) {
+                    s = (s + STAGES - 1) % STAGES;
+                    if (s == STAGES - 1) ph ^= 1;
+                    const uint64_t t0 = gtimer();
+                    while (!mbar_try(&full[s], ph) && gtimer() - t0 < kTimeoutNs) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            const uint32_t id_pos = idesc(128, N, false), id_neg = idesc(128, N, true);
+            const uint32_t id_ii = p.conjA ? id_pos : id_neg;   // sign of Ai*Bi in Re
+            const uint32_t id_ir = p.conjA ? id_neg : id_pos;   // sign of Ai*Br in Im
+            int s = 0, a = 0;
+            uint32_t ph = 0, aph = 0;
+            bool any = false, ok = true;
+            Unit u;
+            for (int i = 0; ok && it.get(i, u); ++i) {
+                if (!mbar_wait(&acc_empty[a], aph ^ 1, abort_flag)) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dr = tbase + (uint32_t)(a * 2 * N), di = dr + N;
+                for (int kb = 0; kb < p.kb; ++kb) {
+                    if (!mbar_wait(&full[s], ph, abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + s * STAGE);
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        uint64_t ad[4], bd[4];
+#pragma unroll
+                        for (int pl = 0; pl < 4; ++pl) {
+                            ad[pl] = sdesc(base + pl * kATile + kk * 32);
+                            bd[pl] = sdesc(base + 4 * kATile + pl * B_TILE + kk * 32);
+                        }
+                        const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+                        // Re: Ar Br (+), Ai Bi (-, or + for conj A)
+                        mma(dr, ad[0], bd[0], id_pos, first);
+                        mma(dr, ad[0], bd[1], id_pos, 1);
+                        mma(dr, ad[1], bd[0], id_pos, 1);
+                        mma(dr, ad[2], bd[2], id_ii, 1);
+                        mma(dr, ad[2], bd[3], id_ii, 1);
+                        mma(dr, ad[3], bd[2], id_ii, 1);
+                        // Im: Ar Bi (+), Ai Br (+, or - for conj A)
+                        mma(di, ad[0], bd[2], id_pos, first);
+                        mma(di, ad[0], bd[3], id_pos, 1);
+                        mma(di, ad[1], bd[2], id_pos, 1);
+                        mma(di, ad[2], bd[0], id_ir, 1);
+                        mma(di, ad[2], bd[1], id_ir, 1);
+                        mma(di, ad[3], bd[0], id_ir, 1);
+                    }
+                    any = true;
+                    mma_commit(&empty[s]);
+                    if (++s == STAGES) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(&acc_full[a]);
+                if (++a == NACC) {
+                    a = 0;
+                    aph ^= 1;
+                }
+            }
+            if (any) {
+                // every MMA issued has finished before TMEM is released
+                mma_commit(drain);
+                const uint64_t t0 = gtimer();
+                while (!mbar_try(drain, 0) && gtimer() - t0 < kTimeoutNs) {
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
+        const int q = warp & 3;
+        const int et = threadIdx.x - 64;            // 0..127 over the epilogue warps
+        int a = 0;
+        uint32_t aph = 0;
+        Unit u;
+        for (int i = 0; it.get(i, u); ++i) {
+            // one thread waits; all 128 take the same branch, so no warp can
+            // be left alone at a named barrier
+            if (et == 0) {
+                const bool ok = mbar_wait(&acc_full[a], aph, abort_flag);
+                *ep_ok = ok ? 1 : 0;
+                if (!ok) fail();
+            }
+            named_sync(1, 128);
+            if (!*ep_ok) break;
+            tc_fence_after();
+            const int row = u.mt * 128 + q * 32 + lane;      // accumulator row of this thread
+            const uint32_t tr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 2 * N);
+            if (EPI == TC_EPI_QUAD && u.mt == 0) {
+                for (int c = et; c < N; c += 128) qacc[c] = 0.f;
+            }
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float vr[16], vi[16];
+                tmem_ld16(tr + c0, vr);
+                tmem_ld16(tr + N + c0, vi);
+                tmem_ld_wait();
+                if (EPI == TC_EPI_MT) {
+                    // coupling entry (row d, column n = (ch, b)) -> Mt[b][ch * Dp + d]
+                    uint16_t* o = p.out16 + (int64_t)u.bs * p.out_site;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int n = u.nt * N + c0 + j;
+                        const int ch = n / p.ep_B, b = n % p.ep_B;
+                        const int64_t at = (int64_t)b * p.out_ld + (int64_t)ch * p.ep_Dp + row;
+                        const uint16_t rh = bf16_rn(vr[j]), ih = bf16_rn(vi[j]);
+                        o[at] = rh;
+                        o[p.out_plane + at] = bf16_rn(vr[j] - bf16_f(rh));
+                        o[2 * p.out_plane + at] = ih;
+                        o[3 * p.out_plane + at] = bf16_rn(vi[j] - bf16_f(ih));
+                    }
+                } else if (EPI == TC_EPI_Q) {
+                    uint16_t* o = p.out16 + (int64_t)u.bs * p.out_site + (int64_t)row * p.out_ld + u.nt * N + c0;
+                    uint32_t w[4][8];
+#pragma unroll
+                    for (int j = 0; j < 16; j += 2) {
+                        const uint16_t r0 = bf16_rn(vr[j]), r1 = bf16_rn(vr[j + 1]);
+                        const uint16_t i0 = bf16_rn(vi[j]), i1 = bf16_rn(vi[j + 1]);
+                        w[0][j / 2] = (uint32_t)r0 | ((uint32_t)r1 << 16);
+                        w[1][j / 2] = (uint32_t)bf16_rn(vr[j] - bf16_f(r0)) |
+                                      ((uint32_t)bf16_rn(vr[j + 1] - bf16_f(r1)) << 16);
+                        w[2][j / 2] = (uint32_t)i0 | ((uint32_t)i1 << 16);
+                        w[3][j / 2] = (uint32_t)bf16_rn(vi[j] - bf16_f(i0)) |
+                                      ((uint32_t)bf16_rn(vi[j + 1] - bf16_f(i1)) << 16);
+                    }
+#pragma unroll
+                    for (int pl = 0; pl < 4; ++pl) {
+                        uint4* dst = reinterpret_cast<uint4*>(o + pl * p.out_plane);
+                        dst[0] = make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
+                        dst[1] = make_uint4(w[pl][4], w[pl][5], w[pl][6], w[pl][7]);
+                    }
+                } else if (EPI == TC_EPI_C32) {
+                    float2* o = p.out32 + (int64_t)u.bs * p.out32_site + (int64_t)row * p.out32_ld + u.nt * N + c0;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) o[j] = make_float2(vr[j], vi[j]);
+                } else {
+                    // QUAD: v_j = Re(conj(c_b(rho_j)) Y_{b, rho_j}), summed over b
+                    float v[16];
+                    const int scan0 = u.nt * N + c0;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float2 cb = __ldg(&p.ct32[(int64_t)(scan0 + j) * p.bpad + row]);
+                        v[j] = fmaf(cb.x, vr[j], cb.y * vi[j]);
+                    }
+                    // reduce 16 columns over the 32 lanes: halve the columns each step
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const bool up = lane & 16;
+                        const float send = up ? v[j] : v[j + 8];
+                        const float keep = up ? v[j + 8] : v[j];
+                        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const bool up = lane & 8;
+                        const float send = up ? v[j] : v[j + 4];
+                        const float keep = up ? v[j + 4] : v[j];
+                        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const bool up = lane & 4;
+                        const float send = up ? v[j] : v[j + 2];
+                        const float keep = up ? v[j + 2] : v[j];
+                        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                    }
+                    {
+                        const bool up = lane & 2;
+                        const float send = up ? v[0] : v[1];
+                        const float keep = up ? v[1] : v[0];
+                        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+                    }
+                    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+                    const int col = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
+                                    ((lane >> 1) & 1);
+                    if ((lane & 1) == 0) red[q * N + c0 + col] = v[0];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[a]);
+            if (EPI == TC_EPI_QUAD) {
+                named_sync(1, 128);
+                for (int c = et; c < N; c += 128) qacc[c] += red[c] + red[N + c] + red[2 * N + c] + red[3 * N + c];
+                named_sync(1, 128);
+                if (u.mt == p.mt_per - 1) {
+                    const int site = p.site_ids[u.bs];
+                    const SiteDev st = p.sites[site];
+                    for (int c = et; c < N; c += 128) {
+                        const int n = u.nt * N + c;
+                        if (n >= p.P) continue;
+                        const bool in = in_crop(p.scans[2 * n], p.scans[2 * n + 1], st.ty, st.tx, p.ny, p.nx, p.fy,
+                                                p.fx);
+                        p.partial[(int64_t)site * p.P + n] = in ? p.scale * qacc[c] : 0.f;
+                    }
+                    named_sync(1, 128);
+                }
+            }
+            if (++a == NACC) {
+                a = 0;
+                aph ^= 1;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols));
+    }
+}
+
+// ---- host side -----------------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+cudaError_t make_map(CUtensorMap* m, const TcOperand& op, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    if (op.k % 32 || op.rows <= 0 || op.rows > 0x7fffffff) return cudaErrorInvalidValue;
+    if (((uintptr_t)op.base) % 16) return cudaErrorInvalidValue;
+    const cuuint64_t dims[2] = {(cuuint64_t)op.k, (cuuint64_t)op.rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)op.k * 2};
+    const cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(op.base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int N, int EPI>
+cudaError_t launch(const TcArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid, cudaStream_t s) {
+    constexpr int STAGES = N == 256 ? 2 : 3;
+    constexpr size_t smem = 1024 + STAGES * (4 * kATile + 4 * N * 64) + 256 + 5 * N * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc_kernel<N, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    tc_kernel<N, EPI><<<grid, kThreads, smem, s>>>(ma, mb, a);
+    return cudaGetLastError();
+}
+
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+
+}  // namespace
+
+cudaError_t bip_tc_gemm(const TcArgs& a, cudaStream_t s) {
+    if (a.N != 128 && a.N != 256) return cudaErrorInvalidValue;
+    // every tile must lie inside its operand
+    if (a.A.k != a.B.k || a.kb * 32 != a.A.k) return cudaErrorInvalidValue;
+    if (a.epi != TC_EPI_QUAD) {
+        if (a.n_sites < 1 || a.mt_per < 1 || a.nt_per < 1) return cudaErrorInvalidValue;
+        if ((int64_t)(a.n_sites - 1) * a.A.site_rows + 3 * a.A.plane_rows + (int64_t)a.mt_per * 128 > a.A.rows)
+            return cudaErrorInvalidValue;
+        if ((int64_t)(a.n_sites - 1) * a.B.site_rows + 3 * a.B.plane_rows + (int64_t)a.nt_per * a.N > a.B.rows)
+            return cudaErrorInvalidValue;
+    } else {
+        if (a.n_work == 0) return cudaSuccess;
+        if ((int64_t)a.mt_per * 128 > a.A.plane_rows || a.bpad != a.mt_per * 128) return cudaErrorInvalidValue;
+    }
+    CUtensorMap ma, mb;
+    cudaError_t e = make_map(&ma, a.A, 128);
+    if (e != cudaSuccess) return e;
+    e = make_map(&mb, a.B, a.N);
+    if (e != cudaSuccess) return e;
+    const int units = a.epi == TC_EPI_QUAD ? a.n_work : a.n_sites * a.mt_per * a.nt_per;
+    const int grid = units < num_sms() ? units : num_sms();
+    switch (a.epi * 2 + (a.N == 256)) {
+        case TC_EPI_MT * 2: return launch<128, TC_EPI_MT>(a, ma, mb, grid, s);
+        case TC_EPI_MT * 2 + 1: return launch<256, TC_EPI_MT>(a, ma, mb, grid, s);
+        case TC_EPI_Q * 2: return launch<128, TC_EPI_Q>(a, ma, mb, grid, s);
+        case TC_EPI_Q * 2 + 1: return launch<256, TC_EPI_Q>(a, ma, mb, grid, s);
+        case TC_EPI_C32 * 2: return launch<128, TC_EPI_C32>(a, ma, mb, grid, s);
+        case TC_EPI_C32 * 2 + 1: return launch<256, TC_EPI_C32>(a, ma, mb, grid, s);
+        case TC_EPI_QUAD * 2: return launch<128, TC_EPI_QUAD>(a, ma, mb, grid, s);
+        case TC_EPI_QUAD * 2 + 1: return launch<256, TC_EPI_QUAD>(a, ma, mb, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
