@@ -49,12 +49,20 @@ def load_peaks():
 # ---------------------------------------------------------------------------
 # workload
 
-def workload(name, rank):
+def workload(name, rank, max_sites=0):
     import synth
     cfg = synth.CONFIGS[name]()
     if rank:
         cfg = cfg.replace(seed=rank)          # another frozen-phonon configuration
     sp = synth.make_specimen(cfg)
+    if max_sites:
+        # keep only the first max_sites ionized sites (small profiling case)
+        ion = np.nonzero(sp.nch > 0)[0]
+        keep = ion[:max_sites]
+        nch = np.zeros_like(sp.nch)
+        nch[keep] = sp.nch[keep]
+        per = len(cfg.channels)
+        sp = synth.Specimen(cfg=cfg, atoms=sp.atoms, nch=nch, V=sp.V, H=sp.H[:len(keep) * per], scans=sp.scans)
     return cfg, sp
 
 
@@ -168,7 +176,7 @@ def run_gpu(args, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    cfg, sp = workload(args.workload, rank)
+    cfg, sp = workload(args.workload, rank, args.max_sites)
     V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
     H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
     atoms, nch_a, scans = sp.atoms, sp.nch, sp.scans
@@ -379,6 +387,8 @@ def main():
     ap.add_argument("--paths", default="split_bf16,fp32")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
+    ap.add_argument("--max-sites", type=int, default=0,
+                    help="keep only the first N ionized sites (profiling case)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -387,7 +397,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cfg, sp = workload(args.workload, 0)
+        cfg, sp = workload(args.workload, 0, args.max_sites)
         vals = []
         sample = ""
         for _ in range(args.warmup):

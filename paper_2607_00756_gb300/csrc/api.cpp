@@ -34,14 +34,14 @@ struct bip_ctx {
     // device geometry tables
     bool tables = false;
     DevBuf twy, twx, py, px, ey, ex, shift1, shift2, hbeam, hdet, coef;
-    DevBuf ell1_idx, ell1_w, ell2_idx, ell2_w;
+    DevBuf ell1_idx, ell1_w, ell2_idx, ell2_w, ell1_n, ell2_n;
     int ell1_k = 0, ell2_k = 0;
 
     // sites of the current builds
     std::vector<SiteDev> sites;
     std::vector<int32_t> plane_ids;     // site ids grouped by plane
     std::vector<int32_t> plane_off;     // [nz + 1]
-    DevBuf sites_d, plane_ids_d, seq_ids_d;
+    DevBuf sites_d, plane_ids_d, seq_ids_d, row_off_d, row_ent_d;
     int n_sites = 0, nch_max = 0, n_ch_total = 0;
     uint64_t sig1 = 0, sig2 = 0;        // site-list signatures of the builds
     bool s1 = false, s2 = false;
@@ -160,22 +160,24 @@ int signed_bin(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 // sparse (ELL) copy of a dense weight matrix
-void to_ell(const std::vector<double>& w, int rows, int cols, int& k, std::vector<int32_t>& idx,
-            std::vector<float>& val) {
+void to_ell(const std::vector<double>& w, int rows, int cols, int& k, std::vector<uint16_t>& idx,
+            std::vector<float>& val, std::vector<int32_t>& nnz) {
     k = 1;
     for (int r = 0; r < rows; ++r) {
         int n = 0;
         for (int c = 0; c < cols; ++c) n += w[(size_t)r * cols + c] != 0.0;
         k = std::max(k, n);
     }
+    k = (k + 7) / 8 * 8;     // rows padded to whole 16-byte index vectors
     idx.assign((size_t)rows * k, 0);
     val.assign((size_t)rows * k, 0.f);
+    nnz.assign(rows, 0);
     for (int r = 0; r < rows; ++r) {
-        int n = 0;
+        int& n = nnz[r];
         for (int c = 0; c < cols; ++c) {
             const double x = w[(size_t)r * cols + c];
             if (x != 0.0) {
-                idx[(size_t)r * k + n] = c;
+                idx[(size_t)r * k + n] = (uint16_t)c;
                 val[(size_t)r * k + n] = (float)x;
                 ++n;
             }
@@ -217,10 +219,11 @@ bip_status make_tables(bip_ctx* c, cudaStream_t s) {
         const std::complex<double> v = fyfx * geo.psi_beam[b] / geo.psi_norm;
         coef[b] = double2{v.real(), v.imag()};
     }
-    std::vector<int32_t> i1, i2;
+    std::vector<uint16_t> i1, i2;
+    std::vector<int32_t> n1, n2;
     std::vector<float> w1, w2;
-    to_ell(geo.w1, geo.B, geo.Bp1, c->ell1_k, i1, w1);
-    to_ell(geo.w2, geo.n_det, geo.Bp2, c->ell2_k, i2, w2);
+    to_ell(geo.w1, geo.B, geo.Bp1, c->ell1_k, i1, w1, n1);
+    to_ell(geo.w2, geo.n_det, geo.Bp2, c->ell2_k, i2, w2, n2);
     CUDA_TRY(c, upload(c->twy, twy, s));
     CUDA_TRY(c, upload(c->twx, twx, s));
     CUDA_TRY(c, upload(c->ey, ey, s));
@@ -236,6 +239,8 @@ bip_status make_tables(bip_ctx* c, cudaStream_t s) {
     CUDA_TRY(c, upload(c->ell1_w, w1, s));
     CUDA_TRY(c, upload(c->ell2_idx, i2, s));
     CUDA_TRY(c, upload(c->ell2_w, w2, s));
+    CUDA_TRY(c, upload(c->ell1_n, n1, s));
+    CUDA_TRY(c, upload(c->ell2_n, n2, s));
     CUDA_TRY(c, ensure(c->errflag, 64, true, s));
     c->tables = true;
     return BIP_OK;
@@ -290,6 +295,40 @@ bip_status parse_sites(bip_ctx* c, const bip_atom* atoms, int32_t n_atoms, std::
     return BIP_OK;
 }
 
+// Windows crossing each grid row, per plane: row_off[j * (ny + 1) + y] ..
+// row_off[j * (ny + 1) + y + 1] - 1 index (site, window row, window x
+// origin, 0) entries; the multislice row pass stashes exactly those.
+void row_windows(const bip_config& g, const std::vector<SiteDev>& sites, std::vector<int32_t>& off,
+                 std::vector<int4>& ent) {
+    const int ny1 = g.ny + 1;
+    std::vector<int32_t> cnt((size_t)g.nz * ny1, 0);
+    for (const SiteDev& sd : sites)
+        for (int u = 0; u < g.win; ++u) {
+            int y = (sd.oy + u) % g.ny;
+            if (y < 0) y += g.ny;
+            cnt[(size_t)sd.plane * ny1 + y + 1]++;
+        }
+    off.assign((size_t)g.nz * ny1, 0);
+    int32_t run = 0;
+    for (int j = 0; j < g.nz; ++j) {
+        for (int y = 0; y < g.ny; ++y) {
+            off[(size_t)j * ny1 + y] = run;
+            run += cnt[(size_t)j * ny1 + y + 1];
+        }
+        off[(size_t)j * ny1 + g.ny] = run;
+    }
+    ent.assign(run, int4{0, 0, 0, 0});
+    std::vector<int32_t> fill(off);
+    for (int s = 0; s < (int)sites.size(); ++s) {
+        const SiteDev& sd = sites[s];
+        for (int u = 0; u < g.win; ++u) {
+            int y = (sd.oy + u) % g.ny;
+            if (y < 0) y += g.ny;
+            ent[fill[(size_t)sd.plane * ny1 + y]++] = int4{s, u, sd.ox, 0};
+        }
+    }
+}
+
 bip_status set_sites(bip_ctx* c, std::vector<SiteDev>& sites, int nmax, int total, cudaStream_t s) {
     const bip_config& g = c->cfg;
     const uint64_t sig = site_signature(sites);
@@ -311,6 +350,11 @@ bip_status set_sites(bip_ctx* c, std::vector<SiteDev>& sites, int nmax, int tota
     CUDA_TRY(c, upload(c->sites_d, c->sites, s));
     CUDA_TRY(c, upload(c->plane_ids_d, c->plane_ids, s));
     CUDA_TRY(c, upload(c->seq_ids_d, seq, s));
+    std::vector<int32_t> roff;
+    std::vector<int4> rent;
+    row_windows(g, c->sites, roff, rent);
+    CUDA_TRY(c, upload(c->row_off_d, roff, s));
+    CUDA_TRY(c, upload(c->row_ent_d, rent, s));
     return BIP_OK;
 }
 
@@ -382,8 +426,8 @@ bip_status bip_create(const bip_config* cfg, bip_ctx** out) {
 bip_status bip_destroy(bip_ctx* c) {
     if (!c) return BIP_ERR_INVALID_ARG;
     DevBuf* all[] = {&c->twy, &c->twx, &c->py, &c->px, &c->ey, &c->ex, &c->shift1, &c->shift2, &c->hbeam,
-                     &c->hdet, &c->coef, &c->ell1_idx, &c->ell1_w, &c->ell2_idx, &c->ell2_w, &c->sites_d,
-                     &c->plane_ids_d, &c->seq_ids_d, &c->stash1, &c->stash2, &c->cols, &c->scans_d, &c->ct,
+                     &c->hdet, &c->coef, &c->ell1_idx, &c->ell1_w, &c->ell2_idx, &c->ell2_w, &c->ell1_n, &c->ell2_n, &c->sites_d,
+                     &c->plane_ids_d, &c->seq_ids_d, &c->row_off_d, &c->row_ent_d, &c->stash1, &c->stash2, &c->cols, &c->scans_d, &c->ct,
                      &c->ctb, &c->work_d, &c->partial, &c->opA32, &c->opB32, &c->mt32, &c->q32, &c->opA16,
                      &c->opB16, &c->mt16, &c->q16, &c->errflag};
     for (DevBuf* b : all) release(*b);
@@ -450,9 +494,10 @@ bip_status bip_build_s1(bip_ctx* c, const float* V, const bip_atom* atoms, int32
         a.v_pre = nullptr;
         a.v_post = j < last ? V + (size_t)j * G : nullptr;
         a.do_fft = j < last;
-        a.sites = (const SiteDev*)c->sites_d.p;
-        a.site_ids = (const int32_t*)c->plane_ids_d.p + c->plane_off[j];
-        a.n_sites = c->plane_off[j + 1] - c->plane_off[j];
+        if (c->plane_off[j + 1] > c->plane_off[j]) {
+            a.row_off = (const int32_t*)c->row_off_d.p + (size_t)j * (g.ny + 1);
+            a.row_ent = (const int4*)c->row_ent_d.p;
+        }
         a.win = g.win;
         a.stash = (float2*)c->stash1.p;
         TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
@@ -484,8 +529,6 @@ bip_status bip_build_s2(bip_ctx* c, const float* V, const bip_atom* atoms, int32
         a.init_val = (float)(1.0 / std::sqrt((double)G));
         a.do_fft = 1;
         a.win = g.win;
-        a.sites = (const SiteDev*)c->sites_d.p;
-        a.site_ids = (const int32_t*)c->plane_ids_d.p;
         a.stash = (float2*)c->stash2.p;
         TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
         TIMED(c, BIP_STAGE_MS_COL, s, bip_ms_col_pass(plan, (float2*)c->cols.p, s));
@@ -496,9 +539,10 @@ bip_status bip_build_s2(bip_ctx* c, const float* V, const bip_atom* atoms, int32
         a.do_ifft = 1;
         a.v_pre = V + (size_t)j * G;
         a.do_fft = j > first;
-        a.sites = (const SiteDev*)c->sites_d.p;
-        a.site_ids = (const int32_t*)c->plane_ids_d.p + c->plane_off[j];
-        a.n_sites = c->plane_off[j + 1] - c->plane_off[j];
+        if (c->plane_off[j + 1] > c->plane_off[j]) {
+            a.row_off = (const int32_t*)c->row_off_d.p + (size_t)j * (g.ny + 1);
+            a.row_ent = (const int4*)c->row_ent_d.p;
+        }
         a.win = g.win;
         a.stash = (float2*)c->stash2.p;
         TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
@@ -633,7 +677,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         GatherArgs g2 = ga;
         g2.Bp = geo.Bp2; g2.n_targets = geo.n_det; g2.rows_pad = Dpad;
         g2.stash = (const float2*)c->stash2.p;
-        g2.ell = EllDev{c->ell2_k, (const int32_t*)c->ell2_idx.p, (const float*)c->ell2_w.p};
+        g2.ell = EllDev{c->ell2_k, (const uint16_t*)c->ell2_idx.p, (const float*)c->ell2_w.p, (const int32_t*)c->ell2_n.p};
         g2.h_t = (const int2*)c->hdet.p;
         g2.tilt_sign = -1;
         g2.nch = 0;
@@ -648,7 +692,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         GatherArgs g1 = ga;
         g1.Bp = geo.Bp1; g1.n_targets = geo.B; g1.rows_pad = Bpad;
         g1.stash = (const float2*)c->stash1.p;
-        g1.ell = EllDev{c->ell1_k, (const int32_t*)c->ell1_idx.p, (const float*)c->ell1_w.p};
+        g1.ell = EllDev{c->ell1_k, (const uint16_t*)c->ell1_idx.p, (const float*)c->ell1_w.p, (const int32_t*)c->ell1_n.p};
         g1.h_t = (const int2*)c->hbeam.p;
         g1.tilt_sign = +1;
         g1.nch = nch;
@@ -666,6 +710,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             TcArgs A{};
             A.epi = TC_EPI_MT;
             A.N = (rowsB % 256 == 0) ? 256 : 128;
+            if (const char* e = std::getenv("BIP_COUPLING_N")) A.N = std::atoi(e) == 128 ? 128 : A.N;
             A.A = TcOperand{c->opA16.p, (int64_t)SB * 4 * (int64_t)rowsA, K, 4 * (int64_t)rowsA, (int64_t)rowsA};
             A.B = TcOperand{c->opB16.p, (int64_t)SB * 4 * (int64_t)rowsB, K, 4 * (int64_t)rowsB, (int64_t)rowsB};
             A.kb = K / 32;
@@ -690,6 +735,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             Gq.mt_per = Bpad / 128;
             Gq.nt_per = Bpad / Gq.N;
             Gq.conjA = 1;
+            Gq.tri = 1;
             Gq.out16 = (uint16_t*)c->q16.p;
             Gq.out_site = 4 * (int64_t)perQ;
             Gq.out_plane = (int64_t)perQ;
@@ -703,6 +749,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             Qd.B = TcOperand{c->ctb.p, 4 * (int64_t)Ppad, Bpad, 0, Ppad};
             Qd.kb = Bpad / 32;
             Qd.mt_per = Bpad / 128;
+            Qd.tri = 1;
             Qd.work = (const int32_t*)c->work_d.p + 2 * batch_off[bi];
             Qd.n_work = batch_off[bi + 1] - batch_off[bi];
             Qd.ct32 = (const float2*)c->ct.p;
@@ -830,7 +877,7 @@ bip_status bip_site_windows(bip_ctx* c, int32_t site, void* s1_out, void* s2_out
         GatherArgs a = ga;
         a.Bp = c->geo.Bp1; a.n_targets = c->geo.B; a.rows_pad = c->geo.B;
         a.stash = (const float2*)c->stash1.p;
-        a.ell = EllDev{c->ell1_k, (const int32_t*)c->ell1_idx.p, (const float*)c->ell1_w.p};
+        a.ell = EllDev{c->ell1_k, (const uint16_t*)c->ell1_idx.p, (const float*)c->ell1_w.p, (const int32_t*)c->ell1_n.p};
         a.h_t = (const int2*)c->hbeam.p;
         a.tilt_sign = +1;
         a.out_c64 = (float2*)s1_out;
@@ -841,7 +888,7 @@ bip_status bip_site_windows(bip_ctx* c, int32_t site, void* s1_out, void* s2_out
         GatherArgs a = ga;
         a.Bp = c->geo.Bp2; a.n_targets = c->geo.n_det; a.rows_pad = c->geo.n_det;
         a.stash = (const float2*)c->stash2.p;
-        a.ell = EllDev{c->ell2_k, (const int32_t*)c->ell2_idx.p, (const float*)c->ell2_w.p};
+        a.ell = EllDev{c->ell2_k, (const uint16_t*)c->ell2_idx.p, (const float*)c->ell2_w.p, (const int32_t*)c->ell2_n.p};
         a.h_t = (const int2*)c->hdet.p;
         a.tilt_sign = -1;
         a.out_c64 = (float2*)s2_out;
@@ -905,13 +952,13 @@ bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_ou
     GatherArgs g2 = ga;
     g2.Bp = geo.Bp2; g2.n_targets = geo.n_det; g2.rows_pad = Dpad;
     g2.stash = (const float2*)c->stash2.p;
-    g2.ell = EllDev{c->ell2_k, (const int32_t*)c->ell2_idx.p, (const float*)c->ell2_w.p};
+    g2.ell = EllDev{c->ell2_k, (const uint16_t*)c->ell2_idx.p, (const float*)c->ell2_w.p, (const int32_t*)c->ell2_n.p};
     g2.h_t = (const int2*)c->hdet.p;
     g2.tilt_sign = -1;
     GatherArgs g1 = ga;
     g1.Bp = geo.Bp1; g1.n_targets = geo.B; g1.rows_pad = Bpad;
     g1.stash = (const float2*)c->stash1.p;
-    g1.ell = EllDev{c->ell1_k, (const int32_t*)c->ell1_idx.p, (const float*)c->ell1_w.p};
+    g1.ell = EllDev{c->ell1_k, (const uint16_t*)c->ell1_idx.p, (const float*)c->ell1_w.p, (const int32_t*)c->ell1_n.p};
     g1.h_t = (const int2*)c->hbeam.p;
     g1.tilt_sign = +1;
     g1.nch = nch;
@@ -985,7 +1032,6 @@ extern "C" bip_status bip_build_s1_noalloc(bip_ctx* c, const float* V, const bip
     bip_status st = parse_sites(c, atoms, n_atoms, sites, nmax, total);
     if (st != BIP_OK) return st;
     const int ncol = geo.Bp1;
-    const int n = (int)sites.size();
     const size_t G = (size_t)g.ny * g.nx;
 
     // layout of the scratch array, every region 256-byte aligned
@@ -996,9 +1042,12 @@ extern "C" bip_status bip_build_s1_noalloc(bip_ctx* c, const float* V, const bip
     const size_t o_py = o_twx + al((size_t)g.nx * sizeof(float2));
     const size_t o_px = o_py + al((size_t)g.ny * sizeof(float2));
     const size_t o_sh = o_px + al((size_t)g.nx * sizeof(float2));
-    const size_t o_sites = o_sh + al((size_t)ncol * sizeof(int2));
-    const size_t o_ids = o_sites + al((size_t)n * sizeof(SiteDev));
-    const size_t need = o_ids + al((size_t)n * sizeof(int32_t));
+    std::vector<int32_t> roff;
+    std::vector<int4> rent;
+    row_windows(g, sites, roff, rent);
+    const size_t o_roff = o_sh + al((size_t)ncol * sizeof(int2));
+    const size_t o_rent = o_roff + al(roff.size() * sizeof(int32_t));
+    const size_t need = o_rent + al(rent.size() * sizeof(int4));
     if (need > kNoallocScratchBytes)
         return fail(c, BIP_ERR_SHAPE,
                     "bip_build_s1_noalloc needs " + std::to_string(need) + " bytes of scratch (" +
@@ -1032,14 +1081,10 @@ extern "C" bip_status bip_build_s1_noalloc(bip_ctx* c, const float* V, const bip
     }
     std::vector<int2> sh(ncol);
     for (int i = 0; i < ncol; ++i) sh[i] = int2{geo.h_beam[2 * geo.p1[i]], geo.h_beam[2 * geo.p1[i] + 1]};
-    // sites grouped by plane
-    std::vector<int32_t> off(g.nz + 1, 0), ids(n);
+    // planes that hold sites
+    std::vector<int32_t> off(g.nz + 1, 0);
     for (auto& sd : sites) off[sd.plane + 1]++;
     for (int j = 0; j < g.nz; ++j) off[j + 1] += off[j];
-    {
-        std::vector<int32_t> fill(off.begin(), off.end() - 1);
-        for (int i = 0; i < n; ++i) ids[fill[sites[i].plane]++] = i;
-    }
     auto put = [&](size_t o, const void* h, size_t bytes) {
         return cudaMemcpyAsync(sc + o, h, bytes, cudaMemcpyHostToDevice, s);
     };
@@ -1048,8 +1093,8 @@ extern "C" bip_status bip_build_s1_noalloc(bip_ctx* c, const float* V, const bip
     CUDA_TRY(c, put(o_py, py.data(), py.size() * sizeof(float2)));
     CUDA_TRY(c, put(o_px, px.data(), px.size() * sizeof(float2)));
     CUDA_TRY(c, put(o_sh, sh.data(), sh.size() * sizeof(int2)));
-    CUDA_TRY(c, put(o_sites, sites.data(), sites.size() * sizeof(SiteDev)));
-    CUDA_TRY(c, put(o_ids, ids.data(), ids.size() * sizeof(int32_t)));
+    CUDA_TRY(c, put(o_roff, roff.data(), roff.size() * sizeof(int32_t)));
+    CUDA_TRY(c, put(o_rent, rent.data(), rent.size() * sizeof(int4)));
 
     MsPlan plan{};
     plan.ny = g.ny;
@@ -1072,9 +1117,10 @@ extern "C" bip_status bip_build_s1_noalloc(bip_ctx* c, const float* V, const bip
         a.do_ifft = j > 0;
         a.v_post = j < last ? V + (size_t)j * G : nullptr;
         a.do_fft = j < last;
-        a.sites = (const SiteDev*)(sc + o_sites);
-        a.site_ids = (const int32_t*)(sc + o_ids) + off[j];
-        a.n_sites = off[j + 1] - off[j];
+        if (off[j + 1] > off[j]) {
+            a.row_off = (const int32_t*)(sc + o_roff) + (size_t)j * (g.ny + 1);
+            a.row_ent = (const int4*)(sc + o_rent);
+        }
         a.win = g.win;
         a.stash = (float2*)stash;
         CUDA_TRY(c, bip_ms_row_pass(plan, a, s));

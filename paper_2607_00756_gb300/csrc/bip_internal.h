@@ -45,10 +45,11 @@ struct SiteDev {            // one ionized site, as the kernels see it
     double ty, tx;          // position in pixels
 };
 
-struct EllDev {             // sparse NNW weights, fixed nnz per target row
-    int32_t k;              // entries per row (padded with w = 0)
-    const int32_t* idx;     // [rows * k] parent index
+struct EllDev {             // sparse NNW weights, fixed row width
+    int32_t k;              // entries per row (a multiple of 8, padded with w = 0)
+    const uint16_t* idx;    // [rows * k] parent index
     const float* w;         // [rows * k] weight
+    const int32_t* nnz;     // [rows] nonzero entries of each row (<= k)
 };
 
 // ---------------------------------------------------------------------------
@@ -72,9 +73,10 @@ struct MsRowArgs {
     int init;                       // 1: start from a constant field `init_val`
     float init_val;
     int do_ifft, do_fft;
-    const SiteDev* sites;           // sites stashed at this pass (device)
-    const int32_t* site_ids;        // their indices into the stash
-    int n_sites;
+    // windows crossing each row of this plane: entries row_off[y] ..
+    // row_off[y+1]-1 of row_ent, each (site, window row u, window x origin)
+    const int32_t* row_off;         // [ny + 1] (null: no stash at this pass)
+    const int4* row_ent;
     int win;
     float2* stash;                  // [n_sites_total, ncol, win, win]
 };
@@ -169,6 +171,11 @@ struct TcArgs {
     int kb;                         // K blocks of 32
     int n_sites, mt_per, nt_per;    // tiles per site (MT, Q, C32)
     int conjA;
+    // Hermitian use of the Gram matrix: Q writes only its upper triangle as
+    // Q' (diagonal kept, off-diagonal doubled, lower zero) and skips tiles
+    // below the diagonal; QUAD then starts each M tile at the diagonal,
+    // since c^H Q c = Re(c^H Q' c).
+    int tri;
     // MT / Q epilogues: bf16 planes out[site][plane][row][ld]
     uint16_t* out16;
     int64_t out_site, out_plane, out_ld;

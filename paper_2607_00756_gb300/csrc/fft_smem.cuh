@@ -5,8 +5,9 @@
 // radix 4 or 2.  Each thread always holds 8 values per pass (one radix-8,
 // two radix-4 or four radix-2 butterflies).  Twiddles W_N^m =
 // exp(-2 pi i m / N) come from a table computed on the host in FP64 and
-// rounded to FP32.  Data live in shared memory with one padding slot per 16
-// entries to spread the strided accesses over the banks.
+// rounded to FP32 (kept in shared memory by the callers).  Data live in
+// shared memory with one padding slot per 16 entries to spread the strided
+// accesses over the banks.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -70,7 +71,7 @@ __device__ __forceinline__ void dft8(float2* v) {
 // Thread t of nt = N/8 handles 8/R butterflies j = t + b*nt.
 // Both __syncthreads are block-wide: every thread of the block calls this.
 template <int N, int R, bool INV>
-__device__ __forceinline__ void stockham_pass(float2* buf, int Ns, int t, const float2* __restrict__ tw) {
+__device__ __forceinline__ void stockham_pass(float2* buf, int Ns, int t, const float2* tw) {
     constexpr int NT = N / 8;
     constexpr int NB = 8 / R;
     constexpr int STRIDE = N / R;
@@ -90,7 +91,7 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int Ns, int t, const 
             const int step = k * (N / (Ns * R));
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = __ldg(&tw[r * step]);
+                float2 w = tw[r * step];
                 if (INV) w.y = -w.y;
                 v[b * R + r] = c_mul(v[b * R + r], w);
             }
@@ -109,7 +110,7 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int Ns, int t, const 
 // thread's rank within this transform; the caller syncs before (data
 // written) -- the last pass ends with a block-wide sync.
 template <int N, bool INV>
-__device__ __forceinline__ void fft_smem(float2* buf, int t, const float2* __restrict__ tw) {
+__device__ __forceinline__ void fft_smem(float2* buf, int t, const float2* tw) {
     __syncthreads();
     int Ns = 1;
 #pragma unroll

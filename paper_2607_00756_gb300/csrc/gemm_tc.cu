@@ -146,12 +146,15 @@ __device__ __forceinline__ void named_sync(int id, int n) {
 // Work units: (site in batch, M tile, N tile); QUAD: (work item, M tile).
 struct Unit {
     int bs, mt, nt, w;
+    bool skip;    // tile below the diagonal of a Hermitian Gram matrix
+    int kb0;      // first K block
 };
 
 template <int EPI>
 struct UnitIter {
     const TcArgs& p;
     int total;
+    __device__ int N_of() const { return p.N; }
     __device__ UnitIter(const TcArgs& a) : p(a) {
         total = EPI == TC_EPI_QUAD ? a.n_work * a.mt_per : a.n_sites * a.mt_per * a.nt_per;
     }
@@ -164,6 +167,8 @@ struct UnitIter {
             u.mt = i % p.mt_per;
             u.bs = p.work[2 * wi];
             u.nt = p.work[2 * wi + 1];
+            u.skip = false;
+            u.kb0 = p.tri ? u.mt * 4 : 0;      // 128 rows = 4 K blocks of 32
             return true;
         }
         const int idx = blockIdx.x + i * gridDim.x;
@@ -174,6 +179,8 @@ struct UnitIter {
         u.mt = r / p.nt_per;
         u.nt = r % p.nt_per;
         u.w = 0;
+        u.skip = p.tri && (u.nt + 1) * N_of() <= u.mt * 128;
+        u.kb0 = 0;
         return true;
     }
 };
@@ -237,9 +244,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             Unit u;
             bool ok = true;
             for (int i = 0; ok && it.get(i, u); ++i) {
+                if (u.skip) continue;
                 const int64_t a0 = (int64_t)u.bs * p.A.site_rows + (int64_t)u.mt * 128;
                 const int64_t b0 = (int64_t)u.bs * p.B.site_rows + (int64_t)u.nt * N;
-                for (int kb = 0; kb < p.kb; ++kb) {
+                for (int kb = u.kb0; kb < p.kb; ++kb) {
                     if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
                         fail();
                         ok = false;
@@ -283,13 +291,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool any = false, ok = true;
             Unit u;
             for (int i = 0; ok && it.get(i, u); ++i) {
+                if (u.skip) continue;
                 if (!mbar_wait(&acc_empty[a], aph ^ 1, abort_flag)) {
                     fail();
                     break;
                 }
                 tc_fence_after();
                 const uint32_t dr = tbase + (uint32_t)(a * 2 * N), di = dr + N;
-                for (int kb = 0; kb < p.kb; ++kb) {
+                for (int kb = u.kb0; kb < p.kb; ++kb) {
                     if (!mbar_wait(&full[s], ph, abort_flag)) {
                         fail();
                         ok = false;
@@ -305,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             ad[pl] = sdesc(base + pl * kATile + kk * 32);
                             bd[pl] = sdesc(base + 4 * kATile + pl * B_TILE + kk * 32);
                         }
-                        const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+                        const uint32_t first = (kb == u.kb0 && kk == 0) ? 0u : 1u;
                         // Re: Ar Br (+), Ai Bi (-, or + for conj A)
                         mma(dr, ad[0], bd[0], id_pos, first);
                         mma(dr, ad[0], bd[1], id_pos, 1);
@@ -351,6 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t aph = 0;
         Unit u;
         for (int i = 0; it.get(i, u); ++i) {
+            if (u.skip) continue;
             // one thread waits; all 128 take the same branch, so no warp can
             // be left alone at a named barrier
             if (et == 0) {
@@ -387,6 +397,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 } else if (EPI == TC_EPI_Q) {
                     uint16_t* o = p.out16 + (int64_t)u.bs * p.out_site + (int64_t)row * p.out_ld + u.nt * N + c0;
+                    if (p.tri) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int col = u.nt * N + c0 + j;
+                            const float f = col > row ? 2.f : (col == row ? 1.f : 0.f);
+                            vr[j] *= f;
+                            vi[j] *= f;
+                        }
+                    }
                     uint32_t w[4][8];
 #pragma unroll
                     for (int j = 0; j < 16; j += 2) {

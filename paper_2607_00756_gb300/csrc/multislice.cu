@@ -30,6 +30,8 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(MsPlan plan, MsRowAr
     constexpr int RPB = kThreads / NT;         // rows per block
     constexpr int ROWLEN = NX + NX / 16;       // padded
     extern __shared__ float2 smem[];
+    float2* tw = smem + RPB * ROWLEN;          // [NX] twiddles
+    for (int i = threadIdx.x; i < NX; i += kThreads) tw[i] = __ldg(&plan.twx[i]);
     const int sub = threadIdx.x / NT;
     const int t = threadIdx.x % NT;
     float2* row = smem + sub * ROWLEN;
@@ -45,8 +47,8 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(MsPlan plan, MsRowAr
         for (int x = t; x < NX; x += NT)
             row[FFT_PAD(x)] = a.init ? make_float2(a.init_val, 0.f) : g[x];
     }
-    if (a.do_ifft) fft_smem<NX, true>(row, t, plan.twx);
-    else __syncthreads();
+    __syncthreads();
+    if (a.do_ifft) fft_smem<NX, true>(row, t, tw);
 
     if (active && a.v_pre) {
         const float* v = a.v_pre + (size_t)y * NX;
@@ -57,15 +59,13 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(MsPlan plan, MsRowAr
         }
     }
     __syncthreads();
-    if (active) {
-        for (int i = 0; i < a.n_sites; ++i) {
-            const SiteDev st = a.sites[a.site_ids[i]];
-            int u = (y - st.oy) % plan.ny;
-            if (u < 0) u += plan.ny;
-            if (u >= a.win) continue;
-            float2* dst = a.stash + (((size_t)a.site_ids[i] * plan.ncol + c) * a.win + u) * a.win;
+    if (active && a.row_off) {
+        const int e1 = __ldg(&a.row_off[y + 1]);
+        for (int e = __ldg(&a.row_off[y]); e < e1; ++e) {
+            const int4 en = __ldg(&a.row_ent[e]);      // (site, u, ox, -)
+            float2* dst = a.stash + (((size_t)en.x * plan.ncol + c) * a.win + en.y) * a.win;
             for (int v = t; v < a.win; v += NT) {
-                int x = (st.ox + v) % NX;
+                int x = (en.z + v) % NX;
                 if (x < 0) x += NX;
                 dst[v] = row[FFT_PAD(x)];
             }
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(MsPlan plan, MsRowAr
             row[FFT_PAD(x)] = c_mul(row[FFT_PAD(x)], make_float2(co, s));
         }
     }
-    if (a.do_fft) fft_smem<NX, false>(row, t, plan.twx);
+    if (a.do_fft) fft_smem<NX, false>(row, t, tw);
     else __syncthreads();
     if (active) {
         for (int x = t; x < NX; x += NT) g[x] = row[FFT_PAD(x)];
@@ -94,6 +94,8 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(MsPlan plan, float2*
     constexpr int XB = NPAR > 16 ? NPAR : 16;   // x columns per block
     constexpr int COLLEN = NY + NY / 16 + 1;    // padded, odd stride
     extern __shared__ float2 smem[];
+    float2* tw = smem + XB * COLLEN;            // [NY] twiddles
+    for (int i = threadIdx.x; i < NY; i += kThreads) tw[i] = __ldg(&plan.twy[i]);
     const int c = blockIdx.y;
     const int x0 = blockIdx.x * XB;
     float2* g = cols + (size_t)c * NY * plan.nx;
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(MsPlan plan, float2*
     for (int grp = 0; grp < XB; grp += NPAR) {
         const int xx = grp + sub;
         float2* col = smem + xx * COLLEN;
-        fft_smem<NY, false>(col, t, plan.twy);
+        fft_smem<NY, false>(col, t, tw);
         // shifted propagator at (k_y, k_x = x0 + xx)
         int kx = (x0 + xx + sh.y) % plan.nx;
         if (kx < 0) kx += plan.nx;
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(MsPlan plan, float2*
             const float2 p = c_mul(__ldg(&plan.py[iy]), px);
             col[FFT_PAD(ky)] = c_mul(col[FFT_PAD(ky)], p);
         }
-        fft_smem<NY, true>(col, t, plan.twy);
+        fft_smem<NY, true>(col, t, tw);
     }
     for (int i = threadIdx.x; i < NY * XB; i += kThreads) {
         const int y = i / XB, xx = i % XB;
@@ -131,7 +133,7 @@ cudaError_t launch_row(const MsPlan& p, const MsRowArgs& a, cudaStream_t s) {
     constexpr int NT = NX / 8, RPB = kThreads / NT, ROWLEN = NX + NX / 16;
     const long long npairs = (long long)p.ncol * p.ny;
     const int blocks = (int)((npairs + RPB - 1) / RPB);
-    const size_t sm = (size_t)RPB * ROWLEN * sizeof(float2);
+    const size_t sm = ((size_t)RPB * ROWLEN + NX) * sizeof(float2);
     row_pass_kernel<NX><<<blocks, kThreads, sm, s>>>(p, a);
     return cudaGetLastError();
 }
@@ -140,7 +142,7 @@ template <int NY>
 cudaError_t launch_col(const MsPlan& p, float2* cols, cudaStream_t s) {
     constexpr int NT = NY / 8, NPAR = kThreads / NT, XB = NPAR > 16 ? NPAR : 16;
     constexpr int COLLEN = NY + NY / 16 + 1;
-    const size_t sm = (size_t)XB * COLLEN * sizeof(float2);
+    const size_t sm = ((size_t)XB * COLLEN + NY) * sizeof(float2);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(col_pass_kernel<NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
