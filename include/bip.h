@@ -57,7 +57,11 @@ typedef enum {
 
 typedef enum {
     BIP_PREC_FP32 = 0,         /* FP32 SIMT complex GEMMs                     */
-    BIP_PREC_SPLIT_BF16 = 1    /* tcgen05 BF16 hi+lo (3 products), FP32 acc.  */
+    BIP_PREC_SPLIT_BF16 = 1,   /* tcgen05, every contraction in BF16 hi+lo
+                                  (3 products per real product), FP32 acc.    */
+    BIP_PREC_MIXED = 2         /* tcgen05, coupling and Gram in BF16 (one
+                                  product), the quadratic form in BF16 hi+lo;
+                                  FP32 accumulation throughout               */
 } bip_precision;
 
 typedef enum {

@@ -408,7 +408,8 @@ bip_status bip_create(const bip_config* cfg, bip_ctx** out) {
     if (g.win < 16 || g.win % 16 || g.win > g.ny / g.fy || g.win > g.nx / g.fx) return bad(BIP_ERR_SHAPE, "win");
     if (g.nrad1 < 0 || g.nrad2 < 0 || g.nang1 < 1 || g.nang2 < 1) return bad(BIP_ERR_INVALID_ARG, "rings");
     if (g.recon != BIP_RECON_COMPLEX && g.recon != BIP_RECON_MAGNITUDE) return bad(BIP_ERR_INVALID_ARG, "recon");
-    if (g.prec != BIP_PREC_FP32 && g.prec != BIP_PREC_SPLIT_BF16) return bad(BIP_ERR_INVALID_ARG, "prec");
+    if (g.prec != BIP_PREC_FP32 && g.prec != BIP_PREC_SPLIT_BF16 && g.prec != BIP_PREC_MIXED)
+        return bad(BIP_ERR_INVALID_ARG, "prec");
     c->cfg = g;
     c->prec = g.prec;
     std::string err;
@@ -461,7 +462,7 @@ bip_status bip_get_geometry(const bip_ctx* c, int32_t* h_beam, int32_t* h_det, i
 
 bip_status bip_set_precision(bip_ctx* c, int32_t prec) {
     if (!c) return BIP_ERR_INVALID_ARG;
-    if (prec != BIP_PREC_FP32 && prec != BIP_PREC_SPLIT_BF16)
+    if (prec != BIP_PREC_FP32 && prec != BIP_PREC_SPLIT_BF16 && prec != BIP_PREC_MIXED)
         return fail(c, BIP_ERR_INVALID_ARG, "unknown precision");
     c->prec = prec;
     return BIP_OK;
@@ -592,7 +593,9 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     const int K = g.win * g.win;
     const int Bpad = c->Bpad, Dpad = c->Dpad;
     const int nch = c->nch_max;
-    const bool tc = c->prec == BIP_PREC_SPLIT_BF16;
+    const bool tc = c->prec != BIP_PREC_FP32;
+    // planes of the coupling and Gram operands: split BF16 (4) or BF16 (2)
+    const int npl = c->prec == BIP_PREC_MIXED ? 2 : 4;
     const int tile = tc ? kScanTileTc : kScanTile;
     const int n_tiles = (P + tile - 1) / tile;
 
@@ -683,7 +686,8 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         g2.nch = 0;
         if (tc) {
             g2.out_bf16 = (uint16_t*)c->opA16.p;
-            g2.site_stride = (int64_t)(4 * perA);
+            g2.out_planes = npl;
+            g2.site_stride = (int64_t)(npl * perA);
         } else {
             g2.out_c64 = (float2*)c->opA32.p;
             g2.site_stride = (int64_t)perA;
@@ -699,7 +703,8 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         g1.H = (const float2*)H;
         if (tc) {
             g1.out_bf16 = (uint16_t*)c->opB16.p;
-            g1.site_stride = (int64_t)(4 * perB);
+            g1.out_planes = npl;
+            g1.site_stride = (int64_t)(npl * perB);
         } else {
             g1.out_c64 = (float2*)c->opB32.p;
             g1.site_stride = (int64_t)perB;
@@ -710,15 +715,16 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             TcArgs A{};
             A.epi = TC_EPI_MT;
             A.N = (rowsB % 256 == 0) ? 256 : 128;
-            if (const char* e = std::getenv("BIP_COUPLING_N")) A.N = std::atoi(e) == 128 ? 128 : A.N;
-            A.A = TcOperand{c->opA16.p, (int64_t)SB * 4 * (int64_t)rowsA, K, 4 * (int64_t)rowsA, (int64_t)rowsA};
-            A.B = TcOperand{c->opB16.p, (int64_t)SB * 4 * (int64_t)rowsB, K, 4 * (int64_t)rowsB, (int64_t)rowsB};
+            A.npl = npl;
+            A.out_planes = npl;
+            A.A = TcOperand{c->opA16.p, (int64_t)SB * npl * (int64_t)rowsA, K, npl * (int64_t)rowsA, (int64_t)rowsA};
+            A.B = TcOperand{c->opB16.p, (int64_t)SB * npl * (int64_t)rowsB, K, npl * (int64_t)rowsB, (int64_t)rowsB};
             A.kb = K / 32;
             A.n_sites = nb;
             A.mt_per = Dpad / 128;
             A.nt_per = (int)(rowsB / A.N);
             A.out16 = (uint16_t*)c->mt16.p;
-            A.out_site = 4 * (int64_t)perMt;
+            A.out_site = npl * (int64_t)perMt;
             A.out_plane = (int64_t)perMt;
             A.out_ld = (int64_t)nch * Dpad;
             A.ep_B = Bpad;
@@ -728,7 +734,8 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             TcArgs Gq{};
             Gq.epi = TC_EPI_Q;
             Gq.N = (Bpad % 256 == 0) ? 256 : 128;
-            Gq.A = TcOperand{c->mt16.p, (int64_t)SB * 4 * Bpad, (int64_t)nch * Dpad, 4 * (int64_t)Bpad, Bpad};
+            Gq.npl = npl;
+            Gq.A = TcOperand{c->mt16.p, (int64_t)SB * npl * Bpad, (int64_t)nch * Dpad, npl * (int64_t)Bpad, Bpad};
             Gq.B = Gq.A;
             Gq.kb = nch * Dpad / 32;
             Gq.n_sites = nb;
@@ -745,6 +752,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             TcArgs Qd{};
             Qd.epi = TC_EPI_QUAD;
             Qd.N = tile;
+            Qd.npl = 4;
             Qd.A = TcOperand{c->q16.p, (int64_t)SB * 4 * Bpad, Bpad, 4 * (int64_t)Bpad, Bpad};
             Qd.B = TcOperand{c->ctb.p, 4 * (int64_t)Ppad, Bpad, 0, Ppad};
             Qd.kb = Bpad / 32;
@@ -933,7 +941,8 @@ bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_ou
     const bip_config& g = c->cfg;
     const BipGeometry& geo = c->geo;
     const int K = g.win * g.win, Bpad = c->Bpad, Dpad = c->Dpad, nch = c->nch_max;
-    const bool tc = c->prec == BIP_PREC_SPLIT_BF16;
+    const bool tc = c->prec != BIP_PREC_FP32;
+    const int npl = c->prec == BIP_PREC_MIXED ? 2 : 4;
     const size_t perA = (size_t)Dpad * K, perB = (size_t)nch * Bpad * K;
     const size_t ldc = (size_t)nch * Bpad;
     DevBuf& opA = tc ? c->opA16 : c->opA32;
@@ -964,8 +973,8 @@ bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_ou
     g1.nch = nch;
     g1.H = (const float2*)H;
     if (tc) {
-        g2.out_bf16 = (uint16_t*)opA.p; g2.site_stride = (int64_t)(4 * perA);
-        g1.out_bf16 = (uint16_t*)opB.p; g1.site_stride = (int64_t)(4 * perB);
+        g2.out_bf16 = (uint16_t*)opA.p; g2.out_planes = npl; g2.site_stride = (int64_t)(npl * perA);
+        g1.out_bf16 = (uint16_t*)opB.p; g1.out_planes = npl; g1.site_stride = (int64_t)(npl * perB);
     } else {
         g2.out_c64 = (float2*)opA.p; g2.site_stride = (int64_t)perA;
         g1.out_c64 = (float2*)opB.p; g1.site_stride = (int64_t)perB;
@@ -978,8 +987,9 @@ bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_ou
         TcArgs A{};
         A.epi = TC_EPI_C32;
         A.N = (ldc % 256 == 0) ? 256 : 128;
-        A.A = TcOperand{opA.p, 4 * (int64_t)Dpad, K, 4 * (int64_t)Dpad, Dpad};
-        A.B = TcOperand{opB.p, 4 * (int64_t)ldc, K, 4 * (int64_t)ldc, (int64_t)ldc};
+        A.npl = npl;
+        A.A = TcOperand{opA.p, npl * (int64_t)Dpad, K, npl * (int64_t)Dpad, Dpad};
+        A.B = TcOperand{opB.p, npl * (int64_t)ldc, K, npl * (int64_t)ldc, (int64_t)ldc};
         A.kb = K / 32;
         A.n_sites = 1;
         A.mt_per = Dpad / 128;

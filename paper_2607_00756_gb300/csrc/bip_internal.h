@@ -102,7 +102,9 @@ struct GatherArgs {
     const float2* H;                // [sum nch, win, win]
     // outputs (one of the two layouts)
     float2* out_c64;                // [n_sites][rows_total][K] complex64
-    uint16_t* out_bf16;             // [n_sites][4 planes][rows_total][K]  (re_hi, re_lo, im_hi, im_lo)
+    uint16_t* out_bf16;             // [n_sites][planes][rows_total][K]: 4 planes (re_hi, re_lo,
+                                    // im_hi, im_lo) or 2 planes (re, im)
+    int out_planes;                 // 4 or 2
     int64_t site_stride;            // elements per site in the output
     int K;                          // window pixels (row length)
 };
@@ -154,10 +156,10 @@ cudaError_t bip_reduce_sites(const float* partial, int n_sites, int P, const dou
 cudaError_t bip_zero_outside(float* partial, int n_sites, int P, const double* scans,
                              const SiteDev* sites, int ny, int nx, int fy, int fx, cudaStream_t s);
 
-// gemm_tc.cu : tcgen05 split-BF16 complex contractions.
-// Operands are four bf16 planes (re_hi, re_lo, im_hi, im_lo), K contiguous,
-// seen by TMA as one 2-D tensor [rows][K]; row (site, plane, r) is at
-// site * site_rows + plane * plane_rows + r.
+// gemm_tc.cu : tcgen05 complex contractions in split BF16 or BF16.
+// Operands are bf16 planes, K contiguous -- four (re_hi, re_lo, im_hi,
+// im_lo) or two (re, im) -- seen by TMA as one 2-D tensor [rows][K]; row
+// (site, plane, r) is at site * site_rows + plane * plane_rows + r.
 enum TcEpilogue { TC_EPI_MT = 0, TC_EPI_Q = 1, TC_EPI_C32 = 2, TC_EPI_QUAD = 3 };
 struct TcOperand {
     const void* base;               // bf16 planes
@@ -167,6 +169,8 @@ struct TcOperand {
 struct TcArgs {
     int epi;                        // TcEpilogue
     int N;                          // 128 or 256 (tile columns)
+    int npl;                        // operand planes: 4 (split BF16) or 2 (BF16: re, im)
+    int out_planes;                 // MT epilogue: planes written (4 or 2)
     TcOperand A, B;                 // A tiles of 128 rows, B tiles of N rows
     int kb;                         // K blocks of 32
     int n_sites, mt_per, nt_per;    // tiles per site (MT, Q, C32)

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 3) gather_kernel(GatherArgs a, int t
                 float4* dst = reinterpret_cast<float4*>(a.out_c64 + (size_t)bs * a.site_stride + row * a.K + rr);
                 dst[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
                 dst[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
-            } else {
+            } else if (a.out_planes == 4) {
                 uint16_t* base = a.out_bf16 + (size_t)bs * a.site_stride + row * a.K + rr;
                 const Split4 re = split4(o[0].x, o[1].x, o[2].x, o[3].x);
                 const Split4 im = split4(o[0].y, o[1].y, o[2].y, o[3].y);
@@ -210,6 +210,12 @@ __global__ void __launch_bounds__(kThreads, 3) gather_kernel(GatherArgs a, int t
                 *reinterpret_cast<uint2*>(base + plane) = re.lo;
                 *reinterpret_cast<uint2*>(base + 2 * plane) = im.hi;
                 *reinterpret_cast<uint2*>(base + 3 * plane) = im.lo;
+            } else {
+                uint16_t* base = a.out_bf16 + (size_t)bs * a.site_stride + row * a.K + rr;
+                *reinterpret_cast<uint2*>(base) =
+                    make_uint2(pack_bf16x2(o[0].x, o[1].x), pack_bf16x2(o[2].x, o[3].x));
+                *reinterpret_cast<uint2*>(base + plane) =
+                    make_uint2(pack_bf16x2(o[0].y, o[1].y), pack_bf16x2(o[2].y, o[3].y));
             }
         }
         cur = nxt;

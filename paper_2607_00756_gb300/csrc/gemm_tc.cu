@@ -1,14 +1,15 @@
-// Split-BF16 complex contractions on the 5th-generation tensor cores
-// (tcgen05.mma, TMEM accumulators, TMA operand staging).
+// Complex contractions on the 5th-generation tensor cores (tcgen05.mma,
+// TMEM accumulators, TMA operand staging), in split BF16 or BF16.
 //
-// Every complex FP32 operand is stored as four BF16 planes: x = hi + lo with
-// hi = bf16(x), lo = bf16(x - hi), for the real and the imaginary part.  A
-// real product A B is taken as A_hi B_hi + A_hi B_lo + A_lo B_hi (the
-// lo*lo term is below FP32 rounding), accumulated in FP32 in TMEM, and the
-// complex product as
+// Split BF16: every complex FP32 operand is stored as four BF16 planes,
+// x = hi + lo with hi = bf16(x), lo = bf16(x - hi), for the real and the
+// imaginary part.  A real product A B is taken as A_hi B_hi + A_hi B_lo +
+// A_lo B_hi (the lo*lo term is below FP32 rounding), accumulated in FP32 in
+// TMEM, and the complex product as
 //   Re += Ar Br -/+ Ai Bi,   Im += Ar Bi +/- Ai Br     (-/+: op(A) = A / conj A)
 // -- twelve MMAs per K step into two accumulators, the signs carried by the
-// instruction descriptor's negate-A bit.
+// instruction descriptor's negate-A bit.  BF16: two planes (re, im), one
+// product per real product, four MMAs per K step.
 //
 // Kernel: persistent, one CTA per SM, 192 threads:
 //   warp 0      TMA producer (one elected thread): 4 A planes + 4 B planes
@@ -185,13 +186,23 @@ struct UnitIter {
     }
 };
 
-template <int N, int EPI>
+template <int N, int NPL>
+struct TcShape {
+    static constexpr int B_TILE = N * 64;
+    static constexpr int STAGE = NPL * kATile + NPL * B_TILE;
+    static constexpr int STAGES = (196608 / STAGE) > 6 ? 6 : (196608 / STAGE);
+    static constexpr int NACC = N == 256 ? 1 : 2;
+    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256 + 5 * N * sizeof(float);
+};
+
+template <int N, int EPI, int NPL>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const TcArgs p) {
-    constexpr int STAGES = N == 256 ? 2 : 3;
-    constexpr int NACC = N == 256 ? 1 : 2;
-    constexpr int B_TILE = N * 64;
-    constexpr int STAGE = 4 * kATile + 4 * B_TILE;
+    using Sh = TcShape<N, NPL>;
+    constexpr int STAGES = Sh::STAGES;
+    constexpr int NACC = Sh::NACC;
+    constexpr int B_TILE = Sh::B_TILE;
+    constexpr int STAGE = Sh::STAGE;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE);
@@ -256,11 +267,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     uint8_t* st = smem + s * STAGE;
                     mbar_expect_tx(&full[s], STAGE);
 #pragma unroll
-                    for (int pl = 0; pl < 4; ++pl)
+                    for (int pl = 0; pl < NPL; ++pl)
                         tma_2d(st + pl * kATile, &mapA, kb * 32, (int)(a0 + pl * p.A.plane_rows), &full[s]);
 #pragma unroll
-                    for (int pl = 0; pl < 4; ++pl)
-                        tma_2d(st + 4 * kATile + pl * B_TILE, &mapB, kb * 32, (int)(b0 + pl * p.B.plane_rows),
+                    for (int pl = 0; pl < NPL; ++pl)
+                        tma_2d(st + NPL * kATile + pl * B_TILE, &mapB, kb * 32, (int)(b0 + pl * p.B.plane_rows),
                                &full[s]);
                     ++issued;
                     if (++s == STAGES) {
@@ -308,27 +319,36 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t base = smem_u32(smem + s * STAGE);
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
-                        uint64_t ad[4], bd[4];
+                        uint64_t ad[NPL], bd[NPL];
 #pragma unroll
-                        for (int pl = 0; pl < 4; ++pl) {
+                        for (int pl = 0; pl < NPL; ++pl) {
                             ad[pl] = sdesc(base + pl * kATile + kk * 32);
-                            bd[pl] = sdesc(base + 4 * kATile + pl * B_TILE + kk * 32);
+                            bd[pl] = sdesc(base + NPL * kATile + pl * B_TILE + kk * 32);
                         }
                         const uint32_t first = (kb == u.kb0 && kk == 0) ? 0u : 1u;
-                        // Re: Ar Br (+), Ai Bi (-, or + for conj A)
-                        mma(dr, ad[0], bd[0], id_pos, first);
-                        mma(dr, ad[0], bd[1], id_pos, 1);
-                        mma(dr, ad[1], bd[0], id_pos, 1);
-                        mma(dr, ad[2], bd[2], id_ii, 1);
-                        mma(dr, ad[2], bd[3], id_ii, 1);
-                        mma(dr, ad[3], bd[2], id_ii, 1);
-                        // Im: Ar Bi (+), Ai Br (+, or - for conj A)
-                        mma(di, ad[0], bd[2], id_pos, first);
-                        mma(di, ad[0], bd[3], id_pos, 1);
-                        mma(di, ad[1], bd[2], id_pos, 1);
-                        mma(di, ad[2], bd[0], id_ir, 1);
-                        mma(di, ad[2], bd[1], id_ir, 1);
-                        mma(di, ad[3], bd[0], id_ir, 1);
+                        if (NPL == 4) {
+                            // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
+                            // Re: Ar Br (+), Ai Bi (-, or + for conj A)
+                            mma(dr, ad[0], bd[0], id_pos, first);
+                            mma(dr, ad[0], bd[1], id_pos, 1);
+                            mma(dr, ad[1], bd[0], id_pos, 1);
+                            mma(dr, ad[2], bd[2], id_ii, 1);
+                            mma(dr, ad[2], bd[3], id_ii, 1);
+                            mma(dr, ad[3], bd[2], id_ii, 1);
+                            // Im: Ar Bi (+), Ai Br (+, or - for conj A)
+                            mma(di, ad[0], bd[2], id_pos, first);
+                            mma(di, ad[0], bd[3], id_pos, 1);
+                            mma(di, ad[1], bd[2], id_pos, 1);
+                            mma(di, ad[2], bd[0], id_ir, 1);
+                            mma(di, ad[2], bd[1], id_ir, 1);
+                            mma(di, ad[3], bd[0], id_ir, 1);
+                        } else {
+                            // planes: 0 re, 1 im
+                            mma(dr, ad[0], bd[0], id_pos, first);
+                            mma(dr, ad[NPL - 1], bd[NPL - 1], id_ii, 1);
+                            mma(di, ad[0], bd[NPL - 1], id_pos, first);
+                            mma(di, ad[NPL - 1], bd[0], id_ir, 1);
+                        }
                     }
                     any = true;
                     mma_commit(&empty[s]);
@@ -390,10 +410,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int ch = n / p.ep_B, b = n % p.ep_B;
                         const int64_t at = (int64_t)b * p.out_ld + (int64_t)ch * p.ep_Dp + row;
                         const uint16_t rh = bf16_rn(vr[j]), ih = bf16_rn(vi[j]);
-                        o[at] = rh;
-                        o[p.out_plane + at] = bf16_rn(vr[j] - bf16_f(rh));
-                        o[2 * p.out_plane + at] = ih;
-                        o[3 * p.out_plane + at] = bf16_rn(vi[j] - bf16_f(ih));
+                        if (p.out_planes == 4) {
+                            o[at] = rh;
+                            o[p.out_plane + at] = bf16_rn(vr[j] - bf16_f(rh));
+                            o[2 * p.out_plane + at] = ih;
+                            o[3 * p.out_plane + at] = bf16_rn(vi[j] - bf16_f(ih));
+                        } else {
+                            o[at] = rh;
+                            o[p.out_plane + at] = ih;
+                        }
                     }
                 } else if (EPI == TC_EPI_Q) {
                     uint16_t* o = p.out16 + (int64_t)u.bs * p.out_site + (int64_t)row * p.out_ld + u.nt * N + c0;
@@ -540,18 +565,23 @@ cudaError_t make_map(CUtensorMap* m, const TcOperand& op, int box_rows) {
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int N, int EPI>
+template <int N, int EPI, int NPL>
 cudaError_t launch(const TcArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid, cudaStream_t s) {
-    constexpr int STAGES = N == 256 ? 2 : 3;
-    constexpr size_t smem = 1024 + STAGES * (4 * kATile + 4 * N * 64) + 256 + 5 * N * sizeof(float);
+    constexpr size_t smem = TcShape<N, NPL>::SMEM;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_kernel<N, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(tc_kernel<N, EPI, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    tc_kernel<N, EPI><<<grid, kThreads, smem, s>>>(ma, mb, a);
+    tc_kernel<N, EPI, NPL><<<grid, kThreads, smem, s>>>(ma, mb, a);
     return cudaGetLastError();
+}
+
+template <int EPI, int NPL>
+cudaError_t launch_n(const TcArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid, cudaStream_t s) {
+    return a.N == 256 ? launch<256, EPI, NPL>(a, ma, mb, grid, s) : launch<128, EPI, NPL>(a, ma, mb, grid, s);
 }
 
 int num_sms() {
@@ -573,9 +603,10 @@ cudaError_t bip_tc_gemm(const TcArgs& a, cudaStream_t s) {
     if (a.A.k != a.B.k || a.kb * 32 != a.A.k) return cudaErrorInvalidValue;
     if (a.epi != TC_EPI_QUAD) {
         if (a.n_sites < 1 || a.mt_per < 1 || a.nt_per < 1) return cudaErrorInvalidValue;
-        if ((int64_t)(a.n_sites - 1) * a.A.site_rows + 3 * a.A.plane_rows + (int64_t)a.mt_per * 128 > a.A.rows)
+        const int64_t pl = a.npl - 1;
+        if ((int64_t)(a.n_sites - 1) * a.A.site_rows + pl * a.A.plane_rows + (int64_t)a.mt_per * 128 > a.A.rows)
             return cudaErrorInvalidValue;
-        if ((int64_t)(a.n_sites - 1) * a.B.site_rows + 3 * a.B.plane_rows + (int64_t)a.nt_per * a.N > a.B.rows)
+        if ((int64_t)(a.n_sites - 1) * a.B.site_rows + pl * a.B.plane_rows + (int64_t)a.nt_per * a.N > a.B.rows)
             return cudaErrorInvalidValue;
     } else {
         if (a.n_work == 0) return cudaSuccess;
@@ -588,15 +619,17 @@ cudaError_t bip_tc_gemm(const TcArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const int units = a.epi == TC_EPI_QUAD ? a.n_work : a.n_sites * a.mt_per * a.nt_per;
     const int grid = units < num_sms() ? units : num_sms();
-    switch (a.epi * 2 + (a.N == 256)) {
-        case TC_EPI_MT * 2: return launch<128, TC_EPI_MT>(a, ma, mb, grid, s);
-        case TC_EPI_MT * 2 + 1: return launch<256, TC_EPI_MT>(a, ma, mb, grid, s);
-        case TC_EPI_Q * 2: return launch<128, TC_EPI_Q>(a, ma, mb, grid, s);
-        case TC_EPI_Q * 2 + 1: return launch<256, TC_EPI_Q>(a, ma, mb, grid, s);
-        case TC_EPI_C32 * 2: return launch<128, TC_EPI_C32>(a, ma, mb, grid, s);
-        case TC_EPI_C32 * 2 + 1: return launch<256, TC_EPI_C32>(a, ma, mb, grid, s);
-        case TC_EPI_QUAD * 2: return launch<128, TC_EPI_QUAD>(a, ma, mb, grid, s);
-        case TC_EPI_QUAD * 2 + 1: return launch<256, TC_EPI_QUAD>(a, ma, mb, grid, s);
+    if (a.npl != 4 && a.npl != 2) return cudaErrorInvalidValue;
+    const bool split = a.npl == 4;
+    switch (a.epi) {
+        case TC_EPI_MT: return split ? launch_n<TC_EPI_MT, 4>(a, ma, mb, grid, s)
+                                     : launch_n<TC_EPI_MT, 2>(a, ma, mb, grid, s);
+        case TC_EPI_Q: return split ? launch_n<TC_EPI_Q, 4>(a, ma, mb, grid, s)
+                                    : launch_n<TC_EPI_Q, 2>(a, ma, mb, grid, s);
+        case TC_EPI_C32: return split ? launch_n<TC_EPI_C32, 4>(a, ma, mb, grid, s)
+                                      : launch_n<TC_EPI_C32, 2>(a, ma, mb, grid, s);
+        case TC_EPI_QUAD: return split ? launch_n<TC_EPI_QUAD, 4>(a, ma, mb, grid, s)
+                                       : cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
 }

@@ -156,7 +156,7 @@ def test_anisotropic_grid(lib):
 # ---------------------------------------------------------------------------
 # split-BF16 tensor-core path (tcgen05): rel L2 <= 1e-3 for maps
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("split_bf16", 1e-4)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("split_bf16", 1e-4), ("mixed", 1e-2)])
 def test_coupling_parity(lib, c1, prec, tol):
     """Coupling matrices M^(n) (Eq. coupling) of every site, both precisions."""
     cfg, sp, pr, ref = c1
@@ -168,30 +168,34 @@ def test_coupling_parity(lib, c1, prec, tol):
         assert rel(got, want) < tol, (prec, k, rel(got, want))
 
 
-def test_map_split_bf16_config1(lib, c1):
-    """Config 3: config 1 with the contraction in split-BF16 (hi + lo)."""
+@pytest.mark.parametrize("prec", ["split_bf16", "mixed"])
+def test_map_split_bf16_config1(lib, c1, prec):
+    """Config 3: config 1 with the contraction in split-BF16 (hi + lo), and
+    the mixed mode (BF16 coupling and Gram, split-BF16 quadratic form)."""
     cfg, sp, pr, ref = c1
-    _, m, parts, _ = gpu_run(lib, cfg, sp, prec="split_bf16")
+    _, m, parts, _ = gpu_run(lib, cfg, sp, prec=prec)
     assert rel(m, ref.map) < 1e-3
     assert rel(parts, ref.partials) < 1e-3
     for k in range(len(pr.ion)):
         assert np.all(parts[k][~obip.crop_mask(pr, k, pr.scans)] == 0.0)
 
 
-def test_map_split_bf16_edge_cases(lib):
+@pytest.mark.parametrize("prec", ["split_bf16", "mixed"])
+def test_map_split_bf16_edge_cases(lib, prec):
     cfg, sp = _edge_specimen()
     pr = obip.make_problem(sp)
     ref = obip.bip_map(pr)
-    _, m, parts, _ = gpu_run(lib, cfg, sp, prec="split_bf16")
+    _, m, parts, _ = gpu_run(lib, cfg, sp, prec=prec)
     assert rel(m, ref.map) < 1e-3
     assert rel(parts, ref.partials) < 1e-3
 
 
-def test_map_split_bf16_anisotropic(lib):
+@pytest.mark.parametrize("prec", ["split_bf16", "mixed"])
+def test_map_split_bf16_anisotropic(lib, prec):
     cfg = synth.config1().replace(name="aniso", ny=64, nx=128, ly=7.5, lx=10.0, cells_y=3, cells_x=4,
                                   fy=1, fx=2, win=32, ion_cells=(1, 3), ion_slices=(1, 4),
                                   scan_y=(10.3, 3.5, 9), scan_x=(20.7, 6.25, 7))
     sp = synth.make_specimen(cfg)
     ref = obip.bip_map(obip.make_problem(sp))
-    _, m, _, _ = gpu_run(lib, cfg, sp, prec="split_bf16")
+    _, m, _, _ = gpu_run(lib, cfg, sp, prec=prec)
     assert rel(m, ref.map) < 1e-3
