@@ -146,7 +146,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # GPU arm
 
-def algorithmic(cfg, geo_sizes, n_sites, n_crop, nch):
+def algorithmic(cfg, geo_sizes, n_sites, n_crop, nch, geo_beams=None):
     """Per-stage algorithmic work of one step (flops or bytes), the figures
     the roofline fractions divide."""
     B, n_det, bp1, bp2 = geo_sizes
@@ -154,7 +154,13 @@ def algorithmic(cfg, geo_sizes, n_sites, n_crop, nch):
     G = cfg.ny * cfg.nx
     cmac_coupling = n_det * nch * B * K * n_sites
     cmac_gram = B * B * nch * n_det * n_sites
-    cmac_quad = B * B * n_crop
+    # c^H Q c per scan as a polynomial over beam-lattice differences: the
+    # Q binning (B (B+1)/2 pairs per site) plus one complex MAC per
+    # difference (half of the (4K_y+1)(4K_x+1) lattice) per in-crop scan
+    ky = max(abs(int(h[0])) // cfg.fy for h in geo_beams) if geo_beams is not None else 0
+    kx = max(abs(int(h[1])) // cfg.fx for h in geo_beams) if geo_beams is not None else 0
+    n_diff = ((4 * ky + 1) * (4 * kx + 1) + 1) // 2
+    cmac_quad = n_sites * B * (B + 1) // 2 + n_diff * n_crop
     return {
         "coupling": 8.0 * cmac_coupling,        # real flops (complex MAC = 8)
         "gram": 8.0 * cmac_gram,
@@ -286,7 +292,7 @@ def roofline(cfg, path, res, info, geo_sizes):
     """Roofline of the step's dominant kernel, from the live per-stage
     event timings."""
     prof = res["profile"]
-    alg = algorithmic(cfg, geo_sizes, info["n_sites"], info["n_crop"], info["nch"])
+    alg = algorithmic(cfg, geo_sizes, info["n_sites"], info["n_crop"], info["nch"], info.get("beams"))
     stage, (ms, n) = max(prof.items(), key=lambda kv: kv[1][0])
     peaks = info["peaks"]
     steps = None
@@ -297,7 +303,13 @@ def roofline(cfg, path, res, info, geo_sizes):
         # per launch: the step's work over the step's launches of this stage
         per_step_launches = n / res["steps"]
         per_launch = flops_step / per_step_launches
-        if path in ("split_bf16", "mixed"):
+        if stage == "quadform":
+            # FP32 SIMT evaluation of the difference polynomial
+            achieved = per_launch / (ms_launch / 1e3) / 1e12
+            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            out.update(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
+                       peak_source="FP32 FMA: 152 SM x 128 lanes x 2 flop x max SM clock")
+        elif path in ("split_bf16", "mixed"):
             # BF16 products per real product: three for hi*hi + hi*lo + lo*hi,
             # one for plain BF16 (coupling and Gram of the mixed mode)
             terms = 1.0 if (path == "mixed" and stage in ("coupling", "gram")) else 3.0
@@ -434,6 +446,7 @@ def main():
     from paper_2607_00756_gb300 import capi
     ctx = capi.bip_create(capi.make_config(cfg))
     geo_sizes = capi.bip_query(ctx)[:4]
+    info["beams"] = capi.bip_get_geometry(ctx)["h_beam"]
     capi.bip_destroy(ctx)
     ok = [p for p in paths if "error" not in results[p]]
     head = ok[0]

@@ -14,8 +14,7 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kRowPad = 128;        // operand rows padded to the MMA tile
-constexpr int kScanTile = 64;       // scans per quadratic-form work item (FP32 path)
-constexpr int kScanTileTc = 128;    // scans per work item (split-BF16 path)
+constexpr int kScanTile = 256;      // scans per quadratic-form work item
 
 struct DevBuf {
     void* p = nullptr;
@@ -35,6 +34,8 @@ struct bip_ctx {
     bool tables = false;
     DevBuf twy, twx, py, px, ey, ex, shift1, shift2, hbeam, hdet, coef;
     DevBuf ell1_idx, ell1_w, ell2_idx, ell2_w, ell1_n, ell2_n;
+    DevBuf kb_d, lat_d;                 // beam lattice of the difference transform
+    int Ky = 0, Kx = 0;
     int ell1_k = 0, ell2_k = 0;
 
     // sites of the current builds
@@ -49,7 +50,7 @@ struct bip_ctx {
     DevBuf stash1, stash2, cols;
 
     // map workspaces
-    DevBuf scans_d, ct, ctb, work_d, partial;
+    DevBuf scans_d, work_d, partial, gdiff;
     DevBuf opA32, opB32, mt32, q32;     // FP32 path (zeroed at allocation)
     DevBuf opA16, opB16, mt16, q16;     // split-BF16 path (zeroed at allocation)
     DevBuf errflag;
@@ -219,6 +220,20 @@ bip_status make_tables(bip_ctx* c, cudaStream_t s) {
         const std::complex<double> v = fyfx * geo.psi_beam[b] / geo.psi_norm;
         coef[b] = double2{v.real(), v.imag()};
     }
+    // beam lattice k = h / f of the difference transform
+    std::vector<int2> kb(geo.B);
+    int Ky = 0, Kx = 0;
+    for (int b = 0; b < geo.B; ++b) {
+        kb[b] = int2{geo.h_beam[2 * b] / g.fy, geo.h_beam[2 * b + 1] / g.fx};
+        Ky = std::max(Ky, std::abs(kb[b].x));
+        Kx = std::max(Kx, std::abs(kb[b].y));
+    }
+    std::vector<int32_t> lat((size_t)(2 * Ky + 1) * (2 * Kx + 1), -1);
+    for (int b = 0; b < geo.B; ++b) lat[(size_t)(kb[b].x + Ky) * (2 * Kx + 1) + kb[b].y + Kx] = b;
+    c->Ky = Ky;
+    c->Kx = Kx;
+    CUDA_TRY(c, upload(c->kb_d, kb, s));
+    CUDA_TRY(c, upload(c->lat_d, lat, s));
     std::vector<uint16_t> i1, i2;
     std::vector<int32_t> n1, n2;
     std::vector<float> w1, w2;
@@ -428,8 +443,8 @@ bip_status bip_destroy(bip_ctx* c) {
     if (!c) return BIP_ERR_INVALID_ARG;
     DevBuf* all[] = {&c->twy, &c->twx, &c->py, &c->px, &c->ey, &c->ex, &c->shift1, &c->shift2, &c->hbeam,
                      &c->hdet, &c->coef, &c->ell1_idx, &c->ell1_w, &c->ell2_idx, &c->ell2_w, &c->ell1_n, &c->ell2_n, &c->sites_d,
-                     &c->plane_ids_d, &c->seq_ids_d, &c->row_off_d, &c->row_ent_d, &c->stash1, &c->stash2, &c->cols, &c->scans_d, &c->ct,
-                     &c->ctb, &c->work_d, &c->partial, &c->opA32, &c->opB32, &c->mt32, &c->q32, &c->opA16,
+                     &c->plane_ids_d, &c->seq_ids_d, &c->row_off_d, &c->row_ent_d, &c->stash1, &c->stash2, &c->cols, &c->scans_d,
+                     &c->gdiff, &c->kb_d, &c->lat_d, &c->work_d, &c->partial, &c->opA32, &c->opB32, &c->mt32, &c->q32, &c->opA16,
                      &c->opB16, &c->mt16, &c->q16, &c->errflag};
     for (DevBuf* b : all) release(*b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -596,19 +611,12 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     const bool tc = c->prec != BIP_PREC_FP32;
     // planes of the coupling and Gram operands: split BF16 (4) or BF16 (2)
     const int npl = c->prec == BIP_PREC_MIXED ? 2 : 4;
-    const int tile = tc ? kScanTileTc : kScanTile;
+    const int tile = kScanTile;
     const int n_tiles = (P + tile - 1) / tile;
+    const int nd = (2 * c->Ky + 1) * (4 * c->Kx + 1);
 
     CUDA_TRY(c, ensure(c->scans_d, (size_t)P * 2 * sizeof(double), false, s));
     CUDA_TRY(c, cudaMemcpyAsync(c->scans_d.p, scans, (size_t)P * 2 * sizeof(double), cudaMemcpyHostToDevice, s));
-    const int Ppad = n_tiles * tile;
-    CUDA_TRY(c, ensure(c->ct, (size_t)Ppad * Bpad * sizeof(float2), true, s));
-    size_t ct_plane = (size_t)Ppad * Bpad;
-    if (tc) CUDA_TRY(c, ensure(c->ctb, 4 * ct_plane * sizeof(uint16_t), true, s));
-    TIMED(c, BIP_STAGE_REDUCE, s, bip_illumination((const double*)c->scans_d.p, P, (const int2*)c->hbeam.p,
-                                 (const double2*)c->coef.p, geo.B, Bpad, g.ny, g.nx, (float2*)c->ct.p,
-                                 tc ? (uint16_t*)c->ctb.p : nullptr, ct_plane, s));
-
     float* partial = partial_out;
     if (!partial) {
         CUDA_TRY(c, ensure(c->partial, (size_t)c->n_sites * P * sizeof(float), false, s));
@@ -636,17 +644,17 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         CUDA_TRY(c, ensure(c->opA32, SB * perA * sizeof(float2), true, s));
         CUDA_TRY(c, ensure(c->opB32, SB * perB * sizeof(float2), true, s));
         CUDA_TRY(c, ensure(c->mt32, SB * perMt * sizeof(float2), true, s));
-        CUDA_TRY(c, ensure(c->q32, SB * perQ * sizeof(float2), true, s));
     } else {
-        // four bf16 planes per complex element: 8 bytes, as complex64
+        // up to four bf16 planes per complex element: 8 bytes, as complex64
         CUDA_TRY(c, ensure(c->opA16, SB * perA * 8, true, s));
         CUDA_TRY(c, ensure(c->opB16, SB * perB * 8, true, s));
         CUDA_TRY(c, ensure(c->mt16, SB * perMt * 8, true, s));
-        CUDA_TRY(c, ensure(c->q16, SB * perQ * 8, true, s));
         CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
     }
+    CUDA_TRY(c, ensure(c->q32, SB * perQ * sizeof(float2), true, s));
+    CUDA_TRY(c, ensure(c->gdiff, (size_t)SB * nd * sizeof(float2), false, s));
 
-    // work lists for all batches, uploaded once
+    // work lists (site in batch, scan tile) for all batches, uploaded once
     std::vector<int32_t>& work = c->work_h;
     work.clear();
     std::vector<int> batch_off;
@@ -684,15 +692,6 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         g2.h_t = (const int2*)c->hdet.p;
         g2.tilt_sign = -1;
         g2.nch = 0;
-        if (tc) {
-            g2.out_bf16 = (uint16_t*)c->opA16.p;
-            g2.out_planes = npl;
-            g2.site_stride = (int64_t)(npl * perA);
-        } else {
-            g2.out_c64 = (float2*)c->opA32.p;
-            g2.site_stride = (int64_t)perA;
-        }
-        TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g2, s));
         GatherArgs g1 = ga;
         g1.Bp = geo.Bp1; g1.n_targets = geo.B; g1.rows_pad = Bpad;
         g1.stash = (const float2*)c->stash1.p;
@@ -702,16 +701,22 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         g1.nch = nch;
         g1.H = (const float2*)H;
         if (tc) {
+            g2.out_bf16 = (uint16_t*)c->opA16.p;
+            g2.out_planes = npl;
+            g2.site_stride = (int64_t)(npl * perA);
             g1.out_bf16 = (uint16_t*)c->opB16.p;
             g1.out_planes = npl;
             g1.site_stride = (int64_t)(npl * perB);
         } else {
+            g2.out_c64 = (float2*)c->opA32.p;
+            g2.site_stride = (int64_t)perA;
             g1.out_c64 = (float2*)c->opB32.p;
             g1.site_stride = (int64_t)perB;
         }
+        TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g2, s));
         TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g1, s));
         if (tc) {
-            // coupling -> Mt planes, Gram -> Q planes, quadratic form -> partials
+            // coupling M = S2^T diag(H) S1, written transposed (bf16 planes)
             TcArgs A{};
             A.epi = TC_EPI_MT;
             A.N = (rowsB % 256 == 0) ? 256 : 128;
@@ -731,8 +736,9 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             A.ep_Dp = Dpad;
             A.err = (int*)c->errflag.p;
             TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(A, s));
+            // Gram Q = sum_n M^(n)H M^(n), upper triangle, FP32
             TcArgs Gq{};
-            Gq.epi = TC_EPI_Q;
+            Gq.epi = TC_EPI_C32;
             Gq.N = (Bpad % 256 == 0) ? 256 : 128;
             Gq.npl = npl;
             Gq.A = TcOperand{c->mt16.p, (int64_t)SB * npl * Bpad, (int64_t)nch * Dpad, npl * (int64_t)Bpad, Bpad};
@@ -743,72 +749,59 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             Gq.nt_per = Bpad / Gq.N;
             Gq.conjA = 1;
             Gq.tri = 1;
-            Gq.out16 = (uint16_t*)c->q16.p;
-            Gq.out_site = 4 * (int64_t)perQ;
-            Gq.out_plane = (int64_t)perQ;
-            Gq.out_ld = Bpad;
+            Gq.out32 = (float2*)c->q32.p;
+            Gq.out32_site = (int64_t)perQ;
+            Gq.out32_ld = Bpad;
             Gq.err = (int*)c->errflag.p;
             TIMED(c, BIP_STAGE_GRAM, s, bip_tc_gemm(Gq, s));
-            TcArgs Qd{};
-            Qd.epi = TC_EPI_QUAD;
-            Qd.N = tile;
-            Qd.npl = 4;
-            Qd.A = TcOperand{c->q16.p, (int64_t)SB * 4 * Bpad, Bpad, 4 * (int64_t)Bpad, Bpad};
-            Qd.B = TcOperand{c->ctb.p, 4 * (int64_t)Ppad, Bpad, 0, Ppad};
-            Qd.kb = Bpad / 32;
-            Qd.mt_per = Bpad / 128;
-            Qd.tri = 1;
-            Qd.work = (const int32_t*)c->work_d.p + 2 * batch_off[bi];
-            Qd.n_work = batch_off[bi + 1] - batch_off[bi];
-            Qd.ct32 = (const float2*)c->ct.p;
-            Qd.bpad = Bpad;
-            Qd.P = P;
-            Qd.scans = (const double*)c->scans_d.p;
-            Qd.sites = (const SiteDev*)c->sites_d.p;
-            Qd.site_ids = ids;
-            Qd.ny = g.ny; Qd.nx = g.nx; Qd.fy = g.fy; Qd.fx = g.fx;
-            Qd.scale = (float)(g.fy * g.fx);
-            Qd.partial = partial;
-            Qd.err = (int*)c->errflag.p;
-            TIMED(c, BIP_STAGE_QUADFORM, s, bip_tc_gemm(Qd, s));
-            continue;
+        } else {
+            // coupling M = S2^T diag(H) S1, stored transposed for the Gram step
+            CGemmArgs A{};
+            A.M = geo.n_det; A.N = (int)rowsB; A.K = K;
+            A.A = (const float2*)c->opA32.p; A.lda = K; A.strideA = (int64_t)perA;
+            A.Bm = (const float2*)c->opB32.p; A.ldb = K; A.strideB = (int64_t)perB;
+            A.batch = nb;
+            A.epi = 1;
+            A.C = (float2*)c->mt32.p; A.ldc = (int64_t)nch * Dpad; A.strideC = (int64_t)perMt;
+            A.ep_B = Bpad; A.ep_Dp = Dpad;
+            TIMED(c, BIP_STAGE_COUPLING, s, bip_cgemm_simt(A, s));
+            // Gram Q = sum_n M^(n)H M^(n)
+            CGemmArgs Bq{};
+            Bq.M = Bpad; Bq.N = Bpad; Bq.K = nch * Dpad;
+            Bq.A = (const float2*)c->mt32.p; Bq.lda = (int64_t)nch * Dpad; Bq.strideA = (int64_t)perMt;
+            Bq.Bm = Bq.A; Bq.ldb = Bq.lda; Bq.strideB = Bq.strideA;
+            Bq.conjA = 1;
+            Bq.batch = nb;
+            Bq.epi = 0;
+            Bq.C = (float2*)c->q32.p; Bq.ldc = Bpad; Bq.strideC = (int64_t)perQ;
+            TIMED(c, BIP_STAGE_GRAM, s, bip_cgemm_simt(Bq, s));
         }
-        // coupling M = S2^T diag(H) S1, stored transposed for the Gram step
-        CGemmArgs A{};
-        A.M = geo.n_det; A.N = (int)rowsB; A.K = K;
-        A.A = (const float2*)c->opA32.p; A.lda = K; A.strideA = (int64_t)perA;
-        A.Bm = (const float2*)c->opB32.p; A.ldb = K; A.strideB = (int64_t)perB;
-        A.batch = nb;
-        A.epi = 1;
-        A.C = (float2*)c->mt32.p; A.ldc = (int64_t)nch * Dpad; A.strideC = (int64_t)perMt;
-        A.ep_B = Bpad; A.ep_Dp = Dpad;
-        TIMED(c, BIP_STAGE_COUPLING, s, bip_cgemm_simt(A, s));
-        // Gram Q = sum_n M^(n)H M^(n)
-        CGemmArgs Bq{};
-        Bq.M = Bpad; Bq.N = Bpad; Bq.K = nch * Dpad;
-        Bq.A = (const float2*)c->mt32.p; Bq.lda = (int64_t)nch * Dpad; Bq.strideA = (int64_t)perMt;
-        Bq.Bm = Bq.A; Bq.ldb = Bq.lda; Bq.strideB = Bq.strideA;
-        Bq.conjA = 1;
-        Bq.batch = nb;
-        Bq.epi = 0;
-        Bq.C = (float2*)c->q32.p; Bq.ldc = Bpad; Bq.strideC = (int64_t)perQ;
-        TIMED(c, BIP_STAGE_GRAM, s, bip_cgemm_simt(Bq, s));
-        // quadratic form over the site's crop-window scan tiles
-        QuadArgs q{};
-        q.Bpad = Bpad;
-        q.Q = (const float2*)c->q32.p; q.strideQ = (int64_t)perQ;
-        q.Ct = (const float2*)c->ct.p;
-        q.work = (const int32_t*)c->work_d.p + 2 * batch_off[bi];
-        q.n_work = batch_off[bi + 1] - batch_off[bi];
-        q.tile = tile;
-        q.P = P;
-        q.scans = (const double*)c->scans_d.p;
-        q.sites = (const SiteDev*)c->sites_d.p;
-        q.site_ids = ids;
-        q.ny = g.ny; q.nx = g.nx; q.fy = g.fy; q.fx = g.fx;
-        q.scale = (float)(g.fy * g.fx);
-        q.partial = partial;
-        TIMED(c, BIP_STAGE_QUADFORM, s, bip_quadform_simt(q, s));
+        // I_tau(rho) = f_y f_x c^H Q c as a trigonometric polynomial over
+        // beam-lattice differences, on the site's crop-window scan tiles
+        DiffArgs d{};
+        d.n_sites = nb;
+        d.Q = (const float2*)c->q32.p;
+        d.q_site = (int64_t)perQ;
+        d.ldq = Bpad;
+        d.B = geo.B;
+        d.kb = (const int2*)c->kb_d.p;
+        d.coef = (const double2*)c->coef.p;
+        d.Ky = c->Ky;
+        d.Kx = c->Kx;
+        d.lat = (const int32_t*)c->lat_d.p;
+        d.G = (float2*)c->gdiff.p;
+        d.work = (const int32_t*)c->work_d.p + 2 * batch_off[bi];
+        d.n_work = batch_off[bi + 1] - batch_off[bi];
+        d.tile = tile;
+        d.P = P;
+        d.scans = (const double*)c->scans_d.p;
+        d.sites = (const SiteDev*)c->sites_d.p;
+        d.site_ids = ids;
+        d.ny = g.ny; d.nx = g.nx; d.fy = g.fy; d.fx = g.fx;
+        d.scale = (float)(g.fy * g.fx);
+        d.partial = partial;
+        TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_bin(d, s));
+        TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_eval(d, s));
     }
     if (tc) {
         int flag = 0;
@@ -818,10 +811,10 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     }
     if (map_out) {
         TIMED(c, BIP_STAGE_REDUCE, s, bip_reduce_sites(partial, c->n_sites, P, (const double*)c->scans_d.p,
-                                     (const SiteDev*)c->sites_d.p, g.ny, g.nx, g.fy, g.fx, map_out, s));
+                                                       (const SiteDev*)c->sites_d.p, g.ny, g.nx, g.fy, g.fx, map_out, s));
     } else {
         TIMED(c, BIP_STAGE_REDUCE, s, bip_zero_outside(partial, c->n_sites, P, (const double*)c->scans_d.p,
-                                     (const SiteDev*)c->sites_d.p, g.ny, g.nx, g.fy, g.fx, s));
+                                                       (const SiteDev*)c->sites_d.p, g.ny, g.nx, g.fy, g.fx, s));
     }
     return BIP_OK;
 }

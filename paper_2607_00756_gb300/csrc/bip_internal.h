@@ -124,30 +124,31 @@ struct CGemmArgs {
 };
 cudaError_t bip_cgemm_simt(const CGemmArgs& a, cudaStream_t s);
 
-// stage C: per (site, scan tile) quadratic form f_yf_x Re(c^H Q c)
-struct QuadArgs {
-    int Bpad;                       // padded beam count (multiple of 64)
-    const float2* Q;                // [n_sites][Bpad][Bpad] per-site Q (complex)
-    int64_t strideQ;
-    const float2* Ct;               // [P][Bpad] c_b(rho), complex
-    const int32_t* work;            // [n_work][2] (site index in batch, scan tile)
-    int n_work;
-    int tile;                       // scans per tile
-    int P;
-    const double* scans;            // [P][2]
+// difftrans.cu : the per-site quadratic form c^H Q c as a trigonometric
+// polynomial over beam-lattice differences (see the file's header)
+struct DiffArgs {
+    int n_sites;                    // binning: sites in the batch
+    const float2* Q;                // FP32 Gram matrices [site][B..][ldq], upper triangle valid
+    int64_t q_site;
+    int ldq;
+    int B;
+    const int2* kb;                 // [B] beam lattice coordinates h / f (y, x)
+    const double2* coef;            // [B] probe coefficients f_y f_x Psi / norm
+    int Ky, Kx;                     // largest |k| on each axis
+    const int32_t* lat;             // [(2Ky+1)(2Kx+1)] beam at each lattice point, -1 if none
+    float2* G;                      // [site][(2Ky+1)(4Kx+1)] coefficients, Delta <= 0 (lex)
+    // evaluation over (site, scan tile) work items
+    const int32_t* work;
+    int n_work, tile, P;
+    const double* scans;
     const SiteDev* sites;
-    const int32_t* site_ids;        // batch -> global site index
+    const int32_t* site_ids;
     int ny, nx, fy, fx;
     float scale;                    // f_y f_x
     float* partial;                 // [n_sites_total][P]
 };
-cudaError_t bip_quadform_simt(const QuadArgs& a, cudaStream_t s);
-
-// illumination table Ct[rho][b] (complex64) and/or its split-BF16 planes
-// (4 planes of `plane` elements: re_hi, re_lo, im_hi, im_lo)
-cudaError_t bip_illumination(const double* scans, int P, const int2* h_beam, const double2* coef,
-                             int B, int Bpad, int ny, int nx, float2* Ct, uint16_t* Ct_bf16,
-                             size_t plane, cudaStream_t s);
+cudaError_t bip_diff_bin(const DiffArgs& a, cudaStream_t s);
+cudaError_t bip_diff_eval(const DiffArgs& a, cudaStream_t s);
 
 // reduce.cu : map[rho] = Neumaier sum over sites of the in-crop partials
 cudaError_t bip_reduce_sites(const float* partial, int n_sites, int P, const double* scans,
@@ -160,7 +161,7 @@ cudaError_t bip_zero_outside(float* partial, int n_sites, int P, const double* s
 // Operands are bf16 planes, K contiguous -- four (re_hi, re_lo, im_hi,
 // im_lo) or two (re, im) -- seen by TMA as one 2-D tensor [rows][K]; row
 // (site, plane, r) is at site * site_rows + plane * plane_rows + r.
-enum TcEpilogue { TC_EPI_MT = 0, TC_EPI_Q = 1, TC_EPI_C32 = 2, TC_EPI_QUAD = 3 };
+enum TcEpilogue { TC_EPI_MT = 0, TC_EPI_C32 = 2 };
 struct TcOperand {
     const void* base;               // bf16 planes
     int64_t rows, k;                // tensor extent (k multiple of 32)
@@ -175,29 +176,15 @@ struct TcArgs {
     int kb;                         // K blocks of 32
     int n_sites, mt_per, nt_per;    // tiles per site (MT, Q, C32)
     int conjA;
-    // Hermitian use of the Gram matrix: Q writes only its upper triangle as
-    // Q' (diagonal kept, off-diagonal doubled, lower zero) and skips tiles
-    // below the diagonal; QUAD then starts each M tile at the diagonal,
-    // since c^H Q c = Re(c^H Q' c).
+    // Hermitian output: tiles entirely below the diagonal are skipped
     int tri;
-    // MT / Q epilogues: bf16 planes out[site][plane][row][ld]
+    // MT epilogue: bf16 planes out[site][plane][row][ld]
     uint16_t* out16;
     int64_t out_site, out_plane, out_ld;
     int ep_B, ep_Dp;                // MT: column n = (n / ep_B, n % ep_B) -> Mt[b][ch*ep_Dp + m]
     // C32 epilogue: complex64 out32[site][m][ld]
     float2* out32;
     int64_t out32_site, out32_ld;
-    // QUAD epilogue: per (site, scan tile) work items, M tiles looped inside
-    const int32_t* work;            // [n_work][2] (site in batch, scan tile)
-    int n_work;
-    const float2* ct32;             // [Ppad][bpad] c_b(rho)
-    int bpad, P;
-    const double* scans;
-    const SiteDev* sites;
-    const int32_t* site_ids;
-    int ny, nx, fy, fx;
-    float scale;
-    float* partial;                 // [n_sites_total][P]
     int* err;                       // device flag: set when a wait gives up
 };
 cudaError_t bip_tc_gemm(const TcArgs& a, cudaStream_t s);

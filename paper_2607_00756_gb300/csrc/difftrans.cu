@@ -1,0 +1,159 @@
+// The scan contraction of the map as a trigonometric polynomial.
+//
+// With c_b(rho) = coef_b exp(-2 pi i h_b.rho/N) and the Gram matrix
+// Q = sum_n M^(n)H M^(n) (Hermitian), Eq. map-sum per site is
+//   I_tau(rho) = f_y f_x c^H Q c
+//              = f_y f_x Re sum_{b <= b'} w_bb' conj(coef_b) Q_bb' coef_b'
+//                         exp(2 pi i (h_b - h_b').rho/N),
+// w = 1 on the diagonal and 2 above it.  The aperture beams lie on the
+// lattice h = f k, so grouping the pairs by their difference
+// Delta = k_b - k_b' gives
+//   I_tau(rho) = f_y f_x Re sum_Delta G(Delta) exp(2 pi i f Delta.rho/N),
+//   G(Delta)   = sum_{b <= b', k_b - k_b' = Delta} w_bb' conj(coef_b) Q_bb' coef_b'.
+// Beams are sorted by (h_y, h_x), so b <= b' means Delta <= 0
+// lexicographically: Delta_y in [-2K_y, 0], Delta_x in [-2K_x, 2K_x].
+// This is an exact regrouping of the sums; it replaces the B x B x scans
+// product by a binning of Q (B^2 terms) and ~(2K_y+1)(4K_x+1) terms per scan.
+//
+//   diff_bin  : warp per (site, Delta), lanes over b, fixed reduction tree
+//   diff_eval : thread per scan of a (site, scan tile) work item; the
+//               phases exp(2 pi i f Delta.rho/N) advance by one rotation
+//               per step of Delta from an FP64-reduced start angle.
+#include "bip_device.cuh"
+#include "bip_internal.h"
+#include "fft_smem.cuh"
+
+namespace {
+
+// One warp per difference Delta; the lanes split the beams b and the
+// partial sums meet in a fixed shuffle tree, so the result is deterministic.
+constexpr int kBinWarps = 8;
+
+__global__ void __launch_bounds__(kBinWarps * 32) diff_bin_kernel(DiffArgs a) {
+    extern __shared__ unsigned char smb[];
+    int2* kb = reinterpret_cast<int2*>(smb);                         // [B]
+    float2* cf = reinterpret_cast<float2*>(kb + a.B);                // [B]
+    int* lat = reinterpret_cast<int*>(cf + a.B);                     // [(2Ky+1)(2Kx+1)]
+    const int lw = 2 * a.Kx + 1;
+    const int nlat = (2 * a.Ky + 1) * lw;
+    for (int i = threadIdx.x; i < a.B; i += blockDim.x) {
+        kb[i] = __ldg(&a.kb[i]);
+        const double2 c = __ldg(&a.coef[i]);
+        cf[i] = make_float2((float)c.x, (float)c.y);
+    }
+    for (int i = threadIdx.x; i < nlat; i += blockDim.x) lat[i] = __ldg(&a.lat[i]);
+    __syncthreads();
+
+    const int bs = blockIdx.y;
+    const int nd = (2 * a.Ky + 1) * (4 * a.Kx + 1);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int di = blockIdx.x * kBinWarps + warp;
+    if (di >= nd) return;
+    const int dy = di / (4 * a.Kx + 1) - 2 * a.Ky;       // in [-2Ky, 0]
+    const int dx = di % (4 * a.Kx + 1) - 2 * a.Kx;       // in [-2Kx, 2Kx]
+    const float2* Q = a.Q + (size_t)bs * a.q_site;
+    float gr = 0.f, gi = 0.f;
+    if (dy < 0 || dx <= 0) {
+        for (int b = lane; b < a.B; b += 32) {
+            const int2 k = kb[b];
+            const int ky = k.x - dy, kx = k.y - dx;          // partner k_b' = k_b - Delta
+            if (ky < -a.Ky || ky > a.Ky || kx < -a.Kx || kx > a.Kx) continue;
+            const int bp = lat[(ky + a.Ky) * lw + kx + a.Kx];
+            if (bp < 0) continue;
+            const float2 q = __ldg(&Q[(size_t)b * a.ldq + bp]);
+            const float2 cb = cf[b], cp = cf[bp];
+            // w conj(c_b) q c_b', w = 1 on the diagonal, 2 above it
+            const float w = (bp == b) ? 1.f : 2.f;
+            const float2 t = c_mul(make_float2(cb.x, -cb.y), c_mul(q, cp));
+            gr = fmaf(w, t.x, gr);
+            gi = fmaf(w, t.y, gi);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        gr += __shfl_xor_sync(0xffffffffu, gr, o);
+        gi += __shfl_xor_sync(0xffffffffu, gi, o);
+    }
+    if (lane == 0) a.G[(size_t)bs * nd + di] = make_float2(gr, gi);
+}
+
+// exp(2 pi i * turns) with the angle reduced to [0, 1) turns in FP64
+__device__ __forceinline__ float2 turn(double t) {
+    t -= floor(t);
+    double s, c;
+    sincospi(2.0 * t, &s, &c);
+    return make_float2((float)c, (float)s);
+}
+
+__global__ void __launch_bounds__(256) diff_eval_kernel(DiffArgs a) {
+    extern __shared__ float2 gs[];
+    const int w = blockIdx.x;
+    const int bs = a.work[2 * w], tile = a.work[2 * w + 1];
+    const int rows = 2 * a.Ky + 1, cols = 4 * a.Kx + 1;
+    const int nd = rows * cols;
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) gs[i] = a.G[(size_t)bs * nd + i];
+    __syncthreads();
+    const int site = a.site_ids[bs];
+    const SiteDev st = a.sites[site];
+    for (int n = tile * a.tile + threadIdx.x; n < min((tile + 1) * a.tile, a.P); n += blockDim.x) {
+        const double ry = a.scans[2 * n], rx = a.scans[2 * n + 1];
+        if (!in_crop(ry, rx, st.ty, st.tx, a.ny, a.nx, a.fy, a.fx)) {
+            a.partial[(size_t)site * a.P + n] = 0.f;
+            continue;
+        }
+        const double ty = (double)a.fy * ry / a.ny, tx = (double)a.fx * rx / a.nx;   // turns per lattice step
+        float2 ey = turn(-2.0 * a.Ky * ty);
+        const float2 ey_step = turn(ty);
+        const float2 ex0 = turn(-2.0 * a.Kx * tx);
+        const float2 ex_step = turn(tx);
+        float acc = 0.f;
+        for (int iy = 0; iy < rows; ++iy) {
+            const float2* g = gs + iy * cols;
+            float2 ex = ex0;
+            float sr = 0.f, si = 0.f;
+            const int last = iy == rows - 1 ? 2 * a.Kx + 1 : cols;   // Delta_y = 0: Delta_x <= 0 only
+            for (int ix = 0; ix < last; ++ix) {
+                const float2 gv = g[ix];
+                sr = fmaf(gv.x, ex.x, fmaf(-gv.y, ex.y, sr));
+                si = fmaf(gv.x, ex.y, fmaf(gv.y, ex.x, si));
+                ex = c_mul(ex, ex_step);
+            }
+            acc = fmaf(ey.x, sr, fmaf(-ey.y, si, acc));
+            ey = c_mul(ey, ey_step);
+        }
+        a.partial[(size_t)site * a.P + n] = a.scale * acc;
+    }
+}
+
+}  // namespace
+
+cudaError_t bip_diff_bin(const DiffArgs& a, cudaStream_t s) {
+    const int nd = (2 * a.Ky + 1) * (4 * a.Kx + 1);
+    const size_t sm = (size_t)a.B * (sizeof(int2) + sizeof(float2)) +
+                      (size_t)(2 * a.Ky + 1) * (2 * a.Kx + 1) * sizeof(int);
+    if (sm > 200 * 1024) return cudaErrorInvalidValue;
+    static size_t attr = 0;
+    if (sm > 48 * 1024 && sm > attr) {
+        cudaError_t e = cudaFuncSetAttribute(diff_bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = sm;
+    }
+    dim3 grid((nd + kBinWarps - 1) / kBinWarps, a.n_sites);
+    diff_bin_kernel<<<grid, kBinWarps * 32, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t bip_diff_eval(const DiffArgs& a, cudaStream_t s) {
+    if (a.n_work == 0) return cudaSuccess;
+    const size_t nd = (size_t)(2 * a.Ky + 1) * (4 * a.Kx + 1);
+    const size_t sm = nd * sizeof(float2);
+    if (sm > 200 * 1024) return cudaErrorInvalidValue;
+    static size_t attr = 0;
+    if (sm > 48 * 1024 && sm > attr) {
+        cudaError_t e = cudaFuncSetAttribute(diff_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = sm;
+    }
+    diff_eval_kernel<<<a.n_work, 256, sm, s>>>(a);
+    return cudaGetLastError();
+}

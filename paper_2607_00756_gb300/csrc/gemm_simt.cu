@@ -2,16 +2,15 @@
 //
 //   coupling   M^{(n)}_{d,b} = sum_r S2^d(r) [H_n S1^b](r)          (Eq. coupling)
 //   Gram       Q_{b,b'} = sum_{n,d} conj(M^{(n)}_{d,b}) M^{(n)}_{d,b'}
-//   quadratic  I_tau(rho) = f_y f_x Re( c(rho)^H Q c(rho) )
-// The last two are an exact regrouping of Eq. map-sum:
+// The Gram matrix is an exact regrouping of Eq. map-sum:
 //   sum_n sum_d |sum_b M^{(n)}_{d,b} c_b|^2 = c^H (sum_n M^{(n)H} M^{(n)}) c,
-// which contracts the detector index once per site instead of once per scan.
+// which contracts the detector index once per site instead of once per
+// scan; c^H Q c itself is evaluated in difftrans.cu.
 //
 // cgemm: C[m][n] = sum_k op(A[m][k]) B[n][k], complex64, both operands
 // K-contiguous; 64x64 complex tile, 256 threads with 4x4 complex register
 // blocks, K step 16, double-buffered shared memory.  4 FFMA per complex MAC.
 #include "bip_internal.h"
-#include "bip_device.cuh"
 #include "fft_smem.cuh"
 
 namespace {
@@ -110,66 +109,11 @@ __global__ void __launch_bounds__(256) cgemm_kernel(CGemmArgs p) {
     }
 }
 
-// one block per work item (site, tile of 64 scans): Y = Q C over all b,
-// folded into f_y f_x Re(sum_b conj(c_b) Y_b) per scan.
-__global__ void __launch_bounds__(256) quadform_kernel(QuadArgs q) {
-    __shared__ float2 As[2][BK][BM + 1];
-    __shared__ float2 Bs[2][BK][BN + 1];
-    __shared__ float red[16][BN];
-    const int w = blockIdx.x;
-    const int bs = q.work[2 * w], tile = q.work[2 * w + 1];
-    const int site = q.site_ids[bs];
-    const float2* Q = q.Q + (size_t)bs * q.strideQ;
-    const int n0 = tile * q.tile;
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    float part[TN] = {0.f, 0.f, 0.f, 0.f};
-    for (int m0 = 0; m0 < q.Bpad; m0 += BM) {
-        float2 acc[TM][TN];
-#pragma unroll
-        for (int i = 0; i < TM; ++i)
-#pragma unroll
-            for (int j = 0; j < TN; ++j) acc[i][j] = make_float2(0.f, 0.f);
-        tile_mainloop(acc, Q, q.Bpad, q.Ct, q.Bpad, q.Bpad, q.P, q.Bpad, m0, n0, false, As, Bs);
-#pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            const int n = n0 + tx + 16 * j;
-            if (n >= q.P) continue;
-#pragma unroll
-            for (int i = 0; i < TM; ++i) {
-                const int b = m0 + ty + 16 * i;
-                const float2 c = __ldg(&q.Ct[(size_t)n * q.Bpad + b]);
-                part[j] = fmaf(c.x, acc[i][j].x, part[j]);
-                part[j] = fmaf(c.y, acc[i][j].y, part[j]);
-            }
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < TN; ++j) red[ty][tx + 16 * j] = part[j];
-    __syncthreads();
-    if (threadIdx.x < BN) {
-        const int n = n0 + threadIdx.x;
-        if (n < q.P && threadIdx.x < q.tile) {
-            float s = 0.f;
-            for (int k = 0; k < 16; ++k) s += red[k][threadIdx.x];
-            const SiteDev st = q.sites[site];
-            const bool ok = in_crop(q.scans[2 * n], q.scans[2 * n + 1], st.ty, st.tx, q.ny, q.nx, q.fy, q.fx);
-            q.partial[(size_t)site * q.P + n] = ok ? q.scale * s : 0.f;
-        }
-    }
-}
-
 }  // namespace
 
 cudaError_t bip_cgemm_simt(const CGemmArgs& a, cudaStream_t s) {
     if (a.K % BK != 0 || (a.lda % 2) || (a.ldb % 2)) return cudaErrorInvalidValue;
     dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.batch);
     cgemm_kernel<<<grid, 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t bip_quadform_simt(const QuadArgs& q, cudaStream_t s) {
-    if (q.Bpad % BM != 0 || q.tile != BN) return cudaErrorInvalidValue;
-    if (q.n_work == 0) return cudaSuccess;
-    quadform_kernel<<<q.n_work, 256, 0, s>>>(q);
     return cudaGetLastError();
 }

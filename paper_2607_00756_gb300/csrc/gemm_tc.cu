@@ -17,16 +17,13 @@
 //   warp 1      TMEM allocator and MMA issuer (one elected thread);
 //   warps 2-5   epilogue: tcgen05.ld of the accumulators, then
 //     MT   : coupling M written transposed as bf16 planes for the Gram step
-//     Q    : Gram matrix written as bf16 planes for the quadratic form
-//     C32  : complex64 row-major copy (validation of the coupling)
-//     QUAD : f_y f_x Re(sum_b conj(c_b) Y_b) reduced over the 128 lanes
-//            of each M tile and over the M tiles of a site's scan tile.
+//     C32  : complex64 row-major copy (the Gram matrix for the scan
+//            contraction, or the coupling for validation).
 // Every wait is bounded (a few seconds of %globaltimer); on a timeout the
 // kernel sets *err, stops issuing work, drains what it issued and frees
 // TMEM before returning.
 #include <cuda.h>
 
-#include "bip_device.cuh"
 #include "bip_internal.h"
 
 namespace {
@@ -144,7 +141,7 @@ __device__ __forceinline__ void named_sync(int id, int n) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-// Work units: (site in batch, M tile, N tile); QUAD: (work item, M tile).
+// Work units: (site in batch, M tile, N tile).
 struct Unit {
     int bs, mt, nt, w;
     bool skip;    // tile below the diagonal of a Hermitian Gram matrix
@@ -156,22 +153,9 @@ struct UnitIter {
     const TcArgs& p;
     int total;
     __device__ int N_of() const { return p.N; }
-    __device__ UnitIter(const TcArgs& a) : p(a) {
-        total = EPI == TC_EPI_QUAD ? a.n_work * a.mt_per : a.n_sites * a.mt_per * a.nt_per;
-    }
+    __device__ UnitIter(const TcArgs& a) : p(a) { total = a.n_sites * a.mt_per * a.nt_per; }
     // the i-th unit of this CTA (i = 0, 1, ...), false past the end
     __device__ bool get(int i, Unit& u) const {
-        if (EPI == TC_EPI_QUAD) {
-            const int wi = blockIdx.x + (i / p.mt_per) * gridDim.x;
-            if (wi >= p.n_work) return false;
-            u.w = wi;
-            u.mt = i % p.mt_per;
-            u.bs = p.work[2 * wi];
-            u.nt = p.work[2 * wi + 1];
-            u.skip = false;
-            u.kb0 = p.tri ? u.mt * 4 : 0;      // 128 rows = 4 K blocks of 32
-            return true;
-        }
         const int idx = blockIdx.x + i * gridDim.x;
         if (idx >= total) return false;
         const int per = p.mt_per * p.nt_per;
@@ -192,7 +176,7 @@ struct TcShape {
     static constexpr int STAGE = NPL * kATile + NPL * B_TILE;
     static constexpr int STAGES = (196608 / STAGE) > 6 ? 6 : (196608 / STAGE);
     static constexpr int NACC = N == 256 ? 1 : 2;
-    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256 + 5 * N * sizeof(float);
+    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256;
 };
 
 template <int N, int EPI, int NPL>
@@ -213,8 +197,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t* tmem_slot = (uint32_t*)(drain + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     volatile int* ep_ok = abort_flag + 1;                    // epilogue's shared wait result
-    float* red = (float*)(smem + STAGES * STAGE + 256);     // [4][N]
-    float* qacc = red + 4 * N;                               // [N]
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) {
@@ -393,9 +375,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const int row = u.mt * 128 + q * 32 + lane;      // accumulator row of this thread
             const uint32_t tr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 2 * N);
-            if (EPI == TC_EPI_QUAD && u.mt == 0) {
-                for (int c = et; c < N; c += 128) qacc[c] = 0.f;
-            }
             for (int c0 = 0; c0 < N; c0 += 16) {
                 float vr[16], vi[16];
                 tmem_ld16(tr + c0, vr);
@@ -420,102 +399,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                             o[p.out_plane + at] = ih;
                         }
                     }
-                } else if (EPI == TC_EPI_Q) {
-                    uint16_t* o = p.out16 + (int64_t)u.bs * p.out_site + (int64_t)row * p.out_ld + u.nt * N + c0;
-                    if (p.tri) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int col = u.nt * N + c0 + j;
-                            const float f = col > row ? 2.f : (col == row ? 1.f : 0.f);
-                            vr[j] *= f;
-                            vi[j] *= f;
-                        }
-                    }
-                    uint32_t w[4][8];
-#pragma unroll
-                    for (int j = 0; j < 16; j += 2) {
-                        const uint16_t r0 = bf16_rn(vr[j]), r1 = bf16_rn(vr[j + 1]);
-                        const uint16_t i0 = bf16_rn(vi[j]), i1 = bf16_rn(vi[j + 1]);
-                        w[0][j / 2] = (uint32_t)r0 | ((uint32_t)r1 << 16);
-                        w[1][j / 2] = (uint32_t)bf16_rn(vr[j] - bf16_f(r0)) |
-                                      ((uint32_t)bf16_rn(vr[j + 1] - bf16_f(r1)) << 16);
-                        w[2][j / 2] = (uint32_t)i0 | ((uint32_t)i1 << 16);
-                        w[3][j / 2] = (uint32_t)bf16_rn(vi[j] - bf16_f(i0)) |
-                                      ((uint32_t)bf16_rn(vi[j + 1] - bf16_f(i1)) << 16);
-                    }
-#pragma unroll
-                    for (int pl = 0; pl < 4; ++pl) {
-                        uint4* dst = reinterpret_cast<uint4*>(o + pl * p.out_plane);
-                        dst[0] = make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
-                        dst[1] = make_uint4(w[pl][4], w[pl][5], w[pl][6], w[pl][7]);
-                    }
                 } else if (EPI == TC_EPI_C32) {
                     float2* o = p.out32 + (int64_t)u.bs * p.out32_site + (int64_t)row * p.out32_ld + u.nt * N + c0;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) o[j] = make_float2(vr[j], vi[j]);
-                } else {
-                    // QUAD: v_j = Re(conj(c_b(rho_j)) Y_{b, rho_j}), summed over b
-                    float v[16];
-                    const int scan0 = u.nt * N + c0;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float2 cb = __ldg(&p.ct32[(int64_t)(scan0 + j) * p.bpad + row]);
-                        v[j] = fmaf(cb.x, vr[j], cb.y * vi[j]);
-                    }
-                    // reduce 16 columns over the 32 lanes: halve the columns each step
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const bool up = lane & 16;
-                        const float send = up ? v[j] : v[j + 8];
-                        const float keep = up ? v[j + 8] : v[j];
-                        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const bool up = lane & 8;
-                        const float send = up ? v[j] : v[j + 4];
-                        const float keep = up ? v[j + 4] : v[j];
-                        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-                    }
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const bool up = lane & 4;
-                        const float send = up ? v[j] : v[j + 2];
-                        const float keep = up ? v[j + 2] : v[j];
-                        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-                    }
-                    {
-                        const bool up = lane & 2;
-                        const float send = up ? v[0] : v[1];
-                        const float keep = up ? v[1] : v[0];
-                        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-                    }
-                    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-                    const int col = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
-                                    ((lane >> 1) & 1);
-                    if ((lane & 1) == 0) red[q * N + c0 + col] = v[0];
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[a]);
-            if (EPI == TC_EPI_QUAD) {
-                named_sync(1, 128);
-                for (int c = et; c < N; c += 128) qacc[c] += red[c] + red[N + c] + red[2 * N + c] + red[3 * N + c];
-                named_sync(1, 128);
-                if (u.mt == p.mt_per - 1) {
-                    const int site = p.site_ids[u.bs];
-                    const SiteDev st = p.sites[site];
-                    for (int c = et; c < N; c += 128) {
-                        const int n = u.nt * N + c;
-                        if (n >= p.P) continue;
-                        const bool in = in_crop(p.scans[2 * n], p.scans[2 * n + 1], st.ty, st.tx, p.ny, p.nx, p.fy,
-                                                p.fx);
-                        p.partial[(int64_t)site * p.P + n] = in ? p.scale * qacc[c] : 0.f;
-                    }
-                    named_sync(1, 128);
-                }
-            }
             if (++a == NACC) {
                 a = 0;
                 aph ^= 1;
@@ -601,35 +493,28 @@ cudaError_t bip_tc_gemm(const TcArgs& a, cudaStream_t s) {
     if (a.N != 128 && a.N != 256) return cudaErrorInvalidValue;
     // every tile must lie inside its operand
     if (a.A.k != a.B.k || a.kb * 32 != a.A.k) return cudaErrorInvalidValue;
-    if (a.epi != TC_EPI_QUAD) {
+    {
         if (a.n_sites < 1 || a.mt_per < 1 || a.nt_per < 1) return cudaErrorInvalidValue;
         const int64_t pl = a.npl - 1;
         if ((int64_t)(a.n_sites - 1) * a.A.site_rows + pl * a.A.plane_rows + (int64_t)a.mt_per * 128 > a.A.rows)
             return cudaErrorInvalidValue;
         if ((int64_t)(a.n_sites - 1) * a.B.site_rows + pl * a.B.plane_rows + (int64_t)a.nt_per * a.N > a.B.rows)
             return cudaErrorInvalidValue;
-    } else {
-        if (a.n_work == 0) return cudaSuccess;
-        if ((int64_t)a.mt_per * 128 > a.A.plane_rows || a.bpad != a.mt_per * 128) return cudaErrorInvalidValue;
     }
     CUtensorMap ma, mb;
     cudaError_t e = make_map(&ma, a.A, 128);
     if (e != cudaSuccess) return e;
     e = make_map(&mb, a.B, a.N);
     if (e != cudaSuccess) return e;
-    const int units = a.epi == TC_EPI_QUAD ? a.n_work : a.n_sites * a.mt_per * a.nt_per;
+    const int units = a.n_sites * a.mt_per * a.nt_per;
     const int grid = units < num_sms() ? units : num_sms();
     if (a.npl != 4 && a.npl != 2) return cudaErrorInvalidValue;
     const bool split = a.npl == 4;
     switch (a.epi) {
         case TC_EPI_MT: return split ? launch_n<TC_EPI_MT, 4>(a, ma, mb, grid, s)
                                      : launch_n<TC_EPI_MT, 2>(a, ma, mb, grid, s);
-        case TC_EPI_Q: return split ? launch_n<TC_EPI_Q, 4>(a, ma, mb, grid, s)
-                                    : launch_n<TC_EPI_Q, 2>(a, ma, mb, grid, s);
         case TC_EPI_C32: return split ? launch_n<TC_EPI_C32, 4>(a, ma, mb, grid, s)
                                       : launch_n<TC_EPI_C32, 2>(a, ma, mb, grid, s);
-        case TC_EPI_QUAD: return split ? launch_n<TC_EPI_QUAD, 4>(a, ma, mb, grid, s)
-                                       : cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
 }
