@@ -69,7 +69,8 @@ struct MsPlan {
 struct MsRowArgs {
     float2* cols;                   // [ncol, ny, nx]
     const float* v_pre;             // V slice applied before the stash (or null)
-    const float* v_post;            // V slice applied after the stash (or null)
+    const float* v_post;            // V slice applied after the stash (or null);
+                                    // at most one of the two is set
     int init;                       // 1: start from a constant field `init_val`
     float init_val;
     int do_ifft, do_fft;

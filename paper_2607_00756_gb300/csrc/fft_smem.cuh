@@ -122,3 +122,94 @@ __device__ __forceinline__ void fft_smem(float2* buf, int t, const float2* tw) {
     if (LOG % 3 == 2) stockham_pass<N, 4, INV>(buf, Ns, t, tw);
     if (LOG % 3 == 1) stockham_pass<N, 2, INV>(buf, Ns, t, tw);
 }
+
+// Register-resident transform of length N by NT = N/8 threads.  Thread t
+// holds x[t + m NT] in v[m] (m = 0..7) on entry and X[t + m NT] on exit:
+// the first radix-8 pass reads exactly that distribution and the last pass
+// writes it, so only the data between passes go through shared memory.
+// Pass p works on sub-transforms of length Ns = 8^p; for p = 1..NPASS-1 a
+// caller stores v at out_pos(p, r, t) (r = 0..7), synchronises, loads
+// u[e] from in_pos<p>(e, t) (e = 0..7) and calls pass<p>(u, v, t, tw).
+template <int N, bool INV>
+struct FftReg {
+    static constexpr int NT = N / 8;
+    static constexpr int LOG = (N == 64) ? 6 : (N == 128) ? 7 : (N == 256) ? 8 : (N == 512) ? 9 : 10;
+    static constexpr int RL = (LOG % 3 == 2) ? 4 : (LOG % 3 == 1) ? 2 : 8;   // radix of the last pass
+    static constexpr int NPASS = LOG / 3 + (RL == 8 ? 0 : 1);
+    template <int P>
+    __host__ __device__ static constexpr int radix() { return P == NPASS - 1 ? RL : 8; }
+
+    __device__ __forceinline__ static void first(float2 (&v)[8]) { dft8<INV>(v); }
+
+    // where output r of pass p-1 goes (that pass has radix 8, butterfly j = t)
+    __device__ __forceinline__ static int out_pos(int p, int r, int t) {
+        const int Ns = 1 << (3 * (p - 1));
+        return (t / Ns) * Ns * 8 + t % Ns + r * Ns;
+    }
+    // where input e = b R + r of pass P comes from (butterfly j = t + b NT)
+    template <int P>
+    __device__ __forceinline__ static int in_pos(int e, int t) {
+        constexpr int R = radix<P>();
+        return t + (e / R) * NT + (e % R) * (N / R);
+    }
+    // twiddles and butterflies of pass P; the outputs go to v in the
+    // order the next pass's put expects, and for the last pass in the
+    // cyclic layout: output r of butterfly b is X[t + (b + r NB) NT]
+    template <int P>
+    __device__ __forceinline__ static void pass(float2 (&u)[8], float2 (&v)[8], int t, const float2* tw) {
+        constexpr int R = radix<P>();
+        constexpr int NB = 8 / R;
+        constexpr int Ns = 1 << (3 * P);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int j = t + b * NT;
+            const int step = (j % Ns) * (N / (Ns * R));
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = tw[r * step];
+                if (INV) w.y = -w.y;
+                u[b * R + r] = c_mul(u[b * R + r], w);
+            }
+            if (R == 8) dft8<INV>(&u[b * R]);
+            if (R == 4) dft4<INV>(u[b * R], u[b * R + 1], u[b * R + 2], u[b * R + 3]);
+            if (R == 2) dft2<INV>(u[b * R], u[b * R + 1]);
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b + r * NB] = u[b * R + r];
+    }
+};
+
+// One exchange of fft_reg: pass P through buffer `buf` (padded).
+template <int N, bool INV, int P>
+__device__ __forceinline__ void fft_reg_step(float2 (&v)[8], float2* buf, int t, const float2* tw) {
+    using F = FftReg<N, INV>;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) buf[FFT_PAD(F::out_pos(P, r, t))] = v[r];
+    __syncthreads();
+    float2 u[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) u[e] = buf[FFT_PAD(F::template in_pos<P>(e, t))];
+    F::template pass<P>(u, v, t, tw);
+}
+
+// One transform with two alternating exchange buffers (one barrier per
+// exchange).  `ph` selects the buffer of the next exchange and is carried
+// across calls, so a buffer is rewritten only after a barrier that follows
+// every thread's last read of it.  Every thread of the block calls this.
+template <int N, bool INV>
+__device__ __forceinline__ void fft_reg(float2 (&v)[8], float2* b0, float2* b1, int& ph, int t, const float2* tw) {
+    using F = FftReg<N, INV>;
+    F::first(v);
+    fft_reg_step<N, INV, 1>(v, ph ? b1 : b0, t, tw);
+    ph ^= 1;
+    if constexpr (F::NPASS > 2) {
+        fft_reg_step<N, INV, 2>(v, ph ? b1 : b0, t, tw);
+        ph ^= 1;
+    }
+    if constexpr (F::NPASS > 3) {
+        fft_reg_step<N, INV, 3>(v, ph ? b1 : b0, t, tw);
+        ph ^= 1;
+    }
+}

@@ -24,132 +24,191 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Row pass: a block takes one y and up to RPB consecutive columns, so its
+// rows share the transmission exp(i sigma V(y, .)), computed once into
+// shared memory.  Each row is held in registers by NT = NX/8 threads in the
+// cyclic layout x = t + m NT (the layout the register FFT keeps), so the
+// transmission multiply and the stash act on registers and the row crosses
+// shared memory only between FFT passes.
 template <int NX>
 __global__ void __launch_bounds__(kThreads) row_pass_kernel(MsPlan plan, MsRowArgs a) {
     constexpr int NT = NX / 8;                 // threads per row
     constexpr int RPB = kThreads / NT;         // rows per block
     constexpr int ROWLEN = NX + NX / 16;       // padded
     extern __shared__ float2 smem[];
-    float2* tw = smem + RPB * ROWLEN;          // [NX] twiddles
-    for (int i = threadIdx.x; i < NX; i += kThreads) tw[i] = __ldg(&plan.twx[i]);
     const int sub = threadIdx.x / NT;
     const int t = threadIdx.x % NT;
-    float2* row = smem + sub * ROWLEN;
-    const long long pair = (long long)blockIdx.x * RPB + sub;
-    const long long npairs = (long long)plan.ncol * plan.ny;
-    const bool active = pair < npairs;
-    // rows are ordered (y, column) so the rows of a block share V's row
-    const int y = active ? (int)(pair / plan.ncol) : 0;
-    const int c = active ? (int)(pair % plan.ncol) : 0;
-    float2* g = a.cols + ((size_t)c * plan.ny + y) * NX;
+    float2* b0 = smem + 2 * sub * ROWLEN;      // exchange buffers of this row
+    float2* b1 = b0 + ROWLEN;
+    float2* tw = smem + 2 * RPB * ROWLEN;      // [NX] twiddles
+    float2* tt = tw + NX;                      // [NX] transmission of this y
+    const int gpy = (plan.ncol + RPB - 1) / RPB;
+    const int y = blockIdx.x / gpy;
+    const int c = (blockIdx.x % gpy) * RPB + sub;
+    const bool active = c < plan.ncol;
+    float2* g = a.cols + ((size_t)(active ? c : 0) * plan.ny + y) * NX;
+    const float* vsl = a.v_pre ? a.v_pre : a.v_post;
 
-    if (active) {
-        for (int x = t; x < NX; x += NT)
-            row[FFT_PAD(x)] = a.init ? make_float2(a.init_val, 0.f) : g[x];
-    }
-    __syncthreads();
-    if (a.do_ifft) fft_smem<NX, true>(row, t, tw);
-
-    if (active && a.v_pre) {
-        const float* v = a.v_pre + (size_t)y * NX;
-        for (int x = t; x < NX; x += NT) {
+    float2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+        v[m] = !active ? make_float2(0.f, 0.f) : a.init ? make_float2(a.init_val, 0.f) : g[t + m * NT];
+    for (int i = threadIdx.x; i < NX; i += kThreads) {
+        tw[i] = __ldg(&plan.twx[i]);
+        if (vsl) {
             float s, co;
-            sincosf(plan.sigma * __ldg(&v[x]), &s, &co);
-            row[FFT_PAD(x)] = c_mul(row[FFT_PAD(x)], make_float2(co, s));
+            sincosf(plan.sigma * __ldg(&vsl[(size_t)y * NX + i]), &s, &co);
+            tt[i] = make_float2(co, s);
         }
     }
     __syncthreads();
+    int ph = 0;
+    if (a.do_ifft) fft_reg<NX, true>(v, b0, b1, ph, t, tw);
+    if (a.v_pre) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = c_mul(v[m], tt[t + m * NT]);
+    }
     if (active && a.row_off) {
         const int e1 = __ldg(&a.row_off[y + 1]);
         for (int e = __ldg(&a.row_off[y]); e < e1; ++e) {
             const int4 en = __ldg(&a.row_ent[e]);      // (site, u, ox, -)
             float2* dst = a.stash + (((size_t)en.x * plan.ncol + c) * a.win + en.y) * a.win;
-            for (int v = t; v < a.win; v += NT) {
-                int x = (en.z + v) % NX;
-                if (x < 0) x += NX;
-                dst[v] = row[FFT_PAD(x)];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                int u = (t + m * NT - en.z) % NX;      // column of x = t + m NT in the window
+                if (u < 0) u += NX;
+                if (u < a.win) dst[u] = v[m];
             }
         }
     }
-    __syncthreads();
-    if (active && a.v_post) {
-        const float* v = a.v_post + (size_t)y * NX;
-        for (int x = t; x < NX; x += NT) {
-            float s, co;
-            sincosf(plan.sigma * __ldg(&v[x]), &s, &co);
-            row[FFT_PAD(x)] = c_mul(row[FFT_PAD(x)], make_float2(co, s));
-        }
+    if (a.v_post) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[m] = c_mul(v[m], tt[t + m * NT]);
     }
-    if (a.do_fft) fft_smem<NX, false>(row, t, tw);
-    else __syncthreads();
+    if (a.do_fft) fft_reg<NX, false>(v, b0, b1, ph, t, tw);
     if (active) {
-        for (int x = t; x < NX; x += NT) g[x] = row[FFT_PAD(x)];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) g[t + m * NT] = v[m];
     }
 }
 
+// Column pass geometry: XB columns per block, two adjacent columns per
+// thread (16-byte loads), NT = NY/8 threads per column pair.
 template <int NY>
-__global__ void __launch_bounds__(kThreads) col_pass_kernel(MsPlan plan, float2* cols) {
-    constexpr int NT = NY / 8;                  // threads per column FFT
-    constexpr int NPAR = kThreads / NT;         // column FFTs in parallel
-    constexpr int XB = NPAR > 16 ? NPAR : 16;   // x columns per block
-    constexpr int COLLEN = NY + NY / 16 + 1;    // padded, odd stride
-    extern __shared__ float2 smem[];
-    float2* tw = smem + XB * COLLEN;            // [NY] twiddles
-    for (int i = threadIdx.x; i < NY; i += kThreads) tw[i] = __ldg(&plan.twy[i]);
+struct ColShape {
+    static constexpr int NT = NY / 8;
+    static constexpr int XB = NY <= 256 ? 512 / NT : (NY == 512 ? 16 : 8);
+    static constexpr int THREADS = NT * XB / 2;
+};
+
+// One exchange of col_fft: pass P of the two columns a, b of every thread
+// through the shared [NY][XB] tile; column pair cp sits at 2 cp, 2 cp + 1,
+// so a warp's accesses are runs of 16-byte words.
+template <int NY, int XB, bool INV, int P>
+__device__ __forceinline__ void col_fft_step(float2 (&va)[8], float2 (&vb)[8], float4* tile, int cp, int t,
+                                             const float2* tw) {
+    using F = FftReg<NY, INV>;
+    constexpr int CP = XB / 2;
+    __syncthreads();                           // earlier reads of the tile are done
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+        tile[F::out_pos(P, r, t) * CP + cp] = make_float4(va[r].x, va[r].y, vb[r].x, vb[r].y);
+    __syncthreads();
+    // one column at a time, to keep fewer values live
+    const float2* t2 = reinterpret_cast<const float2*>(tile);
+    float2 u[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) u[e] = t2[2 * (F::template in_pos<P>(e, t) * CP + cp)];
+    F::template pass<P>(u, va, t, tw);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) u[e] = t2[2 * (F::template in_pos<P>(e, t) * CP + cp) + 1];
+    F::template pass<P>(u, vb, t, tw);
+}
+
+template <int NY, int XB, bool INV>
+__device__ __forceinline__ void col_fft(float2 (&va)[8], float2 (&vb)[8], float4* tile, int cp, int t,
+                                        const float2* tw) {
+    using F = FftReg<NY, INV>;
+    F::first(va);
+    F::first(vb);
+    col_fft_step<NY, XB, INV, 1>(va, vb, tile, cp, t, tw);
+    if constexpr (F::NPASS > 2) col_fft_step<NY, XB, INV, 2>(va, vb, tile, cp, t, tw);
+    if constexpr (F::NPASS > 3) col_fft_step<NY, XB, INV, 3>(va, vb, tile, cp, t, tw);
+}
+
+// Column pass: FFT along y, times the shifted propagator, inverse FFT along
+// y, for XB adjacent columns x of one parent field; every thread holds two
+// adjacent columns at y = t + m NT in registers.
+template <int NY>
+__global__ void __launch_bounds__(ColShape<NY>::THREADS, 2048 / ColShape<NY>::THREADS / 2) col_pass_kernel(MsPlan plan, float2* cols) {
+    constexpr int NT = ColShape<NY>::NT;
+    constexpr int XB = ColShape<NY>::XB;
+    constexpr int CP = XB / 2;
+    extern __shared__ float4 tile[];                                 // [NY][CP]
+    float2* tw = reinterpret_cast<float2*>(tile + NY * CP);          // [NY] twiddles
+    const int cp = threadIdx.x % CP, t = threadIdx.x / CP;
     const int c = blockIdx.y;
-    const int x0 = blockIdx.x * XB;
-    float2* g = cols + (size_t)c * NY * plan.nx;
-    for (int i = threadIdx.x; i < NY * XB; i += kThreads) {
-        const int y = i / XB, xx = i % XB;
-        smem[xx * COLLEN + FFT_PAD(y)] = g[(size_t)y * plan.nx + x0 + xx];
+    const int x = blockIdx.x * XB + 2 * cp;                          // columns x, x + 1
+    float2* g = cols + (size_t)c * NY * plan.nx + x;
+    float2 va[8], vb[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const float4 q = *reinterpret_cast<const float4*>(g + (size_t)(t + m * NT) * plan.nx);
+        va[m] = make_float2(q.x, q.y);
+        vb[m] = make_float2(q.z, q.w);
     }
+    for (int i = threadIdx.x; i < NY; i += ColShape<NY>::THREADS) tw[i] = __ldg(&plan.twy[i]);
+    __syncthreads();
+    col_fft<NY, XB, false>(va, vb, tile, cp, t, tw);
+    // shifted propagator at (k_y, k_x) = (t + m NT, x) and (., x + 1)
     const int2 sh = plan.shift[c];
-    const int sub = threadIdx.x / NT;
-    const int t = threadIdx.x % NT;
-    for (int grp = 0; grp < XB; grp += NPAR) {
-        const int xx = grp + sub;
-        float2* col = smem + xx * COLLEN;
-        fft_smem<NY, false>(col, t, tw);
-        // shifted propagator at (k_y, k_x = x0 + xx)
-        int kx = (x0 + xx + sh.y) % plan.nx;
-        if (kx < 0) kx += plan.nx;
-        const float2 px = __ldg(&plan.px[kx]);
-        for (int ky = t; ky < NY; ky += NT) {
-            int iy = (ky + sh.x) % NY;
-            if (iy < 0) iy += NY;
-            const float2 p = c_mul(__ldg(&plan.py[iy]), px);
-            col[FFT_PAD(ky)] = c_mul(col[FFT_PAD(ky)], p);
-        }
-        fft_smem<NY, true>(col, t, tw);
+    int kx = (x + sh.y) % plan.nx;
+    if (kx < 0) kx += plan.nx;
+    const float2 pxa = __ldg(&plan.px[kx]);
+    const float2 pxb = __ldg(&plan.px[kx + 1 == plan.nx ? 0 : kx + 1]);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        int iy = (t + m * NT + sh.x) % NY;
+        if (iy < 0) iy += NY;
+        const float2 py = __ldg(&plan.py[iy]);
+        va[m] = c_mul(va[m], c_mul(py, pxa));
+        vb[m] = c_mul(vb[m], c_mul(py, pxb));
     }
-    for (int i = threadIdx.x; i < NY * XB; i += kThreads) {
-        const int y = i / XB, xx = i % XB;
-        g[(size_t)y * plan.nx + x0 + xx] = smem[xx * COLLEN + FFT_PAD(y)];
-    }
+    col_fft<NY, XB, true>(va, vb, tile, cp, t, tw);
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+        *reinterpret_cast<float4*>(g + (size_t)(t + m * NT) * plan.nx) =
+            make_float4(va[m].x, va[m].y, vb[m].x, vb[m].y);
 }
 
 template <int NX>
 cudaError_t launch_row(const MsPlan& p, const MsRowArgs& a, cudaStream_t s) {
     constexpr int NT = NX / 8, RPB = kThreads / NT, ROWLEN = NX + NX / 16;
-    const long long npairs = (long long)p.ncol * p.ny;
-    const int blocks = (int)((npairs + RPB - 1) / RPB);
-    const size_t sm = ((size_t)RPB * ROWLEN + NX) * sizeof(float2);
-    row_pass_kernel<NX><<<blocks, kThreads, sm, s>>>(p, a);
+    const long long blocks = (long long)p.ny * ((p.ncol + RPB - 1) / RPB);
+    const size_t sm = ((size_t)2 * RPB * ROWLEN + 2 * NX) * sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(row_pass_kernel<NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    row_pass_kernel<NX><<<(unsigned)blocks, kThreads, sm, s>>>(p, a);
     return cudaGetLastError();
 }
 
 template <int NY>
 cudaError_t launch_col(const MsPlan& p, float2* cols, cudaStream_t s) {
-    constexpr int NT = NY / 8, NPAR = kThreads / NT, XB = NPAR > 16 ? NPAR : 16;
-    constexpr int COLLEN = NY + NY / 16 + 1;
-    const size_t sm = ((size_t)XB * COLLEN + NY) * sizeof(float2);
+    using C = ColShape<NY>;
+    if (p.nx % C::XB != 0) return cudaErrorInvalidValue;
+    const size_t sm = (size_t)NY * C::XB * sizeof(float2) + NY * sizeof(float2);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(col_pass_kernel<NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = cudaFuncSetAttribute(col_pass_kernel<NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid(p.nx / XB, p.ncol);
-    col_pass_kernel<NY><<<grid, kThreads, sm, s>>>(p, cols);
+    dim3 grid(p.nx / C::XB, p.ncol);
+    col_pass_kernel<NY><<<grid, C::THREADS, sm, s>>>(p, cols);
     return cudaGetLastError();
 }
 
