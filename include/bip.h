@@ -157,7 +157,8 @@ bip_status bip_build_s2(bip_ctx* ctx, const float* V, const bip_atom* atoms,
  * lies in [-N/(2f), N/(2f)) on both axes (crop mask).  Sites are summed in
  * a fixed order in FP64 with Neumaier compensation.
  *   H        [sum nch, win, win] complex64 device: transition potentials of
- *            each site's channels sampled on its window, sites in order.
+ *            each site's channels sampled on its window, sites in order;
+ *            16-byte aligned (else BIP_ERR_INVALID_ARG).
  *   scan_px  [P, 2] float64 host: scan positions in pixels (y, x).
  *   map_out  [P] float64 device.
  * Requires both builds on this context (else BIP_ERR_INVALID_ARG). */
@@ -183,7 +184,8 @@ bip_status bip_coreloss_cube(bip_ctx* ctx, const void* H, const double* scan_px,
  * bip_site_coupling: the coupling matrices of one site, [nch_max, n_det, B]
  *   complex64 device (Eq. coupling), nch_max the largest channel count of
  *   the built sites (missing channels of a site come out zero), computed in
- *   the context's precision. */
+ *   the context's precision.
+ * H, s1_out and s2_out must be 16-byte aligned (else BIP_ERR_INVALID_ARG). */
 bip_status bip_copy_stash(bip_ctx* ctx, int32_t which, int32_t site, void* out,
                           void* stream);
 bip_status bip_site_windows(bip_ctx* ctx, int32_t site, void* s1_out, void* s2_out,

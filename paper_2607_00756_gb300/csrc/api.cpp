@@ -33,10 +33,10 @@ struct bip_ctx {
     // device geometry tables
     bool tables = false;
     DevBuf twy, twx, py, px, ey, ex, shift1, shift2, hbeam, hdet, coef;
-    DevBuf ell1_idx, ell1_w, ell2_idx, ell2_w, ell1_n, ell2_n;
+    DevBuf grp1_off, grp1_par, grp1_w, grp2_off, grp2_par, grp2_w, ytab, xtab;
     DevBuf kb_d, lat_d;                 // beam lattice of the difference transform
     int Ky = 0, Kx = 0;
-    int ell1_k = 0, ell2_k = 0;
+    int grp1_n = 0, grp2_n = 0;
 
     // sites of the current builds
     std::vector<SiteDev> sites;
@@ -160,30 +160,34 @@ int signed_bin(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// sparse (ELL) copy of a dense weight matrix
-void to_ell(const std::vector<double>& w, int rows, int cols, int& k, std::vector<uint16_t>& idx,
-            std::vector<float>& val, std::vector<int32_t>& nnz) {
-    k = 1;
-    for (int r = 0; r < rows; ++r) {
-        int n = 0;
-        for (int c = 0; c < cols; ++c) n += w[(size_t)r * cols + c] != 0.0;
-        k = std::max(k, n);
-    }
-    k = (k + 7) / 8 * 8;     // rows padded to whole 16-byte index vectors
-    idx.assign((size_t)rows * k, 0);
-    val.assign((size_t)rows * k, 0.f);
-    nnz.assign(rows, 0);
-    for (int r = 0; r < rows; ++r) {
-        int& n = nnz[r];
+// Grouped sparse copy of a dense weight matrix [rows][cols]: rows
+// kGatherGroup g .. + kGatherGroup - 1 form group g, whose entries are the
+// columns (parents) any of its rows uses, with the rows' weights side by side.
+int to_groups(const std::vector<double>& w, int rows, int cols, std::vector<int32_t>& off,
+              std::vector<uint16_t>& par, std::vector<float4>& wt) {
+    const int ng = (rows + kGatherGroup - 1) / kGatherGroup;
+    off.assign(1, 0);
+    par.clear();
+    wt.clear();
+    for (int g = 0; g < ng; ++g) {
         for (int c = 0; c < cols; ++c) {
-            const double x = w[(size_t)r * cols + c];
-            if (x != 0.0) {
-                idx[(size_t)r * k + n] = (uint16_t)c;
-                val[(size_t)r * k + n] = (float)x;
-                ++n;
+            float v[kGatherGroup] = {0.f, 0.f, 0.f, 0.f};
+            bool any = false;
+            for (int i = 0; i < kGatherGroup; ++i) {
+                const int r = g * kGatherGroup + i;
+                if (r < rows && w[(size_t)r * cols + c] != 0.0) {
+                    v[i] = (float)w[(size_t)r * cols + c];
+                    any = true;
+                }
+            }
+            if (any) {
+                par.push_back((uint16_t)c);
+                wt.push_back(float4{v[0], v[1], v[2], v[3]});
             }
         }
+        off.push_back((int32_t)par.size());
     }
+    return ng;
 }
 
 bip_status make_tables(bip_ctx* c, cudaStream_t s) {
@@ -234,11 +238,17 @@ bip_status make_tables(bip_ctx* c, cudaStream_t s) {
     c->Kx = Kx;
     CUDA_TRY(c, upload(c->kb_d, kb, s));
     CUDA_TRY(c, upload(c->lat_d, lat, s));
-    std::vector<uint16_t> i1, i2;
-    std::vector<int32_t> n1, n2;
-    std::vector<float> w1, w2;
-    to_ell(geo.w1, geo.B, geo.Bp1, c->ell1_k, i1, w1, n1);
-    to_ell(geo.w2, geo.n_det, geo.Bp2, c->ell2_k, i2, w2, n2);
+    std::vector<int32_t> o1, o2;
+    std::vector<uint16_t> p1, p2;
+    std::vector<float4> w1, w2;
+    c->grp1_n = to_groups(geo.w1, geo.B, geo.Bp1, o1, p1, w1);
+    c->grp2_n = to_groups(geo.w2, geo.n_det, geo.Bp2, o2, p2, w2);
+    // separable re-tilt factors exp(+2 pi i h u / n) for window offsets u
+    std::vector<float2> yt((size_t)g.ny * g.win), xt((size_t)g.nx * g.win);
+    for (int h = 0; h < g.ny; ++h)
+        for (int u = 0; u < g.win; ++u) yt[(size_t)h * g.win + u] = turn((int)((int64_t)h * u % g.ny), g.ny, +1.0);
+    for (int h = 0; h < g.nx; ++h)
+        for (int v = 0; v < g.win; ++v) xt[(size_t)h * g.win + v] = turn((int)((int64_t)h * v % g.nx), g.nx, +1.0);
     CUDA_TRY(c, upload(c->twy, twy, s));
     CUDA_TRY(c, upload(c->twx, twx, s));
     CUDA_TRY(c, upload(c->ey, ey, s));
@@ -250,12 +260,14 @@ bip_status make_tables(bip_ctx* c, cudaStream_t s) {
     CUDA_TRY(c, upload(c->hbeam, hb, s));
     CUDA_TRY(c, upload(c->hdet, hd, s));
     CUDA_TRY(c, upload(c->coef, coef, s));
-    CUDA_TRY(c, upload(c->ell1_idx, i1, s));
-    CUDA_TRY(c, upload(c->ell1_w, w1, s));
-    CUDA_TRY(c, upload(c->ell2_idx, i2, s));
-    CUDA_TRY(c, upload(c->ell2_w, w2, s));
-    CUDA_TRY(c, upload(c->ell1_n, n1, s));
-    CUDA_TRY(c, upload(c->ell2_n, n2, s));
+    CUDA_TRY(c, upload(c->grp1_off, o1, s));
+    CUDA_TRY(c, upload(c->grp1_par, p1, s));
+    CUDA_TRY(c, upload(c->grp1_w, w1, s));
+    CUDA_TRY(c, upload(c->grp2_off, o2, s));
+    CUDA_TRY(c, upload(c->grp2_par, p2, s));
+    CUDA_TRY(c, upload(c->grp2_w, w2, s));
+    CUDA_TRY(c, upload(c->ytab, yt, s));
+    CUDA_TRY(c, upload(c->xtab, xt, s));
     CUDA_TRY(c, ensure(c->errflag, 64, true, s));
     c->tables = true;
     return BIP_OK;
@@ -442,7 +454,8 @@ bip_status bip_create(const bip_config* cfg, bip_ctx** out) {
 bip_status bip_destroy(bip_ctx* c) {
     if (!c) return BIP_ERR_INVALID_ARG;
     DevBuf* all[] = {&c->twy, &c->twx, &c->py, &c->px, &c->ey, &c->ex, &c->shift1, &c->shift2, &c->hbeam,
-                     &c->hdet, &c->coef, &c->ell1_idx, &c->ell1_w, &c->ell2_idx, &c->ell2_w, &c->ell1_n, &c->ell2_n, &c->sites_d,
+                     &c->hdet, &c->coef, &c->grp1_off, &c->grp1_par, &c->grp1_w, &c->grp2_off, &c->grp2_par, &c->grp2_w, &c->ytab,
+                     &c->xtab, &c->sites_d,
                      &c->plane_ids_d, &c->seq_ids_d, &c->row_off_d, &c->row_ent_d, &c->stash1, &c->stash2, &c->cols, &c->scans_d,
                      &c->gdiff, &c->kb_d, &c->lat_d, &c->work_d, &c->partial, &c->opA32, &c->opB32, &c->mt32, &c->q32, &c->opA16,
                      &c->opB16, &c->mt16, &c->q16, &c->errflag};
@@ -576,11 +589,42 @@ bip_status bip_build_s2(bip_ctx* c, const float* V, const bip_atom* atoms, int32
 
 namespace {
 
+// Gather arguments of one side (1: S1 windows of the aperture beams,
+// 2: S2 windows of the detector beams) for sites ids[0 .. n).
+GatherArgs gather_args(const bip_ctx* c, int side, const int32_t* ids, int n) {
+    const bip_config& g = c->cfg;
+    GatherArgs a{};
+    a.n_sites = n;
+    a.site_ids = ids;
+    a.sites = (const SiteDev*)c->sites_d.p;
+    a.win = g.win; a.ny = g.ny; a.nx = g.nx; a.K = g.win * g.win;
+    a.magnitude = g.recon == BIP_RECON_MAGNITUDE;
+    a.ey = (const float2*)c->ey.p;
+    a.ex = (const float2*)c->ex.p;
+    a.ytab = (const float2*)c->ytab.p;
+    a.xtab = (const float2*)c->xtab.p;
+    if (side == 1) {
+        a.Bp = c->geo.Bp1; a.n_targets = c->geo.B; a.rows_pad = c->geo.B;
+        a.stash = (const float2*)c->stash1.p;
+        a.grp = GroupDev{c->grp1_n, (const int32_t*)c->grp1_off.p, (const uint16_t*)c->grp1_par.p, (const float4*)c->grp1_w.p};
+        a.h_t = (const int2*)c->hbeam.p;
+        a.tilt_sign = +1;
+    } else {
+        a.Bp = c->geo.Bp2; a.n_targets = c->geo.n_det; a.rows_pad = c->geo.n_det;
+        a.stash = (const float2*)c->stash2.p;
+        a.grp = GroupDev{c->grp2_n, (const int32_t*)c->grp2_off.p, (const uint16_t*)c->grp2_par.p, (const float4*)c->grp2_w.p};
+        a.h_t = (const int2*)c->hdet.p;
+        a.tilt_sign = -1;
+    }
+    return a;
+}
+
 bip_status check_map_args(bip_ctx* c, const void* H, const double* scans, int32_t P, const void* out) {
     if (!c) return BIP_ERR_INVALID_ARG;
     if (!c->s1 || !c->s2 || c->sig1 != c->sig2)
         return fail(c, BIP_ERR_INVALID_ARG, "bip_build_s1 and bip_build_s2 must run first on the same sites");
     if (!H || !scans || !out) return fail(c, BIP_ERR_INVALID_ARG, "null pointer argument");
+    if ((reinterpret_cast<uintptr_t>(H) & 15) != 0) return fail(c, BIP_ERR_INVALID_ARG, "H must be 16-byte aligned");
     if (P < 1) return fail(c, BIP_ERR_INVALID_ARG, "P must be >= 1");
     for (int i = 0; i < 2 * P; ++i)
         if (!std::isfinite(scans[i])) return fail(c, BIP_ERR_INVALID_ARG, "scan position is not finite");
@@ -677,27 +721,10 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         const int nb = std::min(SB, c->n_sites - b0);
         const int32_t* ids = (const int32_t*)c->seq_ids_d.p + b0;
         // S2 windows -> coupling A operand, S1 windows x H_n -> B operand
-        GatherArgs ga{};
-        ga.n_sites = nb;
-        ga.site_ids = ids;
-        ga.sites = (const SiteDev*)c->sites_d.p;
-        ga.win = g.win; ga.ny = g.ny; ga.nx = g.nx; ga.K = K;
-        ga.magnitude = g.recon == BIP_RECON_MAGNITUDE;
-        ga.ey = (const float2*)c->ey.p;
-        ga.ex = (const float2*)c->ex.p;
-        GatherArgs g2 = ga;
-        g2.Bp = geo.Bp2; g2.n_targets = geo.n_det; g2.rows_pad = Dpad;
-        g2.stash = (const float2*)c->stash2.p;
-        g2.ell = EllDev{c->ell2_k, (const uint16_t*)c->ell2_idx.p, (const float*)c->ell2_w.p, (const int32_t*)c->ell2_n.p};
-        g2.h_t = (const int2*)c->hdet.p;
-        g2.tilt_sign = -1;
-        g2.nch = 0;
-        GatherArgs g1 = ga;
-        g1.Bp = geo.Bp1; g1.n_targets = geo.B; g1.rows_pad = Bpad;
-        g1.stash = (const float2*)c->stash1.p;
-        g1.ell = EllDev{c->ell1_k, (const uint16_t*)c->ell1_idx.p, (const float*)c->ell1_w.p, (const int32_t*)c->ell1_n.p};
-        g1.h_t = (const int2*)c->hbeam.p;
-        g1.tilt_sign = +1;
+        GatherArgs g2 = gather_args(c, 2, ids, nb);
+        g2.rows_pad = Dpad;
+        GatherArgs g1 = gather_args(c, 1, ids, nb);
+        g1.rows_pad = Bpad;
         g1.nch = nch;
         g1.H = (const float2*)H;
         if (tc) {
@@ -863,35 +890,20 @@ bip_status bip_site_windows(bip_ctx* c, int32_t site, void* s1_out, void* s2_out
     if (!c->s1 || !c->s2 || c->sig1 != c->sig2)
         return fail(c, BIP_ERR_INVALID_ARG, "bip_build_s1 and bip_build_s2 must run first on the same sites");
     if (site < 0 || site >= c->n_sites) return fail(c, BIP_ERR_INVALID_ARG, "site out of range");
+    if (((reinterpret_cast<uintptr_t>(s1_out) | reinterpret_cast<uintptr_t>(s2_out)) & 15) != 0)
+        return fail(c, BIP_ERR_INVALID_ARG, "window outputs must be 16-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     const bip_config& g = c->cfg;
     const int K = g.win * g.win;
-    GatherArgs ga{};
-    ga.n_sites = 1;
-    ga.site_ids = (const int32_t*)c->seq_ids_d.p + site;
-    ga.sites = (const SiteDev*)c->sites_d.p;
-    ga.win = g.win; ga.ny = g.ny; ga.nx = g.nx; ga.K = K;
-    ga.magnitude = g.recon == BIP_RECON_MAGNITUDE;
-    ga.ey = (const float2*)c->ey.p;
-    ga.ex = (const float2*)c->ex.p;
+    const int32_t* ids = (const int32_t*)c->seq_ids_d.p + site;
     if (s1_out) {
-        GatherArgs a = ga;
-        a.Bp = c->geo.Bp1; a.n_targets = c->geo.B; a.rows_pad = c->geo.B;
-        a.stash = (const float2*)c->stash1.p;
-        a.ell = EllDev{c->ell1_k, (const uint16_t*)c->ell1_idx.p, (const float*)c->ell1_w.p, (const int32_t*)c->ell1_n.p};
-        a.h_t = (const int2*)c->hbeam.p;
-        a.tilt_sign = +1;
+        GatherArgs a = gather_args(c, 1, ids, 1);
         a.out_c64 = (float2*)s1_out;
         a.site_stride = (int64_t)c->geo.B * K;
         CUDA_TRY(c, bip_gather(a, s));
     }
     if (s2_out) {
-        GatherArgs a = ga;
-        a.Bp = c->geo.Bp2; a.n_targets = c->geo.n_det; a.rows_pad = c->geo.n_det;
-        a.stash = (const float2*)c->stash2.p;
-        a.ell = EllDev{c->ell2_k, (const uint16_t*)c->ell2_idx.p, (const float*)c->ell2_w.p, (const int32_t*)c->ell2_n.p};
-        a.h_t = (const int2*)c->hdet.p;
-        a.tilt_sign = -1;
+        GatherArgs a = gather_args(c, 2, ids, 1);
         a.out_c64 = (float2*)s2_out;
         a.site_stride = (int64_t)c->geo.n_det * K;
         CUDA_TRY(c, bip_gather(a, s));
@@ -929,6 +941,7 @@ bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_ou
     if (!c->s1 || !c->s2 || c->sig1 != c->sig2)
         return fail(c, BIP_ERR_INVALID_ARG, "bip_build_s1 and bip_build_s2 must run first on the same sites");
     if (!H || !m_out) return fail(c, BIP_ERR_INVALID_ARG, "null pointer argument");
+    if ((reinterpret_cast<uintptr_t>(H) & 15) != 0) return fail(c, BIP_ERR_INVALID_ARG, "H must be 16-byte aligned");
     if (site < 0 || site >= c->n_sites) return fail(c, BIP_ERR_INVALID_ARG, "site out of range");
     cudaStream_t s = (cudaStream_t)stream;
     const bip_config& g = c->cfg;
@@ -943,26 +956,11 @@ bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_ou
     CUDA_TRY(c, ensure(opA, perA * 8, true, s));
     CUDA_TRY(c, ensure(opB, perB * 8, true, s));
     CUDA_TRY(c, ensure(c->partial, (size_t)Dpad * ldc * sizeof(float2), false, s));
-    GatherArgs ga{};
-    ga.n_sites = 1;
-    ga.site_ids = (const int32_t*)c->seq_ids_d.p + site;
-    ga.sites = (const SiteDev*)c->sites_d.p;
-    ga.win = g.win; ga.ny = g.ny; ga.nx = g.nx; ga.K = K;
-    ga.magnitude = g.recon == BIP_RECON_MAGNITUDE;
-    ga.ey = (const float2*)c->ey.p;
-    ga.ex = (const float2*)c->ex.p;
-    GatherArgs g2 = ga;
-    g2.Bp = geo.Bp2; g2.n_targets = geo.n_det; g2.rows_pad = Dpad;
-    g2.stash = (const float2*)c->stash2.p;
-    g2.ell = EllDev{c->ell2_k, (const uint16_t*)c->ell2_idx.p, (const float*)c->ell2_w.p, (const int32_t*)c->ell2_n.p};
-    g2.h_t = (const int2*)c->hdet.p;
-    g2.tilt_sign = -1;
-    GatherArgs g1 = ga;
-    g1.Bp = geo.Bp1; g1.n_targets = geo.B; g1.rows_pad = Bpad;
-    g1.stash = (const float2*)c->stash1.p;
-    g1.ell = EllDev{c->ell1_k, (const uint16_t*)c->ell1_idx.p, (const float*)c->ell1_w.p, (const int32_t*)c->ell1_n.p};
-    g1.h_t = (const int2*)c->hbeam.p;
-    g1.tilt_sign = +1;
+    const int32_t* ids = (const int32_t*)c->seq_ids_d.p + site;
+    GatherArgs g2 = gather_args(c, 2, ids, 1);
+    g2.rows_pad = Dpad;
+    GatherArgs g1 = gather_args(c, 1, ids, 1);
+    g1.rows_pad = Bpad;
     g1.nch = nch;
     g1.H = (const float2*)H;
     if (tc) {

@@ -45,11 +45,16 @@ struct SiteDev {            // one ionized site, as the kernels see it
     double ty, tx;          // position in pixels
 };
 
-struct EllDev {             // sparse NNW weights, fixed row width
-    int32_t k;              // entries per row (a multiple of 8, padded with w = 0)
-    const uint16_t* idx;    // [rows * k] parent index
-    const float* w;         // [rows * k] weight
-    const int32_t* nnz;     // [rows] nonzero entries of each row (<= k)
+// Natural-neighbour weights of consecutive target groups: the targets
+// kGatherGroup g .. kGatherGroup g + kGatherGroup - 1 share one list of
+// parents (the union of their neighbours), each entry with the weights of
+// all the group's targets (0 where the parent is not a neighbour).
+constexpr int kGatherGroup = 4;
+struct GroupDev {
+    int32_t n_groups;
+    const int32_t* off;     // [n_groups + 1] entry range of each group
+    const uint16_t* par;    // [entries] parent index
+    const float4* w;        // [entries] weights of the group's targets
 };
 
 // ---------------------------------------------------------------------------
@@ -92,12 +97,14 @@ struct GatherArgs {
     int win, ny, nx;
     int Bp, n_targets, rows_pad;    // parents, targets, padded rows
     const float2* stash;            // [n_sites_total, Bp, win, win]
-    EllDev ell;                     // weights of the targets
+    GroupDev grp;                   // weights of the targets
     const int2* h_t;                // [n_targets] target beams (y, x)
     int tilt_sign;                  // +1 (S1) or -1 (S2)
     int magnitude;                  // 1: magnitude-preserving
     const float2* ey;               // [ny] exp(+2 pi i m / ny)
     const float2* ex;               // [nx]
+    const float2* ytab;             // [ny][win] exp(+2 pi i h u / ny), row h mod ny
+    const float2* xtab;             // [nx][win] exp(+2 pi i h v / nx), row h mod nx
     // channel expansion (S1 side): out row (n * rows_pad + t) = H_n * S
     int nch;                        // 0: no channel product (S2 side)
     const float2* H;                // [sum nch, win, win]
