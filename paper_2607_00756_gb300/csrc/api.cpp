@@ -160,6 +160,30 @@ int signed_bin(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// Twiddles of the register FFT of length n (n a power of two, 64..1024),
+// pass by pass: pass p = 1 .. npass-1 combines sub-transforms of length
+// Ns = 8^p with radix R (8, or 4 / 2 for the last pass), and its entry
+// (r - 1) Ns + k holds exp(-2 pi i r k / (Ns R)), r = 1..R-1, k < Ns.
+// Evaluated in FP64, rounded to FP32; the rest of the n entries is zero.
+std::vector<float2> fft_twiddles(int n) {
+    int lg = 0;
+    while ((1 << lg) < n) ++lg;
+    const int rl = lg % 3 == 2 ? 4 : (lg % 3 == 1 ? 2 : 8);
+    const int npass = lg / 3 + (rl == 8 ? 0 : 1);
+    std::vector<float2> t(n, float2{0.f, 0.f});
+    size_t o = 0;
+    for (int p = 1; p < npass; ++p) {
+        const int ns = 1 << (3 * p), R = p == npass - 1 ? rl : 8;
+        for (int r = 1; r < R; ++r)
+            for (int k = 0; k < ns; ++k) {
+                const double a = -2.0 * kPi * (double)r * k / ((double)ns * R);
+                t[o + (size_t)(r - 1) * ns + k] = float2{(float)std::cos(a), (float)std::sin(a)};
+            }
+        o += (size_t)(R - 1) * ns;
+    }
+    return t;
+}
+
 // Grouped sparse copy of a dense weight matrix [rows][cols]: rows
 // kGatherGroup g .. + kGatherGroup - 1 form group g, whose entries are the
 // columns (parents) any of its rows uses, with the rows' weights side by side.
@@ -198,9 +222,10 @@ bip_status make_tables(bip_ctx* c, cudaStream_t s) {
         const double a = sign * 2.0 * kPi * (double)m / (double)n;
         return float2{(float)std::cos(a), (float)std::sin(a)};
     };
-    std::vector<float2> twy(g.ny), twx(g.nx), ey(g.ny), ex(g.nx), py(g.ny), px(g.nx);
-    for (int m = 0; m < g.ny; ++m) { twy[m] = turn(m, g.ny, -1.0); ey[m] = turn(m, g.ny, +1.0); }
-    for (int m = 0; m < g.nx; ++m) { twx[m] = turn(m, g.nx, -1.0); ex[m] = turn(m, g.nx, +1.0); }
+    const std::vector<float2> twy = fft_twiddles(g.ny), twx = fft_twiddles(g.nx);
+    std::vector<float2> ey(g.ny), ex(g.nx), py(g.ny), px(g.nx);
+    for (int m = 0; m < g.ny; ++m) ey[m] = turn(m, g.ny, +1.0);
+    for (int m = 0; m < g.nx; ++m) ex[m] = turn(m, g.nx, +1.0);
     // separable propagator exp(-i pi lambda dz q^2) per axis, with the 1/N
     // of the unnormalised inverse FFT folded in
     for (int k = 0; k < g.ny; ++k) {
@@ -603,6 +628,7 @@ GatherArgs gather_args(const bip_ctx* c, int side, const int32_t* ids, int n) {
     a.ex = (const float2*)c->ex.p;
     a.ytab = (const float2*)c->ytab.p;
     a.xtab = (const float2*)c->xtab.p;
+    a.fx = g.fx;
     if (side == 1) {
         a.Bp = c->geo.Bp1; a.n_targets = c->geo.B; a.rows_pad = c->geo.B;
         a.stash = (const float2*)c->stash1.p;
@@ -1061,15 +1087,8 @@ extern "C" bip_status bip_build_s1_noalloc(bip_ctx* c, const float* V, const bip
     unsigned char* sc = (unsigned char*)base;
 
     // host tables (same definitions as the context's: FP64 then rounded)
-    std::vector<float2> twy(g.ny), twx(g.nx), py(g.ny), px(g.nx);
-    for (int m = 0; m < g.ny; ++m) {
-        const double a = -2.0 * kPi * m / g.ny;
-        twy[m] = float2{(float)std::cos(a), (float)std::sin(a)};
-    }
-    for (int m = 0; m < g.nx; ++m) {
-        const double a = -2.0 * kPi * m / g.nx;
-        twx[m] = float2{(float)std::cos(a), (float)std::sin(a)};
-    }
+    const std::vector<float2> twy = fft_twiddles(g.ny), twx = fft_twiddles(g.nx);
+    std::vector<float2> py(g.ny), px(g.nx);
     for (int k = 0; k < g.ny; ++k) {
         const double q = signed_bin(k, g.ny) / g.ly;
         const double a = -kPi * geo.lambda * g.dz * q * q;

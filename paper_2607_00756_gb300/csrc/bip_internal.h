@@ -64,7 +64,7 @@ struct GroupDev {
 struct MsPlan {
     int ny, nx, ncol;
     float sigma;                    // interaction constant (FP32)
-    const float2* twy;              // [ny] exp(-2 pi i m / ny)
+    const float2* twy;              // [ny] register-FFT twiddles, pass by pass
     const float2* twx;              // [nx]
     const float2* py;               // [ny] exp(-i pi lambda dz qy^2) / ny
     const float2* px;               // [nx]
@@ -105,6 +105,7 @@ struct GatherArgs {
     const float2* ex;               // [nx]
     const float2* ytab;             // [ny][win] exp(+2 pi i h u / ny), row h mod ny
     const float2* xtab;             // [nx][win] exp(+2 pi i h v / nx), row h mod nx
+    int fx;                         // lattice step of the targets along x
     // channel expansion (S1 side): out row (n * rows_pad + t) = H_n * S
     int nch;                        // 0: no channel product (S2 side)
     const float2* H;                // [sum nch, win, win]

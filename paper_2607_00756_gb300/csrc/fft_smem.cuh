@@ -1,19 +1,21 @@
-// Shared-memory Stockham FFT for power-of-two lengths 64..1024.
+// Register-resident radix-8 Stockham FFT for power-of-two lengths 64..1024.
 //
-// A transform of length N is done by N/8 threads; every pass is a radix-8
-// pass while at least 8 points remain per sub-transform, the last one
-// radix 4 or 2.  Each thread always holds 8 values per pass (one radix-8,
-// two radix-4 or four radix-2 butterflies).  Twiddles W_N^m =
-// exp(-2 pi i m / N) come from a table computed on the host in FP64 and
-// rounded to FP32 (kept in shared memory by the callers).  Data live in
-// shared memory with one padding slot per 16 entries to spread the strided
-// accesses over the banks.
+// A transform of length N is done by N/8 threads, each holding 8 values.
+// Every pass is a radix-8 pass while at least 8 points remain per
+// sub-transform, the last one radix 4 or 2.  The first pass reads and the
+// last pass writes the cyclic distribution x[t + m N/8] (thread t, value
+// m), so data cross shared memory only between passes.  Twiddles come from
+// a table computed on the host in FP64 and rounded to FP32, laid out pass by
+// pass so that the threads of a warp read consecutive entries.
 #pragma once
 
 #include <cuda_runtime.h>
 
-#define FFT_PAD(i) ((i) + ((i) >> 4))
-
+// Exchange-buffer index: an XOR swizzle inside each 16-entry (128-byte)
+// row that keeps both the strided writes and the contiguous reads of every
+// pass free of shared-memory bank conflicts (bits 4-6 of the index are
+// folded into bits 0-3; it permutes each aligned group of 16).
+#define FFT_SWZ(i) ((i) ^ (((i) >> 4) & 7) ^ ((((i) >> 6) & 1) << 3))
 __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
@@ -67,69 +69,13 @@ __device__ __forceinline__ void dft8(float2* v) {
     v[7] = c_sub(e3, t3);
 }
 
-// One in-place Stockham pass of radix R over `buf` (length N, padded).
-// Thread t of nt = N/8 handles 8/R butterflies j = t + b*nt.
-// Both __syncthreads are block-wide: every thread of the block calls this.
-template <int N, int R, bool INV>
-__device__ __forceinline__ void stockham_pass(float2* buf, int Ns, int t, const float2* tw) {
-    constexpr int NT = N / 8;
-    constexpr int NB = 8 / R;
-    constexpr int STRIDE = N / R;
-    float2 v[8];
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        const int j = t + b * NT;
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[b * R + r] = buf[FFT_PAD(j + r * STRIDE)];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        const int j = t + b * NT;
-        const int k = j % Ns;
-        if (Ns > 1) {
-            const int step = k * (N / (Ns * R));
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                float2 w = tw[r * step];
-                if (INV) w.y = -w.y;
-                v[b * R + r] = c_mul(v[b * R + r], w);
-            }
-        }
-        if (R == 8) dft8<INV>(&v[b * R]);
-        if (R == 4) dft4<INV>(v[b * R], v[b * R + 1], v[b * R + 2], v[b * R + 3]);
-        if (R == 2) dft2<INV>(v[b * R], v[b * R + 1]);
-        const int base = (j / Ns) * Ns * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) buf[FFT_PAD(base + r * Ns)] = v[b * R + r];
-    }
-    __syncthreads();
-}
-
-// Full transform of length N (unnormalised).  `t` in [0, N/8) is the
-// thread's rank within this transform; the caller syncs before (data
-// written) -- the last pass ends with a block-wide sync.
-template <int N, bool INV>
-__device__ __forceinline__ void fft_smem(float2* buf, int t, const float2* tw) {
-    __syncthreads();
-    int Ns = 1;
-#pragma unroll
-    for (int rem = N; rem >= 8; rem /= 8) {
-        stockham_pass<N, 8, INV>(buf, Ns, t, tw);
-        Ns *= 8;
-    }
-    constexpr int LOG = (N == 64) ? 6 : (N == 128) ? 7 : (N == 256) ? 8 : (N == 512) ? 9 : 10;
-    if (LOG % 3 == 2) stockham_pass<N, 4, INV>(buf, Ns, t, tw);
-    if (LOG % 3 == 1) stockham_pass<N, 2, INV>(buf, Ns, t, tw);
-}
-
-// Register-resident transform of length N by NT = N/8 threads.  Thread t
-// holds x[t + m NT] in v[m] (m = 0..7) on entry and X[t + m NT] on exit:
-// the first radix-8 pass reads exactly that distribution and the last pass
-// writes it, so only the data between passes go through shared memory.
-// Pass p works on sub-transforms of length Ns = 8^p; for p = 1..NPASS-1 a
-// caller stores v at out_pos(p, r, t) (r = 0..7), synchronises, loads
-// u[e] from in_pos<p>(e, t) (e = 0..7) and calls pass<p>(u, v, t, tw).
+// Transform of length N by NT = N/8 threads.  Thread t holds x[t + m NT]
+// in v[m] (m = 0..7) on entry and X[t + m NT] on exit.  Pass p combines
+// sub-transforms of length Ns = 8^p; for p = 1..NPASS-1 a caller stores v
+// at out_pos(p, r, t) (r = 0..7), synchronises, loads u[e] from
+// in_pos<p>(e, t) (e = 0..7) and calls pass<p>(u, v, t, tw).  The twiddle
+// table holds, for each such pass in turn, entry (r - 1) Ns + k =
+// exp(-2 pi i r k / (Ns R)), r = 1..R-1, k < Ns (R the pass's radix).
 template <int N, bool INV>
 struct FftReg {
     static constexpr int NT = N / 8;
@@ -138,6 +84,12 @@ struct FftReg {
     static constexpr int NPASS = LOG / 3 + (RL == 8 ? 0 : 1);
     template <int P>
     __host__ __device__ static constexpr int radix() { return P == NPASS - 1 ? RL : 8; }
+    // start of pass P's twiddles in the table
+    template <int P>
+    __host__ __device__ static constexpr int tw_off() {
+        if constexpr (P <= 1) return 0;
+        else return tw_off<P - 1>() + (radix<P - 1>() - 1) * (1 << (3 * (P - 1)));
+    }
 
     __device__ __forceinline__ static void first(float2 (&v)[8]) { dft8<INV>(v); }
 
@@ -162,11 +114,11 @@ struct FftReg {
         constexpr int Ns = 1 << (3 * P);
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            const int j = t + b * NT;
-            const int step = (j % Ns) * (N / (Ns * R));
+            const int k = (t + b * NT) % Ns;
+            const float2* twp = tw + tw_off<P>() + k;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = tw[r * step];
+                float2 w = twp[(r - 1) * Ns];
                 if (INV) w.y = -w.y;
                 u[b * R + r] = c_mul(u[b * R + r], w);
             }
@@ -181,16 +133,16 @@ struct FftReg {
     }
 };
 
-// One exchange of fft_reg: pass P through buffer `buf` (padded).
+// One exchange of fft_reg: pass P through buffer `buf` (N entries, swizzled).
 template <int N, bool INV, int P>
 __device__ __forceinline__ void fft_reg_step(float2 (&v)[8], float2* buf, int t, const float2* tw) {
     using F = FftReg<N, INV>;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) buf[FFT_PAD(F::out_pos(P, r, t))] = v[r];
+    for (int r = 0; r < 8; ++r) buf[FFT_SWZ(F::out_pos(P, r, t))] = v[r];
     __syncthreads();
     float2 u[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) u[e] = buf[FFT_PAD(F::template in_pos<P>(e, t))];
+    for (int e = 0; e < 8; ++e) u[e] = buf[FFT_SWZ(F::template in_pos<P>(e, t))];
     F::template pass<P>(u, v, t, tw);
 }
 

@@ -97,6 +97,12 @@ __global__ void __launch_bounds__(kThreads, 3) gather_kernel(GatherArgs a) {
     const int gb = blockIdx.y * (kWarps * kGroupsPerWarp);
     const int ge = min(gb + kWarps * kGroupsPerWarp, a.grp.n_groups);
 
+    float2 stp0 = __ldg(&a.ex[(a.fx * (st.ox + v)) & (a.nx - 1)]);
+    float2 stp1 = __ldg(&a.ex[(a.fx * (st.ox + v + 1)) & (a.nx - 1)]);
+    if (a.tilt_sign < 0) {
+        stp0.y = -stp0.y;
+        stp1.y = -stp1.y;
+    }
     for (int gi = gb + warp; gi < ge; gi += kWarps) {
         float ur[kG][2], ui[kG][2], am[kG][2];
 #pragma unroll
@@ -120,23 +126,31 @@ __global__ void __launch_bounds__(kThreads, 3) gather_kernel(GatherArgs a) {
                 am[t][1] = fmaf(w[t], pm.y, am[t][1]);
             }
         }
+        float2 t0 = make_float2(1.f, 0.f), t1 = t0;
+        int2 hp = make_int2(a.ny, 0);          // no previous target
 #pragma unroll
         for (int tt = 0; tt < kG; ++tt) {
             const int t = gi * kG + tt;
             if (t < a.n_targets) {
-                // re-tilt exp(sign 2 pi i (h_y (oy + u)/ny + h_x (ox + v)/nx))
                 const int2 h = __ldg(&a.h_t[t]);
-                const float2 base = c_mul(__ldg(&a.ey[(h.x * st.oy) & (a.ny - 1)]),
-                                          __ldg(&a.ex[(h.y * st.ox) & (a.nx - 1)]));
-                const float2 ty = __ldg(&a.ytab[(size_t)(h.x & (a.ny - 1)) * a.win + u]);
-                const float4 tx = __ldg(reinterpret_cast<const float4*>(a.xtab + (size_t)(h.y & (a.nx - 1)) * a.win + v));
-                const float2 by = c_mul(base, ty);
-                float2 t0 = c_mul(by, make_float2(tx.x, tx.y));
-                float2 t1 = c_mul(by, make_float2(tx.z, tx.w));
-                if (a.tilt_sign < 0) {
-                    t0.y = -t0.y;
-                    t1.y = -t1.y;
+                if (h.x == hp.x && h.y == hp.y + a.fx) {
+                    t0 = c_mul(t0, stp0);
+                    t1 = c_mul(t1, stp1);
+                } else {
+                    const float2 base = c_mul(__ldg(&a.ey[(h.x * st.oy) & (a.ny - 1)]),
+                                              __ldg(&a.ex[(h.y * st.ox) & (a.nx - 1)]));
+                    const float2 ty = __ldg(&a.ytab[(size_t)(h.x & (a.ny - 1)) * a.win + u]);
+                    const float4 tx =
+                        __ldg(reinterpret_cast<const float4*>(a.xtab + (size_t)(h.y & (a.nx - 1)) * a.win + v));
+                    const float2 by = c_mul(base, ty);
+                    t0 = c_mul(by, make_float2(tx.x, tx.y));
+                    t1 = c_mul(by, make_float2(tx.z, tx.w));
+                    if (a.tilt_sign < 0) {
+                        t0.y = -t0.y;
+                        t1.y = -t1.y;
+                    }
                 }
+                hp = h;
                 const float2 S0 = c_mul(recon_value(ur[tt][0], ui[tt][0], am[tt][0], a.magnitude), t0);
                 const float2 S1 = c_mul(recon_value(ur[tt][1], ui[tt][1], am[tt][1], a.magnitude), t1);
 #pragma unroll

@@ -34,13 +34,13 @@ template <int NX>
 __global__ void __launch_bounds__(kThreads) row_pass_kernel(MsPlan plan, MsRowArgs a) {
     constexpr int NT = NX / 8;                 // threads per row
     constexpr int RPB = kThreads / NT;         // rows per block
-    constexpr int ROWLEN = NX + NX / 16;       // padded
+    constexpr int ROWLEN = NX;
     extern __shared__ float2 smem[];
     const int sub = threadIdx.x / NT;
     const int t = threadIdx.x % NT;
     float2* b0 = smem + 2 * sub * ROWLEN;      // exchange buffers of this row
     float2* b1 = b0 + ROWLEN;
-    float2* tw = smem + 2 * RPB * ROWLEN;      // [NX] twiddles
+    float2* tw = smem + 2 * RPB * ROWLEN;      // [NX] pass twiddles
     float2* tt = tw + NX;                      // [NX] transmission of this y
     const int gpy = (plan.ncol + RPB - 1) / RPB;
     const int y = blockIdx.x / gpy;
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(ColShape<NY>::THREADS, 2048 / ColShape<NY>::TH
 
 template <int NX>
 cudaError_t launch_row(const MsPlan& p, const MsRowArgs& a, cudaStream_t s) {
-    constexpr int NT = NX / 8, RPB = kThreads / NT, ROWLEN = NX + NX / 16;
+    constexpr int NT = NX / 8, RPB = kThreads / NT, ROWLEN = NX;
     const long long blocks = (long long)p.ny * ((p.ncol + RPB - 1) / RPB);
     const size_t sm = ((size_t)2 * RPB * ROWLEN + 2 * NX) * sizeof(float2);
     static bool attr = false;
