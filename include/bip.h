@@ -200,7 +200,9 @@ bip_status bip_site_coupling(bip_ctx* ctx, const void* H, int32_t site, void* m_
  * Stages: multislice row pass, multislice column pass, window
  * reconstruction, coupling GEMM, Gram GEMM, quadratic form, illumination +
  * site sum.  ms / launches: [BIP_N_STAGES] host arrays (either may be
- * NULL).  bip_set_profiling(ctx, 1) clears earlier records. */
+ * NULL).  bip_set_profiling(ctx, on): on = 0 stops timing, on < 0 times
+ * every stage, on > 0 times the stages whose bit (1 << stage) is set; the
+ * launch counts cover every stage.  Each call clears earlier records. */
 enum {
     BIP_STAGE_MS_ROW = 0, BIP_STAGE_MS_COL = 1, BIP_STAGE_GATHER = 2, BIP_STAGE_COUPLING = 3,
     BIP_STAGE_GRAM = 4, BIP_STAGE_QUADFORM = 5, BIP_STAGE_REDUCE = 6, BIP_N_STAGES = 7

@@ -249,8 +249,12 @@ N_STAGES = 7
 STAGES = ["ms_row", "ms_col", "gather", "coupling", "gram", "quadform", "reduce"]
 
 
-def bip_set_profiling(ctx, on):
-    _check("bip_set_profiling", ctx, _lib.bip_set_profiling(ctx, int(bool(on))))
+def bip_set_profiling(ctx, on, stages=None):
+    """Time every stage (on true), none (on false), or only `stages` (names)."""
+    mask = 0
+    if on:
+        mask = -1 if stages is None else sum(1 << STAGES.index(n) for n in stages)
+    _check("bip_set_profiling", ctx, _lib.bip_set_profiling(ctx, mask))
 
 
 def bip_get_profile(ctx):

@@ -57,7 +57,7 @@ struct bip_ctx {
     std::vector<int32_t> work_h;
 
     // per-stage event timing
-    bool prof = false;
+    uint32_t prof = 0;                  // stages timed (bit s: stage s)
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_rec;
@@ -101,14 +101,14 @@ struct StageTimer {
     }
     StageTimer(bip_ctx* c_, int st, cudaStream_t s_) : c(c_), stage(st), s(s_) {
         c->launches[stage]++;
-        if (c->prof) {
+        if (c->prof >> stage & 1u) {
             e0 = take();
             e1 = take();
             if (e0) cudaEventRecord(e0, s);
         }
     }
     ~StageTimer() {
-        if (c->prof && e0 && e1) {
+        if (e0 && e1) {
             cudaEventRecord(e1, s);
             c->ev_rec.push_back({stage, {e0, e1}});
         }
@@ -939,7 +939,7 @@ bip_status bip_site_windows(bip_ctx* c, int32_t site, void* s1_out, void* s2_out
 
 bip_status bip_set_profiling(bip_ctx* c, int32_t on) {
     if (!c) return BIP_ERR_INVALID_ARG;
-    c->prof = on != 0;
+    c->prof = on < 0 ? (1u << BIP_N_STAGES) - 1u : (uint32_t)on & ((1u << BIP_N_STAGES) - 1u);
     c->ev_used = 0;
     c->ev_rec.clear();
     for (int i = 0; i < BIP_N_STAGES; ++i) c->launches[i] = 0;
