@@ -122,14 +122,14 @@ def make_config(cfg, prec=None, recon=None):
 
 def make_atoms(atoms, nch):
     """bip_atom array from [n,3] (y, x, slice) and [n] channel counts."""
-    atoms = np.asarray(atoms, dtype=np.float64)
-    nch = np.asarray(nch)
+    atoms = np.asarray(atoms, dtype=np.float64).reshape(-1, 3)
+    nch = np.asarray(nch).reshape(-1)
     arr = (BipAtom * len(atoms))()
-    for i in range(len(atoms)):
-        arr[i].y = float(atoms[i, 0])
-        arr[i].x = float(atoms[i, 1])
-        arr[i].slice = int(atoms[i, 2])
-        arr[i].nch = int(nch[i])
+    view = np.ctypeslib.as_array(arr)          # structured view of the same memory
+    view["y"] = atoms[:, 0]
+    view["x"] = atoms[:, 1]
+    view["slice"] = atoms[:, 2].astype(np.int32)
+    view["nch"] = nch.astype(np.int32)
     return arr
 
 

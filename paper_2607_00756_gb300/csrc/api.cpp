@@ -50,7 +50,7 @@ struct bip_ctx {
     DevBuf stash1, stash2, cols;
 
     // map workspaces
-    DevBuf scans_d, work_d, partial, gdiff;
+    DevBuf scans_d, work_d, partial, gdiff, rsum;
     DevBuf opA32, opB32, mt32, q32;     // FP32 path (zeroed at allocation)
     DevBuf opA16, opB16, mt16, q16;     // split-BF16 path (zeroed at allocation)
     DevBuf errflag;
@@ -483,7 +483,7 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->xtab, &c->sites_d,
                      &c->plane_ids_d, &c->seq_ids_d, &c->row_off_d, &c->row_ent_d, &c->stash1, &c->stash2, &c->cols, &c->scans_d,
                      &c->gdiff, &c->kb_d, &c->lat_d, &c->work_d, &c->partial, &c->opA32, &c->opB32, &c->mt32, &c->q32, &c->opA16,
-                     &c->opB16, &c->mt16, &c->q16, &c->errflag};
+                     &c->opB16, &c->mt16, &c->q16, &c->errflag, &c->rsum};
     for (DevBuf* b : all) release(*b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
@@ -692,6 +692,9 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         CUDA_TRY(c, ensure(c->partial, (size_t)c->n_sites * P * sizeof(float), false, s));
         partial = (float*)c->partial.p;
     }
+    // scans outside a site's crop mask stay 0: the evaluation writes only
+    // the scan tiles that can meet the mask
+    CUDA_TRY(c, cudaMemsetAsync(partial, 0, (size_t)c->n_sites * P * sizeof(float), s));
 
     // scan-tile bounding boxes (host)
     std::vector<double> bb((size_t)n_tiles * 4);
@@ -854,7 +857,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         d.scale = (float)(g.fy * g.fx);
         d.partial = partial;
         TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_bin(d, s));
-        TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_eval(d, s));
+        if (d.n_work > 0) TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_eval(d, s));
     }
     if (tc) {
         int flag = 0;
@@ -863,11 +866,9 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         if (flag) return fail(c, BIP_ERR_TIMEOUT, "a tensor-core contraction gave up waiting (device timeout)");
     }
     if (map_out) {
-        TIMED(c, BIP_STAGE_REDUCE, s, bip_reduce_sites(partial, c->n_sites, P, (const double*)c->scans_d.p,
-                                                       (const SiteDev*)c->sites_d.p, g.ny, g.nx, g.fy, g.fx, map_out, s));
-    } else {
-        TIMED(c, BIP_STAGE_REDUCE, s, bip_zero_outside(partial, c->n_sites, P, (const double*)c->scans_d.p,
-                                                       (const SiteDev*)c->sites_d.p, g.ny, g.nx, g.fy, g.fx, s));
+        CUDA_TRY(c, ensure(c->rsum, bip_reduce_scratch_bytes(c->n_sites, P), false, s));
+        TIMED(c, BIP_STAGE_REDUCE, s, bip_reduce_sites(partial, c->n_sites, P, c->rsum.p, map_out, s));
+        if (c->n_sites > 0) c->launches[BIP_STAGE_REDUCE]++;   // two kernels: chunks, then their sum
     }
     return BIP_OK;
 }

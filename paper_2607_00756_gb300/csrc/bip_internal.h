@@ -159,12 +159,12 @@ struct DiffArgs {
 cudaError_t bip_diff_bin(const DiffArgs& a, cudaStream_t s);
 cudaError_t bip_diff_eval(const DiffArgs& a, cudaStream_t s);
 
-// reduce.cu : map[rho] = Neumaier sum over sites of the in-crop partials
-cudaError_t bip_reduce_sites(const float* partial, int n_sites, int P, const double* scans,
-                             const SiteDev* sites, int ny, int nx, int fy, int fx,
-                             double* map_out, cudaStream_t s);
-cudaError_t bip_zero_outside(float* partial, int n_sites, int P, const double* scans,
-                             const SiteDev* sites, int ny, int nx, int fy, int fx, cudaStream_t s);
+// reduce.cu : map[rho] = FP64 Neumaier sum over sites of the partials
+// (already zero outside each site's crop mask), in a fixed order; scratch
+// of bip_reduce_scratch_bytes(n_sites, P) bytes.
+size_t bip_reduce_scratch_bytes(int n_sites, int P);
+cudaError_t bip_reduce_sites(const float* partial, int n_sites, int P, void* scratch, double* map_out,
+                             cudaStream_t s);
 
 // gemm_tc.cu : tcgen05 complex contractions in split BF16 or BF16.
 // Operands are bf16 planes, K contiguous -- four (re_hi, re_lo, im_hi,

@@ -1,53 +1,62 @@
 // Sum of the per-site map contributions (Eq. map-sum, incoherent sum over
-// sites): every scan adds the in-crop contributions of all sites in site
-// order, in FP64 with Neumaier compensation, so the result does not depend
-// on how the sites were batched.
-#include "bip_device.cuh"
+// sites).  The partials are zero outside each site's crop mask (the map
+// clears them before the per-site evaluation writes the in-crop scans), so
+// the sum runs over all sites.  It is done in FP64 with Neumaier
+// compensation in a fixed order -- sites in chunks of kChunk in site order,
+// then the chunks in order -- so the result does not depend on how the
+// sites were batched or scheduled.
 #include "bip_internal.h"
 
 namespace {
 
-__global__ void reduce_kernel(const float* __restrict__ partial, int n_sites, int P,
-                              const double* __restrict__ scans, const SiteDev* __restrict__ sites, int ny,
-                              int nx, int fy, int fx, double* __restrict__ out) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+constexpr int kChunk = 64;
+constexpr int kThreads = 256;
+
+// Neumaier step: s + x with the rounding error of the addition kept in c
+__device__ __forceinline__ void neumaier(double& s, double& c, double x) {
+    const double t = s + x;
+    if (fabs(s) >= fabs(x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+}
+
+__global__ void __launch_bounds__(kThreads) reduce_chunk_kernel(const float* __restrict__ partial, int n_sites,
+                                                                int P, double2* __restrict__ chunk_sum) {
+    const int p = blockIdx.x * kThreads + threadIdx.x;
     if (p >= P) return;
-    const double ry = scans[2 * p], rx = scans[2 * p + 1];
+    const int k0 = blockIdx.y * kChunk, k1 = min(k0 + kChunk, n_sites);
     double s = 0.0, c = 0.0;
-    for (int k = 0; k < n_sites; ++k) {
-        const SiteDev st = sites[k];
-        if (!in_crop(ry, rx, st.ty, st.tx, ny, nx, fy, fx)) continue;
-        const double x = (double)partial[(size_t)k * P + p];
-        const double t = s + x;
-        if (fabs(s) >= fabs(x)) c += (s - t) + x;
-        else c += (x - t) + s;
-        s = t;
+#pragma unroll 8
+    for (int k = k0; k < k1; ++k) neumaier(s, c, (double)__ldg(&partial[(size_t)k * P + p]));
+    chunk_sum[(size_t)blockIdx.y * P + p] = make_double2(s, c);
+}
+
+__global__ void __launch_bounds__(kThreads) reduce_final_kernel(const double2* __restrict__ chunk_sum, int n_chunks,
+                                                                int P, double* __restrict__ out) {
+    const int p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= P) return;
+    double s = 0.0, c = 0.0;
+    for (int j = 0; j < n_chunks; ++j) {
+        const double2 v = chunk_sum[(size_t)j * P + p];
+        neumaier(s, c, v.x);
+        neumaier(s, c, v.y);
     }
     out[p] = s + c;
 }
 
-__global__ void zero_outside_kernel(float* __restrict__ partial, int n_sites, int P,
-                                    const double* __restrict__ scans, const SiteDev* __restrict__ sites, int ny,
-                                    int nx, int fy, int fx) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k = blockIdx.y;
-    if (p >= P) return;
-    const SiteDev st = sites[k];
-    if (!in_crop(scans[2 * p], scans[2 * p + 1], st.ty, st.tx, ny, nx, fy, fx)) partial[(size_t)k * P + p] = 0.f;
-}
-
 }  // namespace
 
-cudaError_t bip_reduce_sites(const float* partial, int n_sites, int P, const double* scans, const SiteDev* sites,
-                             int ny, int nx, int fy, int fx, double* out, cudaStream_t s) {
-    reduce_kernel<<<(P + 255) / 256, 256, 0, s>>>(partial, n_sites, P, scans, sites, ny, nx, fy, fx, out);
-    return cudaGetLastError();
+size_t bip_reduce_scratch_bytes(int n_sites, int P) {
+    return (size_t)((n_sites + kChunk - 1) / kChunk) * P * sizeof(double2);
 }
 
-cudaError_t bip_zero_outside(float* partial, int n_sites, int P, const double* scans, const SiteDev* sites,
-                             int ny, int nx, int fy, int fx, cudaStream_t s) {
-    if (n_sites == 0) return cudaSuccess;
-    dim3 grid((P + 255) / 256, n_sites);
-    zero_outside_kernel<<<grid, 256, 0, s>>>(partial, n_sites, P, scans, sites, ny, nx, fy, fx);
+cudaError_t bip_reduce_sites(const float* partial, int n_sites, int P, void* scratch, double* out, cudaStream_t s) {
+    const int n_chunks = (n_sites + kChunk - 1) / kChunk;
+    if (n_chunks == 0) return cudaMemsetAsync(out, 0, (size_t)P * sizeof(double), s);
+    double2* cs = static_cast<double2*>(scratch);
+    reduce_chunk_kernel<<<dim3((P + kThreads - 1) / kThreads, n_chunks), kThreads, 0, s>>>(partial, n_sites, P, cs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce_final_kernel<<<(P + kThreads - 1) / kThreads, kThreads, 0, s>>>(cs, n_chunks, P, out);
     return cudaGetLastError();
 }
