@@ -169,9 +169,12 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # GPU arm
 
-def algorithmic(cfg, geo_sizes, n_sites, n_crop, nch, geo_beams=None):
+def algorithmic(cfg, geo_sizes, n_sites, n_crop, nch, geo_beams=None, path="fp32"):
     """Per-stage algorithmic work of one step (flops or bytes), the figures
     the roofline fractions divide."""
+    # bytes per complex operand element: complex64, four bf16 planes
+    # (split BF16) or two (mixed)
+    op_bytes = {"fp32": 8.0, "split_bf16": 8.0, "mixed": 4.0}[path]
     B, n_det, bp1, bp2 = geo_sizes
     K = cfg.win * cfg.win
     G = cfg.ny * cfg.nx
@@ -191,7 +194,8 @@ def algorithmic(cfg, geo_sizes, n_sites, n_crop, nch, geo_beams=None):
         # multislice: one read + one write of every column per pass
         "ms_row_bytes": 16.0 * G,               # per column per pass (+ V from L2)
         "ms_col_bytes": 16.0 * G,
-        "gather_bytes": 8.0 * K * (n_det + nch * B) * n_sites,   # operand writes
+        # operand writes plus the two stashes read once
+        "gather_bytes": (op_bytes * K * (n_det + nch * B) + 8.0 * K * (bp1 + bp2)) * n_sites,
     }
 
 
@@ -318,53 +322,84 @@ def run_gpu(args, rank, world):
                                   peak_kind=peak_kind)
 
 
-def roofline(cfg, path, res, info, geo_sizes):
-    """Roofline of the step's dominant kernel, from CUDA events recorded
-    around each of its launches inside the timed region."""
-    alg = algorithmic(cfg, geo_sizes, info["n_sites"], info["n_crop"], info["nch"], info.get("beams"))
-    stage, ms, n = res["dominant"]
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture of
+# the same launch size (profiles/coupling_gram_tc_config2_16site_batch.md);
+# reported only while the kernel's source file is unchanged.
+NCU_TRAFFIC = {
+    ("mixed", "coupling"): {"bytes": 930134016 + 122630400,
+                            "source": "paper_2607_00756_gb300/csrc/gemm_tc.cu",
+                            "sha256": "390a2af8f476685d2353f3b4c5d968a91921336812925dc1ff5352be8adfc08a"},
+}
+
+
+def ncu_traffic(path, stage):
+    import hashlib
+    rec = NCU_TRAFFIC.get((path, stage))
+    if rec is None:
+        return None
+    try:
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
+                return None
+    except OSError:
+        return None
+    return rec["bytes"]
+
+
+def stage_roofline(cfg, path, stage, ms, n, steps, info, geo_sizes):
+    """Achieved rate and roofline fraction of one stage: ms and n are the
+    stage's summed event time and launch count over `steps` steps."""
+    alg = algorithmic(cfg, geo_sizes, info["n_sites"], info["n_crop"], info["nch"], info.get("beams"), path)
     peaks = info["peaks"]
-    steps = None
     ms_launch = ms / max(n, 1)
     out = {"kernel": stage, "launches": n, "ms_per_launch": ms_launch}
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fp32_src = "FP32 FMA: 152 SM x 128 lanes x 2 flop x max SM clock"
     if stage in ("coupling", "gram", "quadform"):
-        flops_step = alg[stage]
         # per launch: the step's work over the step's launches of this stage
-        per_step_launches = n / res["steps"]
-        per_launch = flops_step / per_step_launches
-        if stage == "quadform":
-            # FP32 SIMT evaluation of the difference polynomial
+        per_launch = alg[stage] / (n / steps)
+        if stage == "quadform" or path == "fp32":
             achieved = per_launch / (ms_launch / 1e3) / 1e12
-            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            out.update(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
-                       peak_source="FP32 FMA: 152 SM x 128 lanes x 2 flop x max SM clock")
-        elif path in ("split_bf16", "mixed"):
+            out.update(bound="alu", achieved=achieved, peak=fp32_peak, unit="TFLOP/s", peak_source=fp32_src)
+        else:
             # BF16 products per real product: three for hi*hi + hi*lo + lo*hi,
             # one for plain BF16 (coupling and Gram of the mixed mode)
-            terms = 1.0 if (path == "mixed" and stage in ("coupling", "gram")) else 3.0
+            terms = 1.0 if path == "mixed" else 3.0
             achieved = terms * per_launch / (ms_launch / 1e3) / 1e12
             peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
             out.update(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s",
                        peak_source=f"{info['peak_kind']} bf16 sustained")
-        else:
-            achieved = per_launch / (ms_launch / 1e3) / 1e12
-            # FP32 FFMA: 152 SMs x 128 lanes x 2 flop x max SM clock
-            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            out.update(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
-                       peak_source="FP32 FMA: 152 SM x 128 lanes x 2 flop x max SM clock")
     else:
-        key = {"ms_row": "ms_row_bytes", "ms_col": "ms_col_bytes", "gather": "gather_bytes"}.get(stage)
-        if key in ("ms_row_bytes", "ms_col_bytes"):
-            B, n_det, bp1, bp2 = geo_sizes
-            per_launch = alg[key] * (bp1 + bp2) / 2.0
-        else:
-            per_launch = alg.get(key, 0.0) / max(n / res["steps"], 1)
+        B, n_det, bp1, bp2 = geo_sizes
+        if stage in ("ms_row", "ms_col"):
+            # one read + one write of each parent column per pass (the mean
+            # of the S1 and S2 launches, which carry bp1 and bp2 columns)
+            per_launch = alg[stage + "_bytes"] * (bp1 + bp2) / 2.0
+        elif stage == "gather":
+            per_launch = alg["gather_bytes"] / (n / steps)
+        else:   # reduce: every partial read once
+            per_launch = 4.0 * info["n_sites"] * info["P"] / (n / steps)
         achieved = per_launch / (ms_launch / 1e3) / 1e9
         out.update(bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
                    peak_source=f"{info['peak_kind']} copy")
     out["frac"] = out["achieved"] / out["peak"]
-    out["traffic"] = None
+    out["traffic"] = ncu_traffic(path, stage)
     return out
+
+
+def roofline(cfg, path, res, info, geo_sizes):
+    """Roofline of the step's dominant kernel, from CUDA events recorded
+    around each of its launches inside the timed region."""
+    stage, ms, n = res["dominant"]
+    return stage_roofline(cfg, path, stage, ms, n, res["steps"], info, geo_sizes)
+
+
+def stage_rooflines(cfg, path, res, info, geo_sizes):
+    """Every stage's fraction of its roofline, from the profiled step."""
+    return {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
+                for kk, vv in stage_roofline(cfg, path, k, v[0], v[1], 1, info, geo_sizes).items()
+                if kk in ("bound", "achieved", "peak", "unit", "frac")}
+            for k, v in res["profile"].items() if v[1] > 0}
 
 
 # ---------------------------------------------------------------------------
@@ -496,7 +531,8 @@ def main():
         r["steps"] = args.steps
         paths_out[p] = {"evals_per_s": r["evals_per_s"], "ms_per_step": r["ms_per_step"],
                         "stage_ms_per_step": {k: v[0] for k, v in r["profile"].items()},
-                        "roofline": roofline(cfg, p, r, info, geo_sizes)}
+                        "roofline": roofline(cfg, p, r, info, geo_sizes),
+                        "stage_roofline": stage_rooflines(cfg, p, r, info, geo_sizes)}
     line["paths"] = paths_out
     if "fp32" in ok and len(ok) > 1:
         b = results["fp32"]["map"]
