@@ -37,6 +37,8 @@ struct bip_ctx {
     DevBuf kb_d, lat_d;                 // beam lattice of the difference transform
     int Ky = 0, Kx = 0;
     int grp1_n = 0, grp2_n = 0;
+    DevBuf wtc, xtc;                    // tensor-core reconstruction: W hi/lo, X planes
+    bool recon_tc = false;              // both parent sets fit its K = 64
 
     // sites of the current builds
     std::vector<SiteDev> sites;
@@ -159,6 +161,20 @@ bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1))
 int signed_bin(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// float -> bfloat16 bits, round to nearest even (finite inputs), and back
+uint16_t bf16_bits(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float bf16_value(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float x;
+    std::memcpy(&x, &u, 4);
+    return x;
+}
 
 // Twiddles of the register FFT of length n (n a power of two, 64..1024),
 // pass by pass: pass p = 1 .. npass-1 combines sub-transforms of length
@@ -293,6 +309,24 @@ bip_status make_tables(bip_ctx* c, cudaStream_t s) {
     CUDA_TRY(c, upload(c->grp2_w, w2, s));
     CUDA_TRY(c, upload(c->ytab, yt, s));
     CUDA_TRY(c, upload(c->xtab, xt, s));
+    // NNW weights as dense hi + lo bf16 rows [side][plane][rows_pad][64 parents]
+    // for the tensor-core reconstruction (side 0: detector beams, 1: aperture)
+    c->recon_tc = geo.Bp1 <= 64 && geo.Bp2 <= 64;
+    if (c->recon_tc) {
+        std::vector<uint16_t> wt((size_t)(2 * c->Dpad + 2 * c->Bpad) * 64, 0);
+        auto fill = [&](const std::vector<double>& w, int n, int bp, int row0, int rows_pad) {
+            for (int t = 0; t < n; ++t)
+                for (int p = 0; p < bp; ++p) {
+                    const float x = (float)w[(size_t)t * bp + p];
+                    const uint16_t hi = bf16_bits(x);
+                    wt[(size_t)(row0 + t) * 64 + p] = hi;
+                    wt[(size_t)(row0 + rows_pad + t) * 64 + p] = bf16_bits(x - bf16_value(hi));
+                }
+        };
+        fill(geo.w2, geo.n_det, geo.Bp2, 0, c->Dpad);
+        fill(geo.w1, geo.B, geo.Bp1, 2 * c->Dpad, c->Bpad);
+        CUDA_TRY(c, upload(c->wtc, wt, s));
+    }
     CUDA_TRY(c, ensure(c->errflag, 64, true, s));
     c->tables = true;
     return BIP_OK;
@@ -483,7 +517,7 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->xtab, &c->sites_d,
                      &c->plane_ids_d, &c->seq_ids_d, &c->row_off_d, &c->row_ent_d, &c->stash1, &c->stash2, &c->cols, &c->scans_d,
                      &c->gdiff, &c->kb_d, &c->lat_d, &c->work_d, &c->partial, &c->opA32, &c->opB32, &c->mt32, &c->q32, &c->opA16,
-                     &c->opB16, &c->mt16, &c->q16, &c->errflag, &c->rsum};
+                     &c->opB16, &c->mt16, &c->q16, &c->errflag, &c->rsum, &c->wtc, &c->xtc};
     for (DevBuf* b : all) release(*b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
@@ -645,6 +679,50 @@ GatherArgs gather_args(const bip_ctx* c, int side, const int32_t* ids, int n) {
     return a;
 }
 
+// Tensor-core reconstruction of one batch (mixed path): X planes from the
+// stashes, then W X with the epilogue writing both coupling operands.
+bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H, void* opA, void* opB,
+                          cudaStream_t s) {
+    const bip_config& g = c->cfg;
+    const BipGeometry& geo = c->geo;
+    const int K = g.win * g.win, Dpad = c->Dpad, Bpad = c->Bpad, nch = c->nch_max;
+    CUDA_TRY(c, ensure(c->xtc, (size_t)2 * nb * 3 * K * 64 * sizeof(uint16_t), false, s));
+    XprepArgs x{};
+    x.n_sites = nb;
+    x.site_ids = ids;
+    x.K = K;
+    x.X = (uint16_t*)c->xtc.p;
+    x.side[0] = XprepSide{(const float2*)c->stash2.p, geo.Bp2, 0};
+    x.side[1] = XprepSide{(const float2*)c->stash1.p, geo.Bp1, 3 * nb};
+    TIMED(c, BIP_STAGE_GATHER, s, bip_xprep(x, s));
+    ReconArgs r{};
+    r.n_sites = nb;
+    r.site_ids = ids;
+    r.sites = (const SiteDev*)c->sites_d.p;
+    r.K = K; r.win = g.win; r.ny = g.ny; r.nx = g.nx;
+    r.chunk_px = std::min(K, 1024);
+    r.chunks = K / r.chunk_px;
+    r.magnitude = g.recon == BIP_RECON_MAGNITUDE;
+    r.ey = (const float2*)c->ey.p;
+    r.ex = (const float2*)c->ex.p;
+    r.ytab = (const float2*)c->ytab.p;
+    r.xtab = (const float2*)c->xtab.p;
+    r.H = (const float2*)H;
+    r.W = (const uint16_t*)c->wtc.p;
+    r.w_rows = 2 * Dpad + 2 * Bpad;
+    r.Xb = (const uint16_t*)c->xtc.p;
+    r.x_rows = (int64_t)2 * nb * 3 * K;
+    r.out[0] = (uint16_t*)opA;
+    r.out[1] = (uint16_t*)opB;
+    r.side[0] = ReconSide{geo.n_det, Dpad, Dpad / 128, 0, -1, (const int2*)c->hdet.p, 0, 0,
+                          (int64_t)2 * Dpad * K, (int64_t)Dpad * K};
+    r.side[1] = ReconSide{geo.B, Bpad, Bpad / 128, nch, +1, (const int2*)c->hbeam.p, 2 * Dpad, 3 * nb,
+                          (int64_t)2 * nch * Bpad * K, (int64_t)nch * Bpad * K};
+    r.err = (int*)c->errflag.p;
+    TIMED(c, BIP_STAGE_GATHER, s, bip_recon_tc(r, s));
+    return BIP_OK;
+}
+
 bip_status check_map_args(bip_ctx* c, const void* H, const double* scans, int32_t P, const void* out) {
     if (!c) return BIP_ERR_INVALID_ARG;
     if (!c->s1 || !c->s2 || c->sig1 != c->sig2)
@@ -769,8 +847,13 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             g1.out_c64 = (float2*)c->opB32.p;
             g1.site_stride = (int64_t)perB;
         }
-        TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g2, s));
-        TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g1, s));
+        if (c->prec == BIP_PREC_MIXED && c->recon_tc) {
+            bip_status st = recon_tc_batch(c, ids, nb, H, c->opA16.p, c->opB16.p, s);
+            if (st != BIP_OK) return st;
+        } else {
+            TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g2, s));
+            TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g1, s));
+        }
         if (tc) {
             // coupling M = S2^T diag(H) S1, written transposed (bf16 planes)
             TcArgs A{};
@@ -997,11 +1080,16 @@ bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_ou
         g2.out_c64 = (float2*)opA.p; g2.site_stride = (int64_t)perA;
         g1.out_c64 = (float2*)opB.p; g1.site_stride = (int64_t)perB;
     }
-    TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g2, s));
-    TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g1, s));
+    if (tc) CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
+    if (c->prec == BIP_PREC_MIXED && c->recon_tc) {
+        bip_status st = recon_tc_batch(c, ids, 1, H, opA.p, opB.p, s);
+        if (st != BIP_OK) return st;
+    } else {
+        TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g2, s));
+        TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g1, s));
+    }
     float2* tmp = (float2*)c->partial.p;      // [Dpad][nch * Bpad] complex64
     if (tc) {
-        CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
         TcArgs A{};
         A.epi = TC_EPI_C32;
         A.N = (ldc % 256 == 0) ? 256 : 128;

@@ -119,6 +119,55 @@ struct GatherArgs {
 };
 cudaError_t bip_gather(const GatherArgs& a, cudaStream_t s);
 
+// recon_tc.cu : window reconstruction on the tensor cores (mixed path).
+// X [site-plane rows][K px][64 parents] bf16: row (x_site0 + 3 bs + plane) K
+// + px, planes re, im, magnitude of the de-tilted stash.
+struct XprepSide {
+    const float2* stash;            // [n_sites_total][Bp][K]
+    int Bp;                         // parents (<= 64)
+    int x_site0;                    // first site-plane row block of this side
+};
+struct XprepArgs {
+    int n_sites;                    // sites in this batch
+    const int32_t* site_ids;        // [n_sites]
+    int K;                          // window pixels
+    uint16_t* X;
+    XprepSide side[2];              // 0: S2 (detector), 1: S1 (aperture)
+};
+cudaError_t bip_xprep(const XprepArgs& a, cudaStream_t s);
+
+struct ReconSide {
+    int n_targets, rows_pad, mt_tiles;   // rows_pad = 128 mt_tiles
+    int nch;                        // 0: no channel product (S2 side)
+    int tilt_sign;                  // +1 (S1) or -1 (S2)
+    const int2* h_t;                // [n_targets] target beams
+    int w_row0;                     // first row of this side's W planes (hi, lo)
+    int x_site0;                    // as in XprepSide
+    int64_t site_stride;            // output elements per site
+    int64_t plane_stride;           // output elements per plane (re, im)
+};
+struct ReconArgs {
+    int n_sites;
+    const int32_t* site_ids;
+    const SiteDev* sites;
+    int K, win, ny, nx;
+    int chunk_px, chunks;           // pixels per work unit, units per target tile
+    int magnitude;
+    const float2* ey;               // [ny] exp(+2 pi i m / ny)
+    const float2* ex;               // [nx]
+    const float2* ytab;             // [ny][win]
+    const float2* xtab;             // [nx][win]
+    const float2* H;                // [sum nch][K], 16-byte aligned
+    const uint16_t* W;              // [w_rows][64] bf16: per side hi then lo planes
+    int w_rows;
+    const uint16_t* Xb;             // X of XprepArgs
+    int64_t x_rows;
+    uint16_t* out[2];               // coupling operands (2 bf16 planes each)
+    ReconSide side[2];
+    int* err;                       // set to 1 on a device timeout
+};
+cudaError_t bip_recon_tc(const ReconArgs& a, cudaStream_t s);
+
 // gemm_simt.cu : FP32 complex GEMMs, C[m][n] = sum_k op(A[m][k]) B[n][k]
 struct CGemmArgs {
     int M, N, K;                    // complex sizes (K multiple of 16)

@@ -22,124 +22,12 @@
 // Every wait is bounded (a few seconds of %globaltimer); on a timeout the
 // kernel sets *err, stops issuing work, drains what it issued and frees
 // TMEM before returning.
-#include <cuda.h>
-
-#include "bip_internal.h"
+#include "tc_common.cuh"
 
 namespace {
 
 constexpr int kThreads = 192;
-constexpr uint64_t kTimeoutNs = 4000000000ull;   // 4 s per wait
-constexpr uint32_t kTmemCols = 512;
 constexpr int kATile = 128 * 64;                 // one plane: 128 rows x 32 bf16
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t gtimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// ---- mbarrier ---------------------------------------------------------------
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait; false on timeout or when another role aborted
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
-    if (mbar_try(b, parity)) return true;
-    const uint64_t t0 = gtimer();
-    for (uint32_t n = 1;; ++n) {
-        if (mbar_try(b, parity)) return true;
-        if ((n & 255u) == 0) {
-            if (*abort_flag) return false;
-            if (gtimer() - t0 > kTimeoutNs) return false;
-        }
-    }
-}
-
-// ---- TMA ----------------------------------------------------------------------
-__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-            "r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// ---- tcgen05 ----------------------------------------------------------------------
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// K-major operand tile, rows of 64 bytes (32 bf16), 64-byte swizzle:
-// 8-row groups are 512 bytes apart (stride byte offset); the leading
-// offset is unused for swizzled K-major tiles.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;              // leading byte offset (unused)
-    d |= (uint64_t)(512 >> 4) << 32;     // stride byte offset
-    d |= (uint64_t)1 << 46;              // descriptor version
-    d |= (uint64_t)4 << 61;              // 64-byte swizzle
-    return d;
-}
-// kind::f16 instruction descriptor: BF16 x BF16 -> F32, both K-major
-__host__ __device__ constexpr uint32_t idesc(int M, int N, bool negA) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(id), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ uint16_t bf16_rn(float x) {
-    uint32_t u = __float_as_uint(x);
-    u += 0x7fffu + ((u >> 16) & 1u);
-    return (uint16_t)(u >> 16);
-}
-__device__ __forceinline__ float bf16_f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
-
-__device__ __forceinline__ void named_sync(int id, int n) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
 
 // Work units: (site in batch, M tile, N tile).
 struct Unit {
@@ -423,40 +311,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// ---- host side -----------------------------------------------------------------
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    }
-    return fn;
-}
-
-cudaError_t make_map(CUtensorMap* m, const TcOperand& op, int box_rows) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return cudaErrorNotSupported;
-    if (op.k % 32 || op.rows <= 0 || op.rows > 0x7fffffff) return cudaErrorInvalidValue;
-    if (((uintptr_t)op.base) % 16) return cudaErrorInvalidValue;
-    const cuuint64_t dims[2] = {(cuuint64_t)op.k, (cuuint64_t)op.rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)op.k * 2};
-    const cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
-    const cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(op.base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 template <int N, int EPI, int NPL>
 cudaError_t launch(const TcArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid, cudaStream_t s) {
     constexpr size_t smem = TcShape<N, NPL>::SMEM;
@@ -476,17 +330,6 @@ cudaError_t launch_n(const TcArgs& a, const CUtensorMap& ma, const CUtensorMap& 
     return a.N == 256 ? launch<256, EPI, NPL>(a, ma, mb, grid, s) : launch<128, EPI, NPL>(a, ma, mb, grid, s);
 }
 
-int num_sms() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 148;
-    }
-    return n;
-}
-
 }  // namespace
 
 cudaError_t bip_tc_gemm(const TcArgs& a, cudaStream_t s) {
@@ -502,9 +345,9 @@ cudaError_t bip_tc_gemm(const TcArgs& a, cudaStream_t s) {
             return cudaErrorInvalidValue;
     }
     CUtensorMap ma, mb;
-    cudaError_t e = make_map(&ma, a.A, 128);
+    cudaError_t e = make_map_2d(&ma, a.A.base, a.A.rows, a.A.k, 128);
     if (e != cudaSuccess) return e;
-    e = make_map(&mb, a.B, a.N);
+    e = make_map_2d(&mb, a.B.base, a.B.rows, a.B.k, a.N);
     if (e != cudaSuccess) return e;
     const int units = a.n_sites * a.mt_per * a.nt_per;
     const int grid = units < num_sms() ? units : num_sms();

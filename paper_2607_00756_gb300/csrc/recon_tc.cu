@@ -1,0 +1,502 @@
+// Window reconstruction on the tensor cores (mixed path): Eq. window-recon
+// with Eq. magpreserve, the re-tilt and diag(H_n), written as the BF16
+// operands of the coupling contraction.
+//
+// For the targets t of one side (detector beams for S2, aperture beams for
+// S1) and the window pixels r of one site, the three sums
+//   U_re(t, r) = sum_p w_tp Re S_p(r),  U_im(t, r) = sum_p w_tp Im S_p(r),
+//   A(t, r)    = sum_p w_tp |S_p(r)|
+// are one product W X with W [targets x 64 parents] and X [64 parents x
+// pixels] per plane (re, im, magnitude), K = the parents (zero-padded to 64).
+// W is exact to FP32 as hi + lo BF16 (two products per plane); X is BF16 --
+// the same rounding the mixed path applies to the operands it produces.
+//
+//   xprep_kernel    stash [Bp][K] complex64 -> X [3 planes][K px][64] bf16
+//                   (transposed so the parents are contiguous: K-major B)
+//   recon_tc_kernel persistent, one CTA per SM, 576 threads:
+//     warp 0     TMA producer: the unit's W tile (128 targets x 64 parents,
+//                hi and lo) once, then X tiles (64 pixels x 64 parents, three
+//                planes) through a 4-stage ring
+//     warp 1     TMEM allocator and MMA issuer: per 64-pixel tile, 24 MMAs
+//                (M=128, N=64, K=16) into three accumulators, two TMEM
+//                buffers so the epilogue of one tile overlaps the next
+//     warps 2-17 epilogue: thread = target row (TMEM lane), 16 pixels per
+//                warp and tile; magnitude preservation, re-tilt stepped
+//                along the window row in four independent chains, H_n
+//                (staged per tile in shared memory) products, 16 bf16
+//                stored per thread as one 32-byte sector
+// Work unit: (side, site in batch, 128-target tile, chunk of up to 1024
+// pixels).  Every wait is bounded; on a timeout the kernel sets *err, stops,
+// drains the copies and MMAs it issued and frees TMEM.
+#include <cuda_bf16.h>
+
+#include "fft_smem.cuh"
+#include "tc_common.cuh"
+
+namespace {
+
+constexpr int kEpiWarps = 16;                    // 4 per TMEM lane quadrant
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kN = 64;                           // pixels per MMA tile
+constexpr int kChunk = 1024;                     // pixels per work unit (at most)
+constexpr int kStages = 4;
+constexpr int kAPlane = 128 * 64;                // bytes: 128 rows x 32 bf16 (one K block)
+constexpr int kABuf = 2 * 2 * kAPlane;           // hi, lo x two K blocks
+constexpr int kBPlane = kN * 64;                 // bytes: 64 rows x 32 bf16
+constexpr int kBStage = 3 * 2 * kBPlane;         // re, im, mag x two K blocks
+constexpr int kAccCols = 3 * kN;                 // TMEM columns per accumulator set
+constexpr int kHBuf = 9 * 16 * 8;                // H_n of one warp's 16 pixels, up to 9 channels
+constexpr size_t kSmem = 1024 + 2 * (size_t)kABuf + (size_t)kStages * kBStage + (size_t)kEpiWarps * kHBuf + 256;
+
+struct Unit {
+    int side, bs, mt, pc;
+};
+
+__device__ __forceinline__ bool unit_of(const ReconArgs& a, int idx, Unit& u) {
+    int per0 = a.n_sites * a.side[0].mt_tiles * a.chunks;
+    int per1 = a.n_sites * a.side[1].mt_tiles * a.chunks;
+    if (idx >= per0 + per1) return false;
+    u.side = idx < per0 ? 0 : 1;
+    if (u.side) idx -= per0;
+    const int per_site = a.side[u.side].mt_tiles * a.chunks;
+    u.bs = idx / per_site;
+    const int r = idx % per_site;
+    u.mt = r / a.chunks;
+    u.pc = r % a.chunks;
+    return true;
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// 32-byte store (one full sector) of eight 32-bit words; p 32-byte aligned
+__device__ __forceinline__ void st_v8(void* p, const uint32_t (&v)[8]) {
+    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]),
+                 "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    recon_tc_kernel(const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapX,
+                    const ReconArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* abuf = smem;                                   // [2][kABuf]
+    uint8_t* bbuf = smem + 2 * kABuf;                       // [kStages][kBStage]
+    float2* hsm = (float2*)(bbuf + kStages * kBStage);     // [kEpiWarps][9][16] H_n per warp
+    uint64_t* full = (uint64_t*)((uint8_t*)hsm + kEpiWarps * kHBuf);
+    uint64_t* empty = full + kStages;
+    uint64_t* a_full = empty + kStages;
+    uint64_t* a_empty = a_full + 2;
+    uint64_t* acc_full = a_empty + 2;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* drain = acc_empty + 2;
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    volatile int* ep_ok = abort_flag + 1;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&a_full[i], 1);
+            mbar_init(&a_empty[i], 1);
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], kEpiWarps);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+    const int tiles = a.chunk_px / kN;                      // MMA tiles per unit
+
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicExch(a.err, 1);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            int s = 0;
+            uint32_t ph = 0;
+            int issued = 0;                    // X stages issued
+            int a_last[2] = {-1, -1};          // last unit whose W went to each buffer
+            bool ok = true;
+            Unit u;
+            for (int i = 0; ok && unit_of(a, blockIdx.x + i * gridDim.x, u); ++i) {
+                const ReconSide& sd = a.side[u.side];
+                const int ab = i & 1;
+                if (!mbar_wait(&a_empty[ab], ((i >> 1) & 1) ^ 1, abort_flag)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                uint8_t* at = abuf + ab * kABuf;
+                mbar_expect_tx(&a_full[ab], kABuf);
+#pragma unroll
+                for (int pl = 0; pl < 2; ++pl)
+#pragma unroll
+                    for (int kb = 0; kb < 2; ++kb)
+                        tma_2d(at + (pl * 2 + kb) * kAPlane, &mapW, kb * 32,
+                               sd.w_row0 + pl * sd.rows_pad + u.mt * 128, &a_full[ab]);
+                a_last[ab] = i;
+                const int xrow0 = (sd.x_site0 + u.bs * 3) * a.K + u.pc * a.chunk_px;
+                for (int t = 0; t < tiles; ++t) {
+                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* st = bbuf + s * kBStage;
+                    mbar_expect_tx(&full[s], kBStage);
+#pragma unroll
+                    for (int pl = 0; pl < 3; ++pl)
+#pragma unroll
+                        for (int kb = 0; kb < 2; ++kb)
+                            tma_2d(st + (pl * 2 + kb) * kBPlane, &mapX, kb * 32, xrow0 + pl * a.K + t * kN, &full[s]);
+                    ++issued;
+                    if (++s == kStages) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+            }
+            if (!ok) {
+                // let the copies in flight land before the CTA exits
+                const uint64_t t0 = gtimer();
+                for (int k = 0; k < kStages && k < issued; ++k) {
+                    s = (s + kStages - 1) % kStages;
+                    if (s == kStages - 1) ph ^= 1;
+                    while (!mbar_try(&full[s], ph) && gtimer() - t0 < kTimeoutNs) {
+                    }
+                }
+                for (int ab = 0; ab < 2; ++ab)
+                    if (a_last[ab] >= 0)
+                        while (!mbar_try(&a_full[ab], (a_last[ab] >> 1) & 1) && gtimer() - t0 < kTimeoutNs) {
+                        }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            const uint32_t id = idesc(128, kN, false);
+            int s = 0, acc = 0;
+            uint32_t ph = 0, aph = 0;
+            bool any = false, ok = true;
+            Unit u;
+            for (int i = 0; ok && unit_of(a, blockIdx.x + i * gridDim.x, u); ++i) {
+                const int ab = i & 1;
+                if (!mbar_wait(&a_full[ab], (i >> 1) & 1, abort_flag)) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t abase = smem_u32(abuf + ab * kABuf);
+                for (int t = 0; t < tiles; ++t) {
+                    if (!mbar_wait(&acc_empty[acc], aph ^ 1, abort_flag) || !mbar_wait(&full[s], ph, abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t bbase = smem_u32(bbuf + s * kBStage);
+                    const uint32_t d0 = tbase + (uint32_t)(acc * kAccCols);
+#pragma unroll
+                    for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint64_t whi = sdesc(abase + (0 * 2 + kb) * kAPlane + kk * 32);
+                            const uint64_t wlo = sdesc(abase + (1 * 2 + kb) * kAPlane + kk * 32);
+                            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+#pragma unroll
+                            for (int pl = 0; pl < 3; ++pl) {
+                                const uint64_t xd = sdesc(bbase + (pl * 2 + kb) * kBPlane + kk * 32);
+                                mma(d0 + pl * kN, whi, xd, id, first);
+                                mma(d0 + pl * kN, wlo, xd, id, 1);
+                            }
+                        }
+                    any = true;
+                    mma_commit(&empty[s]);
+                    mma_commit(&acc_full[acc]);
+                    if (++s == kStages) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                    if (++acc == 2) {
+                        acc = 0;
+                        aph ^= 1;
+                    }
+                }
+                mma_commit(&a_empty[ab]);
+            }
+            if (any) {
+                mma_commit(drain);
+                const uint64_t t0 = gtimer();
+                while (!mbar_try(drain, 0) && gtimer() - t0 < kTimeoutNs) {
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 2 .. 2 + kEpiWarps - 1; TMEM lane
+        // quadrant warp % 4, 16-pixel quarter (warp - 2) / 4 of each tile.
+        // Warps run independently: each waits on the accumulator barrier
+        // itself and stages its own H_n.
+        const int q = warp & 3;
+        const int quarter = (warp - 2) >> 2;
+        const int c0 = quarter * 16;                          // first column of this warp
+        float2* hw = hsm + (warp - 2) * 9 * 16;               // this warp's H_n [9][16]
+        int acc = 0;
+        uint32_t aph = 0;
+        Unit u;
+        bool ok = true;
+        for (int i = 0; ok && unit_of(a, blockIdx.x + i * gridDim.x, u); ++i) {
+            const ReconSide& sd = a.side[u.side];
+            const int t = u.mt * 128 + q * 32 + lane;       // target of this thread
+            const bool valid = t < sd.n_targets;
+            const int site = a.site_ids[u.bs];
+            const SiteDev st = a.sites[site];
+            const int nrep = sd.nch > 0 ? sd.nch : 1;
+            const int nuse = min(sd.nch, st.nch);
+            // re-tilt exp(sign 2 pi i (h_y (oy + u)/ny + h_x (ox + v)/nx)) at the
+            // first pixel of this warp's columns, carried from tile to tile:
+            // +64 pixels is X^64 and, per window-row wrap, Z = Y X^-win, with
+            // X = exp(sign 2 pi i h_x/nx), Y = exp(sign 2 pi i h_y/ny)
+            float2 F = make_float2(1.f, 0.f), sx1 = F, sx4 = F, sx8 = F, X64 = F, Z = F;
+            int wv = 0;
+            if (valid) {
+                const int2 h = __ldg(&sd.h_t[t]);
+                const int px0 = u.pc * a.chunk_px + c0;
+                const int wu = px0 / a.win;
+                wv = px0 - wu * a.win;
+                const float2 base =
+                    c_mul(__ldg(&a.ey[(h.x * st.oy) & (a.ny - 1)]), __ldg(&a.ex[(h.y * st.ox) & (a.nx - 1)]));
+                F = c_mul(base, c_mul(__ldg(&a.ytab[(size_t)(h.x & (a.ny - 1)) * a.win + wu]),
+                                      __ldg(&a.xtab[(size_t)(h.y & (a.nx - 1)) * a.win + wv])));
+                sx1 = __ldg(&a.ex[h.y & (a.nx - 1)]);
+                sx4 = __ldg(&a.ex[(4 * h.y) & (a.nx - 1)]);
+                sx8 = __ldg(&a.ex[(8 * h.y) & (a.nx - 1)]);
+                X64 = __ldg(&a.ex[(64 * h.y) & (a.nx - 1)]);
+                Z = c_mul(__ldg(&a.ey[h.x & (a.ny - 1)]), __ldg(&a.ex[(-a.win * h.y) & (a.nx - 1)]));
+                if (sd.tilt_sign < 0) {
+                    F.y = -F.y;
+                    sx1.y = -sx1.y;
+                    sx4.y = -sx4.y;
+                    sx8.y = -sx8.y;
+                    X64.y = -X64.y;
+                    Z.y = -Z.y;
+                }
+            }
+            uint16_t* out = a.out[u.side] + (size_t)u.bs * sd.site_stride + (size_t)t * a.K;
+            const size_t ch_stride = (size_t)sd.rows_pad * a.K;
+            const float2* Hs = a.H + (size_t)st.ch_off * a.K;
+            const int nh = sd.nch * 16;                       // H_n values of a warp per tile
+            for (int tt = 0; tt < tiles; ++tt) {
+                const int px = u.pc * a.chunk_px + tt * kN + c0;     // this warp's 16 pixels
+                // this tile's H_n, in flight during the waits below
+                float2 hv[5];
+#pragma unroll
+                for (int r = 0; r < 5; ++r) {
+                    const int k = lane + 32 * r;
+                    hv[r] = make_float2(0.f, 0.f);
+                    if (k < nh && k / 16 < nuse) hv[r] = __ldg(&Hs[(size_t)(k / 16) * a.K + px + (k % 16)]);
+                }
+                int okw = 1;
+                if (lane == 0) {
+                    okw = mbar_wait(&acc_full[acc], aph, abort_flag) ? 1 : 0;
+                    if (!okw) fail();
+                }
+                okw = __shfl_sync(0xffffffffu, okw, 0);
+                if (!okw) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols);
+                float vr[16], vi[16], vm[16];
+                tmem_ld16(tr + c0, vr);
+                tmem_ld16(tr + kN + c0, vi);
+                tmem_ld16(tr + 2 * kN + c0, vm);
+#pragma unroll
+                for (int r = 0; r < 5; ++r) {
+                    const int k = lane + 32 * r;
+                    if (k < nh) hw[k] = hv[r];
+                }
+                tmem_ld_wait();
+                // the accumulator buffer is free for the next MMA once read
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[acc]);
+                if (++acc == 2) {
+                    acc = 0;
+                    aph ^= 1;
+                }
+                if (valid) {
+                    // re-tilt in four independent chains (pixels j, j + 4, j + 8, j + 12)
+                    float2 tc[4];
+                    tc[0] = F;
+                    tc[1] = c_mul(F, sx4);
+                    tc[2] = c_mul(F, sx8);
+                    tc[3] = c_mul(tc[1], sx8);
+                    float2 S[16];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int k = 4 * c + j;
+                            float2 v;
+                            if (a.magnitude) {
+                                const float m2 = vr[k] * vr[k] + vi[k] * vi[k];
+                                const float sc = m2 > 0.f ? vm[k] * rsqrtf(m2) : 0.f;
+                                v = m2 > 0.f ? make_float2(vr[k] * sc, vi[k] * sc) : make_float2(vm[k], 0.f);
+                            } else {
+                                v = make_float2(vr[k], vi[k]);
+                            }
+                            S[k] = c_mul(v, tc[c]);
+                            tc[c] = c_mul(tc[c], sx1);
+                        }
+                    }
+                    uint16_t* o = out + px;
+                    for (int n = 0; n < nrep; ++n) {
+                        uint32_t re[8], im[8];
+                        if (sd.nch > 0) {
+                            const float4* hp = reinterpret_cast<const float4*>(hw + n * 16);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const float4 hq = hp[j];
+                                const float2 o0 = c_mul(make_float2(hq.x, hq.y), S[2 * j]);
+                                const float2 o1 = c_mul(make_float2(hq.z, hq.w), S[2 * j + 1]);
+                                re[j] = pack2(o0.x, o1.x);
+                                im[j] = pack2(o0.y, o1.y);
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                re[j] = pack2(S[2 * j].x, S[2 * j + 1].x);
+                                im[j] = pack2(S[2 * j].y, S[2 * j + 1].y);
+                            }
+                        }
+                        st_v8(o, re);
+                        st_v8(o + sd.plane_stride, im);
+                        o += ch_stride;
+                    }
+                    // tilt at this warp's first pixel of the next tile
+                    F = c_mul(F, X64);
+                    wv += kN;
+                    while (wv >= a.win) {
+                        wv -= a.win;
+                        F = c_mul(F, Z);
+                    }
+                }
+                __syncwarp();                                  // hw reads done before the next tile's writes
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols));
+    }
+}
+
+// stash [Bp][K] complex64 of one site -> X planes [3][K][64] bf16 (re, im,
+// magnitude; parents past Bp zero).  Block: 64 pixels of one site and side.
+constexpr int kPrepThreads = 256;
+__global__ void __launch_bounds__(kPrepThreads) xprep_kernel(XprepArgs a) {
+    __shared__ float2 s[64][65];
+    const int side = blockIdx.z;
+    const XprepSide& sd = a.side[side];
+    const int bs = blockIdx.y;
+    const int site = a.site_ids[bs];
+    const int px0 = blockIdx.x * 64;
+    const float2* src = sd.stash + (size_t)site * sd.Bp * a.K + px0;
+    for (int i = threadIdx.x; i < 64 * 64; i += kPrepThreads) {
+        const int p = i >> 6, x = i & 63;
+        s[p][x] = p < sd.Bp ? src[(size_t)p * a.K + x] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    // thread: one pixel (lane) and eight consecutive parents, for one plane
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;   // 8 warps
+    uint16_t* dst = a.X + ((size_t)(sd.x_site0 + bs * 3) * a.K + px0) * 64;
+    for (int job = w; job < 2 * 3 * 8; job += 8) {
+        const int xh = job / 24, r = job % 24, pl = r / 8, p0 = (r % 8) * 8;
+        const int x = xh * 32 + lane;
+        uint32_t v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 e0 = s[p0 + 2 * k][x], e1 = s[p0 + 2 * k + 1][x];
+            float f0, f1;
+            if (pl == 0) {
+                f0 = e0.x; f1 = e1.x;
+            } else if (pl == 1) {
+                f0 = e0.y; f1 = e1.y;
+            } else {
+                f0 = sqrtf(e0.x * e0.x + e0.y * e0.y);
+                f1 = sqrtf(e1.x * e1.x + e1.y * e1.y);
+            }
+            v[k] = pack2(f0, f1);
+        }
+        *reinterpret_cast<uint4*>(dst + ((size_t)pl * a.K + x) * 64 + p0) = make_uint4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+}  // namespace
+
+cudaError_t bip_xprep(const XprepArgs& a, cudaStream_t s) {
+    if (a.K % 64 || a.n_sites < 1) return cudaErrorInvalidValue;
+    if (a.side[0].Bp > 64 || a.side[1].Bp > 64) return cudaErrorInvalidValue;
+    xprep_kernel<<<dim3(a.K / 64, a.n_sites, 2), kPrepThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t bip_recon_tc(const ReconArgs& a, cudaStream_t s) {
+    if (a.K % kN || a.chunk_px % kN || a.K % a.chunk_px || a.chunk_px > kChunk || a.win % 16) return cudaErrorInvalidValue;
+    if (a.n_sites < 1 || a.chunks != a.K / a.chunk_px) return cudaErrorInvalidValue;
+    for (int i = 0; i < 2; ++i) {
+        const ReconSide& sd = a.side[i];
+        if (sd.mt_tiles * 128 != sd.rows_pad || sd.n_targets > sd.rows_pad || sd.nch > 9) return cudaErrorInvalidValue;
+        if (sd.nch > 0 && ((uintptr_t)a.H & 15)) return cudaErrorMisalignedAddress;
+        if (sd.w_row0 + 2 * sd.rows_pad > a.w_rows) return cudaErrorInvalidValue;
+        if ((int64_t)(sd.x_site0 + 3 * a.n_sites) * a.K > a.x_rows) return cudaErrorInvalidValue;
+    }
+    CUtensorMap mw, mx;
+    cudaError_t e = make_map_2d(&mw, a.W, a.w_rows, 64, 128);
+    if (e != cudaSuccess) return e;
+    e = make_map_2d(&mx, a.Xb, a.x_rows, 64, kN);
+    if (e != cudaSuccess) return e;
+    static bool attr = false;
+    if (!attr) {
+        e = cudaFuncSetAttribute(recon_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int units = a.n_sites * (a.side[0].mt_tiles + a.side[1].mt_tiles) * a.chunks;
+    const int grid = units < num_sms() ? units : num_sms();
+    recon_tc_kernel<<<grid, kThreads, kSmem, s>>>(mw, mx, a);
+    return cudaGetLastError();
+}
