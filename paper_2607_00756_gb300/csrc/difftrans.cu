@@ -16,9 +16,10 @@
 // product by a binning of Q (B^2 terms) and ~(2K_y+1)(4K_x+1) terms per scan.
 //
 //   diff_bin  : warp per (site, Delta), lanes over b, fixed reduction tree
-//   diff_eval : thread per scan of a (site, scan tile) work item; the
-//               phases exp(2 pi i f Delta.rho/N) advance by one rotation
-//               per step of Delta from an FP64-reduced start angle.
+//   diff_eval : persistent; thread per scan of a (site, scan tile) work
+//               item; Horner's rule in exp(2 pi i f rho/N) along the
+//               lattice rows and over them, start angles reduced to [0, 1)
+//               turns in FP64.
 #include "bip_device.cuh"
 #include "bip_internal.h"
 #include "fft_smem.cuh"
@@ -77,51 +78,62 @@ __global__ void __launch_bounds__(kBinWarps * 32) diff_bin_kernel(DiffArgs a) {
     if (lane == 0) a.G[(size_t)bs * nd + di] = make_float2(gr, gi);
 }
 
-// exp(2 pi i * turns) with the angle reduced to [0, 1) turns in FP64
+// exp(2 pi i * turns): the angle is reduced to [0, 1) turns in FP64 (exact
+// for the integer part), the rest is FP32 sincospif
 __device__ __forceinline__ float2 turn(double t) {
-    t -= floor(t);
-    double s, c;
-    sincospi(2.0 * t, &s, &c);
-    return make_float2((float)c, (float)s);
+    const float r = (float)(t - floor(t));
+    float s, c;
+    sincospif(2.0f * r, &s, &c);
+    return make_float2(c, s);
 }
 
+// Persistent over the (site in batch, scan tile) work items, in a fixed
+// round-robin order.  Per scan rho the polynomial
+//   sum_{iy, j} G[iy][j] rx^(j - 2K_x) ry^(iy - 2K_y),
+//   rx = exp(2 pi i f_x rho_x / N_x), ry = exp(2 pi i f_y rho_y / N_y),
+// is evaluated by Horner's rule in rx along each row and in ry over the
+// rows (one complex multiply-add per term), then multiplied by the start
+// phase rx^(-2K_x) ry^(-2K_y).
 __global__ void __launch_bounds__(256) diff_eval_kernel(DiffArgs a) {
     extern __shared__ float2 gs[];
-    const int w = blockIdx.x;
-    const int bs = a.work[2 * w], tile = a.work[2 * w + 1];
     const int rows = 2 * a.Ky + 1, cols = 4 * a.Kx + 1;
     const int nd = rows * cols;
-    for (int i = threadIdx.x; i < nd; i += blockDim.x) gs[i] = a.G[(size_t)bs * nd + i];
-    __syncthreads();
-    const int site = a.site_ids[bs];
-    const SiteDev st = a.sites[site];
-    for (int n = tile * a.tile + threadIdx.x; n < min((tile + 1) * a.tile, a.P); n += blockDim.x) {
-        const double ry = a.scans[2 * n], rx = a.scans[2 * n + 1];
-        if (!in_crop(ry, rx, st.ty, st.tx, a.ny, a.nx, a.fy, a.fx)) {
-            a.partial[(size_t)site * a.P + n] = 0.f;
-            continue;
-        }
-        const double ty = (double)a.fy * ry / a.ny, tx = (double)a.fx * rx / a.nx;   // turns per lattice step
-        float2 ey = turn(-2.0 * a.Ky * ty);
-        const float2 ey_step = turn(ty);
-        const float2 ex0 = turn(-2.0 * a.Kx * tx);
-        const float2 ex_step = turn(tx);
-        float acc = 0.f;
-        for (int iy = 0; iy < rows; ++iy) {
-            const float2* g = gs + iy * cols;
-            float2 ex = ex0;
-            float sr = 0.f, si = 0.f;
-            const int last = iy == rows - 1 ? 2 * a.Kx + 1 : cols;   // Delta_y = 0: Delta_x <= 0 only
-            for (int ix = 0; ix < last; ++ix) {
-                const float2 gv = g[ix];
-                sr = fmaf(gv.x, ex.x, fmaf(-gv.y, ex.y, sr));
-                si = fmaf(gv.x, ex.y, fmaf(gv.y, ex.x, si));
-                ex = c_mul(ex, ex_step);
+    for (int w = blockIdx.x; w < a.n_work; w += gridDim.x) {
+        const int bs = a.work[2 * w], tile = a.work[2 * w + 1];
+        __syncthreads();                           // the previous item's reads of gs are done
+        for (int i = threadIdx.x; i < nd; i += blockDim.x) gs[i] = a.G[(size_t)bs * nd + i];
+        __syncthreads();
+        const int site = a.site_ids[bs];
+        const SiteDev st = a.sites[site];
+        const int n1 = min((tile + 1) * a.tile, a.P);
+        for (int n = tile * a.tile + threadIdx.x; n < n1; n += blockDim.x) {
+            const double ry = a.scans[2 * n], rx = a.scans[2 * n + 1];
+            if (!in_crop(ry, rx, st.ty, st.tx, a.ny, a.nx, a.fy, a.fx)) {
+                a.partial[(size_t)site * a.P + n] = 0.f;
+                continue;
             }
-            acc = fmaf(ey.x, sr, fmaf(-ey.y, si, acc));
-            ey = c_mul(ey, ey_step);
+            const double ty = (double)a.fy * ry / a.ny, tx = (double)a.fx * rx / a.nx;   // turns per lattice step
+            const float2 zy = turn(ty), zx = turn(tx);
+            float2 T = make_float2(0.f, 0.f);
+            for (int iy = rows - 1; iy >= 0; --iy) {
+                const float2* g = gs + iy * cols;
+                const int last = iy == rows - 1 ? 2 * a.Kx + 1 : cols;   // Delta_y = 0: Delta_x <= 0 only
+                float2 sr = g[last - 1];
+#pragma unroll 4
+                for (int j = last - 2; j >= 0; --j) {     // sr = sr zx + g[j]
+                    const float2 gv = g[j];
+                    const float xr = fmaf(sr.x, zx.x, fmaf(-sr.y, zx.y, gv.x));
+                    const float xi = fmaf(sr.x, zx.y, fmaf(sr.y, zx.x, gv.y));
+                    sr = make_float2(xr, xi);
+                }
+                // T = T zy + row sum
+                const float yr = fmaf(T.x, zy.x, fmaf(-T.y, zy.y, sr.x));
+                const float yi = fmaf(T.x, zy.y, fmaf(T.y, zy.x, sr.y));
+                T = make_float2(yr, yi);
+            }
+            const float2 e0 = turn(-2.0 * a.Kx * tx - 2.0 * a.Ky * ty);
+            a.partial[(size_t)site * a.P + n] = a.scale * fmaf(e0.x, T.x, -e0.y * T.y);
         }
-        a.partial[(size_t)site * a.P + n] = a.scale * acc;
     }
 }
 
@@ -154,6 +166,19 @@ cudaError_t bip_diff_eval(const DiffArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr = sm;
     }
-    diff_eval_kernel<<<a.n_work, 256, sm, s>>>(a);
+    // persistent grid: every resident block slot, at most one block per item
+    static int per_sm = 0, sms = 0;
+    static size_t sm_at = 0;
+    if (per_sm == 0 || sm_at != sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, diff_eval_kernel, 256, sm) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        sm_at = sm;
+    }
+    const int grid = a.n_work < per_sm * sms ? a.n_work : per_sm * sms;
+    diff_eval_kernel<<<grid, 256, sm, s>>>(a);
     return cudaGetLastError();
 }

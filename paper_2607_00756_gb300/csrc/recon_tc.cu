@@ -369,9 +369,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const int k = 4 * c + j;
                             float2 v;
                             if (a.magnitude) {
-                                const float m2 = vr[k] * vr[k] + vi[k] * vi[k];
-                                const float sc = m2 > 0.f ? vm[k] * rsqrtf(m2) : 0.f;
-                                v = m2 > 0.f ? make_float2(vr[k] * sc, vi[k] * sc) : make_float2(vm[k], 0.f);
+                                const float m2 = fmaf(vr[k], vr[k], vi[k] * vi[k]);
+                                const float sc = vm[k] * rsqrtf(fmaxf(m2, 1.17549435e-38f));
+                                v = make_float2(m2 > 0.f ? vr[k] * sc : vm[k], vi[k] * sc);
                             } else {
                                 v = make_float2(vr[k], vi[k]);
                             }
