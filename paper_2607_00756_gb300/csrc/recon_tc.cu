@@ -435,9 +435,17 @@ __global__ void __launch_bounds__(kPrepThreads) xprep_kernel(XprepArgs a) {
     const int site = a.site_ids[bs];
     const int px0 = blockIdx.x * 64;
     const float2* src = sd.stash + (size_t)site * sd.Bp * a.K + px0;
-    for (int i = threadIdx.x; i < 64 * 64; i += kPrepThreads) {
-        const int p = i >> 6, x = i & 63;
-        s[p][x] = p < sd.Bp ? src[(size_t)p * a.K + x] : make_float2(0.f, 0.f);
+    // 16 loads per thread in flight at once (parents p = i / 64, pixels i % 64)
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int i = threadIdx.x + r * kPrepThreads, p = i >> 6;
+        v[r] = p < sd.Bp ? __ldg(&src[(size_t)p * a.K + (i & 63)]) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int i = threadIdx.x + r * kPrepThreads;
+        s[i >> 6][i & 63] = v[r];
     }
     __syncthreads();
     // thread: one pixel (lane) and eight consecutive parents, for one plane
