@@ -13,7 +13,8 @@
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kRowPad = 128;        // operand rows padded to the MMA tile
+constexpr int kRowPad = 128;        // aperture-side operand rows: the MMA's 128-row tiles
+constexpr int kDetPad = 32;         // detector-side rows: the N of a tile (multiple of 16, K of the Gram a multiple of 32)
 constexpr int kScanTile = 256;      // scans per quadratic-form work item
 
 struct DevBuf {
@@ -200,6 +201,13 @@ std::vector<float2> fft_twiddles(int n) {
     return t;
 }
 
+// Column tile width for n detector rows: as few tiles of at most 256 as
+// possible, as even as the multiple-of-16 widths allow.
+int tile_width(int n) {
+    const int tiles = (n + 255) / 256;
+    return round_up((n + tiles - 1) / tiles, 16);
+}
+
 // Grouped sparse copy of a dense weight matrix [rows][cols]: rows
 // kGatherGroup g .. + kGatherGroup - 1 form group g, whose entries are the
 // columns (parents) any of its rows uses, with the rows' weights side by side.
@@ -313,7 +321,8 @@ bip_status make_tables(bip_ctx* c, cudaStream_t s) {
     // for the tensor-core reconstruction (side 0: detector beams, 1: aperture)
     c->recon_tc = geo.Bp1 <= 64 && geo.Bp2 <= 64;
     if (c->recon_tc) {
-        std::vector<uint16_t> wt((size_t)(2 * c->Dpad + 2 * c->Bpad) * 64, 0);
+        const int Dw = round_up(geo.n_det, kRowPad);
+        std::vector<uint16_t> wt((size_t)(2 * Dw + 2 * c->Bpad) * 64, 0);
         auto fill = [&](const std::vector<double>& w, int n, int bp, int row0, int rows_pad) {
             for (int t = 0; t < n; ++t)
                 for (int p = 0; p < bp; ++p) {
@@ -323,8 +332,8 @@ bip_status make_tables(bip_ctx* c, cudaStream_t s) {
                     wt[(size_t)(row0 + rows_pad + t) * 64 + p] = bf16_bits(x - bf16_value(hi));
                 }
         };
-        fill(geo.w2, geo.n_det, geo.Bp2, 0, c->Dpad);
-        fill(geo.w1, geo.B, geo.Bp1, 2 * c->Dpad, c->Bpad);
+        fill(geo.w2, geo.n_det, geo.Bp2, 0, Dw);
+        fill(geo.w1, geo.B, geo.Bp1, 2 * Dw, c->Bpad);
         CUDA_TRY(c, upload(c->wtc, wt, s));
     }
     CUDA_TRY(c, ensure(c->errflag, 64, true, s));
@@ -505,7 +514,7 @@ bip_status bip_create(const bip_config* cfg, bip_ctx** out) {
         return st;
     }
     c->Bpad = round_up(c->geo.B, kRowPad);
-    c->Dpad = round_up(c->geo.n_det, kRowPad);
+    c->Dpad = round_up(c->geo.n_det, kDetPad);
     *out = c;
     return BIP_OK;
 }
@@ -709,14 +718,15 @@ bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H,
     r.xtab = (const float2*)c->xtab.p;
     r.H = (const float2*)H;
     r.W = (const uint16_t*)c->wtc.p;
-    r.w_rows = 2 * Dpad + 2 * Bpad;
+    const int Dw = round_up(geo.n_det, kRowPad);
+    r.w_rows = 2 * Dw + 2 * Bpad;
     r.Xb = (const uint16_t*)c->xtc.p;
     r.x_rows = (int64_t)2 * nb * 3 * K;
     r.out[0] = (uint16_t*)opA;
     r.out[1] = (uint16_t*)opB;
-    r.side[0] = ReconSide{geo.n_det, Dpad, Dpad / 128, 0, -1, (const int2*)c->hdet.p, 0, 0,
+    r.side[0] = ReconSide{geo.n_det, Dpad, Dw, Dw / 128, 0, -1, (const int2*)c->hdet.p, 0, 0,
                           (int64_t)2 * Dpad * K, (int64_t)Dpad * K};
-    r.side[1] = ReconSide{geo.B, Bpad, Bpad / 128, nch, +1, (const int2*)c->hbeam.p, 2 * Dpad, 3 * nb,
+    r.side[1] = ReconSide{geo.B, Bpad, Bpad, Bpad / 128, nch, +1, (const int2*)c->hbeam.p, 2 * Dw, 3 * nb,
                           (int64_t)2 * nch * Bpad * K, (int64_t)nch * Bpad * K};
     r.err = (int*)c->errflag.p;
     TIMED(c, BIP_STAGE_GATHER, s, bip_recon_tc(r, s));
@@ -855,18 +865,21 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g1, s));
         }
         if (tc) {
-            // coupling M = S2^T diag(H) S1, written transposed (bf16 planes)
+            // coupling M = S2^T diag(H) S1 with the aperture side (rows (ch, b),
+            // 128-row tiles) as A and the detector side (columns d, 256-wide
+            // tiles and a narrower last one) as B; written as Mt[b][ch Dp + d]
             TcArgs A{};
-            A.epi = TC_EPI_MT;
-            A.N = (rowsB % 256 == 0) ? 256 : 128;
+            A.epi = TC_EPI_ROWS;
+            A.N = tile_width(Dpad);
             A.npl = npl;
             A.out_planes = npl;
-            A.A = TcOperand{c->opA16.p, (int64_t)SB * npl * (int64_t)rowsA, K, npl * (int64_t)rowsA, (int64_t)rowsA};
-            A.B = TcOperand{c->opB16.p, (int64_t)SB * npl * (int64_t)rowsB, K, npl * (int64_t)rowsB, (int64_t)rowsB};
+            A.A = TcOperand{c->opB16.p, (int64_t)SB * npl * (int64_t)rowsB, K, npl * (int64_t)rowsB, (int64_t)rowsB};
+            A.B = TcOperand{c->opA16.p, (int64_t)SB * npl * (int64_t)rowsA, K, npl * (int64_t)rowsA, (int64_t)rowsA};
             A.kb = K / 32;
             A.n_sites = nb;
-            A.mt_per = Dpad / 128;
-            A.nt_per = (int)(rowsB / A.N);
+            A.mt_per = (int)(rowsB / 128);
+            A.nt_per = (Dpad + A.N - 1) / A.N;
+            A.n_cols = Dpad;
             A.out16 = (uint16_t*)c->mt16.p;
             A.out_site = npl * (int64_t)perMt;
             A.out_plane = (int64_t)perMt;
@@ -886,6 +899,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             Gq.n_sites = nb;
             Gq.mt_per = Bpad / 128;
             Gq.nt_per = Bpad / Gq.N;
+            Gq.n_cols = Bpad;
             Gq.conjA = 1;
             Gq.tri = 1;
             Gq.out32 = (float2*)c->q32.p;
@@ -1090,19 +1104,23 @@ bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_ou
     }
     float2* tmp = (float2*)c->partial.p;      // [Dpad][nch * Bpad] complex64
     if (tc) {
+        // the map's orientation: aperture side (ch, b) as A, detector side as
+        // B; the C32 epilogue writes tmp[d][(ch, b)]
         TcArgs A{};
         A.epi = TC_EPI_C32;
-        A.N = (ldc % 256 == 0) ? 256 : 128;
+        A.N = tile_width(Dpad);
         A.npl = npl;
-        A.A = TcOperand{opA.p, npl * (int64_t)Dpad, K, npl * (int64_t)Dpad, Dpad};
-        A.B = TcOperand{opB.p, npl * (int64_t)ldc, K, npl * (int64_t)ldc, (int64_t)ldc};
+        A.A = TcOperand{opB.p, npl * (int64_t)ldc, K, npl * (int64_t)ldc, (int64_t)ldc};
+        A.B = TcOperand{opA.p, npl * (int64_t)Dpad, K, npl * (int64_t)Dpad, Dpad};
         A.kb = K / 32;
         A.n_sites = 1;
-        A.mt_per = Dpad / 128;
-        A.nt_per = (int)(ldc / A.N);
+        A.mt_per = (int)(ldc / 128);
+        A.nt_per = (Dpad + A.N - 1) / A.N;
+        A.n_cols = Dpad;
         A.out32 = tmp;
         A.out32_site = 0;
         A.out32_ld = (int64_t)ldc;
+        A.out32_trans = 1;
         A.err = (int*)c->errflag.p;
         TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(A, s));
     } else {

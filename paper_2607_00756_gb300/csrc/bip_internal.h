@@ -137,7 +137,10 @@ struct XprepArgs {
 cudaError_t bip_xprep(const XprepArgs& a, cudaStream_t s);
 
 struct ReconSide {
-    int n_targets, rows_pad, mt_tiles;   // rows_pad = 128 mt_tiles
+    int n_targets;
+    int rows_pad;                   // output rows per channel plane (>= n_targets)
+    int w_pad;                      // rows of each W plane, = 128 mt_tiles
+    int mt_tiles;
     int nch;                        // 0: no channel product (S2 side)
     int tilt_sign;                  // +1 (S1) or -1 (S2)
     const int2* h_t;                // [n_targets] target beams
@@ -219,30 +222,35 @@ cudaError_t bip_reduce_sites(const float* partial, int n_sites, int P, void* scr
 // Operands are bf16 planes, K contiguous -- four (re_hi, re_lo, im_hi,
 // im_lo) or two (re, im) -- seen by TMA as one 2-D tensor [rows][K]; row
 // (site, plane, r) is at site * site_rows + plane * plane_rows + r.
-enum TcEpilogue { TC_EPI_MT = 0, TC_EPI_C32 = 2 };
+enum TcEpilogue { TC_EPI_ROWS = 0, TC_EPI_C32 = 2 };
 struct TcOperand {
-    const void* base;               // bf16 planes
-    int64_t rows, k;                // tensor extent (k multiple of 32)
-    int64_t site_rows, plane_rows;  // row strides
+    const void* base;               // bf16 planes, 16-byte aligned
+    int64_t rows;                   // rows of the 2-D tensor
+    int k;                          // row length (multiple of 32)
+    int64_t site_rows, plane_rows;  // row offsets of a site and of a plane
 };
 struct TcArgs {
     int epi;                        // TcEpilogue
     int N;                          // 128 or 256 (tile columns)
     int npl;                        // operand planes: 4 (split BF16) or 2 (BF16: re, im)
-    int out_planes;                 // MT epilogue: planes written (4 or 2)
+    int out_planes;                 // ROWS epilogue: planes written (4 or 2)
     TcOperand A, B;                 // A tiles of 128 rows, B tiles of N rows
     int kb;                         // K blocks of 32
-    int n_sites, mt_per, nt_per;    // tiles per site (MT, Q, C32)
+    int n_sites, mt_per, nt_per;    // tiles per site
+    int n_cols;                     // B rows per site in use: the last tile has
+                                    // n_cols - (nt_per - 1) N columns (multiple of 16)
     int conjA;
     // Hermitian output: tiles entirely below the diagonal are skipped
     int tri;
-    // MT epilogue: bf16 planes out[site][plane][row][ld]
+    // ROWS epilogue: A row r = (ch, b) = (r / ep_B, r % ep_B), output column n
+    // -> out16[site][plane][b][ch * ep_Dp + n] (bf16 planes)
     uint16_t* out16;
     int64_t out_site, out_plane, out_ld;
-    int ep_B, ep_Dp;                // MT: column n = (n / ep_B, n % ep_B) -> Mt[b][ch*ep_Dp + m]
-    // C32 epilogue: complex64 out32[site][m][ld]
+    int ep_B, ep_Dp;
+    // C32 epilogue: complex64 out32[site][row][n] (or [n][row] when transposed)
     float2* out32;
     int64_t out32_site, out32_ld;
+    int out32_trans;
     int* err;                       // device flag: set when a wait gives up
 };
 cudaError_t bip_tc_gemm(const TcArgs& a, cudaStream_t s);

@@ -34,6 +34,7 @@ struct Unit {
     int bs, mt, nt, w;
     bool skip;    // tile below the diagonal of a Hermitian Gram matrix
     int kb0;      // first K block
+    int nc;       // columns of this tile: N, or fewer for the last one
 };
 
 template <int EPI>
@@ -54,6 +55,8 @@ struct UnitIter {
         u.w = 0;
         u.skip = p.tri && (u.nt + 1) * N_of() <= u.mt * 128;
         u.kb0 = 0;
+        const int left = p.n_cols - u.nt * N_of();
+        u.nc = left < N_of() ? left : N_of();
         return true;
     }
 };
@@ -69,7 +72,8 @@ struct TcShape {
 
 template <int N, int EPI, int NPL>
 __global__ void __launch_bounds__(kThreads, 1)
-    tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const TcArgs p) {
+    tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+              const __grid_constant__ CUtensorMap mapBt, const TcArgs p) {
     using Sh = TcShape<N, NPL>;
     constexpr int STAGES = Sh::STAGES;
     constexpr int NACC = Sh::NACC;
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int i = 0; ok && it.get(i, u); ++i) {
                 if (u.skip) continue;
                 const int64_t a0 = (int64_t)u.bs * p.A.site_rows + (int64_t)u.mt * 128;
-                const int64_t b0 = (int64_t)u.bs * p.B.site_rows + (int64_t)u.nt * N;
+                const int64_t b0 = (int64_t)u.bs * p.B.site_rows + (int64_t)u.nt * p.N;
                 for (int kb = u.kb0; kb < p.kb; ++kb) {
                     if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
                         fail();
@@ -135,13 +139,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     uint8_t* st = smem + s * STAGE;
-                    mbar_expect_tx(&full[s], STAGE);
+                    // a narrower last tile loads only its rows (its own map)
+                    const CUtensorMap* mb = u.nc == p.N ? &mapB : &mapBt;
+                    mbar_expect_tx(&full[s], NPL * kATile + NPL * u.nc * 64);
 #pragma unroll
                     for (int pl = 0; pl < NPL; ++pl)
                         tma_2d(st + pl * kATile, &mapA, kb * 32, (int)(a0 + pl * p.A.plane_rows), &full[s]);
 #pragma unroll
                     for (int pl = 0; pl < NPL; ++pl)
-                        tma_2d(st + NPL * kATile + pl * B_TILE, &mapB, kb * 32, (int)(b0 + pl * p.B.plane_rows),
+                        tma_2d(st + NPL * kATile + pl * B_TILE, mb, kb * 32, (int)(b0 + pl * p.B.plane_rows),
                                &full[s]);
                     ++issued;
                     if (++s == STAGES) {
@@ -164,9 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer
-            const uint32_t id_pos = idesc(128, N, false), id_neg = idesc(128, N, true);
-            const uint32_t id_ii = p.conjA ? id_pos : id_neg;   // sign of Ai*Bi in Re
-            const uint32_t id_ir = p.conjA ? id_neg : id_pos;   // sign of Ai*Br in Im
+            uint32_t id_pos = idesc(128, N, false), id_neg = idesc(128, N, true);
             int s = 0, a = 0;
             uint32_t ph = 0, aph = 0;
             bool any = false, ok = true;
@@ -178,6 +182,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 tc_fence_after();
+                id_pos = idesc(128, u.nc, false);
+                id_neg = idesc(128, u.nc, true);
+                const uint32_t id_ii = p.conjA ? id_pos : id_neg;   // sign of Ai*Bi in Re
+                const uint32_t id_ir = p.conjA ? id_neg : id_pos;   // sign of Ai*Br in Im
                 const uint32_t dr = tbase + (uint32_t)(a * 2 * N), di = dr + N;
                 for (int kb = u.kb0; kb < p.kb; ++kb) {
                     if (!mbar_wait(&full[s], ph, abort_flag)) {
@@ -263,34 +271,47 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const int row = u.mt * 128 + q * 32 + lane;      // accumulator row of this thread
             const uint32_t tr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 2 * N);
-            for (int c0 = 0; c0 < N; c0 += 16) {
+            for (int c0 = 0; c0 < u.nc; c0 += 16) {
                 float vr[16], vi[16];
                 tmem_ld16(tr + c0, vr);
                 tmem_ld16(tr + N + c0, vi);
                 tmem_ld_wait();
-                if (EPI == TC_EPI_MT) {
-                    // coupling entry (row d, column n = (ch, b)) -> Mt[b][ch * Dp + d]
-                    uint16_t* o = p.out16 + (int64_t)u.bs * p.out_site;
+                const int n0 = u.nt * p.N + c0;                   // first output column
+                if (EPI == TC_EPI_ROWS) {
+                    // A row (ch, b) -> Mt[b][ch * Dp + n]: 16 consecutive columns
+                    const int ch = row / p.ep_B, b = row % p.ep_B;
+                    uint16_t* o = p.out16 + (int64_t)u.bs * p.out_site + (int64_t)b * p.out_ld +
+                                  (int64_t)ch * p.ep_Dp + n0;
+                    uint32_t rh[8], ih[8];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int n = u.nt * N + c0 + j;
-                        const int ch = n / p.ep_B, b = n % p.ep_B;
-                        const int64_t at = (int64_t)b * p.out_ld + (int64_t)ch * p.ep_Dp + row;
-                        const uint16_t rh = bf16_rn(vr[j]), ih = bf16_rn(vi[j]);
-                        if (p.out_planes == 4) {
-                            o[at] = rh;
-                            o[p.out_plane + at] = bf16_rn(vr[j] - bf16_f(rh));
-                            o[2 * p.out_plane + at] = ih;
-                            o[3 * p.out_plane + at] = bf16_rn(vi[j] - bf16_f(ih));
-                        } else {
-                            o[at] = rh;
-                            o[p.out_plane + at] = ih;
+                    for (int j = 0; j < 8; ++j) {
+                        rh[j] = pack_bf16x2(vr[2 * j], vr[2 * j + 1]);
+                        ih[j] = pack_bf16x2(vi[2 * j], vi[2 * j + 1]);
+                    }
+                    st_v8(o, rh);
+                    if (p.out_planes == 4) {
+                        uint32_t rl[8], il[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            rl[j] = pack_bf16x2(vr[2 * j] - bf16_lo(rh[j]), vr[2 * j + 1] - bf16_hi(rh[j]));
+                            il[j] = pack_bf16x2(vi[2 * j] - bf16_lo(ih[j]), vi[2 * j + 1] - bf16_hi(ih[j]));
                         }
+                        st_v8(o + p.out_plane, rl);
+                        st_v8(o + 2 * p.out_plane, ih);
+                        st_v8(o + 3 * p.out_plane, il);
+                    } else {
+                        st_v8(o + p.out_plane, ih);
                     }
                 } else if (EPI == TC_EPI_C32) {
-                    float2* o = p.out32 + (int64_t)u.bs * p.out32_site + (int64_t)row * p.out32_ld + u.nt * N + c0;
+                    float2* o = p.out32 + (int64_t)u.bs * p.out32_site;
+                    if (p.out32_trans) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) o[j] = make_float2(vr[j], vi[j]);
+                        for (int j = 0; j < 16; ++j) o[(int64_t)(n0 + j) * p.out32_ld + row] = make_float2(vr[j], vi[j]);
+                    } else {
+                        o += (int64_t)row * p.out32_ld + n0;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) o[j] = make_float2(vr[j], vi[j]);
+                    }
                 }
             }
             tc_fence_before();
@@ -312,7 +333,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <int N, int EPI, int NPL>
-cudaError_t launch(const TcArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid, cudaStream_t s) {
+cudaError_t launch(const TcArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mbt, int grid,
+                   cudaStream_t s) {
     constexpr size_t smem = TcShape<N, NPL>::SMEM;
     static bool attr = false;
     if (!attr) {
@@ -321,43 +343,51 @@ cudaError_t launch(const TcArgs& a, const CUtensorMap& ma, const CUtensorMap& mb
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    tc_kernel<N, EPI, NPL><<<grid, kThreads, smem, s>>>(ma, mb, a);
+    tc_kernel<N, EPI, NPL><<<grid, kThreads, smem, s>>>(ma, mb, mbt, a);
     return cudaGetLastError();
 }
 
 template <int EPI, int NPL>
-cudaError_t launch_n(const TcArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, int grid, cudaStream_t s) {
-    return a.N == 256 ? launch<256, EPI, NPL>(a, ma, mb, grid, s) : launch<128, EPI, NPL>(a, ma, mb, grid, s);
+cudaError_t launch_n(const TcArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mbt, int grid,
+                     cudaStream_t s) {
+    // the template width bounds the shared-memory and TMEM layout; the tile
+    // width a.N (a multiple of 16) may be smaller
+    return a.N > 128 ? launch<256, EPI, NPL>(a, ma, mb, mbt, grid, s) : launch<128, EPI, NPL>(a, ma, mb, mbt, grid, s);
 }
 
 }  // namespace
 
 cudaError_t bip_tc_gemm(const TcArgs& a, cudaStream_t s) {
-    if (a.N != 128 && a.N != 256) return cudaErrorInvalidValue;
-    // every tile must lie inside its operand
+    if (a.N < 16 || a.N > 256 || a.N % 16) return cudaErrorInvalidValue;
     if (a.A.k != a.B.k || a.kb * 32 != a.A.k) return cudaErrorInvalidValue;
+    if (a.npl != 4 && a.npl != 2) return cudaErrorInvalidValue;
+    if (a.n_sites < 1 || a.mt_per < 1 || a.nt_per < 1) return cudaErrorInvalidValue;
+    // the last tile: 16 .. N columns, a multiple of 16
+    const int tail = a.n_cols - (a.nt_per - 1) * a.N;
+    if (tail < 16 || tail > a.N || tail % 16) return cudaErrorInvalidValue;
+    // every tile must lie inside its operand
     {
-        if (a.n_sites < 1 || a.mt_per < 1 || a.nt_per < 1) return cudaErrorInvalidValue;
         const int64_t pl = a.npl - 1;
         if ((int64_t)(a.n_sites - 1) * a.A.site_rows + pl * a.A.plane_rows + (int64_t)a.mt_per * 128 > a.A.rows)
             return cudaErrorInvalidValue;
-        if ((int64_t)(a.n_sites - 1) * a.B.site_rows + pl * a.B.plane_rows + (int64_t)a.nt_per * a.N > a.B.rows)
+        if ((int64_t)(a.n_sites - 1) * a.B.site_rows + pl * a.B.plane_rows + (int64_t)a.n_cols > a.B.rows)
             return cudaErrorInvalidValue;
     }
-    CUtensorMap ma, mb;
+    CUtensorMap ma, mb, mbt;
     cudaError_t e = make_map_2d(&ma, a.A.base, a.A.rows, a.A.k, 128);
     if (e != cudaSuccess) return e;
     e = make_map_2d(&mb, a.B.base, a.B.rows, a.B.k, a.N);
     if (e != cudaSuccess) return e;
+    e = make_map_2d(&mbt, a.B.base, a.B.rows, a.B.k, tail);
+    if (e != cudaSuccess) return e;
     const int units = a.n_sites * a.mt_per * a.nt_per;
     const int grid = units < num_sms() ? units : num_sms();
-    if (a.npl != 4 && a.npl != 2) return cudaErrorInvalidValue;
     const bool split = a.npl == 4;
     switch (a.epi) {
-        case TC_EPI_MT: return split ? launch_n<TC_EPI_MT, 4>(a, ma, mb, grid, s)
-                                     : launch_n<TC_EPI_MT, 2>(a, ma, mb, grid, s);
-        case TC_EPI_C32: return split ? launch_n<TC_EPI_C32, 4>(a, ma, mb, grid, s)
-                                      : launch_n<TC_EPI_C32, 2>(a, ma, mb, grid, s);
+        case TC_EPI_ROWS: return split ? launch_n<TC_EPI_ROWS, 4>(a, ma, mb, mbt, grid, s)
+                                       : launch_n<TC_EPI_ROWS, 2>(a, ma, mb, mbt, grid, s);
+        case TC_EPI_C32: return split ? launch_n<TC_EPI_C32, 4>(a, ma, mb, mbt, grid, s)
+                                      : launch_n<TC_EPI_C32, 2>(a, ma, mb, mbt, grid, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -71,13 +71,6 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// 32-byte store (one full sector) of eight 32-bit words; p 32-byte aligned
-__device__ __forceinline__ void st_v8(void* p, const uint32_t (&v)[8]) {
-    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]),
-                 "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-                 : "memory");
-}
-
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
     uint32_t r[8];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -162,7 +155,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int kb = 0; kb < 2; ++kb)
                         tma_2d(at + (pl * 2 + kb) * kAPlane, &mapW, kb * 32,
-                               sd.w_row0 + pl * sd.rows_pad + u.mt * 128, &a_full[ab]);
+                               sd.w_row0 + pl * sd.w_pad + u.mt * 128, &a_full[ab]);
                 a_last[ab] = i;
                 const int xrow0 = (sd.x_site0 + u.bs * 3) * a.K + u.pc * a.chunk_px;
                 for (int t = 0; t < tiles; ++t) {
@@ -487,9 +480,10 @@ cudaError_t bip_recon_tc(const ReconArgs& a, cudaStream_t s) {
     if (a.n_sites < 1 || a.chunks != a.K / a.chunk_px) return cudaErrorInvalidValue;
     for (int i = 0; i < 2; ++i) {
         const ReconSide& sd = a.side[i];
-        if (sd.mt_tiles * 128 != sd.rows_pad || sd.n_targets > sd.rows_pad || sd.nch > 9) return cudaErrorInvalidValue;
+        if (sd.mt_tiles * 128 != sd.w_pad || sd.n_targets > sd.rows_pad || sd.n_targets > sd.w_pad || sd.nch > 9)
+            return cudaErrorInvalidValue;
         if (sd.nch > 0 && ((uintptr_t)a.H & 15)) return cudaErrorMisalignedAddress;
-        if (sd.w_row0 + 2 * sd.rows_pad > a.w_rows) return cudaErrorInvalidValue;
+        if (sd.w_row0 + 2 * sd.w_pad > a.w_rows) return cudaErrorInvalidValue;
         if ((int64_t)(sd.x_site0 + 3 * a.n_sites) * a.K > a.x_rows) return cudaErrorInvalidValue;
     }
     CUtensorMap mw, mx;
