@@ -733,6 +733,49 @@ bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H,
     return BIP_OK;
 }
 
+// Sites per batch of the tensor-core map path: the batch whose tile counts
+// fill whole rounds of the SMs best (the coupling, the reconstruction and
+// the Gram launch one CTA per SM and walk their tiles in rounds), weighted
+// by the stages' usual shares of the map time, between 16 and 32 sites, and
+// -- above 16 -- small enough that the batch's coupling output (which the
+// Gram re-reads several times) stays within 1.2 x the L2 cache.
+int tc_batch(const bip_ctx* c) {
+    static int sms = 0, l2 = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 148;
+        if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || l2 < 1) l2 = 64 << 20;
+    }
+    const int npl = c->prec == BIP_PREC_MIXED ? 2 : 4;
+    const double mt_site = 2.0 * npl * c->Bpad * (double)c->nch_max * c->Dpad;   // bytes of Mt per site
+    // at least 16 sites: fewer leave the Gram (a few tiles per site) without
+    // enough tiles to fill the SMs
+    const int sb_max = std::max(16, std::min(32, (int)(1.2 * l2 / mt_site)));
+    const int K = c->cfg.win * c->cfg.win, nch = c->nch_max;
+    const int cw = tile_width(c->Dpad);
+    const int coupling = (nch * c->Bpad / 128) * ((c->Dpad + cw - 1) / cw);
+    const int recon = (round_up(c->geo.n_det, kRowPad) / 128 + c->Bpad / 128) * (K / std::min(K, 1024));
+    int gram = 0;
+    for (int mt = 0; mt < c->Bpad / 128; ++mt)
+        for (int nt = 0; nt < c->Bpad / 256; ++nt) gram += (nt + 1) * 256 > mt * 128;
+    auto eff = [&](int per, int sb) {
+        const int units = per * sb;
+        return (double)units / ((double)((units + sms - 1) / sms) * sms);
+    };
+    int best = 16;
+    double best_e = -1.0;
+    for (int sb = 16; sb <= sb_max; ++sb) {
+        const double e = 0.6 * eff(coupling, sb) + 0.3 * eff(recon, sb) + 0.1 * eff(gram, sb);
+        if (e > best_e + 1e-9) {
+            best_e = e;
+            best = sb;
+        }
+    }
+    return std::min(c->n_sites, best);
+}
+
 bip_status check_map_args(bip_ctx* c, const void* H, const double* scans, int32_t P, const void* out) {
     if (!c) return BIP_ERR_INVALID_ARG;
     if (!c->s1 || !c->s2 || c->sig1 != c->sig2)
@@ -797,7 +840,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         bb[4 * t] = y0; bb[4 * t + 1] = y1; bb[4 * t + 2] = x0; bb[4 * t + 3] = x1;
     }
 
-    const int SB = std::min(c->n_sites, tc ? 16 : 8);
+    const int SB = tc ? tc_batch(c) : std::min(c->n_sites, 8);
     const size_t rowsA = Dpad, rowsB = (size_t)nch * Bpad;
     const size_t perA = rowsA * K, perB = rowsB * K;
     const size_t perMt = (size_t)Bpad * nch * Dpad, perQ = (size_t)Bpad * Bpad;
