@@ -220,6 +220,23 @@ def site_map(M, C, mask, fyfx):
     return out
 
 
+def site_cube(M, C, mask, fyfx):
+    """Momentum-resolved contribution of one site, [P, n_det]: per detector
+    beam d, f_y f_x sum_n |sum_b M_{d,b} c_b(rho)|^2 on the masked scans,
+    zero elsewhere -- the terms of Eq. map-sum before the detector sum (the
+    energy-filtered 4D cube of Sec. 2.2.6)."""
+    out = np.zeros((C.shape[1], M[0].shape[0]), dtype=np.float64)
+    if not np.any(mask):
+        return out
+    Cm = C[:, mask]
+    acc = np.zeros((M[0].shape[0], Cm.shape[1]), dtype=np.float64)
+    for Mn in M:
+        a = Mn @ Cm
+        acc += a.real ** 2 + a.imag ** 2
+    out[mask] = fyfx * acc.T
+    return out
+
+
 def sum_sites(partials):
     """Exactly rounded FP64 sum over sites for every scan."""
     partials = np.asarray(partials, dtype=np.float64)
@@ -257,6 +274,39 @@ def bip_map(prob: Problem, scans=None, mode=None, keep_stages=False, sites=None)
             stages[k] = dict(stash1=W1[k], stash2=W2[k], S1w=S1w, S2w=S2w, M=M)
     partials = np.array(partials).reshape(len(partials), len(scans))
     return MapResult(sum_sites(partials), partials, stages)
+
+
+def bip_cube(prob: Problem, scans=None, mode=None):
+    """Algorithm 5 with the detector sum left open: the 4D cube [P, n_det]
+    (detector beams in geometry order), sites added in order in FP64."""
+    cfg, geo = prob.cfg, prob.geo
+    mode = mode or cfg.recon
+    scans = prob.scans if scans is None else np.asarray(scans, dtype=np.float64)
+    W1 = s1_windows(prob, geo.h_p1, detilt=True)
+    W2 = s2_windows(prob, geo.h_p2, detilt=True)
+    C = illumination(prob, geo.h_beam, geo.psi_beam, scans)
+    out = np.zeros((len(scans), geo.n_det), dtype=np.float64)
+    for k in range(len(prob.ion)):
+        iy, ix = prob.window_index(k)
+        S1w = reconstruct(W1[k], geo.w1, geo.h_beam, iy, ix, cfg.ny, cfg.nx, +1, mode)
+        S2w = reconstruct(W2[k], geo.w2, geo.h_det, iy, ix, cfg.ny, cfg.nx, -1, mode)
+        M = coupling(S2w, prob.H[k], S1w)
+        out += site_cube(M, C, crop_mask(prob, k, scans), cfg.fy * cfg.fx)
+    return out
+
+
+def exact_cube(prob: Problem, scans=None):
+    """Algorithm 4 with the detector sum left open, [P, n_det]."""
+    cfg, geo = prob.cfg, prob.geo
+    scans = prob.scans if scans is None else np.asarray(scans, dtype=np.float64)
+    W1 = s1_windows(prob, geo.h_beam, detilt=False)
+    W2 = s2_windows(prob, geo.h_det, detilt=False)
+    C = illumination(prob, geo.h_beam, geo.psi_beam, scans)
+    out = np.zeros((len(scans), geo.n_det), dtype=np.float64)
+    for k in range(len(prob.ion)):
+        M = coupling(W2[k], prob.H[k], W1[k])
+        out += site_cube(M, C, crop_mask(prob, k, scans), cfg.fy * cfg.fx)
+    return out
 
 
 def exact_map(prob: Problem, scans=None, keep_stages=False):
@@ -326,6 +376,28 @@ def conventional_map(prob: Problem, scans=None, det_h=None):
                     acc.append(float(np.sum(np.abs(a) ** 2)))
             psi = ph.step(psi, prob.T(i), prob.P)
         out[p] = math.fsum(acc)
+    return out
+
+
+def conventional_cube(prob: Problem, scans=None, det_h=None):
+    """Algorithm 1 per detector beam: [P, n_det] intensities |F_u .|^2 at the
+    detector beams det_h (default: the geometry's detector beams, in order)
+    summed over sites and channels."""
+    cfg, geo = prob.cfg, prob.geo
+    scans = prob.scans if scans is None else np.asarray(scans, dtype=np.float64)
+    det_h = geo.h_det if det_h is None else det_h
+    dsel = (det_h[:, 0] % cfg.ny, det_h[:, 1] % cfg.nx)
+    Hfull = {k: full_grid_H(prob, k) for k in range(len(prob.ion))}
+    out = np.zeros((len(scans), len(det_h)))
+    for p, rho in enumerate(scans):
+        psi = exact_probe(prob, rho)
+        for i in range(cfg.nz):
+            for k in np.nonzero(prob.plane == i)[0]:
+                for Hn in Hfull[k]:
+                    e = exit_operator(prob, Hn * psi, i)
+                    a = ph.unitary_dft(e)[dsel]
+                    out[p] += np.abs(a) ** 2
+            psi = ph.step(psi, prob.T(i), prob.P)
     return out
 
 

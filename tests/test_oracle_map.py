@@ -195,3 +195,37 @@ def test_subsampling_scale_consistency(c1):
     for k in range(len(pr.ion)):
         near = np.all(np.abs(pr.scans - pr.tau_px[k]) < 16, axis=1)
         assert rel(corr * ex.partials[k][near], e1.partials[k][near]) < 0.03
+
+
+# ---------------------------------------------------------------------------
+# the 4D cube (Sec. 2.2.6): the same terms with the detector sum left open
+
+def test_cube_alg4_equals_conventional_per_beam():
+    """Pin 4 beam by beam: at f = 1 with a window covering the grid, the
+    dual-matrix cube equals per-probe conventional multislice resolved over
+    the detector beams -- this fixes which S2 row is which detector beam."""
+    cfg = synth.tiny_config(nz=5, ion_slices=(1, 4), ion_cells=(0, 1))
+    sp = synth.make_specimen(cfg)
+    pr = bip.make_problem(sp)
+    a4 = bip.exact_cube(pr)
+    a1 = bip.conventional_cube(pr)
+    assert a4.shape == (len(pr.scans), pr.geo.n_det)
+    assert rel(a4, a1) < 1e-11
+    # the detector sum of either is the map
+    assert rel(a1.sum(axis=1), bip.conventional_map(pr)) < 1e-13
+
+
+def test_cube_sums_to_map(c1):
+    """The detector sum of the Algorithm 5 cube is the Algorithm 5 map."""
+    sp, pr, _ = c1
+    cube = bip.bip_cube(pr)
+    assert np.all(cube >= 0.0)
+    assert rel(cube.sum(axis=1), bip.bip_map(pr).map) < 1e-13
+
+
+def test_cube_full_parent_limit(c1):
+    """Every beam its own parent: the Algorithm 5 cube is the exact cube."""
+    sp, pr, _ = c1
+    geo = G.Geometry(pr.cfg, pr.lam, parents_override=(np.arange(pr.geo.B), np.arange(pr.geo.n_det)))
+    prf = bip.make_problem(sp, geometry=geo)
+    assert rel(bip.bip_cube(prf), bip.exact_cube(pr)) < 1e-12
