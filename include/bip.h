@@ -171,8 +171,15 @@ bip_status bip_coreloss_map(bip_ctx* ctx, const void* H, const double* scan_px,
 bip_status bip_coreloss_sites(bip_ctx* ctx, const void* H, const double* scan_px,
                               int32_t P, float* partial_out, void* stream);
 
-/* Energy-filtered 4D cube I(q, rho) (Sec. 2.2.6).  Not implemented in this
- * build: returns BIP_ERR_UNSUPPORTED after checking its arguments. */
+/* Energy-filtered 4D cube I(q, rho) (Sec. 2.2.6): the terms of Eq. map-sum
+ * with the detector sum left open,
+ *   cube[rho][d] = f_y f_x sum_sites sum_n |sum_b M^{(n)}_{d,b} c_b(rho)|^2
+ * over the sites whose crop mask holds rho; detector beams d in the order of
+ * bip_get_geometry.  Its detector sum is the map (up to FP32 rounding).
+ *   cube_out [P, n_det] float32 device, overwritten.
+ * The per-beam values carry the S2 reconstruction error of the context's
+ * parent set; with every detector beam a parent they are exact.  Sites are
+ * added in a fixed order (deterministic).  Requirements as bip_coreloss_map. */
 bip_status bip_coreloss_cube(bip_ctx* ctx, const void* H, const double* scan_px,
                              int32_t P, float* cube_out, void* stream);
 

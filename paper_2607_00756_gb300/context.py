@@ -50,6 +50,14 @@ class BipContext:
             out = torch.empty(len(scans), dtype=torch.float64, device=H.device)
         return capi.bip_coreloss_map(self.ctx, H, scans, out, stream)
 
+    def cube(self, H, scans, out=None, stream=None):
+        """The 4D cube [P, n_det] (detector beams in geometry order); its
+        detector sum is the map."""
+        scans = np.asarray(scans, dtype=np.float64)
+        if out is None:
+            out = torch.empty((len(scans), self.n_det), dtype=torch.float32, device=H.device)
+        return capi.bip_coreloss_cube(self.ctx, H, scans, out, stream)
+
     def sites(self, H, scans, out=None, stream=None):
         scans = np.asarray(scans, dtype=np.float64)
         if out is None:

@@ -53,7 +53,7 @@ struct bip_ctx {
     DevBuf stash1, stash2, cols;
 
     // map workspaces
-    DevBuf scans_d, work_d, partial, gdiff, rsum;
+    DevBuf scans_d, work_d, partial, gdiff, rsum, illum;
     DevBuf opA32, opB32, mt32, q32;     // FP32 path (zeroed at allocation)
     DevBuf opA16, opB16, mt16, q16;     // split-BF16 path (zeroed at allocation)
     DevBuf errflag;
@@ -526,7 +526,7 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->xtab, &c->sites_d,
                      &c->plane_ids_d, &c->seq_ids_d, &c->row_off_d, &c->row_ent_d, &c->stash1, &c->stash2, &c->cols, &c->scans_d,
                      &c->gdiff, &c->kb_d, &c->lat_d, &c->work_d, &c->partial, &c->opA32, &c->opB32, &c->mt32, &c->q32, &c->opA16,
-                     &c->opB16, &c->mt16, &c->q16, &c->errflag, &c->rsum, &c->wtc, &c->xtc};
+                     &c->opB16, &c->mt16, &c->q16, &c->errflag, &c->rsum, &c->wtc, &c->xtc, &c->illum};
     for (DevBuf* b : all) release(*b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
@@ -802,8 +802,33 @@ bool box_meets_crop(double y0, double y1, double x0, double x1, double ty, doubl
     return axis(y0, y1, ty, g.ny, g.fy) && axis(x0, x1, tx, g.nx, g.fx);
 }
 
+// Cube accumulation arguments of one batch (the coupling's format is set by
+// the caller).
+CubeArgs cube_args(const bip_ctx* c, const int32_t* ids, int nb, int P, float* cube) {
+    const bip_config& g = c->cfg;
+    CubeArgs a{};
+    a.n_sites = nb;
+    a.site_ids = ids;
+    a.sites = (const SiteDev*)c->sites_d.p;
+    a.n_det = c->geo.n_det;
+    a.Bpad = c->Bpad;
+    a.nch = c->nch_max;
+    a.Dp = c->Dpad;
+    a.m_ld = (int64_t)c->nch_max * c->Dpad;
+    a.C = (const float2*)c->illum.p;
+    a.P = P;
+    a.scans = (const double*)c->scans_d.p;
+    a.ny = g.ny; a.nx = g.nx; a.fy = g.fy; a.fx = g.fx;
+    a.scale = (float)(g.fy * g.fx);
+    a.cube = cube;
+    return a;
+}
+
+// The map, its per-site contributions, or the 4D cube (cube_out [P][n_det]):
+// the reconstruction and the coupling are shared, then either the Gram
+// matrix and the scan polynomial or the per-beam contraction.
 bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, float* partial_out,
-                   double* map_out, cudaStream_t s) {
+                   double* map_out, float* cube_out, cudaStream_t s) {
     const bip_config& g = c->cfg;
     const BipGeometry& geo = c->geo;
     const int K = g.win * g.win;
@@ -819,13 +844,22 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     CUDA_TRY(c, ensure(c->scans_d, (size_t)P * 2 * sizeof(double), false, s));
     CUDA_TRY(c, cudaMemcpyAsync(c->scans_d.p, scans, (size_t)P * 2 * sizeof(double), cudaMemcpyHostToDevice, s));
     float* partial = partial_out;
-    if (!partial) {
-        CUDA_TRY(c, ensure(c->partial, (size_t)c->n_sites * P * sizeof(float), false, s));
-        partial = (float*)c->partial.p;
+    if (cube_out) {
+        // the cube: c_b(rho) for every scan, the cube cleared
+        CUDA_TRY(c, cudaMemsetAsync(cube_out, 0, (size_t)P * geo.n_det * sizeof(float), s));
+        CUDA_TRY(c, ensure(c->illum, (size_t)Bpad * P * sizeof(float2), false, s));
+        IllumArgs ia{P, geo.B, Bpad, (const int2*)c->hbeam.p, (const double2*)c->coef.p, (const double*)c->scans_d.p,
+                     g.ny, g.nx, (float2*)c->illum.p};
+        CUDA_TRY(c, bip_illum(ia, s));
+    } else {
+        if (!partial) {
+            CUDA_TRY(c, ensure(c->partial, (size_t)c->n_sites * P * sizeof(float), false, s));
+            partial = (float*)c->partial.p;
+        }
+        // scans outside a site's crop mask stay 0: the evaluation writes only
+        // the scan tiles that can meet the mask
+        CUDA_TRY(c, cudaMemsetAsync(partial, 0, (size_t)c->n_sites * P * sizeof(float), s));
     }
-    // scans outside a site's crop mask stay 0: the evaluation writes only
-    // the scan tiles that can meet the mask
-    CUDA_TRY(c, cudaMemsetAsync(partial, 0, (size_t)c->n_sites * P * sizeof(float), s));
 
     // scan-tile bounding boxes (host)
     std::vector<double> bb((size_t)n_tiles * 4);
@@ -853,6 +887,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         CUDA_TRY(c, ensure(c->opA16, SB * perA * 8, true, s));
         CUDA_TRY(c, ensure(c->opB16, SB * perB * 8, true, s));
         CUDA_TRY(c, ensure(c->mt16, SB * perMt * 8, true, s));
+        if (cube_out) CUDA_TRY(c, ensure(c->mt32, SB * perMt * sizeof(float2), true, s));
         CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
     }
     CUDA_TRY(c, ensure(c->q32, SB * perQ * sizeof(float2), true, s));
@@ -930,7 +965,24 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             A.ep_B = Bpad;
             A.ep_Dp = Dpad;
             A.err = (int*)c->errflag.p;
+            if (cube_out) {
+                // per-beam values want M itself to FP32: complex64 rows (ch, b)
+                A.epi = TC_EPI_C32;
+                A.out32 = (float2*)c->mt32.p;
+                A.out32_site = (int64_t)perMt;
+                A.out32_ld = Dpad;
+            }
             TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(A, s));
+            if (cube_out) {
+                CubeArgs ca = cube_args(c, ids, nb, P, cube_out);
+                ca.fmt = 0;
+                ca.m32 = (const float2*)c->mt32.p;
+                ca.m_site = (int64_t)perMt;
+                ca.m_ld = Dpad;                              // element ((ch Bpad + b) Dpad + d)
+                ca.Dp = Bpad * Dpad;
+                TIMED(c, BIP_STAGE_QUADFORM, s, bip_cube_accumulate(ca, s));
+                continue;
+            }
             // Gram Q = sum_n M^(n)H M^(n), upper triangle, FP32
             TcArgs Gq{};
             Gq.epi = TC_EPI_C32;
@@ -961,6 +1013,14 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             A.C = (float2*)c->mt32.p; A.ldc = (int64_t)nch * Dpad; A.strideC = (int64_t)perMt;
             A.ep_B = Bpad; A.ep_Dp = Dpad;
             TIMED(c, BIP_STAGE_COUPLING, s, bip_cgemm_simt(A, s));
+            if (cube_out) {
+                CubeArgs ca = cube_args(c, ids, nb, P, cube_out);
+                ca.fmt = 0;
+                ca.m32 = (const float2*)c->mt32.p;
+                ca.m_site = (int64_t)perMt;
+                TIMED(c, BIP_STAGE_QUADFORM, s, bip_cube_accumulate(ca, s));
+                continue;
+            }
             // Gram Q = sum_n M^(n)H M^(n)
             CGemmArgs Bq{};
             Bq.M = Bpad; Bq.N = Bpad; Bq.K = nch * Dpad;
@@ -1005,7 +1065,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         CUDA_TRY(c, cudaStreamSynchronize(s));
         if (flag) return fail(c, BIP_ERR_TIMEOUT, "a tensor-core contraction gave up waiting (device timeout)");
     }
-    if (map_out) {
+    if (map_out && !cube_out) {
         CUDA_TRY(c, ensure(c->rsum, bip_reduce_scratch_bytes(c->n_sites, P), false, s));
         TIMED(c, BIP_STAGE_REDUCE, s, bip_reduce_sites(partial, c->n_sites, P, c->rsum.p, map_out, s));
         if (c->n_sites > 0) c->launches[BIP_STAGE_REDUCE]++;   // two kernels: chunks, then their sum
@@ -1021,22 +1081,21 @@ bip_status bip_coreloss_map(bip_ctx* c, const void* H, const double* scan_px, in
                             void* stream) {
     bip_status st = check_map_args(c, H, scan_px, P, map_out);
     if (st != BIP_OK) return st;
-    return run_map(c, H, scan_px, P, nullptr, map_out, (cudaStream_t)stream);
+    return run_map(c, H, scan_px, P, nullptr, map_out, nullptr, (cudaStream_t)stream);
 }
 
 bip_status bip_coreloss_sites(bip_ctx* c, const void* H, const double* scan_px, int32_t P, float* partial_out,
                               void* stream) {
     bip_status st = check_map_args(c, H, scan_px, P, partial_out);
     if (st != BIP_OK) return st;
-    return run_map(c, H, scan_px, P, partial_out, nullptr, (cudaStream_t)stream);
+    return run_map(c, H, scan_px, P, partial_out, nullptr, nullptr, (cudaStream_t)stream);
 }
 
 bip_status bip_coreloss_cube(bip_ctx* c, const void* H, const double* scan_px, int32_t P, float* cube_out,
                              void* stream) {
-    (void)stream;
     bip_status st = check_map_args(c, H, scan_px, P, cube_out);
     if (st != BIP_OK) return st;
-    return fail(c, BIP_ERR_UNSUPPORTED, "the 4D cube is not implemented in this build");
+    return run_map(c, H, scan_px, P, nullptr, nullptr, cube_out, (cudaStream_t)stream);
 }
 
 bip_status bip_copy_stash(bip_ctx* c, int32_t which, int32_t site, void* out, void* stream) {

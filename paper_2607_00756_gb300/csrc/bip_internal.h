@@ -255,6 +255,35 @@ struct TcArgs {
 };
 cudaError_t bip_tc_gemm(const TcArgs& a, cudaStream_t s);
 
+// cube.cu : the 4D cube (the detector sum of Eq. map-sum left open)
+struct IllumArgs {
+    int P, B, Bpad;                 // scans, aperture beams, padded rows
+    const int2* h;                  // [B] aperture beams (h_y, h_x)
+    const double2* coef;            // [B] f_y f_x Psi / sqrt(G sum |Psi|^2)
+    const double* scans;            // [P][2] pixels
+    int ny, nx;
+    float2* C;                      // [Bpad][P] c_b(rho), rows >= B zero
+};
+cudaError_t bip_illum(const IllumArgs& a, cudaStream_t s);
+
+struct CubeArgs {
+    int n_sites;                    // sites of this batch, added in order
+    const int32_t* site_ids;
+    const SiteDev* sites;
+    int n_det, Bpad, nch, Dp;       // M^(n)_{d,b} at element (b, n Dp + d)
+    int64_t m_ld, m_site, m_plane;  // row stride, site stride, plane stride
+    int fmt;                        // 0 complex64, 2 bf16 (re, im), 4 bf16 hi + lo
+    const float2* m32;
+    const uint16_t* m16;
+    const float2* C;                // [Bpad][P]
+    int P;
+    const double* scans;
+    int ny, nx, fy, fx;
+    float scale;                    // f_y f_x
+    float* cube;                    // [P][n_det], accumulated
+};
+cudaError_t bip_cube_accumulate(const CubeArgs& a, cudaStream_t s);
+
 // noalloc.cu : the static device scratch used by bip_build_s1_noalloc
 constexpr size_t kNoallocScratchBytes = size_t(32) << 20;   // 32 MiB per GPU
 // Device address of that array on the current device; the first call on a

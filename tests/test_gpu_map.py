@@ -199,3 +199,32 @@ def test_map_split_bf16_anisotropic(lib, prec):
     ref = obip.bip_map(obip.make_problem(sp))
     _, m, _, _ = gpu_run(lib, cfg, sp, prec=prec)
     assert rel(m, ref.map) < 1e-3
+
+
+# ---------------------------------------------------------------------------
+# the 4D cube (Sec. 2.2.6)
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("split_bf16", 1e-3), ("mixed", 1e-3)])
+def test_cube_config1(lib, c1, prec, tol):
+    """The cube against the oracle's Algorithm 5 cube, and its detector sum
+    against the library's map (computed through the Gram route)."""
+    cfg, sp, pr, ref = c1
+    want = obip.bip_cube(pr)
+    ctx, m, _, H = gpu_run(lib, cfg, sp, prec=prec)
+    cube = ctx.cube(H, sp.scans).cpu().numpy()
+    assert cube.shape == want.shape
+    assert rel(cube, want) < tol
+    assert rel(cube.astype(np.float64).sum(axis=1), m) < 1e-4
+    # zero outside every crop mask
+    outside = np.ones(len(sp.scans), bool)
+    for k in range(len(pr.ion)):
+        outside &= ~obip.crop_mask(pr, k, pr.scans)
+    assert np.all(cube[outside] == 0.0)
+
+
+def test_cube_edge_cases(lib):
+    cfg, sp = _edge_specimen()
+    pr = obip.make_problem(sp)
+    want = obip.bip_cube(pr)
+    ctx, _, _, H = gpu_run(lib, cfg, sp)
+    assert rel(ctx.cube(H, sp.scans).cpu().numpy(), want) < 1e-4
