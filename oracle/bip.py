@@ -295,6 +295,19 @@ def bip_cube(prob: Problem, scans=None, mode=None):
     return out
 
 
+def qeels(prob: Problem, cube, axis):
+    """Momentum-resolved output (qEELS): the cube summed over the detector
+    beams that share their component along `axis` (0: h_y, 1: h_x) -- one
+    resolved axis q_par, the perpendicular one summed.  Returns the bin
+    values h_par (ascending) and [P, n_bins] (Sec. 2.2.6 outputs)."""
+    h = np.asarray(prob.geo.h_det)[:, axis]
+    bins = np.unique(h)
+    out = np.zeros((cube.shape[0], len(bins)), dtype=np.float64)
+    for i, q in enumerate(bins):
+        out[:, i] = cube[:, h == q].sum(axis=1)
+    return bins, out
+
+
 def exact_cube(prob: Problem, scans=None):
     """Algorithm 4 with the detector sum left open, [P, n_det]."""
     cfg, geo = prob.cfg, prob.geo

@@ -229,3 +229,19 @@ def test_cube_full_parent_limit(c1):
     geo = G.Geometry(pr.cfg, pr.lam, parents_override=(np.arange(pr.geo.B), np.arange(pr.geo.n_det)))
     prf = bip.make_problem(sp, geometry=geo)
     assert rel(bip.bip_cube(prf), bip.exact_cube(pr)) < 1e-12
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_qeels_bins_and_invariant(c1, axis):
+    """qEELS: every detector beam lands in the bin of its component along
+    the resolved axis; the resolved axis summed recovers the map."""
+    sp, pr, _ = c1
+    cube = bip.bip_cube(pr)
+    bins, q = bip.qeels(pr, cube, axis)
+    h = pr.geo.h_det[:, axis]
+    assert np.all(np.diff(bins) > 0) and set(bins.tolist()) == set(h.tolist())
+    assert np.all(bins % (pr.cfg.fy if axis == 0 else pr.cfg.fx) == 0)
+    assert rel(q.sum(axis=1), bip.bip_map(pr).map) < 1e-13
+    # one bin by hand
+    i = len(bins) // 2
+    assert np.allclose(q[:, i], cube[:, h == bins[i]].sum(axis=1), rtol=1e-14, atol=0)
