@@ -183,6 +183,19 @@ bip_status bip_coreloss_sites(bip_ctx* ctx, const void* H, const double* scan_px
 bip_status bip_coreloss_cube(bip_ctx* ctx, const void* H, const double* scan_px,
                              int32_t P, float* cube_out, void* stream);
 
+/* Momentum-resolved output (qEELS, Sec. 2.2.6): the cube above summed over
+ * the detector beams that share their component along one axis,
+ *   qeels[rho][i] = sum_{d : h_d[axis] = bins[i]} cube[rho][d],
+ * axis 0: resolved along q_y (h_y), 1: along q_x; bins ascending.  Its sum
+ * over the bins is the map.
+ *   bip_qeels_bins: the number of bins and (h_values, nullable host int32
+ *   [n_bins]) their h components.  Host only.
+ *   qeels_out [P, n_bins] float32 device, overwritten.
+ * BIP_ERR_INVALID_ARG for another axis; requirements as bip_coreloss_map. */
+bip_status bip_qeels_bins(const bip_ctx* ctx, int32_t axis, int32_t* n_bins, int32_t* h_values);
+bip_status bip_coreloss_qeels(bip_ctx* ctx, const void* H, const double* scan_px, int32_t P,
+                              int32_t axis, float* qeels_out, void* stream);
+
 /* Stage access for validation.
  * bip_copy_stash: the de-tilted parent windows of one site, which = 1 (S1,
  *   [Bp1, win, win]) or 2 (S2, [Bp2, win, win]) complex64, to device `out`.

@@ -60,6 +60,8 @@ def _load():
         "bip_coreloss_map": [VP, VP, P(D), I32, VP, VP],
         "bip_coreloss_sites": [VP, VP, P(D), I32, VP, VP],
         "bip_coreloss_cube": [VP, VP, P(D), I32, VP, VP],
+        "bip_qeels_bins": [VP, I32, P(I32), P(I32)],
+        "bip_coreloss_qeels": [VP, VP, P(D), I32, I32, VP, VP],
         "bip_copy_stash": [VP, I32, I32, VP, VP],
         "bip_site_windows": [VP, I32, VP, VP, VP],
         "bip_site_coupling": [VP, VP, I32, VP, VP],
@@ -220,6 +222,25 @@ def bip_coreloss_cube(ctx, H, scans, out, stream=None):
     s, sp = _scans(scans)
     _check("bip_coreloss_cube", ctx, _lib.bip_coreloss_cube(ctx, _dev(H, torch.complex64, "H"), sp, len(s),
                                                              _dev(out, torch.float32, "out"), _stream(stream)))
+    return out
+
+
+def bip_qeels_bins(ctx, axis):
+    """Bin components h (ascending) of the qEELS output along `axis`."""
+    n = ctypes.c_int32(0)
+    _check("bip_qeels_bins", ctx, _lib.bip_qeels_bins(ctx, int(axis), ctypes.byref(n), None))
+    h = np.zeros(n.value, dtype=np.int32)
+    _check("bip_qeels_bins", ctx, _lib.bip_qeels_bins(ctx, int(axis), ctypes.byref(n),
+                                                       h.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return h
+
+
+def bip_coreloss_qeels(ctx, H, scans, axis, out, stream=None):
+    import torch
+    s, sp = _scans(scans)
+    _check("bip_coreloss_qeels", ctx, _lib.bip_coreloss_qeels(ctx, _dev(H, torch.complex64, "H"), sp, len(s),
+                                                               int(axis), _dev(out, torch.float32, "out"),
+                                                               _stream(stream)))
     return out
 
 

@@ -58,6 +58,15 @@ class BipContext:
             out = torch.empty((len(scans), self.n_det), dtype=torch.float32, device=H.device)
         return capi.bip_coreloss_cube(self.ctx, H, scans, out, stream)
 
+    def qeels(self, H, scans, axis, out=None, stream=None):
+        """Momentum-resolved output: (bin h values, [P, n_bins]) resolved along
+        axis 0 (q_y) or 1 (q_x); its sum over the bins is the map."""
+        scans = np.asarray(scans, dtype=np.float64)
+        bins = capi.bip_qeels_bins(self.ctx, axis)
+        if out is None:
+            out = torch.empty((len(scans), len(bins)), dtype=torch.float32, device=H.device)
+        return bins, capi.bip_coreloss_qeels(self.ctx, H, scans, axis, out, stream)
+
     def sites(self, H, scans, out=None, stream=None):
         scans = np.asarray(scans, dtype=np.float64)
         if out is None:

@@ -53,7 +53,7 @@ struct bip_ctx {
     DevBuf stash1, stash2, cols;
 
     // map workspaces
-    DevBuf scans_d, work_d, partial, gdiff, rsum, illum;
+    DevBuf scans_d, work_d, partial, gdiff, rsum, illum, cube_scratch, bin_of_d;
     DevBuf opA32, opB32, mt32, q32;     // FP32 path (zeroed at allocation)
     DevBuf opA16, opB16, mt16, q16;     // split-BF16 path (zeroed at allocation)
     DevBuf errflag;
@@ -526,7 +526,8 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->xtab, &c->sites_d,
                      &c->plane_ids_d, &c->seq_ids_d, &c->row_off_d, &c->row_ent_d, &c->stash1, &c->stash2, &c->cols, &c->scans_d,
                      &c->gdiff, &c->kb_d, &c->lat_d, &c->work_d, &c->partial, &c->opA32, &c->opB32, &c->mt32, &c->q32, &c->opA16,
-                     &c->opB16, &c->mt16, &c->q16, &c->errflag, &c->rsum, &c->wtc, &c->xtc, &c->illum};
+                     &c->opB16, &c->mt16, &c->q16, &c->errflag, &c->rsum, &c->wtc, &c->xtc, &c->illum,
+                     &c->cube_scratch, &c->bin_of_d};
     for (DevBuf* b : all) release(*b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
@@ -975,7 +976,6 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(A, s));
             if (cube_out) {
                 CubeArgs ca = cube_args(c, ids, nb, P, cube_out);
-                ca.fmt = 0;
                 ca.m32 = (const float2*)c->mt32.p;
                 ca.m_site = (int64_t)perMt;
                 ca.m_ld = Dpad;                              // element ((ch Bpad + b) Dpad + d)
@@ -1015,7 +1015,6 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             TIMED(c, BIP_STAGE_COUPLING, s, bip_cgemm_simt(A, s));
             if (cube_out) {
                 CubeArgs ca = cube_args(c, ids, nb, P, cube_out);
-                ca.fmt = 0;
                 ca.m32 = (const float2*)c->mt32.p;
                 ca.m_site = (int64_t)perMt;
                 TIMED(c, BIP_STAGE_QUADFORM, s, bip_cube_accumulate(ca, s));
@@ -1096,6 +1095,46 @@ bip_status bip_coreloss_cube(bip_ctx* c, const void* H, const double* scan_px, i
     bip_status st = check_map_args(c, H, scan_px, P, cube_out);
     if (st != BIP_OK) return st;
     return run_map(c, H, scan_px, P, nullptr, nullptr, cube_out, (cudaStream_t)stream);
+}
+
+// qEELS bins: the distinct components of the detector beams along `axis`,
+// ascending, and each beam's bin.
+static bool qeels_bins(const bip_ctx* c, int axis, std::vector<int32_t>& bins, std::vector<int32_t>& bin_of) {
+    if (axis != 0 && axis != 1) return false;
+    const BipGeometry& geo = c->geo;
+    bins.clear();
+    for (int d = 0; d < geo.n_det; ++d) bins.push_back(geo.h_det[2 * d + axis]);
+    std::sort(bins.begin(), bins.end());
+    bins.erase(std::unique(bins.begin(), bins.end()), bins.end());
+    bin_of.resize(geo.n_det);
+    for (int d = 0; d < geo.n_det; ++d)
+        bin_of[d] = (int32_t)(std::lower_bound(bins.begin(), bins.end(), geo.h_det[2 * d + axis]) - bins.begin());
+    return true;
+}
+
+bip_status bip_qeels_bins(const bip_ctx* c, int32_t axis, int32_t* n_bins, int32_t* h_values) {
+    if (!c || !n_bins) return BIP_ERR_INVALID_ARG;
+    std::vector<int32_t> bins, bin_of;
+    if (!qeels_bins(c, axis, bins, bin_of)) return BIP_ERR_INVALID_ARG;
+    *n_bins = (int32_t)bins.size();
+    if (h_values) std::copy(bins.begin(), bins.end(), h_values);
+    return BIP_OK;
+}
+
+bip_status bip_coreloss_qeels(bip_ctx* c, const void* H, const double* scan_px, int32_t P, int32_t axis,
+                              float* qeels_out, void* stream) {
+    bip_status st = check_map_args(c, H, scan_px, P, qeels_out);
+    if (st != BIP_OK) return st;
+    std::vector<int32_t> bins, bin_of;
+    if (!qeels_bins(c, axis, bins, bin_of)) return fail(c, BIP_ERR_INVALID_ARG, "axis must be 0 (q_y) or 1 (q_x)");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(c, ensure(c->cube_scratch, (size_t)P * c->geo.n_det * sizeof(float), false, s));
+    CUDA_TRY(c, upload(c->bin_of_d, bin_of, s));
+    st = run_map(c, H, scan_px, P, nullptr, nullptr, (float*)c->cube_scratch.p, s);
+    if (st != BIP_OK) return st;
+    CUDA_TRY(c, bip_qeels_bin((const float*)c->cube_scratch.p, P, c->geo.n_det, (const int32_t*)c->bin_of_d.p,
+                              (int)bins.size(), qeels_out, s));
+    return BIP_OK;
 }
 
 bip_status bip_copy_stash(bip_ctx* c, int32_t which, int32_t site, void* out, void* stream) {

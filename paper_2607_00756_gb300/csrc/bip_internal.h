@@ -270,11 +270,9 @@ struct CubeArgs {
     int n_sites;                    // sites of this batch, added in order
     const int32_t* site_ids;
     const SiteDev* sites;
-    int n_det, Bpad, nch, Dp;       // M^(n)_{d,b} at element (b, n Dp + d)
-    int64_t m_ld, m_site, m_plane;  // row stride, site stride, plane stride
-    int fmt;                        // 0 complex64, 2 bf16 (re, im), 4 bf16 hi + lo
-    const float2* m32;
-    const uint16_t* m16;
+    int n_det, Bpad, nch, Dp;       // M^(n)_{d,b} at element b m_ld + n Dp + d
+    int64_t m_ld, m_site;           // row stride, site stride
+    const float2* m32;              // the coupling, complex64
     const float2* C;                // [Bpad][P]
     int P;
     const double* scans;
@@ -283,6 +281,9 @@ struct CubeArgs {
     float* cube;                    // [P][n_det], accumulated
 };
 cudaError_t bip_cube_accumulate(const CubeArgs& a, cudaStream_t s);
+// qEELS: out[rho][bin_of[d]] = sum of cube[rho][d] over the beams of a bin
+cudaError_t bip_qeels_bin(const float* cube, int P, int n_det, const int32_t* bin_of, int n_bins, float* out,
+                          cudaStream_t s);
 
 // noalloc.cu : the static device scratch used by bip_build_s1_noalloc
 constexpr size_t kNoallocScratchBytes = size_t(32) << 20;   // 32 MiB per GPU

@@ -38,18 +38,7 @@ __global__ void illum_kernel(IllumArgs a) {
     a.C[(size_t)b * a.P + p] = v;
 }
 
-// M^(n)_{d,b} from the stored coupling: FMT 0 complex64, 2 bf16 (re, im),
-// 4 bf16 hi + lo (re_hi, re_lo, im_hi, im_lo); element (b, n Dp + d)
-template <int FMT>
-__device__ __forceinline__ float2 m_at(const CubeArgs& a, int bs, int64_t e) {
-    if (FMT == 0) return a.m32[(size_t)bs * a.m_site + e];
-    const uint16_t* m = a.m16 + (size_t)bs * a.m_site;
-    auto f = [](uint16_t h) { return __uint_as_float((uint32_t)h << 16); };
-    if (FMT == 2) return make_float2(f(m[e]), f(m[a.m_plane + e]));
-    return make_float2(f(m[e]) + f(m[a.m_plane + e]), f(m[2 * a.m_plane + e]) + f(m[3 * a.m_plane + e]));
-}
-
-template <int FMT>
+// M^(n)_{d,b} is the complex64 coupling at element (b m_ld + n Dp + d)
 __global__ void __launch_bounds__(kThreads) cube_kernel(CubeArgs a) {
     __shared__ float2 ms[kKb][kTile];     // [b][d]
     __shared__ float2 cs[kKb][kTile];     // [b][rho]
@@ -81,7 +70,8 @@ __global__ void __launch_bounds__(kThreads) cube_kernel(CubeArgs a) {
                 for (int k = threadIdx.x; k < kKb * kTile; k += kThreads) {
                     const int bb = k / kTile, x = k % kTile;
                     const int d = d0 + x, p = p0 + x;
-                    ms[bb][x] = d < a.n_det ? m_at<FMT>(a, bs, (int64_t)(b0 + bb) * a.m_ld + (int64_t)n * a.Dp + d)
+                    ms[bb][x] = d < a.n_det ? a.m32[(size_t)bs * a.m_site + (int64_t)(b0 + bb) * a.m_ld +
+                                                    (int64_t)n * a.Dp + d]
                                             : make_float2(0.f, 0.f);
                     cs[bb][x] = p < a.P ? a.C[(size_t)(b0 + bb) * a.P + p] : make_float2(0.f, 0.f);
                 }
@@ -121,6 +111,18 @@ __global__ void __launch_bounds__(kThreads) cube_kernel(CubeArgs a) {
     }
 }
 
+// qEELS: row rho of the cube binned by each beam's bin (beams in order,
+// one thread per scan row, so the sums are deterministic)
+__global__ void qeels_kernel(const float* __restrict__ cube, int P, int n_det, const int32_t* __restrict__ bin_of,
+                             int n_bins, float* __restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    float* o = out + (size_t)p * n_bins;
+    for (int i = 0; i < n_bins; ++i) o[i] = 0.f;
+    const float* c = cube + (size_t)p * n_det;
+    for (int d = 0; d < n_det; ++d) o[__ldg(&bin_of[d])] += c[d];
+}
+
 }  // namespace
 
 cudaError_t bip_illum(const IllumArgs& a, cudaStream_t s) {
@@ -133,11 +135,13 @@ cudaError_t bip_cube_accumulate(const CubeArgs& a, cudaStream_t s) {
     if (a.n_sites < 1) return cudaSuccess;
     if (a.Bpad % kKb) return cudaErrorInvalidValue;
     const dim3 grid((a.n_det + kTile - 1) / kTile, (a.P + kTile - 1) / kTile);
-    switch (a.fmt) {
-        case 0: cube_kernel<0><<<grid, kThreads, 0, s>>>(a); break;
-        case 2: cube_kernel<2><<<grid, kThreads, 0, s>>>(a); break;
-        case 4: cube_kernel<4><<<grid, kThreads, 0, s>>>(a); break;
-        default: return cudaErrorInvalidValue;
-    }
+    cube_kernel<<<grid, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t bip_qeels_bin(const float* cube, int P, int n_det, const int32_t* bin_of, int n_bins, float* out,
+                          cudaStream_t s) {
+    if (P < 1 || n_det < 1 || n_bins < 1) return cudaErrorInvalidValue;
+    qeels_kernel<<<(P + 127) / 128, 128, 0, s>>>(cube, P, n_det, bin_of, n_bins, out);
     return cudaGetLastError();
 }

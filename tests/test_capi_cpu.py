@@ -108,3 +108,19 @@ def test_calls_out_of_order_return_errors(capi):
         capi.bip_destroy(ctx)
     assert capi.lib().bip_last_error(None) == b"null context"
     assert capi.lib().bip_destroy(None) == 1
+
+
+def test_qeels_bins_host(capi):
+    """The qEELS bins: the distinct detector-beam components along the axis,
+    ascending; another axis is an argument error."""
+    cfg = synth.config1()
+    ctx = capi.bip_create(capi.make_config(cfg))
+    try:
+        geo = capi.bip_get_geometry(ctx)
+        for axis in (0, 1):
+            h = capi.bip_qeels_bins(ctx, axis)
+            assert np.array_equal(h, np.unique(geo["h_det"][:, axis]))
+        with pytest.raises(capi.BipError):
+            capi.bip_qeels_bins(ctx, 2)
+    finally:
+        capi.bip_destroy(ctx)

@@ -228,3 +228,17 @@ def test_cube_edge_cases(lib):
     want = obip.bip_cube(pr)
     ctx, _, _, H = gpu_run(lib, cfg, sp)
     assert rel(ctx.cube(H, sp.scans).cpu().numpy(), want) < 1e-4
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_qeels_config1(lib, c1, axis):
+    """qEELS against the oracle's binning of its cube; the bins summed give
+    the library's map."""
+    cfg, sp, pr, ref = c1
+    hb_want, want = obip.qeels(pr, obip.bip_cube(pr), axis)
+    ctx, m, _, H = gpu_run(lib, cfg, sp)
+    hb, q = ctx.qeels(H, sp.scans, axis)
+    assert np.array_equal(hb, hb_want)
+    q = q.cpu().numpy()
+    assert rel(q, want) < 1e-4
+    assert rel(q.astype(np.float64).sum(axis=1), m) < 1e-4
