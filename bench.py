@@ -323,12 +323,12 @@ def run_gpu(args, rank, world):
 
 
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of
-# the same launch size (profiles/coupling_gram_tc_config2_16site_batch.md);
+# the same launch size (profiles/coupling_gram_tc_config2_19site_batch.md);
 # reported only while the kernel's source file is unchanged.
 NCU_TRAFFIC = {
-    ("mixed", "coupling"): {"bytes": 930073856 + 123078400,
+    ("mixed", "coupling"): {"bytes": 1070466000 + 139107584,
                             "source": "paper_2607_00756_gb300/csrc/gemm_tc.cu",
-                            "sha256": "92f9248123259f4c9573c939da67bfa519e3196dc1fde9a7f162e4c0ba26347f"},
+                            "sha256": "aa3a3688b7d1fc953647f1ceea5e381ea39274aa0b09bd9c020bb45788982ce5"},
 }
 
 
