@@ -59,9 +59,17 @@ typedef enum {
     BIP_PREC_FP32 = 0,         /* FP32 SIMT complex GEMMs                     */
     BIP_PREC_SPLIT_BF16 = 1,   /* tcgen05, every contraction in BF16 hi+lo
                                   (3 products per real product), FP32 acc.    */
-    BIP_PREC_MIXED = 2         /* tcgen05, coupling and Gram in BF16 (one
+    BIP_PREC_MIXED = 2,        /* tcgen05, coupling and Gram in BF16 (one
                                   product), the quadratic form in BF16 hi+lo;
                                   FP32 accumulation throughout               */
+    BIP_PREC_FP8_TILE = 3      /* as MIXED, but the coupling's operands in
+                                  FP8 E4M3 with one scale per 64x64 window
+                                  (operand row): the scale is an a-priori
+                                  bound of the row, kappa sum_p w_tp
+                                  max_r |dt_p(r)| (times max_r |H_n| on the
+                                  S1 side; kappa = 1 + 2^-6), applied to the
+                                  FP32 products in the epilogue.  Needs both
+                                  parent sets <= 64 (else UNSUPPORTED).    */
 } bip_precision;
 
 typedef enum {

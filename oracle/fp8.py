@@ -83,22 +83,36 @@ def site_coupling_fp8(S2w, Hk, S1w, W2, dt2, W1, dt1):
     return np.stack(out)
 
 
-def bip_map_fp8(prob, scans=None, mode=None):
-    """Algorithm 5 with the coupling operands in scaled E4M3 (everything
-    else as in bip.bip_map, FP64)."""
+def _fp8_sites(prob, scans, mode, per_site):
+    """per_site(M, C, mask, fyfx) for every site, with the FP8 coupling."""
     cfg, geo = prob.cfg, prob.geo
     mode = mode or cfg.recon
-    scans = prob.scans if scans is None else np.asarray(scans, dtype=np.float64)
     W1 = bip.s1_windows(prob, geo.h_p1, detilt=True)
     W2 = bip.s2_windows(prob, geo.h_p2, detilt=True)
     C = bip.illumination(prob, geo.h_beam, geo.psi_beam, scans)
-    fyfx = cfg.fy * cfg.fx
-    partials = []
+    out = []
     for k in range(len(prob.ion)):
         iy, ix = prob.window_index(k)
         S1w = bip.reconstruct(W1[k], geo.w1, geo.h_beam, iy, ix, cfg.ny, cfg.nx, +1, mode)
         S2w = bip.reconstruct(W2[k], geo.w2, geo.h_det, iy, ix, cfg.ny, cfg.nx, -1, mode)
         M = site_coupling_fp8(S2w, prob.H[k], S1w, geo.w2, W2[k], geo.w1, W1[k])
-        partials.append(bip.site_map(M, C, bip.crop_mask(prob, k, scans), fyfx))
+        out.append(per_site(M, C, bip.crop_mask(prob, k, scans), cfg.fy * cfg.fx))
+    return out
+
+
+def bip_map_fp8(prob, scans=None, mode=None):
+    """Algorithm 5 with the coupling operands in scaled E4M3 (everything
+    else as in bip.bip_map, FP64)."""
+    scans = prob.scans if scans is None else np.asarray(scans, dtype=np.float64)
+    partials = _fp8_sites(prob, scans, mode, bip.site_map)
     partials = np.array(partials).reshape(len(partials), len(scans))
     return bip.MapResult(bip.sum_sites(partials), partials)
+
+
+def bip_cube_fp8(prob, scans=None, mode=None):
+    """The 4D cube (bip.bip_cube) with the FP8 coupling, [P, n_det]."""
+    scans = prob.scans if scans is None else np.asarray(scans, dtype=np.float64)
+    out = np.zeros((len(scans), prob.geo.n_det), dtype=np.float64)
+    for c in _fp8_sites(prob, scans, mode, bip.site_cube):
+        out += c
+    return out

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libbip.so")
 BIP_OK = 0
 STATUS = {0: "BIP_OK", 1: "BIP_ERR_INVALID_ARG", 2: "BIP_ERR_SHAPE", 3: "BIP_ERR_OOM",
           4: "BIP_ERR_CUDA", 5: "BIP_ERR_TIMEOUT", 6: "BIP_ERR_UNSUPPORTED"}
-PREC = {"fp32": 0, "split_bf16": 1, "mixed": 2}
+PREC = {"fp32": 0, "split_bf16": 1, "mixed": 2, "fp8": 3}
 RECON = {"complex": 0, "magnitude": 1}
 
 

@@ -56,6 +56,8 @@ struct bip_ctx {
     DevBuf scans_d, work_d, partial, gdiff, rsum, illum, cube_scratch, bin_of_d;
     DevBuf opA32, opB32, mt32, q32;     // FP32 path (zeroed at allocation)
     DevBuf opA16, opB16, mt16, q16;     // split-BF16 path (zeroed at allocation)
+    DevBuf op8A, op8B;                  // FP8 coupling operands, E4M3 (zeroed at allocation)
+    DevBuf f8pmax, f8inv0, f8inv1, f8hmax, f8H, f8sA, f8sB;   // FP8 per-window scales
     DevBuf errflag;
     std::vector<int32_t> work_h;
 
@@ -503,7 +505,8 @@ bip_status bip_create(const bip_config* cfg, bip_ctx** out) {
     if (g.win < 16 || g.win % 16 || g.win > g.ny / g.fy || g.win > g.nx / g.fx) return bad(BIP_ERR_SHAPE, "win");
     if (g.nrad1 < 0 || g.nrad2 < 0 || g.nang1 < 1 || g.nang2 < 1) return bad(BIP_ERR_INVALID_ARG, "rings");
     if (g.recon != BIP_RECON_COMPLEX && g.recon != BIP_RECON_MAGNITUDE) return bad(BIP_ERR_INVALID_ARG, "recon");
-    if (g.prec != BIP_PREC_FP32 && g.prec != BIP_PREC_SPLIT_BF16 && g.prec != BIP_PREC_MIXED)
+    if (g.prec != BIP_PREC_FP32 && g.prec != BIP_PREC_SPLIT_BF16 && g.prec != BIP_PREC_MIXED &&
+        g.prec != BIP_PREC_FP8_TILE)
         return bad(BIP_ERR_INVALID_ARG, "prec");
     c->cfg = g;
     c->prec = g.prec;
@@ -559,7 +562,8 @@ bip_status bip_get_geometry(const bip_ctx* c, int32_t* h_beam, int32_t* h_det, i
 
 bip_status bip_set_precision(bip_ctx* c, int32_t prec) {
     if (!c) return BIP_ERR_INVALID_ARG;
-    if (prec != BIP_PREC_FP32 && prec != BIP_PREC_SPLIT_BF16 && prec != BIP_PREC_MIXED)
+    if (prec != BIP_PREC_FP32 && prec != BIP_PREC_SPLIT_BF16 && prec != BIP_PREC_MIXED &&
+        prec != BIP_PREC_FP8_TILE)
         return fail(c, BIP_ERR_INVALID_ARG, "unknown precision");
     c->prec = prec;
     return BIP_OK;
@@ -689,14 +693,25 @@ GatherArgs gather_args(const bip_ctx* c, int side, const int32_t* ids, int n) {
     return a;
 }
 
-// Tensor-core reconstruction of one batch (mixed path): X planes from the
-// stashes, then W X with the epilogue writing both coupling operands.
+// Tensor-core reconstruction of one batch (mixed and FP8 paths): X planes
+// from the stashes, then W X with the epilogue writing both coupling
+// operands -- BF16, or E4M3 with the per-window scales computed in between
+// from the parents' window maxima (which the X preparation takes).
 bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H, void* opA, void* opB,
                           cudaStream_t s) {
     const bip_config& g = c->cfg;
     const BipGeometry& geo = c->geo;
     const int K = g.win * g.win, Dpad = c->Dpad, Bpad = c->Bpad, nch = c->nch_max;
+    const bool f8 = c->prec == BIP_PREC_FP8_TILE;
     CUDA_TRY(c, ensure(c->xtc, (size_t)2 * nb * 3 * K * 64 * sizeof(uint16_t), false, s));
+    if (f8) {
+        CUDA_TRY(c, ensure(c->f8pmax, (size_t)2 * nb * 64 * sizeof(unsigned), false, s));
+        CUDA_TRY(c, ensure(c->f8inv0, (size_t)nb * Dpad * sizeof(float), false, s));
+        CUDA_TRY(c, ensure(c->f8inv1, (size_t)nb * Bpad * sizeof(float), false, s));
+        CUDA_TRY(c, ensure(c->f8sA, (size_t)nb * nch * Bpad * sizeof(float), false, s));
+        CUDA_TRY(c, ensure(c->f8sB, (size_t)nb * Dpad * sizeof(float), false, s));
+        CUDA_TRY(c, cudaMemsetAsync(c->f8pmax.p, 0, (size_t)2 * nb * 64 * sizeof(unsigned), s));
+    }
     XprepArgs x{};
     x.n_sites = nb;
     x.site_ids = ids;
@@ -704,7 +719,26 @@ bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H,
     x.X = (uint16_t*)c->xtc.p;
     x.side[0] = XprepSide{(const float2*)c->stash2.p, geo.Bp2, 0};
     x.side[1] = XprepSide{(const float2*)c->stash1.p, geo.Bp1, 3 * nb};
+    x.pmax = f8 ? (unsigned*)c->f8pmax.p : nullptr;
     TIMED(c, BIP_STAGE_GATHER, s, bip_xprep(x, s));
+    const int Dw = round_up(geo.n_det, kRowPad);
+    if (f8) {
+        F8ScaleArgs f{};
+        f.n_sites = nb;
+        f.site_ids = ids;
+        f.sites = (const SiteDev*)c->sites_d.p;
+        f.nch = nch;
+        f.hmax = (const float*)c->f8hmax.p;
+        f.W = (const uint16_t*)c->wtc.p;
+        f.w_row0[0] = 0; f.w_pad[0] = Dw; f.n_targets[0] = geo.n_det; f.rows_pad[0] = Dpad;
+        f.w_row0[1] = 2 * Dw; f.w_pad[1] = Bpad; f.n_targets[1] = geo.B; f.rows_pad[1] = Bpad;
+        f.pmax = (const unsigned*)c->f8pmax.p;
+        f.inv_row[0] = (float*)c->f8inv0.p;
+        f.inv_row[1] = (float*)c->f8inv1.p;
+        f.scaleB = (float*)c->f8sB.p;
+        f.scaleA = (float*)c->f8sA.p;
+        TIMED(c, BIP_STAGE_GATHER, s, bip_f8_scales(f, s));
+    }
     ReconArgs r{};
     r.n_sites = nb;
     r.site_ids = ids;
@@ -717,9 +751,8 @@ bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H,
     r.ex = (const float2*)c->ex.p;
     r.ytab = (const float2*)c->ytab.p;
     r.xtab = (const float2*)c->xtab.p;
-    r.H = (const float2*)H;
+    r.H = f8 ? (const float2*)c->f8H.p : (const float2*)H;
     r.W = (const uint16_t*)c->wtc.p;
-    const int Dw = round_up(geo.n_det, kRowPad);
     r.w_rows = 2 * Dw + 2 * Bpad;
     r.Xb = (const uint16_t*)c->xtc.p;
     r.x_rows = (int64_t)2 * nb * 3 * K;
@@ -730,9 +763,30 @@ bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H,
     r.side[1] = ReconSide{geo.B, Bpad, Bpad, Bpad / 128, nch, +1, (const int2*)c->hbeam.p, 2 * Dw, 3 * nb,
                           (int64_t)2 * nch * Bpad * K, (int64_t)nch * Bpad * K};
     r.err = (int*)c->errflag.p;
+    if (f8) {
+        r.f8 = 1;
+        r.inv_row[0] = (const float*)c->f8inv0.p;
+        r.inv_row[1] = (const float*)c->f8inv1.p;
+    }
     TIMED(c, BIP_STAGE_GATHER, s, bip_recon_tc(r, s));
     return BIP_OK;
 }
+
+// FP8 path: max_r |H_n| of every channel of every site and H_n divided by
+// it, once per call
+bip_status f8_hmax(bip_ctx* c, const void* H, cudaStream_t s) {
+    CUDA_TRY(c, ensure(c->f8hmax, (size_t)c->n_sites * 9 * sizeof(float), false, s));
+    const size_t K = (size_t)c->cfg.win * c->cfg.win;
+    CUDA_TRY(c, ensure(c->f8H, (size_t)c->n_ch_total * K * sizeof(float2), false, s));
+    F8HmaxArgs h{c->n_sites, (const SiteDev*)c->sites_d.p, (int)K, (const float2*)H, (float*)c->f8hmax.p,
+                 (float2*)c->f8H.p};
+    TIMED(c, BIP_STAGE_GATHER, s, bip_f8_hmax(h, s));
+    return BIP_OK;
+}
+
+// BF16 planes of the coupling output and the Gram operands: split BF16
+// keeps hi and lo (4), the mixed and FP8 paths one BF16 value (2)
+int gram_planes(int prec) { return prec == BIP_PREC_SPLIT_BF16 ? 4 : 2; }
 
 // Sites per batch of the tensor-core map path: the batch whose tile counts
 // fill whole rounds of the SMs best (the coupling, the reconstruction and
@@ -749,7 +803,7 @@ int tc_batch(const bip_ctx* c) {
             sms = 148;
         if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || l2 < 1) l2 = 64 << 20;
     }
-    const int npl = c->prec == BIP_PREC_MIXED ? 2 : 4;
+    const int npl = gram_planes(c->prec);
     const double mt_site = 2.0 * npl * c->Bpad * (double)c->nch_max * c->Dpad;   // bytes of Mt per site
     // at least 16 sites: fewer leave the Gram (a few tiles per site) without
     // enough tiles to fill the SMs
@@ -836,8 +890,12 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     const int Bpad = c->Bpad, Dpad = c->Dpad;
     const int nch = c->nch_max;
     const bool tc = c->prec != BIP_PREC_FP32;
-    // planes of the coupling and Gram operands: split BF16 (4) or BF16 (2)
-    const int npl = c->prec == BIP_PREC_MIXED ? 2 : 4;
+    // planes of the coupling and Gram operands: split BF16 (4) or BF16 (2);
+    // the FP8 coupling reads two E4M3 planes and writes BF16 for the Gram
+    const int npl = gram_planes(c->prec);
+    const bool f8 = c->prec == BIP_PREC_FP8_TILE;
+    if (f8 && !c->recon_tc)
+        return fail(c, BIP_ERR_UNSUPPORTED, "the FP8 coupling needs at most 64 parents per side");
     const int tile = kScanTile;
     const int n_tiles = (P + tile - 1) / tile;
     const int nd = (2 * c->Ky + 1) * (4 * c->Kx + 1);
@@ -885,14 +943,25 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         CUDA_TRY(c, ensure(c->mt32, SB * perMt * sizeof(float2), true, s));
     } else {
         // up to four bf16 planes per complex element: 8 bytes, as complex64
-        CUDA_TRY(c, ensure(c->opA16, SB * perA * 8, true, s));
-        CUDA_TRY(c, ensure(c->opB16, SB * perB * 8, true, s));
+        if (f8) {
+            // two E4M3 planes per complex element
+            CUDA_TRY(c, ensure(c->op8A, SB * perA * 2, true, s));
+            CUDA_TRY(c, ensure(c->op8B, SB * perB * 2, true, s));
+        } else {
+            CUDA_TRY(c, ensure(c->opA16, SB * perA * 8, true, s));
+            CUDA_TRY(c, ensure(c->opB16, SB * perB * 8, true, s));
+        }
         CUDA_TRY(c, ensure(c->mt16, SB * perMt * 8, true, s));
         if (cube_out) CUDA_TRY(c, ensure(c->mt32, SB * perMt * sizeof(float2), true, s));
         CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
     }
     CUDA_TRY(c, ensure(c->q32, SB * perQ * sizeof(float2), true, s));
     CUDA_TRY(c, ensure(c->gdiff, (size_t)SB * nd * sizeof(float2), false, s));
+
+    if (f8 && c->n_sites > 0) {
+        bip_status st = f8_hmax(c, H, s);
+        if (st != BIP_OK) return st;
+    }
 
     // work lists (site in batch, scan tile) for all batches, uploaded once
     std::vector<int32_t>& work = c->work_h;
@@ -936,7 +1005,10 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             g1.out_c64 = (float2*)c->opB32.p;
             g1.site_stride = (int64_t)perB;
         }
-        if (c->prec == BIP_PREC_MIXED && c->recon_tc) {
+        if (f8) {
+            bip_status st = recon_tc_batch(c, ids, nb, H, c->op8A.p, c->op8B.p, s);
+            if (st != BIP_OK) return st;
+        } else if (c->prec == BIP_PREC_MIXED && c->recon_tc) {
             bip_status st = recon_tc_batch(c, ids, nb, H, c->opA16.p, c->opB16.p, s);
             if (st != BIP_OK) return st;
         } else {
@@ -966,6 +1038,17 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             A.ep_B = Bpad;
             A.ep_Dp = Dpad;
             A.err = (int*)c->errflag.p;
+            if (f8) {
+                // E4M3 rows of K bytes, seen by the tensor maps as K / 2 bf16
+                A.f8 = 1;
+                A.A = TcOperand{c->op8B.p, (int64_t)SB * 2 * (int64_t)rowsB, K / 2, 2 * (int64_t)rowsB, (int64_t)rowsB};
+                A.B = TcOperand{c->op8A.p, (int64_t)SB * 2 * (int64_t)rowsA, K / 2, 2 * (int64_t)rowsA, (int64_t)rowsA};
+                A.kb = K / 64;
+                A.scaleA = (const float*)c->f8sA.p;
+                A.scaleA_site = (int64_t)rowsB;
+                A.scaleB = (const float*)c->f8sB.p;
+                A.scaleB_site = Dpad;
+            }
             if (cube_out) {
                 // per-beam values want M itself to FP32: complex64 rows (ch, b)
                 A.epi = TC_EPI_C32;
@@ -1213,13 +1296,16 @@ bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_ou
     const BipGeometry& geo = c->geo;
     const int K = g.win * g.win, Bpad = c->Bpad, Dpad = c->Dpad, nch = c->nch_max;
     const bool tc = c->prec != BIP_PREC_FP32;
-    const int npl = c->prec == BIP_PREC_MIXED ? 2 : 4;
+    const bool f8 = c->prec == BIP_PREC_FP8_TILE;
+    if (f8 && !c->recon_tc)
+        return fail(c, BIP_ERR_UNSUPPORTED, "the FP8 coupling needs at most 64 parents per side");
+    const int npl = gram_planes(c->prec);
     const size_t perA = (size_t)Dpad * K, perB = (size_t)nch * Bpad * K;
     const size_t ldc = (size_t)nch * Bpad;
-    DevBuf& opA = tc ? c->opA16 : c->opA32;
-    DevBuf& opB = tc ? c->opB16 : c->opB32;
-    CUDA_TRY(c, ensure(opA, perA * 8, true, s));
-    CUDA_TRY(c, ensure(opB, perB * 8, true, s));
+    DevBuf& opA = f8 ? c->op8A : tc ? c->opA16 : c->opA32;
+    DevBuf& opB = f8 ? c->op8B : tc ? c->opB16 : c->opB32;
+    CUDA_TRY(c, ensure(opA, perA * (f8 ? 2 : 8), true, s));
+    CUDA_TRY(c, ensure(opB, perB * (f8 ? 2 : 8), true, s));
     CUDA_TRY(c, ensure(c->partial, (size_t)Dpad * ldc * sizeof(float2), false, s));
     const int32_t* ids = (const int32_t*)c->seq_ids_d.p + site;
     GatherArgs g2 = gather_args(c, 2, ids, 1);
@@ -1236,7 +1322,11 @@ bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_ou
         g1.out_c64 = (float2*)opB.p; g1.site_stride = (int64_t)perB;
     }
     if (tc) CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
-    if (c->prec == BIP_PREC_MIXED && c->recon_tc) {
+    if (f8) {
+        bip_status st = f8_hmax(c, H, s);
+        if (st != BIP_OK) return st;
+    }
+    if ((c->prec == BIP_PREC_MIXED || f8) && c->recon_tc) {
         bip_status st = recon_tc_batch(c, ids, 1, H, opA.p, opB.p, s);
         if (st != BIP_OK) return st;
     } else {
@@ -1263,6 +1353,16 @@ bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_ou
         A.out32_ld = (int64_t)ldc;
         A.out32_trans = 1;
         A.err = (int*)c->errflag.p;
+        if (f8) {
+            A.f8 = 1;
+            A.A = TcOperand{opB.p, 2 * (int64_t)ldc, K / 2, 2 * (int64_t)ldc, (int64_t)ldc};
+            A.B = TcOperand{opA.p, 2 * (int64_t)Dpad, K / 2, 2 * (int64_t)Dpad, Dpad};
+            A.kb = K / 64;
+            A.scaleA = (const float*)c->f8sA.p;
+            A.scaleA_site = (int64_t)ldc;
+            A.scaleB = (const float*)c->f8sB.p;
+            A.scaleB_site = Dpad;
+        }
         TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(A, s));
     } else {
         CGemmArgs A{};

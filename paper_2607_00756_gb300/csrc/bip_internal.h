@@ -133,6 +133,9 @@ struct XprepArgs {
     int K;                          // window pixels
     uint16_t* X;
     XprepSide side[2];              // 0: S2 (detector), 1: S1 (aperture)
+    // FP8 path: largest |dt_p(r)| over the window of each parent, as float
+    // bits, [2 sides][n_sites][64] (cleared by the caller); null: not taken
+    unsigned* pmax;
 };
 cudaError_t bip_xprep(const XprepArgs& a, cudaStream_t s);
 
@@ -168,8 +171,41 @@ struct ReconArgs {
     uint16_t* out[2];               // coupling operands (2 bf16 planes each)
     ReconSide side[2];
     int* err;                       // set to 1 on a device timeout
+    // FP8 path: the operands are E4M3 bytes (out[] then holds bytes, same
+    // element strides), each row scaled by inv_row[side][bs rows_pad + t];
+    // H is then H_n / max_r |H_n| (F8HmaxArgs::Hs)
+    int f8;
+    const float* inv_row[2];
 };
 cudaError_t bip_recon_tc(const ReconArgs& a, cudaStream_t s);
+
+// fp8.cu : per-window scales of the E4M3 coupling operands.  For target t
+// of a side, bound_t = kappa sum_p w_tp pmax_p (kappa = 1 + 2^-6; w = the
+// hi + lo BF16 weights of the W tensor); S1 rows are further scaled by
+// max_r |H_n(r)| of their channel.
+struct F8HmaxArgs {
+    int n_sites;                    // all sites of the context
+    const SiteDev* sites;
+    int K;
+    const float2* H;                // [sum nch][K]
+    float* hmax;                    // [n_sites][9]: max_r |H_n(r)| (0 past the site's channels)
+    float2* Hs;                     // [sum nch][K]: H_n / max_r |H_n| (0 where the max is 0)
+};
+cudaError_t bip_f8_hmax(const F8HmaxArgs& a, cudaStream_t s);
+struct F8ScaleArgs {
+    int n_sites;                    // sites of the batch
+    const int32_t* site_ids;
+    const SiteDev* sites;
+    int nch;                        // channel planes of the S1 operand
+    const float* hmax;              // of F8HmaxArgs, by site id
+    const uint16_t* W;              // [w_rows][64] bf16
+    int w_row0[2], w_pad[2], n_targets[2], rows_pad[2];
+    const unsigned* pmax;           // [2][n_sites][64] (float bits)
+    float* inv_row[2];              // [n_sites][rows_pad[side]]: 448 / bound (0 for empty rows)
+    float* scaleB;                  // S2 rows: [n_sites][rows_pad[0]] bound / 448
+    float* scaleA;                  // S1 rows (ch, b): [n_sites][nch rows_pad[1]] max|H_n| bound / 448
+};
+cudaError_t bip_f8_scales(const F8ScaleArgs& a, cudaStream_t s);
 
 // gemm_simt.cu : FP32 complex GEMMs, C[m][n] = sum_k op(A[m][k]) B[n][k]
 struct CGemmArgs {
@@ -240,6 +276,13 @@ struct TcArgs {
     int n_cols;                     // B rows per site in use: the last tile has
                                     // n_cols - (nt_per - 1) N columns (multiple of 16)
     int conjA;
+    // E4M3 operands (kind::f8f6f4): rows of 2 k bytes, seen by the tensor
+    // maps as k bf16; the products are scaled by scaleA[site][row] and
+    // scaleB[site][column] in the epilogue
+    int f8;
+    const float* scaleA;
+    const float* scaleB;
+    int64_t scaleA_site, scaleB_site;
     // Hermitian output: tiles entirely below the diagonal are skipped
     int tri;
     // ROWS epilogue: A row r = (ch, b) = (r / ep_B, r % ep_B), output column n

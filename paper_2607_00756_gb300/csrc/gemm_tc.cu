@@ -1,5 +1,5 @@
 // Complex contractions on the 5th-generation tensor cores (tcgen05.mma,
-// TMEM accumulators, TMA operand staging), in split BF16 or BF16.
+// TMEM accumulators, TMA operand staging), in split BF16, BF16 or E4M3.
 //
 // Split BF16: every complex FP32 operand is stored as four BF16 planes,
 // x = hi + lo with hi = bf16(x), lo = bf16(x - hi), for the real and the
@@ -9,7 +9,9 @@
 //   Re += Ar Br -/+ Ai Bi,   Im += Ar Bi +/- Ai Br     (-/+: op(A) = A / conj A)
 // -- twelve MMAs per K step into two accumulators, the signs carried by the
 // instruction descriptor's negate-A bit.  BF16: two planes (re, im), one
-// product per real product, four MMAs per K step.
+// product per real product, four MMAs per K step.  E4M3 (kind::f8f6f4):
+// as BF16 with 64 values per 64-byte row, each operand row carrying one
+// scale (its 64x64 window) that the epilogue applies to the FP32 sums.
 //
 // Kernel: persistent, one CTA per SM, 192 threads:
 //   warp 0      TMA producer (one elected thread): 4 A planes + 4 B planes
@@ -70,7 +72,7 @@ struct TcShape {
     static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256;
 };
 
-template <int N, int EPI, int NPL>
+template <int N, int EPI, int NPL, bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const __grid_constant__ CUtensorMap mapBt, const TcArgs p) {
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer
-            uint32_t id_pos = idesc(128, N, false), id_neg = idesc(128, N, true);
+            uint32_t id_pos = 0, id_neg = 0;
             int s = 0, a = 0;
             uint32_t ph = 0, aph = 0;
             bool any = false, ok = true;
@@ -182,8 +184,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                id_pos = idesc(128, u.nc, false);
-                id_neg = idesc(128, u.nc, true);
+                id_pos = F8 ? idesc_e4m3(128, u.nc, false) : idesc(128, u.nc, false);
+                id_neg = F8 ? idesc_e4m3(128, u.nc, true) : idesc(128, u.nc, true);
                 const uint32_t id_ii = p.conjA ? id_pos : id_neg;   // sign of Ai*Bi in Re
                 const uint32_t id_ir = p.conjA ? id_neg : id_pos;   // sign of Ai*Br in Im
                 const uint32_t dr = tbase + (uint32_t)(a * 2 * N), di = dr + N;
@@ -220,6 +222,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                             mma(di, ad[2], bd[0], id_ir, 1);
                             mma(di, ad[2], bd[1], id_ir, 1);
                             mma(di, ad[3], bd[0], id_ir, 1);
+                        } else if (F8) {
+                            // planes: 0 re, 1 im; K = 32 E4M3 per MMA
+                            mma_f8(dr, ad[0], bd[0], id_pos, first);
+                            mma_f8(dr, ad[NPL - 1], bd[NPL - 1], id_ii, 1);
+                            mma_f8(di, ad[0], bd[NPL - 1], id_pos, first);
+                            mma_f8(di, ad[NPL - 1], bd[0], id_ir, 1);
                         } else {
                             // planes: 0 re, 1 im
                             mma(dr, ad[0], bd[0], id_pos, first);
@@ -271,12 +279,28 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const int row = u.mt * 128 + q * 32 + lane;      // accumulator row of this thread
             const uint32_t tr = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * 2 * N);
+            float sa = 1.f;                                  // F8: the row's scale
+            if (F8) sa = __ldg(&p.scaleA[(int64_t)u.bs * p.scaleA_site + row]);
             for (int c0 = 0; c0 < u.nc; c0 += 16) {
                 float vr[16], vi[16];
                 tmem_ld16(tr + c0, vr);
                 tmem_ld16(tr + N + c0, vi);
                 tmem_ld_wait();
                 const int n0 = u.nt * p.N + c0;                   // first output column
+                if (F8) {
+                    // the same 16 column scales for every lane (broadcast loads)
+                    const float4* sb = reinterpret_cast<const float4*>(p.scaleB + (int64_t)u.bs * p.scaleB_site + n0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float4 s4 = __ldg(&sb[j]);
+                        const float s[4] = {s4.x * sa, s4.y * sa, s4.z * sa, s4.w * sa};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            vr[4 * j + k] *= s[k];
+                            vi[4 * j + k] *= s[k];
+                        }
+                    }
+                }
                 if (EPI == TC_EPI_ROWS) {
                     // A row (ch, b) -> Mt[b][ch * Dp + n]: 16 consecutive columns
                     const int ch = row / p.ep_B, b = row % p.ep_B;
@@ -332,27 +356,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <int N, int EPI, int NPL>
+template <int N, int EPI, int NPL, bool F8>
 cudaError_t launch(const TcArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mbt, int grid,
                    cudaStream_t s) {
     constexpr size_t smem = TcShape<N, NPL>::SMEM;
     static bool attr = false;
     if (!attr) {
         cudaError_t e =
-            cudaFuncSetAttribute(tc_kernel<N, EPI, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(tc_kernel<N, EPI, NPL, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    tc_kernel<N, EPI, NPL><<<grid, kThreads, smem, s>>>(ma, mb, mbt, a);
+    tc_kernel<N, EPI, NPL, F8><<<grid, kThreads, smem, s>>>(ma, mb, mbt, a);
     return cudaGetLastError();
 }
 
-template <int EPI, int NPL>
+template <int EPI, int NPL, bool F8 = false>
 cudaError_t launch_n(const TcArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mbt, int grid,
                      cudaStream_t s) {
     // the template width bounds the shared-memory and TMEM layout; the tile
     // width a.N (a multiple of 16) may be smaller
-    return a.N > 128 ? launch<256, EPI, NPL>(a, ma, mb, mbt, grid, s) : launch<128, EPI, NPL>(a, ma, mb, mbt, grid, s);
+    return a.N > 128 ? launch<256, EPI, NPL, F8>(a, ma, mb, mbt, grid, s)
+                     : launch<128, EPI, NPL, F8>(a, ma, mb, mbt, grid, s);
 }
 
 }  // namespace
@@ -383,6 +408,16 @@ cudaError_t bip_tc_gemm(const TcArgs& a, cudaStream_t s) {
     const int units = a.n_sites * a.mt_per * a.nt_per;
     const int grid = units < num_sms() ? units : num_sms();
     const bool split = a.npl == 4;
+    if (a.f8) {
+        // E4M3: two planes (re, im), per-row scales in the epilogue
+        if (split || a.conjA || !a.scaleA || !a.scaleB) return cudaErrorInvalidValue;
+        if (((uintptr_t)a.scaleB | (size_t)a.scaleB_site * 4 | (size_t)a.N * 4) % 16) return cudaErrorMisalignedAddress;
+        switch (a.epi) {
+            case TC_EPI_ROWS: return launch_n<TC_EPI_ROWS, 2, true>(a, ma, mb, mbt, grid, s);
+            case TC_EPI_C32: return launch_n<TC_EPI_C32, 2, true>(a, ma, mb, mbt, grid, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (a.epi) {
         case TC_EPI_ROWS: return split ? launch_n<TC_EPI_ROWS, 4>(a, ma, mb, mbt, grid, s)
                                        : launch_n<TC_EPI_ROWS, 2>(a, ma, mb, mbt, grid, s);

@@ -24,7 +24,9 @@
 //                warp and tile; magnitude preservation, re-tilt stepped
 //                along the window row in four independent chains, H_n
 //                (staged per tile in shared memory) products, 16 bf16
-//                stored per thread as one 32-byte sector
+//                stored per thread as one 32-byte sector -- or, for the FP8
+//                coupling, 16 E4M3 bytes, the row scale folded into the
+//                magnitude factor (H_n comes pre-divided by its maximum)
 // Work unit: (side, site in batch, 128-target tile, chunk of up to 1024
 // pixels).  Every wait is bounded; on a timeout the kernel sets *err, stops,
 // drains the copies and MMAs it issued and frees TMEM.
@@ -71,6 +73,19 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// four E4M3 bytes (satfinite, nearest-even), a in the lowest byte
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+    uint16_t lo, hi;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b), "f"(a));
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(d), "f"(c));
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+__device__ __forceinline__ void st_v4(void* p, const uint32_t (&v)[4]) {
+    asm volatile("st.global.v4.b32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
     uint32_t r[8];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -80,6 +95,9 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// F8: the operands are written as E4M3 bytes, row t scaled by
+// inv_row[side][t] and channel n by inv_h[n] (per-window scales)
+template <bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
     recon_tc_kernel(const __grid_constant__ CUtensorMap mapW, const __grid_constant__ CUtensorMap mapX,
                     const ReconArgs a) {
@@ -303,7 +321,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     Z.y = -Z.y;
                 }
             }
-            uint16_t* out = a.out[u.side] + (size_t)u.bs * sd.site_stride + (size_t)t * a.K;
+            // output element offset of this row (bf16 or E4M3 elements)
+            const size_t out_off = (size_t)u.bs * sd.site_stride + (size_t)t * a.K;
+            float ir = 1.f;                                    // F8: 448 / bound of this row
+            if (F8 && valid) ir = __ldg(&a.inv_row[u.side][(size_t)u.bs * sd.rows_pad + t]);
             const size_t ch_stride = (size_t)sd.rows_pad * a.K;
             const float2* Hs = a.H + (size_t)st.ch_off * a.K;
             const int nh = sd.nch * 16;                       // H_n values of a warp per tile
@@ -363,38 +384,68 @@ __global__ void __launch_bounds__(kThreads, 1)
                             float2 v;
                             if (a.magnitude) {
                                 const float m2 = fmaf(vr[k], vr[k], vi[k] * vi[k]);
-                                const float sc = vm[k] * rsqrtf(fmaxf(m2, 1.17549435e-38f));
-                                v = make_float2(m2 > 0.f ? vr[k] * sc : vm[k], vi[k] * sc);
+                                const float mk = F8 ? vm[k] * ir : vm[k];
+                                const float sc = mk * rsqrtf(fmaxf(m2, 1.17549435e-38f));
+                                v = make_float2(m2 > 0.f ? vr[k] * sc : mk, vi[k] * sc);
                             } else {
-                                v = make_float2(vr[k], vi[k]);
+                                v = F8 ? make_float2(vr[k] * ir, vi[k] * ir) : make_float2(vr[k], vi[k]);
                             }
                             S[k] = c_mul(v, tc[c]);
                             tc[c] = c_mul(tc[c], sx1);
                         }
                     }
-                    uint16_t* o = out + px;
-                    for (int n = 0; n < nrep; ++n) {
-                        uint32_t re[8], im[8];
-                        if (sd.nch > 0) {
-                            const float4* hp = reinterpret_cast<const float4*>(hw + n * 16);
+                    if constexpr (F8) {
+                        uint8_t* o = (uint8_t*)a.out[u.side] + out_off + px;
+                        for (int n = 0; n < nrep; ++n) {
+                            uint32_t re[4], im[4];
+                            if (sd.nch > 0) {
+                                const float4* hp = reinterpret_cast<const float4*>(hw + n * 16);
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const float4 hq = hp[j];
-                                const float2 o0 = c_mul(make_float2(hq.x, hq.y), S[2 * j]);
-                                const float2 o1 = c_mul(make_float2(hq.z, hq.w), S[2 * j + 1]);
-                                re[j] = pack2(o0.x, o1.x);
-                                im[j] = pack2(o0.y, o1.y);
-                            }
-                        } else {
+                                for (int j = 0; j < 4; ++j) {
+                                    const float4 h0 = hp[2 * j], h1 = hp[2 * j + 1];
+                                    const float2 e0 = c_mul(make_float2(h0.x, h0.y), S[4 * j]);
+                                    const float2 e1 = c_mul(make_float2(h0.z, h0.w), S[4 * j + 1]);
+                                    const float2 e2 = c_mul(make_float2(h1.x, h1.y), S[4 * j + 2]);
+                                    const float2 e3 = c_mul(make_float2(h1.z, h1.w), S[4 * j + 3]);
+                                    re[j] = pack_e4m3x4(e0.x, e1.x, e2.x, e3.x);
+                                    im[j] = pack_e4m3x4(e0.y, e1.y, e2.y, e3.y);
+                                }
+                            } else {
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                re[j] = pack2(S[2 * j].x, S[2 * j + 1].x);
-                                im[j] = pack2(S[2 * j].y, S[2 * j + 1].y);
+                                for (int j = 0; j < 4; ++j) {
+                                    re[j] = pack_e4m3x4(S[4 * j].x, S[4 * j + 1].x, S[4 * j + 2].x, S[4 * j + 3].x);
+                                    im[j] = pack_e4m3x4(S[4 * j].y, S[4 * j + 1].y, S[4 * j + 2].y, S[4 * j + 3].y);
+                                }
                             }
+                            st_v4(o, re);
+                            st_v4(o + sd.plane_stride, im);
+                            o += ch_stride;
                         }
-                        st_v8(o, re);
-                        st_v8(o + sd.plane_stride, im);
-                        o += ch_stride;
+                    } else {
+                        uint16_t* o = a.out[u.side] + out_off + px;
+                        for (int n = 0; n < nrep; ++n) {
+                            uint32_t re[8], im[8];
+                            if (sd.nch > 0) {
+                                const float4* hp = reinterpret_cast<const float4*>(hw + n * 16);
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) {
+                                    const float4 hq = hp[j];
+                                    const float2 o0 = c_mul(make_float2(hq.x, hq.y), S[2 * j]);
+                                    const float2 o1 = c_mul(make_float2(hq.z, hq.w), S[2 * j + 1]);
+                                    re[j] = pack2(o0.x, o1.x);
+                                    im[j] = pack2(o0.y, o1.y);
+                                }
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) {
+                                    re[j] = pack2(S[2 * j].x, S[2 * j + 1].x);
+                                    im[j] = pack2(S[2 * j].y, S[2 * j + 1].y);
+                                }
+                            }
+                            st_v8(o, re);
+                            st_v8(o + sd.plane_stride, im);
+                            o += ch_stride;
+                        }
                     }
                     // tilt at this warp's first pixel of the next tile
                     F = c_mul(F, X64);
@@ -428,6 +479,7 @@ __global__ void __launch_bounds__(kPrepThreads) xprep_kernel(XprepArgs a) {
     const int site = a.site_ids[bs];
     const int px0 = blockIdx.x * 64;
     const float2* src = sd.stash + (size_t)site * sd.Bp * a.K + px0;
+    // (FP8 path: the parents' window maxima are taken from the same tile)
     // 16 loads per thread in flight at once (parents p = i / 64, pixels i % 64)
     float2 v[16];
 #pragma unroll
@@ -441,6 +493,21 @@ __global__ void __launch_bounds__(kPrepThreads) xprep_kernel(XprepArgs a) {
         s[i >> 6][i & 63] = v[r];
     }
     __syncthreads();
+    if (a.pmax) {
+        // four threads per parent, 16 pixels each
+        const int p = threadIdx.x >> 2, x0 = (threadIdx.x & 3) * 16;
+        float m = 0.f;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const float2 e = s[p][x0 + j];
+            m = fmaxf(m, sqrtf(e.x * e.x + e.y * e.y));
+        }
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+        // non-negative floats order like their bit patterns
+        if ((threadIdx.x & 3) == 0 && p < sd.Bp && m > 0.f)
+            atomicMax(&a.pmax[((size_t)side * a.n_sites + bs) * 64 + p], __float_as_uint(m));
+    }
     // thread: one pixel (lane) and eight consecutive parents, for one plane
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;   // 8 warps
     uint16_t* dst = a.X + ((size_t)(sd.x_site0 + bs * 3) * a.K + px0) * 64;
@@ -491,14 +558,19 @@ cudaError_t bip_recon_tc(const ReconArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     e = make_map_2d(&mx, a.Xb, a.x_rows, 64, kN);
     if (e != cudaSuccess) return e;
-    static bool attr = false;
-    if (!attr) {
-        e = cudaFuncSetAttribute(recon_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (a.f8 && (!a.inv_row[0] || !a.inv_row[1])) return cudaErrorInvalidValue;
+    static bool attr[2] = {false, false};
+    if (!attr[a.f8 ? 1 : 0]) {
+        e = a.f8 ? cudaFuncSetAttribute(recon_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem)
+                 : cudaFuncSetAttribute(recon_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[a.f8 ? 1 : 0] = true;
     }
     const int units = a.n_sites * (a.side[0].mt_tiles + a.side[1].mt_tiles) * a.chunks;
     const int grid = units < num_sms() ? units : num_sms();
-    recon_tc_kernel<<<grid, kThreads, kSmem, s>>>(mw, mx, a);
+    if (a.f8)
+        recon_tc_kernel<true><<<grid, kThreads, kSmem, s>>>(mw, mx, a);
+    else
+        recon_tc_kernel<false><<<grid, kThreads, kSmem, s>>>(mw, mx, a);
     return cudaGetLastError();
 }

@@ -1,7 +1,8 @@
 // Building blocks of the tcgen05 kernels: bounded mbarrier waits, TMA 2-D
 // loads, shared-memory matrix descriptors for 64-byte-swizzled K-major
 // tiles, the kind::f16 instruction descriptor, MMA issue and commit, TMEM
-// loads, and the host-side tensor-map encoding.
+// loads, and the host-side tensor-map encoding.  E4M3 operands use the
+// same tiles: a 64-byte row holds 64 E4M3 values instead of 32 BF16.
 #pragma once
 
 #include <cuda.h>
@@ -93,6 +94,20 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+// kind::f8f6f4 instruction descriptor: E4M3 x E4M3 -> F32 (type code 0 for
+// both operands), both K-major; same field layout as idesc()
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N, bool negA) {
+    return (1u << 4) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// one MMA of K = 32 E4M3 values (32 bytes of each operand row, like K = 16
+// for BF16, so the descriptors step through a stage the same way)
+__device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
         "l"(a), "l"(b), "r"(id), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {

@@ -7,7 +7,8 @@ the S1 and S2 sweeps are checked over their whole depth -- on every 8th scan
 of each axis (16x16 probes).  Properties that hold at any size are checked
 on the whole output: the map is the FP64 sum of the per-site
 contributions, each contribution is zero outside its crop mask, and the
-mixed-precision map lies within 1e-3 relative L2 of the FP32 map.
+mixed-precision map lies within 1e-3 relative L2 of the FP32 map (the FP8
+map within 3%).
 Tolerances: rel L2 <= 1e-4 for FP32, <= 1e-3 for the mixed path."""
 import numpy as np
 import pytest
@@ -38,7 +39,7 @@ def full():
     V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
     H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
     out = {}
-    for prec in ("mixed", "fp32"):
+    for prec in ("mixed", "fp8", "fp32"):
         ctx = BipContext(cfg, prec=prec)
         ctx.build(V, sp.atoms, sp.nch)
         m = ctx.map(H, sp.scans).cpu().numpy()
@@ -97,7 +98,7 @@ def test_fullsize_sampled_sites_match_oracle(full, oracle_sample, prec, tol):
 def test_fullsize_map_is_the_site_sum(full):
     """Any size: the map is the FP64 sum of the per-site contributions."""
     _, _, out = full
-    for prec in ("mixed", "fp32"):
+    for prec in ("mixed", "fp8", "fp32"):
         m, parts = out[prec]
         want = parts.astype(np.float64).sum(axis=0)
         assert np.max(np.abs(m - want)) <= 1e-9 * np.max(np.abs(want)), prec
@@ -110,7 +111,7 @@ def test_fullsize_zero_outside_crop(full):
     rng = np.random.default_rng(7)
     for k in rng.choice(len(sp.ionized), size=16, replace=False):
         outside = ~obip.crop_mask(pr, k, sp.scans)
-        for prec in ("mixed", "fp32"):
+        for prec in ("mixed", "fp8", "fp32"):
             assert np.all(out[prec][1][k][outside] == 0.0)
 
 
@@ -119,3 +120,12 @@ def test_fullsize_mixed_within_1e3_of_fp32(full):
     relative L2 of the FP32 map on the whole 128x128 raster."""
     _, _, out = full
     assert rel(out["mixed"][0], out["fp32"][0]) < 1e-3
+
+
+def test_fullsize_fp8_near_fp32(full):
+    """The FP8 coupling's map on the whole raster: within 3% relative L2 of
+    the FP32 map (about four times the E4M3 model's 0.7% at config 1; the
+    figure is reported by the benchmark), and not equal to it."""
+    _, _, out = full
+    e = rel(out["fp8"][0], out["fp32"][0])
+    assert 1e-5 < e < 3e-2, e

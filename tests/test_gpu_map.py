@@ -242,3 +242,87 @@ def test_qeels_config1(lib, c1, axis):
     q = q.cpu().numpy()
     assert rel(q, want) < 1e-4
     assert rel(q.astype(np.float64).sum(axis=1), m) < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# FP8 (E4M3) coupling with per-window scales (config 3's FP8 form)
+
+def _fp8_model(pr):
+    from oracle import fp8
+    return fp8.bip_map_fp8(pr)
+
+
+def test_map_fp8_config1(lib, c1):
+    """The FP8 map against the FP64 map and against the oracle's FP8 model
+    (E4M3 operands with the same per-window scale rule, contracted in FP64).
+    The GPU's error may exceed the model's only by what its BF16
+    reconstruction and Gram add on top (<= 1e-3, the mixed path's bound):
+    bounded here by twice the model's error plus 1e-3.  Its distance to
+    the model comes from E4M3 codes that differ by one step where the two
+    pre-quantization values (BF16- vs FP64-reconstructed) straddle a
+    rounding boundary, and stays below the model's own error."""
+    cfg, sp, pr, ref = c1
+    model = _fp8_model(pr)
+    e_model = rel(model.map, ref.map)
+    _, m, parts, _ = gpu_run(lib, cfg, sp, prec="fp8")
+    e_gpu = rel(m, ref.map)
+    assert 0.0 < e_gpu < 2.0 * e_model + 1e-3, (e_gpu, e_model)
+    assert rel(m, model.map) < e_model, (rel(m, model.map), e_model)
+    assert rel(parts, model.partials) < 2.0 * e_model
+    for k in range(len(pr.ion)):
+        assert np.all(parts[k][~obip.crop_mask(pr, k, pr.scans)] == 0.0)
+
+
+def test_coupling_fp8_config1(lib, c1):
+    """M^(n) of every site from the FP8 coupling against the oracle's FP8
+    model of the same contraction and against the FP64 coupling."""
+    from oracle import fp8
+    cfg, sp, pr, ref = c1
+    geo = pr.geo
+    ctx, _, _, H = gpu_run(lib, cfg, sp, prec="fp8")
+    for k in range(len(pr.ion)):
+        st = ref.stages[k]
+        want8 = fp8.site_coupling_fp8(st["S2w"], pr.H[k], st["S1w"], geo.w2, st["stash2"], geo.w1, st["stash1"])
+        e_model = rel(want8, st["M"])
+        got = ctx.coupling(H, k).cpu().numpy()
+        assert got.shape == st["M"].shape
+        assert rel(got, st["M"]) < 2.0 * e_model + 1e-3, (k, rel(got, st["M"]), e_model)
+        assert rel(got, want8) < e_model, (k, rel(got, want8), e_model)
+
+
+def test_map_fp8_edge_cases(lib):
+    cfg, sp = _edge_specimen()
+    pr = obip.make_problem(sp)
+    ref = obip.bip_map(pr)
+    e_model = rel(_fp8_model(pr).map, ref.map)
+    _, m, parts, _ = gpu_run(lib, cfg, sp, prec="fp8")
+    assert rel(m, ref.map) < 2.0 * e_model + 1e-3
+    for k in range(len(pr.ion)):
+        assert np.all(parts[k][~obip.crop_mask(pr, k, pr.scans)] == 0.0)
+
+
+def test_map_fp8_anisotropic(lib):
+    """32x32 windows (K = 1024), f_y != f_x, a non-square grid."""
+    cfg = synth.config1().replace(name="aniso", ny=64, nx=128, ly=7.5, lx=10.0, cells_y=3, cells_x=4,
+                                  fy=1, fx=2, win=32, ion_cells=(1, 3), ion_slices=(1, 4),
+                                  scan_y=(10.3, 3.5, 9), scan_x=(20.7, 6.25, 7))
+    sp = synth.make_specimen(cfg)
+    pr = obip.make_problem(sp)
+    ref = obip.bip_map(pr)
+    e_model = rel(_fp8_model(pr).map, ref.map)
+    _, m, _, _ = gpu_run(lib, cfg, sp, prec="fp8")
+    assert rel(m, ref.map) < 2.0 * e_model + 1e-3
+
+
+def test_cube_fp8_config1(lib, c1):
+    """The cube through the FP8 coupling against the FP64 cube, bounded like
+    the map by twice the FP8 model's own error (per detector beam); its
+    detector sum is the FP8 map."""
+    from oracle import fp8
+    cfg, sp, pr, ref = c1
+    want = obip.bip_cube(pr)
+    e_model = rel(fp8.bip_cube_fp8(pr), want)
+    ctx, m, _, H = gpu_run(lib, cfg, sp, prec="fp8")
+    cube = ctx.cube(H, sp.scans).cpu().numpy()
+    assert rel(cube, want) < 2.0 * e_model + 1e-3, (rel(cube, want), e_model)
+    assert rel(cube.astype(np.float64).sum(axis=1), m) < 1e-4
