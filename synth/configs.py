@@ -40,7 +40,7 @@ class Config:
     jitter: float = 0.05
     seed: int = 0
     # ionization: (slice range [s0, s1), cell range [c0, c1) on both axes)
-    ion_slices: Tuple[int, int] = (2, 3)
+    ion_slices: Tuple[int, ...] = (2, 3)        # (first, end[, stride])
     ion_cells: Tuple[int, int] = (1, 3)
     channels: Tuple[int, ...] = (-1, 0, 1)
     phi_sigma: float = 0.5
@@ -92,6 +92,21 @@ def config3() -> Config:
     return config1().replace(name="config3", prec="split_bf16")
 
 
+def config5() -> Config:
+    """Differentiation workload: 8x8 cells (20x20 A), 256^2 grid, 40 slices of
+    2 A, 200 keV, 20 mrad, f=2; 64 ionized sites (the central 4x4 cells at
+    four depths) with three channels; 32x32 scans at 2 px over the central
+    8x8 A.  The loss is the L2 distance of the map to a seeded perturbed
+    target."""
+    return Config(
+        name="config5", ny=256, nx=256, ly=20.0, lx=20.0, nz=40, dz=2.0,
+        e0=200e3, alpha=0.020, theta_det=0.040, fy=2, fx=2,
+        nrad1=2, nrad2=2, win=64, cells_y=8, cells_x=8,
+        ion_slices=(8, 40, 8), ion_cells=(2, 6),
+        scan_y=(96.0, 2.0, 32), scan_x=(96.0, 2.0, 32),
+        oracle_scan_y=(96.0, 2.0, 32), oracle_scan_x=(96.0, 2.0, 32))
+
+
 def tiny_config(**kw) -> Config:
     """A 2x2-cell (5x5 A) specimen on a 32^2 grid with 3 slices, used by the
     brute-force checks; f=1 and a window covering the whole grid."""
@@ -104,4 +119,4 @@ def tiny_config(**kw) -> Config:
     return base.replace(**kw)
 
 
-CONFIGS = {"config1": config1, "config2": config2, "config3": config3}
+CONFIGS = {"config1": config1, "config2": config2, "config3": config3, "config5": config5}

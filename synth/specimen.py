@@ -7,7 +7,8 @@ Recipe (shared by every workload):
   * projected potential of each atom: peak * exp(-d^2 / (2 s^2)) [V*A],
     d the minimum-image distance, sampled at pixel corners r = (i dy, j dx),
     truncated at 10 s (the neglected tail is below 1e-21 of the peak);
-  * ionized sites: the atoms whose slice lies in ion_slices and whose cell
+  * ionized sites: the atoms whose slice lies in ion_slices = (s0, s1[,
+    stride]) -- s0 <= s < s1, every stride-th slice from s0 -- and whose cell
     lies in ion_cells on both axes, each with the channels m in `channels`;
   * transition potential of channel m, sampled on the atom's window:
     phi_m(d) = exp(-|d|^2 / (2 sp^2)) * ((d_x + i m d_y) / r0)^|m|,
@@ -79,11 +80,12 @@ def _potential(cfg: Config, atoms: np.ndarray) -> np.ndarray:
 
 def _ionized_mask(cfg: Config, n_atoms: int) -> np.ndarray:
     nch = np.zeros(n_atoms, dtype=np.int32)
+    stride = cfg.ion_slices[2] if len(cfg.ion_slices) > 2 else 1
     k = 0
     for s in range(cfg.nz):
         for cy in range(cfg.cells_y):
             for cx in range(cfg.cells_x):
-                if (cfg.ion_slices[0] <= s < cfg.ion_slices[1]
+                if (cfg.ion_slices[0] <= s < cfg.ion_slices[1] and (s - cfg.ion_slices[0]) % stride == 0
                         and cfg.ion_cells[0] <= cy < cfg.ion_cells[1]
                         and cfg.ion_cells[0] <= cx < cfg.ion_cells[1]):
                     nch[k] = len(cfg.channels)
