@@ -204,6 +204,39 @@ bip_status bip_qeels_bins(const bip_ctx* ctx, int32_t axis, int32_t* n_bins, int
 bip_status bip_coreloss_qeels(bip_ctx* ctx, const void* H, const double* scan_px, int32_t P,
                               int32_t axis, float* qeels_out, void* stream);
 
+/* Model parameters of the map beyond the specimen (for fitting; Sec. 5
+ * names the matrices as a forward model for simulation-constrained
+ * reconstruction).
+ * bip_set_occupancy: per-site occupancies o_tau weighting the site sum,
+ *   I = sum_tau o_tau I_tau (Eq. map-sum); occ: host float64 [n_sites] in the
+ *   order of the built sites, or NULL for all 1.  Kept until the next build
+ *   with another site list.  BIP_ERR_INVALID_ARG before a build or for a
+ *   non-finite value.
+ * bip_set_aberrations: probe defocus and Cs (Angstrom) of Psi(h) =
+ *   exp(-i chi), chi = pi lambda df |q|^2 + (pi/2) Cs lambda^3 |q|^4, for
+ *   the following maps (the matrices do not depend on them). */
+bip_status bip_set_occupancy(bip_ctx* ctx, const double* occ);
+bip_status bip_set_aberrations(bip_ctx* ctx, double defocus, double cs, void* stream);
+
+/* Reverse pass of a scalar loss L of the map: given g = dL/dI(rho) on the
+ * scans, the derivatives at the context's current state (occupancies,
+ * aberrations, built matrices):
+ *   d_occ [n_sites] float64 device: dL/do_tau = sum_rho g I_tau;
+ *   d_H   H's layout, complex64 device: dL/dRe H + i dL/dIm H of every
+ *         channel sample (for transition amplitudes a with H = a H0:
+ *         dL/dRe a + i dL/dIm a = sum_r d_H(r) conj(H0(r)));
+ *   d_aberr [2] float64 host: dL/d defocus, dL/d Cs.
+ * Any output may be NULL (not computed).  Steps: R_tau = f_y f_x o_tau
+ * sum_{rho in crop} g c c^H; Mbar = M R; dL/dH_n(r) = 2 sum_{d,b}
+ * Mbar_n(d,b) conj(S2_d(r) S1_b(r)); dL/dtheta = -2 sum_b chi'_b Im
+ * sum_tau (Q_tau R_tau)_bb -- the contractions in FP32 on every precision;
+ * d_occ uses the context's precision for I_tau.
+ *   dL_dI [P] float64 device; other requirements as bip_coreloss_map;
+ *   d_H 8-byte aligned.  Synchronises the stream when d_aberr is given. */
+bip_status bip_coreloss_grad(bip_ctx* ctx, const void* H, const double* scan_px, int32_t P,
+                             const double* dL_dI, double* d_occ, void* d_H, double* d_aberr,
+                             void* stream);
+
 /* Stage access for validation.
  * bip_copy_stash: the de-tilted parent windows of one site, which = 1 (S1,
  *   [Bp1, win, win]) or 2 (S2, [Bp2, win, win]) complex64, to device `out`.

@@ -174,9 +174,10 @@ def loss(prob, params, target, scans=None, mode=None):
     return float(np.sum((I - target) ** 2))
 
 
-def gradients(prob, params, target=None, scans=None, mode=None, dL_dI=None):
+def gradients(prob, params, target=None, scans=None, mode=None, dL_dI=None, want_V=True):
     """dL/d(occ, amp, H, defocus, cs, V) by the reverse pass in the module
-    header.  Returns (L or None, dict); complex entries are dL/dRe + i dL/dIm."""
+    header (without want_V, the sweeps' reverse pass is skipped and "V" is
+    absent).  Returns (L or None, dict); complex entries are dL/dRe + i dL/dIm."""
     cfg, geo = prob.cfg, prob.geo
     scans = prob.scans if scans is None else np.asarray(scans, dtype=np.float64)
     I, fw = forward(prob, params, scans, mode, keep=True)
@@ -223,6 +224,8 @@ def gradients(prob, params, target=None, scans=None, mode=None, dL_dI=None):
         w = cfg.win
         out["amp"][k, :nch] = 2.0 * np.sum(Hbar * np.conj(Hk.reshape(nch, -1)), axis=1)
         out["H"].append((2.0 * np.conj(params.amp[k, :nch, None]) * Hbar).reshape(nch, w, w))
+        if not want_V:
+            continue
         # back through the reconstructions and the window crops
         dt1bar = _recon_adjoint(S1bar.reshape(geo.B, w, w), s["dt1"], geo.w1, s["p1"], mode)
         dt2bar = _recon_adjoint(S2bar.reshape(geo.n_det, w, w), s["dt2"], geo.w2, s["p2"], mode)
@@ -237,6 +240,8 @@ def gradients(prob, params, target=None, scans=None, mode=None, dL_dI=None):
                 np.add.at(inj[i][p], (yy, xx), gw[p])
     for name in ("defocus", "cs"):
         out[name] = float(-2.0 * np.sum(fw["dchi"][name] * np.imag(D)))
+    if not want_V:
+        return L, out
     # slice potentials: the two sweeps backwards
     sigma = prob.sigma
     T, psi, x = fw["T"], fw["psi"], fw["x"]

@@ -68,6 +68,9 @@ def _load():
         "bip_set_profiling": [VP, I32],
         "bip_build_s1_noalloc": [VP, VP, P(BipAtom), I32, VP, VP],
         "bip_get_profile": [VP, VP, VP],
+        "bip_set_occupancy": [VP, P(D)],
+        "bip_set_aberrations": [VP, D, D, VP],
+        "bip_coreloss_grad": [VP, VP, P(D), I32, VP, VP, VP, P(D), VP],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -264,6 +267,33 @@ def bip_site_coupling(ctx, H, site, out, stream=None):
     _check("bip_site_coupling", ctx, _lib.bip_site_coupling(ctx, _dev(H, torch.complex64, "H"), site,
                                                              _dev(out, torch.complex64, "out"), _stream(stream)))
     return out
+
+
+def bip_set_occupancy(ctx, occ):
+    """Per-site occupancies weighting the site sum (None: all 1)."""
+    if occ is None:
+        _check("bip_set_occupancy", ctx, _lib.bip_set_occupancy(ctx, None))
+        return
+    o = np.ascontiguousarray(occ, dtype=np.float64)
+    _check("bip_set_occupancy", ctx, _lib.bip_set_occupancy(ctx, o.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+
+def bip_set_aberrations(ctx, defocus, cs, stream=None):
+    _check("bip_set_aberrations", ctx, _lib.bip_set_aberrations(ctx, float(defocus), float(cs), _stream(stream)))
+
+
+def bip_coreloss_grad(ctx, H, scans, dL_dI, d_occ=None, d_H=None, aberr=False, stream=None):
+    """Reverse pass of a map loss: fills d_occ [n_sites] float64 and d_H
+    (H's shape, complex64: dL/dRe H + i dL/dIm H) when given; returns
+    (dL/d defocus, dL/d Cs) when aberr, else None."""
+    import torch
+    s, sp = _scans(scans)
+    ab = np.zeros(2, dtype=np.float64)
+    abp = ab.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if aberr else None
+    _check("bip_coreloss_grad", ctx, _lib.bip_coreloss_grad(
+        ctx, _dev(H, torch.complex64, "H"), sp, len(s), _dev(dL_dI, torch.float64, "dL_dI"),
+        _dev(d_occ, torch.float64, "d_occ"), _dev(d_H, torch.complex64, "d_H"), abp, _stream(stream)))
+    return (float(ab[0]), float(ab[1])) if aberr else None
 
 
 N_STAGES = 7

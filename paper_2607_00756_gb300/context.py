@@ -92,6 +92,31 @@ class BipContext:
         out = torch.empty((nch, self.n_det, self.B), dtype=torch.complex64, device=device)
         return capi.bip_site_coupling(self.ctx, H, site, out)
 
+    def set_occupancy(self, occ):
+        """Per-site occupancies weighting the site sum (None: all 1)."""
+        capi.bip_set_occupancy(self.ctx, None if occ is None else np.asarray(occ, dtype=np.float64))
+
+    def set_aberrations(self, defocus, cs, stream=None):
+        """Probe defocus and Cs (Angstrom) for the next map."""
+        capi.bip_set_aberrations(self.ctx, defocus, cs, stream)
+
+    def grad(self, H, scans, dL_dI, occ=True, h=True, aberr=True, stream=None):
+        """Reverse pass of a scalar loss of the map, given dL/dI on the scans:
+        {"occ": [n_sites] float64, "H": H's shape complex64 (dL/dRe + i dL/dIm),
+        "defocus", "cs": floats}, each only when asked for."""
+        scans = np.asarray(scans, dtype=np.float64)
+        d_occ = torch.empty(self.n_sites, dtype=torch.float64, device=H.device) if occ else None
+        d_H = torch.empty_like(H) if h else None
+        ab = capi.bip_coreloss_grad(self.ctx, H, scans, dL_dI.contiguous(), d_occ, d_H, aberr, stream)
+        out = {}
+        if occ:
+            out["occ"] = d_occ
+        if h:
+            out["H"] = d_H
+        if aberr:
+            out["defocus"], out["cs"] = ab
+        return out
+
     def close(self):
         if self.ctx:
             capi.bip_destroy(self.ctx)

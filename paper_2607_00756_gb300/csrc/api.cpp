@@ -57,6 +57,9 @@ struct bip_ctx {
     DevBuf opA32, opB32, mt32, q32;     // FP32 path (zeroed at allocation)
     DevBuf opA16, opB16, mt16, q16;     // split-BF16 path (zeroed at allocation)
     DevBuf op8A, op8B;                  // FP8 coupling operands, E4M3 (zeroed at allocation)
+    DevBuf occ_d;                       // site occupancies weighting the site sum
+    int occ_n = 0;                      // sites they were given for (0: none)
+    DevBuf g_s1, g_w, g_R, g_gmt, g_T, g_D, g_Dsum;   // gradient pass workspaces
     DevBuf f8pmax, f8inv0, f8inv1, f8hmax, f8H, f8sA, f8sB;   // FP8 per-window scales
     DevBuf errflag;
     std::vector<int32_t> work_h;
@@ -240,6 +243,18 @@ int to_groups(const std::vector<double>& w, int rows, int cols, std::vector<int3
     return ng;
 }
 
+// c_b(rho) coefficients f_y f_x Psi(h_b) / sqrt(G sum |Psi|^2) (Eq. probe)
+std::vector<double2> coef_host(const bip_ctx* c) {
+    const BipGeometry& geo = c->geo;
+    std::vector<double2> coef(geo.B);
+    const double fyfx = (double)c->cfg.fy * c->cfg.fx;
+    for (int b = 0; b < geo.B; ++b) {
+        const std::complex<double> v = fyfx * geo.psi_beam[b] / geo.psi_norm;
+        coef[b] = double2{v.real(), v.imag()};
+    }
+    return coef;
+}
+
 bip_status make_tables(bip_ctx* c, cudaStream_t s) {
     if (c->tables) return BIP_OK;
     const bip_config& g = c->cfg;
@@ -269,12 +284,7 @@ bip_status make_tables(bip_ctx* c, cudaStream_t s) {
     for (int i = 0; i < geo.Bp2; ++i) sh2[i] = int2{-geo.h_det[2 * geo.p2[i]], -geo.h_det[2 * geo.p2[i] + 1]};
     for (int b = 0; b < geo.B; ++b) hb[b] = int2{geo.h_beam[2 * b], geo.h_beam[2 * b + 1]};
     for (int d = 0; d < geo.n_det; ++d) hd[d] = int2{geo.h_det[2 * d], geo.h_det[2 * d + 1]};
-    std::vector<double2> coef(geo.B);
-    const double fyfx = (double)g.fy * g.fx;
-    for (int b = 0; b < geo.B; ++b) {
-        const std::complex<double> v = fyfx * geo.psi_beam[b] / geo.psi_norm;
-        coef[b] = double2{v.real(), v.imag()};
-    }
+    const std::vector<double2> coef = coef_host(c);
     // beam lattice k = h / f of the difference transform
     std::vector<int2> kb(geo.B);
     int Ky = 0, Kx = 0;
@@ -432,6 +442,7 @@ bip_status set_sites(bip_ctx* c, std::vector<SiteDev>& sites, int nmax, int tota
     if (sig != c->sig1 && sig != c->sig2) {
         c->s1 = c->s2 = false;
     }
+    if (sig != site_signature(c->sites)) c->occ_n = 0;   // occupancies belong to a site list
     c->sites = sites;
     c->n_sites = (int)sites.size();
     c->nch_max = nmax;
@@ -530,7 +541,9 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->plane_ids_d, &c->seq_ids_d, &c->row_off_d, &c->row_ent_d, &c->stash1, &c->stash2, &c->cols, &c->scans_d,
                      &c->gdiff, &c->kb_d, &c->lat_d, &c->work_d, &c->partial, &c->opA32, &c->opB32, &c->mt32, &c->q32, &c->opA16,
                      &c->opB16, &c->mt16, &c->q16, &c->errflag, &c->rsum, &c->wtc, &c->xtc, &c->illum,
-                     &c->cube_scratch, &c->bin_of_d};
+                     &c->cube_scratch, &c->bin_of_d, &c->op8A, &c->op8B, &c->f8pmax, &c->f8inv0, &c->f8inv1,
+                     &c->f8hmax, &c->f8H, &c->f8sA, &c->f8sB, &c->occ_d, &c->g_s1, &c->g_w, &c->g_R,
+                     &c->g_gmt, &c->g_T, &c->g_D, &c->g_Dsum};
     for (DevBuf* b : all) release(*b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
@@ -1149,7 +1162,8 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     }
     if (map_out && !cube_out) {
         CUDA_TRY(c, ensure(c->rsum, bip_reduce_scratch_bytes(c->n_sites, P), false, s));
-        TIMED(c, BIP_STAGE_REDUCE, s, bip_reduce_sites(partial, c->n_sites, P, c->rsum.p, map_out, s));
+        const double* occ = c->occ_n == c->n_sites ? (const double*)c->occ_d.p : nullptr;
+        TIMED(c, BIP_STAGE_REDUCE, s, bip_reduce_sites(partial, c->n_sites, P, c->rsum.p, map_out, s, occ));
         if (c->n_sites > 0) c->launches[BIP_STAGE_REDUCE]++;   // two kernels: chunks, then their sum
     }
     return BIP_OK;
@@ -1217,6 +1231,174 @@ bip_status bip_coreloss_qeels(bip_ctx* c, const void* H, const double* scan_px, 
     if (st != BIP_OK) return st;
     CUDA_TRY(c, bip_qeels_bin((const float*)c->cube_scratch.p, P, c->geo.n_det, (const int32_t*)c->bin_of_d.p,
                               (int)bins.size(), qeels_out, s));
+    return BIP_OK;
+}
+
+bip_status bip_set_occupancy(bip_ctx* c, const double* occ) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (!occ) {
+        c->occ_n = 0;
+        return BIP_OK;
+    }
+    if (c->n_sites < 1) return fail(c, BIP_ERR_INVALID_ARG, "no sites: build the matrices first");
+    for (int k = 0; k < c->n_sites; ++k)
+        if (!std::isfinite(occ[k])) return fail(c, BIP_ERR_INVALID_ARG, "occupancy is not finite");
+    CUDA_TRY(c, ensure(c->occ_d, (size_t)c->n_sites * sizeof(double), false, nullptr));
+    CUDA_TRY(c, cudaMemcpy(c->occ_d.p, occ, (size_t)c->n_sites * sizeof(double), cudaMemcpyHostToDevice));
+    c->occ_n = c->n_sites;
+    return BIP_OK;
+}
+
+bip_status bip_set_aberrations(bip_ctx* c, double defocus, double cs, void* stream) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (!std::isfinite(defocus) || !std::isfinite(cs)) return fail(c, BIP_ERR_INVALID_ARG, "aberration not finite");
+    c->cfg.defocus = defocus;
+    c->cfg.cs = cs;
+    bip_set_psi(c->cfg, c->geo);
+    if (c->tables) CUDA_TRY(c, upload(c->coef, coef_host(c), (cudaStream_t)stream));
+    return BIP_OK;
+}
+
+bip_status bip_coreloss_grad(bip_ctx* c, const void* H, const double* scan_px, int32_t P, const double* dL_dI,
+                             double* d_occ, void* d_H, double* d_aberr, void* stream) {
+    bip_status st = check_map_args(c, H, scan_px, P, dL_dI);
+    if (st != BIP_OK) return st;
+    if ((reinterpret_cast<uintptr_t>(d_H) & 7) != 0) return fail(c, BIP_ERR_INVALID_ARG, "d_H must be 8-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bip_config& g = c->cfg;
+    const BipGeometry& geo = c->geo;
+    const int K = g.win * g.win, Bpad = c->Bpad, Dpad = c->Dpad, nch = c->nch_max, B = geo.B;
+    const double* occ = c->occ_n == c->n_sites ? (const double*)c->occ_d.p : nullptr;
+    if (d_occ) {
+        // dL/do_tau = sum_rho g I_tau with the forward partials
+        CUDA_TRY(c, ensure(c->partial, (size_t)c->n_sites * P * sizeof(float), false, s));
+        st = run_map(c, H, scan_px, P, (float*)c->partial.p, nullptr, nullptr, s);
+        if (st != BIP_OK) return st;
+        CUDA_TRY(c, bip_grad_occ((const float*)c->partial.p, c->n_sites, P, dL_dI, d_occ, s));
+    }
+    if (!d_H && !d_aberr) return BIP_OK;
+    // FP32 contraction per batch of sites: S2, H_n S1 and S1 windows, M (as
+    // Mt[b][(n, d)]), Q, then the reverse steps
+    CUDA_TRY(c, ensure(c->scans_d, (size_t)P * 2 * sizeof(double), false, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->scans_d.p, scan_px, (size_t)P * 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, ensure(c->illum, (size_t)Bpad * P * sizeof(float2), false, s));
+    IllumArgs ia{P, B, Bpad, (const int2*)c->hbeam.p, (const double2*)c->coef.p, (const double*)c->scans_d.p, g.ny,
+                 g.nx, (float2*)c->illum.p};
+    CUDA_TRY(c, bip_illum(ia, s));
+    const int SB = std::min(c->n_sites, 8);
+    const size_t perA = (size_t)Dpad * K, perB = (size_t)nch * Bpad * K, perS1 = (size_t)Bpad * K;
+    const size_t ldm = (size_t)nch * Dpad, perMt = (size_t)Bpad * ldm, perQ = (size_t)Bpad * Bpad;
+    const size_t perT = (size_t)nch * B * K;
+    CUDA_TRY(c, ensure(c->opA32, SB * perA * sizeof(float2), true, s));
+    CUDA_TRY(c, ensure(c->opB32, SB * perB * sizeof(float2), true, s));
+    CUDA_TRY(c, ensure(c->g_s1, SB * perS1 * sizeof(float2), true, s));
+    CUDA_TRY(c, ensure(c->mt32, SB * perMt * sizeof(float2), true, s));
+    CUDA_TRY(c, ensure(c->q32, SB * perQ * sizeof(float2), true, s));
+    CUDA_TRY(c, ensure(c->g_w, (size_t)SB * P * sizeof(float), false, s));
+    CUDA_TRY(c, ensure(c->g_R, SB * perQ * sizeof(float2), true, s));
+    CUDA_TRY(c, ensure(c->g_gmt, SB * perMt * sizeof(float2), true, s));
+    CUDA_TRY(c, ensure(c->g_T, SB * perT * sizeof(float2), false, s));
+    CUDA_TRY(c, ensure(c->g_D, (size_t)SB * B * sizeof(double2), false, s));
+    CUDA_TRY(c, ensure(c->g_Dsum, (size_t)B * sizeof(double2), false, s));
+    CUDA_TRY(c, cudaMemsetAsync(c->g_Dsum.p, 0, (size_t)B * sizeof(double2), s));
+    if (d_H) CUDA_TRY(c, cudaMemsetAsync(d_H, 0, (size_t)c->n_ch_total * K * sizeof(float2), s));
+    GradArgs ga{};
+    ga.P = P; ga.K = K; ga.B = B;
+    ga.scans = (const double*)c->scans_d.p;
+    ga.dL_dI = dL_dI;
+    ga.occ = occ;
+    ga.sites = (const SiteDev*)c->sites_d.p;
+    ga.ny = g.ny; ga.nx = g.nx; ga.fy = g.fy; ga.fx = g.fx;
+    ga.scale = (double)g.fy * g.fx;
+    for (int b0 = 0; b0 < c->n_sites; b0 += SB) {
+        const int nb = std::min(SB, c->n_sites - b0);
+        const int32_t* ids = (const int32_t*)c->seq_ids_d.p + b0;
+        GatherArgs g2 = gather_args(c, 2, ids, nb);
+        g2.rows_pad = Dpad;
+        g2.out_c64 = (float2*)c->opA32.p;
+        g2.site_stride = (int64_t)perA;
+        CUDA_TRY(c, bip_gather(g2, s));
+        GatherArgs g1 = gather_args(c, 1, ids, nb);
+        g1.rows_pad = Bpad;
+        g1.nch = nch;
+        g1.H = (const float2*)H;
+        g1.out_c64 = (float2*)c->opB32.p;
+        g1.site_stride = (int64_t)perB;
+        CUDA_TRY(c, bip_gather(g1, s));
+        GatherArgs g0 = gather_args(c, 1, ids, nb);
+        g0.rows_pad = Bpad;
+        g0.out_c64 = (float2*)c->g_s1.p;
+        g0.site_stride = (int64_t)perS1;
+        CUDA_TRY(c, bip_gather(g0, s));
+        CGemmArgs A{};
+        A.M = geo.n_det; A.N = nch * Bpad; A.K = K;
+        A.A = (const float2*)c->opA32.p; A.lda = K; A.strideA = (int64_t)perA;
+        A.Bm = (const float2*)c->opB32.p; A.ldb = K; A.strideB = (int64_t)perB;
+        A.batch = nb;
+        A.epi = 1;
+        A.C = (float2*)c->mt32.p; A.ldc = (int64_t)ldm; A.strideC = (int64_t)perMt;
+        A.ep_B = Bpad; A.ep_Dp = Dpad;
+        CUDA_TRY(c, bip_cgemm_simt(A, s));
+        // R_tau = f o_tau sum_{rho in crop} g c c^H
+        CUDA_TRY(c, bip_grad_crop_weights(ga, nb, ids, (float*)c->g_w.p, s));
+        CGemmGen r{};
+        r.M = B; r.N = B; r.K = P; r.batch = nb;
+        r.A = (const float2*)c->illum.p; r.sam = P; r.sak = 1; r.sab = 0;
+        r.dk = (const float*)c->g_w.p; r.sdb = P;
+        r.B = (const float2*)c->illum.p; r.sbk = 1; r.sbn = P; r.sbb = 0; r.conjB = 1;
+        r.C = (float2*)c->g_R.p; r.scm = Bpad; r.scn = 1; r.scb = (int64_t)perQ;
+        CUDA_TRY(c, bip_cgemm_gen(r, s));
+        if (d_aberr) {
+            // Q = sum_n M_n^H M_n, then D_b += (Q R)_bb
+            CGemmArgs Bq{};
+            Bq.M = Bpad; Bq.N = Bpad; Bq.K = (int)ldm;
+            Bq.A = (const float2*)c->mt32.p; Bq.lda = (int64_t)ldm; Bq.strideA = (int64_t)perMt;
+            Bq.Bm = Bq.A; Bq.ldb = Bq.lda; Bq.strideB = Bq.strideA;
+            Bq.conjA = 1;
+            Bq.batch = nb;
+            Bq.epi = 0;
+            Bq.C = (float2*)c->q32.p; Bq.ldc = Bpad; Bq.strideC = (int64_t)perQ;
+            CUDA_TRY(c, bip_cgemm_simt(Bq, s));
+            CUDA_TRY(c, bip_grad_aberr(B, Bpad, nb, (const float2*)c->q32.p, (int64_t)perQ, (const float2*)c->g_R.p,
+                                       (int64_t)perQ, (double2*)c->g_D.p, (double2*)c->g_Dsum.p, s));
+        }
+        if (d_H) {
+            // Mbar_n = M_n R, kept as GMt = conj(R) Mt (R Hermitian)
+            CGemmGen m{};
+            m.M = B; m.N = (int)ldm; m.K = B; m.batch = nb;
+            m.A = (const float2*)c->g_R.p; m.sam = Bpad; m.sak = 1; m.sab = (int64_t)perQ; m.conjA = 1;
+            m.B = (const float2*)c->mt32.p; m.sbk = (int64_t)ldm; m.sbn = 1; m.sbb = (int64_t)perMt;
+            m.C = (float2*)c->g_gmt.p; m.scm = (int64_t)ldm; m.scn = 1; m.scb = (int64_t)perMt;
+            CUDA_TRY(c, bip_cgemm_gen(m, s));
+            // T_n(b, r) = sum_d Mbar_n(d, b) conj S2_d(r)
+            for (int n = 0; n < nch; ++n) {
+                CGemmGen t{};
+                t.M = B; t.N = K; t.K = geo.n_det; t.batch = nb;
+                t.A = (const float2*)c->g_gmt.p + (size_t)n * Dpad; t.sam = (int64_t)ldm; t.sak = 1;
+                t.sab = (int64_t)perMt;
+                t.B = (const float2*)c->opA32.p; t.sbk = K; t.sbn = 1; t.sbb = (int64_t)perA; t.conjB = 1;
+                t.C = (float2*)c->g_T.p + (size_t)n * B * K; t.scm = K; t.scn = 1; t.scb = (int64_t)perT;
+                CUDA_TRY(c, bip_cgemm_gen(t, s));
+            }
+            CUDA_TRY(c, bip_grad_h(ga, nb, ids, nch, (const float2*)c->g_s1.p, (int64_t)perS1,
+                                   (const float2*)c->g_T.p, (int64_t)perT, (int64_t)B * K, (float2*)d_H, s));
+        }
+    }
+    if (d_aberr) {
+        std::vector<double2> D(B);
+        CUDA_TRY(c, cudaMemcpyAsync(D.data(), c->g_Dsum.p, (size_t)B * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        // dL/dtheta = -2 sum_b chi'_b Im D_b
+        double gdf = 0.0, gcs = 0.0;
+        for (int b = 0; b < B; ++b) {
+            double ddf = 0.0, dcs = 0.0;
+            bip_aberration_phase(g, geo.lambda, geo.h_beam[2 * b], geo.h_beam[2 * b + 1], nullptr, &ddf, &dcs);
+            gdf += -2.0 * ddf * D[b].y;
+            gcs += -2.0 * dcs * D[b].y;
+        }
+        d_aberr[0] = gdf;
+        d_aberr[1] = gcs;
+    }
     return BIP_OK;
 }
 

@@ -27,6 +27,12 @@ struct BipGeometry {
 };
 
 bip_status bip_build_geometry(const bip_config& cfg, BipGeometry& g, std::string& err);
+// chi(q) = pi lambda df |q|^2 + (pi/2) Cs lambda^3 |q|^4 of beam h (Psi = exp(-i chi))
+// and its derivatives with respect to df and Cs (each output optional)
+void bip_aberration_phase(const bip_config& c, double lambda, int hy, int hx, double* chi, double* d_defocus,
+                          double* d_cs);
+// Psi(h_b) of the aperture beams for the configuration's df and Cs
+void bip_set_psi(const bip_config& c, BipGeometry& g);
 
 // Sibson weights of `queries` against `parents` (integer beam indices,
 // physical scale 1/ly, 1/lx); dense [nq * np] row-major.
@@ -251,8 +257,10 @@ cudaError_t bip_diff_eval(const DiffArgs& a, cudaStream_t s);
 // (already zero outside each site's crop mask), in a fixed order; scratch
 // of bip_reduce_scratch_bytes(n_sites, P) bytes.
 size_t bip_reduce_scratch_bytes(int n_sites, int P);
+// occ (optional, [n_sites]): each site's contribution is weighted by its
+// occupancy before the sum
 cudaError_t bip_reduce_sites(const float* partial, int n_sites, int P, void* scratch, double* map_out,
-                             cudaStream_t s);
+                             cudaStream_t s, const double* occ = nullptr);
 
 // gemm_tc.cu : tcgen05 complex contractions in split BF16 or BF16.
 // Operands are bf16 planes, K contiguous -- four (re_hi, re_lo, im_hi,
@@ -327,6 +335,38 @@ cudaError_t bip_cube_accumulate(const CubeArgs& a, cudaStream_t s);
 // qEELS: out[rho][bin_of[d]] = sum of cube[rho][d] over the beams of a bin
 cudaError_t bip_qeels_bin(const float* cube, int P, int n_det, const int32_t* bin_of, int n_bins, float* out,
                           cudaStream_t s);
+
+// grad.cu : reverse pass of a map loss through the contraction
+// generic complex GEMM: C(m, n) (+)= sum_k opA(A(m, k) dk[k]) opB(B(k, n)),
+// X(i, j) = X[z sXb + i sXi + j sXj] for batch z
+struct CGemmGen {
+    int M, N, K, batch;
+    const float2* A; int64_t sam, sak, sab;
+    const float2* B; int64_t sbk, sbn, sbb;
+    float2* C; int64_t scm, scn, scb;
+    const float* dk; int64_t sdb;   // optional real scale of each k (null: 1)
+    int conjA, conjB, accumulate;
+};
+cudaError_t bip_cgemm_gen(const CGemmGen& a, cudaStream_t s);
+struct GradArgs {
+    int P, K, B;
+    const double* scans;            // [P][2] pixels (device)
+    const double* dL_dI;            // [P] g(rho)
+    const double* occ;              // [n_sites] occupancies (null: 1)
+    const SiteDev* sites;
+    int ny, nx, fy, fx;
+    double scale;                   // f_y f_x
+};
+// w[bs][rho] = f o g(rho) on the site's crop window, 0 elsewhere
+cudaError_t bip_grad_crop_weights(const GradArgs& a, int nb, const int32_t* ids, float* w, cudaStream_t s);
+// dH[ch_off + n][r] = 2 sum_b conj S1[bs][b][r] T[bs][n][b][r]
+cudaError_t bip_grad_h(const GradArgs& a, int nb, const int32_t* ids, int nch, const float2* S1, int64_t s1_site,
+                       const float2* T, int64_t t_site, int64_t t_ch, float2* dH, cudaStream_t s);
+// D[bs][b] = sum_b' Q[bs][b][b'] R[bs][b'][b]; Dsum[b] += sum_bs D[bs][b]
+cudaError_t bip_grad_aberr(int B, int Bpad, int nb, const float2* Q, int64_t q_site, const float2* R, int64_t r_site,
+                           double2* D, double2* Dsum, cudaStream_t s);
+// out[k] = sum_rho g(rho) partial[k][rho]
+cudaError_t bip_grad_occ(const float* partial, int n_sites, int P, const double* g, double* out, cudaStream_t s);
 
 // noalloc.cu : the static device scratch used by bip_build_s1_noalloc
 constexpr size_t kNoallocScratchBytes = size_t(32) << 20;   // 32 MiB per GPU

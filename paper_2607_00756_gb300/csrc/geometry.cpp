@@ -258,6 +258,24 @@ void bip_sibson_weights(const std::vector<int32_t>& parents, const std::vector<i
     }
 }
 
+void bip_aberration_phase(const bip_config& c, double lambda, int hy, int hx, double* chi, double* d_defocus,
+                          double* d_cs) {
+    const double q2 = (hy / c.ly) * (hy / c.ly) + (hx / c.lx) * (hx / c.lx);
+    const double l3 = lambda * lambda * lambda;
+    if (chi) *chi = kPi * lambda * c.defocus * q2 + 0.5 * kPi * c.cs * l3 * q2 * q2;
+    if (d_defocus) *d_defocus = kPi * lambda * q2;
+    if (d_cs) *d_cs = 0.5 * kPi * l3 * q2 * q2;
+}
+
+void bip_set_psi(const bip_config& c, BipGeometry& g) {
+    g.psi_beam.resize(g.B);
+    for (int b = 0; b < g.B; ++b) {
+        double x = 0.0;
+        bip_aberration_phase(c, g.lambda, g.h_beam[2 * b], g.h_beam[2 * b + 1], &x, nullptr, nullptr);
+        g.psi_beam[b] = std::complex<double>(std::cos(x), -std::sin(x));
+    }
+}
+
 bip_status bip_build_geometry(const bip_config& c, BipGeometry& g, std::string& err) {
     g.lambda = kHC / std::sqrt(c.e0 * (2.0 * kM0C2 + c.e0));
     g.sigma = (2.0 * kPi / (g.lambda * c.e0)) * (kM0C2 + c.e0) / (2.0 * kM0C2 + c.e0);
@@ -277,18 +295,10 @@ bip_status bip_build_geometry(const bip_config& c, BipGeometry& g, std::string& 
         err = "empty aperture or detector beam set";
         return BIP_ERR_SHAPE;
     }
-    auto chi = [&](int hy, int hx) {
-        double q2 = (hy / c.ly) * (hy / c.ly) + (hx / c.lx) * (hx / c.lx);
-        return kPi * g.lambda * c.defocus * q2 + 0.5 * kPi * c.cs * g.lambda * g.lambda * g.lambda * q2 * q2;
-    };
     double s = 0.0;
     for (int i = 0; i < g.n_full; ++i) s += 1.0;   // |Psi| = 1 inside the aperture
     g.psi_norm = std::sqrt((double)c.ny * c.nx * s);
-    g.psi_beam.resize(g.B);
-    for (int b = 0; b < g.B; ++b) {
-        double x = chi(g.h_beam[2 * b], g.h_beam[2 * b + 1]);
-        g.psi_beam[b] = std::complex<double>(std::cos(x), -std::sin(x));
-    }
+    bip_set_psi(c, g);
     g.p1 = hex_ring(g.h_beam, c.ly, c.lx, c.nrad1, c.nang1);
     g.p2 = hex_ring(g.h_det, c.ly, c.lx, c.nrad2, c.nang2);
     g.Bp1 = (int)g.p1.size();

@@ -1,5 +1,5 @@
 // Sum of the per-site map contributions (Eq. map-sum, incoherent sum over
-// sites).  The partials are zero outside each site's crop mask (the map
+// sites), each optionally weighted by the site's occupancy.  The partials are zero outside each site's crop mask (the map
 // clears them before the per-site evaluation writes the in-crop scans), so
 // the sum runs over all sites.  It is done in FP64 with Neumaier
 // compensation in a fixed order -- sites in chunks of kChunk in site order,
@@ -21,13 +21,18 @@ __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
 }
 
 __global__ void __launch_bounds__(kThreads) reduce_chunk_kernel(const float* __restrict__ partial, int n_sites,
-                                                                int P, double2* __restrict__ chunk_sum) {
+                                                                int P, const double* __restrict__ occ,
+                                                                double2* __restrict__ chunk_sum) {
     const int p = blockIdx.x * kThreads + threadIdx.x;
     if (p >= P) return;
     const int k0 = blockIdx.y * kChunk, k1 = min(k0 + kChunk, n_sites);
     double s = 0.0, c = 0.0;
+    if (occ) {
+        for (int k = k0; k < k1; ++k) neumaier(s, c, __ldg(&occ[k]) * (double)__ldg(&partial[(size_t)k * P + p]));
+    } else {
 #pragma unroll 8
-    for (int k = k0; k < k1; ++k) neumaier(s, c, (double)__ldg(&partial[(size_t)k * P + p]));
+        for (int k = k0; k < k1; ++k) neumaier(s, c, (double)__ldg(&partial[(size_t)k * P + p]));
+    }
     chunk_sum[(size_t)blockIdx.y * P + p] = make_double2(s, c);
 }
 
@@ -50,11 +55,13 @@ size_t bip_reduce_scratch_bytes(int n_sites, int P) {
     return (size_t)((n_sites + kChunk - 1) / kChunk) * P * sizeof(double2);
 }
 
-cudaError_t bip_reduce_sites(const float* partial, int n_sites, int P, void* scratch, double* out, cudaStream_t s) {
+cudaError_t bip_reduce_sites(const float* partial, int n_sites, int P, void* scratch, double* out, cudaStream_t s,
+                             const double* occ) {
     const int n_chunks = (n_sites + kChunk - 1) / kChunk;
     if (n_chunks == 0) return cudaMemsetAsync(out, 0, (size_t)P * sizeof(double), s);
     double2* cs = static_cast<double2*>(scratch);
-    reduce_chunk_kernel<<<dim3((P + kThreads - 1) / kThreads, n_chunks), kThreads, 0, s>>>(partial, n_sites, P, cs);
+    reduce_chunk_kernel<<<dim3((P + kThreads - 1) / kThreads, n_chunks), kThreads, 0, s>>>(partial, n_sites, P, occ,
+                                                                                         cs);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     reduce_final_kernel<<<(P + kThreads - 1) / kThreads, kThreads, 0, s>>>(cs, n_chunks, P, out);
