@@ -225,7 +225,12 @@ bip_status bip_set_aberrations(bip_ctx* ctx, double defocus, double cs, void* st
  *   d_H   H's layout, complex64 device: dL/dRe H + i dL/dIm H of every
  *         channel sample (for transition amplitudes a with H = a H0:
  *         dL/dRe a + i dL/dIm a = sum_r d_H(r) conj(H0(r)));
- *   d_aberr [2] float64 host: dL/d defocus, dL/d Cs.
+ *   d_aberr [2] float64 host: dL/d defocus, dL/d Cs;
+ *   d_V [nz, ny, nx] float32 device: dL/dV_j of every slice potential,
+ *         through the reconstruction (Eq. magpreserve) and both sweeps
+ *         (Eq. smatrix-advance, Eq. s2); V (device, the potential the
+ *         matrices were built from) is then required.  The sweeps' forward
+ *         states are recomputed from checkpoints every ceil(sqrt(n)) slices.
  * Any output may be NULL (not computed).  Steps: R_tau = f_y f_x o_tau
  * sum_{rho in crop} g c c^H; Mbar = M R; dL/dH_n(r) = 2 sum_{d,b}
  * Mbar_n(d,b) conj(S2_d(r) S1_b(r)); dL/dtheta = -2 sum_b chi'_b Im
@@ -233,9 +238,9 @@ bip_status bip_set_aberrations(bip_ctx* ctx, double defocus, double cs, void* st
  * d_occ uses the context's precision for I_tau.
  *   dL_dI [P] float64 device; other requirements as bip_coreloss_map;
  *   d_H 8-byte aligned.  Synchronises the stream when d_aberr is given. */
-bip_status bip_coreloss_grad(bip_ctx* ctx, const void* H, const double* scan_px, int32_t P,
-                             const double* dL_dI, double* d_occ, void* d_H, double* d_aberr,
-                             void* stream);
+bip_status bip_coreloss_grad(bip_ctx* ctx, const float* V, const void* H, const double* scan_px,
+                             int32_t P, const double* dL_dI, double* d_occ, void* d_H,
+                             double* d_aberr, float* d_V, void* stream);
 
 /* Stage access for validation.
  * bip_copy_stash: the de-tilted parent windows of one site, which = 1 (S1,

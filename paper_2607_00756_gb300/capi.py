@@ -70,7 +70,7 @@ def _load():
         "bip_get_profile": [VP, VP, VP],
         "bip_set_occupancy": [VP, P(D)],
         "bip_set_aberrations": [VP, D, D, VP],
-        "bip_coreloss_grad": [VP, VP, P(D), I32, VP, VP, VP, P(D), VP],
+        "bip_coreloss_grad": [VP, VP, VP, P(D), I32, VP, VP, VP, P(D), VP, VP],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -282,17 +282,18 @@ def bip_set_aberrations(ctx, defocus, cs, stream=None):
     _check("bip_set_aberrations", ctx, _lib.bip_set_aberrations(ctx, float(defocus), float(cs), _stream(stream)))
 
 
-def bip_coreloss_grad(ctx, H, scans, dL_dI, d_occ=None, d_H=None, aberr=False, stream=None):
-    """Reverse pass of a map loss: fills d_occ [n_sites] float64 and d_H
-    (H's shape, complex64: dL/dRe H + i dL/dIm H) when given; returns
-    (dL/d defocus, dL/d Cs) when aberr, else None."""
+def bip_coreloss_grad(ctx, H, scans, dL_dI, d_occ=None, d_H=None, aberr=False, V=None, d_V=None, stream=None):
+    """Reverse pass of a map loss: fills d_occ [n_sites] float64, d_H (H's
+    shape, complex64: dL/dRe H + i dL/dIm H) and d_V ([nz, ny, nx] float32,
+    needs V) when given; returns (dL/d defocus, dL/d Cs) when aberr, else None."""
     import torch
     s, sp = _scans(scans)
     ab = np.zeros(2, dtype=np.float64)
     abp = ab.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if aberr else None
     _check("bip_coreloss_grad", ctx, _lib.bip_coreloss_grad(
-        ctx, _dev(H, torch.complex64, "H"), sp, len(s), _dev(dL_dI, torch.float64, "dL_dI"),
-        _dev(d_occ, torch.float64, "d_occ"), _dev(d_H, torch.complex64, "d_H"), abp, _stream(stream)))
+        ctx, _dev(V, torch.float32, "V"), _dev(H, torch.complex64, "H"), sp, len(s),
+        _dev(dL_dI, torch.float64, "dL_dI"), _dev(d_occ, torch.float64, "d_occ"), _dev(d_H, torch.complex64, "d_H"),
+        abp, _dev(d_V, torch.float32, "d_V"), _stream(stream)))
     return (float(ab[0]), float(ab[1])) if aberr else None
 
 

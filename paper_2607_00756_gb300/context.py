@@ -100,15 +100,20 @@ class BipContext:
         """Probe defocus and Cs (Angstrom) for the next map."""
         capi.bip_set_aberrations(self.ctx, defocus, cs, stream)
 
-    def grad(self, H, scans, dL_dI, occ=True, h=True, aberr=True, stream=None):
+    def grad(self, H, scans, dL_dI, occ=True, h=True, aberr=True, V=None, stream=None):
         """Reverse pass of a scalar loss of the map, given dL/dI on the scans:
         {"occ": [n_sites] float64, "H": H's shape complex64 (dL/dRe + i dL/dIm),
-        "defocus", "cs": floats}, each only when asked for."""
+        "defocus", "cs": floats, "V": [nz, ny, nx] float32 when V (the
+        potential the matrices were built from) is given}, each only when
+        asked for."""
         scans = np.asarray(scans, dtype=np.float64)
         d_occ = torch.empty(self.n_sites, dtype=torch.float64, device=H.device) if occ else None
         d_H = torch.empty_like(H) if h else None
-        ab = capi.bip_coreloss_grad(self.ctx, H, scans, dL_dI.contiguous(), d_occ, d_H, aberr, stream)
+        d_V = torch.empty_like(V) if V is not None else None
+        ab = capi.bip_coreloss_grad(self.ctx, H, scans, dL_dI.contiguous(), d_occ, d_H, aberr, V, d_V, stream)
         out = {}
+        if d_V is not None:
+            out["V"] = d_V
         if occ:
             out["occ"] = d_occ
         if h:

@@ -60,6 +60,10 @@ struct bip_ctx {
     DevBuf occ_d;                       // site occupancies weighting the site sum
     int occ_n = 0;                      // sites they were given for (0: none)
     DevBuf g_s1, g_w, g_R, g_gmt, g_T, g_D, g_Dsum;   // gradient pass workspaces
+    DevBuf g_s1bar, g_s2bar, g_ubar, g_dA, g_dt1, g_dt2, g_adj, g_ckpt, g_seg, g_gvp;
+    DevBuf pyc, pxc;                    // conjugated propagator tables (adjoint sweeps)
+    DevBuf aw1[6], aw2[6];              // per-target / per-parent weights (reconstruction adjoint)
+    bool adj_tables = false;
     DevBuf f8pmax, f8inv0, f8inv1, f8hmax, f8H, f8sA, f8sB;   // FP8 per-window scales
     DevBuf errflag;
     std::vector<int32_t> work_h;
@@ -543,8 +547,13 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->opB16, &c->mt16, &c->q16, &c->errflag, &c->rsum, &c->wtc, &c->xtc, &c->illum,
                      &c->cube_scratch, &c->bin_of_d, &c->op8A, &c->op8B, &c->f8pmax, &c->f8inv0, &c->f8inv1,
                      &c->f8hmax, &c->f8H, &c->f8sA, &c->f8sB, &c->occ_d, &c->g_s1, &c->g_w, &c->g_R,
-                     &c->g_gmt, &c->g_T, &c->g_D, &c->g_Dsum};
+                     &c->g_gmt, &c->g_T, &c->g_D, &c->g_Dsum, &c->g_s1bar, &c->g_s2bar, &c->g_ubar, &c->g_dA,
+                     &c->g_dt1, &c->g_dt2, &c->g_adj, &c->g_ckpt, &c->g_seg, &c->g_gvp, &c->pyc, &c->pxc};
     for (DevBuf* b : all) release(*b);
+    for (int i = 0; i < 6; ++i) {
+        release(c->aw1[i]);
+        release(c->aw2[i]);
+    }
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
     return BIP_OK;
@@ -782,6 +791,244 @@ bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H,
         r.inv_row[1] = (const float*)c->f8inv1.p;
     }
     TIMED(c, BIP_STAGE_GATHER, s, bip_recon_tc(r, s));
+    return BIP_OK;
+}
+
+// ---- reverse pass through the reconstruction and the sweeps
+
+// per-target and per-parent lists of the non-zero weights of one side
+bip_status adj_tables(bip_ctx* c, cudaStream_t s) {
+    if (c->adj_tables) return BIP_OK;
+    const BipGeometry& geo = c->geo;
+    const bip_config& g = c->cfg;
+    auto build = [&](const std::vector<double>& w, int nt, int bp, DevBuf* out) -> bip_status {
+        std::vector<int32_t> toff(1, 0), tpar, poff(1, 0), ptgt;
+        std::vector<float> tw, pw;
+        for (int t = 0; t < nt; ++t) {
+            for (int p = 0; p < bp; ++p)
+                if (w[(size_t)t * bp + p] != 0.0) {
+                    tpar.push_back(p);
+                    tw.push_back((float)w[(size_t)t * bp + p]);
+                }
+            toff.push_back((int32_t)tpar.size());
+        }
+        for (int p = 0; p < bp; ++p) {
+            for (int t = 0; t < nt; ++t)
+                if (w[(size_t)t * bp + p] != 0.0) {
+                    ptgt.push_back(t);
+                    pw.push_back((float)w[(size_t)t * bp + p]);
+                }
+            poff.push_back((int32_t)ptgt.size());
+        }
+        CUDA_TRY(c, upload(out[0], toff, s));
+        CUDA_TRY(c, upload(out[1], tpar, s));
+        CUDA_TRY(c, upload(out[2], tw, s));
+        CUDA_TRY(c, upload(out[3], poff, s));
+        CUDA_TRY(c, upload(out[4], ptgt, s));
+        CUDA_TRY(c, upload(out[5], pw, s));
+        return BIP_OK;
+    };
+    bip_status st = build(geo.w1, geo.B, geo.Bp1, c->aw1);
+    if (st != BIP_OK) return st;
+    st = build(geo.w2, geo.n_det, geo.Bp2, c->aw2);
+    if (st != BIP_OK) return st;
+    // conj(P): the propagator tables of the forward sweep, conjugated
+    std::vector<float2> py(g.ny), px(g.nx);
+    CUDA_TRY(c, cudaMemcpyAsync(py.data(), c->py.p, g.ny * sizeof(float2), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaMemcpyAsync(px.data(), c->px.p, g.nx * sizeof(float2), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    for (auto& v : py) v.y = -v.y;
+    for (auto& v : px) v.y = -v.y;
+    CUDA_TRY(c, upload(c->pyc, py, s));
+    CUDA_TRY(c, upload(c->pxc, px, s));
+    c->adj_tables = true;
+    return BIP_OK;
+}
+
+AdjWeights adj_weights(DevBuf* w) {
+    return AdjWeights{(const int32_t*)w[0].p, (const int32_t*)w[1].p, (const float*)w[2].p,
+                      (const int32_t*)w[3].p, (const int32_t*)w[4].p, (const float*)w[5].p};
+}
+
+int isqrt_up(int n) {
+    int k = 1;
+    while (k * k < n) ++k;
+    return k;
+}
+
+// dL/dV_j through the S1 sweep (psi_{j+1} = Prop(T_j psi_j)), j < the last
+// ionization plane, from the window adjoints dtbar1 of every site; forward
+// states recomputed from checkpoints every ceil(sqrt(n)) slices
+bip_status adjoint_s1(bip_ctx* c, const float* V, float* dV, cudaStream_t s) {
+    const bip_config& g = c->cfg;
+    const size_t G = (size_t)g.ny * g.nx;
+    const int ncol = c->geo.Bp1;
+    int jmax = 0;
+    for (auto& sd : c->sites) jmax = std::max(jmax, (int)sd.plane);
+    if (jmax == 0) return BIP_OK;
+    const int n = jmax, k = isqrt_up(n), nck = (n + k - 1) / k;
+    const size_t state = (size_t)ncol * G;
+    CUDA_TRY(c, ensure(c->g_adj, state * sizeof(float2), false, s));
+    CUDA_TRY(c, ensure(c->g_ckpt, (size_t)nck * state * sizeof(float2), false, s));
+    CUDA_TRY(c, ensure(c->g_seg, (size_t)k * state * sizeof(float2), false, s));
+    CUDA_TRY(c, ensure(c->g_gvp, (size_t)ncol * G * sizeof(float), false, s));
+    MsPlan fp = plan_for(c, ncol, c->shift1), cp = fp;
+    cp.py = (const float2*)c->pyc.p;
+    cp.px = (const float2*)c->pxc.p;
+    float2* cols = (float2*)c->cols.p;
+    float2* adj = (float2*)c->g_adj.p;
+    auto row_off = [&](int j) -> const int32_t* {
+        return c->plane_off[j + 1] > c->plane_off[j] ? (const int32_t*)c->row_off_d.p + (size_t)j * (g.ny + 1) : nullptr;
+    };
+    auto fwd_row = [&](int j, float2* save, bool fft) -> cudaError_t {
+        MsRowArgs a{};
+        a.cols = cols;
+        a.init = j == 0;
+        a.init_val = 1.0f;
+        a.do_ifft = j > 0;
+        a.v_post = V + (size_t)j * G;
+        a.do_fft = fft;
+        a.win = g.win;
+        a.save = save;
+        return bip_ms_row_pass(fp, a, s);
+    };
+    // forward sweep, keeping the field at the start of every k-th step
+    const int last_ck = (nck - 1) * k;
+    for (int j = 0; j < last_ck; ++j) {
+        if (j % k == 0 && j > 0)
+            CUDA_TRY(c, cudaMemcpyAsync((float2*)c->g_ckpt.p + (size_t)(j / k) * state, cols, state * sizeof(float2),
+                                        cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(c, fwd_row(j, nullptr, true));
+        CUDA_TRY(c, bip_ms_col_pass(fp, cols, s));
+    }
+    if (last_ck > 0)
+        CUDA_TRY(c, cudaMemcpyAsync((float2*)c->g_ckpt.p + (size_t)(last_ck / k) * state, cols, state * sizeof(float2),
+                                    cudaMemcpyDeviceToDevice, s));
+    int groups = 0;
+    auto adj_row = [&](int j, bool zero_in, const float2* st, bool fft) -> bip_status {
+        MsAdjArgs a{};
+        a.cols = adj;
+        a.zero_in = zero_in;
+        a.do_ifft = !zero_in;
+        a.v = zero_in ? nullptr : V + (size_t)j * G;
+        a.state = st;
+        a.state_times_T = 1;
+        a.inj_before = 0;
+        a.row_off = row_off(j);
+        a.row_ent = (const int4*)c->row_ent_d.p;
+        a.win = g.win;
+        a.inj = (const float2*)c->g_dt1.p;
+        a.gv_part = (float*)c->g_gvp.p;
+        a.do_fft = fft;
+        CUDA_TRY(c, bip_ms_adj_row_pass(fp, a, &groups, s));
+        if (st) CUDA_TRY(c, bip_gv_reduce((const float*)c->g_gvp.p, groups, (int)G, dV + (size_t)j * G, s));
+        return BIP_OK;
+    };
+    // lambda at the last plane: its window adjoints only
+    bip_status st = adj_row(jmax, true, nullptr, true);
+    if (st != BIP_OK) return st;
+    CUDA_TRY(c, bip_ms_col_pass(cp, adj, s));
+    for (int m = nck - 1; m >= 0; --m) {
+        const int j0 = m * k, j1 = std::min(j0 + k, n) - 1;
+        if (m > 0)
+            CUDA_TRY(c, cudaMemcpyAsync(cols, (float2*)c->g_ckpt.p + (size_t)m * state, state * sizeof(float2),
+                                        cudaMemcpyDeviceToDevice, s));
+        for (int j = j0; j <= j1; ++j) {
+            CUDA_TRY(c, fwd_row(j, (float2*)c->g_seg.p + (size_t)(j - j0) * state, j < j1));
+            if (j < j1) CUDA_TRY(c, bip_ms_col_pass(fp, cols, s));
+        }
+        for (int j = j1; j >= j0; --j) {
+            st = adj_row(j, false, (const float2*)c->g_seg.p + (size_t)(j - j0) * state, j > 0);
+            if (st != BIP_OK) return st;
+            if (j > 0) CUDA_TRY(c, bip_ms_col_pass(cp, adj, s));
+        }
+    }
+    return BIP_OK;
+}
+
+// dL/dV_j through the S2 sweep (x_j = T_j Prop(x_{j+1})), j >= the first
+// ionization plane, ascending, from the window adjoints dtbar2
+bip_status adjoint_s2(bip_ctx* c, const float* V, float* dV, cudaStream_t s) {
+    const bip_config& g = c->cfg;
+    const size_t G = (size_t)g.ny * g.nx;
+    const int ncol = c->geo.Bp2;
+    int first = g.nz;
+    for (auto& sd : c->sites) first = std::min(first, (int)sd.plane);
+    if (first >= g.nz) return BIP_OK;
+    const int n = g.nz - first, k = isqrt_up(n), nck = (n + k - 1) / k;
+    const size_t state = (size_t)ncol * G;
+    CUDA_TRY(c, ensure(c->g_adj, state * sizeof(float2), false, s));
+    CUDA_TRY(c, ensure(c->g_ckpt, (size_t)nck * state * sizeof(float2), false, s));
+    CUDA_TRY(c, ensure(c->g_seg, (size_t)k * state * sizeof(float2), false, s));
+    CUDA_TRY(c, ensure(c->g_gvp, (size_t)ncol * G * sizeof(float), false, s));
+    MsPlan fp = plan_for(c, ncol, c->shift2), cp = fp;
+    cp.py = (const float2*)c->pyc.p;
+    cp.px = (const float2*)c->pxc.p;
+    float2* cols = (float2*)c->cols.p;
+    float2* adj = (float2*)c->g_adj.p;
+    auto row_off = [&](int j) -> const int32_t* {
+        return c->plane_off[j + 1] > c->plane_off[j] ? (const int32_t*)c->row_off_d.p + (size_t)j * (g.ny + 1) : nullptr;
+    };
+    auto fwd_row = [&](int j, float2* save, bool fft) -> cudaError_t {
+        MsRowArgs a{};
+        a.cols = cols;
+        a.do_ifft = 1;
+        a.v_pre = V + (size_t)j * G;
+        a.do_fft = fft;
+        a.win = g.win;
+        a.save = save;
+        return bip_ms_row_pass(fp, a, s);
+    };
+    // forward: the start column, then j = nz-1 down, keeping the field at the
+    // start of row pass j for j = nz-1 - m k
+    {
+        MsRowArgs a{};
+        a.cols = cols;
+        a.init = 1;
+        a.init_val = (float)(1.0 / std::sqrt((double)G));
+        a.do_fft = 1;
+        a.win = g.win;
+        CUDA_TRY(c, bip_ms_row_pass(fp, a, s));
+        CUDA_TRY(c, bip_ms_col_pass(fp, cols, s));
+    }
+    const int lowest_ck = g.nz - 1 - (nck - 1) * k;
+    for (int j = g.nz - 1; j >= lowest_ck; --j) {
+        if ((g.nz - 1 - j) % k == 0)
+            CUDA_TRY(c, cudaMemcpyAsync((float2*)c->g_ckpt.p + (size_t)((g.nz - 1 - j) / k) * state, cols,
+                                        state * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+        if (j == lowest_ck) break;
+        CUDA_TRY(c, fwd_row(j, nullptr, true));
+        CUDA_TRY(c, bip_ms_col_pass(fp, cols, s));
+    }
+    int groups = 0;
+    for (int m = nck - 1; m >= 0; --m) {
+        const int jhi = g.nz - 1 - m * k, jlo = std::max(first, jhi - k + 1);
+        CUDA_TRY(c, cudaMemcpyAsync(cols, (float2*)c->g_ckpt.p + (size_t)m * state, state * sizeof(float2),
+                                    cudaMemcpyDeviceToDevice, s));
+        for (int j = jhi; j >= jlo; --j) {
+            CUDA_TRY(c, fwd_row(j, (float2*)c->g_seg.p + (size_t)(j - jlo) * state, j > jlo));
+            if (j > jlo) CUDA_TRY(c, bip_ms_col_pass(fp, cols, s));
+        }
+        for (int j = jlo; j <= jhi; ++j) {
+            MsAdjArgs a{};
+            a.cols = adj;
+            a.zero_in = j == first;
+            a.do_ifft = j > first;
+            a.v = V + (size_t)j * G;
+            a.state = (const float2*)c->g_seg.p + (size_t)(j - jlo) * state;
+            a.state_times_T = 0;
+            a.inj_before = 1;
+            a.row_off = row_off(j);
+            a.row_ent = (const int4*)c->row_ent_d.p;
+            a.win = g.win;
+            a.inj = (const float2*)c->g_dt2.p;
+            a.gv_part = (float*)c->g_gvp.p;
+            a.do_fft = j < g.nz - 1;
+            CUDA_TRY(c, bip_ms_adj_row_pass(fp, a, &groups, s));
+            CUDA_TRY(c, bip_gv_reduce((const float*)c->g_gvp.p, groups, (int)G, dV + (size_t)j * G, s));
+            if (j < g.nz - 1) CUDA_TRY(c, bip_ms_col_pass(cp, adj, s));
+        }
+    }
     return BIP_OK;
 }
 
@@ -1259,10 +1506,12 @@ bip_status bip_set_aberrations(bip_ctx* c, double defocus, double cs, void* stre
     return BIP_OK;
 }
 
-bip_status bip_coreloss_grad(bip_ctx* c, const void* H, const double* scan_px, int32_t P, const double* dL_dI,
-                             double* d_occ, void* d_H, double* d_aberr, void* stream) {
+bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const double* scan_px, int32_t P,
+                             const double* dL_dI, double* d_occ, void* d_H, double* d_aberr, float* d_V,
+                             void* stream) {
     bip_status st = check_map_args(c, H, scan_px, P, dL_dI);
     if (st != BIP_OK) return st;
+    if (d_V && !V) return fail(c, BIP_ERR_INVALID_ARG, "d_V needs the V the matrices were built from");
     if ((reinterpret_cast<uintptr_t>(d_H) & 7) != 0) return fail(c, BIP_ERR_INVALID_ARG, "d_H must be 8-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     const bip_config& g = c->cfg;
@@ -1276,7 +1525,18 @@ bip_status bip_coreloss_grad(bip_ctx* c, const void* H, const double* scan_px, i
         if (st != BIP_OK) return st;
         CUDA_TRY(c, bip_grad_occ((const float*)c->partial.p, c->n_sites, P, dL_dI, d_occ, s));
     }
-    if (!d_H && !d_aberr) return BIP_OK;
+    if (!d_H && !d_aberr && !d_V) return BIP_OK;
+    if (d_V) {
+        st = adj_tables(c, s);
+        if (st != BIP_OK) return st;
+        CUDA_TRY(c, ensure(c->g_dt1, (size_t)c->n_sites * geo.Bp1 * K * sizeof(float2), false, s));
+        CUDA_TRY(c, ensure(c->g_dt2, (size_t)c->n_sites * geo.Bp2 * K * sizeof(float2), false, s));
+        CUDA_TRY(c, ensure(c->g_s1bar, (size_t)std::min(c->n_sites, 8) * Bpad * K * sizeof(float2), true, s));
+        CUDA_TRY(c, ensure(c->g_s2bar, (size_t)std::min(c->n_sites, 8) * Dpad * K * sizeof(float2), true, s));
+        const size_t rows = (size_t)std::max(Bpad, Dpad);
+        CUDA_TRY(c, ensure(c->g_ubar, (size_t)std::min(c->n_sites, 8) * rows * K * sizeof(float2), false, s));
+        CUDA_TRY(c, ensure(c->g_dA, (size_t)std::min(c->n_sites, 8) * rows * K * sizeof(float), false, s));
+    }
     // FP32 contraction per batch of sites: S2, H_n S1 and S1 windows, M (as
     // Mt[b][(n, d)]), Q, then the reverse steps
     CUDA_TRY(c, ensure(c->scans_d, (size_t)P * 2 * sizeof(double), false, s));
@@ -1362,7 +1622,7 @@ bip_status bip_coreloss_grad(bip_ctx* c, const void* H, const double* scan_px, i
             CUDA_TRY(c, bip_grad_aberr(B, Bpad, nb, (const float2*)c->q32.p, (int64_t)perQ, (const float2*)c->g_R.p,
                                        (int64_t)perQ, (double2*)c->g_D.p, (double2*)c->g_Dsum.p, s));
         }
-        if (d_H) {
+        if (d_H || d_V) {
             // Mbar_n = M_n R, kept as GMt = conj(R) Mt (R Hermitian)
             CGemmGen m{};
             m.M = B; m.N = (int)ldm; m.K = B; m.batch = nb;
@@ -1380,9 +1640,62 @@ bip_status bip_coreloss_grad(bip_ctx* c, const void* H, const double* scan_px, i
                 t.C = (float2*)c->g_T.p + (size_t)n * B * K; t.scm = K; t.scn = 1; t.scb = (int64_t)perT;
                 CUDA_TRY(c, bip_cgemm_gen(t, s));
             }
-            CUDA_TRY(c, bip_grad_h(ga, nb, ids, nch, (const float2*)c->g_s1.p, (int64_t)perS1,
-                                   (const float2*)c->g_T.p, (int64_t)perT, (int64_t)B * K, (float2*)d_H, s));
+            if (d_H)
+                CUDA_TRY(c, bip_grad_h(ga, nb, ids, nch, (const float2*)c->g_s1.p, (int64_t)perS1,
+                                       (const float2*)c->g_T.p, (int64_t)perT, (int64_t)B * K, (float2*)d_H, s));
         }
+        if (d_V) {
+            // S1bar_b(r) = sum_n conj H_n(r) T_n(b, r);
+            // S2bar_d(r) = sum_n sum_b Mbar_n(d, b) conj(H_n(r) S1_b(r))
+            CUDA_TRY(c, bip_s1bar(nb, ids, (const SiteDev*)c->sites_d.p, B, K, (const float2*)H,
+                                  (const float2*)c->g_T.p, (int64_t)perT, (int64_t)B * K, (float2*)c->g_s1bar.p,
+                                  (int64_t)perS1, s));
+            for (int n = 0; n < nch; ++n) {
+                CGemmGen u{};
+                u.M = geo.n_det; u.N = K; u.K = B; u.batch = nb;
+                u.A = (const float2*)c->g_gmt.p + (size_t)n * Dpad; u.sam = 1; u.sak = (int64_t)ldm;
+                u.sab = (int64_t)perMt;
+                u.B = (const float2*)c->opB32.p + (size_t)n * Bpad * K; u.sbk = K; u.sbn = 1; u.sbb = (int64_t)perB;
+                u.conjB = 1;
+                u.C = (float2*)c->g_s2bar.p; u.scm = K; u.scn = 1; u.scb = (int64_t)perA;
+                u.accumulate = n > 0;
+                CUDA_TRY(c, bip_cgemm_gen(u, s));
+            }
+            // back through the reconstructions into the window adjoints
+            for (int side = 1; side <= 2; ++side) {
+                ReconAdjArgs ra{};
+                ra.n_sites = nb;
+                ra.site_ids = ids;
+                ra.sites = (const SiteDev*)c->sites_d.p;
+                ra.K = K; ra.win = g.win; ra.ny = g.ny; ra.nx = g.nx;
+                ra.magnitude = g.recon == BIP_RECON_MAGNITUDE;
+                if (side == 1) {
+                    ra.Bp = geo.Bp1; ra.n_targets = B; ra.tilt_sign = +1;
+                    ra.h_t = (const int2*)c->hbeam.p;
+                    ra.stash = (const float2*)c->stash1.p;
+                    ra.w = adj_weights(c->aw1);
+                    ra.Sbar = (const float2*)c->g_s1bar.p; ra.sbar_rows = Bpad;
+                    ra.dtbar = (float2*)c->g_dt1.p;
+                } else {
+                    ra.Bp = geo.Bp2; ra.n_targets = geo.n_det; ra.tilt_sign = -1;
+                    ra.h_t = (const int2*)c->hdet.p;
+                    ra.stash = (const float2*)c->stash2.p;
+                    ra.w = adj_weights(c->aw2);
+                    ra.Sbar = (const float2*)c->g_s2bar.p; ra.sbar_rows = Dpad;
+                    ra.dtbar = (float2*)c->g_dt2.p;
+                }
+                ra.Ubar = (float2*)c->g_ubar.p;
+                ra.dA = (float*)c->g_dA.p;
+                CUDA_TRY(c, bip_recon_adjoint(ra, s));
+            }
+        }
+    }
+    if (d_V) {
+        CUDA_TRY(c, cudaMemsetAsync(d_V, 0, (size_t)g.nz * g.ny * g.nx * sizeof(float), s));
+        st = adjoint_s1(c, V, d_V, s);
+        if (st != BIP_OK) return st;
+        st = adjoint_s2(c, V, d_V, s);
+        if (st != BIP_OK) return st;
     }
     if (d_aberr) {
         std::vector<double2> D(B);

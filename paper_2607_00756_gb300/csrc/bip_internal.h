@@ -91,6 +91,8 @@ struct MsRowArgs {
     const int4* row_ent;
     int win;
     float2* stash;                  // [n_sites_total, ncol, win, win]
+    float2* save;                   // the real-space field at the stash point,
+                                    // [ncol, ny, nx] (null: not kept)
 };
 cudaError_t bip_ms_row_pass(const MsPlan& plan, const MsRowArgs& a, cudaStream_t s);
 cudaError_t bip_ms_col_pass(const MsPlan& plan, float2* cols, cudaStream_t s);
@@ -335,6 +337,60 @@ cudaError_t bip_cube_accumulate(const CubeArgs& a, cudaStream_t s);
 // qEELS: out[rho][bin_of[d]] = sum of cube[rho][d] over the beams of a bin
 cudaError_t bip_qeels_bin(const float* cube, int P, int n_det, const int32_t* bin_of, int n_bins, float* out,
                           cudaStream_t s);
+
+// adjoint_ms.cu : the reverse pass through the reconstruction and the two
+// multislice sweeps, in the de-tilted frame of the forward sweep (where a
+// site's stash is the column itself, so window adjoints enter unchanged).
+// Adjoint row pass: [inverse row FFT] [+inj if inj_before] [gV] [x conj T]
+// [+inj if after] [row FFT]; with a column pass on conjugated propagator
+// tables it applies Prop^H.  gV: -2 sigma sum_p Im(conj(val) u), val the
+// adjoint field at that point and u = T_j state (S1) or state (S2), summed
+// over the block's parents into gv_part[group][y][x].
+struct MsAdjArgs {
+    float2* cols;                   // adjoint field [ncol, ny, nx]
+    int zero_in;                    // 1: the incoming field is zero
+    int do_ifft, do_fft;
+    const float* v;                 // V_j: multiply by conj(T_j) (null: none)
+    const float2* state;            // forward state [ncol, ny, nx] real space (null: no gV)
+    int state_times_T;              // 1: u = T_j state (S1), 0: u = state (S2)
+    int inj_before;                 // 1: inject before gV and conj(T_j) (S2)
+    const int32_t* row_off;         // injection windows of this plane (as MsRowArgs)
+    const int4* row_ent;
+    int win;
+    const float2* inj;              // [n_sites_total, ncol, win, win]
+    float* gv_part;                 // [groups][ny][nx]
+};
+cudaError_t bip_ms_adj_row_pass(const MsPlan& plan, const MsAdjArgs& a, int* groups, cudaStream_t s);
+// gV[y][x] += sum_g part[g][y][x] (groups in order)
+cudaError_t bip_gv_reduce(const float* part, int groups, int G, float* gV, cudaStream_t s);
+// per-target / per-parent transposed weights of one side
+struct AdjWeights {
+    const int32_t* t_off;           // [n_targets + 1]
+    const int32_t* t_par;           // parents of each target
+    const float* t_w;
+    const int32_t* p_off;           // [Bp + 1]
+    const int32_t* p_tgt;           // targets of each parent
+    const float* p_w;
+};
+struct ReconAdjArgs {
+    int n_sites;                    // batch
+    const int32_t* site_ids;
+    const SiteDev* sites;
+    int K, win, ny, nx, Bp, n_targets;
+    int magnitude, tilt_sign;
+    const int2* h_t;
+    const float2* stash;            // [n_sites_total][Bp][K]
+    AdjWeights w;
+    const float2* Sbar;             // [bs][rows][K] dL/dS*, row stride sbar_rows
+    int sbar_rows;
+    float2* Ubar;                   // scratch [bs][n_targets][K]
+    float* dA;                      // scratch [bs][n_targets][K]
+    float2* dtbar;                  // out [n_sites_total][Bp][K] (overwritten for the batch's sites)
+};
+cudaError_t bip_recon_adjoint(const ReconAdjArgs& a, cudaStream_t s);
+// S1bar[bs][b][r] = sum_n conj H_n(r) T[bs][n][b][r]
+cudaError_t bip_s1bar(int nb, const int32_t* ids, const SiteDev* sites, int B, int K, const float2* H,
+                      const float2* T, int64_t t_site, int64_t t_ch, float2* S1bar, int64_t s1_site, cudaStream_t s);
 
 // grad.cu : reverse pass of a map loss through the contraction
 // generic complex GEMM: C(m, n) (+)= sum_k opA(A(m, k) dk[k]) opB(B(k, n)),

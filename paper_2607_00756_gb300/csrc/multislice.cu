@@ -12,7 +12,7 @@
 // unnormalised forward/inverse FFT pair.
 //
 // One step of a column is two passes over global memory:
-//   row pass    [inverse FFT along x] [T_pre] [stash] [T_post] [FFT along x]
+//   row pass    [inverse FFT along x] [T_pre] [stash, save] [T_post] [FFT along x]
 //   column pass FFT along y, times the shifted propagator, inverse FFT along y
 // with T_j = exp(i sigma V_j) evaluated in-kernel from V (sincosf).
 #include <cstdio>
@@ -67,6 +67,11 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(MsPlan plan, MsRowAr
     if (a.v_pre) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = c_mul(v[m], tt[t + m * NT]);
+    }
+    if (active && a.save) {
+        float2* o = a.save + ((size_t)c * plan.ny + y) * NX;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) o[t + m * NT] = v[m];
     }
     if (active && a.row_off) {
         const int e1 = __ldg(&a.row_off[y + 1]);

@@ -1,7 +1,9 @@
 """GPU parity of the reverse pass (bip_coreloss_grad and the torch.autograd
 bridge) against the oracle's hand-written reverse pass (oracle/grad.py,
 itself pinned by finite differences): occupancies, transition potentials H
-(and through them the transition amplitudes), probe defocus and Cs.  The
+(and through them the transition amplitudes), probe defocus and Cs, and the
+slice potentials V (through the reconstruction and both sweeps, with the
+sweeps' forward states recomputed from checkpoints).  The
 same dL/dI (from the oracle's forward map) drives both sides.  Tolerance:
 rel <= 1e-4 on the FP32 path (the gradient contractions are FP32), the
 occupancies through a mixed-precision context's partials at 1e-3."""
@@ -154,4 +156,64 @@ def test_grad_config5(lib):
     assert rel(got["H"].cpu().numpy(), wH) < 1e-4
     for name in ("defocus", "cs"):
         assert got[name] == pytest.approx(want[name], rel=1e-4), (name, got[name], want[name])
+    ctx.close()
+
+
+@pytest.mark.parametrize("which", ["small_magnitude", "small_complex", "config1"])
+def test_grad_V_matches_oracle(lib, which):
+    if which == "config1":
+        cfg, sp, pr, par, target = config1_case()
+    else:
+        cfg, sp, pr, par, target = small_case(which.split("_")[1])
+    I = og.forward(pr, par)
+    gI = 2.0 * (I - target)
+    _, want = og.gradients(pr, par, dL_dI=gI)
+    ctx, H = _gpu(lib, cfg, sp)
+    ctx.set_occupancy(par.occ)
+    V = torch.tensor(sp.V, dtype=torch.float32, device=H.device)
+    got = ctx.grad(H, sp.scans, torch.tensor(gI, device=H.device), occ=False, h=False, aberr=False, V=V)
+    gV = got["V"].cpu().numpy()
+    assert gV.shape == want["V"].shape
+    assert np.linalg.norm(want["V"]) > 0
+    assert rel(gV, want["V"]) < 1e-4, rel(gV, want["V"])
+    ctx.close()
+
+
+def test_autograd_V(lib):
+    """loss.backward() with V a leaf: the matrices are built from V inside
+    the call and V.grad matches the oracle."""
+    from paper_2607_00756_gb300.autograd import coreloss_map
+    cfg, sp, pr, par, target = small_case()
+    L_want, want = og.gradients(pr, par, target)
+    dev = torch.device("cuda:0")
+    ctx = lib(cfg, prec="fp32")
+    V = torch.tensor(sp.V, dtype=torch.float32, device=dev, requires_grad=True)
+    H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+    occ = torch.tensor(par.occ, dtype=torch.float64, device=dev)
+    m = coreloss_map(ctx, H, sp.scans, occ=occ, V=V, atoms=sp.atoms, nch=sp.nch)
+    loss = ((m - torch.tensor(target, device=dev)) ** 2).sum()
+    loss.backward()
+    assert float(loss.detach()) == pytest.approx(L_want, rel=1e-4)
+    assert rel(V.grad.cpu().numpy(), want["V"]) < 1e-4
+    ctx.close()
+
+
+@pytest.mark.slow
+def test_grad_V_config5(lib):
+    """The slice-potential derivative on the differentiation workload: 40
+    slices, sites at planes 8..32, so both sweeps run through several
+    checkpoint segments."""
+    cfg = synth.config5()
+    sp = synth.make_specimen(cfg)
+    pr = obip.make_problem(sp)
+    rng = np.random.default_rng(56)
+    par = og.Params(pr)
+    I = og.forward(pr, par)
+    target = I * (1.0 + 0.05 * rng.standard_normal(I.shape))
+    gI = 2.0 * (I - target)
+    _, want = og.gradients(pr, par, dL_dI=gI)
+    ctx, H = _gpu(lib, cfg, sp)
+    V = torch.tensor(sp.V, dtype=torch.float32, device=H.device)
+    got = ctx.grad(H, sp.scans, torch.tensor(gI, device=H.device), occ=False, h=False, aberr=False, V=V)
+    assert rel(got["V"].cpu().numpy(), want["V"]) < 1e-4
     ctx.close()
