@@ -204,6 +204,26 @@ bip_status bip_qeels_bins(const bip_ctx* ctx, int32_t axis, int32_t* n_bins, int
 bip_status bip_coreloss_qeels(bip_ctx* ctx, const void* H, const double* scan_px, int32_t P,
                               int32_t axis, float* qeels_out, void* stream);
 
+/* Launch control.
+ * bip_set_capture_safe(ctx, on): the map calls issue no host
+ *   synchronisation and upload the scan list and work lists only when they
+ *   change, so that after one warm-up call with the same arguments a CUDA
+ *   graph can capture them (several contexts -- specimens of uneven size --
+ *   into one graph).  Device timeouts are then reported by
+ *   bip_check_errors (which synchronises the stream) instead of by the map.
+ * bip_set_launch: sites per batch and coupling tile width (multiple of 16,
+ *   <= 256) of the tensor-core path; 0 restores the built-in choice (tile
+ *   counts against the SM count and the L2 size).
+ * bip_autotune: times maps (two after a warm-up, CUDA events) over sites per
+ *   batch and then coupling tile widths, keeps the fastest in the context
+ *   and returns it; map_out holds the last map.  Results do not depend on
+ *   these choices (each site's arithmetic and the site-sum order are fixed). */
+bip_status bip_set_capture_safe(bip_ctx* ctx, int32_t on);
+bip_status bip_check_errors(bip_ctx* ctx, void* stream);
+bip_status bip_set_launch(bip_ctx* ctx, int32_t sites_per_batch, int32_t coupling_tile);
+bip_status bip_autotune(bip_ctx* ctx, const void* H, const double* scan_px, int32_t P, double* map_out,
+                        void* stream, int32_t* sites_per_batch, int32_t* coupling_tile, double* best_ms);
+
 /* Model parameters of the map beyond the specimen (for fitting; Sec. 5
  * names the matrices as a forward model for simulation-constrained
  * reconstruction).

@@ -69,6 +69,10 @@ def _load():
         "bip_build_s1_noalloc": [VP, VP, P(BipAtom), I32, VP, VP],
         "bip_get_profile": [VP, VP, VP],
         "bip_set_occupancy": [VP, P(D)],
+        "bip_set_capture_safe": [VP, I32],
+        "bip_check_errors": [VP, VP],
+        "bip_set_launch": [VP, I32, I32],
+        "bip_autotune": [VP, VP, P(D), I32, VP, VP, P(I32), P(I32), P(D)],
         "bip_set_aberrations": [VP, D, D, VP],
         "bip_coreloss_grad": [VP, VP, VP, P(D), I32, VP, VP, VP, P(D), VP, VP],
     }
@@ -267,6 +271,30 @@ def bip_site_coupling(ctx, H, site, out, stream=None):
     _check("bip_site_coupling", ctx, _lib.bip_site_coupling(ctx, _dev(H, torch.complex64, "H"), site,
                                                              _dev(out, torch.complex64, "out"), _stream(stream)))
     return out
+
+
+def bip_set_capture_safe(ctx, on):
+    _check("bip_set_capture_safe", ctx, _lib.bip_set_capture_safe(ctx, 1 if on else 0))
+
+
+def bip_check_errors(ctx, stream=None):
+    _check("bip_check_errors", ctx, _lib.bip_check_errors(ctx, _stream(stream)))
+
+
+def bip_set_launch(ctx, sites_per_batch=0, coupling_tile=0):
+    _check("bip_set_launch", ctx, _lib.bip_set_launch(ctx, int(sites_per_batch), int(coupling_tile)))
+
+
+def bip_autotune(ctx, H, scans, out, stream=None):
+    """Times launch choices on this map; returns (sites per batch, coupling
+    tile width (0: built-in), ms per map) and keeps them in the context."""
+    import torch
+    s, sp = _scans(scans)
+    sb, cw, ms = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
+    _check("bip_autotune", ctx, _lib.bip_autotune(ctx, _dev(H, torch.complex64, "H"), sp, len(s),
+                                                   _dev(out, torch.float64, "out"), _stream(stream),
+                                                   ctypes.byref(sb), ctypes.byref(cw), ctypes.byref(ms)))
+    return sb.value, cw.value, ms.value
 
 
 def bip_set_occupancy(ctx, occ):

@@ -92,6 +92,17 @@ class BipContext:
         out = torch.empty((nch, self.n_det, self.B), dtype=torch.complex64, device=device)
         return capi.bip_site_coupling(self.ctx, H, site, out)
 
+    def autotune(self, H, scans, out=None, stream=None):
+        """Time launch choices on this map and keep the fastest: returns
+        (sites per batch, coupling tile width (0: built-in), ms per map)."""
+        scans = np.asarray(scans, dtype=np.float64)
+        if out is None:
+            out = torch.empty(len(scans), dtype=torch.float64, device=H.device)
+        return capi.bip_autotune(self.ctx, H, scans, out, stream)
+
+    def set_launch(self, sites_per_batch=0, coupling_tile=0):
+        capi.bip_set_launch(self.ctx, sites_per_batch, coupling_tile)
+
     def set_occupancy(self, occ):
         """Per-site occupancies weighting the site sum (None: all 1)."""
         capi.bip_set_occupancy(self.ctx, None if occ is None else np.asarray(occ, dtype=np.float64))

@@ -62,6 +62,14 @@ struct bip_ctx {
     DevBuf g_s1, g_w, g_R, g_gmt, g_T, g_D, g_Dsum;   // gradient pass workspaces
     DevBuf g_s1bar, g_s2bar, g_ubar, g_dA, g_dt1, g_dt2, g_adj, g_ckpt, g_seg, g_gvp;
     DevBuf pyc, pxc;                    // conjugated propagator tables (adjoint sweeps)
+    // capture-safe maps: no host synchronisation, uploads only when the
+    // scans or the batching change (so a CUDA graph can hold the launches)
+    bool capture_safe = false;
+    std::vector<double> scans_cache;
+    std::vector<int> batch_off_cache;
+    uint64_t work_key = 0;
+    // tuned launch parameters (0: the built-in choice)
+    int sb_override = 0, cw_override = 0;
     DevBuf aw1[6], aw2[6];              // per-target / per-parent weights (reconstruction adjoint)
     bool adj_tables = false;
     DevBuf f8pmax, f8inv0, f8inv1, f8hmax, f8H, f8sA, f8sB;   // FP8 per-window scales
@@ -1160,8 +1168,14 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     const int n_tiles = (P + tile - 1) / tile;
     const int nd = (2 * c->Ky + 1) * (4 * c->Kx + 1);
 
-    CUDA_TRY(c, ensure(c->scans_d, (size_t)P * 2 * sizeof(double), false, s));
-    CUDA_TRY(c, cudaMemcpyAsync(c->scans_d.p, scans, (size_t)P * 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+    // the scan list, uploaded unless a capture-safe context already holds it
+    const bool same_scans = c->capture_safe && c->scans_cache.size() == (size_t)P * 2 &&
+                            std::equal(scans, scans + 2 * P, c->scans_cache.begin());
+    if (!same_scans) {
+        CUDA_TRY(c, ensure(c->scans_d, (size_t)P * 2 * sizeof(double), false, s));
+        CUDA_TRY(c, cudaMemcpyAsync(c->scans_d.p, scans, (size_t)P * 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+        c->scans_cache.assign(scans, scans + 2 * P);
+    }
     float* partial = partial_out;
     if (cube_out) {
         // the cube: c_b(rho) for every scan, the cube cleared
@@ -1193,7 +1207,8 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         bb[4 * t] = y0; bb[4 * t + 1] = y1; bb[4 * t + 2] = x0; bb[4 * t + 3] = x1;
     }
 
-    const int SB = tc ? tc_batch(c) : std::min(c->n_sites, 8);
+    const int SB = c->sb_override > 0 ? std::min(c->n_sites, c->sb_override)
+                                      : (tc ? tc_batch(c) : std::min(c->n_sites, 8));
     const size_t rowsA = Dpad, rowsB = (size_t)nch * Bpad;
     const size_t perA = rowsA * K, perB = rowsB * K;
     const size_t perMt = (size_t)Bpad * nch * Dpad, perQ = (size_t)Bpad * Bpad;
@@ -1224,9 +1239,15 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     }
 
     // work lists (site in batch, scan tile) for all batches, uploaded once
+    // (kept across calls of a capture-safe context while scans, sites and
+    // batching are unchanged)
+    const uint64_t work_key = (c->sig1 * 1000003ull) ^ ((uint64_t)SB << 32) ^ (uint64_t)P;
+    const bool same_work = same_scans && c->work_key == work_key;
     std::vector<int32_t>& work = c->work_h;
+    std::vector<int>& batch_off = c->batch_off_cache;
+    if (!same_work) {
     work.clear();
-    std::vector<int> batch_off;
+    batch_off.clear();
     for (int b0 = 0; b0 < c->n_sites; b0 += SB) {
         batch_off.push_back((int)work.size() / 2);
         for (int bs = 0; bs < std::min(SB, c->n_sites - b0); ++bs) {
@@ -1240,6 +1261,8 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     }
     batch_off.push_back((int)work.size() / 2);
     CUDA_TRY(c, upload(c->work_d, work, s));
+    c->work_key = work_key;
+    }
 
     int bi = 0;
     for (int b0 = 0; b0 < c->n_sites; b0 += SB, ++bi) {
@@ -1281,7 +1304,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             // tiles and a narrower last one) as B; written as Mt[b][ch Dp + d]
             TcArgs A{};
             A.epi = TC_EPI_ROWS;
-            A.N = tile_width(Dpad);
+            A.N = c->cw_override > 0 ? std::min(c->cw_override, Dpad) : tile_width(Dpad);
             A.npl = npl;
             A.out_planes = npl;
             A.A = TcOperand{c->opB16.p, (int64_t)SB * npl * (int64_t)rowsB, K, npl * (int64_t)rowsB, (int64_t)rowsB};
@@ -1401,7 +1424,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_bin(d, s));
         if (d.n_work > 0) TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_eval(d, s));
     }
-    if (tc) {
+    if (tc && !c->capture_safe) {
         int flag = 0;
         CUDA_TRY(c, cudaMemcpyAsync(&flag, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(c, cudaStreamSynchronize(s));
@@ -1478,6 +1501,103 @@ bip_status bip_coreloss_qeels(bip_ctx* c, const void* H, const double* scan_px, 
     if (st != BIP_OK) return st;
     CUDA_TRY(c, bip_qeels_bin((const float*)c->cube_scratch.p, P, c->geo.n_det, (const int32_t*)c->bin_of_d.p,
                               (int)bins.size(), qeels_out, s));
+    return BIP_OK;
+}
+
+bip_status bip_set_capture_safe(bip_ctx* c, int32_t on) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    c->capture_safe = on != 0;
+    c->scans_cache.clear();
+    c->work_key = 0;
+    return BIP_OK;
+}
+
+bip_status bip_check_errors(bip_ctx* c, void* stream) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (!c->errflag.p) return BIP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int flag = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&flag, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (flag) {
+        CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
+        return fail(c, BIP_ERR_TIMEOUT, "a tensor-core contraction gave up waiting (device timeout)");
+    }
+    return BIP_OK;
+}
+
+bip_status bip_set_launch(bip_ctx* c, int32_t sites_per_batch, int32_t coupling_tile) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (sites_per_batch < 0 || coupling_tile < 0 || coupling_tile > 256 || coupling_tile % 16)
+        return fail(c, BIP_ERR_INVALID_ARG, "sites_per_batch >= 0, coupling_tile a multiple of 16 in 0..256");
+    c->sb_override = sites_per_batch;
+    c->cw_override = coupling_tile;
+    return BIP_OK;
+}
+
+bip_status bip_autotune(bip_ctx* c, const void* H, const double* scan_px, int32_t P, double* map_out, void* stream,
+                        int32_t* sites_per_batch, int32_t* coupling_tile, double* best_ms) {
+    bip_status st = check_map_args(c, H, scan_px, P, map_out);
+    if (st != BIP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool tc = c->prec != BIP_PREC_FP32;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(c, BIP_ERR_CUDA, "cudaEventCreate");
+    }
+    // mean device time of two maps after one warm-up map (allocations, uploads)
+    auto time_map = [&](int sb, int cw, double* ms) -> bip_status {
+        c->sb_override = sb;
+        c->cw_override = cw;
+        bip_status r = run_map(c, H, scan_px, P, nullptr, map_out, nullptr, s);
+        if (r != BIP_OK) return r;
+        CUDA_TRY(c, cudaEventRecord(e0, s));
+        for (int i = 0; i < 2 && r == BIP_OK; ++i) r = run_map(c, H, scan_px, P, nullptr, map_out, nullptr, s);
+        if (r != BIP_OK) return r;
+        CUDA_TRY(c, cudaEventRecord(e1, s));
+        CUDA_TRY(c, cudaEventSynchronize(e1));
+        float t = 0.f;
+        CUDA_TRY(c, cudaEventElapsedTime(&t, e0, e1));
+        *ms = t / 2.0;
+        return BIP_OK;
+    };
+    std::vector<int> sbs;
+    const int base = tc ? tc_batch(c) : std::min(c->n_sites, 8);
+    for (int v : tc ? std::vector<int>{base, 16, 19, 20, 24, 28, 32} : std::vector<int>{base, 4, 8, 16})
+        if (v >= 1 && v <= std::max(1, c->n_sites) && std::find(sbs.begin(), sbs.end(), v) == sbs.end())
+            sbs.push_back(v);
+    int best_sb = base, best_cw = 0;
+    double best = 1e300, t = 0.0;
+    for (int sb : sbs) {
+        st = time_map(sb, 0, &t);
+        if (st != BIP_OK) break;
+        if (t < best) {
+            best = t;
+            best_sb = sb;
+        }
+    }
+    if (st == BIP_OK && tc) {
+        // coupling tile width: the built-in even split, or fixed widths
+        for (int cw : {128, 160, 192, 224, 256}) {
+            if (cw > c->Dpad) continue;
+            st = time_map(best_sb, cw, &t);
+            if (st != BIP_OK) break;
+            if (t < best) {
+                best = t;
+                best_cw = cw;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->sb_override = best_sb;
+    c->cw_override = best_cw;
+    if (st != BIP_OK) return st;
+    if (sites_per_batch) *sites_per_batch = best_sb;
+    if (coupling_tile) *coupling_tile = best_cw;
+    if (best_ms) *best_ms = best;
     return BIP_OK;
 }
 

@@ -1,0 +1,90 @@
+"""Batched evaluation under a CUDA graph and the launch autotuner.
+
+Specimens of uneven size -- grids 64x128 to 256^2, 4 to 12 slices, f = 1, 2
+and 4, one, three and nine channels, FP32, mixed and FP8 contexts -- are
+captured into one CUDA graph; every replay must reproduce the eager maps
+bit for bit, and each map matches the oracle within its precision's
+tolerance.  The autotuner must return valid choices whose map equals the
+built-in choice's (the site arithmetic and the site-sum order do not depend
+on the launch shape)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import bip as obip
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2607_00756_gb300 import build
+    build.build()
+    from paper_2607_00756_gb300.context import BipContext
+    return BipContext
+
+
+def specimens():
+    c1 = synth.config1()
+    return [
+        (c1, "mixed", 1e-3),
+        (c1.replace(name="nine", seed=3, channels=tuple(range(-4, 5))), "fp32", 1e-4),
+        (synth.config1().replace(name="aniso", ny=64, nx=128, ly=7.5, lx=10.0, cells_y=3, cells_x=4, fy=1, fx=2,
+                                 win=32, ion_cells=(1, 3), ion_slices=(1, 4), channels=(0,),
+                                 scan_y=(10.3, 3.5, 9), scan_x=(20.7, 6.25, 7)), "mixed", 1e-3),
+        (synth.config1().replace(name="wide", ny=256, nx=256, ly=20.0, lx=20.0, nz=12, cells_y=8, cells_x=8,
+                                 fy=4, fx=4, ion_cells=(3, 5), ion_slices=(3, 12, 4), seed=7,
+                                 scan_y=(100.0, 4.0, 12), scan_x=(100.0, 4.0, 12)), "fp8", None),
+    ]
+
+
+def test_graph_replay_matches_eager_and_oracle(lib):
+    from paper_2607_00756_gb300.graphs import GraphedMaps
+    dev = torch.device("cuda:0")
+    items, eager, refs, tols = [], [], [], []
+    for cfg, prec, tol in specimens():
+        sp = synth.make_specimen(cfg)
+        ctx = lib(cfg, prec=prec)
+        ctx.build(torch.tensor(sp.V, dtype=torch.float32, device=dev), sp.atoms, sp.nch)
+        H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+        eager.append(ctx.map(H, sp.scans).cpu().numpy())
+        items.append((ctx, H, sp.scans))
+        refs.append(obip.bip_map(obip.make_problem(sp)).map)
+        tols.append(tol)
+    g = GraphedMaps(items)
+    for _ in range(3):
+        outs = g.replay()
+        torch.cuda.synchronize()
+        g.check()
+        for o, e in zip(outs, eager):
+            assert np.array_equal(o.cpu().numpy(), e)
+    for e, r, tol in zip(eager, refs, tols):
+        # the FP8 context: within 3% (its E4M3 rounding), the others their bars
+        assert rel(e, r) < (tol if tol is not None else 3e-2)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+def test_autotune_keeps_the_map(lib, prec):
+    cfg = synth.config1()
+    sp = synth.make_specimen(cfg)
+    dev = torch.device("cuda:0")
+    ctx = lib(cfg, prec=prec)
+    ctx.build(torch.tensor(sp.V, dtype=torch.float32, device=dev), sp.atoms, sp.nch)
+    H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+    m0 = ctx.map(H, sp.scans).cpu().numpy()
+    sb, cw, ms = ctx.autotune(H, sp.scans)
+    assert 1 <= sb <= 32 and (cw == 0 or (cw % 16 == 0 and cw <= 256)) and ms > 0.0
+    m1 = ctx.map(H, sp.scans).cpu().numpy()
+    assert rel(m1, m0) < 1e-6
+    # any explicit choice gives the same map too
+    ctx.set_launch(1, 128 if prec != "fp32" else 0)
+    assert rel(ctx.map(H, sp.scans).cpu().numpy(), m0) < 1e-6
+    ctx.close()
