@@ -323,13 +323,119 @@ def run_gpu(args, rank, world):
                                   peak_kind=peak_kind)
 
 
+# ---------------------------------------------------------------------------
+# extra lines: specimens under one CUDA graph; the reverse pass
+
+def graph_specimens():
+    """Sixteen small specimens of uneven size: grids 128^2 / 256^2, 5 to 20
+    slices, f = 2 / 4, one, three or nine channels, seeds 0..15."""
+    import synth
+    out = []
+    for i in range(16):
+        big = i % 4 == 3
+        nz = (5, 10, 20)[i % 3]
+        cfg = synth.config1().replace(
+            name=f"spec{i}", seed=i, nz=nz, ion_slices=(1, nz, max(1, nz // 3)),
+            channels=((0,), (-1, 0, 1), tuple(range(-4, 5)))[i % 3])
+        if big:
+            cfg = cfg.replace(ny=256, nx=256, ly=20.0, lx=20.0, cells_y=8, cells_x=8, fy=4, fx=4,
+                              ion_cells=(3, 5), scan_y=(100.0, 4.0, 12), scan_x=(100.0, 4.0, 12))
+        out.append(cfg)
+    return out
+
+
+def run_graphs(prec="mixed", reps=20):
+    """Eager maps of the 16 specimens one after another against one replay
+    of their CUDA graph: wall time per round, evals/s."""
+    import torch
+    import synth
+    from paper_2607_00756_gb300.context import BipContext
+    from paper_2607_00756_gb300.graphs import GraphedMaps
+    dev = torch.device("cuda:0")
+    items, evals = [], 0
+    for cfg in graph_specimens():
+        sp = synth.make_specimen(cfg)
+        ctx = BipContext(cfg, prec=prec)
+        ctx.build(torch.tensor(sp.V, dtype=torch.float32, device=dev), sp.atoms, sp.nch)
+        H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+        items.append((ctx, H, sp.scans))
+        evals += int((sp.nch > 0).sum()) * len(sp.scans)
+    outs = [torch.empty(len(sc), dtype=torch.float64, device=dev) for _, _, sc in items]
+
+    def eager():
+        for (ctx, H, sc), o in zip(items, outs):
+            ctx.map(H, sc, out=o)
+    for _ in range(3):
+        eager()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        eager()
+    torch.cuda.synchronize()
+    t_eager = (time.perf_counter() - t0) / reps
+    g = GraphedMaps(items)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        g.replay()
+    torch.cuda.synchronize()
+    t_graph = (time.perf_counter() - t0) / reps
+    g.check()
+    for ctx, _, _ in items:
+        ctx.close()
+    return {"specimens": len(items), "precision": prec, "evals_per_round": evals,
+            "eager_ms": t_eager * 1e3, "graph_ms": t_graph * 1e3,
+            "eager_evals_per_s": evals / t_eager, "graph_evals_per_s": evals / t_graph,
+            "timing": "host wall clock around 20 rounds, synchronised"}
+
+
+def run_grad(reps=3):
+    """The reverse pass on the differentiation workload (config 5): forward
+    map plus dL/d(occupancy, H, defocus, Cs, V), CUDA events."""
+    import torch
+    import synth
+    from paper_2607_00756_gb300.context import BipContext
+    cfg = synth.config5().replace(defocus=25.0, cs=5.0e5)
+    sp = synth.make_specimen(cfg)
+    dev = torch.device("cuda:0")
+    ctx = BipContext(cfg, prec="fp32")
+    V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
+    H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+    gI = torch.randn(len(sp.scans), dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(1))
+
+    def step():
+        ctx.build(V, sp.atoms, sp.nch)
+        ctx.map(H, sp.scans)
+        return ctx.grad(H, sp.scans, gI, V=V)
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    n_sites = int((sp.nch > 0).sum())
+    ctx.close()
+    return {"workload": "config5: 256x256 grid, 40 slices, 64 sites x 3 channels, 1024 scans",
+            "ms_per_step": ms, "step": "S1+S2 build, map, reverse pass (occupancy, H, defocus, Cs, V)",
+            "evals_per_s": n_sites * len(sp.scans) / (ms / 1e3), "precision": "fp32"}
+
+
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of
-# the same launch size (profiles/coupling_gram_tc_config2_19site_batch.md);
-# reported only while the kernel's source file is unchanged.
+# the same launch size (profiles/recon_coupling_tc_config2_19site_batch.md,
+# profiles/fp8_recon_coupling_gram_config2_19site_batch.md); reported only
+# while the kernel's source file is unchanged.
 NCU_TRAFFIC = {
-    ("mixed", "coupling"): {"bytes": 1070466000 + 139107584,
+    ("mixed", "coupling"): {"bytes": 1070910000 + 139325184,
                             "source": "paper_2607_00756_gb300/csrc/gemm_tc.cu",
-                            "sha256": "aa3a3688b7d1fc953647f1ceea5e381ea39274aa0b09bd9c020bb45788982ce5"},
+                            "sha256": "7eb277c7c3bc1bd2f2394f3b7de8a968a26acd725e48b8615e1edae23e0ce2df"},
+    ("fp8", "coupling"): {"bytes": 470694912 + 130577152,
+                          "source": "paper_2607_00756_gb300/csrc/gemm_tc.cu",
+                          "sha256": "7eb277c7c3bc1bd2f2394f3b7de8a968a26acd725e48b8615e1edae23e0ce2df"},
 }
 
 
@@ -474,6 +580,8 @@ def main():
     ap.add_argument("--paths", default="mixed,split_bf16,fp8,fp32")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the CUDA-graph batch and the reverse-pass lines")
     ap.add_argument("--max-sites", type=int, default=0,
                     help="keep only the first N ionized sites (profiling case)")
     args = ap.parse_args()
@@ -545,6 +653,9 @@ def main():
         b = results["fp32"]["map"]
         line["accuracy"] = {f"{p}_vs_fp32_rel_l2": float(np.linalg.norm(results[p]["map"] - b) / np.linalg.norm(b))
                             for p in ok if p != "fp32"}
+    if args.extras:
+        line["graphs"] = run_graphs()
+        line["grad"] = run_grad()
     line["e2e"] = res.get("e2e")
     line["gpu_launches"] = res["launches"]
     line["clocks"] = res["clocks"]
