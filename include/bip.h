@@ -219,6 +219,11 @@ bip_status bip_coreloss_qeels(bip_ctx* ctx, const void* H, const double* scan_px
  *   and returns it; map_out holds the last map.  Results do not depend on
  *   these choices (each site's arithmetic and the site-sum order are fixed). */
 bip_status bip_set_capture_safe(bip_ctx* ctx, int32_t on);
+/* bip_set_raster_eval(ctx, on): with on (the default) a scan list that is a
+ * raster (rows of equal y, every row the same x sequence) takes the
+ * separable evaluation of the scan polynomial (two small dense stages per
+ * site); off, or for any other list, Horner's rule per scan. */
+bip_status bip_set_raster_eval(bip_ctx* ctx, int32_t on);
 bip_status bip_check_errors(bip_ctx* ctx, void* stream);
 bip_status bip_set_launch(bip_ctx* ctx, int32_t sites_per_batch, int32_t coupling_tile);
 bip_status bip_autotune(bip_ctx* ctx, const void* H, const double* scan_px, int32_t P, double* map_out,

@@ -70,6 +70,7 @@ def _load():
         "bip_get_profile": [VP, VP, VP],
         "bip_set_occupancy": [VP, P(D)],
         "bip_set_capture_safe": [VP, I32],
+        "bip_set_raster_eval": [VP, I32],
         "bip_check_errors": [VP, VP],
         "bip_set_launch": [VP, I32, I32],
         "bip_autotune": [VP, VP, P(D), I32, VP, VP, P(I32), P(I32), P(D)],
@@ -275,6 +276,10 @@ def bip_site_coupling(ctx, H, site, out, stream=None):
 
 def bip_set_capture_safe(ctx, on):
     _check("bip_set_capture_safe", ctx, _lib.bip_set_capture_safe(ctx, 1 if on else 0))
+
+
+def bip_set_raster_eval(ctx, on):
+    _check("bip_set_raster_eval", ctx, _lib.bip_set_raster_eval(ctx, 1 if on else 0))
 
 
 def bip_check_errors(ctx, stream=None):

@@ -100,6 +100,11 @@ class BipContext:
             out = torch.empty(len(scans), dtype=torch.float64, device=H.device)
         return capi.bip_autotune(self.ctx, H, scans, out, stream)
 
+    def set_raster_eval(self, on):
+        """Separable scan-polynomial evaluation on raster scan lists (default
+        on); off: Horner's rule per scan."""
+        capi.bip_set_raster_eval(self.ctx, on)
+
     def set_launch(self, sites_per_batch=0, coupling_tile=0):
         capi.bip_set_launch(self.ctx, sites_per_batch, coupling_tile)
 

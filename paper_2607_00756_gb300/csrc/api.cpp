@@ -70,6 +70,8 @@ struct bip_ctx {
     uint64_t work_key = 0;
     // tuned launch parameters (0: the built-in choice)
     int sb_override = 0, cw_override = 0;
+    bool raster_eval = true;            // separable evaluation on raster scan lists
+    DevBuf ray, rax;                    // its phase tables
     DevBuf aw1[6], aw2[6];              // per-target / per-parent weights (reconstruction adjoint)
     bool adj_tables = false;
     DevBuf f8pmax, f8inv0, f8inv1, f8hmax, f8H, f8sA, f8sB;   // FP8 per-window scales
@@ -556,7 +558,8 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->cube_scratch, &c->bin_of_d, &c->op8A, &c->op8B, &c->f8pmax, &c->f8inv0, &c->f8inv1,
                      &c->f8hmax, &c->f8H, &c->f8sA, &c->f8sB, &c->occ_d, &c->g_s1, &c->g_w, &c->g_R,
                      &c->g_gmt, &c->g_T, &c->g_D, &c->g_Dsum, &c->g_s1bar, &c->g_s2bar, &c->g_ubar, &c->g_dA,
-                     &c->g_dt1, &c->g_dt2, &c->g_adj, &c->g_ckpt, &c->g_seg, &c->g_gvp, &c->pyc, &c->pxc};
+                     &c->g_dt1, &c->g_dt2, &c->g_adj, &c->g_ckpt, &c->g_seg, &c->g_gvp, &c->pyc, &c->pxc,
+                     &c->ray, &c->rax};
     for (DevBuf* b : all) release(*b);
     for (int i = 0; i < 6; ++i) {
         release(c->aw1[i]);
@@ -1111,6 +1114,36 @@ bip_status check_map_args(bip_ctx* c, const void* H, const double* scans, int32_
     return BIP_OK;
 }
 
+// A scan list that is a raster: scan my Mx + mx at (y_my, x_mx), rows of
+// equal y, the x of every row the same sequence (equal within 1e-9 px).
+struct Raster {
+    bool ok = false;
+    int My = 0, Mx = 0;
+};
+Raster detect_raster(const double* sc, int P) {
+    Raster r;
+    if (P < 1) return r;
+    int Mx = 1;
+    while (Mx < P && sc[2 * Mx] == sc[0]) ++Mx;
+    if (P % Mx) return r;
+    const int My = P / Mx;
+    for (int p = 0; p < P; ++p) {
+        const int i = p / Mx, j = p % Mx;
+        if (std::fabs(sc[2 * p] - sc[2 * (size_t)i * Mx]) > 1e-9 || std::fabs(sc[2 * p + 1] - sc[2 * j + 1]) > 1e-9)
+            return r;
+    }
+    r.ok = true;
+    r.My = My;
+    r.Mx = Mx;
+    return r;
+}
+
+// exp(2 pi i t), t reduced to [0, 1) turns in FP64
+float2 turn_d(double t) {
+    t -= std::floor(t);
+    return float2{(float)std::cos(2.0 * kPi * t), (float)std::sin(2.0 * kPi * t)};
+}
+
 // conservative test: can any scan with y in [y0, y1] and x in [x0, x1] lie
 // inside the crop window of site (ty, tx)?
 bool box_meets_crop(double y0, double y1, double x0, double x1, double ty, double tx, const bip_config& g) {
@@ -1194,6 +1227,30 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         CUDA_TRY(c, cudaMemsetAsync(partial, 0, (size_t)c->n_sites * P * sizeof(float), s));
     }
 
+    // raster scan lists take the separable evaluation: phase tables per scan
+    // row and column, angles reduced in FP64
+    Raster raster;
+    RasterArgs rargs{};
+    if (!cube_out && c->raster_eval) raster = detect_raster(scans, P);
+    if (raster.ok) {
+        const int rows = 2 * c->Ky + 1, cols = 4 * c->Kx + 1;
+        if (!same_scans) {
+            std::vector<float2> ay((size_t)raster.My * rows), ax((size_t)cols * raster.Mx);
+            for (int my = 0; my < raster.My; ++my) {
+                const double ry = scans[2 * (size_t)my * raster.Mx];
+                for (int iy = 0; iy < rows; ++iy)
+                    ay[(size_t)my * rows + iy] = turn_d((double)g.fy * (iy - 2 * c->Ky) * ry / g.ny);
+            }
+            for (int mx = 0; mx < raster.Mx; ++mx) {
+                const double rx = scans[2 * (size_t)mx + 1];
+                for (int j = 0; j < cols; ++j) ax[(size_t)j * raster.Mx + mx] = turn_d((double)g.fx * (j - 2 * c->Kx) * rx / g.nx);
+            }
+            CUDA_TRY(c, upload(c->ray, ay, s));
+            CUDA_TRY(c, upload(c->rax, ax, s));
+        }
+        rargs = RasterArgs{raster.My, raster.Mx, (const float2*)c->ray.p, (const float2*)c->rax.p};
+    }
+
     // scan-tile bounding boxes (host)
     std::vector<double> bb((size_t)n_tiles * 4);
     for (int t = 0; t < n_tiles; ++t) {
@@ -1231,7 +1288,9 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
     }
     CUDA_TRY(c, ensure(c->q32, SB * perQ * sizeof(float2), true, s));
-    CUDA_TRY(c, ensure(c->gdiff, (size_t)SB * nd * sizeof(float2), false, s));
+    // G(Delta) of every site when the raster evaluation runs once at the end,
+    // else of one batch
+    CUDA_TRY(c, ensure(c->gdiff, (size_t)(raster.ok ? c->n_sites : SB) * nd * sizeof(float2), false, s));
 
     if (f8 && c->n_sites > 0) {
         bip_status st = f8_hmax(c, H, s);
@@ -1410,7 +1469,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         d.Ky = c->Ky;
         d.Kx = c->Kx;
         d.lat = (const int32_t*)c->lat_d.p;
-        d.G = (float2*)c->gdiff.p;
+        d.G = (float2*)c->gdiff.p + (raster.ok ? (size_t)b0 * nd : 0);
         d.work = (const int32_t*)c->work_d.p + 2 * batch_off[bi];
         d.n_work = batch_off[bi + 1] - batch_off[bi];
         d.tile = tile;
@@ -1422,7 +1481,23 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         d.scale = (float)(g.fy * g.fx);
         d.partial = partial;
         TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_bin(d, s));
-        if (d.n_work > 0) TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_eval(d, s));
+        if (!raster.ok && d.n_work > 0) TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_eval(d, s));
+    }
+    if (raster.ok && c->n_sites > 0 && !cube_out) {
+        // the scan polynomial of every site at once (sites in order)
+        DiffArgs d{};
+        d.n_sites = c->n_sites;
+        d.Ky = c->Ky;
+        d.Kx = c->Kx;
+        d.G = (float2*)c->gdiff.p;
+        d.P = P;
+        d.scans = (const double*)c->scans_d.p;
+        d.sites = (const SiteDev*)c->sites_d.p;
+        d.site_ids = (const int32_t*)c->seq_ids_d.p;
+        d.ny = g.ny; d.nx = g.nx; d.fy = g.fy; d.fx = g.fx;
+        d.scale = (float)(g.fy * g.fx);
+        d.partial = partial;
+        TIMED(c, BIP_STAGE_QUADFORM, s, bip_raster_eval(d, rargs, s));
     }
     if (tc && !c->capture_safe) {
         int flag = 0;
@@ -1523,6 +1598,13 @@ bip_status bip_check_errors(bip_ctx* c, void* stream) {
         CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
         return fail(c, BIP_ERR_TIMEOUT, "a tensor-core contraction gave up waiting (device timeout)");
     }
+    return BIP_OK;
+}
+
+bip_status bip_set_raster_eval(bip_ctx* c, int32_t on) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    c->raster_eval = on != 0;
+    c->scans_cache.clear();      // the phase tables follow the next call's scans
     return BIP_OK;
 }
 

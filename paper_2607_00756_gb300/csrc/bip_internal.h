@@ -254,6 +254,18 @@ struct DiffArgs {
 };
 cudaError_t bip_diff_bin(const DiffArgs& a, cudaStream_t s);
 cudaError_t bip_diff_eval(const DiffArgs& a, cudaStream_t s);
+// Raster scans rho(my, mx) = (y0 + sy my, x0 + sx mx), scan index my Mx + mx:
+// the same polynomial as two separable stages per site,
+//   I(my, mx) = f Re sum_iy Ay[my][iy] sum_j G[iy][j] Ax[j][mx],
+//   Ay[my][iy] = exp(2 pi i f_y (iy - 2K_y) rho_y(my) / N_y)   [My][rows]
+//   Ax[j][mx]  = exp(2 pi i f_x (j - 2K_x) rho_x(mx) / N_x)    [cols][Mx]
+// written for the scans inside each site's crop mask (others stay 0).
+struct RasterArgs {
+    int My, Mx;
+    const float2* Ay;
+    const float2* Ax;
+};
+cudaError_t bip_raster_eval(const DiffArgs& a, const RasterArgs& r, cudaStream_t s);
 
 // reduce.cu : map[rho] = FP64 Neumaier sum over sites of the partials
 // (already zero outside each site's crop mask), in a fixed order; scratch

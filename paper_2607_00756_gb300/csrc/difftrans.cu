@@ -20,6 +20,9 @@
 //               item; Horner's rule in exp(2 pi i f rho/N) along the
 //               lattice rows and over them, start angles reduced to [0, 1)
 //               turns in FP64.
+//   raster_eval: scans on a raster: the polynomial factorises over the two
+//               axes, two small dense stages per site (tables of the phases
+//               per scan row and column, angles reduced in FP64 on the host).
 #include "bip_device.cuh"
 #include "bip_internal.h"
 #include "fft_smem.cuh"
@@ -137,7 +140,87 @@ __global__ void __launch_bounds__(256) diff_eval_kernel(DiffArgs a) {
     }
 }
 
+// Raster scans: block = (64 scan rows, site), four warps of 16 rows each;
+// stage 1 Y[r][j] = sum_iy Ay[my][iy] G[iy][j] for the block's rows into
+// shared memory, stage 2 lane = four adjacent scan columns, 16 rows x 4
+// columns of Re(Y Ax) per thread (Ax[j][.] loaded once per j and lane).
+constexpr int kRasterWarpRows = 16;
+constexpr int kRasterRows = 4 * kRasterWarpRows;
+__global__ void __launch_bounds__(128) raster_eval_kernel(DiffArgs a, RasterArgs r) {
+    extern __shared__ float2 rs[];
+    const int rows = 2 * a.Ky + 1, cols = 4 * a.Kx + 1;
+    const int nd = rows * cols;
+    float2* gs = rs;                       // [rows][cols]
+    float2* ys = rs + nd;                  // [kRasterRows][cols]
+    const int bs = blockIdx.y;
+    const int my0 = blockIdx.x * kRasterRows;
+    const int nr = min(kRasterRows, r.My - my0);
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) gs[i] = a.G[(size_t)bs * nd + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr * cols; i += blockDim.x) {
+        const int q = i / cols, j = i % cols;
+        const float2* ay = r.Ay + (size_t)(my0 + q) * rows;
+        float sx = 0.f, sy = 0.f;
+        for (int iy = 0; iy < rows; ++iy) {
+            const float2 u = __ldg(&ay[iy]), g = gs[iy * cols + j];
+            sx = fmaf(u.x, g.x, fmaf(-u.y, g.y, sx));
+            sy = fmaf(u.x, g.y, fmaf(u.y, g.x, sy));
+        }
+        ys[q * cols + j] = make_float2(sx, sy);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int q0 = warp * kRasterWarpRows;                 // this warp's first row in the block
+    const int wr = min(kRasterWarpRows, nr - q0);          // its rows (may be <= 0)
+    if (wr <= 0) return;
+    const int site = a.site_ids[bs];
+    const SiteDev st = a.sites[site];
+    for (int mx0 = 4 * lane; mx0 < r.Mx; mx0 += 128) {
+        float acc[kRasterWarpRows][4];
+#pragma unroll
+        for (int q = 0; q < kRasterWarpRows; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[q][k] = 0.f;
+        for (int j = 0; j < cols; ++j) {
+            float2 x[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x[k] = mx0 + k < r.Mx ? __ldg(&r.Ax[(size_t)j * r.Mx + mx0 + k]) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < kRasterWarpRows; ++q) {
+                const float2 y = ys[(q0 + (q < wr ? q : 0)) * cols + j];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[q][k] = fmaf(y.x, x[k].x, fmaf(-y.y, x[k].y, acc[q][k]));   // Re(y x)
+            }
+        }
+        for (int q = 0; q < wr; ++q) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int mx = mx0 + k;
+                if (mx >= r.Mx) continue;
+                const int n = (my0 + q0 + q) * r.Mx + mx;
+                if (in_crop(a.scans[2 * n], a.scans[2 * n + 1], st.ty, st.tx, a.ny, a.nx, a.fy, a.fx))
+                    a.partial[(size_t)site * a.P + n] = a.scale * acc[q][k];
+            }
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t bip_raster_eval(const DiffArgs& a, const RasterArgs& r, cudaStream_t s) {
+    if (a.n_sites < 1 || r.My < 1 || r.Mx < 1 || (int64_t)r.My * r.Mx != a.P) return cudaErrorInvalidValue;
+    const size_t nd = (size_t)(2 * a.Ky + 1) * (4 * a.Kx + 1);
+    const size_t sm = (nd + (size_t)kRasterRows * (4 * a.Kx + 1)) * sizeof(float2);
+    if (sm > 200 * 1024) return cudaErrorInvalidValue;
+    static size_t attr = 0;
+    if (sm > 48 * 1024 && sm > attr) {
+        cudaError_t e = cudaFuncSetAttribute(raster_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr = sm;
+    }
+    raster_eval_kernel<<<dim3((r.My + kRasterRows - 1) / kRasterRows, a.n_sites), 128, sm, s>>>(a, r);
+    return cudaGetLastError();
+}
 
 cudaError_t bip_diff_bin(const DiffArgs& a, cudaStream_t s) {
     const int nd = (2 * a.Ky + 1) * (4 * a.Kx + 1);

@@ -326,3 +326,37 @@ def test_cube_fp8_config1(lib, c1):
     cube = ctx.cube(H, sp.scans).cpu().numpy()
     assert rel(cube, want) < 2.0 * e_model + 1e-3, (rel(cube, want), e_model)
     assert rel(cube.astype(np.float64).sum(axis=1), m) < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# the two evaluations of the scan polynomial
+
+@pytest.mark.parametrize("which", ["config1", "aniso"])
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_raster_and_horner_evaluations_agree(lib, which, prec):
+    """A raster scan list takes the separable evaluation; switched off, the
+    same scans go through Horner's rule per scan.  Both are the same
+    polynomial (FP32 sums in different orders), and both match the oracle."""
+    if which == "config1":
+        cfg = synth.config1()
+    else:
+        cfg = synth.config1().replace(name="aniso", ny=64, nx=128, ly=7.5, lx=10.0, cells_y=3, cells_x=4, fy=1,
+                                      fx=2, win=32, ion_cells=(1, 3), ion_slices=(1, 4),
+                                      scan_y=(10.3, 3.5, 9), scan_x=(20.7, 6.25, 7))
+    sp = synth.make_specimen(cfg)
+    ref = obip.bip_map(obip.make_problem(sp))
+    dev = torch.device("cuda:0")
+    ctx = lib(cfg, prec=prec)
+    ctx.build(torch.tensor(sp.V, dtype=torch.float32, device=dev), sp.atoms, sp.nch)
+    H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+    m_r = ctx.map(H, sp.scans).cpu().numpy()
+    p_r = ctx.sites(H, sp.scans).cpu().numpy()
+    ctx.set_raster_eval(False)
+    m_h = ctx.map(H, sp.scans).cpu().numpy()
+    p_h = ctx.sites(H, sp.scans).cpu().numpy()
+    assert rel(m_r, m_h) < 1e-5
+    assert rel(p_r, p_h) < 1e-5
+    assert np.array_equal(p_r == 0.0, p_h == 0.0)            # the same crop masks
+    tol = 1e-4 if prec == "fp32" else 1e-3
+    assert rel(m_r, ref.map) < tol and rel(m_h, ref.map) < tol
+    ctx.close()
