@@ -391,16 +391,17 @@ def run_graphs(prec="mixed", reps=20):
             "timing": "host wall clock around 20 rounds, synchronised"}
 
 
-def run_grad(reps=3):
+def run_grad(reps=3, prec="mixed"):
     """The reverse pass on the differentiation workload (config 5): forward
-    map plus dL/d(occupancy, H, defocus, Cs, V), CUDA events."""
+    map plus dL/d(occupancy, H, defocus, Cs, V), CUDA events.  A mixed
+    context runs the reverse pass's contractions on tcgen05 in split BF16."""
     import torch
     import synth
     from paper_2607_00756_gb300.context import BipContext
     cfg = synth.config5().replace(defocus=25.0, cs=5.0e5)
     sp = synth.make_specimen(cfg)
     dev = torch.device("cuda:0")
-    ctx = BipContext(cfg, prec="fp32")
+    ctx = BipContext(cfg, prec=prec)
     V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
     H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
     gI = torch.randn(len(sp.scans), dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(1))
@@ -422,7 +423,7 @@ def run_grad(reps=3):
     ctx.close()
     return {"workload": "config5: 256x256 grid, 40 slices, 64 sites x 3 channels, 1024 scans",
             "ms_per_step": ms, "step": "S1+S2 build, map, reverse pass (occupancy, H, defocus, Cs, V)",
-            "evals_per_s": n_sites * len(sp.scans) / (ms / 1e3), "precision": "fp32"}
+            "evals_per_s": n_sites * len(sp.scans) / (ms / 1e3), "precision": prec}
 
 
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of

@@ -61,6 +61,7 @@ struct bip_ctx {
     int occ_n = 0;                      // sites they were given for (0: none)
     DevBuf g_s1, g_w, g_R, g_gmt, g_T, g_D, g_Dsum;   // gradient pass workspaces
     DevBuf g_s1bar, g_s2bar, g_ubar, g_dA, g_dt1, g_dt2, g_adj, g_ckpt, g_seg, g_gvp;
+    DevBuf g_tA, g_tB, g_sA2, g_sB2;    // split-BF16 operands of the reverse-pass contractions
     DevBuf pyc, pxc;                    // conjugated propagator tables (adjoint sweeps)
     // capture-safe maps: no host synchronisation, uploads only when the
     // scans or the batching change (so a CUDA graph can hold the launches)
@@ -559,7 +560,7 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->f8hmax, &c->f8H, &c->f8sA, &c->f8sB, &c->occ_d, &c->g_s1, &c->g_w, &c->g_R,
                      &c->g_gmt, &c->g_T, &c->g_D, &c->g_Dsum, &c->g_s1bar, &c->g_s2bar, &c->g_ubar, &c->g_dA,
                      &c->g_dt1, &c->g_dt2, &c->g_adj, &c->g_ckpt, &c->g_seg, &c->g_gvp, &c->pyc, &c->pxc,
-                     &c->ray, &c->rax};
+                     &c->ray, &c->rax, &c->g_tA, &c->g_tB, &c->g_sA2, &c->g_sB2};
     for (DevBuf* b : all) release(*b);
     for (int i = 0; i < 6; ++i) {
         release(c->aw1[i]);
@@ -1734,7 +1735,8 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
         CUDA_TRY(c, ensure(c->g_dt1, (size_t)c->n_sites * geo.Bp1 * K * sizeof(float2), false, s));
         CUDA_TRY(c, ensure(c->g_dt2, (size_t)c->n_sites * geo.Bp2 * K * sizeof(float2), false, s));
         CUDA_TRY(c, ensure(c->g_s1bar, (size_t)std::min(c->n_sites, 8) * Bpad * K * sizeof(float2), true, s));
-        CUDA_TRY(c, ensure(c->g_s2bar, (size_t)std::min(c->n_sites, 8) * Dpad * K * sizeof(float2), true, s));
+        CUDA_TRY(c, ensure(c->g_s2bar, (size_t)std::min(c->n_sites, 8) * round_up(Dpad, 128) * K * sizeof(float2),
+                           true, s));
         const size_t rows = (size_t)std::max(Bpad, Dpad);
         CUDA_TRY(c, ensure(c->g_ubar, (size_t)std::min(c->n_sites, 8) * rows * K * sizeof(float2), false, s));
         CUDA_TRY(c, ensure(c->g_dA, (size_t)std::min(c->n_sites, 8) * rows * K * sizeof(float), false, s));
@@ -1750,7 +1752,24 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
     const int SB = std::min(c->n_sites, 8);
     const size_t perA = (size_t)Dpad * K, perB = (size_t)nch * Bpad * K, perS1 = (size_t)Bpad * K;
     const size_t ldm = (size_t)nch * Dpad, perMt = (size_t)Bpad * ldm, perQ = (size_t)Bpad * Bpad;
-    const size_t perT = (size_t)nch * B * K;
+    const size_t perT = (size_t)nch * Bpad * K;
+    // contractions of the reverse pass on the tensor cores (split BF16, three
+    // products) for the tensor-core precisions, FP32 SIMT for FP32
+    const bool tcg = c->prec != BIP_PREC_FP32;
+    const int D128 = round_up(Dpad, 128);
+    const size_t KB = (size_t)nch * Bpad;
+    const size_t perS2bar = (size_t)(tcg ? D128 : Dpad) * K;
+    if (tcg) {
+        CUDA_TRY(c, ensure(c->opA16, SB * perA * 8, true, s));
+        CUDA_TRY(c, ensure(c->opB16, SB * perB * 8, true, s));
+        CUDA_TRY(c, ensure(c->g_tA, SB * 4 * (size_t)Bpad * Dpad * sizeof(uint16_t), true, s));
+        CUDA_TRY(c, ensure(c->g_tB, SB * 4 * (size_t)K * Dpad * sizeof(uint16_t), true, s));
+        if (d_V) {
+            CUDA_TRY(c, ensure(c->g_sA2, SB * 4 * (size_t)D128 * KB * sizeof(uint16_t), true, s));
+            CUDA_TRY(c, ensure(c->g_sB2, SB * 4 * (size_t)K * KB * sizeof(uint16_t), true, s));
+        }
+        CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
+    }
     CUDA_TRY(c, ensure(c->opA32, SB * perA * sizeof(float2), true, s));
     CUDA_TRY(c, ensure(c->opB32, SB * perB * sizeof(float2), true, s));
     CUDA_TRY(c, ensure(c->g_s1, SB * perS1 * sizeof(float2), true, s));
@@ -1792,15 +1811,44 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
         g0.out_c64 = (float2*)c->g_s1.p;
         g0.site_stride = (int64_t)perS1;
         CUDA_TRY(c, bip_gather(g0, s));
-        CGemmArgs A{};
-        A.M = geo.n_det; A.N = nch * Bpad; A.K = K;
-        A.A = (const float2*)c->opA32.p; A.lda = K; A.strideA = (int64_t)perA;
-        A.Bm = (const float2*)c->opB32.p; A.ldb = K; A.strideB = (int64_t)perB;
-        A.batch = nb;
-        A.epi = 1;
-        A.C = (float2*)c->mt32.p; A.ldc = (int64_t)ldm; A.strideC = (int64_t)perMt;
-        A.ep_B = Bpad; A.ep_Dp = Dpad;
-        CUDA_TRY(c, bip_cgemm_simt(A, s));
+        if (tcg) {
+            // operands as split planes, then M on tcgen05 written as Mt[b][(n, d)]
+            SplitArgs sa{(const float2*)c->opA32.p, K, 1, (int64_t)perA, Dpad, K, nb, (uint16_t*)c->opA16.p,
+                         (int64_t)(4 * perA), Dpad, K, 0, 0};
+            CUDA_TRY(c, bip_split_planes(sa, s));
+            SplitArgs sb{(const float2*)c->opB32.p, K, 1, (int64_t)perB, (int)KB, K, nb, (uint16_t*)c->opB16.p,
+                         (int64_t)(4 * perB), (int)KB, K, 0, 0};
+            CUDA_TRY(c, bip_split_planes(sb, s));
+            TcArgs A{};
+            A.epi = TC_EPI_C32;
+            A.N = tile_width(Dpad);
+            A.npl = 4;
+            A.A = TcOperand{c->opB16.p, (int64_t)nb * 4 * (int64_t)KB, K, 4 * (int64_t)KB, (int64_t)KB};
+            A.B = TcOperand{c->opA16.p, (int64_t)nb * 4 * (int64_t)Dpad, K, 4 * (int64_t)Dpad, (int64_t)Dpad};
+            A.kb = K / 32;
+            A.n_sites = nb;
+            A.mt_per = (int)(KB / 128);
+            A.nt_per = (Dpad + A.N - 1) / A.N;
+            A.n_cols = Dpad;
+            A.out32 = (float2*)c->mt32.p;
+            A.out32_site = (int64_t)perMt;
+            A.out32_ld = (int64_t)ldm;
+            A.out32_rows = 1;
+            A.ep_B = Bpad;
+            A.ep_Dp = Dpad;
+            A.err = (int*)c->errflag.p;
+            CUDA_TRY(c, bip_tc_gemm(A, s));
+        } else {
+            CGemmArgs A{};
+            A.M = geo.n_det; A.N = nch * Bpad; A.K = K;
+            A.A = (const float2*)c->opA32.p; A.lda = K; A.strideA = (int64_t)perA;
+            A.Bm = (const float2*)c->opB32.p; A.ldb = K; A.strideB = (int64_t)perB;
+            A.batch = nb;
+            A.epi = 1;
+            A.C = (float2*)c->mt32.p; A.ldc = (int64_t)ldm; A.strideC = (int64_t)perMt;
+            A.ep_B = Bpad; A.ep_Dp = Dpad;
+            CUDA_TRY(c, bip_cgemm_simt(A, s));
+        }
         // R_tau = f o_tau sum_{rho in crop} g c c^H
         CUDA_TRY(c, bip_grad_crop_weights(ga, nb, ids, (float*)c->g_w.p, s));
         CGemmGen r{};
@@ -1833,35 +1881,92 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
             m.C = (float2*)c->g_gmt.p; m.scm = (int64_t)ldm; m.scn = 1; m.scb = (int64_t)perMt;
             CUDA_TRY(c, bip_cgemm_gen(m, s));
             // T_n(b, r) = sum_d Mbar_n(d, b) conj S2_d(r)
+            if (tcg) {
+                // B operand: conj(S2) transposed to rows r, K = d (once per batch)
+                SplitArgs st{(const float2*)c->opA32.p, 1, K, (int64_t)perA, K, Dpad, nb, (uint16_t*)c->g_tB.p,
+                             (int64_t)4 * K * Dpad, K, Dpad, 0, 1};
+                CUDA_TRY(c, bip_split_planes(st, s));
+            }
             for (int n = 0; n < nch; ++n) {
-                CGemmGen t{};
-                t.M = B; t.N = K; t.K = geo.n_det; t.batch = nb;
-                t.A = (const float2*)c->g_gmt.p + (size_t)n * Dpad; t.sam = (int64_t)ldm; t.sak = 1;
-                t.sab = (int64_t)perMt;
-                t.B = (const float2*)c->opA32.p; t.sbk = K; t.sbn = 1; t.sbb = (int64_t)perA; t.conjB = 1;
-                t.C = (float2*)c->g_T.p + (size_t)n * B * K; t.scm = K; t.scn = 1; t.scb = (int64_t)perT;
-                CUDA_TRY(c, bip_cgemm_gen(t, s));
+                if (tcg) {
+                    SplitArgs sg{(const float2*)c->g_gmt.p + (size_t)n * Dpad, (int64_t)ldm, 1, (int64_t)perMt, Bpad,
+                                 Dpad, nb, (uint16_t*)c->g_tA.p, (int64_t)4 * Bpad * Dpad, Bpad, Dpad, 0, 0};
+                    CUDA_TRY(c, bip_split_planes(sg, s));
+                    TcArgs t{};
+                    t.epi = TC_EPI_C32;
+                    t.N = 256;
+                    t.npl = 4;
+                    t.A = TcOperand{c->g_tA.p, (int64_t)nb * 4 * Bpad, Dpad, 4 * (int64_t)Bpad, Bpad};
+                    t.B = TcOperand{c->g_tB.p, (int64_t)nb * 4 * K, Dpad, 4 * (int64_t)K, K};
+                    t.kb = Dpad / 32;
+                    t.n_sites = nb;
+                    t.mt_per = Bpad / 128;
+                    t.nt_per = (K + 255) / 256;
+                    t.n_cols = K;
+                    t.out32 = (float2*)c->g_T.p + (size_t)n * Bpad * K;
+                    t.out32_site = (int64_t)perT;
+                    t.out32_ld = K;
+                    t.err = (int*)c->errflag.p;
+                    CUDA_TRY(c, bip_tc_gemm(t, s));
+                } else {
+                    CGemmGen t{};
+                    t.M = B; t.N = K; t.K = geo.n_det; t.batch = nb;
+                    t.A = (const float2*)c->g_gmt.p + (size_t)n * Dpad; t.sam = (int64_t)ldm; t.sak = 1;
+                    t.sab = (int64_t)perMt;
+                    t.B = (const float2*)c->opA32.p; t.sbk = K; t.sbn = 1; t.sbb = (int64_t)perA; t.conjB = 1;
+                    t.C = (float2*)c->g_T.p + (size_t)n * Bpad * K; t.scm = K; t.scn = 1; t.scb = (int64_t)perT;
+                    CUDA_TRY(c, bip_cgemm_gen(t, s));
+                }
             }
             if (d_H)
                 CUDA_TRY(c, bip_grad_h(ga, nb, ids, nch, (const float2*)c->g_s1.p, (int64_t)perS1,
-                                       (const float2*)c->g_T.p, (int64_t)perT, (int64_t)B * K, (float2*)d_H, s));
+                                       (const float2*)c->g_T.p, (int64_t)perT, (int64_t)Bpad * K, (float2*)d_H, s));
         }
         if (d_V) {
             // S1bar_b(r) = sum_n conj H_n(r) T_n(b, r);
             // S2bar_d(r) = sum_n sum_b Mbar_n(d, b) conj(H_n(r) S1_b(r))
             CUDA_TRY(c, bip_s1bar(nb, ids, (const SiteDev*)c->sites_d.p, B, K, (const float2*)H,
-                                  (const float2*)c->g_T.p, (int64_t)perT, (int64_t)B * K, (float2*)c->g_s1bar.p,
+                                  (const float2*)c->g_T.p, (int64_t)perT, (int64_t)Bpad * K, (float2*)c->g_s1bar.p,
                                   (int64_t)perS1, s));
-            for (int n = 0; n < nch; ++n) {
-                CGemmGen u{};
-                u.M = geo.n_det; u.N = K; u.K = B; u.batch = nb;
-                u.A = (const float2*)c->g_gmt.p + (size_t)n * Dpad; u.sam = 1; u.sak = (int64_t)ldm;
-                u.sab = (int64_t)perMt;
-                u.B = (const float2*)c->opB32.p + (size_t)n * Bpad * K; u.sbk = K; u.sbn = 1; u.sbb = (int64_t)perB;
-                u.conjB = 1;
-                u.C = (float2*)c->g_s2bar.p; u.scm = K; u.scn = 1; u.scb = (int64_t)perA;
-                u.accumulate = n > 0;
-                CUDA_TRY(c, bip_cgemm_gen(u, s));
+            if (tcg) {
+                // one contraction over K = (n, b): A = Mbar^T rows d, B = conj(H S1)^T rows r
+                for (int n = 0; n < nch; ++n) {
+                    SplitArgs sg{(const float2*)c->g_gmt.p + (size_t)n * Dpad, 1, (int64_t)ldm, (int64_t)perMt, Dpad,
+                                 Bpad, nb, (uint16_t*)c->g_sA2.p, (int64_t)4 * D128 * KB, D128, (int)KB, n * Bpad, 0};
+                    CUDA_TRY(c, bip_split_planes(sg, s));
+                }
+                SplitArgs sx{(const float2*)c->opB32.p, 1, K, (int64_t)perB, K, (int)KB, nb, (uint16_t*)c->g_sB2.p,
+                             (int64_t)4 * K * KB, K, (int)KB, 0, 1};
+                CUDA_TRY(c, bip_split_planes(sx, s));
+                TcArgs u{};
+                u.epi = TC_EPI_C32;
+                u.N = 256;
+                u.npl = 4;
+                u.A = TcOperand{c->g_sA2.p, (int64_t)nb * 4 * D128, (int)KB, 4 * (int64_t)D128, D128};
+                u.B = TcOperand{c->g_sB2.p, (int64_t)nb * 4 * K, (int)KB, 4 * (int64_t)K, K};
+                u.kb = (int)(KB / 32);
+                u.n_sites = nb;
+                u.mt_per = D128 / 128;
+                u.nt_per = (K + 255) / 256;
+                u.n_cols = K;
+                u.out32 = (float2*)c->g_s2bar.p;
+                u.out32_site = (int64_t)perS2bar;
+                u.out32_ld = K;
+                u.err = (int*)c->errflag.p;
+                CUDA_TRY(c, bip_tc_gemm(u, s));
+            } else {
+                for (int n = 0; n < nch; ++n) {
+                    CGemmGen u{};
+                    u.M = geo.n_det; u.N = K; u.K = B; u.batch = nb;
+                    u.A = (const float2*)c->g_gmt.p + (size_t)n * Dpad; u.sam = 1; u.sak = (int64_t)ldm;
+                    u.sab = (int64_t)perMt;
+                    u.B = (const float2*)c->opB32.p + (size_t)n * Bpad * K; u.sbk = K; u.sbn = 1;
+                    u.sbb = (int64_t)perB;
+                    u.conjB = 1;
+                    u.C = (float2*)c->g_s2bar.p; u.scm = K; u.scn = 1; u.scb = (int64_t)perS2bar;
+                    u.accumulate = n > 0;
+                    CUDA_TRY(c, bip_cgemm_gen(u, s));
+                }
             }
             // back through the reconstructions into the window adjoints
             for (int side = 1; side <= 2; ++side) {
@@ -1883,7 +1988,7 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
                     ra.h_t = (const int2*)c->hdet.p;
                     ra.stash = (const float2*)c->stash2.p;
                     ra.w = adj_weights(c->aw2);
-                    ra.Sbar = (const float2*)c->g_s2bar.p; ra.sbar_rows = Dpad;
+                    ra.Sbar = (const float2*)c->g_s2bar.p; ra.sbar_rows = (int)(perS2bar / K);
                     ra.dtbar = (float2*)c->g_dt2.p;
                 }
                 ra.Ubar = (float2*)c->g_ubar.p;
@@ -1891,6 +1996,12 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
                 CUDA_TRY(c, bip_recon_adjoint(ra, s));
             }
         }
+    }
+    if (tcg) {
+        int flag = 0;
+        CUDA_TRY(c, cudaMemcpyAsync(&flag, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        if (flag) return fail(c, BIP_ERR_TIMEOUT, "a tensor-core contraction gave up waiting (device timeout)");
     }
     if (d_V) {
         CUDA_TRY(c, cudaMemsetAsync(d_V, 0, (size_t)g.nz * g.ny * g.nx * sizeof(float), s));

@@ -316,6 +316,7 @@ struct TcArgs {
     float2* out32;
     int64_t out32_site, out32_ld;
     int out32_trans;
+    int out32_rows;                 // A row (ch, b) -> out32[site][b][ch ep_Dp + n] (as ROWS)
     int* err;                       // device flag: set when a wait gives up
 };
 cudaError_t bip_tc_gemm(const TcArgs& a, cudaStream_t s);
@@ -435,6 +436,22 @@ cudaError_t bip_grad_aberr(int B, int Bpad, int nb, const float2* Q, int64_t q_s
                            double2* D, double2* Dsum, cudaStream_t s);
 // out[k] = sum_rho g(rho) partial[k][rho]
 cudaError_t bip_grad_occ(const float* partial, int n_sites, int P, const double* g, double* out, cudaStream_t s);
+// complex64 matrix -> the four split-BF16 planes (re_hi, re_lo, im_hi, im_lo)
+// of a tensor-core operand: dst[z][plane][i][dcol0 + k] (row length d_cols,
+// plane stride d_rows d_cols, batch stride d_batch) = split(op(src[z s_batch
+// + i s_row + k s_col])), op = conj when conj; i < rows, k < cols (the rest
+// of the destination is left as it is).  Tiled through shared memory, so
+// either source stride may be the contiguous one.
+struct SplitArgs {
+    const float2* src;
+    int64_t s_row, s_col, s_batch;
+    int rows, cols, batch;
+    uint16_t* dst;
+    int64_t d_batch;
+    int d_rows, d_cols, dcol0;
+    int conj;
+};
+cudaError_t bip_split_planes(const SplitArgs& a, cudaStream_t s);
 
 // noalloc.cu : the static device scratch used by bip_build_s1_noalloc
 constexpr size_t kNoallocScratchBytes = size_t(32) << 20;   // 32 MiB per GPU

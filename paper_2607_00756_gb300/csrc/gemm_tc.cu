@@ -328,7 +328,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 } else if (EPI == TC_EPI_C32) {
                     float2* o = p.out32 + (int64_t)u.bs * p.out32_site;
-                    if (p.out32_trans) {
+                    if (p.out32_rows) {
+                        // A row (ch, b) -> out32[b][ch Dp + n], 16 consecutive columns
+                        const int ch = row / p.ep_B, b = row % p.ep_B;
+                        o += (int64_t)b * p.out32_ld + (int64_t)ch * p.ep_Dp + n0;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) o[j] = make_float2(vr[j], vi[j]);
+                    } else if (p.out32_trans) {
 #pragma unroll
                         for (int j = 0; j < 16; ++j) o[(int64_t)(n0 + j) * p.out32_ld + row] = make_float2(vr[j], vi[j]);
                     } else {

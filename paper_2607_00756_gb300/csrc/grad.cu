@@ -181,7 +181,56 @@ __global__ void occ_grad_kernel(const float* partial, int P, const double* g, do
     }
 }
 
+// split into BF16 hi + lo, tile = 32 x 32 of the destination (i, k)
+__device__ __forceinline__ uint16_t bf16_rn_u(float x) {
+    uint32_t u = __float_as_uint(x);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+__global__ void split_planes_kernel(SplitArgs a) {
+    __shared__ float2 tile[32][33];
+    const int k0 = blockIdx.x * 32, i0 = blockIdx.y * 32, z = blockIdx.z;
+    const int tx = threadIdx.x, ty = threadIdx.y;           // 32 x 8
+    const float2* src = a.src + (int64_t)z * a.s_batch;
+    // read with the source's contiguous axis across the lanes
+    for (int r = ty; r < 32; r += 8) {
+        int i, k;
+        if (a.s_col == 1) { i = i0 + r; k = k0 + tx; } else { i = i0 + tx; k = k0 + r; }
+        float2 v = make_float2(0.f, 0.f);
+        if (i < a.rows && k < a.cols) v = __ldg(&src[(int64_t)i * a.s_row + (int64_t)k * a.s_col]);
+        if (a.conj) v.y = -v.y;
+        if (a.s_col == 1) tile[r][tx] = v; else tile[tx][r] = v;
+    }
+    __syncthreads();
+    const int64_t plane = (int64_t)a.d_rows * a.d_cols;
+    uint16_t* dst = a.dst + (int64_t)z * a.d_batch;
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + r, k = k0 + tx;
+        if (i >= a.rows || k >= a.cols) continue;
+        const float2 v = tile[r][tx];
+        const uint16_t rh = bf16_rn_u(v.x), ih = bf16_rn_u(v.y);
+        const uint16_t rl = bf16_rn_u(v.x - __uint_as_float((uint32_t)rh << 16));
+        const uint16_t il = bf16_rn_u(v.y - __uint_as_float((uint32_t)ih << 16));
+        const int64_t o = (int64_t)i * a.d_cols + a.dcol0 + k;
+        dst[o] = rh;
+        dst[o + plane] = rl;
+        dst[o + 2 * plane] = ih;
+        dst[o + 3 * plane] = il;
+    }
+}
+
 }  // namespace
+
+cudaError_t bip_split_planes(const SplitArgs& a, cudaStream_t s) {
+    if (a.rows < 1 || a.cols < 1 || a.batch < 1 || a.rows > a.d_rows || a.dcol0 + a.cols > a.d_cols)
+        return cudaErrorInvalidValue;
+    if (a.s_col != 1 && a.s_row != 1) return cudaErrorInvalidValue;
+    const dim3 grid((a.cols + 31) / 32, (a.rows + 31) / 32, a.batch);
+    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
+    split_planes_kernel<<<grid, dim3(32, 8), 0, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t bip_cgemm_gen(const CGemmGen& a, cudaStream_t s) {
     if (a.M < 1 || a.N < 1 || a.K < 1 || a.batch < 1) return cudaErrorInvalidValue;
