@@ -426,6 +426,35 @@ def run_grad(reps=3, prec="mixed"):
             "evals_per_s": n_sites * len(sp.scans) / (ms / 1e3), "precision": prec}
 
 
+def run_cube(cfg, sp, prec="mixed", reps=2):
+    """The 4D cube (the detector sum left open) on the benchmark workload:
+    S1 + S2 builds and the cube, CUDA events; P x n_det floats out."""
+    import torch
+    from paper_2607_00756_gb300.context import BipContext
+    dev = torch.device("cuda:0")
+    ctx = BipContext(cfg, prec=prec)
+    V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
+    H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+    out = torch.empty((len(sp.scans), ctx.n_det), dtype=torch.float32, device=dev)
+
+    def step():
+        ctx.build(V, sp.atoms, sp.nch)
+        ctx.cube(H, sp.scans, out=out)
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    n_sites = int((sp.nch > 0).sum())
+    ctx.close()
+    return {"ms_per_step": ms, "evals_per_s": n_sites * len(sp.scans) / (ms / 1e3), "precision": prec,
+            "step": "S1+S2 build and the cube [P, n_det] (per-beam contraction on tcgen05, split BF16)"}
+
+
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of
 # the same launch size (profiles/recon_coupling_tc_config2_19site_batch.md,
 # profiles/fp8_recon_coupling_gram_config2_19site_batch.md); reported only
@@ -657,6 +686,7 @@ def main():
     if args.extras:
         line["graphs"] = run_graphs()
         line["grad"] = run_grad()
+        line["cube"] = run_cube(cfg, sp)
     line["e2e"] = res.get("e2e")
     line["gpu_launches"] = res["launches"]
     line["clocks"] = res["clocks"]

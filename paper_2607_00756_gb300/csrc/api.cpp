@@ -62,6 +62,7 @@ struct bip_ctx {
     DevBuf g_s1, g_w, g_R, g_gmt, g_T, g_D, g_Dsum;   // gradient pass workspaces
     DevBuf g_s1bar, g_s2bar, g_ubar, g_dA, g_dt1, g_dt2, g_adj, g_ckpt, g_seg, g_gvp;
     DevBuf g_tA, g_tB, g_sA2, g_sB2;    // split-BF16 operands of the reverse-pass contractions
+    DevBuf cubeA, cubeB, cube_work, cube_mask;   // the cube on tcgen05
     DevBuf pyc, pxc;                    // conjugated propagator tables (adjoint sweeps)
     // capture-safe maps: no host synchronisation, uploads only when the
     // scans or the batching change (so a CUDA graph can hold the launches)
@@ -560,7 +561,8 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->f8hmax, &c->f8H, &c->f8sA, &c->f8sB, &c->occ_d, &c->g_s1, &c->g_w, &c->g_R,
                      &c->g_gmt, &c->g_T, &c->g_D, &c->g_Dsum, &c->g_s1bar, &c->g_s2bar, &c->g_ubar, &c->g_dA,
                      &c->g_dt1, &c->g_dt2, &c->g_adj, &c->g_ckpt, &c->g_seg, &c->g_gvp, &c->pyc, &c->pxc,
-                     &c->ray, &c->rax, &c->g_tA, &c->g_tB, &c->g_sA2, &c->g_sB2};
+                     &c->ray, &c->rax, &c->g_tA, &c->g_tB, &c->g_sA2, &c->g_sB2, &c->cubeA, &c->cubeB,
+                     &c->cube_work, &c->cube_mask};
     for (DevBuf* b : all) release(*b);
     for (int i = 0; i < 6; ++i) {
         release(c->aw1[i]);
@@ -1324,6 +1326,45 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     c->work_key = work_key;
     }
 
+    // the cube on tcgen05: c_b(rho) as split planes [4][P64][Bpad] once, and
+    // work lists of (site in batch, 64-scan tile meeting its crop mask)
+    const bool cube_tc = cube_out && tc;
+    const int P64 = round_up(P, 64), D128 = round_up(Dpad, 128);
+    const size_t KB = (size_t)nch * Bpad;
+    std::vector<int> cube_off;
+    if (cube_tc) {
+        CUDA_TRY(c, ensure(c->cubeB, (size_t)4 * P64 * Bpad * sizeof(uint16_t), true, s));
+        CUDA_TRY(c, ensure(c->cubeA, (size_t)SB * 4 * D128 * KB * sizeof(uint16_t), true, s));
+        SplitArgs sc{(const float2*)c->illum.p, 1, P, 0, P, Bpad, 1, (uint16_t*)c->cubeB.p, 0, P64, Bpad, 0, 0};
+        CUDA_TRY(c, bip_split_planes(sc, s));
+        std::vector<double> bb64;
+        for (int t = 0; t < P64 / 64; ++t) {
+            double y0 = INFINITY, y1 = -INFINITY, x0 = INFINITY, x1 = -INFINITY;
+            for (int p = t * 64; p < std::min(P, (t + 1) * 64); ++p) {
+                y0 = std::min(y0, scans[2 * p]);
+                y1 = std::max(y1, scans[2 * p]);
+                x0 = std::min(x0, scans[2 * p + 1]);
+                x1 = std::max(x1, scans[2 * p + 1]);
+            }
+            bb64.insert(bb64.end(), {y0, y1, x0, x1});
+        }
+        std::vector<int32_t> cw;
+        for (int b0 = 0; b0 < c->n_sites; b0 += SB) {
+            cube_off.push_back((int)cw.size() / 2);
+            for (int bs = 0; bs < std::min(SB, c->n_sites - b0); ++bs) {
+                const SiteDev& sd = c->sites[b0 + bs];
+                for (int t = 0; t < P64 / 64; ++t)
+                    if (box_meets_crop(bb64[4 * t], bb64[4 * t + 1], bb64[4 * t + 2], bb64[4 * t + 3], sd.ty, sd.tx, g)) {
+                        cw.push_back(bs);
+                        cw.push_back(t);
+                    }
+            }
+        }
+        cube_off.push_back((int)cw.size() / 2);
+        CUDA_TRY(c, upload(c->cube_work, cw, s));
+        CUDA_TRY(c, ensure(c->cube_mask, std::max<size_t>(1, cw.size() / 2) * sizeof(unsigned long long), false, s));
+    }
+
     int bi = 0;
     for (int b0 = 0; b0 < c->n_sites; b0 += SB, ++bi) {
         const int nb = std::min(SB, c->n_sites - b0);
@@ -1401,12 +1442,37 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             }
             TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(A, s));
             if (cube_out) {
-                CubeArgs ca = cube_args(c, ids, nb, P, cube_out);
-                ca.m32 = (const float2*)c->mt32.p;
-                ca.m_site = (int64_t)perMt;
-                ca.m_ld = Dpad;                              // element ((ch Bpad + b) Dpad + d)
-                ca.Dp = Bpad * Dpad;
-                TIMED(c, BIP_STAGE_QUADFORM, s, bip_cube_accumulate(ca, s));
+                // A = M transposed to rows d, K = (ch, b), as split planes; then
+                // the per-beam contraction and |.|^2 channel sum on tcgen05
+                SplitArgs sa{(const float2*)c->mt32.p, 1, Dpad, (int64_t)perMt, Dpad, (int)KB, nb,
+                             (uint16_t*)c->cubeA.p, (int64_t)4 * D128 * KB, D128, (int)KB, 0, 0};
+                TIMED(c, BIP_STAGE_QUADFORM, s, bip_split_planes(sa, s));
+                CubeTcArgs ct{};
+                ct.n_work = cube_off[bi + 1] - cube_off[bi];
+                ct.work = (const int32_t*)c->cube_work.p + 2 * (size_t)cube_off[bi];
+                ct.mask = (unsigned long long*)c->cube_mask.p + cube_off[bi];
+                ct.n_sites = nb;
+                ct.n_tiles = P64 / 64;
+                ct.mt_per = D128 / 128;
+                ct.kb_ch = Bpad / 32;
+                ct.a_site_rows = 4 * (int64_t)D128;
+                ct.a_plane_rows = D128;
+                ct.b_plane_rows = P64;
+                ct.n_det = geo.n_det;
+                ct.P = P;
+                ct.scans = (const double*)c->scans_d.p;
+                ct.sites = (const SiteDev*)c->sites_d.p;
+                ct.site_ids = ids;
+                ct.ny = g.ny; ct.nx = g.nx; ct.fy = g.fy; ct.fx = g.fx;
+                ct.scale = (float)(g.fy * g.fx);
+                ct.cube = cube_out;
+                ct.err = (int*)c->errflag.p;
+                for (int ch0 = 0; ch0 < nch; ch0 += 4) {
+                    ct.ch0 = ch0;
+                    ct.nacc = std::min(4, nch - ch0);
+                    TIMED(c, BIP_STAGE_QUADFORM, s,
+                          bip_cube_tc(ct, c->cubeA.p, (int64_t)nb * 4 * D128, (int)KB, c->cubeB.p, (int64_t)4 * P64, s));
+                }
                 continue;
             }
             // Gram Q = sum_n M^(n)H M^(n), upper triangle, FP32

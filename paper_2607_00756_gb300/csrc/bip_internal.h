@@ -347,6 +347,29 @@ struct CubeArgs {
     float* cube;                    // [P][n_det], accumulated
 };
 cudaError_t bip_cube_accumulate(const CubeArgs& a, cudaStream_t s);
+// cube_tc.cu : the cube on tcgen05 (split BF16).  A = M transposed to rows d,
+// K = (channel, b): [site][4 planes][rows (128 multiple)][nch Bpad] bf16;
+// B = c_b(rho): [4 planes][scans (64 multiple)][Bpad] bf16.  Work items (site
+// in batch, 64-scan tile meeting its crop mask) x 128-row tiles of d;
+// channels ch0 .. ch0 + nacc - 1 (nacc <= 4) per launch.
+struct CubeTcArgs {
+    int n_work;
+    const int32_t* work;            // [n_work][2] (site in batch, scan tile)
+    unsigned long long* mask;       // [n_work] crop masks (written by the launch)
+    int n_sites, n_tiles;           // sites in the batch, scan tiles of B
+    int mt_per, kb_ch, ch0, nacc;   // d tiles, K blocks per channel, channel range
+    int64_t a_site_rows, a_plane_rows, b_plane_rows;
+    int n_det, P;
+    const double* scans;
+    const SiteDev* sites;
+    const int32_t* site_ids;
+    int ny, nx, fy, fx;
+    float scale;                    // f_y f_x
+    float* cube;                    // [P][n_det], added to (atomically)
+    int* err;
+};
+cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int a_k, const void* B, int64_t b_rows,
+                        cudaStream_t s);
 // qEELS: out[rho][bin_of[d]] = sum of cube[rho][d] over the beams of a bin
 cudaError_t bip_qeels_bin(const float* cube, int P, int n_det, const int32_t* bin_of, int n_bins, float* out,
                           cudaStream_t s);

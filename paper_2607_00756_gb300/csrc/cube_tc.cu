@@ -1,0 +1,295 @@
+// The 4D cube (Sec. 2.2.6) on the tensor cores: per site, channel and
+// detector beam d, a_d(rho) = sum_b M^(n)_{d,b} c_b(rho), and
+//   cube[rho][d] += f_y f_x sum_n |a_d(rho)|^2
+// for the scans of the site's crop mask.  Split BF16 (hi + lo, three
+// products per real product, twelve per complex one), FP32 accumulation in
+// TMEM.
+//
+// Work unit: (site in batch, tile of 64 scans that meets the site's crop
+// mask, tile of 128 detector beams).  K runs over (channel, aperture beam);
+// each channel accumulates into its own TMEM pair (re, im; 64 columns
+// each), so the epilogue has every channel of an element at once and adds
+// the channel sum of |a|^2 to the cube with one atomic add per element
+// (sites of a batch run concurrently; the order of the additions, and so the
+// last bits of the cube, is not fixed).  The crop mask of a unit's 64 scans
+// is a precomputed 64-bit word.  Persistent, one CTA per SM, 192 threads:
+// warp 0 TMA producer, warp 1 TMEM allocator and MMA issuer, warps 2-5
+// epilogue.  Every wait is bounded; on a timeout the kernel sets *err,
+// drains what it issued and frees TMEM.
+#include "bip_device.cuh"
+#include "tc_common.cuh"
+
+namespace {
+
+constexpr int kThreads = 192;
+constexpr int kN = 64;                            // scans per tile
+constexpr int kATile = 128 * 64;                  // bytes: 128 rows x 32 bf16
+constexpr int kBTile = kN * 64;
+constexpr int kStage = 4 * kATile + 4 * kBTile;   // hi/lo re/im planes
+constexpr int kStages = 4;
+constexpr size_t kSmem = 1024 + (size_t)kStages * kStage + 256;
+
+__device__ __forceinline__ bool unit_of(const CubeTcArgs& a, int idx, int& w, int& mt) {
+    if (idx >= a.n_work * a.mt_per) return false;
+    w = idx / a.mt_per;
+    mt = idx % a.mt_per;
+    return true;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    cube_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   const CubeTcArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + kStages * kStage);
+    uint64_t* empty = full + kStages;
+    uint64_t* acc_full = empty + kStages;
+    uint64_t* acc_empty = acc_full + 1;
+    uint64_t* drain = acc_empty + 1;
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    volatile int* ep_ok = abort_flag + 1;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, 4);
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+    const int kb0 = a.ch0 * a.kb_ch, kb1 = (a.ch0 + a.nacc) * a.kb_ch;
+
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicExch(a.err, 1);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            int s = 0;
+            uint32_t ph = 0;
+            int issued = 0;
+            bool ok = true;
+            int w, mt;
+            for (int i = 0; ok && unit_of(a, blockIdx.x + i * gridDim.x, w, mt); ++i) {
+                const int bs = a.work[2 * w], t = a.work[2 * w + 1];
+                const int64_t a0 = (int64_t)bs * a.a_site_rows + (int64_t)mt * 128;
+                const int64_t b0 = (int64_t)t * kN;
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* st = smem + s * kStage;
+                    mbar_expect_tx(&full[s], kStage);
+                    const int kx = (kb % a.kb_ch) * 32;           // the aperture beam block
+#pragma unroll
+                    for (int pl = 0; pl < 4; ++pl)
+                        tma_2d(st + pl * kATile, &mapA, kb * 32, (int)(a0 + pl * a.a_plane_rows), &full[s]);
+#pragma unroll
+                    for (int pl = 0; pl < 4; ++pl)
+                        tma_2d(st + 4 * kATile + pl * kBTile, &mapB, kx, (int)(b0 + pl * a.b_plane_rows), &full[s]);
+                    ++issued;
+                    if (++s == kStages) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+            }
+            if (!ok) {
+                for (int k = 0; k < kStages && k < issued; ++k) {
+                    s = (s + kStages - 1) % kStages;
+                    if (s == kStages - 1) ph ^= 1;
+                    const uint64_t t0 = gtimer();
+                    while (!mbar_try(&full[s], ph) && gtimer() - t0 < kTimeoutNs) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer: one accumulator pair per channel
+            const uint32_t id_pos = idesc(128, kN, false), id_neg = idesc(128, kN, true);
+            int s = 0;
+            uint32_t ph = 0, aph = 0;
+            bool any = false, ok = true;
+            int w, mt;
+            for (int i = 0; ok && unit_of(a, blockIdx.x + i * gridDim.x, w, mt); ++i) {
+                if (!mbar_wait(acc_empty, aph ^ 1, abort_flag)) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    if (!mbar_wait(&full[s], ph, abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + s * kStage);
+                    const int ch = (kb - kb0) / a.kb_ch;
+                    const uint32_t dr = tbase + (uint32_t)(ch * 2 * kN), di = dr + kN;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        uint64_t ad[4], bd[4];
+#pragma unroll
+                        for (int pl = 0; pl < 4; ++pl) {
+                            ad[pl] = sdesc(base + pl * kATile + kk * 32);
+                            bd[pl] = sdesc(base + 4 * kATile + pl * kBTile + kk * 32);
+                        }
+                        const uint32_t first = (kb % a.kb_ch == 0 && kk == 0) ? 0u : 1u;
+                        // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
+                        mma(dr, ad[0], bd[0], id_pos, first);
+                        mma(dr, ad[0], bd[1], id_pos, 1);
+                        mma(dr, ad[1], bd[0], id_pos, 1);
+                        mma(dr, ad[2], bd[2], id_neg, 1);
+                        mma(dr, ad[2], bd[3], id_neg, 1);
+                        mma(dr, ad[3], bd[2], id_neg, 1);
+                        mma(di, ad[0], bd[2], id_pos, first);
+                        mma(di, ad[0], bd[3], id_pos, 1);
+                        mma(di, ad[1], bd[2], id_pos, 1);
+                        mma(di, ad[2], bd[0], id_pos, 1);
+                        mma(di, ad[2], bd[1], id_pos, 1);
+                        mma(di, ad[3], bd[0], id_pos, 1);
+                    }
+                    any = true;
+                    mma_commit(&empty[s]);
+                    if (++s == kStages) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(acc_full);
+                aph ^= 1;
+            }
+            if (any) {
+                mma_commit(drain);
+                const uint64_t t0 = gtimer();
+                while (!mbar_try(drain, 0) && gtimer() - t0 < kTimeoutNs) {
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
+        const int q = warp & 3;
+        const int et = threadIdx.x - 64;
+        uint32_t aph = 0;
+        int w, mt;
+        for (int i = 0; unit_of(a, blockIdx.x + i * gridDim.x, w, mt); ++i) {
+            if (et == 0) {
+                const bool ok = mbar_wait(acc_full, aph, abort_flag);
+                *ep_ok = ok ? 1 : 0;
+                if (!ok) fail();
+            }
+            named_sync(1, 128);
+            if (!*ep_ok) break;
+            tc_fence_after();
+            const int t = a.work[2 * w + 1];
+            const unsigned long long mask = a.mask[w];
+            const int d = mt * 128 + q * 32 + lane;
+            const uint32_t tr = tbase + ((uint32_t)(q * 32) << 16);
+            for (int c0 = 0; c0 < kN; c0 += 16) {
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = 0.f;
+                for (int ch = 0; ch < a.nacc; ++ch) {
+                    float vr[16], vi[16];
+                    tmem_ld16(tr + ch * 2 * kN + c0, vr);
+                    tmem_ld16(tr + ch * 2 * kN + kN + c0, vi);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = fmaf(vr[j], vr[j], fmaf(vi[j], vi[j], v[j]));
+                }
+                if (d < a.n_det) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int rho = t * kN + c0 + j;
+                        if ((mask >> (c0 + j)) & 1ull) atomicAdd(&a.cube[(size_t)rho * a.n_det + d], a.scale * v[j]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty);
+            aph ^= 1;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols));
+    }
+}
+
+// 64-bit crop mask of each work item's scan tile (bit j: scan 64 t + j)
+__global__ void crop_mask_kernel(CubeTcArgs a) {
+    __shared__ unsigned long long part[4][2];
+    const int w = blockIdx.x * (blockDim.x / 64) + threadIdx.x / 64;
+    const int j = threadIdx.x % 64;
+    bool in = false;
+    if (w < a.n_work) {
+        const int bs = a.work[2 * w], t = a.work[2 * w + 1];
+        const SiteDev st = a.sites[a.site_ids[bs]];
+        const int rho = t * kN + j;
+        in = rho < a.P && in_crop(a.scans[2 * rho], a.scans[2 * rho + 1], st.ty, st.tx, a.ny, a.nx, a.fy, a.fx);
+    }
+    // every lane takes part in the vote and the barrier
+    const unsigned bits = __ballot_sync(0xffffffffu, in);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x / 64][(threadIdx.x / 32) & 1] = bits;
+    __syncthreads();
+    if (j == 0 && w < a.n_work)
+        a.mask[w] = part[threadIdx.x / 64][0] | (part[threadIdx.x / 64][1] << 32);
+}
+
+}  // namespace
+
+cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int a_k, const void* B, int64_t b_rows,
+                        cudaStream_t s) {
+    if (a.n_work < 1) return cudaSuccess;
+    if (a.nacc < 1 || a.nacc > 4 || a.kb_ch < 1 || a.mt_per < 1 || a.ch0 < 0 || a_k % 32)
+        return cudaErrorInvalidValue;
+    if ((a.ch0 + a.nacc) * a.kb_ch * 32 > a_k) return cudaErrorInvalidValue;
+    // every tile inside its operand: A rows of the last site, B rows of the last scan tile
+    if ((int64_t)(a.n_sites - 1) * a.a_site_rows + 3 * a.a_plane_rows + (int64_t)a.mt_per * 128 > a_rows)
+        return cudaErrorInvalidValue;
+    if (3 * a.b_plane_rows + (int64_t)a.n_tiles * kN > b_rows) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    cudaError_t e = make_map_2d(&ma, A, a_rows, a_k, 128);
+    if (e != cudaSuccess) return e;
+    e = make_map_2d(&mb, B, b_rows, a.kb_ch * 32, kN);
+    if (e != cudaSuccess) return e;
+    // the crop masks of the work items (4 items per 256-thread block)
+    crop_mask_kernel<<<(a.n_work + 3) / 4, 256, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    static bool attr = false;
+    if (!attr) {
+        e = cudaFuncSetAttribute(cube_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int units = a.n_work * a.mt_per;
+    const int grid = units < num_sms() ? units : num_sms();
+    cube_tc_kernel<<<grid, kThreads, kSmem, s>>>(ma, mb, a);
+    return cudaGetLastError();
+}
