@@ -124,3 +124,41 @@ def test_qeels_bins_host(capi):
             capi.bip_qeels_bins(ctx, 2)
     finally:
         capi.bip_destroy(ctx)
+
+
+def test_model_and_launch_controls_host(capi):
+    """Argument checks of the model-parameter, launch-control and reverse-pass
+    entry points, all before any GPU work (the calls fail or succeed on the
+    host alone)."""
+    ctx = capi.bip_create(capi.make_config(synth.config1()))
+    try:
+        lib = capi.lib()
+        D = ctypes.c_double
+        # occupancies need built sites; NULL restores the unit weights
+        occ = (D * 4)(1.0, 1.0, 1.0, 1.0)
+        assert lib.bip_set_occupancy(ctx, occ) == 1
+        assert "build" in capi.bip_last_error(ctx)
+        assert lib.bip_set_occupancy(ctx, None) == 0
+        # aberrations: finite values only
+        assert lib.bip_set_aberrations(ctx, D(float("nan")), D(0.0), None) == 1
+        assert lib.bip_set_aberrations(ctx, D(25.0), D(1.0e5), None) == 0
+        # launch shapes: tile widths multiples of 16 up to 256, no negatives
+        assert lib.bip_set_launch(ctx, 0, 17) == 1
+        assert lib.bip_set_launch(ctx, -1, 0) == 1
+        assert lib.bip_set_launch(ctx, 0, 272) == 1
+        assert lib.bip_set_launch(ctx, 19, 224) == 0
+        assert lib.bip_set_launch(ctx, 0, 0) == 0
+        assert lib.bip_set_capture_safe(ctx, 1) == 0 and lib.bip_set_capture_safe(ctx, 0) == 0
+        assert lib.bip_set_raster_eval(ctx, 0) == 0 and lib.bip_set_raster_eval(ctx, 1) == 0
+        assert lib.bip_check_errors(ctx, None) == 0
+        # the reverse pass and the autotuner need the builds first
+        scans = np.zeros((4, 2))
+        sp = scans.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        dummy = ctypes.c_void_p(16)
+        assert lib.bip_coreloss_grad(ctx, None, dummy, sp, 4, dummy, dummy, None, None, None, None) == 1
+        assert "bip_build_s1" in capi.bip_last_error(ctx)
+        assert lib.bip_autotune(ctx, dummy, sp, 4, dummy, None, None, None, None) == 1
+    finally:
+        capi.bip_destroy(ctx)
+    assert capi.lib().bip_set_launch(None, 0, 0) == 1
+    assert capi.lib().bip_set_occupancy(None, None) == 1
