@@ -1445,7 +1445,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
                 // A = M transposed to rows d, K = (ch, b), as split planes; then
                 // the per-beam contraction and |.|^2 channel sum on tcgen05
                 SplitArgs sa{(const float2*)c->mt32.p, 1, Dpad, (int64_t)perMt, Dpad, (int)KB, nb,
-                             (uint16_t*)c->cubeA.p, (int64_t)4 * D128 * KB, D128, (int)KB, 0, 0};
+                             (uint16_t*)c->cubeA.p, (int64_t)(4 * D128 * KB), D128, (int)KB, 0, 0};
                 TIMED(c, BIP_STAGE_QUADFORM, s, bip_split_planes(sa, s));
                 CubeTcArgs ct{};
                 ct.n_work = cube_off[bi + 1] - cube_off[bi];
@@ -1480,7 +1480,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             Gq.epi = TC_EPI_C32;
             Gq.N = (Bpad % 256 == 0) ? 256 : 128;
             Gq.npl = npl;
-            Gq.A = TcOperand{c->mt16.p, (int64_t)SB * npl * Bpad, (int64_t)nch * Dpad, npl * (int64_t)Bpad, Bpad};
+            Gq.A = TcOperand{c->mt16.p, (int64_t)SB * npl * Bpad, nch * Dpad, npl * (int64_t)Bpad, Bpad};
             Gq.B = Gq.A;
             Gq.kb = nch * Dpad / 32;
             Gq.n_sites = nb;
@@ -1998,11 +1998,11 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
                 // one contraction over K = (n, b): A = Mbar^T rows d, B = conj(H S1)^T rows r
                 for (int n = 0; n < nch; ++n) {
                     SplitArgs sg{(const float2*)c->g_gmt.p + (size_t)n * Dpad, 1, (int64_t)ldm, (int64_t)perMt, Dpad,
-                                 Bpad, nb, (uint16_t*)c->g_sA2.p, (int64_t)4 * D128 * KB, D128, (int)KB, n * Bpad, 0};
+                                 Bpad, nb, (uint16_t*)c->g_sA2.p, (int64_t)(4 * D128 * KB), D128, (int)KB, n * Bpad, 0};
                     CUDA_TRY(c, bip_split_planes(sg, s));
                 }
                 SplitArgs sx{(const float2*)c->opB32.p, 1, K, (int64_t)perB, K, (int)KB, nb, (uint16_t*)c->g_sB2.p,
-                             (int64_t)4 * K * KB, K, (int)KB, 0, 1};
+                             (int64_t)(4 * K * KB), K, (int)KB, 0, 1};
                 CUDA_TRY(c, bip_split_planes(sx, s));
                 TcArgs u{};
                 u.epi = TC_EPI_C32;

@@ -86,15 +86,6 @@ __device__ __forceinline__ void st_v4(void* p, const uint32_t (&v)[4]) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // F8: the operands are written as E4M3 bytes, row t scaled by
 // inv_row[side][t] and channel n by inv_h[n] (per-window scales)
 template <bool F8>
@@ -115,7 +106,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* drain = acc_empty + 2;
     uint32_t* tmem_slot = (uint32_t*)(drain + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-    volatile int* ep_ok = abort_flag + 1;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) {
