@@ -170,7 +170,26 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # GPU arm
 
-def algorithmic(cfg, geo_sizes, n_sites, n_crop, nch, geo_beams=None, path="fp32"):
+def raster_shape(scans):
+    """(rows, columns) when the scan list is a raster (the library then
+    evaluates the scan polynomial separably), else None."""
+    sc = np.asarray(scans, dtype=np.float64)
+    P = len(sc)
+    if P == 0:
+        return None
+    mx = 1
+    while mx < P and sc[mx, 0] == sc[0, 0]:
+        mx += 1
+    if P % mx:
+        return None
+    my = P // mx
+    g = sc.reshape(my, mx, 2)
+    if np.max(np.abs(g[:, :, 0] - g[:, :1, 0])) > 1e-9 or np.max(np.abs(g[:, :, 1] - g[:1, :, 1])) > 1e-9:
+        return None
+    return my, mx
+
+
+def algorithmic(cfg, geo_sizes, n_sites, n_crop, nch, geo_beams=None, path="fp32", raster=None):
     """Per-stage algorithmic work of one step (flops or bytes), the figures
     the roofline fractions divide."""
     # bytes per complex operand element: complex64, four bf16 planes
@@ -187,7 +206,14 @@ def algorithmic(cfg, geo_sizes, n_sites, n_crop, nch, geo_beams=None, path="fp32
     ky = max(abs(int(h[0])) // cfg.fy for h in geo_beams) if geo_beams is not None else 0
     kx = max(abs(int(h[1])) // cfg.fx for h in geo_beams) if geo_beams is not None else 0
     n_diff = ((4 * ky + 1) * (4 * kx + 1) + 1) // 2
-    cmac_quad = n_sites * B * (B + 1) // 2 + n_diff * n_crop
+    if raster is not None:
+        # separable evaluation on a raster: (2K_y+1)(4K_x+1) differences, two
+        # dense stages over every scan row and column of each site
+        my, mx = raster
+        rows, cols = 2 * ky + 1, 4 * kx + 1
+        cmac_quad = n_sites * (B * (B + 1) // 2 + my * rows * cols + my * mx * cols // 2)
+    else:
+        cmac_quad = n_sites * B * (B + 1) // 2 + n_diff * n_crop
     return {
         "coupling": 8.0 * cmac_coupling,        # real flops (complex MAC = 8)
         "gram": 8.0 * cmac_gram,
@@ -320,7 +346,7 @@ def run_gpu(args, rank, world):
         results[path] = res
 
     return cfg, sp, results, dict(n_sites=n_sites, P=P, nch=nch, n_crop=n_crop, peaks=peaks,
-                                  peak_kind=peak_kind)
+                                  peak_kind=peak_kind, raster=raster_shape(scans))
 
 
 # ---------------------------------------------------------------------------
@@ -486,7 +512,8 @@ def ncu_traffic(path, stage):
 def stage_roofline(cfg, path, stage, ms, n, steps, info, geo_sizes):
     """Achieved rate and roofline fraction of one stage: ms and n are the
     stage's summed event time and launch count over `steps` steps."""
-    alg = algorithmic(cfg, geo_sizes, info["n_sites"], info["n_crop"], info["nch"], info.get("beams"), path)
+    alg = algorithmic(cfg, geo_sizes, info["n_sites"], info["n_crop"], info["nch"], info.get("beams"), path,
+                      info.get("raster"))
     peaks = info["peaks"]
     ms_launch = ms / max(n, 1)
     out = {"kernel": stage, "launches": n, "ms_per_launch": ms_launch}
