@@ -452,6 +452,34 @@ def run_grad(reps=3, prec="mixed"):
             "evals_per_s": n_sites * len(sp.scans) / (ms / 1e3), "precision": prec}
 
 
+def run_precision():
+    """Config 3's report: the config-1 map in every precision, its relative
+    L2 distance to the FP64 oracle's map (stored in tests/golden) and to the
+    FP32 path's map."""
+    import torch
+    import synth
+    from paper_2607_00756_gb300.context import BipContext
+    dev = torch.device("cuda:0")
+    cfg = synth.config1()
+    sp = synth.make_specimen(cfg)
+    # the FP64 oracle's map, stored by tests/golden/make_config1_map.py
+    ref = np.loadtxt(os.path.join(ROOT, "tests", "golden", "config1_map.txt"))
+    V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
+    H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+    maps = {}
+    for prec in ("fp32", "split_bf16", "mixed", "fp8"):
+        ctx = BipContext(cfg, prec=prec)
+        ctx.build(V, sp.atoms, sp.nch)
+        maps[prec] = ctx.map(H, sp.scans).cpu().numpy()
+        ctx.close()
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return {"workload": "config1: 128x128 grid, 5 slices, 4 sites x 3 channels, 16x16 scans",
+            "vs_oracle_rel_l2": {p: rel(m, ref) for p, m in maps.items()},
+            "vs_fp32_rel_l2": {p: rel(m, maps["fp32"]) for p, m in maps.items() if p != "fp32"}}
+
+
 def run_cube(cfg, sp, prec="mixed", reps=2):
     """The 4D cube (the detector sum left open) on the benchmark workload:
     S1 + S2 builds and the cube, CUDA events; P x n_det floats out."""
@@ -714,6 +742,7 @@ def main():
         line["graphs"] = run_graphs()
         line["grad"] = run_grad()
         line["cube"] = run_cube(cfg, sp)
+        line["precision"] = run_precision()
     line["e2e"] = res.get("e2e")
     line["gpu_launches"] = res["launches"]
     line["clocks"] = res["clocks"]

@@ -245,3 +245,15 @@ def test_qeels_bins_and_invariant(c1, axis):
     # one bin by hand
     i = len(bins) // 2
     assert np.allclose(q[:, i], cube[:, h == bins[i]].sum(axis=1), rtol=1e-14, atol=0)
+
+
+def test_golden_config1_map_is_the_oracles():
+    """tests/golden/config1_map.txt (the benchmark's precision reference)
+    holds exactly what the oracle computes for config 1 today."""
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    stored = np.loadtxt(os.path.join(here, "golden", "config1_map.txt"))
+    sp = synth.make_specimen(synth.config1())
+    m = bip.bip_map(bip.make_problem(sp)).map
+    assert stored.shape == m.shape
+    assert np.max(np.abs(stored - m)) <= 1e-15 * np.max(np.abs(m))
