@@ -215,8 +215,9 @@ bip_status bip_coreloss_qeels(bip_ctx* ctx, const void* H, const double* scan_px
  *   <= 256) of the tensor-core path; 0 restores the built-in choice (tile
  *   counts against the SM count and the L2 size).
  * bip_autotune: times maps (two after a warm-up, CUDA events) over sites per
- *   batch and then coupling tile widths, keeps the fastest in the context
- *   and returns it; map_out holds the last map.  Results do not depend on
+ *   batch, then coupling tile widths, then the contraction order (see
+ *   bip_set_order), keeps the fastest in the context and returns it;
+ *   map_out holds the last map.  Results do not depend on
  *   these choices (each site's arithmetic and the site-sum order are fixed). */
 bip_status bip_set_capture_safe(bip_ctx* ctx, int32_t on);
 /* bip_set_raster_eval(ctx, on): with on (the default) a scan list that is a
@@ -227,7 +228,17 @@ bip_status bip_set_raster_eval(bip_ctx* ctx, int32_t on);
 bip_status bip_check_errors(bip_ctx* ctx, void* stream);
 bip_status bip_set_launch(bip_ctx* ctx, int32_t sites_per_batch, int32_t coupling_tile);
 bip_status bip_autotune(bip_ctx* ctx, const void* H, const double* scan_px, int32_t P, double* map_out,
-                        void* stream, int32_t* sites_per_batch, int32_t* coupling_tile, double* best_ms);
+                        void* stream, int32_t* sites_per_batch, int32_t* coupling_tile, int32_t* order,
+                        double* best_ms);
+/* bip_set_order: the scan contraction of the map, 0 (default) through the
+ * Gram matrix Q = sum_n M^H M and the lattice-difference polynomial
+ * (Algorithm 4's c^H Q c), 1 "beam order": |sum_b M_{d,b} c_b(rho)|^2 for
+ * every detector beam on tcgen05 (split BF16) with the detector sum taken in
+ * the epilogue -- cheaper when few scans meet each site; tensor-core
+ * precisions only (FP32 contexts keep the Gram route).  Beam order adds
+ * the terms of a site's map atomically, so its last bits may vary from run
+ * to run.  bip_autotune also times the other order. */
+bip_status bip_set_order(bip_ctx* ctx, int32_t order);
 
 /* Model parameters of the map beyond the specimen (for fitting; Sec. 5
  * names the matrices as a forward model for simulation-constrained

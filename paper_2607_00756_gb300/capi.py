@@ -73,7 +73,8 @@ def _load():
         "bip_set_raster_eval": [VP, I32],
         "bip_check_errors": [VP, VP],
         "bip_set_launch": [VP, I32, I32],
-        "bip_autotune": [VP, VP, P(D), I32, VP, VP, P(I32), P(I32), P(D)],
+        "bip_autotune": [VP, VP, P(D), I32, VP, VP, P(I32), P(I32), P(I32), P(D)],
+        "bip_set_order": [VP, I32],
         "bip_set_aberrations": [VP, D, D, VP],
         "bip_coreloss_grad": [VP, VP, VP, P(D), I32, VP, VP, VP, P(D), VP, VP],
     }
@@ -292,14 +293,20 @@ def bip_set_launch(ctx, sites_per_batch=0, coupling_tile=0):
 
 def bip_autotune(ctx, H, scans, out, stream=None):
     """Times launch choices on this map; returns (sites per batch, coupling
-    tile width (0: built-in), ms per map) and keeps them in the context."""
+    tile width (0: built-in), contraction order (0 Gram, 1 beam), ms per
+    map) and keeps them in the context."""
     import torch
     s, sp = _scans(scans)
-    sb, cw, ms = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
+    sb, cw, od, ms = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
     _check("bip_autotune", ctx, _lib.bip_autotune(ctx, _dev(H, torch.complex64, "H"), sp, len(s),
                                                    _dev(out, torch.float64, "out"), _stream(stream),
-                                                   ctypes.byref(sb), ctypes.byref(cw), ctypes.byref(ms)))
-    return sb.value, cw.value, ms.value
+                                                   ctypes.byref(sb), ctypes.byref(cw), ctypes.byref(od),
+                                                   ctypes.byref(ms)))
+    return sb.value, cw.value, od.value, ms.value
+
+
+def bip_set_order(ctx, order):
+    _check("bip_set_order", ctx, _lib.bip_set_order(ctx, int(order)))
 
 
 def bip_set_occupancy(ctx, occ):

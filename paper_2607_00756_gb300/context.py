@@ -92,9 +92,14 @@ class BipContext:
         out = torch.empty((nch, self.n_det, self.B), dtype=torch.complex64, device=device)
         return capi.bip_site_coupling(self.ctx, H, site, out)
 
+    def set_order(self, order):
+        """Scan contraction: 0 (default) Gram matrix, 1 beam order."""
+        capi.bip_set_order(self.ctx, order)
+
     def autotune(self, H, scans, out=None, stream=None):
         """Time launch choices on this map and keep the fastest: returns
-        (sites per batch, coupling tile width (0: built-in), ms per map)."""
+        (sites per batch, coupling tile width (0: built-in), contraction order,
+        ms per map)."""
         scans = np.asarray(scans, dtype=np.float64)
         if out is None:
             out = torch.empty(len(scans), dtype=torch.float64, device=H.device)

@@ -73,6 +73,7 @@ struct bip_ctx {
     // tuned launch parameters (0: the built-in choice)
     int sb_override = 0, cw_override = 0;
     bool raster_eval = true;            // separable evaluation on raster scan lists
+    int order = 0;                      // scan contraction: 0 Gram matrix, 1 beam order
     DevBuf ray, rax;                    // its phase tables
     DevBuf aw1[6], aw2[6];              // per-target / per-parent weights (reconstruction adjoint)
     bool adj_tables = false;
@@ -1213,13 +1214,19 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         c->scans_cache.assign(scans, scans + 2 * P);
     }
     float* partial = partial_out;
-    if (cube_out) {
-        // the cube: c_b(rho) for every scan, the cube cleared
-        CUDA_TRY(c, cudaMemsetAsync(cube_out, 0, (size_t)P * geo.n_det * sizeof(float), s));
+    // beam order: the map as |M c|^2 summed over the detector beams on the
+    // cube kernel, without the Gram matrix (tensor-core precisions)
+    const bool beam = !cube_out && tc && c->order == 1;
+    if (cube_out || beam) {
+        // c_b(rho) for every scan
         CUDA_TRY(c, ensure(c->illum, (size_t)Bpad * P * sizeof(float2), false, s));
         IllumArgs ia{P, geo.B, Bpad, (const int2*)c->hbeam.p, (const double2*)c->coef.p, (const double*)c->scans_d.p,
                      g.ny, g.nx, (float2*)c->illum.p};
         CUDA_TRY(c, bip_illum(ia, s));
+    }
+    if (cube_out) {
+        // the cube cleared
+        CUDA_TRY(c, cudaMemsetAsync(cube_out, 0, (size_t)P * geo.n_det * sizeof(float), s));
     } else {
         if (!partial) {
             CUDA_TRY(c, ensure(c->partial, (size_t)c->n_sites * P * sizeof(float), false, s));
@@ -1234,7 +1241,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     // row and column, angles reduced in FP64
     Raster raster;
     RasterArgs rargs{};
-    if (!cube_out && c->raster_eval) raster = detect_raster(scans, P);
+    if (!cube_out && !beam && c->raster_eval) raster = detect_raster(scans, P);
     if (raster.ok) {
         const int rows = 2 * c->Ky + 1, cols = 4 * c->Kx + 1;
         if (!same_scans) {
@@ -1287,7 +1294,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             CUDA_TRY(c, ensure(c->opB16, SB * perB * 8, true, s));
         }
         CUDA_TRY(c, ensure(c->mt16, SB * perMt * 8, true, s));
-        if (cube_out) CUDA_TRY(c, ensure(c->mt32, SB * perMt * sizeof(float2), true, s));
+        if (cube_out || beam) CUDA_TRY(c, ensure(c->mt32, SB * perMt * sizeof(float2), true, s));
         CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
     }
     CUDA_TRY(c, ensure(c->q32, SB * perQ * sizeof(float2), true, s));
@@ -1328,7 +1335,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
 
     // the cube on tcgen05: c_b(rho) as split planes [4][P64][Bpad] once, and
     // work lists of (site in batch, 64-scan tile meeting its crop mask)
-    const bool cube_tc = cube_out && tc;
+    const bool cube_tc = (cube_out || beam) && tc;
     const int P64 = round_up(P, 64), D128 = round_up(Dpad, 128);
     const size_t KB = (size_t)nch * Bpad;
     std::vector<int> cube_off;
@@ -1433,7 +1440,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
                 A.scaleB = (const float*)c->f8sB.p;
                 A.scaleB_site = Dpad;
             }
-            if (cube_out) {
+            if (cube_out || beam) {
                 // per-beam values want M itself to FP32: complex64 rows (ch, b)
                 A.epi = TC_EPI_C32;
                 A.out32 = (float2*)c->mt32.p;
@@ -1441,7 +1448,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
                 A.out32_ld = Dpad;
             }
             TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(A, s));
-            if (cube_out) {
+            if (cube_out || beam) {
                 // A = M transposed to rows d, K = (ch, b), as split planes; then
                 // the per-beam contraction and |.|^2 channel sum on tcgen05
                 SplitArgs sa{(const float2*)c->mt32.p, 1, Dpad, (int64_t)perMt, Dpad, (int)KB, nb,
@@ -1466,6 +1473,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
                 ct.ny = g.ny; ct.nx = g.nx; ct.fy = g.fy; ct.fx = g.fx;
                 ct.scale = (float)(g.fy * g.fx);
                 ct.cube = cube_out;
+                ct.partial = beam ? partial : nullptr;
                 ct.err = (int*)c->errflag.p;
                 for (int ch0 = 0; ch0 < nch; ch0 += 4) {
                     ct.ch0 = ch0;
@@ -1550,7 +1558,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_bin(d, s));
         if (!raster.ok && d.n_work > 0) TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_eval(d, s));
     }
-    if (raster.ok && c->n_sites > 0 && !cube_out) {
+    if (raster.ok && c->n_sites > 0 && !cube_out && !beam) {
         // the scan polynomial of every site at once (sites in order)
         DiffArgs d{};
         d.n_sites = c->n_sites;
@@ -1675,6 +1683,13 @@ bip_status bip_set_raster_eval(bip_ctx* c, int32_t on) {
     return BIP_OK;
 }
 
+bip_status bip_set_order(bip_ctx* c, int32_t order) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (order != 0 && order != 1) return fail(c, BIP_ERR_INVALID_ARG, "order must be 0 (Gram) or 1 (beam)");
+    c->order = order;
+    return BIP_OK;
+}
+
 bip_status bip_set_launch(bip_ctx* c, int32_t sites_per_batch, int32_t coupling_tile) {
     if (!c) return BIP_ERR_INVALID_ARG;
     if (sites_per_batch < 0 || coupling_tile < 0 || coupling_tile > 256 || coupling_tile % 16)
@@ -1685,7 +1700,7 @@ bip_status bip_set_launch(bip_ctx* c, int32_t sites_per_batch, int32_t coupling_
 }
 
 bip_status bip_autotune(bip_ctx* c, const void* H, const double* scan_px, int32_t P, double* map_out, void* stream,
-                        int32_t* sites_per_batch, int32_t* coupling_tile, double* best_ms) {
+                        int32_t* sites_per_batch, int32_t* coupling_tile, int32_t* order, double* best_ms) {
     bip_status st = check_map_args(c, H, scan_px, P, map_out);
     if (st != BIP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1739,13 +1754,30 @@ bip_status bip_autotune(bip_ctx* c, const void* H, const double* scan_px, int32_
             }
         }
     }
+    // the scan contraction's order: the Gram matrix, or |M c|^2 per beam
+    const int order0 = c->order;
+    int best_order = order0;
+    if (st == BIP_OK && tc) {
+        for (int o : {0, 1}) {
+            if (o == order0) continue;
+            c->order = o;
+            st = time_map(best_sb, best_cw, &t);
+            if (st != BIP_OK) break;
+            if (t < best) {
+                best = t;
+                best_order = o;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->sb_override = best_sb;
     c->cw_override = best_cw;
+    c->order = best_order;
     if (st != BIP_OK) return st;
     if (sites_per_batch) *sites_per_batch = best_sb;
     if (coupling_tile) *coupling_tile = best_cw;
+    if (order) *order = best_order;
     if (best_ms) *best_ms = best;
     return BIP_OK;
 }

@@ -365,7 +365,9 @@ struct CubeTcArgs {
     const int32_t* site_ids;
     int ny, nx, fy, fx;
     float scale;                    // f_y f_x
-    float* cube;                    // [P][n_det], added to (atomically)
+    float* cube;                    // [P][n_det], added to (atomically); or
+    float* partial;                 // map mode: [n_sites_total][P] per-site map, the
+                                    // detector sum taken in the epilogue (atomically)
     int* err;
 };
 cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int a_k, const void* B, int64_t b_rows,

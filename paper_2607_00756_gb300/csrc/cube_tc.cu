@@ -1,7 +1,9 @@
 // The 4D cube (Sec. 2.2.6) on the tensor cores: per site, channel and
 // detector beam d, a_d(rho) = sum_b M^(n)_{d,b} c_b(rho), and
 //   cube[rho][d] += f_y f_x sum_n |a_d(rho)|^2
-// for the scans of the site's crop mask.  Split BF16 (hi + lo, three
+// for the scans of the site's crop mask -- or, in map mode, the same terms
+// summed over d into the site's map (the "beam order" of the scan
+// contraction: |M c|^2 directly, without the Gram matrix).  Split BF16 (hi + lo, three
 // products per real product, twelve per complex one), FP32 accumulation in
 // TMEM.
 //
@@ -218,7 +220,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int j = 0; j < 16; ++j) v[j] = fmaf(vr[j], vr[j], fmaf(vi[j], vi[j], v[j]));
                 }
-                if (d < a.n_det) {
+                if (a.partial) {
+                    // map mode: the detector sum over this warp's 32 beams, one
+                    // addition per scan and warp into the site's map
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        float x = d < a.n_det ? v[j] : 0.f;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                        const int rho = t * kN + c0 + j;
+                        if (lane == 0 && ((mask >> (c0 + j)) & 1ull))
+                            atomicAdd(&a.partial[(size_t)a.site_ids[a.work[2 * w]] * a.P + rho], a.scale * x);
+                    }
+                } else if (d < a.n_det) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int rho = t * kN + c0 + j;

@@ -157,7 +157,8 @@ def test_model_and_launch_controls_host(capi):
         dummy = ctypes.c_void_p(16)
         assert lib.bip_coreloss_grad(ctx, None, dummy, sp, 4, dummy, dummy, None, None, None, None) == 1
         assert "bip_build_s1" in capi.bip_last_error(ctx)
-        assert lib.bip_autotune(ctx, dummy, sp, 4, dummy, None, None, None, None) == 1
+        assert lib.bip_autotune(ctx, dummy, sp, 4, dummy, None, None, None, None, None) == 1
+        assert lib.bip_set_order(ctx, 2) == 1 and lib.bip_set_order(ctx, 1) == 0 and lib.bip_set_order(ctx, 0) == 0
     finally:
         capi.bip_destroy(ctx)
     assert capi.lib().bip_set_launch(None, 0, 0) == 1

@@ -80,11 +80,50 @@ def test_autotune_keeps_the_map(lib, prec):
     ctx.build(torch.tensor(sp.V, dtype=torch.float32, device=dev), sp.atoms, sp.nch)
     H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
     m0 = ctx.map(H, sp.scans).cpu().numpy()
-    sb, cw, ms = ctx.autotune(H, sp.scans)
+    sb, cw, order, ms = ctx.autotune(H, sp.scans)
     assert 1 <= sb <= 32 and (cw == 0 or (cw % 16 == 0 and cw <= 256)) and ms > 0.0
+    assert order in (0, 1) and (prec != "fp32" or order == 0)
     m1 = ctx.map(H, sp.scans).cpu().numpy()
-    assert rel(m1, m0) < 1e-6
+    # the Gram route repeats the map exactly; the beam order (split BF16,
+    # another summation) within the mixed path's bar
+    assert rel(m1, m0) < (1e-6 if order == 0 else 1e-3)
+    ctx.set_order(0)
     # any explicit choice gives the same map too
     ctx.set_launch(1, 128 if prec != "fp32" else 0)
     assert rel(ctx.map(H, sp.scans).cpu().numpy(), m0) < 1e-6
+    ctx.close()
+
+
+
+@pytest.mark.parametrize("which", ["config1", "edge", "aniso"])
+@pytest.mark.parametrize("prec", ["mixed", "split_bf16"])
+def test_beam_order_map(lib, which, prec):
+    """The map in beam order (|M c|^2 per detector beam on tcgen05, the
+    detector sum in the epilogue) against the oracle and the Gram route."""
+    if which == "config1":
+        cfg = synth.config1()
+    elif which == "aniso":
+        cfg = synth.config1().replace(name="aniso", ny=64, nx=128, ly=7.5, lx=10.0, cells_y=3, cells_x=4, fy=1,
+                                      fx=2, win=32, ion_cells=(1, 3), ion_slices=(1, 4),
+                                      scan_y=(10.3, 3.5, 9), scan_x=(20.7, 6.25, 7))
+    else:
+        from test_gpu_map import _edge_specimen
+        cfg, sp = _edge_specimen()
+    if which != "edge":
+        sp = synth.make_specimen(cfg)
+    ref = obip.bip_map(obip.make_problem(sp))
+    dev = torch.device("cuda:0")
+    ctx = lib(cfg, prec=prec)
+    ctx.build(torch.tensor(sp.V, dtype=torch.float32, device=dev), sp.atoms, sp.nch)
+    H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+    m_gram = ctx.map(H, sp.scans).cpu().numpy()
+    ctx.set_order(1)
+    m_beam = ctx.map(H, sp.scans).cpu().numpy()
+    parts = ctx.sites(H, sp.scans).cpu().numpy()
+    assert rel(m_beam, ref.map) < 1e-3
+    assert rel(parts, ref.partials) < 1e-3
+    assert rel(m_beam, m_gram) < 1e-3
+    pr = obip.make_problem(sp)
+    for k in range(len(pr.ion)):
+        assert np.all(parts[k][~obip.crop_mask(pr, k, sp.scans)] == 0.0)
     ctx.close()
