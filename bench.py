@@ -480,6 +480,53 @@ def run_precision():
             "vs_fp32_rel_l2": {p: rel(m, maps["fp32"]) for p, m in maps.items() if p != "fp32"}}
 
 
+def run_orders(cfg, sp, prec="mixed", reps=2):
+    """The three orders of the scan contraction (Gram matrix, beam order,
+    probe order) on sub-rasters of the benchmark's scan grid: map time after
+    one S1 + S2 build (CUDA events, one warm-up map), the autotuner's pick,
+    and each order's distance to the Gram route's map."""
+    import torch
+    from paper_2607_00756_gb300.context import BipContext
+    dev = torch.device("cuda:0")
+    ctx = BipContext(cfg, prec=prec)
+    V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
+    H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+    ctx.build(V, sp.atoms, sp.nch)
+    n = int(round(np.sqrt(len(sp.scans))))
+    grid = sp.scans.reshape(n, n, 2)
+    c = n // 2
+    out = {"step": "map only (matrices built once); sub-rasters of the scan grid at its centre",
+           "precision": prec}
+    for side in (4, 32):
+        sc = np.ascontiguousarray(grid[c - side // 2:c + side // 2, c - side // 2:c + side // 2].reshape(-1, 2))
+        row = {}
+        maps = {}
+        for order, name in ((0, "gram"), (1, "beam"), (2, "probe")):
+            ctx.set_order(order)
+            m = ctx.map(H, sc)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                ctx.map(H, sc)
+            e1.record()
+            torch.cuda.synchronize()
+            row[f"{name}_ms"] = e0.elapsed_time(e1) / reps
+            maps[name] = m.cpu().numpy()
+        ref = maps["gram"]
+        for name in ("beam", "probe"):
+            row[f"{name}_vs_gram_rel_l2"] = float(np.linalg.norm(maps[name] - ref) / np.linalg.norm(ref))
+        ctx.set_order(0)
+        sb, cw, order, ms = ctx.autotune(H, sc)
+        row["autotune"] = {"sites_per_batch": sb, "coupling_tile": cw, "order": ["gram", "beam", "probe"][order],
+                           "ms": ms}
+        ctx.set_order(0)
+        ctx.set_launch(0, 0)
+        out[f"P{len(sc)}"] = row
+    ctx.close()
+    return out
+
+
 def run_cube(cfg, sp, prec="mixed", reps=2):
     """The 4D cube (the detector sum left open) on the benchmark workload:
     S1 + S2 builds and the cube, CUDA events; P x n_det floats out."""
@@ -742,6 +789,7 @@ def main():
         line["graphs"] = run_graphs()
         line["grad"] = run_grad()
         line["cube"] = run_cube(cfg, sp)
+        line["orders"] = run_orders(cfg, sp)
         line["precision"] = run_precision()
     line["e2e"] = res.get("e2e")
     line["gpu_launches"] = res["launches"]

@@ -235,9 +235,15 @@ bip_status bip_autotune(bip_ctx* ctx, const void* H, const double* scan_px, int3
  * (Algorithm 4's c^H Q c), 1 "beam order": |sum_b M_{d,b} c_b(rho)|^2 for
  * every detector beam on tcgen05 (split BF16) with the detector sum taken in
  * the epilogue -- cheaper when few scans meet each site; tensor-core
- * precisions only (FP32 contexts keep the Gram route).  Beam order adds
- * the terms of a site's map atomically, so its last bits may vary from run
- * to run.  bip_autotune also times the other order. */
+ * precisions only (FP32 contexts keep the Gram route); 2 "probe order":
+ * the windowed probes Psi(rho, r) = sum_b c_b(rho) S1_b(r) of every scan
+ * (one tcgen05 GEMM per site), then a^(n)_d(rho) = sum_r S2_d(r) H_n(r)
+ * Psi(rho, r) and |a|^2 summed over d and n as in beam order -- the cheapest
+ * order when few scans meet each site (work ~ P instead of the coupling's
+ * n_det nch B); mixed precision only (else BIP_ERR_UNSUPPORTED), at most
+ * 2048 scans per map (BIP_ERR_UNSUPPORTED from the map).  Beam and probe
+ * order add the terms of a site's map atomically, so its last bits may vary
+ * from run to run.  bip_autotune also times the other orders. */
 bip_status bip_set_order(bip_ctx* ctx, int32_t order);
 
 /* Model parameters of the map beyond the specimen (for fitting; Sec. 5

@@ -93,7 +93,8 @@ class BipContext:
         return capi.bip_site_coupling(self.ctx, H, site, out)
 
     def set_order(self, order):
-        """Scan contraction: 0 (default) Gram matrix, 1 beam order."""
+        """Scan contraction: 0 (default) Gram matrix, 1 beam order, 2 probe
+        order (mixed precision, up to 2048 scans)."""
         capi.bip_set_order(self.ctx, order)
 
     def autotune(self, H, scans, out=None, stream=None):

@@ -16,6 +16,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kRowPad = 128;        // aperture-side operand rows: the MMA's 128-row tiles
 constexpr int kDetPad = 32;         // detector-side rows: the N of a tile (multiple of 16, K of the Gram a multiple of 32)
 constexpr int kScanTile = 256;      // scans per quadratic-form work item
+constexpr int kProbeMaxScans = 2048; // the probe order keeps Psi of every scan for a batch of sites
 
 struct DevBuf {
     void* p = nullptr;
@@ -63,6 +64,7 @@ struct bip_ctx {
     DevBuf g_s1bar, g_s2bar, g_ubar, g_dA, g_dt1, g_dt2, g_adj, g_ckpt, g_seg, g_gvp;
     DevBuf g_tA, g_tB, g_sA2, g_sB2;    // split-BF16 operands of the reverse-pass contractions
     DevBuf cubeA, cubeB, cube_work, cube_mask;   // the cube on tcgen05
+    DevBuf s1t, psi, ybuf;              // the probe order: S1 transposed, Psi, H_n x Psi
     DevBuf pyc, pxc;                    // conjugated propagator tables (adjoint sweeps)
     // capture-safe maps: no host synchronisation, uploads only when the
     // scans or the batching change (so a CUDA graph can hold the launches)
@@ -73,7 +75,7 @@ struct bip_ctx {
     // tuned launch parameters (0: the built-in choice)
     int sb_override = 0, cw_override = 0;
     bool raster_eval = true;            // separable evaluation on raster scan lists
-    int order = 0;                      // scan contraction: 0 Gram matrix, 1 beam order
+    int order = 0;                      // scan contraction: 0 Gram matrix, 1 beam order, 2 probe order
     DevBuf ray, rax;                    // its phase tables
     DevBuf aw1[6], aw2[6];              // per-target / per-parent weights (reconstruction adjoint)
     bool adj_tables = false;
@@ -563,7 +565,7 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->g_gmt, &c->g_T, &c->g_D, &c->g_Dsum, &c->g_s1bar, &c->g_s2bar, &c->g_ubar, &c->g_dA,
                      &c->g_dt1, &c->g_dt2, &c->g_adj, &c->g_ckpt, &c->g_seg, &c->g_gvp, &c->pyc, &c->pxc,
                      &c->ray, &c->rax, &c->g_tA, &c->g_tB, &c->g_sA2, &c->g_sB2, &c->cubeA, &c->cubeB,
-                     &c->cube_work, &c->cube_mask};
+                     &c->cube_work, &c->cube_mask, &c->s1t, &c->psi, &c->ybuf};
     for (DevBuf* b : all) release(*b);
     for (int i = 0; i < 6; ++i) {
         release(c->aw1[i]);
@@ -734,8 +736,11 @@ GatherArgs gather_args(const bip_ctx* c, int side, const int32_t* ids, int n) {
 // from the stashes, then W X with the epilogue writing both coupling
 // operands -- BF16, or E4M3 with the per-window scales computed in between
 // from the parents' window maxima (which the X preparation takes).
+// probe: the aperture side written transposed and without H_n, the probe
+// order's operand: [site][4 planes][K][Bpad], re in plane 0 and im in plane 2
+// (the split-BF16 layout with zero lo planes)
 bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H, void* opA, void* opB,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool probe = false) {
     const bip_config& g = c->cfg;
     const BipGeometry& geo = c->geo;
     const int K = g.win * g.win, Dpad = c->Dpad, Bpad = c->Bpad, nch = c->nch_max;
@@ -799,6 +804,13 @@ bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H,
                           (int64_t)2 * Dpad * K, (int64_t)Dpad * K};
     r.side[1] = ReconSide{geo.B, Bpad, Bpad, Bpad / 128, nch, +1, (const int2*)c->hbeam.p, 2 * Dw, 3 * nb,
                           (int64_t)2 * nch * Bpad * K, (int64_t)nch * Bpad * K};
+    if (probe) {
+        r.side[1].nch = 0;
+        r.side[1].site_stride = (int64_t)4 * K * Bpad;
+        r.side[1].plane_stride = (int64_t)2 * K * Bpad;
+        r.side[1].trans = 1;
+        r.side[1].ld = Bpad;
+    }
     r.err = (int*)c->errflag.p;
     if (f8) {
         r.f8 = 1;
@@ -1217,7 +1229,13 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     // beam order: the map as |M c|^2 summed over the detector beams on the
     // cube kernel, without the Gram matrix (tensor-core precisions)
     const bool beam = !cube_out && tc && c->order == 1;
-    if (cube_out || beam) {
+    // probe order: the windowed probes Psi = C^T S1 of every scan, then
+    // |S2^T (H_n x Psi)|^2 summed over d and n on the cube kernel (mixed)
+    const bool probe = !cube_out && c->order == 2;
+    if (probe && (c->prec != BIP_PREC_MIXED || !c->recon_tc))
+        return fail(c, BIP_ERR_UNSUPPORTED, "the probe order needs the mixed precision and at most 64 parents per side");
+    if (probe && P > kProbeMaxScans) return fail(c, BIP_ERR_UNSUPPORTED, "the probe order takes at most 2048 scans");
+    if (cube_out || beam || probe) {
         // c_b(rho) for every scan
         CUDA_TRY(c, ensure(c->illum, (size_t)Bpad * P * sizeof(float2), false, s));
         IllumArgs ia{P, geo.B, Bpad, (const int2*)c->hbeam.p, (const double2*)c->coef.p, (const double*)c->scans_d.p,
@@ -1241,7 +1259,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     // row and column, angles reduced in FP64
     Raster raster;
     RasterArgs rargs{};
-    if (!cube_out && !beam && c->raster_eval) raster = detect_raster(scans, P);
+    if (!cube_out && !beam && !probe && c->raster_eval) raster = detect_raster(scans, P);
     if (raster.ok) {
         const int rows = 2 * c->Ky + 1, cols = 4 * c->Kx + 1;
         if (!same_scans) {
@@ -1295,6 +1313,12 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         }
         CUDA_TRY(c, ensure(c->mt16, SB * perMt * 8, true, s));
         if (cube_out || beam) CUDA_TRY(c, ensure(c->mt32, SB * perMt * sizeof(float2), true, s));
+        if (probe) {
+            const size_t P128 = round_up(P, 128), P64r = round_up(P, 64);
+            CUDA_TRY(c, ensure(c->s1t, SB * 4 * (size_t)K * Bpad * sizeof(uint16_t), true, s));
+            CUDA_TRY(c, ensure(c->psi, SB * P128 * K * sizeof(float2), false, s));
+            CUDA_TRY(c, ensure(c->ybuf, SB * 2 * P64r * nch * K * sizeof(uint16_t), false, s));
+        }
         CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
     }
     CUDA_TRY(c, ensure(c->q32, SB * perQ * sizeof(float2), true, s));
@@ -1335,14 +1359,17 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
 
     // the cube on tcgen05: c_b(rho) as split planes [4][P64][Bpad] once, and
     // work lists of (site in batch, 64-scan tile meeting its crop mask)
-    const bool cube_tc = (cube_out || beam) && tc;
+    const bool cube_tc = (cube_out || beam || probe) && tc;
     const int P64 = round_up(P, 64), D128 = round_up(Dpad, 128);
+    // rows of each plane of C^T: the cube kernel's 64-scan tiles, or the
+    // probe order's 128-row tiles of Psi = C^T S1
+    const int crow = probe ? round_up(P, 128) : P64;
     const size_t KB = (size_t)nch * Bpad;
     std::vector<int> cube_off;
     if (cube_tc) {
-        CUDA_TRY(c, ensure(c->cubeB, (size_t)4 * P64 * Bpad * sizeof(uint16_t), true, s));
-        CUDA_TRY(c, ensure(c->cubeA, (size_t)SB * 4 * D128 * KB * sizeof(uint16_t), true, s));
-        SplitArgs sc{(const float2*)c->illum.p, 1, P, 0, P, Bpad, 1, (uint16_t*)c->cubeB.p, 0, P64, Bpad, 0, 0};
+        CUDA_TRY(c, ensure(c->cubeB, (size_t)4 * crow * Bpad * sizeof(uint16_t), true, s));
+        if (!probe) CUDA_TRY(c, ensure(c->cubeA, (size_t)SB * 4 * D128 * KB * sizeof(uint16_t), true, s));
+        SplitArgs sc{(const float2*)c->illum.p, 1, P, 0, P, Bpad, 1, (uint16_t*)c->cubeB.p, 0, crow, Bpad, 0, 0};
         CUDA_TRY(c, bip_split_planes(sc, s));
         std::vector<double> bb64;
         for (int t = 0; t < P64 / 64; ++t) {
@@ -1395,6 +1422,77 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             g2.site_stride = (int64_t)perA;
             g1.out_c64 = (float2*)c->opB32.p;
             g1.site_stride = (int64_t)perB;
+        }
+        if (probe) {
+            bip_status st = recon_tc_batch(c, ids, nb, H, c->opA16.p, c->s1t.p, s, true);
+            if (st != BIP_OK) return st;
+            // Psi[rho][r] = sum_b c_b(rho) S1_b(r): A = C^T (scans; split BF16,
+            // so that c enters exact to FP32), B = S1 transposed (BF16, zero lo
+            // planes), complex64 out
+            const int P128 = crow;
+            TcArgs G1{};
+            G1.epi = TC_EPI_C32;
+            G1.N = std::min(256, K);
+            G1.npl = 4;
+            G1.A = TcOperand{c->cubeB.p, (int64_t)4 * crow, Bpad, 0, (int64_t)crow};
+            G1.B = TcOperand{c->s1t.p, (int64_t)SB * 4 * K, Bpad, (int64_t)4 * K, (int64_t)K};
+            G1.kb = Bpad / 32;
+            G1.n_sites = nb;
+            G1.mt_per = P128 / 128;
+            G1.nt_per = (K + G1.N - 1) / G1.N;
+            G1.n_cols = K;
+            G1.out32 = (float2*)c->psi.p;
+            G1.out32_site = (int64_t)P128 * K;
+            G1.out32_ld = K;
+            G1.err = (int*)c->errflag.p;
+            TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(G1, s));
+            // Y^(n) = H_n x Psi, then a^(n)_d(rho) = sum_r S2_d(r) Y^(n)(rho, r)
+            // and the |.|^2 sums over d and n into the sites' maps
+            ProbeYArgs y{};
+            y.n_sites = nb;
+            y.rows = P64;
+            y.K = K;
+            y.nch = nch;
+            y.site_ids = ids;
+            y.sites = (const SiteDev*)c->sites_d.p;
+            y.psi = (const float2*)c->psi.p;
+            y.psi_rows = P128;
+            y.H = (const float2*)H;
+            y.Y = (uint16_t*)c->ybuf.p;
+            y.y_rows = P64;
+            TIMED(c, BIP_STAGE_QUADFORM, s, bip_probe_y(y, s));
+            CubeTcArgs ct{};
+            ct.n_work = cube_off[bi + 1] - cube_off[bi];
+            ct.work = (const int32_t*)c->cube_work.p + 2 * (size_t)cube_off[bi];
+            ct.mask = (unsigned long long*)c->cube_mask.p + cube_off[bi];
+            ct.n_sites = nb;
+            ct.n_tiles = P64 / 64;
+            ct.mt_per = D128 / 128;
+            ct.kb_ch = K / 32;
+            ct.a_site_rows = 2 * (int64_t)Dpad;
+            ct.a_plane_rows = Dpad;
+            ct.b_site_rows = 2 * (int64_t)P64;
+            ct.b_plane_rows = P64;
+            ct.swap_ch = 1;
+            ct.hi_only = 1;
+            ct.n_det = geo.n_det;
+            ct.P = P;
+            ct.scans = (const double*)c->scans_d.p;
+            ct.sites = (const SiteDev*)c->sites_d.p;
+            ct.site_ids = ids;
+            ct.ny = g.ny; ct.nx = g.nx; ct.fy = g.fy; ct.fx = g.fx;
+            ct.scale = (float)(g.fy * g.fx);
+            ct.partial = partial;
+            ct.err = (int*)c->errflag.p;
+            // A: the S2 windows (opA16 holds four planes' room: 4 SB Dpad rows of K)
+            for (int ch0 = 0; ch0 < nch; ch0 += 4) {
+                ct.ch0 = ch0;
+                ct.nacc = std::min(4, nch - ch0);
+                TIMED(c, BIP_STAGE_QUADFORM, s,
+                      bip_cube_tc(ct, c->opA16.p, (int64_t)SB * 4 * Dpad, K, c->ybuf.p, (int64_t)SB * 2 * P64,
+                                  nch * K, s));
+            }
+            continue;
         }
         if (f8) {
             bip_status st = recon_tc_batch(c, ids, nb, H, c->op8A.p, c->op8B.p, s);
@@ -1479,7 +1577,8 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
                     ct.ch0 = ch0;
                     ct.nacc = std::min(4, nch - ch0);
                     TIMED(c, BIP_STAGE_QUADFORM, s,
-                          bip_cube_tc(ct, c->cubeA.p, (int64_t)nb * 4 * D128, (int)KB, c->cubeB.p, (int64_t)4 * P64, s));
+                          bip_cube_tc(ct, c->cubeA.p, (int64_t)nb * 4 * D128, (int)KB, c->cubeB.p, (int64_t)4 * P64, Bpad,
+                                      s));
                 }
                 continue;
             }
@@ -1558,7 +1657,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_bin(d, s));
         if (!raster.ok && d.n_work > 0) TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_eval(d, s));
     }
-    if (raster.ok && c->n_sites > 0 && !cube_out && !beam) {
+    if (raster.ok && c->n_sites > 0 && !cube_out && !beam && !probe) {
         // the scan polynomial of every site at once (sites in order)
         DiffArgs d{};
         d.n_sites = c->n_sites;
@@ -1685,7 +1784,9 @@ bip_status bip_set_raster_eval(bip_ctx* c, int32_t on) {
 
 bip_status bip_set_order(bip_ctx* c, int32_t order) {
     if (!c) return BIP_ERR_INVALID_ARG;
-    if (order != 0 && order != 1) return fail(c, BIP_ERR_INVALID_ARG, "order must be 0 (Gram) or 1 (beam)");
+    if (order < 0 || order > 2) return fail(c, BIP_ERR_INVALID_ARG, "order must be 0 (Gram), 1 (beam) or 2 (probe)");
+    if (order == 2 && c->prec != BIP_PREC_MIXED)
+        return fail(c, BIP_ERR_UNSUPPORTED, "the probe order runs in the mixed precision only");
     c->order = order;
     return BIP_OK;
 }
@@ -1754,12 +1855,14 @@ bip_status bip_autotune(bip_ctx* c, const void* H, const double* scan_px, int32_
             }
         }
     }
-    // the scan contraction's order: the Gram matrix, or |M c|^2 per beam
+    // the scan contraction's order: the Gram matrix, |M c|^2 per beam, or
+    // the windowed probes (mixed precision, up to kProbeMaxScans scans)
     const int order0 = c->order;
     int best_order = order0;
     if (st == BIP_OK && tc) {
-        for (int o : {0, 1}) {
-            if (o == order0) continue;
+        const bool probe_ok = c->prec == BIP_PREC_MIXED && c->recon_tc && P <= kProbeMaxScans;
+        for (int o : {0, 1, 2}) {
+            if (o == order0 || (o == 2 && !probe_ok)) continue;
             c->order = o;
             st = time_map(best_sb, best_cw, &t);
             if (st != BIP_OK) break;

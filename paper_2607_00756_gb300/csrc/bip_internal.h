@@ -159,6 +159,10 @@ struct ReconSide {
     int x_site0;                    // as in XprepSide
     int64_t site_stride;            // output elements per site
     int64_t plane_stride;           // output elements per plane (re, im)
+    // transposed output (BF16, nch = 0): element (t, px) at px ld + t, so
+    // that the targets are the contiguous index (the probe order's S1)
+    int trans;
+    int64_t ld;
 };
 struct ReconArgs {
     int n_sites;
@@ -368,10 +372,32 @@ struct CubeTcArgs {
     float* cube;                    // [P][n_det], added to (atomically); or
     float* partial;                 // map mode: [n_sites_total][P] per-site map, the
                                     // detector sum taken in the epilogue (atomically)
+    // probe order: B rows per site (0: one B for every site), the channel in
+    // B's columns instead of A's (A = S2 windows, B = H_n x windowed probes),
+    // and operands of two BF16 planes (re, im) instead of four (split BF16)
+    int64_t b_site_rows;
+    int swap_ch;
+    int hi_only;
     int* err;
 };
+// a_k, b_k: row lengths of A and B (bf16 elements)
 cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int a_k, const void* B, int64_t b_rows,
-                        cudaStream_t s);
+                        int b_k, cudaStream_t s);
+
+// probe.cu : the probe order of the scan contraction.  Y[site][plane][rho][n K
+// + r] = H_n(r) Psi(rho, r) as BF16 planes (re, im), from the windowed probes
+// Psi = C^T S1 (complex64 [site][rho][K]); channels a site lacks are zero
+struct ProbeYArgs {
+    int n_sites, rows, K, nch;      // rows: scans per site (Psi and Y)
+    const int32_t* site_ids;
+    const SiteDev* sites;
+    const float2* psi;              // [n_sites][psi_rows][K]
+    int64_t psi_rows;
+    const float2* H;                // [sum nch][K]
+    uint16_t* Y;                    // [n_sites][2][y_rows][nch K]
+    int64_t y_rows;
+};
+cudaError_t bip_probe_y(const ProbeYArgs& a, cudaStream_t s);
 // qEELS: out[rho][bin_of[d]] = sum of cube[rho][d] over the beams of a bin
 cudaError_t bip_qeels_bin(const float* cube, int P, int n_det, const int32_t* bin_of, int n_bins, float* out,
                           cudaStream_t s);

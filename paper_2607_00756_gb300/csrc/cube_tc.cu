@@ -5,7 +5,9 @@
 // summed over d into the site's map (the "beam order" of the scan
 // contraction: |M c|^2 directly, without the Gram matrix).  Split BF16 (hi + lo, three
 // products per real product, twelve per complex one), FP32 accumulation in
-// TMEM.
+// TMEM.  The "probe order" runs the same kernel on other operands:
+// a_d(rho) = sum_r S2_d(r) Y^(n)(rho, r) with Y^(n) = H_n x the windowed
+// probes, the channel then in B's columns, BF16 planes (four products).
 //
 // Work unit: (site in batch, tile of 64 scans that meets the site's crop
 // mask, tile of 128 detector beams).  K runs over (channel, aperture beam);
@@ -30,6 +32,8 @@ constexpr int kBTile = kN * 64;
 constexpr int kStage = 4 * kATile + 4 * kBTile;   // hi/lo re/im planes
 constexpr int kStages = 4;
 constexpr size_t kSmem = 1024 + (size_t)kStages * kStage + 256;
+// planes as loaded into a stage: split BF16 0 re_hi, 1 re_lo, 2 im_hi, 3
+// im_lo; BF16 (hi_only) re -> slot 0, im -> slot 2
 
 __device__ __forceinline__ bool unit_of(const CubeTcArgs& a, int idx, int& w, int& mt) {
     if (idx >= a.n_work * a.mt_per) return false;
@@ -91,7 +95,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int i = 0; ok && unit_of(a, blockIdx.x + i * gridDim.x, w, mt); ++i) {
                 const int bs = a.work[2 * w], t = a.work[2 * w + 1];
                 const int64_t a0 = (int64_t)bs * a.a_site_rows + (int64_t)mt * 128;
-                const int64_t b0 = (int64_t)t * kN;
+                const int64_t b0 = (int64_t)bs * a.b_site_rows + (int64_t)t * kN;
                 for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
                         fail();
@@ -99,14 +103,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     uint8_t* st = smem + s * kStage;
-                    mbar_expect_tx(&full[s], kStage);
-                    const int kx = (kb % a.kb_ch) * 32;           // the aperture beam block
+                    // K block within the channel (the operand without channels)
+                    // and across channels (the one that has them)
+                    const int kx = (kb % a.kb_ch) * 32, kc = kb * 32;
+                    const int ax = a.swap_ch ? kx : kc, bx = a.swap_ch ? kc : kx;
+                    if (a.hi_only) {
+                        mbar_expect_tx(&full[s], 2 * kATile + 2 * kBTile);
 #pragma unroll
-                    for (int pl = 0; pl < 4; ++pl)
-                        tma_2d(st + pl * kATile, &mapA, kb * 32, (int)(a0 + pl * a.a_plane_rows), &full[s]);
+                        for (int pl = 0; pl < 2; ++pl) {
+                            tma_2d(st + 2 * pl * kATile, &mapA, ax, (int)(a0 + pl * a.a_plane_rows), &full[s]);
+                            tma_2d(st + 4 * kATile + 2 * pl * kBTile, &mapB, bx, (int)(b0 + pl * a.b_plane_rows),
+                                   &full[s]);
+                        }
+                    } else {
+                        mbar_expect_tx(&full[s], kStage);
 #pragma unroll
-                    for (int pl = 0; pl < 4; ++pl)
-                        tma_2d(st + 4 * kATile + pl * kBTile, &mapB, kx, (int)(b0 + pl * a.b_plane_rows), &full[s]);
+                        for (int pl = 0; pl < 4; ++pl)
+                            tma_2d(st + pl * kATile, &mapA, ax, (int)(a0 + pl * a.a_plane_rows), &full[s]);
+#pragma unroll
+                        for (int pl = 0; pl < 4; ++pl)
+                            tma_2d(st + 4 * kATile + pl * kBTile, &mapB, bx, (int)(b0 + pl * a.b_plane_rows), &full[s]);
+                    }
                     ++issued;
                     if (++s == kStages) {
                         s = 0;
@@ -157,6 +174,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                             bd[pl] = sdesc(base + 4 * kATile + pl * kBTile + kk * 32);
                         }
                         const uint32_t first = (kb % a.kb_ch == 0 && kk == 0) ? 0u : 1u;
+                        if (a.hi_only) {
+                            mma(dr, ad[0], bd[0], id_pos, first);
+                            mma(dr, ad[2], bd[2], id_neg, 1);
+                            mma(di, ad[0], bd[2], id_pos, first);
+                            mma(di, ad[2], bd[0], id_pos, 1);
+                            continue;
+                        }
                         // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
                         mma(dr, ad[0], bd[0], id_pos, first);
                         mma(dr, ad[0], bd[1], id_pos, 1);
@@ -278,19 +302,25 @@ __global__ void crop_mask_kernel(CubeTcArgs a) {
 }  // namespace
 
 cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int a_k, const void* B, int64_t b_rows,
-                        cudaStream_t s) {
+                        int b_k, cudaStream_t s) {
     if (a.n_work < 1) return cudaSuccess;
-    if (a.nacc < 1 || a.nacc > 4 || a.kb_ch < 1 || a.mt_per < 1 || a.ch0 < 0 || a_k % 32)
+    if (a.nacc < 1 || a.nacc > 4 || a.kb_ch < 1 || a.mt_per < 1 || a.ch0 < 0 || a_k % 32 || b_k % 32)
         return cudaErrorInvalidValue;
-    if ((a.ch0 + a.nacc) * a.kb_ch * 32 > a_k) return cudaErrorInvalidValue;
-    // every tile inside its operand: A rows of the last site, B rows of the last scan tile
-    if ((int64_t)(a.n_sites - 1) * a.a_site_rows + 3 * a.a_plane_rows + (int64_t)a.mt_per * 128 > a_rows)
+    // the channel range inside the operand that has channels, one channel's
+    // K blocks inside the other
+    const int ch_k = a.swap_ch ? b_k : a_k, one_k = a.swap_ch ? a_k : b_k;
+    if ((a.ch0 + a.nacc) * a.kb_ch * 32 > ch_k || a.kb_ch * 32 > one_k) return cudaErrorInvalidValue;
+    // every tile inside its operand: A rows of the last site, B rows of the
+    // last site's last scan tile
+    const int64_t pl = a.hi_only ? 1 : 3;
+    if ((int64_t)(a.n_sites - 1) * a.a_site_rows + pl * a.a_plane_rows + (int64_t)a.mt_per * 128 > a_rows)
         return cudaErrorInvalidValue;
-    if (3 * a.b_plane_rows + (int64_t)a.n_tiles * kN > b_rows) return cudaErrorInvalidValue;
+    if ((int64_t)(a.n_sites - 1) * a.b_site_rows + pl * a.b_plane_rows + (int64_t)a.n_tiles * kN > b_rows)
+        return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     cudaError_t e = make_map_2d(&ma, A, a_rows, a_k, 128);
     if (e != cudaSuccess) return e;
-    e = make_map_2d(&mb, B, b_rows, a.kb_ch * 32, kN);
+    e = make_map_2d(&mb, B, b_rows, b_k, kN);
     if (e != cudaSuccess) return e;
     // the crop masks of the work items (4 items per 256-thread block)
     crop_mask_kernel<<<(a.n_work + 3) / 4, 256, 0, s>>>(a);

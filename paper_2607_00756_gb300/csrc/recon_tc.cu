@@ -26,7 +26,9 @@
 //                (staged per tile in shared memory) products, 16 bf16
 //                stored per thread as one 32-byte sector -- or, for the FP8
 //                coupling, 16 E4M3 bytes, the row scale folded into the
-//                magnitude factor (H_n comes pre-divided by its maximum)
+//                magnitude factor (H_n comes pre-divided by its maximum);
+//                a side may instead be written transposed (pixels x targets,
+//                no H_n), the probe order's operand
 // Work unit: (side, site in batch, 128-target tile, chunk of up to 1024
 // pixels).  Every wait is bounded; on a timeout the kernel sets *err, stops,
 // drains the copies and MMAs it issued and frees TMEM.
@@ -411,6 +413,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                             st_v4(o + sd.plane_stride, im);
                             o += ch_stride;
                         }
+                    } else if (sd.trans) {
+                        // targets contiguous: element (t, px + j) at (px + j) ld + t,
+                        // so each store of the warp's 32 targets is one 64-byte run
+                        uint16_t* o = a.out[u.side] + (size_t)u.bs * sd.site_stride + (size_t)px * sd.ld + t;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const uint32_t v = pack2(S[j].x, S[j].y);
+                            o[(size_t)j * sd.ld] = (uint16_t)(v & 0xffffu);
+                            o[sd.plane_stride + (size_t)j * sd.ld] = (uint16_t)(v >> 16);
+                        }
                     } else {
                         uint16_t* o = a.out[u.side] + out_off + px;
                         for (int n = 0; n < nrep; ++n) {
@@ -540,6 +552,9 @@ cudaError_t bip_recon_tc(const ReconArgs& a, cudaStream_t s) {
         if (sd.mt_tiles * 128 != sd.w_pad || sd.n_targets > sd.rows_pad || sd.n_targets > sd.w_pad || sd.nch > 9)
             return cudaErrorInvalidValue;
         if (sd.nch > 0 && ((uintptr_t)a.H & 15)) return cudaErrorMisalignedAddress;
+        if (sd.trans && (sd.nch != 0 || a.f8 || sd.ld < sd.n_targets || sd.plane_stride < (int64_t)a.K * sd.ld ||
+                         sd.site_stride < 2 * sd.plane_stride))
+            return cudaErrorInvalidValue;
         if (sd.w_row0 + 2 * sd.w_pad > a.w_rows) return cudaErrorInvalidValue;
         if ((int64_t)(sd.x_site0 + 3 * a.n_sites) * a.K > a.x_rows) return cudaErrorInvalidValue;
     }

@@ -158,7 +158,15 @@ def test_model_and_launch_controls_host(capi):
         assert lib.bip_coreloss_grad(ctx, None, dummy, sp, 4, dummy, dummy, None, None, None, None) == 1
         assert "bip_build_s1" in capi.bip_last_error(ctx)
         assert lib.bip_autotune(ctx, dummy, sp, 4, dummy, None, None, None, None, None) == 1
-        assert lib.bip_set_order(ctx, 2) == 1 and lib.bip_set_order(ctx, 1) == 0 and lib.bip_set_order(ctx, 0) == 0
+        assert lib.bip_set_order(ctx, 3) == 1 and lib.bip_set_order(ctx, -1) == 1
+        assert lib.bip_set_order(ctx, 1) == 0 and lib.bip_set_order(ctx, 0) == 0
+        # the probe order: mixed precision only
+        assert lib.bip_set_order(ctx, 2) == (0 if synth.config1().prec == "mixed" else 6)
+        mixed = capi.bip_create(capi.make_config(synth.config1(), prec="mixed"))
+        try:
+            assert lib.bip_set_order(mixed, 2) == 0 and lib.bip_set_order(mixed, 0) == 0
+        finally:
+            capi.bip_destroy(mixed)
     finally:
         capi.bip_destroy(ctx)
     assert capi.lib().bip_set_launch(None, 0, 0) == 1

@@ -82,10 +82,10 @@ def test_autotune_keeps_the_map(lib, prec):
     m0 = ctx.map(H, sp.scans).cpu().numpy()
     sb, cw, order, ms = ctx.autotune(H, sp.scans)
     assert 1 <= sb <= 32 and (cw == 0 or (cw % 16 == 0 and cw <= 256)) and ms > 0.0
-    assert order in (0, 1) and (prec != "fp32" or order == 0)
+    assert order in (0, 1, 2) and (prec != "fp32" or order == 0) and (prec == "mixed" or order != 2)
     m1 = ctx.map(H, sp.scans).cpu().numpy()
-    # the Gram route repeats the map exactly; the beam order (split BF16,
-    # another summation) within the mixed path's bar
+    # the Gram route repeats the map exactly; the beam and probe orders
+    # (another summation) within the mixed path's bar
     assert rel(m1, m0) < (1e-6 if order == 0 else 1e-3)
     ctx.set_order(0)
     # any explicit choice gives the same map too
@@ -95,35 +95,86 @@ def test_autotune_keeps_the_map(lib, prec):
 
 
 
-@pytest.mark.parametrize("which", ["config1", "edge", "aniso"])
-@pytest.mark.parametrize("prec", ["mixed", "split_bf16"])
-def test_beam_order_map(lib, which, prec):
-    """The map in beam order (|M c|^2 per detector beam on tcgen05, the
-    detector sum in the epilogue) against the oracle and the Gram route."""
-    if which == "config1":
-        cfg = synth.config1()
-    elif which == "aniso":
+def _order_case(which):
+    """Workloads of the contraction-order tests: config 1; the edge-case
+    specimen (every plane, wrapping windows, 21 sites with one or three
+    channels, a ragged scan line); an anisotropic grid; config 1 with six
+    channels per site (two passes of the cube kernel's four accumulators)."""
+    if which == "edge":
+        from test_gpu_map import _edge_specimen
+        return _edge_specimen()
+    if which == "aniso":
         cfg = synth.config1().replace(name="aniso", ny=64, nx=128, ly=7.5, lx=10.0, cells_y=3, cells_x=4, fy=1,
                                       fx=2, win=32, ion_cells=(1, 3), ion_slices=(1, 4),
                                       scan_y=(10.3, 3.5, 9), scan_x=(20.7, 6.25, 7))
-    else:
-        from test_gpu_map import _edge_specimen
-        cfg, sp = _edge_specimen()
-    if which != "edge":
-        sp = synth.make_specimen(cfg)
+        return cfg, synth.make_specimen(cfg)
+    cfg = synth.config1()
+    sp = synth.make_specimen(cfg)
+    if which == "six_channels":
+        keep = np.nonzero(sp.nch > 0)[0]
+        h3 = sp.H.reshape(len(keep), 3, cfg.win, cfg.win)
+        h6 = np.concatenate([h3, 0.5j * h3[:, ::-1]], axis=1).reshape(-1, cfg.win, cfg.win)
+        nch = sp.nch.copy()
+        nch[keep] = 6
+        sp = synth.Specimen(cfg=cfg, atoms=sp.atoms, nch=nch, V=sp.V, H=h6, scans=sp.scans)
+    return cfg, sp
+
+
+def _order_check(lib, which, prec, order):
+    cfg, sp = _order_case(which)
     ref = obip.bip_map(obip.make_problem(sp))
     dev = torch.device("cuda:0")
     ctx = lib(cfg, prec=prec)
     ctx.build(torch.tensor(sp.V, dtype=torch.float32, device=dev), sp.atoms, sp.nch)
     H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
     m_gram = ctx.map(H, sp.scans).cpu().numpy()
-    ctx.set_order(1)
-    m_beam = ctx.map(H, sp.scans).cpu().numpy()
+    ctx.set_order(order)
+    m = ctx.map(H, sp.scans).cpu().numpy()
     parts = ctx.sites(H, sp.scans).cpu().numpy()
-    assert rel(m_beam, ref.map) < 1e-3
+    assert rel(m, ref.map) < 1e-3
     assert rel(parts, ref.partials) < 1e-3
-    assert rel(m_beam, m_gram) < 1e-3
+    assert rel(m, m_gram) < 1e-3
     pr = obip.make_problem(sp)
     for k in range(len(pr.ion)):
         assert np.all(parts[k][~obip.crop_mask(pr, k, sp.scans)] == 0.0)
+    ctx.close()
+
+
+@pytest.mark.parametrize("which", ["config1", "edge", "aniso"])
+@pytest.mark.parametrize("prec", ["mixed", "split_bf16"])
+def test_beam_order_map(lib, which, prec):
+    """The map in beam order (|M c|^2 per detector beam on tcgen05, the
+    detector sum in the epilogue) against the oracle and the Gram route."""
+    _order_check(lib, which, prec, 1)
+
+
+@pytest.mark.parametrize("which", ["config1", "edge", "aniso", "six_channels"])
+def test_probe_order_map(lib, which):
+    """The map in probe order (the windowed probes Psi = C^T S1 of every
+    scan, then |S2^T (H_n x Psi)|^2 summed over d and n on tcgen05) against
+    the oracle and the Gram route, mixed precision."""
+    _order_check(lib, which, "mixed", 2)
+
+
+def test_probe_order_limits(lib):
+    """The probe order is refused outside its domain, before any launch:
+    other precisions at set time, more than 2048 scans at map time."""
+    from paper_2607_00756_gb300.capi import BipError
+    cfg = synth.config1()
+    sp = synth.make_specimen(cfg)
+    dev = torch.device("cuda:0")
+    ctx = lib(cfg, prec="split_bf16")
+    with pytest.raises(BipError):
+        ctx.set_order(2)
+    ctx.close()
+    ctx = lib(cfg, prec="mixed")
+    ctx.build(torch.tensor(sp.V, dtype=torch.float32, device=dev), sp.atoms, sp.nch)
+    H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+    ctx.set_order(2)
+    scans = np.tile(sp.scans, (2049 // len(sp.scans) + 1, 1))[:2049]
+    with pytest.raises(BipError):
+        ctx.map(H, scans)
+    ctx.set_order(0)
+    m = ctx.map(H, scans).cpu().numpy()
+    assert np.all(np.isfinite(m))
     ctx.close()
