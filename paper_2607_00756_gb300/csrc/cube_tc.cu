@@ -42,6 +42,9 @@ __device__ __forceinline__ bool unit_of(const CubeTcArgs& a, int idx, int& w, in
     return true;
 }
 
+// HI: BF16 operands of two planes (four MMAs per K step) -- a template
+// parameter, so that the split-BF16 issue loop carries no branch
+template <bool HI>
 __global__ void __launch_bounds__(kThreads, 1)
     cube_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const CubeTcArgs a) {
@@ -107,7 +110,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // and across channels (the one that has them)
                     const int kx = (kb % a.kb_ch) * 32, kc = kb * 32;
                     const int ax = a.swap_ch ? kx : kc, bx = a.swap_ch ? kc : kx;
-                    if (a.hi_only) {
+                    if constexpr (HI) {
                         mbar_expect_tx(&full[s], 2 * kATile + 2 * kBTile);
 #pragma unroll
                         for (int pl = 0; pl < 2; ++pl) {
@@ -174,26 +177,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                             bd[pl] = sdesc(base + 4 * kATile + pl * kBTile + kk * 32);
                         }
                         const uint32_t first = (kb % a.kb_ch == 0 && kk == 0) ? 0u : 1u;
-                        if (a.hi_only) {
+                        if constexpr (HI) {
                             mma(dr, ad[0], bd[0], id_pos, first);
                             mma(dr, ad[2], bd[2], id_neg, 1);
                             mma(di, ad[0], bd[2], id_pos, first);
                             mma(di, ad[2], bd[0], id_pos, 1);
-                            continue;
+                        } else {
+                            // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
+                            mma(dr, ad[0], bd[0], id_pos, first);
+                            mma(dr, ad[0], bd[1], id_pos, 1);
+                            mma(dr, ad[1], bd[0], id_pos, 1);
+                            mma(dr, ad[2], bd[2], id_neg, 1);
+                            mma(dr, ad[2], bd[3], id_neg, 1);
+                            mma(dr, ad[3], bd[2], id_neg, 1);
+                            mma(di, ad[0], bd[2], id_pos, first);
+                            mma(di, ad[0], bd[3], id_pos, 1);
+                            mma(di, ad[1], bd[2], id_pos, 1);
+                            mma(di, ad[2], bd[0], id_pos, 1);
+                            mma(di, ad[2], bd[1], id_pos, 1);
+                            mma(di, ad[3], bd[0], id_pos, 1);
                         }
-                        // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
-                        mma(dr, ad[0], bd[0], id_pos, first);
-                        mma(dr, ad[0], bd[1], id_pos, 1);
-                        mma(dr, ad[1], bd[0], id_pos, 1);
-                        mma(dr, ad[2], bd[2], id_neg, 1);
-                        mma(dr, ad[2], bd[3], id_neg, 1);
-                        mma(dr, ad[3], bd[2], id_neg, 1);
-                        mma(di, ad[0], bd[2], id_pos, first);
-                        mma(di, ad[0], bd[3], id_pos, 1);
-                        mma(di, ad[1], bd[2], id_pos, 1);
-                        mma(di, ad[2], bd[0], id_pos, 1);
-                        mma(di, ad[2], bd[1], id_pos, 1);
-                        mma(di, ad[3], bd[0], id_pos, 1);
                     }
                     any = true;
                     mma_commit(&empty[s]);
@@ -326,14 +329,19 @@ cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int 
     crop_mask_kernel<<<(a.n_work + 3) / 4, 256, 0, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    static bool attr = false;
-    if (!attr) {
-        e = cudaFuncSetAttribute(cube_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    static bool attr[2] = {false, false};
+    const int hi = a.hi_only ? 1 : 0;
+    if (!attr[hi]) {
+        e = hi ? cudaFuncSetAttribute(cube_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem)
+               : cudaFuncSetAttribute(cube_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[hi] = true;
     }
     const int units = a.n_work * a.mt_per;
     const int grid = units < num_sms() ? units : num_sms();
-    cube_tc_kernel<<<grid, kThreads, kSmem, s>>>(ma, mb, a);
+    if (hi)
+        cube_tc_kernel<true><<<grid, kThreads, kSmem, s>>>(ma, mb, a);
+    else
+        cube_tc_kernel<false><<<grid, kThreads, kSmem, s>>>(ma, mb, a);
     return cudaGetLastError();
 }
