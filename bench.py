@@ -34,9 +34,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "atom×probe core-loss evals/s, mixed vs FP32 path on GB300, at ≤1e-3 rel L2"
-DTYPES = {"mixed": "bf16 coupling+Gram, bf16x3 (hi+lo) quadratic form / f32 accumulate",
+DTYPES = {"mixed": "fp16 reconstruction, bf16 coupling+Gram, f32 quadratic form / f32 accumulate",
           "split_bf16": "bf16x3 (hi+lo) / f32 accumulate", "fp32": "f32",
-          "fp8": "e4m3 coupling (per-window scales), bf16 Gram, bf16x3 quadratic form / f32 accumulate"}
+          "fp8": "fp16 reconstruction, e4m3 coupling (per-window scales), bf16 Gram, f32 quadratic form / "
+                 "f32 accumulate"}
 UNIT = "atom×probe evals/s"
 
 
@@ -486,6 +487,7 @@ def run_orders(cfg, sp, prec="mixed", reps=2):
     one S1 + S2 build (CUDA events, one warm-up map), the autotuner's pick,
     and each order's distance to the Gram route's map."""
     import torch
+    from paper_2607_00756_gb300 import capi
     from paper_2607_00756_gb300.context import BipContext
     dev = torch.device("cuda:0")
     ctx = BipContext(cfg, prec=prec)
@@ -513,6 +515,13 @@ def run_orders(cfg, sp, prec="mixed", reps=2):
             torch.cuda.synchronize()
             row[f"{name}_ms"] = e0.elapsed_time(e1) / reps
             maps[name] = m.cpu().numpy()
+            # one more map with every launch bracketed by events
+            capi.bip_set_profiling(ctx.ctx, True)
+            ctx.map(H, sc)
+            torch.cuda.synchronize()
+            prof = capi.bip_get_profile(ctx.ctx)
+            capi.bip_set_profiling(ctx.ctx, 0)
+            row[f"{name}_stage_ms"] = {k: round(v[0], 2) for k, v in prof.items() if v[1] > 0}
         ref = maps["gram"]
         for name in ("beam", "probe"):
             row[f"{name}_vs_gram_rel_l2"] = float(np.linalg.norm(maps[name] - ref) / np.linalg.norm(ref))

@@ -8,6 +8,8 @@
 #include <numeric>
 #include <string>
 
+#include <cuda_fp16.h>
+
 #include "bip_internal.h"
 
 namespace {
@@ -187,20 +189,6 @@ int signed_bin(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// float -> bfloat16 bits, round to nearest even (finite inputs), and back
-uint16_t bf16_bits(float x) {
-    uint32_t u;
-    std::memcpy(&u, &x, 4);
-    u += 0x7fffu + ((u >> 16) & 1u);
-    return (uint16_t)(u >> 16);
-}
-float bf16_value(uint16_t h) {
-    const uint32_t u = (uint32_t)h << 16;
-    float x;
-    std::memcpy(&x, &u, 4);
-    return x;
-}
-
 // Twiddles of the register FFT of length n (n a power of two, 64..1024),
 // pass by pass: pass p = 1 .. npass-1 combines sub-transforms of length
 // Ns = 8^p with radix R (8, or 4 / 2 for the last pass), and its entry
@@ -348,7 +336,7 @@ bip_status make_tables(bip_ctx* c, cudaStream_t s) {
     CUDA_TRY(c, upload(c->grp2_w, w2, s));
     CUDA_TRY(c, upload(c->ytab, yt, s));
     CUDA_TRY(c, upload(c->xtab, xt, s));
-    // NNW weights as dense hi + lo bf16 rows [side][plane][rows_pad][64 parents]
+    // NNW weights as dense hi + lo FP16 rows [side][plane][rows_pad][64 parents]
     // for the tensor-core reconstruction (side 0: detector beams, 1: aperture)
     c->recon_tc = geo.Bp1 <= 64 && geo.Bp2 <= 64;
     if (c->recon_tc) {
@@ -358,9 +346,10 @@ bip_status make_tables(bip_ctx* c, cudaStream_t s) {
             for (int t = 0; t < n; ++t)
                 for (int p = 0; p < bp; ++p) {
                     const float x = (float)w[(size_t)t * bp + p];
-                    const uint16_t hi = bf16_bits(x);
-                    wt[(size_t)(row0 + t) * 64 + p] = hi;
-                    wt[(size_t)(row0 + rows_pad + t) * 64 + p] = bf16_bits(x - bf16_value(hi));
+                    const __half hi = __float2half_rn(x);
+                    const __half lo = __float2half_rn(x - __half2float(hi));
+                    wt[(size_t)(row0 + t) * 64 + p] = __half_as_ushort(hi);
+                    wt[(size_t)(row0 + rows_pad + t) * 64 + p] = __half_as_ushort(lo);
                 }
         };
         fill(geo.w2, geo.n_det, geo.Bp2, 0, Dw);
@@ -1316,8 +1305,10 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         if (probe) {
             const size_t P128 = round_up(P, 128), P64r = round_up(P, 64);
             CUDA_TRY(c, ensure(c->s1t, SB * 4 * (size_t)K * Bpad * sizeof(uint16_t), true, s));
-            CUDA_TRY(c, ensure(c->psi, SB * P128 * K * sizeof(float2), false, s));
-            CUDA_TRY(c, ensure(c->ybuf, SB * 2 * P64r * nch * K * sizeof(uint16_t), false, s));
+            // zeroed when allocated: rows of scans beyond the last 16-scan tile
+            // are never written and reach only masked columns of the cube kernel
+            CUDA_TRY(c, ensure(c->psi, SB * P128 * K * sizeof(float2), true, s));
+            CUDA_TRY(c, ensure(c->ybuf, SB * 2 * P64r * nch * K * sizeof(uint16_t), true, s));
         }
         CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
     }
@@ -1360,6 +1351,10 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     // the cube on tcgen05: c_b(rho) as split planes [4][P64][Bpad] once, and
     // work lists of (site in batch, 64-scan tile meeting its crop mask)
     const bool cube_tc = (cube_out || beam || probe) && tc;
+    // the probe order's last contraction: the channels in the tile's columns
+    // ((scan, channel) pairs, one accumulator) when that takes fewer 64-wide
+    // tiles than a 64-scan tile with one accumulator per channel (few scans)
+    const bool probe_cols = probe && (P * nch + 63) / 64 < nch * ((P + 63) / 64);
     const int P64 = round_up(P, 64), D128 = round_up(Dpad, 128);
     // rows of each plane of C^T: the cube kernel's 64-scan tiles, or the
     // probe order's 128-row tiles of Psi = C^T S1
@@ -1371,10 +1366,14 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         if (!probe) CUDA_TRY(c, ensure(c->cubeA, (size_t)SB * 4 * D128 * KB * sizeof(uint16_t), true, s));
         SplitArgs sc{(const float2*)c->illum.p, 1, P, 0, P, Bpad, 1, (uint16_t*)c->cubeB.p, 0, crow, Bpad, 0, 0};
         CUDA_TRY(c, bip_split_planes(sc, s));
+        // tiles of 64 scans -- or, for the probe order with fewer columns that
+        // way, of 64 (scan, channel) columns -- and their scans' bounding boxes
+        const int ncol = probe_cols ? nch : 1;
+        const int n_ct = (P * ncol + 63) / 64;
         std::vector<double> bb64;
-        for (int t = 0; t < P64 / 64; ++t) {
+        for (int t = 0; t < n_ct; ++t) {
             double y0 = INFINITY, y1 = -INFINITY, x0 = INFINITY, x1 = -INFINITY;
-            for (int p = t * 64; p < std::min(P, (t + 1) * 64); ++p) {
+            for (int p = t * 64 / ncol; p < std::min(P, ((t + 1) * 64 + ncol - 1) / ncol); ++p) {
                 y0 = std::min(y0, scans[2 * p]);
                 y1 = std::max(y1, scans[2 * p]);
                 x0 = std::min(x0, scans[2 * p + 1]);
@@ -1387,7 +1386,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             cube_off.push_back((int)cw.size() / 2);
             for (int bs = 0; bs < std::min(SB, c->n_sites - b0); ++bs) {
                 const SiteDev& sd = c->sites[b0 + bs];
-                for (int t = 0; t < P64 / 64; ++t)
+                for (int t = 0; t < n_ct; ++t)
                     if (box_meets_crop(bb64[4 * t], bb64[4 * t + 1], bb64[4 * t + 2], bb64[4 * t + 3], sd.ty, sd.tx, g)) {
                         cw.push_back(bs);
                         cw.push_back(t);
@@ -1426,24 +1425,26 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         if (probe) {
             bip_status st = recon_tc_batch(c, ids, nb, H, c->opA16.p, c->s1t.p, s, true);
             if (st != BIP_OK) return st;
-            // Psi[rho][r] = sum_b c_b(rho) S1_b(r): A = C^T (scans; split BF16,
-            // so that c enters exact to FP32), B = S1 transposed (BF16, zero lo
-            // planes), complex64 out
-            const int P128 = crow;
+            // Psi[rho][r] = sum_b c_b(rho) S1_b(r): A = S1 transposed (pixels in
+            // 128-row tiles; BF16, zero lo planes), B = C^T (the scans as the
+            // tile's columns, so that few scans cost few columns; split BF16,
+            // c exact to FP32), written transposed as complex64 Psi[rho][r]
+            const int P128 = crow, P16 = round_up(P, 16);
             TcArgs G1{};
             G1.epi = TC_EPI_C32;
-            G1.N = std::min(256, K);
+            G1.N = std::min(256, P16);
             G1.npl = 4;
-            G1.A = TcOperand{c->cubeB.p, (int64_t)4 * crow, Bpad, 0, (int64_t)crow};
-            G1.B = TcOperand{c->s1t.p, (int64_t)SB * 4 * K, Bpad, (int64_t)4 * K, (int64_t)K};
+            G1.A = TcOperand{c->s1t.p, (int64_t)SB * 4 * K, Bpad, (int64_t)4 * K, (int64_t)K};
+            G1.B = TcOperand{c->cubeB.p, (int64_t)4 * crow, Bpad, 0, (int64_t)crow};
             G1.kb = Bpad / 32;
             G1.n_sites = nb;
-            G1.mt_per = P128 / 128;
-            G1.nt_per = (K + G1.N - 1) / G1.N;
-            G1.n_cols = K;
+            G1.mt_per = K / 128;
+            G1.nt_per = (P16 + G1.N - 1) / G1.N;
+            G1.n_cols = P16;
             G1.out32 = (float2*)c->psi.p;
             G1.out32_site = (int64_t)P128 * K;
             G1.out32_ld = K;
+            G1.out32_trans = 1;
             G1.err = (int*)c->errflag.p;
             TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(G1, s));
             // Y^(n) = H_n x Psi, then a^(n)_d(rho) = sum_r S2_d(r) Y^(n)(rho, r)
@@ -1461,20 +1462,25 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             y.Y = (uint16_t*)c->ybuf.p;
             y.y_rows = P64;
             TIMED(c, BIP_STAGE_QUADFORM, s, bip_probe_y(y, s));
+            // B = Y: rows rho with the channel in the columns (n K + r), one
+            // accumulator per channel -- or, with few scans, seen as rows
+            // (rho, n) of K, every channel of a scan in the tile's columns and
+            // the channel sum taken over columns
             CubeTcArgs ct{};
             ct.n_work = cube_off[bi + 1] - cube_off[bi];
             ct.work = (const int32_t*)c->cube_work.p + 2 * (size_t)cube_off[bi];
             ct.mask = (unsigned long long*)c->cube_mask.p + cube_off[bi];
             ct.n_sites = nb;
-            ct.n_tiles = P64 / 64;
+            ct.n_tiles = probe_cols ? (P * nch + 63) / 64 : P64 / 64;
             ct.mt_per = D128 / 128;
             ct.kb_ch = K / 32;
             ct.a_site_rows = 2 * (int64_t)Dpad;
             ct.a_plane_rows = Dpad;
-            ct.b_site_rows = 2 * (int64_t)P64;
-            ct.b_plane_rows = P64;
+            ct.b_site_rows = 2 * (int64_t)P64 * (probe_cols ? nch : 1);
+            ct.b_plane_rows = (int64_t)P64 * (probe_cols ? nch : 1);
             ct.swap_ch = 1;
             ct.hi_only = 1;
+            ct.col_nch = probe_cols ? nch : 0;
             ct.n_det = geo.n_det;
             ct.P = P;
             ct.scans = (const double*)c->scans_d.p;
@@ -1485,12 +1491,20 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             ct.partial = partial;
             ct.err = (int*)c->errflag.p;
             // A: the S2 windows (opA16 holds four planes' room: 4 SB Dpad rows of K)
-            for (int ch0 = 0; ch0 < nch; ch0 += 4) {
-                ct.ch0 = ch0;
-                ct.nacc = std::min(4, nch - ch0);
+            if (probe_cols) {
+                ct.ch0 = 0;
+                ct.nacc = 1;
                 TIMED(c, BIP_STAGE_QUADFORM, s,
-                      bip_cube_tc(ct, c->opA16.p, (int64_t)SB * 4 * Dpad, K, c->ybuf.p, (int64_t)SB * 2 * P64,
-                                  nch * K, s));
+                      bip_cube_tc(ct, c->opA16.p, (int64_t)SB * 4 * Dpad, K, c->ybuf.p, (int64_t)SB * 2 * P64 * nch,
+                                  K, s));
+            } else {
+                for (int ch0 = 0; ch0 < nch; ch0 += 4) {
+                    ct.ch0 = ch0;
+                    ct.nacc = std::min(4, nch - ch0);
+                    TIMED(c, BIP_STAGE_QUADFORM, s,
+                          bip_cube_tc(ct, c->opA16.p, (int64_t)SB * 4 * Dpad, K, c->ybuf.p, (int64_t)SB * 2 * P64,
+                                      nch * K, s));
+                }
             }
             continue;
         }

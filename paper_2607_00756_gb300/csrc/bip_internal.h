@@ -378,6 +378,9 @@ struct CubeTcArgs {
     int64_t b_site_rows;
     int swap_ch;
     int hi_only;
+    // map mode with B's rows (scan, channel) pairs, col_nch of them per scan
+    // (one accumulator: the channel sum is taken over columns); 0: off
+    int col_nch;
     int* err;
 };
 // a_k, b_k: row lengths of A and B (bf16 elements)

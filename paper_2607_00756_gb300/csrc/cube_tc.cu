@@ -32,8 +32,10 @@ constexpr int kBTile = kN * 64;
 constexpr int kStage = 4 * kATile + 4 * kBTile;   // hi/lo re/im planes
 constexpr int kStages = 4;
 constexpr size_t kSmem = 1024 + (size_t)kStages * kStage + 256;
-// planes as loaded into a stage: split BF16 0 re_hi, 1 re_lo, 2 im_hi, 3
-// im_lo; BF16 (hi_only) re -> slot 0, im -> slot 2
+// BF16 operands (two planes) fill half a stage: the same shared memory then
+// holds twice the stages, twice the bytes in flight per MMA
+// planes as loaded into a stage: split BF16 A re_hi, re_lo, im_hi, im_lo
+// then B the same; BF16 (HI) A re, im then B re, im
 
 __device__ __forceinline__ bool unit_of(const CubeTcArgs& a, int idx, int& w, int& mt) {
     if (idx >= a.n_work * a.mt_per) return false;
@@ -50,9 +52,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                    const CubeTcArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr int NS = HI ? 2 * kStages : kStages;               // stages
+    constexpr int SBYTES = HI ? kStage / 2 : kStage;             // bytes per stage
+    constexpr int BOFF = HI ? 2 * kATile : 4 * kATile;           // B planes in a stage
     uint64_t* full = (uint64_t*)(smem + kStages * kStage);
-    uint64_t* empty = full + kStages;
-    uint64_t* acc_full = empty + kStages;
+    uint64_t* empty = full + 2 * kStages;
+    uint64_t* acc_full = empty + 2 * kStages;
     uint64_t* acc_empty = acc_full + 1;
     uint64_t* drain = acc_empty + 1;
     uint32_t* tmem_slot = (uint32_t*)(drain + 1);
@@ -61,7 +66,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kStages; ++i) {
+        for (int i = 0; i < NS; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
@@ -105,18 +110,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = false;
                         break;
                     }
-                    uint8_t* st = smem + s * kStage;
+                    uint8_t* st = smem + s * SBYTES;
                     // K block within the channel (the operand without channels)
                     // and across channels (the one that has them)
                     const int kx = (kb % a.kb_ch) * 32, kc = kb * 32;
                     const int ax = a.swap_ch ? kx : kc, bx = a.swap_ch ? kc : kx;
                     if constexpr (HI) {
-                        mbar_expect_tx(&full[s], 2 * kATile + 2 * kBTile);
+                        mbar_expect_tx(&full[s], SBYTES);
 #pragma unroll
                         for (int pl = 0; pl < 2; ++pl) {
-                            tma_2d(st + 2 * pl * kATile, &mapA, ax, (int)(a0 + pl * a.a_plane_rows), &full[s]);
-                            tma_2d(st + 4 * kATile + 2 * pl * kBTile, &mapB, bx, (int)(b0 + pl * a.b_plane_rows),
-                                   &full[s]);
+                            tma_2d(st + pl * kATile, &mapA, ax, (int)(a0 + pl * a.a_plane_rows), &full[s]);
+                            tma_2d(st + BOFF + pl * kBTile, &mapB, bx, (int)(b0 + pl * a.b_plane_rows), &full[s]);
                         }
                     } else {
                         mbar_expect_tx(&full[s], kStage);
@@ -125,19 +129,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                             tma_2d(st + pl * kATile, &mapA, ax, (int)(a0 + pl * a.a_plane_rows), &full[s]);
 #pragma unroll
                         for (int pl = 0; pl < 4; ++pl)
-                            tma_2d(st + 4 * kATile + pl * kBTile, &mapB, bx, (int)(b0 + pl * a.b_plane_rows), &full[s]);
+                            tma_2d(st + BOFF + pl * kBTile, &mapB, bx, (int)(b0 + pl * a.b_plane_rows), &full[s]);
                     }
                     ++issued;
-                    if (++s == kStages) {
+                    if (++s == NS) {
                         s = 0;
                         ph ^= 1;
                     }
                 }
             }
             if (!ok) {
-                for (int k = 0; k < kStages && k < issued; ++k) {
-                    s = (s + kStages - 1) % kStages;
-                    if (s == kStages - 1) ph ^= 1;
+                for (int k = 0; k < NS && k < issued; ++k) {
+                    s = (s + NS - 1) % NS;
+                    if (s == NS - 1) ph ^= 1;
                     const uint64_t t0 = gtimer();
                     while (!mbar_try(&full[s], ph) && gtimer() - t0 < kTimeoutNs) {
                     }
@@ -165,24 +169,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t base = smem_u32(smem + s * kStage);
+                    const uint32_t base = smem_u32(smem + s * SBYTES);
                     const int ch = (kb - kb0) / a.kb_ch;
                     const uint32_t dr = tbase + (uint32_t)(ch * 2 * kN), di = dr + kN;
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
-                        uint64_t ad[4], bd[4];
-#pragma unroll
-                        for (int pl = 0; pl < 4; ++pl) {
-                            ad[pl] = sdesc(base + pl * kATile + kk * 32);
-                            bd[pl] = sdesc(base + 4 * kATile + pl * kBTile + kk * 32);
-                        }
                         const uint32_t first = (kb % a.kb_ch == 0 && kk == 0) ? 0u : 1u;
                         if constexpr (HI) {
-                            mma(dr, ad[0], bd[0], id_pos, first);
-                            mma(dr, ad[2], bd[2], id_neg, 1);
-                            mma(di, ad[0], bd[2], id_pos, first);
-                            mma(di, ad[2], bd[0], id_pos, 1);
+                            const uint64_t ar = sdesc(base + kk * 32), ai = sdesc(base + kATile + kk * 32);
+                            const uint64_t br = sdesc(base + BOFF + kk * 32), bi = sdesc(base + BOFF + kBTile + kk * 32);
+                            mma(dr, ar, br, id_pos, first);
+                            mma(dr, ai, bi, id_neg, 1);
+                            mma(di, ar, bi, id_pos, first);
+                            mma(di, ai, br, id_pos, 1);
                         } else {
+                            uint64_t ad[4], bd[4];
+#pragma unroll
+                            for (int pl = 0; pl < 4; ++pl) {
+                                ad[pl] = sdesc(base + pl * kATile + kk * 32);
+                                bd[pl] = sdesc(base + BOFF + pl * kBTile + kk * 32);
+                            }
                             // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
                             mma(dr, ad[0], bd[0], id_pos, first);
                             mma(dr, ad[0], bd[1], id_pos, 1);
@@ -200,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     any = true;
                     mma_commit(&empty[s]);
-                    if (++s == kStages) {
+                    if (++s == NS) {
                         s = 0;
                         ph ^= 1;
                     }
@@ -255,7 +261,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         float x = d < a.n_det ? v[j] : 0.f;
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                        const int rho = t * kN + c0 + j;
+                        const int col = t * kN + c0 + j;
+                        const int rho = a.col_nch ? col / a.col_nch : col;
                         if (lane == 0 && ((mask >> (c0 + j)) & 1ull))
                             atomicAdd(&a.partial[(size_t)a.site_ids[a.work[2 * w]] * a.P + rho], a.scale * x);
                     }
@@ -282,7 +289,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// 64-bit crop mask of each work item's scan tile (bit j: scan 64 t + j)
+// 64-bit crop mask of each work item's scan tile (bit j: scan 64 t + j; with
+// (scan, channel) columns, the scan of column 64 t + j)
 __global__ void crop_mask_kernel(CubeTcArgs a) {
     __shared__ unsigned long long part[4][2];
     const int w = blockIdx.x * (blockDim.x / 64) + threadIdx.x / 64;
@@ -291,8 +299,10 @@ __global__ void crop_mask_kernel(CubeTcArgs a) {
     if (w < a.n_work) {
         const int bs = a.work[2 * w], t = a.work[2 * w + 1];
         const SiteDev st = a.sites[a.site_ids[bs]];
-        const int rho = t * kN + j;
-        in = rho < a.P && in_crop(a.scans[2 * rho], a.scans[2 * rho + 1], st.ty, st.tx, a.ny, a.nx, a.fy, a.fx);
+        const int col = t * kN + j;
+        const int rho = a.col_nch ? col / a.col_nch : col;
+        in = col < (a.col_nch ? a.P * a.col_nch : a.P) &&
+             in_crop(a.scans[2 * rho], a.scans[2 * rho + 1], st.ty, st.tx, a.ny, a.nx, a.fy, a.fx);
     }
     // every lane takes part in the vote and the barrier
     const unsigned bits = __ballot_sync(0xffffffffu, in);
@@ -309,6 +319,7 @@ cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int 
     if (a.n_work < 1) return cudaSuccess;
     if (a.nacc < 1 || a.nacc > 4 || a.kb_ch < 1 || a.mt_per < 1 || a.ch0 < 0 || a_k % 32 || b_k % 32)
         return cudaErrorInvalidValue;
+    if (a.col_nch < 0 || (a.col_nch > 0 && (a.nacc != 1 || a.ch0 != 0 || !a.partial))) return cudaErrorInvalidValue;
     // the channel range inside the operand that has channels, one channel's
     // K blocks inside the other
     const int ch_k = a.swap_ch ? b_k : a_k, one_k = a.swap_ch ? a_k : b_k;

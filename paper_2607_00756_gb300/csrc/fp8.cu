@@ -15,6 +15,8 @@
 //   f8_scale_kernel : per batch, warp per target row: the bound from the
 //                     row's 64 weights (hi + lo BF16, one coalesced 128-byte
 //                     line per plane) and the parents' window maxima
+#include <cuda_fp16.h>
+
 #include "bip_internal.h"
 
 namespace {
@@ -58,8 +60,9 @@ __global__ void __launch_bounds__(kThreads) f8_hmax_kernel(F8HmaxArgs a) {
     }
 }
 
-__device__ __forceinline__ float bf16_word_lo(uint32_t w) { return __uint_as_float(w << 16); }
-__device__ __forceinline__ float bf16_word_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+// the two FP16 weights of a 32-bit word (the reconstruction's W planes)
+__device__ __forceinline__ float f16_word_lo(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
+__device__ __forceinline__ float f16_word_hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
 
 // grid: (row groups of 8, site in batch, side); warp = one target row
 __global__ void __launch_bounds__(kThreads) f8_scale_kernel(F8ScaleArgs a) {
@@ -75,7 +78,7 @@ __global__ void __launch_bounds__(kThreads) f8_scale_kernel(F8ScaleArgs a) {
         const uint32_t h = __ldg(&whi[lane]), l = __ldg(&wlo[lane]);
         const unsigned* pm = a.pmax + ((size_t)side * a.n_sites + bs) * 64;
         const float m0 = __uint_as_float(__ldg(&pm[2 * lane])), m1 = __uint_as_float(__ldg(&pm[2 * lane + 1]));
-        float s = fmaf(bf16_word_lo(h) + bf16_word_lo(l), m0, (bf16_word_hi(h) + bf16_word_hi(l)) * m1);
+        float s = fmaf(f16_word_lo(h) + f16_word_lo(l), m0, (f16_word_hi(h) + f16_word_hi(l)) * m1);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         bound = kKappa * s;

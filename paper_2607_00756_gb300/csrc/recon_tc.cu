@@ -8,10 +8,11 @@
 //   A(t, r)    = sum_p w_tp |S_p(r)|
 // are one product W X with W [targets x 64 parents] and X [64 parents x
 // pixels] per plane (re, im, magnitude), K = the parents (zero-padded to 64).
-// W is exact to FP32 as hi + lo BF16 (two products per plane); X is BF16 --
-// the same rounding the mixed path applies to the operands it produces.
+// The products are FP16 (kind::f16 with FP16 operands): W exact to FP32 as
+// hi + lo FP16 (two products per plane), X rounded once to FP16 (relative
+// 2^-11; the parent windows are O(1) plane-wave sums, far inside its range).
 //
-//   xprep_kernel    stash [Bp][K] complex64 -> X [3 planes][K px][64] bf16
+//   xprep_kernel    stash [Bp][K] complex64 -> X [3 planes][K px][64] fp16
 //                   (transposed so the parents are contiguous: K-major B)
 //   recon_tc_kernel persistent, one CTA per SM, 576 threads:
 //     warp 0     TMA producer: the unit's W tile (128 targets x 64 parents,
@@ -33,6 +34,7 @@
 // pixels).  Every wait is bounded; on a timeout the kernel sets *err, stops,
 // drains the copies and MMAs it issued and frees TMEM.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "fft_smem.cuh"
 #include "tc_common.cuh"
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer
-            const uint32_t id = idesc(128, kN, false);
+            const uint32_t id = idesc_f16(128, kN, false);
             int s = 0, acc = 0;
             uint32_t ph = 0, aph = 0;
             bool any = false, ok = true;
@@ -470,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// stash [Bp][K] complex64 of one site -> X planes [3][K][64] bf16 (re, im,
+// stash [Bp][K] complex64 of one site -> X planes [3][K][64] fp16 (re, im,
 // magnitude; parents past Bp zero).  Block: 64 pixels of one site and side.
 constexpr int kPrepThreads = 256;
 __global__ void __launch_bounds__(kPrepThreads) xprep_kernel(XprepArgs a) {
@@ -529,7 +531,8 @@ __global__ void __launch_bounds__(kPrepThreads) xprep_kernel(XprepArgs a) {
                 f0 = sqrtf(e0.x * e0.x + e0.y * e0.y);
                 f1 = sqrtf(e1.x * e1.x + e1.y * e1.y);
             }
-            v[k] = pack2(f0, f1);
+            const __half2 hv = __floats2half2_rn(f0, f1);
+            v[k] = *reinterpret_cast<const uint32_t*>(&hv);
         }
         *reinterpret_cast<uint4*>(dst + ((size_t)pl * a.K + x) * 64 + p0) = make_uint4(v[0], v[1], v[2], v[3]);
     }

@@ -89,6 +89,10 @@ __host__ __device__ constexpr uint32_t idesc(int M, int N, bool negA) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
 }
+// the same for FP16 x FP16 -> F32 (a_format = b_format = 0)
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool negA) {
+    return (1u << 4) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"

@@ -99,7 +99,8 @@ def _order_case(which):
     """Workloads of the contraction-order tests: config 1; the edge-case
     specimen (every plane, wrapping windows, 21 sites with one or three
     channels, a ragged scan line); an anisotropic grid; config 1 with six
-    channels per site (two passes of the cube kernel's four accumulators)."""
+    channels per site (two passes of the cube kernel's four accumulators),
+    with all its scans or with 40 of them."""
     if which == "edge":
         from test_gpu_map import _edge_specimen
         return _edge_specimen()
@@ -110,13 +111,16 @@ def _order_case(which):
         return cfg, synth.make_specimen(cfg)
     cfg = synth.config1()
     sp = synth.make_specimen(cfg)
-    if which == "six_channels":
+    if which.startswith("six_channels"):
         keep = np.nonzero(sp.nch > 0)[0]
         h3 = sp.H.reshape(len(keep), 3, cfg.win, cfg.win)
         h6 = np.concatenate([h3, 0.5j * h3[:, ::-1]], axis=1).reshape(-1, cfg.win, cfg.win)
         nch = sp.nch.copy()
         nch[keep] = 6
-        sp = synth.Specimen(cfg=cfg, atoms=sp.atoms, nch=nch, V=sp.V, H=h6, scans=sp.scans)
+        # few scans: the probe order then puts (scan, channel) pairs in the
+        # cube kernel's columns instead of one accumulator per channel
+        scans = sp.scans[100:140] if which.endswith("few_scans") else sp.scans
+        sp = synth.Specimen(cfg=cfg, atoms=sp.atoms, nch=nch, V=sp.V, H=h6, scans=scans)
     return cfg, sp
 
 
@@ -148,11 +152,14 @@ def test_beam_order_map(lib, which, prec):
     _order_check(lib, which, prec, 1)
 
 
-@pytest.mark.parametrize("which", ["config1", "edge", "aniso", "six_channels"])
+@pytest.mark.parametrize("which", ["config1", "edge", "aniso", "six_channels", "six_channels_few_scans"])
 def test_probe_order_map(lib, which):
     """The map in probe order (the windowed probes Psi = C^T S1 of every
     scan, then |S2^T (H_n x Psi)|^2 summed over d and n on tcgen05) against
-    the oracle and the Gram route, mixed precision."""
+    the oracle and the Gram route, mixed precision.  The edge case (101
+    scans, three channels) and the six-channel case with 40 scans take the
+    (scan, channel)-column form of the last contraction; the others one
+    accumulator per channel."""
     _order_check(lib, which, "mixed", 2)
 
 
