@@ -39,6 +39,7 @@ DTYPES = {"mixed": "fp16 reconstruction, bf16 coupling+Gram, f32 quadratic form 
           "fp8": "fp16 reconstruction, e4m3 coupling (per-window scales), bf16 Gram, f32 quadratic form / "
                  "f32 accumulate"}
 UNIT = "atom×probe evals/s"
+ORDERS = ["gram", "beam", "probe"]
 
 
 def load_peaks():
@@ -76,12 +77,20 @@ def phonon_mean(out, world):
 # ---------------------------------------------------------------------------
 # workload
 
-def workload(name, rank, max_sites=0):
+def workload(name, rank, max_sites=0, scan_side=0):
     import synth
     cfg = synth.CONFIGS[name]()
     if rank:
         cfg = cfg.replace(seed=rank)          # another frozen-phonon configuration
     sp = synth.make_specimen(cfg)
+    if scan_side:
+        # the central scan_side x scan_side scans of the raster (analysis and
+        # profiling of the contraction orders with few scans)
+        n = int(round(np.sqrt(len(sp.scans))))
+        c, h = n // 2, scan_side // 2
+        grid = sp.scans.reshape(n, n, 2)[c - h:c - h + scan_side, c - h:c - h + scan_side]
+        sp = synth.Specimen(cfg=cfg, atoms=sp.atoms, nch=sp.nch, V=sp.V, H=sp.H,
+                            scans=np.ascontiguousarray(grid.reshape(-1, 2)))
     if max_sites:
         # keep only the first max_sites ionized sites (small profiling case)
         ion = np.nonzero(sp.nch > 0)[0]
@@ -239,7 +248,7 @@ def run_gpu(args, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    cfg, sp = workload(args.workload, rank, args.max_sites)
+    cfg, sp = workload(args.workload, rank, args.max_sites, args.scan_side)
     V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
     H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
     atoms, nch_a, scans = sp.atoms, sp.nch, sp.scans
@@ -258,6 +267,8 @@ def run_gpu(args, rank, world):
     paths = [p for p in args.paths.split(",") if p]
     for path in paths:
         ctx = BipContext(cfg, prec=path)
+        if args.order != "gram":
+            ctx.set_order(ORDERS.index(args.order))
         out = torch.empty(P, dtype=torch.float64, device=dev)
 
         def step():
@@ -718,6 +729,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="config2")
+    ap.add_argument("--order", default="gram", choices=ORDERS,
+                    help="scan contraction of the map (analysis; the headline runs the Gram route)")
+    ap.add_argument("--scan-side", type=int, default=0,
+                    help="use the central S x S scans of the raster (analysis; 0: all)")
     ap.add_argument("--paths", default="mixed,split_bf16,fp8,fp32")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
@@ -733,7 +748,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cfg, sp = workload(args.workload, 0, args.max_sites)
+        cfg, sp = workload(args.workload, 0, args.max_sites, args.scan_side)
         vals = []
         sample = ""
         for _ in range(args.warmup):
@@ -747,7 +762,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": n_sites * len(sp.scans) / v * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": config_block(cfg, sp),
+                "config": config_block(cfg, sp, args.order),
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                                  "sample": sample},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -776,7 +791,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[head],
-            "data": "synthetic", "config": config_block(cfg, sp)}
+            "data": "synthetic", "config": config_block(cfg, sp, args.order)}
     line["roofline"] = roofline(cfg, head, res, info, geo_sizes)
     paths_out = {}
     for p in paths:
@@ -812,14 +827,14 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def config_block(cfg, sp):
+def config_block(cfg, sp, order="gram"):
     n_sites = int((sp.nch > 0).sum())
     return {"workload": f"{cfg.name}: {cfg.ny}x{cfg.nx} grid, {cfg.nz} slices of {cfg.dz} A, "
                         f"{cfg.e0 / 1e3:.0f} keV, {cfg.alpha * 1e3:.0f} mrad, f={cfg.fy}, "
                         f"{n_sites} ionized sites x {len(cfg.channels)} channels, "
                         f"{len(sp.scans)} scans, 0-{cfg.theta_det * 1e3:.0f} mrad detector",
             "sites": n_sites, "scans": len(sp.scans), "grid": [cfg.ny, cfg.nx], "slices": cfg.nz,
-            "window": cfg.win, "recon": cfg.recon,
+            "window": cfg.win, "recon": cfg.recon, "order": order,
             "l2": "256 MB buffer written between timed steps; working set (6.4 GB stash) >> L2"}
 
 
