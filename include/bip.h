@@ -216,7 +216,8 @@ bip_status bip_coreloss_qeels(bip_ctx* ctx, const void* H, const double* scan_px
  *   counts against the SM count and the L2 size).
  * bip_autotune: times maps (two after a warm-up, CUDA events) over sites per
  *   batch, then coupling tile widths, then the contraction order (see
- *   bip_set_order), keeps the fastest in the context and returns it;
+ *   bip_set_order) -- and, when another order wins, the sites per batch
+ *   again under it -- keeps the fastest in the context and returns it;
  *   map_out holds the last map.  Results do not depend on
  *   these choices (each site's arithmetic and the site-sum order are fixed). */
 bip_status bip_set_capture_safe(bip_ctx* ctx, int32_t on);

@@ -1886,6 +1886,20 @@ bip_status bip_autotune(bip_ctx* c, const void* H, const double* scan_px, int32_
             }
         }
     }
+    if (st == BIP_OK && best_order != order0) {
+        // the batch size again under the chosen order (the beam and probe
+        // orders' last contraction has its own work units per site)
+        c->order = best_order;
+        for (int sb : {8, 12, 13, 14, 16, 19, 24, 27, 28, 32}) {
+            if (sb == best_sb || sb > std::max(1, c->n_sites)) continue;
+            st = time_map(sb, best_cw, &t);
+            if (st != BIP_OK) break;
+            if (t < best) {
+                best = t;
+                best_sb = sb;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->sb_override = best_sb;
