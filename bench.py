@@ -426,7 +426,7 @@ def run_graphs(prec="mixed", reps=20):
     return {"specimens": len(items), "precision": prec, "evals_per_round": evals,
             "eager_ms": t_eager * 1e3, "graph_ms": t_graph * 1e3,
             "eager_evals_per_s": evals / t_eager, "graph_evals_per_s": evals / t_graph,
-            "timing": "host wall clock around 20 rounds, synchronised"}
+            "timing": "host wall clock around 20 repetitions, synchronised"}
 
 
 def run_grad(reps=3, prec="mixed"):
