@@ -1348,17 +1348,21 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     c->work_key = work_key;
     }
 
-    // the cube on tcgen05: c_b(rho) as split planes [4][P64][Bpad] once, and
-    // work lists of (site in batch, 64-scan tile meeting its crop mask)
+    // the cube on tcgen05: c_b(rho) as split planes [4][crow][Bpad] once, and
+    // work lists of (site in batch, scan tile meeting its crop mask)
     const bool cube_tc = (cube_out || beam || probe) && tc;
+    // scans per tile of the cube kernel (its MMA's N) for the cube and the
+    // beam order: 128 once there are that many scans, else 64; the probe
+    // order's last contraction keeps 64
+    const int ctn = (cube_out || beam) && P >= 128 ? 128 : 64;
     // the probe order's last contraction: the channels in the tile's columns
     // ((scan, channel) pairs, one accumulator) when that takes fewer 64-wide
     // tiles than a 64-scan tile with one accumulator per channel (few scans)
     const bool probe_cols = probe && (P * nch + 63) / 64 < nch * ((P + 63) / 64);
     const int P64 = round_up(P, 64), D128 = round_up(Dpad, 128);
-    // rows of each plane of C^T: the cube kernel's 64-scan tiles, or the
-    // probe order's 128-row tiles of Psi = C^T S1
-    const int crow = probe ? round_up(P, 128) : P64;
+    // rows of each plane of C^T: whole scan tiles of the cube kernel, or (probe
+    // order) whole 128-row tiles
+    const int crow = probe ? round_up(P, 128) : round_up(P, ctn);
     const size_t KB = (size_t)nch * Bpad;
     std::vector<int> cube_off;
     if (cube_tc) {
@@ -1366,14 +1370,15 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         if (!probe) CUDA_TRY(c, ensure(c->cubeA, (size_t)SB * 4 * D128 * KB * sizeof(uint16_t), true, s));
         SplitArgs sc{(const float2*)c->illum.p, 1, P, 0, P, Bpad, 1, (uint16_t*)c->cubeB.p, 0, crow, Bpad, 0, 0};
         CUDA_TRY(c, bip_split_planes(sc, s));
-        // tiles of 64 scans -- or, for the probe order with fewer columns that
+        // tiles of ctn scans -- or, for the probe order with fewer columns that
         // way, of 64 (scan, channel) columns -- and their scans' bounding boxes
         const int ncol = probe_cols ? nch : 1;
-        const int n_ct = (P * ncol + 63) / 64;
+        const int tile = probe ? 64 : ctn;
+        const int n_ct = (P * ncol + tile - 1) / tile;
         std::vector<double> bb64;
         for (int t = 0; t < n_ct; ++t) {
             double y0 = INFINITY, y1 = -INFINITY, x0 = INFINITY, x1 = -INFINITY;
-            for (int p = t * 64 / ncol; p < std::min(P, ((t + 1) * 64 + ncol - 1) / ncol); ++p) {
+            for (int p = t * tile / ncol; p < std::min(P, ((t + 1) * tile + ncol - 1) / ncol); ++p) {
                 y0 = std::min(y0, scans[2 * p]);
                 y1 = std::max(y1, scans[2 * p]);
                 x0 = std::min(x0, scans[2 * p + 1]);
@@ -1395,7 +1400,8 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         }
         cube_off.push_back((int)cw.size() / 2);
         CUDA_TRY(c, upload(c->cube_work, cw, s));
-        CUDA_TRY(c, ensure(c->cube_mask, std::max<size_t>(1, cw.size() / 2) * sizeof(unsigned long long), false, s));
+        CUDA_TRY(c, ensure(c->cube_mask, std::max<size_t>(1, cw.size() / 2 * (tile / 64)) * sizeof(unsigned long long),
+                           false, s));
     }
 
     int bi = 0;
@@ -1569,14 +1575,15 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
                 CubeTcArgs ct{};
                 ct.n_work = cube_off[bi + 1] - cube_off[bi];
                 ct.work = (const int32_t*)c->cube_work.p + 2 * (size_t)cube_off[bi];
-                ct.mask = (unsigned long long*)c->cube_mask.p + cube_off[bi];
+                ct.mask = (unsigned long long*)c->cube_mask.p + (size_t)cube_off[bi] * (ctn / 64);
                 ct.n_sites = nb;
-                ct.n_tiles = P64 / 64;
+                ct.tn = ctn;
+                ct.n_tiles = crow / ctn;
                 ct.mt_per = D128 / 128;
                 ct.kb_ch = Bpad / 32;
                 ct.a_site_rows = 4 * (int64_t)D128;
                 ct.a_plane_rows = D128;
-                ct.b_plane_rows = P64;
+                ct.b_plane_rows = crow;
                 ct.n_det = geo.n_det;
                 ct.P = P;
                 ct.scans = (const double*)c->scans_d.p;
@@ -1587,12 +1594,15 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
                 ct.cube = cube_out;
                 ct.partial = beam ? partial : nullptr;
                 ct.err = (int*)c->errflag.p;
-                for (int ch0 = 0; ch0 < nch; ch0 += 4) {
+                // channels per launch: one TMEM accumulator pair (2 ctn columns)
+                // each in 512 columns
+                const int per = 512 / (2 * ctn);
+                for (int ch0 = 0; ch0 < nch; ch0 += per) {
                     ct.ch0 = ch0;
-                    ct.nacc = std::min(4, nch - ch0);
+                    ct.nacc = std::min(per, nch - ch0);
                     TIMED(c, BIP_STAGE_QUADFORM, s,
-                          bip_cube_tc(ct, c->cubeA.p, (int64_t)nb * 4 * D128, (int)KB, c->cubeB.p, (int64_t)4 * P64, Bpad,
-                                      s));
+                          bip_cube_tc(ct, c->cubeA.p, (int64_t)nb * 4 * D128, (int)KB, c->cubeB.p, (int64_t)4 * crow,
+                                      Bpad, s));
                 }
                 continue;
             }

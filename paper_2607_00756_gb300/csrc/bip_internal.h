@@ -359,7 +359,7 @@ cudaError_t bip_cube_accumulate(const CubeArgs& a, cudaStream_t s);
 struct CubeTcArgs {
     int n_work;
     const int32_t* work;            // [n_work][2] (site in batch, scan tile)
-    unsigned long long* mask;       // [n_work] crop masks (written by the launch)
+    unsigned long long* mask;       // [n_work][tn / 64] crop masks (written by the launch)
     int n_sites, n_tiles;           // sites in the batch, scan tiles of B
     int mt_per, kb_ch, ch0, nacc;   // d tiles, K blocks per channel, channel range
     int64_t a_site_rows, a_plane_rows, b_plane_rows;
@@ -381,6 +381,9 @@ struct CubeTcArgs {
     // map mode with B's rows (scan, channel) pairs, col_nch of them per scan
     // (one accumulator: the channel sum is taken over columns); 0: off
     int col_nch;
+    // scans (B rows) per tile and the MMA's N: 64 (0 means 64) or 128; the
+    // crop masks then take tn / 64 words per work item
+    int tn;
     int* err;
 };
 // a_k, b_k: row lengths of A and B (bf16 elements)

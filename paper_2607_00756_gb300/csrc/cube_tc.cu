@@ -26,16 +26,22 @@
 namespace {
 
 constexpr int kThreads = 192;
-constexpr int kN = 64;                            // scans per tile
 constexpr int kATile = 128 * 64;                  // bytes: 128 rows x 32 bf16
-constexpr int kBTile = kN * 64;
-constexpr int kStage = 4 * kATile + 4 * kBTile;   // hi/lo re/im planes
-constexpr int kStages = 4;
-constexpr size_t kSmem = 1024 + (size_t)kStages * kStage + 256;
-// BF16 operands (two planes) fill half a stage: the same shared memory then
-// holds twice the stages, twice the bytes in flight per MMA
-// planes as loaded into a stage: split BF16 A re_hi, re_lo, im_hi, im_lo
-// then B the same; BF16 (HI) A re, im then B re, im
+constexpr int kRing = 4 * (4 * kATile + 4 * 64 * 64);   // bytes of the stage ring
+constexpr int kMaxStages = 8;
+constexpr size_t kSmem = 1024 + (size_t)kRing + 256;
+// A stage holds one 32-wide K block of every plane: split BF16 A re_hi,
+// re_lo, im_hi, im_lo then B the same; BF16 (HI) A re, im then B re, im.
+// The ring holds as many stages as fit: 4 (split, 64-scan tiles), 3 (split,
+// 128), 8 (BF16, 64), 6 (BF16, 128).
+template <bool HI, int TN>
+struct Shape {
+    static constexpr int BTILE = TN * 64;                           // bytes of one B plane
+    static constexpr int SBYTES = HI ? 2 * kATile + 2 * BTILE : 4 * kATile + 4 * BTILE;
+    static constexpr int NS = kRing / SBYTES;
+    static constexpr int BOFF = HI ? 2 * kATile : 4 * kATile;       // B planes in a stage
+    static_assert(NS >= 2 && NS <= kMaxStages, "stage ring");
+};
 
 __device__ __forceinline__ bool unit_of(const CubeTcArgs& a, int idx, int& w, int& mt) {
     if (idx >= a.n_work * a.mt_per) return false;
@@ -44,20 +50,21 @@ __device__ __forceinline__ bool unit_of(const CubeTcArgs& a, int idx, int& w, in
     return true;
 }
 
-// HI: BF16 operands of two planes (four MMAs per K step) -- a template
-// parameter, so that the split-BF16 issue loop carries no branch
-template <bool HI>
+// HI: BF16 operands of two planes (four MMAs per K step); TN: scans (B
+// rows) per tile, the MMA's N.  Template parameters, so that the issue loop
+// carries no branch on them.
+template <bool HI, int TN>
 __global__ void __launch_bounds__(kThreads, 1)
     cube_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const CubeTcArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int NS = HI ? 2 * kStages : kStages;               // stages
-    constexpr int SBYTES = HI ? kStage / 2 : kStage;             // bytes per stage
-    constexpr int BOFF = HI ? 2 * kATile : 4 * kATile;           // B planes in a stage
-    uint64_t* full = (uint64_t*)(smem + kStages * kStage);
-    uint64_t* empty = full + 2 * kStages;
-    uint64_t* acc_full = empty + 2 * kStages;
+    using SH = Shape<HI, TN>;
+    constexpr int NS = SH::NS, SBYTES = SH::SBYTES, BOFF = SH::BOFF, kBTile = SH::BTILE, kN = TN;
+    constexpr int MW = TN / 64;                                  // mask words per work item
+    uint64_t* full = (uint64_t*)(smem + kRing);
+    uint64_t* empty = full + kMaxStages;
+    uint64_t* acc_full = empty + kMaxStages;
     uint64_t* acc_empty = acc_full + 1;
     uint64_t* drain = acc_empty + 1;
     uint32_t* tmem_slot = (uint32_t*)(drain + 1);
@@ -123,7 +130,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             tma_2d(st + BOFF + pl * kBTile, &mapB, bx, (int)(b0 + pl * a.b_plane_rows), &full[s]);
                         }
                     } else {
-                        mbar_expect_tx(&full[s], kStage);
+                        mbar_expect_tx(&full[s], SBYTES);
 #pragma unroll
                         for (int pl = 0; pl < 4; ++pl)
                             tma_2d(st + pl * kATile, &mapA, ax, (int)(a0 + pl * a.a_plane_rows), &full[s]);
@@ -238,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!*ep_ok) break;
             tc_fence_after();
             const int t = a.work[2 * w + 1];
-            const unsigned long long mask = a.mask[w];
+            const unsigned long long* mask = a.mask + (size_t)w * MW;
             const int d = mt * 128 + q * 32 + lane;
             const uint32_t tr = tbase + ((uint32_t)(q * 32) << 16);
             for (int c0 = 0; c0 < kN; c0 += 16) {
@@ -263,14 +270,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
                         const int col = t * kN + c0 + j;
                         const int rho = a.col_nch ? col / a.col_nch : col;
-                        if (lane == 0 && ((mask >> (c0 + j)) & 1ull))
+                        if (lane == 0 && ((mask[c0 >> 6] >> ((c0 & 63) + j)) & 1ull))
                             atomicAdd(&a.partial[(size_t)a.site_ids[a.work[2 * w]] * a.P + rho], a.scale * x);
                     }
                 } else if (d < a.n_det) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int rho = t * kN + c0 + j;
-                        if ((mask >> (c0 + j)) & 1ull) atomicAdd(&a.cube[(size_t)rho * a.n_det + d], a.scale * v[j]);
+                        if ((mask[c0 >> 6] >> ((c0 & 63) + j)) & 1ull)
+                            atomicAdd(&a.cube[(size_t)rho * a.n_det + d], a.scale * v[j]);
                     }
                 }
             }
@@ -289,17 +297,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// 64-bit crop mask of each work item's scan tile (bit j: scan 64 t + j; with
-// (scan, channel) columns, the scan of column 64 t + j)
-__global__ void crop_mask_kernel(CubeTcArgs a) {
+// 64-bit crop masks of the work items' scan tiles, tile/64 words per item
+// (bit j of word h: scan tile t + 64 h + j; with (scan, channel) columns,
+// the scan of that column).  Sub-item = (work item, word).
+__global__ void crop_mask_kernel(CubeTcArgs a, int tn) {
     __shared__ unsigned long long part[4][2];
-    const int w = blockIdx.x * (blockDim.x / 64) + threadIdx.x / 64;
+    const int mw = tn / 64;
+    const int sub = blockIdx.x * (blockDim.x / 64) + threadIdx.x / 64;
+    const int w = sub / mw, h = sub % mw;
     const int j = threadIdx.x % 64;
     bool in = false;
     if (w < a.n_work) {
         const int bs = a.work[2 * w], t = a.work[2 * w + 1];
         const SiteDev st = a.sites[a.site_ids[bs]];
-        const int col = t * kN + j;
+        const int col = t * tn + h * 64 + j;
         const int rho = a.col_nch ? col / a.col_nch : col;
         in = col < (a.col_nch ? a.P * a.col_nch : a.P) &&
              in_crop(a.scans[2 * rho], a.scans[2 * rho + 1], st.ty, st.tx, a.ny, a.nx, a.fy, a.fx);
@@ -309,7 +320,22 @@ __global__ void crop_mask_kernel(CubeTcArgs a) {
     if ((threadIdx.x & 31) == 0) part[threadIdx.x / 64][(threadIdx.x / 32) & 1] = bits;
     __syncthreads();
     if (j == 0 && w < a.n_work)
-        a.mask[w] = part[threadIdx.x / 64][0] | (part[threadIdx.x / 64][1] << 32);
+        a.mask[sub] = part[threadIdx.x / 64][0] | (part[threadIdx.x / 64][1] << 32);
+}
+
+template <bool HI, int TN>
+cudaError_t launch_cube(const CubeTcArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(cube_tc_kernel<HI, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int units = a.n_work * a.mt_per;
+    const int grid = units < num_sms() ? units : num_sms();
+    cube_tc_kernel<HI, TN><<<grid, kThreads, kSmem, s>>>(ma, mb, a);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -317,7 +343,11 @@ __global__ void crop_mask_kernel(CubeTcArgs a) {
 cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int a_k, const void* B, int64_t b_rows,
                         int b_k, cudaStream_t s) {
     if (a.n_work < 1) return cudaSuccess;
-    if (a.nacc < 1 || a.nacc > 4 || a.kb_ch < 1 || a.mt_per < 1 || a.ch0 < 0 || a_k % 32 || b_k % 32)
+    const int tn = a.tn ? a.tn : 64;
+    if (tn != 64 && tn != 128) return cudaErrorInvalidValue;
+    // one TMEM accumulator pair (2 tn columns) per channel in 512 columns
+    if (a.nacc < 1 || a.nacc * 2 * tn > (int)kTmemCols || a.kb_ch < 1 || a.mt_per < 1 || a.ch0 < 0 || a_k % 32 ||
+        b_k % 32)
         return cudaErrorInvalidValue;
     if (a.col_nch < 0 || (a.col_nch > 0 && (a.nacc != 1 || a.ch0 != 0 || !a.partial))) return cudaErrorInvalidValue;
     // the channel range inside the operand that has channels, one channel's
@@ -329,30 +359,19 @@ cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int 
     const int64_t pl = a.hi_only ? 1 : 3;
     if ((int64_t)(a.n_sites - 1) * a.a_site_rows + pl * a.a_plane_rows + (int64_t)a.mt_per * 128 > a_rows)
         return cudaErrorInvalidValue;
-    if ((int64_t)(a.n_sites - 1) * a.b_site_rows + pl * a.b_plane_rows + (int64_t)a.n_tiles * kN > b_rows)
+    if ((int64_t)(a.n_sites - 1) * a.b_site_rows + pl * a.b_plane_rows + (int64_t)a.n_tiles * tn > b_rows)
         return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     cudaError_t e = make_map_2d(&ma, A, a_rows, a_k, 128);
     if (e != cudaSuccess) return e;
-    e = make_map_2d(&mb, B, b_rows, b_k, kN);
+    e = make_map_2d(&mb, B, b_rows, b_k, tn);
     if (e != cudaSuccess) return e;
-    // the crop masks of the work items (4 items per 256-thread block)
-    crop_mask_kernel<<<(a.n_work + 3) / 4, 256, 0, s>>>(a);
+    // the crop masks of the work items (tn / 64 words each, 4 words per
+    // 256-thread block)
+    const int subs = a.n_work * (tn / 64);
+    crop_mask_kernel<<<(subs + 3) / 4, 256, 0, s>>>(a, tn);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    static bool attr[2] = {false, false};
-    const int hi = a.hi_only ? 1 : 0;
-    if (!attr[hi]) {
-        e = hi ? cudaFuncSetAttribute(cube_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem)
-               : cudaFuncSetAttribute(cube_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-        if (e != cudaSuccess) return e;
-        attr[hi] = true;
-    }
-    const int units = a.n_work * a.mt_per;
-    const int grid = units < num_sms() ? units : num_sms();
-    if (hi)
-        cube_tc_kernel<true><<<grid, kThreads, kSmem, s>>>(ma, mb, a);
-    else
-        cube_tc_kernel<false><<<grid, kThreads, kSmem, s>>>(ma, mb, a);
-    return cudaGetLastError();
+    if (a.hi_only) return tn == 128 ? launch_cube<true, 128>(a, ma, mb, s) : launch_cube<true, 64>(a, ma, mb, s);
+    return tn == 128 ? launch_cube<false, 128>(a, ma, mb, s) : launch_cube<false, 64>(a, ma, mb, s);
 }
