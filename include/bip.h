@@ -60,8 +60,12 @@ typedef enum {
     BIP_PREC_SPLIT_BF16 = 1,   /* tcgen05, every contraction in BF16 hi+lo
                                   (3 products per real product), FP32 acc.    */
     BIP_PREC_MIXED = 2,        /* tcgen05, coupling and Gram in BF16 (one
-                                  product), the quadratic form in BF16 hi+lo;
-                                  FP32 accumulation throughout               */
+                                  product); the window reconstruction's sums
+                                  on tcgen05 in FP16 (weights hi+lo, parent
+                                  values rounded once) when both parent sets
+                                  are <= 64, else the FP32 SIMT gather; the
+                                  scan polynomial in FP32; FP32 accumulation
+                                  throughout                                 */
     BIP_PREC_FP8_TILE = 3      /* as MIXED, but the coupling's operands in
                                   FP8 E4M3 with one scale per 64x64 window
                                   (operand row): the scale is an a-priori
