@@ -197,6 +197,30 @@ def test_subsampling_scale_consistency(c1):
         assert rel(corr * ex.partials[k][near], e1.partials[k][near]) < 0.03
 
 
+def test_subsampling_scale_consistency_f3():
+    """The same reading at f = 3 on a grid that is not a power of two (96^2,
+    three cells of 32 px): the f = 3 exact map, corrected for the aperture's
+    beam count (9 beams vs 109/9), matches the f = 1 exact map near each
+    site within 6% (the 9-beam aperture samples the disc coarsely).  A
+    missing or doubled f_y f_x on either side would be off by 9x.  The
+    partitioned map stays within 1e-4 of the exact one there."""
+    cfg = synth.config1().replace(name="f3", ny=96, nx=96, ly=7.5, lx=7.5, cells_y=3, cells_x=3, fy=3, fx=3,
+                                  win=32, ion_cells=(1, 2), ion_slices=(1, 3), scan_y=(36.0, 3.0, 10),
+                                  scan_x=(36.0, 3.0, 10))
+    sp = synth.make_specimen(cfg)
+    pr = bip.make_problem(sp)
+    ex = bip.exact_map(pr)
+    e1 = bip.exact_map(bip.make_problem(sp, fy=1, fx=1))
+    geo = pr.geo
+    assert len(geo.h_beam) == 9
+    corr = len(geo.h_full) / (pr.cfg.fy * pr.cfg.fx * len(geo.h_beam))
+    for k in range(len(pr.ion)):
+        near = np.all(np.abs(pr.scans - pr.tau_px[k]) < 10, axis=1)
+        assert near.sum() >= 25
+        assert rel(corr * ex.partials[k][near], e1.partials[k][near]) < 0.06
+    assert rel(bip.bip_map(pr).map, ex.map) < 1e-4
+
+
 # ---------------------------------------------------------------------------
 # the 4D cube (Sec. 2.2.6): the same terms with the detector sum left open
 
