@@ -33,6 +33,10 @@
  *             text of the last failure on that context.  Calls on one
  *             context are not thread-safe; distinct contexts are
  *             independent.
+ *   devices   one GPU per process (the current device when a context is
+ *             created and used): the kernels' shared-memory launch limits
+ *             are raised once per process, on the device of their first
+ *             launch.  Several GPUs take one process each.
  */
 #ifndef BIP_H
 #define BIP_H
