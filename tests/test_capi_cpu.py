@@ -171,3 +171,25 @@ def test_model_and_launch_controls_host(capi):
         capi.bip_destroy(ctx)
     assert capi.lib().bip_set_launch(None, 0, 0) == 1
     assert capi.lib().bip_set_occupancy(None, None) == 1
+
+
+def test_product_never_imports_the_oracle():
+    """The library package, its C/CUDA sources and the input generators
+    reference nothing under oracle/: the product path runs only in
+    libbip.so, and the oracle is test infrastructure."""
+    import ast
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for sub in ("paper_2607_00756_gb300", "synth"):
+        for dirpath, _, files in os.walk(os.path.join(root, sub)):
+            for f in files:
+                path = os.path.join(dirpath, f)
+                if f.endswith(".py"):
+                    tree = ast.parse(open(path).read())
+                    for node in ast.walk(tree):
+                        if isinstance(node, ast.Import):
+                            assert not any(a.name.split(".")[0] == "oracle" for a in node.names), path
+                        elif isinstance(node, ast.ImportFrom):
+                            assert (node.module or "").split(".")[0] != "oracle", path
+                elif f.endswith((".cu", ".cuh", ".cpp", ".h")):
+                    assert "oracle/" not in open(path).read(), path
