@@ -15,6 +15,9 @@ Plain NumPy complex128 / float64, written step by step from the paper:
                  preserving reconstruction, coupling matrix, map
                  (Algorithm 5), the exact dual-matrix map (Algorithm 4) and
                  conventional multislice (Algorithm 1) used as ground truth.
+  fp8.py       - the coupling with scaled E4M3 operands (FP64 model)
+  mixed.py     - the mixed path's BF16 / FP16 roundings (FP64 model)
+  grad.py      - the hand-written reverse pass of the map (Sec. 5)
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
 closed forms, invariants, brute force or printed values, except the two
