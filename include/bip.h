@@ -137,6 +137,9 @@ bip_status bip_query(const bip_ctx* ctx, int32_t* B, int32_t* n_det,
 bip_status bip_get_geometry(const bip_ctx* ctx, int32_t* h_beam, int32_t* h_det,
                             int32_t* p1, int32_t* p2, double* w1, double* w2);
 
+/* Copies the configuration the context was created with to *out. */
+bip_status bip_get_config(const bip_ctx* ctx, bip_config* out);
+
 /* Chooses the contraction arithmetic for later bip_coreloss_* calls. */
 bip_status bip_set_precision(bip_ctx* ctx, int32_t prec);
 

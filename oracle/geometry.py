@@ -12,7 +12,7 @@ Paper passages followed:
   * Sibson natural-neighbour weights w_{p,b} >= 0, sum_p w = 1, local support
     (Eq. nnw; Sibson 1981), computed on signed-frequency coordinates q.
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
   * beams are ordered by (h_y, h_x) ascending; the aperture edge is
     inclusive with a relative slack of 1e-12;
   * ring radii r_i = R (i + 1) / n_radial, R = max |q| over the retained

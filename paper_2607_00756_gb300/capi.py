@@ -54,6 +54,7 @@ def _load():
         "bip_destroy": [VP],
         "bip_query": [VP, P(I32), P(I32), P(I32), P(I32), P(I32)],
         "bip_get_geometry": [VP, VP, VP, VP, VP, VP, VP],
+        "bip_get_config": [VP, P(BipConfig)],
         "bip_set_precision": [VP, I32],
         "bip_build_s1": [VP, VP, P(BipAtom), I32, VP],
         "bip_build_s2": [VP, VP, P(BipAtom), I32, VP],
@@ -176,6 +177,13 @@ def bip_get_geometry(ctx):
     return dict(h_beam=hb, h_det=hd, p1=p1, p2=p2, w1=w1, w2=w2)
 
 
+def bip_get_config(ctx):
+    """The context's configuration (a BipConfig)."""
+    c = BipConfig()
+    _check("bip_get_config", ctx, _lib.bip_get_config(ctx, ctypes.byref(c)))
+    return c
+
+
 def bip_set_precision(ctx, prec):
     p = PREC[prec] if isinstance(prec, str) else int(prec)
     _check("bip_set_precision", ctx, _lib.bip_set_precision(ctx, p))
@@ -200,10 +208,26 @@ def _scans(scans):
     return s, s.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def noalloc_stash_shape(ctx, atoms_arr):
+    """Shape [n_sites, Bp1, win, win] the caller's stash must have for
+    bip_build_s1_noalloc: n_sites counts the atoms with nch > 0, Bp1 and win
+    come from the context."""
+    n_sites = sum(1 for a in atoms_arr if a.nch > 0)
+    bp1 = bip_query(ctx)[2]
+    win = bip_get_config(ctx).win
+    return (n_sites, bp1, win, win)
+
+
 def bip_build_s1_noalloc(ctx, V, atoms_arr, stash, stream=None):
     """S1 build into the caller's `stash` [n_sites, Bp1, win, win] complex64
-    with no device allocation (scratch in the library's static array)."""
+    with no device allocation (scratch in the library's static array).  The
+    kernels write every element of that shape, so any other shape is
+    refused here, before a launch (the C entry point cannot see the
+    buffer's size)."""
     import torch
+    want = noalloc_stash_shape(ctx, atoms_arr)
+    if tuple(stash.shape) != want:
+        raise ValueError(f"stash must have shape {list(want)} (n_sites, Bp1, win, win), got {list(stash.shape)}")
     _check("bip_build_s1_noalloc", ctx,
            _lib.bip_build_s1_noalloc(ctx, _dev(V, torch.float32, "V"), atoms_arr, len(atoms_arr),
                                      _dev(stash, torch.complex64, "stash"), _stream(stream)))

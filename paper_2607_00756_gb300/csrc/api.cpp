@@ -588,6 +588,12 @@ bip_status bip_get_geometry(const bip_ctx* c, int32_t* h_beam, int32_t* h_det, i
     return BIP_OK;
 }
 
+bip_status bip_get_config(const bip_ctx* c, bip_config* out) {
+    if (!c || !out) return BIP_ERR_INVALID_ARG;
+    *out = c->cfg;
+    return BIP_OK;
+}
+
 bip_status bip_set_precision(bip_ctx* c, int32_t prec) {
     if (!c) return BIP_ERR_INVALID_ARG;
     if (prec != BIP_PREC_FP32 && prec != BIP_PREC_SPLIT_BF16 && prec != BIP_PREC_MIXED &&

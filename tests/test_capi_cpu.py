@@ -193,3 +193,30 @@ def test_product_never_imports_the_oracle():
                             assert (node.module or "").split(".")[0] != "oracle", path
                 elif f.endswith((".cu", ".cuh", ".cpp", ".h")):
                     assert "oracle/" not in open(path).read(), path
+
+
+def test_noalloc_wrapper_refuses_wrong_stash_shape(capi):
+    """The allocation-free S1 build writes n_sites x Bp1 x win x win values
+    into the caller's stash, which the C entry point cannot size-check; the
+    binding refuses any other shape before anything is launched."""
+    torch = pytest.importorskip("torch")
+    cfg = synth.config1()
+    ctx = capi.bip_create(capi.make_config(cfg))
+    try:
+        atoms = capi.make_atoms(np.array([[5.0, 5.0, 2.0], [6.0, 6.0, 2.0], [1.0, 1.0, 0.0]]),
+                                np.array([3, 1, 0]))
+        bp1 = capi.bip_query(ctx)[2]
+        assert capi.noalloc_stash_shape(ctx, atoms) == (2, bp1, cfg.win, cfg.win)
+        assert capi.bip_get_config(ctx).win == cfg.win
+        V = torch.zeros((cfg.nz, cfg.ny, cfg.nx), dtype=torch.float32)
+        for shape in [(1, bp1, cfg.win, cfg.win), (2, bp1 - 1, cfg.win, cfg.win), (2, bp1, 32, 32),
+                      (2 * bp1 * cfg.win * cfg.win,)]:
+            small = torch.empty(shape, dtype=torch.complex64)
+            with pytest.raises(ValueError, match="stash must have shape"):
+                capi.bip_build_s1_noalloc(ctx, V, atoms, small)
+        # the right shape passes the size check and then meets the device check
+        ok = torch.empty((2, bp1, cfg.win, cfg.win), dtype=torch.complex64)
+        with pytest.raises(ValueError, match="CUDA tensor"):
+            capi.bip_build_s1_noalloc(ctx, V, atoms, ok)
+    finally:
+        capi.bip_destroy(ctx)
