@@ -716,7 +716,7 @@ def oracle_sample(cfg, sp, n_site_sample=10, n_slice_sample=20):
         S1 = obip.reconstruct(w1, geo.w1, geo.h_beam, iy, ix, cfg.ny, cfg.nx, +1, cfg.recon)
         S2 = obip.reconstruct(w2, geo.w2, geo.h_det, iy, ix, cfg.ny, cfg.nx, -1, cfg.recon)
         M = obip.coupling(S2, pr.H[k], S1)
-        obip.site_map(M, C, obip.crop_mask(pr, k, pr.scans), cfg.fy * cfg.fx)
+        obip.site_map(M, C, obip.crop_mask(pr, k, pr.scans), obip.detector_factor(pr))
     t_site = (time.perf_counter() - t1) / n_site_sample
     n_sites = len(pr.ion)
     t_full = t_build + n_sites * t_site

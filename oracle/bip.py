@@ -32,8 +32,19 @@ Passages followed, in the order the method takes them:
     lies in [-N/(2f), N/(2f)) on both axes.  Sum over sites in FP64 with
     exactly rounded summation (math.fsum).
 
+Output modes (Sec. 2.2.6):
+  * 4D cube: S1 partitioned, the exit exact on the complete output basis --
+    every beam inside the detector disc, unsubsampled -- through the
+    unpartitioned S2 columns (the reciprocity form of Algorithm 3's exit
+    multislice); no detector-side factor.  Algorithm 3 itself is here too,
+    by brute force (alg3_cube), with the full-grid partitioned probe;
+  * qEELS: the map's per-beam terms binned along one axis, with S2
+    partitioned on detector beams sampled at f = 1 along the resolved axis
+    (dfy or dfx = 1); the factor is the perpendicular subsampling.
+
 Parity unpinned (project readings with no paper value to check against):
-  * the detector-side factor f_y f_x at f > 1 (absolute map scale only);
+  * the detector-side factor (dfy dfx, by default f_y f_x) at f > 1
+    (absolute map scale only);
   * the hull-boundary rule of the weights (see geometry.py).
 """
 import math
@@ -181,6 +192,14 @@ def coupling(S2w, Hk, S1w):
     return np.stack([A @ (h.reshape(-1, 1) * Bm) for h in Hk])
 
 
+def detector_factor(prob: Problem):
+    """The detector-side factor of the map: (dfy dfx), the subsampling of
+    the detector beams (reading: a coarse detector sum is 1/(dfy dfx) of the
+    full one for an exit wave confined to the alias-free window, Poisson
+    summation mirroring the probe-side PRISM rescale, Sec. 2.2.2)."""
+    return prob.geo.dfy * prob.geo.dfx
+
+
 def illumination(prob: Problem, h_beam, psi_beam, scans):
     """c_b(rho) [B, P] (Eq. probe with the PRISM f_y f_x rescale)."""
     cfg = prob.cfg
@@ -260,7 +279,7 @@ def bip_map(prob: Problem, scans=None, mode=None, keep_stages=False, sites=None)
     W1 = s1_windows(prob, geo.h_p1, detilt=True)
     W2 = s2_windows(prob, geo.h_p2, detilt=True)
     C = illumination(prob, geo.h_beam, geo.psi_beam, scans)
-    fyfx = cfg.fy * cfg.fx
+    fyfx = detector_factor(prob)
     sites = range(len(prob.ion)) if sites is None else sites
     partials, stages = [], {}
     for k in sites:
@@ -276,9 +295,11 @@ def bip_map(prob: Problem, scans=None, mode=None, keep_stages=False, sites=None)
     return MapResult(sum_sites(partials), partials, stages)
 
 
-def bip_cube(prob: Problem, scans=None, mode=None):
-    """Algorithm 5 with the detector sum left open: the 4D cube [P, n_det]
-    (detector beams in geometry order), sites added in order in FP64."""
+def per_beam(prob: Problem, scans=None, mode=None):
+    """Algorithm 5's terms with the detector sum left open, on the context's
+    (partitioned, subsampled) detector beams: [P, n_det] with entries
+    (dfy dfx) sum_tau sum_n |a_d|^2 -- the momentum-resolved intensities
+    qEELS bins (Sec. 2.2.6).  Summed over d this is the map."""
     cfg, geo = prob.cfg, prob.geo
     mode = mode or cfg.recon
     scans = prob.scans if scans is None else np.asarray(scans, dtype=np.float64)
@@ -291,34 +312,82 @@ def bip_cube(prob: Problem, scans=None, mode=None):
         S1w = reconstruct(W1[k], geo.w1, geo.h_beam, iy, ix, cfg.ny, cfg.nx, +1, mode)
         S2w = reconstruct(W2[k], geo.w2, geo.h_det, iy, ix, cfg.ny, cfg.nx, -1, mode)
         M = coupling(S2w, prob.H[k], S1w)
-        out += site_cube(M, C, crop_mask(prob, k, scans), cfg.fy * cfg.fx)
+        out += site_cube(M, C, crop_mask(prob, k, scans), detector_factor(prob))
     return out
 
 
-def qeels(prob: Problem, cube, axis):
-    """Momentum-resolved output (qEELS): the cube summed over the detector
-    beams that share their component along `axis` (0: h_y, 1: h_x) -- one
-    resolved axis q_par, the perpendicular one summed.  Returns the bin
-    values h_par (ascending) and [P, n_bins] (Sec. 2.2.6 outputs)."""
+def qeels_bins(prob: Problem, axis):
+    """Bin values h_par (ascending) of the resolved axis and each detector
+    beam's bin, for axis 0 (q_y resolved) or 1 (q_x resolved)."""
     h = np.asarray(prob.geo.h_det)[:, axis]
     bins = np.unique(h)
+    return bins, np.searchsorted(bins, h)
+
+
+def bip_qeels(prob: Problem, axis, scans=None, mode=None):
+    """Momentum-resolved qEELS (Sec. 2.2.6): one diffraction axis resolved,
+    the perpendicular one summed, I(q_par, rho) = (df_perp) sum over the
+    detector beams with that h_par of sum_tau sum_n |a_d|^2.  S2 stays
+    partitioned (its detector basis is rebuilt from parents whatever the
+    binning), which the paper allows only with the resolved axis sampled at
+    f = 1: a geometry whose detector beams are subsampled along `axis` is
+    refused.  Returns (bins, [P, n_bins])."""
+    d_axis = prob.geo.dfy if axis == 0 else prob.geo.dfx
+    if axis not in (0, 1):
+        raise ValueError("axis must be 0 (q_y) or 1 (q_x)")
+    if d_axis != 1:
+        raise ValueError("qEELS needs the resolved axis sampled at f = 1 (dfy or dfx = 1)")
+    cube = per_beam(prob, scans, mode)
+    bins, bin_of = qeels_bins(prob, axis)
     out = np.zeros((cube.shape[0], len(bins)), dtype=np.float64)
-    for i, q in enumerate(bins):
-        out[:, i] = cube[:, h == q].sum(axis=1)
+    for i in range(len(bins)):
+        out[:, i] = cube[:, bin_of == i].sum(axis=1)
     return bins, out
 
 
-def exact_cube(prob: Problem, scans=None):
-    """Algorithm 4 with the detector sum left open, [P, n_det]."""
+def bip_cube(prob: Problem, scans=None, mode=None):
+    """Energy-filtered 4D cube (Sec. 2.2.6, Algorithm 3): S1 partitioned and
+    rebuilt on each window (Eq. window-recon, magpreserve), the exit side
+    exact on the complete output basis -- every beam inside the detector disc
+    at the grid's own sampling (geo.h_cube), S2 neither partitioned nor
+    subsampled, since the cube keeps every output beam.  The exit amplitude
+    of each beam is taken through the unpartitioned S2 column (Eq. s2, the
+    reciprocity form of Algorithm 3's exit multislice):
+      cube[rho][q] = sum_tau sum_n |sum_b M_{q,b} c_b(rho)|^2,
+      M_{q,b} = sum_{r in window} S2^q(r) H_n(r) S~1^b(r),
+    over the sites whose crop mask holds rho; no detector-side factor (the
+    basis is not subsampled).  Returns [P, n_cube], beams in geo.h_cube
+    order."""
+    cfg, geo = prob.cfg, prob.geo
+    mode = mode or cfg.recon
+    scans = prob.scans if scans is None else np.asarray(scans, dtype=np.float64)
+    W1 = s1_windows(prob, geo.h_p1, detilt=True)
+    W2 = s2_windows(prob, geo.h_cube, detilt=False)
+    C = illumination(prob, geo.h_beam, geo.psi_beam, scans)
+    out = np.zeros((len(scans), len(geo.h_cube)), dtype=np.float64)
+    for k in range(len(prob.ion)):
+        iy, ix = prob.window_index(k)
+        S1w = reconstruct(W1[k], geo.w1, geo.h_beam, iy, ix, cfg.ny, cfg.nx, +1, mode)
+        M = coupling(W2[k], prob.H[k], S1w)
+        out += site_cube(M, C, crop_mask(prob, k, scans), 1)
+    return out
+
+
+def exact_cube(prob: Problem, scans=None, det_h=None):
+    """The cube's exact reference (Algorithm 2 with the exit exact): every
+    retained aperture beam propagated (no parents, no weights), S2 exact at
+    the beams det_h (default: the complete output basis geo.h_cube), the
+    crop mask as in the map, no detector-side factor; [P, len(det_h)]."""
     cfg, geo = prob.cfg, prob.geo
     scans = prob.scans if scans is None else np.asarray(scans, dtype=np.float64)
+    det_h = geo.h_cube if det_h is None else np.asarray(det_h)
     W1 = s1_windows(prob, geo.h_beam, detilt=False)
-    W2 = s2_windows(prob, geo.h_det, detilt=False)
+    W2 = s2_windows(prob, det_h, detilt=False)
     C = illumination(prob, geo.h_beam, geo.psi_beam, scans)
-    out = np.zeros((len(scans), geo.n_det), dtype=np.float64)
+    out = np.zeros((len(scans), len(det_h)), dtype=np.float64)
     for k in range(len(prob.ion)):
         M = coupling(W2[k], prob.H[k], W1[k])
-        out += site_cube(M, C, crop_mask(prob, k, scans), cfg.fy * cfg.fx)
+        out += site_cube(M, C, crop_mask(prob, k, scans), 1)
     return out
 
 
@@ -330,7 +399,7 @@ def exact_map(prob: Problem, scans=None, keep_stages=False):
     W1 = s1_windows(prob, geo.h_beam, detilt=False)
     W2 = s2_windows(prob, geo.h_det, detilt=False)
     C = illumination(prob, geo.h_beam, geo.psi_beam, scans)
-    fyfx = cfg.fy * cfg.fx
+    fyfx = detector_factor(prob)
     partials, stages = [], {}
     for k in range(len(prob.ion)):
         M = coupling(W2[k], prob.H[k], W1[k])
@@ -394,11 +463,11 @@ def conventional_map(prob: Problem, scans=None, det_h=None):
 
 def conventional_cube(prob: Problem, scans=None, det_h=None):
     """Algorithm 1 per detector beam: [P, n_det] intensities |F_u .|^2 at the
-    detector beams det_h (default: the geometry's detector beams, in order)
-    summed over sites and channels."""
+    detector beams det_h (default: the cube's complete output basis, in
+    order) summed over sites and channels."""
     cfg, geo = prob.cfg, prob.geo
     scans = prob.scans if scans is None else np.asarray(scans, dtype=np.float64)
-    det_h = geo.h_det if det_h is None else det_h
+    det_h = geo.h_cube if det_h is None else det_h
     dsel = (det_h[:, 0] % cfg.ny, det_h[:, 1] % cfg.nx)
     Hfull = {k: full_grid_H(prob, k) for k in range(len(prob.ion))}
     out = np.zeros((len(scans), len(det_h)))
@@ -412,6 +481,89 @@ def conventional_cube(prob: Problem, scans=None, det_h=None):
                     out[p] += np.abs(a) ** 2
             psi = ph.step(psi, prob.T(i), prob.P)
     return out
+
+
+# --------------------------------------------------------------------------
+# Algorithm 3 (partitioned S1, exit by multislice) and its probes, on the
+# full grid: the brute-force form the cube and the locality result are
+# checked with
+
+def s1_columns(prob: Problem, h_cols, plane):
+    """S1 columns on the full grid at `plane`: unit plane waves
+    e^{2 pi i h.r/N} advanced by psi -> P(T_j psi) for j < plane
+    (Eq. smatrix-advance), [n_cols, ny, nx]."""
+    cfg = prob.cfg
+    psi = np.stack([ph.plane_wave(h, cfg.ny, cfg.nx, +1) for h in np.asarray(h_cols, dtype=np.int64)])
+    for j in range(plane):
+        psi = ph.step(psi, prob.T(j), prob.P)
+    return psi
+
+
+def prism_probe(prob: Problem, scans, plane):
+    """Eq. prism-probe: psi(r, rho) = sum_b c_b(rho) S_b(r) with every
+    retained aperture beam propagated (Algorithm 2), [P, ny, nx]."""
+    geo = prob.geo
+    cols = s1_columns(prob, geo.h_beam, plane)
+    C = illumination(prob, geo.h_beam, geo.psi_beam, np.asarray(scans, dtype=np.float64))
+    return np.tensordot(C.T, cols, axes=(1, 0))
+
+
+def partitioned_probe(prob: Problem, scans, plane, mode=None):
+    """Algorithm 3's probe at `plane`, [P, ny, nx]: the parent columns
+    advanced and de-tilted (Eq. part-basis), every aperture beam's column
+    rebuilt from them by Eq. window-recon -- with Eq. magpreserve in the
+    magnitude mode -- taken over the whole grid instead of a window, then
+    psi(r, rho) = sum_b c_b(rho) S~_b(r) (Eq. prism-probe)."""
+    cfg, geo = prob.cfg, prob.geo
+    mode = mode or cfg.recon
+    iy, ix = np.arange(cfg.ny), np.arange(cfg.nx)
+    dt = s1_columns(prob, geo.h_p1, plane) * window_phase(geo.h_p1, iy, ix, cfg.ny, cfg.nx, -1)
+    S1 = reconstruct(dt, geo.w1, geo.h_beam, iy, ix, cfg.ny, cfg.nx, +1, mode)
+    C = illumination(prob, geo.h_beam, geo.psi_beam, np.asarray(scans, dtype=np.float64))
+    return np.tensordot(C.T, S1, axes=(1, 0))
+
+
+def alg3_cube(prob: Problem, scans=None, det_h=None, probe=None, h_full=None):
+    """Algorithm 3 by brute force, [P, len(det_h)]: at each site's plane the
+    probe of every scan (partitioned_probe unless `probe(scans, plane)` is
+    given), each channel's inelastic wave H_n psi taken to the exit by
+    multislice (M_{i->exit}) and |F_u .|^2 read at the beams det_h (default:
+    the complete output basis geo.h_cube), summed over channels and over the
+    sites whose crop mask holds the scan.  `h_full(k)` gives site k's
+    channels on the whole grid (default: the window samples, zero
+    elsewhere)."""
+    cfg, geo = prob.cfg, prob.geo
+    scans = prob.scans if scans is None else np.asarray(scans, dtype=np.float64)
+    det_h = geo.h_cube if det_h is None else np.asarray(det_h)
+    dsel = (det_h[:, 0] % cfg.ny, det_h[:, 1] % cfg.nx)
+    if probe is None:
+        probe = lambda sc, plane: partitioned_probe(prob, sc, plane)
+    if h_full is None:
+        h_full = lambda k: full_grid_H(prob, k)
+    out = np.zeros((len(scans), len(det_h)), dtype=np.float64)
+    for plane in sorted(set(prob.plane.tolist())):
+        psi = probe(scans, plane)
+        for k in np.nonzero(prob.plane == plane)[0]:
+            sel = np.nonzero(crop_mask(prob, k, scans))[0]
+            if len(sel) == 0:
+                continue
+            for Hn in h_full(k):
+                e = exit_operator(prob, Hn[None] * psi[sel], plane)
+                out[sel] += np.abs(ph.unitary_dft(e)[:, dsel[0], dsel[1]]) ** 2
+    return out
+
+
+def on_atom_error(prob: Problem, k, scans, mode=None):
+    """Eq. onatom for site k at every scan: ||psi_p - psi||_Omega /
+    ||psi||_Omega on the site's window, psi_p the partitioned probe
+    (Algorithm 3) and psi the exact PRISM probe (Eq. prism-probe) at the
+    site's plane."""
+    plane = int(prob.plane[k])
+    iy, ix = prob.window_index(k)
+    pp = partitioned_probe(prob, scans, plane, mode)[:, iy[:, None], ix[None, :]]
+    pe = prism_probe(prob, scans, plane)[:, iy[:, None], ix[None, :]]
+    num = np.sqrt(np.sum(np.abs(pp - pe) ** 2, axis=(1, 2)))
+    return num / np.sqrt(np.sum(np.abs(pe) ** 2, axis=(1, 2)))
 
 
 def elastic_probe_at(prob: Problem, rho, plane):

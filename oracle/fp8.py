@@ -96,7 +96,7 @@ def _fp8_sites(prob, scans, mode, per_site):
         S1w = bip.reconstruct(W1[k], geo.w1, geo.h_beam, iy, ix, cfg.ny, cfg.nx, +1, mode)
         S2w = bip.reconstruct(W2[k], geo.w2, geo.h_det, iy, ix, cfg.ny, cfg.nx, -1, mode)
         M = site_coupling_fp8(S2w, prob.H[k], S1w, geo.w2, W2[k], geo.w1, W1[k])
-        out.append(per_site(M, C, bip.crop_mask(prob, k, scans), cfg.fy * cfg.fx))
+        out.append(per_site(M, C, bip.crop_mask(prob, k, scans), bip.detector_factor(prob)))
     return out
 
 
@@ -109,8 +109,9 @@ def bip_map_fp8(prob, scans=None, mode=None):
     return bip.MapResult(bip.sum_sites(partials), partials)
 
 
-def bip_cube_fp8(prob, scans=None, mode=None):
-    """The 4D cube (bip.bip_cube) with the FP8 coupling, [P, n_det]."""
+def per_beam_fp8(prob, scans=None, mode=None):
+    """The per-detector-beam intensities qEELS bins (bip.per_beam) with the
+    FP8 coupling, [P, n_det]."""
     scans = prob.scans if scans is None else np.asarray(scans, dtype=np.float64)
     out = np.zeros((len(scans), prob.geo.n_det), dtype=np.float64)
     for c in _fp8_sites(prob, scans, mode, bip.site_cube):

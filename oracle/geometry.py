@@ -5,7 +5,10 @@ Paper passages followed:
     probe and specimen"), PRISM subsampling h_y = 0 mod f_y, h_x = 0 mod f_x
     (Algorithm 2, build step; Sec. 2.2.2 "Beam subsampling");
   * detector beams |q| <= theta_det / lambda, PRISM-subsampled (Algorithm 4,
-    first step);
+    first step) -- by the probe's f, or along one axis by 1 for qEELS, whose
+    resolved axis must be sampled at f = 1 (Sec. 2.2.6);
+  * the cube's complete output basis: every beam inside the detector disc,
+    no subsampling (Sec. 2.2.6);
   * hex-ring parents: the DC beam plus n_radial rings with n_angular (1 + i)
     samples on ring i, snapped to the nearest beam and deduplicated
     (Sec. 2.2.3 "Parent selection"; Algorithm 3 build step);
@@ -252,6 +255,15 @@ def sibson_weights(parent_h, query_h, ly, lx):
 # --------------------------------------------------------------------------
 # bundled geometry for a configuration
 
+def detector_subsampling(cfg):
+    """(dfy, dfx): the subsampling of the detector beams (h = 0 mod df); a
+    configuration without dfy/dfx, or with 0, takes the probe's (fy, fx)
+    (Algorithm 4, first step: the output beams PRISM-subsampled)."""
+    dfy = getattr(cfg, "dfy", 0) or cfg.fy
+    dfx = getattr(cfg, "dfx", 0) or cfg.fx
+    return int(dfy), int(dfx)
+
+
 class Geometry:
     """All host geometry of one configuration (Algorithm 5, build steps)."""
 
@@ -262,7 +274,13 @@ class Geometry:
         # full aperture (for the probe normalisation) and retained beams
         self.h_full = disc_beams(ny, nx, ly, lx, lam, cfg.alpha)
         self.h_beam = disc_beams(ny, nx, ly, lx, lam, cfg.alpha, cfg.fy, cfg.fx)
-        self.h_det = disc_beams(ny, nx, ly, lx, lam, cfg.theta_det, cfg.fy, cfg.fx)
+        # detector beams: subsampled by (dfy, dfx), 0 meaning the probe's f
+        # (qEELS resolves one axis at 1 there, Sec. 2.2.6)
+        self.dfy, self.dfx = detector_subsampling(cfg)
+        self.h_det = disc_beams(ny, nx, ly, lx, lam, cfg.theta_det, self.dfy, self.dfx)
+        # the 4D cube's complete output basis: every beam inside the detector
+        # disc, unsubsampled (Sec. 2.2.6: S2 cannot be reduced for the cube)
+        self.h_cube = disc_beams(ny, nx, ly, lx, lam, cfg.theta_det)
         self.psi_full = aperture_function(self.h_full, ly, lx, lam, cfg.defocus, cfg.cs)
         self.psi_beam = aperture_function(self.h_beam, ly, lx, lam, cfg.defocus, cfg.cs)
         if parents_override is None:

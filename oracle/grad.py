@@ -144,7 +144,7 @@ def forward(prob, params, scans=None, mode=None, keep=False):
     coef, dchi = _coef(prob, params.defocus, params.cs)
     E = _scan_phase(prob, scans)
     C = coef[:, None] * E
-    fyfx = cfg.fy * cfg.fx
+    fyfx = bip.detector_factor(prob)
     sites, partials = [], []
     for k in range(len(prob.ion)):
         iy, ix = prob.window_index(k)
@@ -188,7 +188,7 @@ def gradients(prob, params, target=None, scans=None, mode=None, dL_dI=None, want
     else:
         g = np.asarray(dL_dI, dtype=np.float64)
         L = None
-    fyfx = cfg.fy * cfg.fx
+    fyfx = bip.detector_factor(prob)
     C = fw["C"]
     n_ion = len(prob.ion)
     out = {"occ": fw["partials"] @ g, "amp": np.zeros_like(params.amp), "H": [], "defocus": 0.0, "cs": 0.0}

@@ -102,6 +102,6 @@ def bip_map_mixed(prob, scans=None, mode=None, parents="fp16"):
         S1w = reconstruct_mixed(W1[k], geo.w1, geo.h_beam, iy, ix, cfg.ny, cfg.nx, +1, mode, parents)
         S2w = reconstruct_mixed(W2[k], geo.w2, geo.h_det, iy, ix, cfg.ny, cfg.nx, -1, mode, parents)
         M = site_coupling_mixed(S2w, prob.H[k], S1w)
-        partials.append(bip.site_map(M, C, bip.crop_mask(prob, k, scans), cfg.fy * cfg.fx))
+        partials.append(bip.site_map(M, C, bip.crop_mask(prob, k, scans), bip.detector_factor(prob)))
     partials = np.array(partials).reshape(len(partials), len(scans))
     return bip.MapResult(bip.sum_sites(partials), partials)

@@ -24,6 +24,10 @@ class Config:
     cs: float = 0.0
     fy: int = 1
     fx: int = 1
+    # detector-side subsampling of the beams S2 carries (0: fy, fx); qEELS
+    # along x wants dfx = 1, along y dfy = 1
+    dfy: int = 0
+    dfx: int = 0
     nrad1: int = 2
     nang1: int = 6
     nrad2: int = 2

@@ -108,10 +108,10 @@ def test_fp8_map_close_to_but_not_the_fp64_map(case):
     assert 1e-4 < rel < 2e-2, rel
 
 
-def test_fp8_cube_sums_to_fp8_map(case):
-    """The FP8 model's cube summed over the detector is its map (the same
-    coupling feeds both)."""
+def test_fp8_per_beam_sums_to_fp8_map(case):
+    """The FP8 model's per-beam intensities (what qEELS bins) summed over
+    the detector are its map (the same coupling feeds both)."""
     m = fp8.bip_map_fp8(case).map
-    c = fp8.bip_cube_fp8(case)
+    c = fp8.per_beam_fp8(case)
     assert c.shape == (len(case.scans), case.geo.n_det)
     assert np.max(np.abs(c.sum(axis=1) - m)) <= 1e-12 * np.max(np.abs(m))

@@ -222,7 +222,7 @@ def test_subsampling_scale_consistency_f3():
 
 
 # ---------------------------------------------------------------------------
-# the 4D cube (Sec. 2.2.6): the same terms with the detector sum left open
+# per-beam terms (the cube's and qEELS's own pins: test_oracle_outputs.py)
 
 def test_cube_alg4_equals_conventional_per_beam():
     """Pin 4 beam by beam: at f = 1 with a window covering the grid, the
@@ -237,38 +237,6 @@ def test_cube_alg4_equals_conventional_per_beam():
     assert rel(a4, a1) < 1e-11
     # the detector sum of either is the map
     assert rel(a1.sum(axis=1), bip.conventional_map(pr)) < 1e-13
-
-
-def test_cube_sums_to_map(c1):
-    """The detector sum of the Algorithm 5 cube is the Algorithm 5 map."""
-    sp, pr, _ = c1
-    cube = bip.bip_cube(pr)
-    assert np.all(cube >= 0.0)
-    assert rel(cube.sum(axis=1), bip.bip_map(pr).map) < 1e-13
-
-
-def test_cube_full_parent_limit(c1):
-    """Every beam its own parent: the Algorithm 5 cube is the exact cube."""
-    sp, pr, _ = c1
-    geo = G.Geometry(pr.cfg, pr.lam, parents_override=(np.arange(pr.geo.B), np.arange(pr.geo.n_det)))
-    prf = bip.make_problem(sp, geometry=geo)
-    assert rel(bip.bip_cube(prf), bip.exact_cube(pr)) < 1e-12
-
-
-@pytest.mark.parametrize("axis", [0, 1])
-def test_qeels_bins_and_invariant(c1, axis):
-    """qEELS: every detector beam lands in the bin of its component along
-    the resolved axis; the resolved axis summed recovers the map."""
-    sp, pr, _ = c1
-    cube = bip.bip_cube(pr)
-    bins, q = bip.qeels(pr, cube, axis)
-    h = pr.geo.h_det[:, axis]
-    assert np.all(np.diff(bins) > 0) and set(bins.tolist()) == set(h.tolist())
-    assert np.all(bins % (pr.cfg.fy if axis == 0 else pr.cfg.fx) == 0)
-    assert rel(q.sum(axis=1), bip.bip_map(pr).map) < 1e-13
-    # one bin by hand
-    i = len(bins) // 2
-    assert np.allclose(q[:, i], cube[:, h == bins[i]].sum(axis=1), rtol=1e-14, atol=0)
 
 
 def test_golden_config1_map_is_the_oracles():
