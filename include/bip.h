@@ -95,7 +95,8 @@ typedef struct {
 
 /* Simulation parameters (lengths in Angstrom, angles in rad, energy in eV).
  * Constraints checked by bip_create: ny, nx powers of two in [64, 1024];
- * fy | ny and fx | nx; win a multiple of 16 with 16 <= win <=
+ * fy | ny and fx | nx; dfy, dfx 0 or dividing ny, nx; win a multiple of
+ * 16 with 16 <= win <=
  * min(ny/fy, nx/fx); nz >= 1;
  * e0 > 0; 0 < alpha; 0 < theta_det; nrad >= 0; nang >= 1; the aperture and
  * detector discs fit inside the grid's Nyquist band. */
@@ -111,13 +112,20 @@ typedef struct {
     int32_t win;
     int32_t recon;             /* bip_recon     */
     int32_t prec;              /* bip_precision */
+    /* detector-side subsampling of the beams S2 carries (h_y = 0 mod dfy,
+     * h_x = 0 mod dfx); 0 takes the probe's fy, fx.  qEELS resolved along
+     * q_x needs dfx = 1 (along q_y: dfy = 1); the map's detector factor is
+     * dfy dfx. */
+    int32_t dfy, dfx;
 } bip_config;
 
 /* Host geometry (Algorithm 5 build steps; Sec. 2.2.2-2.2.3, Eq. nnw):
  * aperture beams |q| lambda <= alpha with h = 0 mod f, detector beams
- * |q| lambda <= theta_det with h = 0 mod f, hex-ring parents for both and
- * FP64 Sibson natural-neighbour weights, computed once and cached in the
- * context.  Host only: touches no GPU.  *out receives the new context. */
+ * |q| lambda <= theta_det with h = 0 mod (dfy, dfx), hex-ring parents for
+ * both and FP64 Sibson natural-neighbour weights, computed once and cached
+ * in the context; and the 4D cube's complete output basis, every beam with
+ * |q| lambda <= theta_det (no subsampling).  Host only: touches no GPU.
+ * *out receives the new context. */
 bip_status bip_create(const bip_config* cfg, bip_ctx** out);
 
 /* Releases the context and every device workspace it holds.  The caller
@@ -190,27 +198,47 @@ bip_status bip_coreloss_map(bip_ctx* ctx, const void* H, const double* scan_px,
 bip_status bip_coreloss_sites(bip_ctx* ctx, const void* H, const double* scan_px,
                               int32_t P, float* partial_out, void* stream);
 
-/* Energy-filtered 4D cube I(q, rho) (Sec. 2.2.6): the terms of Eq. map-sum
- * with the detector sum left open,
- *   cube[rho][d] = f_y f_x sum_sites sum_n |sum_b M^{(n)}_{d,b} c_b(rho)|^2
- * over the sites whose crop mask holds rho; detector beams d in the order of
- * bip_get_geometry.  Its detector sum is the map (up to FP32 rounding).
- *   cube_out [P, n_det] float32 device, overwritten.
- * The per-beam values carry the S2 reconstruction error of the context's
- * parent set; with every detector beam a parent they are exact.  Sites are
- * added in a fixed order (deterministic).  Requirements as bip_coreloss_map. */
-bip_status bip_coreloss_cube(bip_ctx* ctx, const void* H, const double* scan_px,
+/* Energy-filtered 4D cube I(q, rho) (Sec. 2.2.6; Algorithm 3): the cube
+ * keeps every output beam, so S2 is not reduced.  S1 stays partitioned (the
+ * context's bip_build_s1 windows, rebuilt per site as for the map); the exit
+ * side is exact on the complete basis -- every beam with |q| lambda <=
+ * theta_det, unsubsampled (bip_cube_beams) -- through unpartitioned S2
+ * columns (Eq. s2, the reciprocity form of Algorithm 3's exit multislice):
+ *   cube[rho][q] = sum_sites sum_n |sum_b M^(n)_{q,b} c_b(rho)|^2,
+ *   M^(n)_{q,b} = sum_{r in window} S2^q(r) H_n(r) S~1^b(r),
+ * over the sites whose crop mask holds rho; no detector-side factor.  The
+ * call builds the S2 columns itself, in batches of beams (one backward
+ * sweep each, every site's window kept for the batch), sized to half the
+ * free device memory (at most 96 GB; bip_set_cube_memory sets the bytes);
+ * it needs bip_build_s1 on this context (bip_build_s2 is not used).  Sites
+ * are added in a fixed order and every element has one writer per launch:
+ * the result does not depend on scheduling.
+ *   V        [nz, ny, nx] float32 device, the potential S1 was built from.
+ *   H, scan_px as bip_coreloss_map.
+ *   cube_out [P, n_cube] float32 device, overwritten; beams in the order of
+ *            bip_cube_beams.
+ * Precisions: FP32 (SIMT), SPLIT_BF16 and MIXED (tcgen05); FP8 contexts
+ * return BIP_ERR_UNSUPPORTED.  BIP_ERR_OOM when not even 32 beams fit.
+ * bip_cube_beams: n_cube and (h, nullable host int32 [n_cube, 2]) the
+ *   basis's beams (h_y, h_x), ordered by (h_y, h_x).  Host only. */
+bip_status bip_coreloss_cube(bip_ctx* ctx, const float* V, const void* H, const double* scan_px,
                              int32_t P, float* cube_out, void* stream);
+bip_status bip_cube_beams(const bip_ctx* ctx, int32_t* n_cube, int32_t* h);
+bip_status bip_set_cube_memory(bip_ctx* ctx, int64_t bytes);
 
-/* Momentum-resolved output (qEELS, Sec. 2.2.6): the cube above summed over
- * the detector beams that share their component along one axis,
- *   qeels[rho][i] = sum_{d : h_d[axis] = bins[i]} cube[rho][d],
- * axis 0: resolved along q_y (h_y), 1: along q_x; bins ascending.  Its sum
- * over the bins is the map.
+/* Momentum-resolved output (qEELS, Sec. 2.2.6): one diffraction axis
+ * resolved, the perpendicular one summed,
+ *   qeels[rho][i] = dfy dfx sum_sites sum_n sum_{d : h_d[axis] = bins[i]}
+ *                   |sum_b M^(n)_{d,b} c_b(rho)|^2,
+ * with S2 partitioned as for the map -- which the paper allows only with
+ * the resolved axis sampled at f = 1: axis 0 (q_y resolved) needs a context
+ * created with dfy = 1, axis 1 (q_x) with dfx = 1 (else
+ * BIP_ERR_INVALID_ARG).  The bins partition the detector beams, so their
+ * sum is the map of the same context.  Sites are added in a fixed order.
  *   bip_qeels_bins: the number of bins and (h_values, nullable host int32
- *   [n_bins]) their h components.  Host only.
+ *   [n_bins]) their h components, ascending.  Host only.
  *   qeels_out [P, n_bins] float32 device, overwritten.
- * BIP_ERR_INVALID_ARG for another axis; requirements as bip_coreloss_map. */
+ * Other requirements as bip_coreloss_map. */
 bip_status bip_qeels_bins(const bip_ctx* ctx, int32_t axis, int32_t* n_bins, int32_t* h_values);
 bip_status bip_coreloss_qeels(bip_ctx* ctx, const void* H, const double* scan_px, int32_t P,
                               int32_t axis, float* qeels_out, void* stream);
@@ -253,9 +281,9 @@ bip_status bip_autotune(bip_ctx* ctx, const void* H, const double* scan_px, int3
  * Psi(rho, r) and |a|^2 summed over d and n as in beam order -- the cheapest
  * order when few scans meet each site (work ~ P instead of the coupling's
  * n_det nch B); mixed precision only (else BIP_ERR_UNSUPPORTED), at most
- * 2048 scans per map (BIP_ERR_UNSUPPORTED from the map).  Beam and probe
- * order add the terms of a site's map atomically, so its last bits may vary
- * from run to run.  bip_autotune also times the other orders. */
+ * 2048 scans per map (BIP_ERR_UNSUPPORTED from the map).  Every order
+ * sums in a fixed order (no floating-point atomics), so a map does not
+ * depend on scheduling.  bip_autotune also times the other orders. */
 bip_status bip_set_order(bip_ctx* ctx, int32_t order);
 
 /* Model parameters of the map beyond the specimen (for fitting; Sec. 5

@@ -30,7 +30,8 @@ class BipConfig(ctypes.Structure):
                 ("fy", ctypes.c_int32), ("fx", ctypes.c_int32),
                 ("nrad1", ctypes.c_int32), ("nang1", ctypes.c_int32),
                 ("nrad2", ctypes.c_int32), ("nang2", ctypes.c_int32),
-                ("win", ctypes.c_int32), ("recon", ctypes.c_int32), ("prec", ctypes.c_int32)]
+                ("win", ctypes.c_int32), ("recon", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("dfy", ctypes.c_int32), ("dfx", ctypes.c_int32)]
 
 
 class BipAtom(ctypes.Structure):
@@ -60,7 +61,9 @@ def _load():
         "bip_build_s2": [VP, VP, P(BipAtom), I32, VP],
         "bip_coreloss_map": [VP, VP, P(D), I32, VP, VP],
         "bip_coreloss_sites": [VP, VP, P(D), I32, VP, VP],
-        "bip_coreloss_cube": [VP, VP, P(D), I32, VP, VP],
+        "bip_coreloss_cube": [VP, VP, VP, P(D), I32, VP, VP],
+        "bip_cube_beams": [VP, P(I32), P(I32)],
+        "bip_set_cube_memory": [VP, ctypes.c_int64],
         "bip_qeels_bins": [VP, I32, P(I32), P(I32)],
         "bip_coreloss_qeels": [VP, VP, P(D), I32, I32, VP, VP],
         "bip_copy_stash": [VP, I32, I32, VP, VP],
@@ -124,7 +127,7 @@ def make_config(cfg, prec=None, recon=None):
     for name, _ in BipConfig._fields_:
         if name in ("recon", "prec"):
             continue
-        setattr(c, name, getattr(cfg, name))
+        setattr(c, name, getattr(cfg, name, 0) if name in ("dfy", "dfx") else getattr(cfg, name))
     r = recon if recon is not None else getattr(cfg, "recon", "magnitude")
     p = prec if prec is not None else getattr(cfg, "prec", "fp32")
     c.recon = RECON[r] if isinstance(r, str) else int(r)
@@ -250,12 +253,27 @@ def bip_coreloss_sites(ctx, H, scans, out, stream=None):
     return out
 
 
-def bip_coreloss_cube(ctx, H, scans, out, stream=None):
+def bip_coreloss_cube(ctx, V, H, scans, out, stream=None):
     import torch
     s, sp = _scans(scans)
-    _check("bip_coreloss_cube", ctx, _lib.bip_coreloss_cube(ctx, _dev(H, torch.complex64, "H"), sp, len(s),
+    _check("bip_coreloss_cube", ctx, _lib.bip_coreloss_cube(ctx, _dev(V, torch.float32, "V"),
+                                                             _dev(H, torch.complex64, "H"), sp, len(s),
                                                              _dev(out, torch.float32, "out"), _stream(stream)))
     return out
+
+
+def bip_cube_beams(ctx):
+    """The cube's complete basis, [n_cube, 2] int32 (h_y, h_x)."""
+    n = ctypes.c_int32(0)
+    _check("bip_cube_beams", ctx, _lib.bip_cube_beams(ctx, ctypes.byref(n), None))
+    h = np.zeros((n.value, 2), dtype=np.int32)
+    _check("bip_cube_beams", ctx, _lib.bip_cube_beams(ctx, ctypes.byref(n),
+                                                       h.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return h
+
+
+def bip_set_cube_memory(ctx, nbytes):
+    _check("bip_set_cube_memory", ctx, _lib.bip_set_cube_memory(ctx, int(nbytes)))
 
 
 def bip_qeels_bins(ctx, axis):

@@ -50,17 +50,29 @@ class BipContext:
             out = torch.empty(len(scans), dtype=torch.float64, device=H.device)
         return capi.bip_coreloss_map(self.ctx, H, scans, out, stream)
 
-    def cube(self, H, scans, out=None, stream=None):
-        """The 4D cube [P, n_det] (detector beams in geometry order); its
-        detector sum is the map."""
+    @property
+    def cube_beams(self):
+        """The cube's complete output basis, [n_cube, 2] (h_y, h_x)."""
+        return capi.bip_cube_beams(self.ctx)
+
+    def cube(self, V, H, scans, out=None, stream=None):
+        """The 4D cube [P, n_cube] on the complete output basis (S1
+        partitioned, the exit exact; needs the S1 build and the potential V
+        it was built from)."""
         scans = np.asarray(scans, dtype=np.float64)
         if out is None:
-            out = torch.empty((len(scans), self.n_det), dtype=torch.float32, device=H.device)
-        return capi.bip_coreloss_cube(self.ctx, H, scans, out, stream)
+            out = torch.empty((len(scans), len(self.cube_beams)), dtype=torch.float32, device=H.device)
+        return capi.bip_coreloss_cube(self.ctx, V, H, scans, out, stream)
+
+    def set_cube_memory(self, nbytes):
+        """Device bytes the cube may take per batch of exact S2 columns (0: half
+        the free memory, at most 96 GB)."""
+        capi.bip_set_cube_memory(self.ctx, nbytes)
 
     def qeels(self, H, scans, axis, out=None, stream=None):
         """Momentum-resolved output: (bin h values, [P, n_bins]) resolved along
-        axis 0 (q_y) or 1 (q_x); its sum over the bins is the map."""
+        axis 0 (q_y; the context needs dfy = 1) or 1 (q_x; dfx = 1); its sum
+        over the bins is the map."""
         scans = np.asarray(scans, dtype=np.float64)
         bins = capi.bip_qeels_bins(self.ctx, axis)
         if out is None:

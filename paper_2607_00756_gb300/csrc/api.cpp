@@ -66,6 +66,9 @@ struct bip_ctx {
     DevBuf g_s1bar, g_s2bar, g_ubar, g_dA, g_dt1, g_dt2, g_adj, g_ckpt, g_seg, g_gvp;
     DevBuf g_tA, g_tB, g_sA2, g_sB2;    // split-BF16 operands of the reverse-pass contractions
     DevBuf cubeA, cubeB, cube_work, cube_mask;   // the cube on tcgen05
+    DevBuf cube_grp, pcol;              // cube-mode work groups; probe-order column sums
+    DevBuf hcube, shcube, cstash, ccols; // the exact cube: basis, shifts, S2 windows, columns
+    size_t cube_budget = 0;             // bytes of sweep columns + windows per detector batch (0: auto)
     DevBuf s1t, psi, ybuf;              // the probe order: S1 transposed, Psi, H_n x Psi
     DevBuf pyc, pxc;                    // conjugated propagator tables (adjoint sweeps)
     // capture-safe maps: no host synchronisation, uploads only when the
@@ -250,6 +253,12 @@ int to_groups(const std::vector<double>& w, int rows, int cols, std::vector<int3
     return ng;
 }
 
+// The map's detector-side factor: dfy dfx, the subsampling of the detector
+// beams (a coarse detector sum is 1/(dfy dfx) of the full one for an exit
+// wave inside the alias-free window -- the reading that mirrors the
+// probe-side PRISM rescale, Sec. 2.2.2).
+int det_scale(const bip_ctx* c) { return c->geo.dfy * c->geo.dfx; }
+
 // c_b(rho) coefficients f_y f_x Psi(h_b) / sqrt(G sum |Psi|^2) (Eq. probe)
 std::vector<double2> coef_host(const bip_ctx* c) {
     const BipGeometry& geo = c->geo;
@@ -356,6 +365,14 @@ bip_status make_tables(bip_ctx* c, cudaStream_t s) {
         fill(geo.w1, geo.B, geo.Bp1, 2 * Dw, c->Bpad);
         CUDA_TRY(c, upload(c->wtc, wt, s));
     }
+    // the cube's complete basis: beams and the sweep's propagator shifts -h
+    std::vector<int2> hc(geo.n_cube), shc(geo.n_cube);
+    for (int d = 0; d < geo.n_cube; ++d) {
+        hc[d] = int2{geo.h_cube[2 * d], geo.h_cube[2 * d + 1]};
+        shc[d] = int2{-hc[d].x, -hc[d].y};
+    }
+    CUDA_TRY(c, upload(c->hcube, hc, s));
+    CUDA_TRY(c, upload(c->shcube, shc, s));
     CUDA_TRY(c, ensure(c->errflag, 64, true, s));
     c->tables = true;
     return BIP_OK;
@@ -521,6 +538,8 @@ bip_status bip_create(const bip_config* cfg, bip_ctx** out) {
         !(g.theta_det > 0) || !std::isfinite(g.defocus) || !std::isfinite(g.cs))
         return bad(BIP_ERR_INVALID_ARG, "optics");
     if (g.fy < 1 || g.fx < 1 || g.ny % g.fy || g.nx % g.fx) return bad(BIP_ERR_SHAPE, "f");
+    if (g.dfy < 0 || g.dfx < 0 || (g.dfy > 0 && g.ny % g.dfy) || (g.dfx > 0 && g.nx % g.dfx))
+        return bad(BIP_ERR_SHAPE, "detector subsampling");
     if (g.win < 16 || g.win % 16 || g.win > g.ny / g.fy || g.win > g.nx / g.fx) return bad(BIP_ERR_SHAPE, "win");
     if (g.nrad1 < 0 || g.nrad2 < 0 || g.nang1 < 1 || g.nang2 < 1) return bad(BIP_ERR_INVALID_ARG, "rings");
     if (g.recon != BIP_RECON_COMPLEX && g.recon != BIP_RECON_MAGNITUDE) return bad(BIP_ERR_INVALID_ARG, "recon");
@@ -554,7 +573,8 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->g_gmt, &c->g_T, &c->g_D, &c->g_Dsum, &c->g_s1bar, &c->g_s2bar, &c->g_ubar, &c->g_dA,
                      &c->g_dt1, &c->g_dt2, &c->g_adj, &c->g_ckpt, &c->g_seg, &c->g_gvp, &c->pyc, &c->pxc,
                      &c->ray, &c->rax, &c->g_tA, &c->g_tB, &c->g_sA2, &c->g_sB2, &c->cubeA, &c->cubeB,
-                     &c->cube_work, &c->cube_mask, &c->s1t, &c->psi, &c->ybuf};
+                     &c->cube_work, &c->cube_mask, &c->s1t, &c->psi, &c->ybuf, &c->cube_grp, &c->pcol,
+                     &c->hcube, &c->shcube, &c->cstash, &c->ccols};
     for (DevBuf* b : all) release(*b);
     for (int i = 0; i < 6; ++i) {
         release(c->aw1[i]);
@@ -723,6 +743,7 @@ GatherArgs gather_args(const bip_ctx* c, int side, const int32_t* ids, int n) {
         a.grp = GroupDev{c->grp2_n, (const int32_t*)c->grp2_off.p, (const uint16_t*)c->grp2_par.p, (const float4*)c->grp2_w.p};
         a.h_t = (const int2*)c->hdet.p;
         a.tilt_sign = -1;
+        a.fx = c->geo.dfx;      // the detector beams' lattice step along x
     }
     return a;
 }
@@ -735,7 +756,7 @@ GatherArgs gather_args(const bip_ctx* c, int side, const int32_t* ids, int n) {
 // order's operand: [site][4 planes][K][Bpad], re in plane 0 and im in plane 2
 // (the split-BF16 layout with zero lo planes)
 bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H, void* opA, void* opB,
-                          cudaStream_t s, bool probe = false) {
+                          cudaStream_t s, bool probe = false, bool s2_side = true) {
     const bip_config& g = c->cfg;
     const BipGeometry& geo = c->geo;
     const int K = g.win * g.win, Dpad = c->Dpad, Bpad = c->Bpad, nch = c->nch_max;
@@ -754,7 +775,7 @@ bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H,
     x.site_ids = ids;
     x.K = K;
     x.X = (uint16_t*)c->xtc.p;
-    x.side[0] = XprepSide{(const float2*)c->stash2.p, geo.Bp2, 0};
+    x.side[0] = XprepSide{s2_side ? (const float2*)c->stash2.p : nullptr, s2_side ? geo.Bp2 : 0, 0};
     x.side[1] = XprepSide{(const float2*)c->stash1.p, geo.Bp1, 3 * nb};
     x.pmax = f8 ? (unsigned*)c->f8pmax.p : nullptr;
     TIMED(c, BIP_STAGE_GATHER, s, bip_xprep(x, s));
@@ -797,6 +818,7 @@ bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H,
     r.out[1] = (uint16_t*)opB;
     r.side[0] = ReconSide{geo.n_det, Dpad, Dw, Dw / 128, 0, -1, (const int2*)c->hdet.p, 0, 0,
                           (int64_t)2 * Dpad * K, (int64_t)Dpad * K};
+    if (!s2_side) r.side[0] = ReconSide{0, 0, 0, 0, 0, -1, (const int2*)c->hdet.p, 0, 0, 0, 0};
     r.side[1] = ReconSide{geo.B, Bpad, Bpad, Bpad / 128, nch, +1, (const int2*)c->hbeam.p, 2 * Dw, 3 * nb,
                           (int64_t)2 * nch * Bpad * K, (int64_t)nch * Bpad * K};
     if (probe) {
@@ -1186,8 +1208,9 @@ CubeArgs cube_args(const bip_ctx* c, const int32_t* ids, int nb, int P, float* c
     a.P = P;
     a.scans = (const double*)c->scans_d.p;
     a.ny = g.ny; a.nx = g.nx; a.fy = g.fy; a.fx = g.fx;
-    a.scale = (float)(g.fy * g.fx);
+    a.scale = (float)det_scale(c);
     a.cube = cube;
+    a.cube_ld = c->geo.n_det;
     return a;
 }
 
@@ -1370,7 +1393,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     // order) whole 128-row tiles
     const int crow = probe ? round_up(P, 128) : round_up(P, ctn);
     const size_t KB = (size_t)nch * Bpad;
-    std::vector<int> cube_off;
+    std::vector<int> cube_off, cube_goff;
     if (cube_tc) {
         CUDA_TRY(c, ensure(c->cubeB, (size_t)4 * crow * Bpad * sizeof(uint16_t), true, s));
         if (!probe) CUDA_TRY(c, ensure(c->cubeA, (size_t)SB * 4 * D128 * KB * sizeof(uint16_t), true, s));
@@ -1392,20 +1415,45 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             }
             bb64.insert(bb64.end(), {y0, y1, x0, x1});
         }
-        std::vector<int32_t> cw;
+        // work items per batch; for the per-beam output (cube mode) ordered by
+        // scan tile, then site, with one group per tile: a group's items
+        // write the same cube entries, in site order, from one CTA
+        std::vector<int32_t> cw, cg;
         for (int b0 = 0; b0 < c->n_sites; b0 += SB) {
+            const int nbb = std::min(SB, c->n_sites - b0);
             cube_off.push_back((int)cw.size() / 2);
-            for (int bs = 0; bs < std::min(SB, c->n_sites - b0); ++bs) {
+            cube_goff.push_back((int)cg.size());
+            const int first = (int)cw.size() / 2;
+            auto meets = [&](int bs, int t) {
                 const SiteDev& sd = c->sites[b0 + bs];
-                for (int t = 0; t < n_ct; ++t)
-                    if (box_meets_crop(bb64[4 * t], bb64[4 * t + 1], bb64[4 * t + 2], bb64[4 * t + 3], sd.ty, sd.tx, g)) {
-                        cw.push_back(bs);
-                        cw.push_back(t);
-                    }
+                return box_meets_crop(bb64[4 * t], bb64[4 * t + 1], bb64[4 * t + 2], bb64[4 * t + 3], sd.ty, sd.tx, g);
+            };
+            if (cube_out) {
+                for (int t = 0; t < n_ct; ++t) {
+                    const int g0 = (int)cw.size() / 2 - first;
+                    for (int bs = 0; bs < nbb; ++bs)
+                        if (meets(bs, t)) {
+                            cw.push_back(bs);
+                            cw.push_back(t);
+                        }
+                    if ((int)cw.size() / 2 - first > g0) cg.push_back(g0);
+                }
+                cg.push_back((int)cw.size() / 2 - first);
+            } else {
+                for (int bs = 0; bs < nbb; ++bs)
+                    for (int t = 0; t < n_ct; ++t)
+                        if (meets(bs, t)) {
+                            cw.push_back(bs);
+                            cw.push_back(t);
+                        }
             }
         }
         cube_off.push_back((int)cw.size() / 2);
+        cube_goff.push_back((int)cg.size());
         CUDA_TRY(c, upload(c->cube_work, cw, s));
+        if (cube_out) CUDA_TRY(c, upload(c->cube_grp, cg, s));
+        if (probe_cols)
+            CUDA_TRY(c, ensure(c->pcol, (size_t)SB * round_up(P * nch, 64) * sizeof(float), false, s));
         CUDA_TRY(c, ensure(c->cube_mask, std::max<size_t>(1, cw.size() / 2 * (tile / 64)) * sizeof(unsigned long long),
                            false, s));
     }
@@ -1499,17 +1547,25 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             ct.sites = (const SiteDev*)c->sites_d.p;
             ct.site_ids = ids;
             ct.ny = g.ny; ct.nx = g.nx; ct.fy = g.fy; ct.fx = g.fx;
-            ct.scale = (float)(g.fy * g.fx);
-            ct.partial = partial;
+            ct.scale = (float)det_scale(c);
+            ct.mt_inner = 1;
             ct.err = (int*)c->errflag.p;
             // A: the S2 windows (opA16 holds four planes' room: 4 SB Dpad rows of K)
             if (probe_cols) {
+                // per-column sums of the batch's sites, then the channel sum
+                // of each scan in order
                 ct.ch0 = 0;
                 ct.nacc = 1;
+                ct.pcol = (float*)c->pcol.p;
+                ct.pcol_site = round_up(P * nch, 64);
+                CUDA_TRY(c, cudaMemsetAsync(c->pcol.p, 0, (size_t)nb * ct.pcol_site * sizeof(float), s));
                 TIMED(c, BIP_STAGE_QUADFORM, s,
                       bip_cube_tc(ct, c->opA16.p, (int64_t)SB * 4 * Dpad, K, c->ybuf.p, (int64_t)SB * 2 * P64 * nch,
                                   K, s));
+                TIMED(c, BIP_STAGE_QUADFORM, s,
+                      bip_cube_col_reduce((const float*)c->pcol.p, ct.pcol_site, nb, ids, P, nch, partial, s));
             } else {
+                ct.partial = partial;
                 for (int ch0 = 0; ch0 < nch; ch0 += 4) {
                     ct.ch0 = ch0;
                     ct.nacc = std::min(4, nch - ch0);
@@ -1596,9 +1652,16 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
                 ct.sites = (const SiteDev*)c->sites_d.p;
                 ct.site_ids = ids;
                 ct.ny = g.ny; ct.nx = g.nx; ct.fy = g.fy; ct.fx = g.fx;
-                ct.scale = (float)(g.fy * g.fx);
-                ct.cube = cube_out;
-                ct.partial = beam ? partial : nullptr;
+                ct.scale = (float)det_scale(c);
+                if (beam) {
+                    ct.partial = partial;
+                    ct.mt_inner = 1;
+                } else {
+                    ct.cube = cube_out;
+                    ct.cube_ld = geo.n_det;
+                    ct.n_groups = cube_goff[bi + 1] - cube_goff[bi] - 1;
+                    ct.grp = (const int32_t*)c->cube_grp.p + cube_goff[bi];
+                }
                 ct.err = (int*)c->errflag.p;
                 // channels per launch: one TMEM accumulator pair (2 ctn columns)
                 // each in 512 columns
@@ -1682,7 +1745,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         d.sites = (const SiteDev*)c->sites_d.p;
         d.site_ids = ids;
         d.ny = g.ny; d.nx = g.nx; d.fy = g.fy; d.fx = g.fx;
-        d.scale = (float)(g.fy * g.fx);
+        d.scale = (float)det_scale(c);
         d.partial = partial;
         TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_bin(d, s));
         if (!raster.ok && d.n_work > 0) TIMED(c, BIP_STAGE_QUADFORM, s, bip_diff_eval(d, s));
@@ -1699,7 +1762,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         d.sites = (const SiteDev*)c->sites_d.p;
         d.site_ids = (const int32_t*)c->seq_ids_d.p;
         d.ny = g.ny; d.nx = g.nx; d.fy = g.fy; d.fx = g.fx;
-        d.scale = (float)(g.fy * g.fx);
+        d.scale = (float)det_scale(c);
         d.partial = partial;
         TIMED(c, BIP_STAGE_QUADFORM, s, bip_raster_eval(d, rargs, s));
     }
@@ -1714,6 +1777,274 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         const double* occ = c->occ_n == c->n_sites ? (const double*)c->occ_d.p : nullptr;
         TIMED(c, BIP_STAGE_REDUCE, s, bip_reduce_sites(partial, c->n_sites, P, c->rsum.p, map_out, s, occ));
         if (c->n_sites > 0) c->launches[BIP_STAGE_REDUCE]++;   // two kernels: chunks, then their sum
+    }
+    return BIP_OK;
+}
+
+// The energy-filtered 4D cube (Sec. 2.2.6, Algorithm 3): S1 partitioned
+// (the context's S1 stash, rebuilt on each window), the exit side exact on
+// the complete basis: batches of the cube's beams are taken back from the
+// exit surface as unpartitioned S2 columns (one sweep per batch, windows of
+// every site stashed), re-tilted into the coupling's detector operand, and
+// cube[rho][d] += sum_n |sum_b M_{d,b} c_b(rho)|^2 site by site in order.
+bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const double* scans, int32_t P,
+                          float* cube_out, cudaStream_t s) {
+    const bip_config& g = c->cfg;
+    const BipGeometry& geo = c->geo;
+    if (c->prec == BIP_PREC_FP8_TILE)
+        return fail(c, BIP_ERR_UNSUPPORTED, "the cube has no FP8 path (its exit side has no per-window scales)");
+    const int K = g.win * g.win, Bpad = c->Bpad, nch = c->nch_max;
+    const bool tc = c->prec != BIP_PREC_FP32;
+    const int npl = gram_planes(c->prec);
+    const size_t G = (size_t)g.ny * g.nx;
+    const int n_cube = geo.n_cube;
+
+    CUDA_TRY(c, ensure(c->scans_d, (size_t)P * 2 * sizeof(double), false, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->scans_d.p, scans, (size_t)P * 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+    c->scans_cache.clear();
+    CUDA_TRY(c, ensure(c->illum, (size_t)Bpad * P * sizeof(float2), false, s));
+    IllumArgs ia{P, geo.B, Bpad, (const int2*)c->hbeam.p, (const double2*)c->coef.p, (const double*)c->scans_d.p,
+                 g.ny, g.nx, (float2*)c->illum.p};
+    CUDA_TRY(c, bip_illum(ia, s));
+    CUDA_TRY(c, cudaMemsetAsync(cube_out, 0, (size_t)P * n_cube * sizeof(float), s));
+
+    // beams per sweep: the windows of every site plus the columns, within
+    // half the free device memory (at most 96 GB), a multiple of 32
+    size_t free_b = 0, total_b = 0;
+    CUDA_TRY(c, cudaMemGetInfo(&free_b, &total_b));
+    const size_t per_beam = (size_t)c->n_sites * K * sizeof(float2) + G * sizeof(float2);
+    size_t budget = c->cube_budget ? c->cube_budget : std::min(free_b / 2, (size_t)96 << 30);
+    int nbd = (int)std::min<size_t>((size_t)round_up(n_cube, kDetPad), budget / per_beam / kDetPad * kDetPad);
+    nbd = std::min(nbd, 2048);
+    if (nbd < kDetPad)
+        return fail(c, BIP_ERR_OOM, "not enough device memory for 32 exact S2 columns and their windows");
+    const int Dpb = nbd, D128 = round_up(Dpb, 128);
+    CUDA_TRY(c, ensure(c->cstash, (size_t)c->n_sites * nbd * K * sizeof(float2), false, s));
+    CUDA_TRY(c, ensure(c->ccols, (size_t)nbd * G * sizeof(float2), false, s));
+
+    // site batches and their buffers (as the map's)
+    const int SB = c->sb_override > 0 ? std::min(c->n_sites, c->sb_override)
+                                      : (tc ? tc_batch(c) : std::min(c->n_sites, 8));
+    const size_t rowsB = (size_t)nch * Bpad, perA = (size_t)Dpb * K, perB = rowsB * K;
+    const size_t perMt = (size_t)Bpad * nch * Dpb, KB = (size_t)nch * Bpad;
+    if (tc) {
+        CUDA_TRY(c, ensure(c->opA16, SB * perA * 8, true, s));
+        CUDA_TRY(c, ensure(c->opB16, SB * perB * 8, true, s));
+        CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
+    } else {
+        CUDA_TRY(c, ensure(c->opA32, SB * perA * sizeof(float2), true, s));
+        CUDA_TRY(c, ensure(c->opB32, SB * perB * sizeof(float2), true, s));
+    }
+    CUDA_TRY(c, ensure(c->mt32, SB * perMt * sizeof(float2), true, s));
+
+    // tcgen05 per-beam contraction: c_b(rho) as split planes, and work items
+    // grouped by scan tile (sites ascending), one CTA per cube tile
+    const int ctn = P >= 128 ? 128 : 64;
+    const int crow = round_up(P, ctn), n_ct = crow / ctn;
+    std::vector<int> cube_off, cube_goff;
+    if (tc) {
+        CUDA_TRY(c, ensure(c->cubeB, (size_t)4 * crow * Bpad * sizeof(uint16_t), true, s));
+        CUDA_TRY(c, ensure(c->cubeA, (size_t)SB * 4 * D128 * KB * sizeof(uint16_t), true, s));
+        SplitArgs sc{(const float2*)c->illum.p, 1, P, 0, P, Bpad, 1, (uint16_t*)c->cubeB.p, 0, crow, Bpad, 0, 0};
+        CUDA_TRY(c, bip_split_planes(sc, s));
+        std::vector<double> bb;
+        for (int t = 0; t < n_ct; ++t) {
+            double y0 = INFINITY, y1 = -INFINITY, x0 = INFINITY, x1 = -INFINITY;
+            for (int p = t * ctn; p < std::min(P, (t + 1) * ctn); ++p) {
+                y0 = std::min(y0, scans[2 * p]);
+                y1 = std::max(y1, scans[2 * p]);
+                x0 = std::min(x0, scans[2 * p + 1]);
+                x1 = std::max(x1, scans[2 * p + 1]);
+            }
+            bb.insert(bb.end(), {y0, y1, x0, x1});
+        }
+        std::vector<int32_t> cw, cg;
+        for (int b0 = 0; b0 < c->n_sites; b0 += SB) {
+            const int nbb = std::min(SB, c->n_sites - b0);
+            cube_off.push_back((int)cw.size() / 2);
+            cube_goff.push_back((int)cg.size());
+            const int first = (int)cw.size() / 2;
+            for (int t = 0; t < n_ct; ++t) {
+                const int g0 = (int)cw.size() / 2 - first;
+                for (int bs = 0; bs < nbb; ++bs) {
+                    const SiteDev& sd = c->sites[b0 + bs];
+                    if (box_meets_crop(bb[4 * t], bb[4 * t + 1], bb[4 * t + 2], bb[4 * t + 3], sd.ty, sd.tx, g)) {
+                        cw.push_back(bs);
+                        cw.push_back(t);
+                    }
+                }
+                if ((int)cw.size() / 2 - first > g0) cg.push_back(g0);
+            }
+            cg.push_back((int)cw.size() / 2 - first);
+        }
+        cube_off.push_back((int)cw.size() / 2);
+        cube_goff.push_back((int)cg.size());
+        CUDA_TRY(c, upload(c->cube_work, cw, s));
+        CUDA_TRY(c, upload(c->cube_grp, cg, s));
+        CUDA_TRY(c, ensure(c->cube_mask, std::max<size_t>(1, cw.size() / 2 * (ctn / 64)) * sizeof(unsigned long long),
+                           false, s));
+    }
+
+    int first_plane = g.nz - 1;
+    for (auto& sd : c->sites) first_plane = std::min(first_plane, (int)sd.plane);
+    for (int d0 = 0; d0 < n_cube; d0 += nbd) {
+        const int nd = std::min(nbd, n_cube - d0);
+        // the batch's exact S2 columns, exit surface to the first site plane
+        MsPlan plan = plan_for(c, nd, c->shcube);
+        plan.shift = (const int2*)c->shcube.p + d0;
+        {
+            MsRowArgs a{};
+            a.cols = (float2*)c->ccols.p;
+            a.init = 1;
+            a.init_val = (float)(1.0 / std::sqrt((double)G));
+            a.do_fft = 1;
+            a.win = g.win;
+            a.stash = (float2*)c->cstash.p;
+            TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
+            TIMED(c, BIP_STAGE_MS_COL, s, bip_ms_col_pass(plan, (float2*)c->ccols.p, s));
+        }
+        for (int j = g.nz - 1; j >= first_plane; --j) {
+            MsRowArgs a{};
+            a.cols = (float2*)c->ccols.p;
+            a.do_ifft = 1;
+            a.v_pre = V + (size_t)j * G;
+            a.do_fft = j > first_plane;
+            if (c->plane_off[j + 1] > c->plane_off[j]) {
+                a.row_off = (const int32_t*)c->row_off_d.p + (size_t)j * (g.ny + 1);
+                a.row_ent = (const int4*)c->row_ent_d.p;
+            }
+            a.win = g.win;
+            a.stash = (float2*)c->cstash.p;
+            TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
+            if (j > first_plane) TIMED(c, BIP_STAGE_MS_COL, s, bip_ms_col_pass(plan, (float2*)c->ccols.p, s));
+        }
+        int bi = 0;
+        for (int b0 = 0; b0 < c->n_sites; b0 += SB, ++bi) {
+            const int nb = std::min(SB, c->n_sites - b0);
+            const int32_t* ids = (const int32_t*)c->seq_ids_d.p + b0;
+            // aperture side H_n S1 (partitioned, rebuilt on the windows)
+            if (c->prec == BIP_PREC_MIXED && c->recon_tc) {
+                bip_status st = recon_tc_batch(c, ids, nb, H, nullptr, c->opB16.p, s, false, false);
+                if (st != BIP_OK) return st;
+            } else {
+                GatherArgs g1 = gather_args(c, 1, ids, nb);
+                g1.rows_pad = Bpad;
+                g1.nch = nch;
+                g1.H = (const float2*)H;
+                if (tc) {
+                    g1.out_bf16 = (uint16_t*)c->opB16.p;
+                    g1.out_planes = npl;
+                    g1.site_stride = (int64_t)(npl * perB);
+                } else {
+                    g1.out_c64 = (float2*)c->opB32.p;
+                    g1.site_stride = (int64_t)perB;
+                }
+                TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g1, s));
+            }
+            // detector side: the exact S2 windows re-tilted
+            RetiltArgs ra{};
+            ra.n_sites = nb;
+            ra.site_ids = ids;
+            ra.sites = (const SiteDev*)c->sites_d.p;
+            ra.win = g.win; ra.ny = g.ny; ra.nx = g.nx; ra.K = K;
+            ra.nd = nd;
+            ra.stash = (const float2*)c->cstash.p;
+            ra.h = (const int2*)c->hcube.p + d0;
+            ra.ey = (const float2*)c->ey.p;
+            ra.ex = (const float2*)c->ex.p;
+            ra.rows_pad = Dpb;
+            if (tc) {
+                ra.out_bf16 = (uint16_t*)c->opA16.p;
+                ra.out_planes = npl;
+                ra.site_stride = (int64_t)npl * perA;
+            } else {
+                ra.out_c64 = (float2*)c->opA32.p;
+                ra.site_stride = (int64_t)perA;
+            }
+            TIMED(c, BIP_STAGE_GATHER, s, bip_retilt(ra, s));
+            if (tc) {
+                // M with rows (ch, b) and columns d, complex64
+                TcArgs A{};
+                A.epi = TC_EPI_C32;
+                A.N = tile_width(Dpb);
+                A.npl = npl;
+                A.out_planes = npl;
+                A.A = TcOperand{c->opB16.p, (int64_t)SB * npl * (int64_t)rowsB, K, npl * (int64_t)rowsB, (int64_t)rowsB};
+                A.B = TcOperand{c->opA16.p, (int64_t)SB * npl * (int64_t)Dpb, K, npl * (int64_t)Dpb, (int64_t)Dpb};
+                A.kb = K / 32;
+                A.n_sites = nb;
+                A.mt_per = (int)(rowsB / 128);
+                A.nt_per = (Dpb + A.N - 1) / A.N;
+                A.n_cols = Dpb;
+                A.out32 = (float2*)c->mt32.p;
+                A.out32_site = (int64_t)perMt;
+                A.out32_ld = Dpb;
+                A.ep_B = Bpad;
+                A.ep_Dp = Dpb;
+                A.err = (int*)c->errflag.p;
+                TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(A, s));
+                SplitArgs sa{(const float2*)c->mt32.p, 1, Dpb, (int64_t)perMt, Dpb, (int)KB, nb,
+                             (uint16_t*)c->cubeA.p, (int64_t)(4 * D128 * KB), D128, (int)KB, 0, 0};
+                TIMED(c, BIP_STAGE_QUADFORM, s, bip_split_planes(sa, s));
+                CubeTcArgs ct{};
+                ct.n_work = cube_off[bi + 1] - cube_off[bi];
+                ct.work = (const int32_t*)c->cube_work.p + 2 * (size_t)cube_off[bi];
+                ct.mask = (unsigned long long*)c->cube_mask.p + (size_t)cube_off[bi] * (ctn / 64);
+                ct.n_sites = nb;
+                ct.tn = ctn;
+                ct.n_tiles = n_ct;
+                ct.mt_per = D128 / 128;
+                ct.kb_ch = Bpad / 32;
+                ct.a_site_rows = 4 * (int64_t)D128;
+                ct.a_plane_rows = D128;
+                ct.b_plane_rows = crow;
+                ct.n_det = nd;
+                ct.P = P;
+                ct.scans = (const double*)c->scans_d.p;
+                ct.sites = (const SiteDev*)c->sites_d.p;
+                ct.site_ids = ids;
+                ct.ny = g.ny; ct.nx = g.nx; ct.fy = g.fy; ct.fx = g.fx;
+                ct.scale = 1.0f;
+                ct.cube = cube_out + d0;
+                ct.cube_ld = n_cube;
+                ct.n_groups = cube_goff[bi + 1] - cube_goff[bi] - 1;
+                ct.grp = (const int32_t*)c->cube_grp.p + cube_goff[bi];
+                ct.err = (int*)c->errflag.p;
+                const int per = 512 / (2 * ctn);
+                for (int ch0 = 0; ch0 < nch; ch0 += per) {
+                    ct.ch0 = ch0;
+                    ct.nacc = std::min(per, nch - ch0);
+                    TIMED(c, BIP_STAGE_QUADFORM, s,
+                          bip_cube_tc(ct, c->cubeA.p, (int64_t)nb * 4 * D128, (int)KB, c->cubeB.p, (int64_t)4 * crow,
+                                      Bpad, s));
+                }
+            } else {
+                CGemmArgs A{};
+                A.M = nd; A.N = (int)rowsB; A.K = K;
+                A.A = (const float2*)c->opA32.p; A.lda = K; A.strideA = (int64_t)perA;
+                A.Bm = (const float2*)c->opB32.p; A.ldb = K; A.strideB = (int64_t)perB;
+                A.batch = nb;
+                A.epi = 1;
+                A.C = (float2*)c->mt32.p; A.ldc = (int64_t)nch * Dpb; A.strideC = (int64_t)perMt;
+                A.ep_B = Bpad; A.ep_Dp = Dpb;
+                TIMED(c, BIP_STAGE_COUPLING, s, bip_cgemm_simt(A, s));
+                CubeArgs ca = cube_args(c, ids, nb, P, cube_out + d0);
+                ca.n_det = nd;
+                ca.Dp = Dpb;
+                ca.m_ld = (int64_t)nch * Dpb;
+                ca.m32 = (const float2*)c->mt32.p;
+                ca.m_site = (int64_t)perMt;
+                ca.scale = 1.0f;
+                ca.cube_ld = n_cube;
+                TIMED(c, BIP_STAGE_QUADFORM, s, bip_cube_accumulate(ca, s));
+            }
+        }
+    }
+    if (tc && !c->capture_safe) {
+        int flag = 0;
+        CUDA_TRY(c, cudaMemcpyAsync(&flag, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        if (flag) return fail(c, BIP_ERR_TIMEOUT, "a tensor-core contraction gave up waiting (device timeout)");
     }
     return BIP_OK;
 }
@@ -1736,11 +2067,30 @@ bip_status bip_coreloss_sites(bip_ctx* c, const void* H, const double* scan_px, 
     return run_map(c, H, scan_px, P, partial_out, nullptr, nullptr, (cudaStream_t)stream);
 }
 
-bip_status bip_coreloss_cube(bip_ctx* c, const void* H, const double* scan_px, int32_t P, float* cube_out,
-                             void* stream) {
-    bip_status st = check_map_args(c, H, scan_px, P, cube_out);
-    if (st != BIP_OK) return st;
-    return run_map(c, H, scan_px, P, nullptr, nullptr, cube_out, (cudaStream_t)stream);
+bip_status bip_coreloss_cube(bip_ctx* c, const float* V, const void* H, const double* scan_px, int32_t P,
+                             float* cube_out, void* stream) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (!c->s1 || site_signature(c->sites) != c->sig1)
+        return fail(c, BIP_ERR_INVALID_ARG, "bip_build_s1 must run first (the cube's sites are its sites)");
+    if (!V || !H || !scan_px || !cube_out) return fail(c, BIP_ERR_INVALID_ARG, "null pointer argument");
+    if ((reinterpret_cast<uintptr_t>(H) & 15) != 0) return fail(c, BIP_ERR_INVALID_ARG, "H must be 16-byte aligned");
+    if (P < 1) return fail(c, BIP_ERR_INVALID_ARG, "P must be >= 1");
+    for (int i = 0; i < 2 * P; ++i)
+        if (!std::isfinite(scan_px[i])) return fail(c, BIP_ERR_INVALID_ARG, "scan position is not finite");
+    return run_cube_exact(c, V, H, scan_px, P, cube_out, (cudaStream_t)stream);
+}
+
+bip_status bip_cube_beams(const bip_ctx* c, int32_t* n_cube, int32_t* h) {
+    if (!c || !n_cube) return BIP_ERR_INVALID_ARG;
+    *n_cube = c->geo.n_cube;
+    if (h) std::memcpy(h, c->geo.h_cube.data(), c->geo.h_cube.size() * sizeof(int32_t));
+    return BIP_OK;
+}
+
+bip_status bip_set_cube_memory(bip_ctx* c, int64_t bytes) {
+    if (!c || bytes < 0) return BIP_ERR_INVALID_ARG;
+    c->cube_budget = (size_t)bytes;
+    return BIP_OK;
 }
 
 // qEELS bins: the distinct components of the detector beams along `axis`,
@@ -1773,6 +2123,10 @@ bip_status bip_coreloss_qeels(bip_ctx* c, const void* H, const double* scan_px, 
     if (st != BIP_OK) return st;
     std::vector<int32_t> bins, bin_of;
     if (!qeels_bins(c, axis, bins, bin_of)) return fail(c, BIP_ERR_INVALID_ARG, "axis must be 0 (q_y) or 1 (q_x)");
+    if ((axis == 0 ? c->geo.dfy : c->geo.dfx) != 1)
+        return fail(c, BIP_ERR_INVALID_ARG,
+                    "qEELS needs the resolved axis sampled at f = 1: create the context with dfy = 1 (axis 0) "
+                    "or dfx = 1 (axis 1)");
     cudaStream_t s = (cudaStream_t)stream;
     CUDA_TRY(c, ensure(c->cube_scratch, (size_t)P * c->geo.n_det * sizeof(float), false, s));
     CUDA_TRY(c, upload(c->bin_of_d, bin_of, s));
@@ -2035,7 +2389,7 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
     ga.occ = occ;
     ga.sites = (const SiteDev*)c->sites_d.p;
     ga.ny = g.ny; ga.nx = g.nx; ga.fy = g.fy; ga.fx = g.fx;
-    ga.scale = (double)g.fy * g.fx;
+    ga.scale = (double)det_scale(c);
     for (int b0 = 0; b0 < c->n_sites; b0 += SB) {
         const int nb = std::min(SB, c->n_sites - b0);
         const int32_t* ids = (const int32_t*)c->seq_ids_d.p + b0;

@@ -19,7 +19,10 @@ struct BipGeometry {
     double sigma = 0.0;       // interaction constant, rad/(V*Angstrom)
     int n_full = 0;           // aperture beams before subsampling
     int B = 0, n_det = 0, Bp1 = 0, Bp2 = 0;
+    int dfy = 1, dfx = 1;                          // detector-side subsampling in effect
     std::vector<int32_t> h_beam, h_det;            // [B*2], [n_det*2]  (y, x)
+    std::vector<int32_t> h_cube;                   // [n_cube*2]: the cube's complete basis
+    int n_cube = 0;
     std::vector<int32_t> p1, p2;                   // parent positions in the lists
     std::vector<double> w1, w2;                    // [B*Bp1], [n_det*Bp2]
     std::vector<std::complex<double>> psi_beam;    // Psi(h_b)
@@ -347,15 +350,17 @@ struct CubeArgs {
     int P;
     const double* scans;
     int ny, nx, fy, fx;
-    float scale;                    // f_y f_x
-    float* cube;                    // [P][n_det], accumulated
+    float scale;                    // the detector-side factor (1 for the exact cube)
+    float* cube;                    // [P][cube_ld], rows d accumulated
+    int64_t cube_ld;                // (>= n_det)
 };
 cudaError_t bip_cube_accumulate(const CubeArgs& a, cudaStream_t s);
 // cube_tc.cu : the cube on tcgen05 (split BF16).  A = M transposed to rows d,
 // K = (channel, b): [site][4 planes][rows (128 multiple)][nch Bpad] bf16;
 // B = c_b(rho): [4 planes][scans (64 multiple)][Bpad] bf16.  Work items (site
-// in batch, 64-scan tile meeting its crop mask) x 128-row tiles of d;
-// channels ch0 .. ch0 + nacc - 1 (nacc <= 4) per launch.
+// in batch, scan tile meeting its crop mask) x 128-row tiles of d, grouped
+// so that every output element has one writer per launch (no atomics);
+// channels ch0 .. ch0 + nacc - 1 per launch.
 struct CubeTcArgs {
     int n_work;
     const int32_t* work;            // [n_work][2] (site in batch, scan tile)
@@ -368,10 +373,20 @@ struct CubeTcArgs {
     const SiteDev* sites;
     const int32_t* site_ids;
     int ny, nx, fy, fx;
-    float scale;                    // f_y f_x
-    float* cube;                    // [P][n_det], added to (atomically); or
+    float scale;                    // the detector-side factor (1 for the exact cube)
+    float* cube;                    // cube mode: [P][cube_ld], rows d added to; or
     float* partial;                 // map mode: [n_sites_total][P] per-site map, the
-                                    // detector sum taken in the epilogue (atomically)
+                                    // detector sum taken in the epilogue; or
+    float* pcol;                    // map mode with (scan, channel) columns: [bs][pcol_site]
+                                    // column sums (bip_cube_col_reduce adds them up)
+    int64_t pcol_site;
+    int64_t cube_ld;                // cube row stride (>= n_det)
+    // units: cube mode, (group g of work items grp[g] .. grp[g+1]-1 -- one
+    // scan tile, sites ascending -- x d tile); map mode (mt_inner = 1), one
+    // work item with all its d tiles
+    int n_groups;
+    const int32_t* grp;
+    int mt_inner;
     // probe order: B rows per site (0: one B for every site), the channel in
     // B's columns instead of A's (A = S2 windows, B = H_n x windowed probes),
     // and operands of two BF16 planes (re, im) instead of four (split BF16)
@@ -389,6 +404,8 @@ struct CubeTcArgs {
 // a_k, b_k: row lengths of A and B (bf16 elements)
 cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int a_k, const void* B, int64_t b_rows,
                         int b_k, cudaStream_t s);
+cudaError_t bip_cube_col_reduce(const float* pcol, int64_t pcol_site, int n_sites, const int32_t* site_ids, int P,
+                                int ncol, float* partial, cudaStream_t s);
 
 // probe.cu : the probe order of the scan contraction.  Y[site][plane][rho][n K
 // + r] = H_n(r) Psi(rho, r) as BF16 planes (re, im), from the windowed probes
@@ -509,6 +526,28 @@ struct SplitArgs {
     int conj;
 };
 cudaError_t bip_split_planes(const SplitArgs& a, cudaStream_t s);
+
+// cube_exact.cu : the cube's exit side.  stash [n_sites_total][nd][K] holds
+// the windows of nd unpartitioned S2 columns (beams h[0 .. nd)) in the
+// de-tilted frame; the kernel writes S2_d(r) = stash exp(-2 pi i h_d.r/N) as
+// the coupling's detector operand, row d of [site in batch][rows_pad][K].
+struct RetiltArgs {
+    int n_sites;                    // sites of this batch
+    const int32_t* site_ids;
+    const SiteDev* sites;
+    int win, ny, nx, K;             // ny, nx powers of two
+    int nd;                         // beams in the stash
+    const float2* stash;
+    const int2* h;                  // [nd] (h_y, h_x)
+    const float2* ey;               // [ny] exp(+2 pi i m / ny)
+    const float2* ex;               // [nx]
+    int rows_pad;                   // output rows per plane (>= nd)
+    float2* out_c64;                // complex64 output, or
+    uint16_t* out_bf16;             // BF16 planes (out_planes: 2 re, im; 4 split hi + lo)
+    int out_planes;
+    int64_t site_stride;            // output elements per site
+};
+cudaError_t bip_retilt(const RetiltArgs& a, cudaStream_t s);
 
 // noalloc.cu : the static device scratch used by bip_build_s1_noalloc
 constexpr size_t kNoallocScratchBytes = size_t(32) << 20;   // 32 MiB per GPU

@@ -1,6 +1,6 @@
 // The energy-filtered 4D cube (Sec. 2.2.6): Eq. map-sum with the detector
 // sum left open,
-//   cube[rho][d] = sum_tau f_y f_x sum_n |sum_b M^(n)_{d,b} c_b(rho)|^2
+//   cube[rho][d] = sum_tau scale sum_n |sum_b M^(n)_{d,b} c_b(rho)|^2
 // over the sites tau whose crop mask holds rho.
 //
 //   illum_kernel : c_b(rho) = coef_b exp(-2 pi i h_b.rho/N), [Bpad][P]
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) cube_kernel(CubeArgs a) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (!in[j]) continue;
-            float* row = a.cube + (size_t)(p0 + ty * 4 + j) * a.n_det;
+            float* row = a.cube + (size_t)(p0 + ty * 4 + j) * a.cube_ld;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int d = d0 + tx * 4 + i;
@@ -133,7 +133,7 @@ cudaError_t bip_illum(const IllumArgs& a, cudaStream_t s) {
 
 cudaError_t bip_cube_accumulate(const CubeArgs& a, cudaStream_t s) {
     if (a.n_sites < 1) return cudaSuccess;
-    if (a.Bpad % kKb) return cudaErrorInvalidValue;
+    if (a.Bpad % kKb || a.cube_ld < a.n_det) return cudaErrorInvalidValue;
     const dim3 grid((a.n_det + kTile - 1) / kTile, (a.P + kTile - 1) / kTile);
     cube_kernel<<<grid, kThreads, 0, s>>>(a);
     return cudaGetLastError();

@@ -1,6 +1,6 @@
 // The 4D cube (Sec. 2.2.6) on the tensor cores: per site, channel and
 // detector beam d, a_d(rho) = sum_b M^(n)_{d,b} c_b(rho), and
-//   cube[rho][d] += f_y f_x sum_n |a_d(rho)|^2
+//   cube[rho][d] += scale sum_n |a_d(rho)|^2
 // for the scans of the site's crop mask -- or, in map mode, the same terms
 // summed over d into the site's map (the "beam order" of the scan
 // contraction: |M c|^2 directly, without the Gram matrix).  Split BF16 (hi + lo, three
@@ -9,17 +9,25 @@
 // a_d(rho) = sum_r S2_d(r) Y^(n)(rho, r) with Y^(n) = H_n x the windowed
 // probes, the channel then in B's columns, BF16 planes (four products).
 //
-// Work unit: (site in batch, tile of 64 scans that meets the site's crop
-// mask, tile of 128 detector beams).  K runs over (channel, aperture beam);
-// each channel accumulates into its own TMEM pair (re, im; 64 columns
-// each), so the epilogue has every channel of an element at once and adds
-// the channel sum of |a|^2 to the cube with one atomic add per element
-// (sites of a batch run concurrently; the order of the additions, and so the
-// last bits of the cube, is not fixed).  The crop mask of a unit's 64 scans
-// is a precomputed 64-bit word.  Persistent, one CTA per SM, 192 threads:
-// warp 0 TMA producer, warp 1 TMEM allocator and MMA issuer, warps 2-5
-// epilogue.  Every wait is bounded; on a timeout the kernel sets *err,
-// drains what it issued and frees TMEM.
+// Work item: (site in batch, tile of scans that meets the site's crop
+// mask).  K runs over (channel, aperture beam); each channel accumulates
+// into its own TMEM pair (re, im), so the epilogue has every channel of an
+// element at once.  No floating-point atomics: every output element has one
+// writer per launch, and its additions come in a fixed order, so results do
+// not depend on scheduling.
+//   cube mode: a unit is (group of work items sharing one scan tile, sites
+//     in ascending order; tile of 128 detector beams); the CTA that owns it
+//     adds each site's channel sum to the cube with a plain read-add-write.
+//   map mode: a unit is one work item with every 128-beam tile of d; the
+//     detector sum of each scan column is taken by a fixed shuffle tree per
+//     warp, then over the four epilogue warps and the d tiles in order, and
+//     added once to the site's map (or, with (scan, channel) columns,
+//     stored per column and summed over the channels by col_reduce_kernel).
+// The crop mask of a work item's scans is a precomputed 64-bit word per 64
+// columns.  Persistent, one CTA per SM, 192 threads: warp 0 TMA producer,
+// warp 1 TMEM allocator and MMA issuer, warps 2-5 epilogue.  Every wait is
+// bounded; on a timeout the kernel sets *err, drains what it issued and
+// frees TMEM.
 #include "bip_device.cuh"
 #include "tc_common.cuh"
 
@@ -29,7 +37,8 @@ constexpr int kThreads = 192;
 constexpr int kATile = 128 * 64;                  // bytes: 128 rows x 32 bf16
 constexpr int kRing = 4 * (4 * kATile + 4 * 64 * 64);   // bytes of the stage ring
 constexpr int kMaxStages = 8;
-constexpr size_t kSmem = 1024 + (size_t)kRing + 256;
+constexpr int kRed = 4 * 128 * 4;                 // bytes: per-warp column sums (map mode)
+constexpr size_t kSmem = 1024 + (size_t)kRing + 256 + kRed;
 // A stage holds one 32-wide K block of every plane: split BF16 A re_hi,
 // re_lo, im_hi, im_lo then B the same; BF16 (HI) A re, im then B re, im.
 // The ring holds as many stages as fit: 4 (split, 64-scan tiles), 3 (split,
@@ -43,10 +52,20 @@ struct Shape {
     static_assert(NS >= 2 && NS <= kMaxStages, "stage ring");
 };
 
-__device__ __forceinline__ bool unit_of(const CubeTcArgs& a, int idx, int& w, int& mt) {
-    if (idx >= a.n_work * a.mt_per) return false;
-    w = idx / a.mt_per;
-    mt = idx % a.mt_per;
+// The steps (work item w, d tile mt) of unit u: items w0 .. w1 - 1, tiles
+// mt0 .. mt1 - 1 (one of the two ranges has one entry).
+struct Steps {
+    int w0, w1, mt0, mt1;
+};
+__device__ __forceinline__ bool unit_steps(const CubeTcArgs& a, int u, Steps& st) {
+    if (a.mt_inner) {
+        if (u >= a.n_work) return false;
+        st = Steps{u, u + 1, 0, a.mt_per};
+    } else {
+        if (u >= a.n_groups * a.mt_per) return false;
+        const int g = u / a.mt_per, mt = u % a.mt_per;
+        st = Steps{a.grp[g], a.grp[g + 1], mt, mt + 1};
+    }
     return true;
 }
 
@@ -70,6 +89,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t* tmem_slot = (uint32_t*)(drain + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     volatile int* ep_ok = abort_flag + 1;
+    float* red = (float*)(smem + kRing + 256);              // [4 warps][kN] (map mode)
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) {
@@ -106,8 +126,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t ph = 0;
             int issued = 0;
             bool ok = true;
-            int w, mt;
-            for (int i = 0; ok && unit_of(a, blockIdx.x + i * gridDim.x, w, mt); ++i) {
+            Steps su;
+            for (int i = 0; ok && unit_steps(a, blockIdx.x + i * gridDim.x, su); ++i)
+            for (int w = su.w0; ok && w < su.w1; ++w)
+            for (int mt = su.mt0; ok && mt < su.mt1; ++mt) {
                 const int bs = a.work[2 * w], t = a.work[2 * w + 1];
                 const int64_t a0 = (int64_t)bs * a.a_site_rows + (int64_t)mt * 128;
                 const int64_t b0 = (int64_t)bs * a.b_site_rows + (int64_t)t * kN;
@@ -162,10 +184,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             int s = 0;
             uint32_t ph = 0, aph = 0;
             bool any = false, ok = true;
-            int w, mt;
-            for (int i = 0; ok && unit_of(a, blockIdx.x + i * gridDim.x, w, mt); ++i) {
+            Steps su;
+            for (int i = 0; ok && unit_steps(a, blockIdx.x + i * gridDim.x, su); ++i)
+            for (int w = su.w0; ok && w < su.w1; ++w)
+            for (int mt = su.mt0; ok && mt < su.mt1; ++mt) {
                 if (!mbar_wait(acc_empty, aph ^ 1, abort_flag)) {
                     fail();
+                    ok = false;
                     break;
                 }
                 tc_fence_after();
@@ -233,59 +258,85 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
         const int q = warp & 3;
         const int et = threadIdx.x - 64;
+        const bool map_mode = a.partial || a.pcol;
         uint32_t aph = 0;
-        int w, mt;
-        for (int i = 0; unit_of(a, blockIdx.x + i * gridDim.x, w, mt); ++i) {
-            if (et == 0) {
-                const bool ok = mbar_wait(acc_full, aph, abort_flag);
-                *ep_ok = ok ? 1 : 0;
-                if (!ok) fail();
+        bool ok = true;
+        Steps su;
+        for (int i = 0; ok && unit_steps(a, blockIdx.x + i * gridDim.x, su); ++i) {
+            float colacc = 0.f;                 // map mode: thread et's scan column, over the unit
+            for (int w = su.w0; ok && w < su.w1; ++w)
+            for (int mt = su.mt0; mt < su.mt1; ++mt) {
+                if (et == 0) {
+                    const bool good = mbar_wait(acc_full, aph, abort_flag);
+                    *ep_ok = good ? 1 : 0;
+                    if (!good) fail();
+                }
+                named_sync(1, 128);
+                if (!*ep_ok) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const int t = a.work[2 * w + 1];
+                const unsigned long long* mask = a.mask + (size_t)w * MW;
+                const int d = mt * 128 + q * 32 + lane;
+                const uint32_t tr = tbase + ((uint32_t)(q * 32) << 16);
+                for (int c0 = 0; c0 < kN; c0 += 16) {
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = 0.f;
+                    for (int ch = 0; ch < a.nacc; ++ch) {
+                        float vr[16], vi[16];
+                        tmem_ld16(tr + ch * 2 * kN + c0, vr);
+                        tmem_ld16(tr + ch * 2 * kN + kN + c0, vi);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) v[j] = fmaf(vr[j], vr[j], fmaf(vi[j], vi[j], v[j]));
+                    }
+                    if (map_mode) {
+                        // this warp's 32 beams of each column, by a fixed shuffle tree
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            float x = d < a.n_det ? v[j] : 0.f;
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                            if (lane == 0) red[q * kN + c0 + j] = x;
+                        }
+                    } else if (d < a.n_det) {
+                        // the unit owns these cube entries: sites in order, plain adds
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int rho = t * kN + c0 + j;
+                            if ((mask[c0 >> 6] >> ((c0 & 63) + j)) & 1ull) {
+                                float* e = a.cube + (size_t)rho * a.cube_ld + d;
+                                *e += a.scale * v[j];
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty);
+                aph ^= 1;
+                if (map_mode) {
+                    // the four warps' sums in order, then the d tiles in order
+                    named_sync(1, 128);
+                    if (et < kN) colacc += ((red[et] + red[kN + et]) + red[2 * kN + et]) + red[3 * kN + et];
+                    named_sync(1, 128);
+                }
             }
-            named_sync(1, 128);
-            if (!*ep_ok) break;
-            tc_fence_after();
+            if (!ok || !map_mode || et >= kN) continue;
+            // end of a map-mode unit (one work item): its columns are written once
+            const int w = su.w0;
             const int t = a.work[2 * w + 1];
-            const unsigned long long* mask = a.mask + (size_t)w * MW;
-            const int d = mt * 128 + q * 32 + lane;
-            const uint32_t tr = tbase + ((uint32_t)(q * 32) << 16);
-            for (int c0 = 0; c0 < kN; c0 += 16) {
-                float v[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = 0.f;
-                for (int ch = 0; ch < a.nacc; ++ch) {
-                    float vr[16], vi[16];
-                    tmem_ld16(tr + ch * 2 * kN + c0, vr);
-                    tmem_ld16(tr + ch * 2 * kN + kN + c0, vi);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] = fmaf(vr[j], vr[j], fmaf(vi[j], vi[j], v[j]));
-                }
-                if (a.partial) {
-                    // map mode: the detector sum over this warp's 32 beams, one
-                    // addition per scan and warp into the site's map
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        float x = d < a.n_det ? v[j] : 0.f;
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                        const int col = t * kN + c0 + j;
-                        const int rho = a.col_nch ? col / a.col_nch : col;
-                        if (lane == 0 && ((mask[c0 >> 6] >> ((c0 & 63) + j)) & 1ull))
-                            atomicAdd(&a.partial[(size_t)a.site_ids[a.work[2 * w]] * a.P + rho], a.scale * x);
-                    }
-                } else if (d < a.n_det) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int rho = t * kN + c0 + j;
-                        if ((mask[c0 >> 6] >> ((c0 & 63) + j)) & 1ull)
-                            atomicAdd(&a.cube[(size_t)rho * a.n_det + d], a.scale * v[j]);
-                    }
-                }
+            const bool in = (a.mask[(size_t)w * MW + (et >> 6)] >> (et & 63)) & 1ull;
+            const int col = t * kN + et;
+            if (a.pcol) {
+                if (col < a.P * a.col_nch) a.pcol[(size_t)a.work[2 * w] * a.pcol_site + col] = in ? a.scale * colacc : 0.f;
+            } else if (in) {
+                float* e = a.partial + (size_t)a.site_ids[a.work[2 * w]] * a.P + col;
+                *e += a.scale * colacc;
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty);
-            aph ^= 1;
         }
     }
     tc_fence_before();
@@ -323,6 +374,19 @@ __global__ void crop_mask_kernel(CubeTcArgs a, int tn) {
         a.mask[sub] = part[threadIdx.x / 64][0] | (part[threadIdx.x / 64][1] << 32);
 }
 
+// (scan, channel) columns of the probe order: partial[site][rho] += the
+// site's columns rho ncol .. rho ncol + ncol - 1, in channel order.
+__global__ void col_reduce_kernel(const float* __restrict__ pcol, int64_t pcol_site, int n_sites,
+                                  const int32_t* __restrict__ site_ids, int P, int ncol, float* partial) {
+    const int rho = blockIdx.x * blockDim.x + threadIdx.x;
+    const int bs = blockIdx.y;
+    if (rho >= P || bs >= n_sites) return;
+    const float* c = pcol + (size_t)bs * pcol_site + (size_t)rho * ncol;
+    float v = 0.f;
+    for (int n = 0; n < ncol; ++n) v += c[n];
+    partial[(size_t)site_ids[bs] * P + rho] += v;
+}
+
 template <bool HI, int TN>
 cudaError_t launch_cube(const CubeTcArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, cudaStream_t s) {
     static bool attr = false;
@@ -332,7 +396,7 @@ cudaError_t launch_cube(const CubeTcArgs& a, const CUtensorMap& ma, const CUtens
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int units = a.n_work * a.mt_per;
+    const int units = a.mt_inner ? a.n_work : a.n_groups * a.mt_per;
     const int grid = units < num_sms() ? units : num_sms();
     cube_tc_kernel<HI, TN><<<grid, kThreads, kSmem, s>>>(ma, mb, a);
     return cudaGetLastError();
@@ -349,7 +413,13 @@ cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int 
     if (a.nacc < 1 || a.nacc * 2 * tn > (int)kTmemCols || a.kb_ch < 1 || a.mt_per < 1 || a.ch0 < 0 || a_k % 32 ||
         b_k % 32)
         return cudaErrorInvalidValue;
-    if (a.col_nch < 0 || (a.col_nch > 0 && (a.nacc != 1 || a.ch0 != 0 || !a.partial))) return cudaErrorInvalidValue;
+    // map mode (partial, or pcol with (scan, channel) columns): one work item
+    // per unit; cube mode: groups of items sharing a scan tile
+    const bool map_mode = a.partial || a.pcol;
+    if (map_mode != (a.mt_inner != 0) || (map_mode && a.cube) || (!map_mode && !a.cube)) return cudaErrorInvalidValue;
+    if (!map_mode && (a.n_groups < 1 || !a.grp || a.cube_ld < a.n_det)) return cudaErrorInvalidValue;
+    if (a.col_nch < 0 || (a.col_nch > 0) != (a.pcol != nullptr) || (a.col_nch > 0 && (a.nacc != 1 || a.ch0 != 0)))
+        return cudaErrorInvalidValue;
     // the channel range inside the operand that has channels, one channel's
     // K blocks inside the other
     const int ch_k = a.swap_ch ? b_k : a_k, one_k = a.swap_ch ? a_k : b_k;
@@ -374,4 +444,13 @@ cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int 
     if (e != cudaSuccess) return e;
     if (a.hi_only) return tn == 128 ? launch_cube<true, 128>(a, ma, mb, s) : launch_cube<true, 64>(a, ma, mb, s);
     return tn == 128 ? launch_cube<false, 128>(a, ma, mb, s) : launch_cube<false, 64>(a, ma, mb, s);
+}
+
+cudaError_t bip_cube_col_reduce(const float* pcol, int64_t pcol_site, int n_sites, const int32_t* site_ids, int P,
+                                int ncol, float* partial, cudaStream_t s) {
+    if (n_sites < 1 || P < 1) return cudaSuccess;
+    if (ncol < 1 || pcol_site < (int64_t)P * ncol) return cudaErrorInvalidValue;
+    col_reduce_kernel<<<dim3((P + 127) / 128, n_sites), 128, 0, s>>>(pcol, pcol_site, n_sites, site_ids, P, ncol,
+                                                                   partial);
+    return cudaGetLastError();
 }

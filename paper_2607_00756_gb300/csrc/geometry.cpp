@@ -3,7 +3,9 @@
 //
 //  * aperture beams {h : |q| lambda <= alpha}, kept when h = 0 mod f
 //    (Sec. 2.1; Algorithm 2 build step; Sec. 2.2.2 beam subsampling);
-//  * detector beams |q| lambda <= theta_det, PRISM-subsampled (Algorithm 4);
+//  * detector beams |q| lambda <= theta_det, PRISM-subsampled by (dfy, dfx)
+//    (Algorithm 4; qEELS wants the resolved axis at 1, Sec. 2.2.6), and the
+//    cube's complete basis, the same disc unsubsampled (Sec. 2.2.6);
 //  * hex-ring parents: DC plus n_radial rings with n_angular (1 + i) samples
 //    on ring i, snapped to the nearest beam, deduplicated (Sec. 2.2.3);
 //  * Sibson weights (Eq. nnw): the area the query's Voronoi cell takes from
@@ -288,9 +290,13 @@ bip_status bip_build_geometry(const bip_config& c, BipGeometry& g, std::string& 
     std::vector<int32_t> full = disc(c, g.lambda, c.alpha, 1, 1);
     g.n_full = (int)full.size() / 2;
     g.h_beam = disc(c, g.lambda, c.alpha, c.fy, c.fx);
-    g.h_det = disc(c, g.lambda, c.theta_det, c.fy, c.fx);
+    g.dfy = c.dfy > 0 ? c.dfy : c.fy;
+    g.dfx = c.dfx > 0 ? c.dfx : c.fx;
+    g.h_det = disc(c, g.lambda, c.theta_det, g.dfy, g.dfx);
+    g.h_cube = disc(c, g.lambda, c.theta_det, 1, 1);
     g.B = (int)g.h_beam.size() / 2;
     g.n_det = (int)g.h_det.size() / 2;
+    g.n_cube = (int)g.h_cube.size() / 2;
     if (g.B == 0 || g.n_det == 0) {
         err = "empty aperture or detector beam set";
         return BIP_ERR_SHAPE;

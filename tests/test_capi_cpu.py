@@ -40,7 +40,8 @@ def _cfgs():
     return [c1, synth.config2(), synth.tiny_config(ny=64, nx=64, win=64),
             c1.replace(name="aniso", ny=64, nx=128, ly=6.0, lx=10.0, fy=1, fx=2, win=32),
             c1.replace(name="rings", nrad1=3, nrad2=4, nang1=5, nang2=7),
-            c1.replace(name="aberrated", defocus=-35.0, cs=1e4)]
+            c1.replace(name="aberrated", defocus=-35.0, cs=1e4),
+            c1.replace(name="qeels_x", dfx=1), c1.replace(name="qeels_y", dfy=1, nrad2=3)]
 
 
 @pytest.mark.parametrize("cfg", _cfgs(), ids=lambda c: c.name)
@@ -55,6 +56,7 @@ def test_geometry_matches_oracle(capi, cfg):
         assert np.array_equal(g["p2"], og.p2)
         assert np.max(np.abs(g["w1"] - og.w1)) < 1e-12
         assert np.max(np.abs(g["w2"] - og.w2)) < 1e-12
+        assert np.array_equal(capi.bip_cube_beams(ctx), og.h_cube)
     finally:
         capi.bip_destroy(ctx)
 
@@ -79,6 +81,8 @@ def test_config2_sizes(capi):
     (dict(nz=0), "BIP_ERR_INVALID_ARG"),
     (dict(e0=-1.0), "BIP_ERR_INVALID_ARG"),
     (dict(nang1=0), "BIP_ERR_INVALID_ARG"),
+    (dict(dfx=3), "BIP_ERR_SHAPE"),
+    (dict(dfy=-1), "BIP_ERR_SHAPE"),
 ])
 def test_create_rejects_bad_config(capi, change, status):
     cfg = synth.config1().replace(**change)

@@ -141,6 +141,8 @@ def _order_check(lib, which, prec, order):
     pr = obip.make_problem(sp)
     for k in range(len(pr.ion)):
         assert np.all(parts[k][~obip.crop_mask(pr, k, sp.scans)] == 0.0)
+    # fixed summation order (no atomics): a second map is bit-identical
+    assert np.array_equal(ctx.map(H, sp.scans).cpu().numpy(), m)
     ctx.close()
 
 

@@ -202,24 +202,31 @@ def test_map_split_bf16_anisotropic(lib, prec):
 
 
 # ---------------------------------------------------------------------------
-# the 4D cube (Sec. 2.2.6)
+# the 4D cube and qEELS (Sec. 2.2.6)
+
+def _cube(ctx, sp, H, **kw):
+    V = torch.tensor(sp.V, dtype=torch.float32, device=H.device)
+    return ctx.cube(V, H, sp.scans, **kw).cpu().numpy()
+
 
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("split_bf16", 1e-3), ("mixed", 1e-3)])
 def test_cube_config1(lib, c1, prec, tol):
-    """The cube against the oracle's Algorithm 5 cube, and its detector sum
-    against the library's map (computed through the Gram route)."""
+    """The cube on the complete output basis (S1 partitioned, the exit
+    exact; 793 beams at config 1 against the map's 193) against the
+    oracle's, which is pinned to Algorithm 3 by brute force; zero outside
+    every crop mask; bit-identical on a second run (no atomics)."""
     cfg, sp, pr, ref = c1
     want = obip.bip_cube(pr)
     ctx, m, _, H = gpu_run(lib, cfg, sp, prec=prec)
-    cube = ctx.cube(H, sp.scans).cpu().numpy()
-    assert cube.shape == want.shape
+    assert np.array_equal(ctx.cube_beams, pr.geo.h_cube)
+    cube = _cube(ctx, sp, H)
+    assert cube.shape == want.shape == (len(sp.scans), 793)
     assert rel(cube, want) < tol
-    assert rel(cube.astype(np.float64).sum(axis=1), m) < 1e-4
-    # zero outside every crop mask
     outside = np.ones(len(sp.scans), bool)
     for k in range(len(pr.ion)):
         outside &= ~obip.crop_mask(pr, k, pr.scans)
     assert np.all(cube[outside] == 0.0)
+    assert np.array_equal(_cube(ctx, sp, H), cube)
 
 
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("mixed", 1e-3)])
@@ -231,25 +238,72 @@ def test_cube_edge_cases(lib, prec, tol):
     pr = obip.make_problem(sp)
     want = obip.bip_cube(pr)
     ctx, m, _, H = gpu_run(lib, cfg, sp, prec=prec)
-    cube = ctx.cube(H, sp.scans).cpu().numpy()
+    cube = _cube(ctx, sp, H)
     assert rel(cube, want) < tol
-    assert rel(cube.astype(np.float64).sum(axis=1), m) < 1e-3
+    assert np.array_equal(_cube(ctx, sp, H), cube)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
+def test_cube_in_beam_batches(lib, c1, prec):
+    """A memory limit that splits the complete basis into several backward
+    sweeps (13 batches of 64 beams at config 1) gives the cube of one sweep."""
+    cfg, sp, pr, ref = c1
+    ctx, m, _, H = gpu_run(lib, cfg, sp, prec=prec)
+    one = _cube(ctx, sp, H)
+    per_beam = (len(pr.ion) * cfg.win * cfg.win + cfg.ny * cfg.nx) * 8
+    ctx.set_cube_memory(64 * per_beam + 1)
+    many = _cube(ctx, sp, H)
+    assert rel(many, one) < 1e-6
+    assert rel(many, obip.bip_cube(pr)) < (1e-4 if prec == "fp32" else 1e-3)
+
+
+def test_cube_refuses_fp8_and_a_missing_build(lib, c1):
+    from paper_2607_00756_gb300.capi import BipError, STATUS
+    cfg, sp, pr, ref = c1
+    dev = torch.device("cuda:0")
+    H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+    V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
+    ctx = lib(cfg, prec="mixed")
+    with pytest.raises(BipError) as e:
+        ctx.cube(V, H, sp.scans)
+    assert STATUS[e.value.status] == "BIP_ERR_INVALID_ARG"
+    ctx.close()
+    ctx, *_ = gpu_run(lib, cfg, sp, prec="fp8")
+    with pytest.raises(BipError) as e:
+        ctx.cube(V, H, sp.scans)
+    assert STATUS[e.value.status] == "BIP_ERR_UNSUPPORTED"
+    ctx.close()
 
 
 @pytest.mark.parametrize("prec", ["fp32", "mixed"])
 @pytest.mark.parametrize("axis", [0, 1])
-def test_qeels_config1(lib, c1, axis, prec):
-    """qEELS against the oracle's binning of its cube; the bins summed give
-    the library's map."""
-    cfg, sp, pr, ref = c1
-    hb_want, want = obip.qeels(pr, obip.bip_cube(pr), axis)
+def test_qeels_config1(lib, axis, prec):
+    """qEELS with the resolved axis sampled at f = 1 (S2 partitioned on
+    that detector set) against the oracle's; the bins summed give the
+    library's map of the same context."""
+    cfg = synth.config1().replace(**({"dfy": 1} if axis == 0 else {"dfx": 1}))
+    sp = synth.make_specimen(cfg)
+    pr = obip.make_problem(sp)
+    hb_want, want = obip.bip_qeels(pr, axis)
     ctx, m, _, H = gpu_run(lib, cfg, sp, prec=prec)
+    assert ctx.n_det == pr.geo.n_det
     hb, q = ctx.qeels(H, sp.scans, axis)
     assert np.array_equal(hb, hb_want)
     q = q.cpu().numpy()
     tol = 1e-4 if prec == "fp32" else 1e-3
     assert rel(q, want) < tol
     assert rel(q.astype(np.float64).sum(axis=1), m) < tol
+    assert rel(m, obip.bip_map(pr).map) < tol
+
+
+def test_qeels_refuses_a_subsampled_axis(lib, c1):
+    from paper_2607_00756_gb300.capi import BipError, STATUS
+    cfg, sp, pr, ref = c1
+    ctx, m, _, H = gpu_run(lib, cfg, sp)
+    for axis in (0, 1):
+        with pytest.raises(BipError) as e:
+            ctx.qeels(H, sp.scans, axis)
+        assert STATUS[e.value.status] == "BIP_ERR_INVALID_ARG"
 
 
 # ---------------------------------------------------------------------------
@@ -322,18 +376,24 @@ def test_map_fp8_anisotropic(lib):
     assert rel(m, ref.map) < 2.0 * e_model + 1e-3
 
 
-def test_cube_fp8_config1(lib, c1):
-    """The cube through the FP8 coupling against the FP64 cube, bounded like
+def test_qeels_fp8_config1(lib):
+    """qEELS through the FP8 coupling against the FP64 qEELS, bounded like
     the map by twice the FP8 model's own error (per detector beam); its
-    detector sum is the FP8 map."""
+    bins sum to the FP8 map."""
     from oracle import fp8
-    cfg, sp, pr, ref = c1
-    want = obip.bip_cube(pr)
-    e_model = rel(fp8.bip_cube_fp8(pr), want)
+    cfg = synth.config1().replace(dfx=1)
+    sp = synth.make_specimen(cfg)
+    pr = obip.make_problem(sp)
+    bins, want = obip.bip_qeels(pr, 1)
+    pb = fp8.per_beam_fp8(pr)
+    hd = pr.geo.h_det[:, 1]
+    model = np.stack([pb[:, hd == b].sum(axis=1) for b in bins], axis=1)
+    e_model = rel(model, want)
     ctx, m, _, H = gpu_run(lib, cfg, sp, prec="fp8")
-    cube = ctx.cube(H, sp.scans).cpu().numpy()
-    assert rel(cube, want) < 2.0 * e_model + 1e-3, (rel(cube, want), e_model)
-    assert rel(cube.astype(np.float64).sum(axis=1), m) < 1e-4
+    _, q = ctx.qeels(H, sp.scans, 1)
+    q = q.cpu().numpy()
+    assert rel(q, want) < 2.0 * e_model + 1e-3, (rel(q, want), e_model)
+    assert rel(q.astype(np.float64).sum(axis=1), m) < 1e-4
 
 
 # ---------------------------------------------------------------------------
