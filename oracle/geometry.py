@@ -152,22 +152,33 @@ def convex_hull_int(pts):
 # --------------------------------------------------------------------------
 # Sibson weights
 
-def _edge_weights(hull_idx, hull_q, qb):
+def _hull_edges(hull_pts):
+    """Edges (position pairs in the hull list) of the hull polygon; when
+    every parent lies on one line the hull is a segment, whose edges are
+    only the pieces between consecutive parents (no closing edge back over
+    the whole segment)."""
+    n = len(hull_pts)
+    collinear = all(_cross_int(hull_pts[0], hull_pts[1], hull_pts[i]) == 0 for i in range(2, n))
+    if collinear:
+        return [(e, e + 1) for e in range(n - 1)]
+    return [(e, (e + 1) % n) for e in range(n)]
+
+
+def _edge_weights(hull_idx, hull_q, edges, qb):
     """Linear weights on the hull edge nearest to qb (physical metric)."""
     best = None
-    n = len(hull_idx)
-    for e in range(n):
-        a = hull_q[e]
-        b = hull_q[(e + 1) % n]
+    for e0, e1 in edges:
+        a = hull_q[e0]
+        b = hull_q[e1]
         d = b - a
         dd = float(d @ d)
         t = 0.0 if dd == 0.0 else float(np.clip((qb - a) @ d / dd, 0.0, 1.0))
         p = a + t * d
         dist = float((qb - p) @ (qb - p))
         if best is None or dist < best[0] - 1e-300:
-            best = (dist, e, t)
-    _, e, t = best
-    return {hull_idx[e]: 1.0 - t, hull_idx[(e + 1) % n]: t}
+            best = (dist, e0, e1, t)
+    _, e0, e1, t = best
+    return {hull_idx[e0]: 1.0 - t, hull_idx[e1]: t}
 
 
 def _strictly_inside(hull_pts, hb):
@@ -211,6 +222,7 @@ def sibson_weights(parent_h, query_h, ly, lx):
     hull_pts = convex_hull_int(parent_h)
     hull_idx = [lut[p] for p in hull_pts]
     hull_q = pq[hull_idx]
+    edges = _hull_edges(hull_pts) if len(hull_pts) >= 2 else []
     for b in range(nq):
         hb = (int(query_h[b, 0]), int(query_h[b, 1]))
         if hb in lut:
@@ -221,7 +233,7 @@ def sibson_weights(parent_h, query_h, ly, lx):
             W[b, 0] = 1.0
             continue
         if not _strictly_inside(hull_pts, hb):
-            for p, w in _edge_weights(hull_idx, hull_q, qb).items():
+            for p, w in _edge_weights(hull_idx, hull_q, edges, qb).items():
                 W[b, p] += w
             continue
         rel = pq - qb

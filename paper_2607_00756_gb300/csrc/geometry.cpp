@@ -9,7 +9,9 @@
 //  * hex-ring parents: DC plus n_radial rings with n_angular (1 + i) samples
 //    on ring i, snapped to the nearest beam, deduplicated (Sec. 2.2.3);
 //  * Sibson weights (Eq. nnw): the area the query's Voronoi cell takes from
-//    each parent's cell over the cell's area, by half-plane clipping.
+//    each parent's cell over the cell's area, from the parents' Delaunay
+//    triangulation and the circumcentres of the triangles the query's
+//    insertion removes (Watson's construction).
 //
 // Readings where the paper is silent: beams sorted by (h_y, h_x); aperture
 // edge inclusive with 1e-12 relative slack; ring radius R (i+1)/n_radial
@@ -96,78 +98,110 @@ std::vector<int32_t> hex_ring(const std::vector<int32_t>& h, double ly, double l
     return chosen;
 }
 
-// ---- convex polygons in relative physical coordinates
-using Pt = std::pair<double, double>;   // (y, x)
+// ---- natural-neighbour (Sibson) coordinates from the Delaunay
+// triangulation of the parents and the circumcentres of the triangles a
+// query would destroy (Watson's construction): inserting q removes the
+// triangles whose circumcircle holds it (the cavity); q's Voronoi cell is
+// the polygon of the circumcentres of the new triangles (q, v_i, v_i+1)
+// around the cavity boundary, and the part it takes from v_i's old cell is
+// the convex polygon of the new circumcentres on either side of v_i and the
+// circumcentres of the cavity triangles at v_i, in order around v_i.
+//
+// Positions are physical (x = h_x / l_x, y = h_y / l_y); orientation tests
+// run exactly on the integer indices (scaling the axes keeps their sign),
+// the in-circle test in FP64 with an error bound, within which the point is
+// taken as on the circle (lattice points: exact zeros stay zero).
 
-std::vector<Pt> clip(const std::vector<Pt>& poly, double a0, double a1, double c) {
-    std::vector<Pt> out;
-    const size_t n = poly.size();
-    out.reserve(n + 2);
-    for (size_t i = 0; i < n; ++i) {
-        const Pt& p = poly[i];
-        const Pt& q = poly[(i + 1) % n];
-        double fp = a0 * p.first + a1 * p.second - c;
-        double fq = a0 * q.first + a1 * q.second - c;
-        if (fp <= 0.0) out.push_back(p);
-        if ((fp < 0.0 && fq > 0.0) || (fq < 0.0 && fp > 0.0)) {
-            double t = fp / (fp - fq);
-            out.push_back({p.first + t * (q.first - p.first), p.second + t * (q.second - p.second)});
-        }
-    }
-    return out;
+struct Node {
+    int64_t ix, iy;     // integer beam index (h_x, h_y)
+    double x, y;        // physical position
+};
+
+// > 0: c left of a -> b (counter-clockwise a, b, c), exact
+int orient(const Node& a, const Node& b, const Node& c) {
+    const int64_t v = (b.ix - a.ix) * (c.iy - a.iy) - (b.iy - a.iy) * (c.ix - a.ix);
+    return (v > 0) - (v < 0);
 }
 
-double area(const std::vector<Pt>& poly) {
-    if (poly.size() < 3) return 0.0;
+// > 0: d strictly inside the circumcircle of the counter-clockwise triangle
+// (a, b, c); 0 on it (within the FP64 error bound); < 0 outside
+int incircle(const Node& a, const Node& b, const Node& c, const Node& d) {
+    const double ax = a.x - d.x, ay = a.y - d.y, bx = b.x - d.x, by = b.y - d.y, cx = c.x - d.x, cy = c.y - d.y;
+    const double al = ax * ax + ay * ay, bl = bx * bx + by * by, cl = cx * cx + cy * cy;
+    const double t1 = al * (bx * cy - by * cx), t2 = bl * (cx * ay - cy * ax), t3 = cl * (ax * by - ay * bx);
+    const double det = t1 + t2 + t3;
+    const double perm = al * (std::fabs(bx * cy) + std::fabs(by * cx)) + bl * (std::fabs(cx * ay) + std::fabs(cy * ax)) +
+                        cl * (std::fabs(ax * by) + std::fabs(ay * bx));
+    if (std::fabs(det) <= 1e-12 * perm) return 0;
+    return det > 0.0 ? 1 : -1;
+}
+
+struct Tri {
+    int v[3];           // counter-clockwise
+};
+
+// centre of the circle through p, q, r, relative to the origin of (x, y)
+void circumcentre(double px, double py, double qx, double qy, double rx, double ry, double& cx, double& cy) {
+    const double ax = qx - px, ay = qy - py, bx = rx - px, by = ry - py;
+    const double d = 2.0 * (ax * by - ay * bx);
+    const double a2 = ax * ax + ay * ay, b2 = bx * bx + by * by;
+    cx = px + (by * a2 - ay * b2) / d;
+    cy = py + (ax * b2 - bx * a2) / d;
+}
+
+double polygon_area(const std::vector<double>& xs, const std::vector<double>& ys) {
     double s = 0.0;
-    for (size_t i = 0; i < poly.size(); ++i) {
-        const Pt& a = poly[i];
-        const Pt& b = poly[(i + 1) % poly.size()];
-        s += a.second * b.first - b.second * a.first;
+    const size_t n = xs.size();
+    for (size_t i = 0; i < n; ++i) {
+        const size_t j = (i + 1) % n;
+        s += xs[i] * ys[j] - xs[j] * ys[i];
     }
     return 0.5 * std::fabs(s);
 }
 
-using IPt = std::pair<int64_t, int64_t>;
-
-int64_t cross(const IPt& o, const IPt& a, const IPt& b) {
-    return (a.first - o.first) * (b.second - o.second) - (a.second - o.second) * (b.first - o.first);
-}
-
-// convex hull keeping collinear boundary points (monotone chain)
-std::vector<IPt> hull(std::vector<IPt> P) {
-    std::sort(P.begin(), P.end());
-    P.erase(std::unique(P.begin(), P.end()), P.end());
-    if (P.size() <= 2) return P;
-    std::vector<IPt> lo, up;
-    for (auto& p : P) {
-        while (lo.size() >= 2 && cross(lo[lo.size() - 2], lo.back(), p) < 0) lo.pop_back();
-        lo.push_back(p);
+// Delaunay triangulation by walking edges: every directed edge a -> b still
+// open gets the triangle on its left whose circumcircle holds no other
+// point (the candidate replaced only by a point strictly inside the current
+// circle; among points on one circle any choice triangulates the empty
+// polygon, since later edges only see points on their own left).
+std::vector<Tri> delaunay(const std::vector<Node>& P) {
+    const int n = (int)P.size();
+    std::vector<Tri> tris;
+    if (n < 3) return tris;
+    // first hull edge: from the lowest point (then leftmost) to the point
+    // with no other point strictly right of the edge, the nearest of any
+    // collinear ones
+    int a = 0;
+    for (int i = 1; i < n; ++i)
+        if (P[i].iy < P[a].iy || (P[i].iy == P[a].iy && P[i].ix < P[a].ix)) a = i;
+    int b = -1;
+    for (int i = 0; i < n; ++i) {
+        if (i == a) continue;
+        if (b < 0) { b = i; continue; }
+        const int o = orient(P[a], P[b], P[i]);
+        const auto d2 = [&](int k) { return (P[k].ix - P[a].ix) * (P[k].ix - P[a].ix) + (P[k].iy - P[a].iy) * (P[k].iy - P[a].iy); };
+        if (o < 0 || (o == 0 && d2(i) < d2(b))) b = i;
     }
-    for (auto it = P.rbegin(); it != P.rend(); ++it) {
-        while (up.size() >= 2 && cross(up[up.size() - 2], up.back(), *it) < 0) up.pop_back();
-        up.push_back(*it);
+    std::set<std::pair<int, int>> done;
+    std::vector<std::pair<int, int>> open{{a, b}};
+    while (!open.empty()) {
+        const auto e = open.back();
+        open.pop_back();
+        if (!done.insert(e).second) continue;
+        int best = -1;
+        for (int c = 0; c < n; ++c) {
+            if (c == e.first || c == e.second || orient(P[e.first], P[e.second], P[c]) <= 0) continue;
+            if (best < 0 || incircle(P[e.first], P[e.second], P[best], P[c]) > 0) best = c;
+        }
+        if (best < 0) continue;   // a hull edge: nothing on its left
+        tris.push_back(Tri{{e.first, e.second, best}});
+        done.insert({e.second, best});
+        done.insert({best, e.first});
+        // the neighbours across the two new edges lie on the left of their reverses
+        open.push_back({best, e.second});
+        open.push_back({e.first, best});
     }
-    std::vector<IPt> h(lo.begin(), lo.end() - 1);
-    h.insert(h.end(), up.begin(), up.end() - 1);
-    std::vector<IPt> out;
-    std::set<IPt> seen;
-    for (auto& p : h)
-        if (seen.insert(p).second) out.push_back(p);
-    return out;
-}
-
-bool strictly_inside(const std::vector<IPt>& H, const IPt& q) {
-    const size_t n = H.size();
-    if (n < 3) return false;
-    int64_t s = 0;
-    for (size_t i = 0; i < n; ++i) s += cross({0, 0}, H[i], H[(i + 1) % n]);
-    const int orient = s > 0 ? 1 : -1;
-    for (size_t i = 0; i < n; ++i) {
-        int64_t c = cross(H[i], H[(i + 1) % n], q);
-        if (c * orient <= 0) return false;
-    }
-    return true;
+    return tris;
 }
 
 }  // namespace
@@ -177,86 +211,112 @@ void bip_sibson_weights(const std::vector<int32_t>& parents, const std::vector<i
     const int np = (int)parents.size() / 2, nq = (int)queries.size() / 2;
     W.assign((size_t)nq * np, 0.0);
     if (np == 0) return;
-    std::vector<double> py(np), px(np);
-    std::map<IPt, int> lut;
-    std::vector<IPt> pts;
+    std::vector<Node> P(np);
+    std::map<std::pair<int64_t, int64_t>, int> at;
     for (int i = 0; i < np; ++i) {
-        py[i] = parents[2 * i] / ly;
-        px[i] = parents[2 * i + 1] / lx;
-        IPt ip{parents[2 * i], parents[2 * i + 1]};
-        lut[ip] = i;
-        pts.push_back(ip);
+        P[i] = Node{parents[2 * i + 1], parents[2 * i], parents[2 * i + 1] / lx, parents[2 * i] / ly};
+        at[{P[i].ix, P[i].iy}] = i;
     }
-    const std::vector<IPt> H = hull(pts);
-    std::vector<int> hidx;
-    for (auto& p : H) hidx.push_back(lut[p]);
+    const std::vector<Tri> T = delaunay(P);
+    // hull edges: directed triangle edges (counter-clockwise) without the
+    // reverse; with no triangle (collinear parents) the chain of consecutive
+    // points along the line, both ways
+    std::set<std::pair<int, int>> dir;
+    for (const Tri& t : T)
+        for (int k = 0; k < 3; ++k) dir.insert({t.v[k], t.v[(k + 1) % 3]});
+    std::vector<std::pair<int, int>> hull;
+    for (const auto& e : dir)
+        if (!dir.count({e.second, e.first})) hull.push_back(e);
+    if (T.empty() && np >= 2) {
+        std::vector<int> ord(np);
+        for (int i = 0; i < np; ++i) ord[i] = i;
+        const double ux = P[np - 1].x - P[0].x, uy = P[np - 1].y - P[0].y;
+        std::sort(ord.begin(), ord.end(), [&](int i, int j) { return P[i].x * ux + P[i].y * uy < P[j].x * ux + P[j].y * uy; });
+        for (int i = 0; i + 1 < np; ++i) hull.push_back({ord[i], ord[i + 1]});
+    }
 
-    for (int b = 0; b < nq; ++b) {
-        double* w = &W[(size_t)b * np];
-        IPt hb{queries[2 * b], queries[2 * b + 1]};
-        auto it = lut.find(hb);
-        if (it != lut.end()) { w[it->second] = 1.0; continue; }
+    for (int qi = 0; qi < nq; ++qi) {
+        double* w = &W[(size_t)qi * np];
+        const Node q{queries[2 * qi + 1], queries[2 * qi], queries[2 * qi + 1] / lx, queries[2 * qi] / ly};
+        auto it = at.find({q.ix, q.iy});
+        if (it != at.end()) { w[it->second] = 1.0; continue; }
         if (np == 1) { w[0] = 1.0; continue; }
-        const double qy = hb.first / ly, qx = hb.second / lx;
-        if (!strictly_inside(H, hb)) {
-            // nearest hull edge, linear weights of its end points
+        // strictly inside the hull: strictly left of every hull edge
+        bool inside = !T.empty();
+        for (const auto& e : hull)
+            if (inside && orient(P[e.first], P[e.second], q) <= 0) inside = false;
+        if (!inside) {
+            // on or outside the hull: the nearest hull edge's linear weights
             double best = INFINITY, bt = 0.0;
-            int be = 0;
-            const int nh = (int)hidx.size();
-            for (int e = 0; e < nh; ++e) {
-                int i0 = hidx[e], i1 = hidx[(e + 1) % nh];
-                double dy = py[i1] - py[i0], dx = px[i1] - px[i0];
-                double dd = dy * dy + dx * dx;
-                double t = dd == 0.0 ? 0.0 : ((qy - py[i0]) * dy + (qx - px[i0]) * dx) / dd;
-                t = std::min(1.0, std::max(0.0, t));
-                double ey = qy - (py[i0] + t * dy), ex = qx - (px[i0] + t * dx);
-                double d = ey * ey + ex * ex;
-                if (d < best) { best = d; be = e; bt = t; }
+            int e0 = hull[0].first, e1 = hull[0].second;
+            for (const auto& e : hull) {
+                const Node &u = P[e.first], &v = P[e.second];
+                const double dx = v.x - u.x, dy = v.y - u.y, dd = dx * dx + dy * dy;
+                double t = ((q.x - u.x) * dx + (q.y - u.y) * dy) / dd;
+                t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+                const double ex = q.x - (u.x + t * dx), ey = q.y - (u.y + t * dy), d = ex * ex + ey * ey;
+                if (d < best) { best = d; bt = t; e0 = e.first; e1 = e.second; }
             }
-            w[hidx[be]] += 1.0 - bt;
-            w[hidx[(be + 1) % nh]] += bt;
+            w[e0] += 1.0 - bt;
+            w[e1] += bt;
             continue;
         }
-        // interior: Voronoi cell of the query against all parents
-        std::vector<double> ry(np), rx(np), dist(np);
-        for (int i = 0; i < np; ++i) {
-            ry[i] = py[i] - qy;
-            rx[i] = px[i] - qx;
-            dist[i] = std::sqrt(ry[i] * ry[i] + rx[i] * rx[i]);
+        // the cavity: triangles whose circumcircle holds q strictly
+        std::vector<int> cav;
+        for (int t = 0; t < (int)T.size(); ++t)
+            if (incircle(P[T[t].v[0]], P[T[t].v[1]], P[T[t].v[2]], q) > 0) cav.push_back(t);
+        std::map<std::pair<int, int>, int> edge_tri;      // directed cavity edge -> its triangle
+        for (int t : cav)
+            for (int k = 0; k < 3; ++k) edge_tri[{T[t].v[k], T[t].v[(k + 1) % 3]}] = t;
+        std::map<int, int> next;                          // boundary, counter-clockwise around q
+        for (const auto& et : edge_tri)
+            if (!edge_tri.count({et.first.second, et.first.first})) next[et.first.first] = et.first.second;
+        std::vector<int> ring{next.begin()->first};
+        while ((int)ring.size() <= (int)next.size()) {
+            const int v = next[ring.back()];
+            if (v == ring[0]) break;
+            ring.push_back(v);
         }
-        std::vector<int> order(np);
-        for (int i = 0; i < np; ++i) order[i] = i;
-        std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return dist[a] < dist[c]; });
-        double box = 4.0 * *std::max_element(dist.begin(), dist.end());
-        std::vector<Pt> cell;
-        for (;;) {
-            cell = {{-box, -box}, {-box, box}, {box, box}, {box, -box}};
-            for (int j : order) {
-                cell = clip(cell, 2.0 * ry[j], 2.0 * rx[j], ry[j] * ry[j] + rx[j] * rx[j]);
-                if (cell.empty()) break;
+        const int m = (int)ring.size();
+        // circumcentres relative to q
+        auto cc = [&](int i, int j, int k, bool with_q, double& cx, double& cy) {
+            if (with_q)
+                circumcentre(0.0, 0.0, P[i].x - q.x, P[i].y - q.y, P[j].x - q.x, P[j].y - q.y, cx, cy);
+            else
+                circumcentre(P[i].x - q.x, P[i].y - q.y, P[j].x - q.x, P[j].y - q.y, P[k].x - q.x, P[k].y - q.y, cx,
+                             cy);
+        };
+        std::vector<double> stolen(m, 0.0);
+        double total = 0.0;
+        for (int i = 0; i < m; ++i) {
+            const int vi = ring[i], vn = ring[(i + 1) % m], vp = ring[(i + m - 1) % m];
+            std::vector<double> xs, ys;
+            double cx, cy;
+            cc(vi, vn, -1, true, cx, cy);
+            xs.push_back(cx);
+            ys.push_back(cy);
+            // the cavity triangles at vi, counter-clockwise from the edge vi -> vn
+            int a = vn;
+            for (int guard = 0; guard <= (int)cav.size(); ++guard) {
+                auto f = edge_tri.find({vi, a});
+                if (f == edge_tri.end()) break;
+                const Tri& t = T[f->second];
+                int b = -1;
+                for (int k = 0; k < 3; ++k)
+                    if (t.v[k] == vi) b = t.v[(k + 2) % 3];
+                cc(t.v[0], t.v[1], t.v[2], false, cx, cy);
+                xs.push_back(cx);
+                ys.push_back(cy);
+                if (b == vp) break;
+                a = b;
             }
-            double rmax = 0.0;
-            for (auto& p : cell) rmax = std::max(rmax, std::max(std::fabs(p.first), std::fabs(p.second)));
-            if (rmax < box * (1.0 - 1e-9)) break;
-            box *= 4.0;
+            cc(vp, vi, -1, true, cx, cy);
+            xs.push_back(cx);
+            ys.push_back(cy);
+            stolen[i] = polygon_area(xs, ys);
+            total += stolen[i];
         }
-        const double a_new = area(cell);
-        double r_new = 0.0;
-        for (auto& p : cell) r_new = std::max(r_new, std::hypot(p.first, p.second));
-        const double lim = 2.0 * r_new + dist[order[0]] + 1e-12 * r_new;
-        std::vector<int> cand;
-        for (int j : order)
-            if (dist[j] <= lim) cand.push_back(j);
-        for (int p : cand) {
-            std::vector<Pt> piece = cell;
-            for (int j : cand) {
-                if (j == p) continue;
-                piece = clip(piece, 2.0 * (ry[j] - ry[p]), 2.0 * (rx[j] - rx[p]),
-                             (ry[j] * ry[j] + rx[j] * rx[j]) - (ry[p] * ry[p] + rx[p] * rx[p]));
-                if (piece.empty()) break;
-            }
-            w[p] = area(piece) / a_new;
-        }
+        for (int i = 0; i < m; ++i) w[ring[i]] += stolen[i] / total;
     }
 }
 

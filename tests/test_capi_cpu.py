@@ -224,3 +224,54 @@ def test_noalloc_wrapper_refuses_wrong_stash_shape(capi):
             capi.bip_build_s1_noalloc(ctx, V, atoms, ok)
     finally:
         capi.bip_destroy(ctx)
+
+
+def test_geometry_random_rings_match_oracle(capi):
+    """The library's Sibson weights (Delaunay triangulation, Watson's
+    circumcentre construction) against the oracle's (half-plane clipping of
+    Voronoi cells) on seeded random geometries: ring counts 0..5 with 1..8
+    samples (collinear and tiny parent sets included), anisotropic cells,
+    f = 1 or 2, several apertures and detector discs."""
+    rng = np.random.default_rng(7)
+    checked = 0
+    for _ in range(30):
+        cfg = synth.config1().replace(
+            ny=int(rng.choice([64, 128])), nx=int(rng.choice([64, 128])),
+            ly=float(rng.choice([5.0, 7.5, 10.0, 12.3])), lx=float(rng.choice([5.0, 7.5, 10.0, 13.7])),
+            fy=int(rng.choice([1, 2])), fx=int(rng.choice([1, 2])), win=16,
+            nrad1=int(rng.integers(0, 6)), nang1=int(rng.integers(1, 9)),
+            nrad2=int(rng.integers(0, 6)), nang2=int(rng.integers(1, 9)),
+            alpha=float(rng.choice([0.01, 0.02, 0.03])), theta_det=float(rng.choice([0.02, 0.04])))
+        try:
+            ctx = capi.bip_create(capi.make_config(cfg))
+        except capi.BipError:
+            continue          # a disc beyond the grid's band
+        try:
+            g = capi.bip_get_geometry(ctx)
+        finally:
+            capi.bip_destroy(ctx)
+        og = G.Geometry(cfg, ph.wavelength(cfg.e0))
+        assert np.array_equal(g["p1"], og.p1) and np.array_equal(g["p2"], og.p2)
+        assert np.max(np.abs(g["w1"] - og.w1)) < 1e-12
+        assert np.max(np.abs(g["w2"] - og.w2)) < 1e-12
+        checked += 1
+    assert checked >= 20
+
+
+def test_geometry_many_parents_is_fast(capi):
+    """n_radial = 12 (443 and 469 parents at config 2's sizes): the host
+    geometry stays well under a second and agrees with the oracle."""
+    import time
+    cfg = synth.config2().replace(nrad1=12, nrad2=12)
+    t0 = time.perf_counter()
+    ctx = capi.bip_create(capi.make_config(cfg))
+    dt = time.perf_counter() - t0
+    try:
+        assert capi.bip_query(ctx)[2:4] == (443, 469)
+        g = capi.bip_get_geometry(ctx)
+    finally:
+        capi.bip_destroy(ctx)
+    assert dt < 1.0
+    og = G.Geometry(cfg, ph.wavelength(cfg.e0))
+    assert np.max(np.abs(g["w1"] - og.w1)) < 1e-12
+    assert np.max(np.abs(g["w2"] - og.w2)) < 1e-12

@@ -129,3 +129,18 @@ def test_hull_rule_linear_on_edges():
     assert np.allclose(W[0], [0.75, 0.25, 0, 0, 0], atol=1e-15)
     assert np.allclose(W[1], [0, 0.75, 0, 0.25, 0], atol=1e-15)
     assert np.allclose(W[2], [0.5, 0.5, 0, 0, 0], atol=1e-15)
+
+
+def test_hull_rule_on_a_collinear_parent_set():
+    """Parents all on one line (a ring of two samples): the hull is a
+    segment, and a query on it or off it takes the linear weights of the
+    two consecutive parents around its projection -- never of the segment's
+    far end (reading of the hull rule for a degenerate hull)."""
+    parents = np.array([[0, 0], [0, 5], [0, -5]])
+    queries = np.array([[0, 3], [0, 4], [0, -2], [2, 1], [-1, 7]])
+    W = G.sibson_weights(parents, queries, 7.5, 7.5)
+    np.testing.assert_allclose(W[0], [0.4, 0.6, 0.0], atol=1e-15)
+    np.testing.assert_allclose(W[1], [0.2, 0.8, 0.0], atol=1e-15)
+    np.testing.assert_allclose(W[2], [0.6, 0.0, 0.4], atol=1e-15)
+    np.testing.assert_allclose(W[3], [0.8, 0.2, 0.0], atol=1e-15)
+    np.testing.assert_allclose(W[4], [0.0, 1.0, 0.0], atol=1e-15)
