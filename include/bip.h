@@ -385,6 +385,24 @@ bip_status bip_get_profile(bip_ctx* ctx, double* ms, int64_t* launches);
 bip_status bip_build_s1_noalloc(bip_ctx* ctx, const float* V, const bip_atom* atoms,
                                 int32_t n_atoms, void* stash, void* stream);
 
+/* Failure handling, for tests and for callers that want short limits.
+ * bip_set_wait_limit: the give-up limit (ns) of every wait inside the
+ *   tensor-core kernels of this context (0: the built-in 4 s).  A wait that
+ *   gives up makes the kernel stop issuing work, let its copies and MMAs in
+ *   flight finish (bounded by the built-in limit), free its tensor memory
+ *   and set a flag, which the call returns as BIP_ERR_TIMEOUT (capture-safe
+ *   contexts: bip_check_errors).  The context stays usable.
+ * bip_debug_fail_alloc(k): the k-th device allocation the library makes
+ *   from now on (in any context) fails as if the device were out of memory,
+ *   so that the call returns BIP_ERR_OOM; 0 turns it off.  Resets the count
+ *   bip_debug_allocs reports as made.
+ * bip_debug_allocs: the device allocations of the library alive now (every
+ *   context's workspaces) and made since the last bip_debug_fail_alloc
+ *   (either pointer may be NULL). */
+bip_status bip_set_wait_limit(bip_ctx* ctx, int64_t ns);
+bip_status bip_debug_fail_alloc(int64_t k);
+bip_status bip_debug_allocs(int64_t* live, int64_t* made);
+
 /* Text of the last error on this context ("" if none; static text if ctx
  * is NULL). */
 const char* bip_last_error(const bip_ctx* ctx);

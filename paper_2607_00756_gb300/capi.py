@@ -64,6 +64,9 @@ def _load():
         "bip_coreloss_cube": [VP, VP, VP, P(D), I32, VP, VP],
         "bip_cube_beams": [VP, P(I32), P(I32)],
         "bip_set_cube_memory": [VP, ctypes.c_int64],
+        "bip_set_wait_limit": [VP, ctypes.c_int64],
+        "bip_debug_fail_alloc": [ctypes.c_int64],
+        "bip_debug_allocs": [P(ctypes.c_int64), P(ctypes.c_int64)],
         "bip_qeels_bins": [VP, I32, P(I32), P(I32)],
         "bip_coreloss_qeels": [VP, VP, P(D), I32, I32, VP, VP],
         "bip_copy_stash": [VP, I32, I32, VP, VP],
@@ -270,6 +273,22 @@ def bip_cube_beams(ctx):
     _check("bip_cube_beams", ctx, _lib.bip_cube_beams(ctx, ctypes.byref(n),
                                                        h.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
     return h
+
+
+def bip_set_wait_limit(ctx, ns):
+    _check("bip_set_wait_limit", ctx, _lib.bip_set_wait_limit(ctx, int(ns)))
+
+
+def bip_debug_fail_alloc(k):
+    _check("bip_debug_fail_alloc", None, _lib.bip_debug_fail_alloc(int(k)))
+
+
+def bip_debug_allocs():
+    """(live device allocations of the library, allocations made since the
+    last bip_debug_fail_alloc)."""
+    live, made = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check("bip_debug_allocs", None, _lib.bip_debug_allocs(ctypes.byref(live), ctypes.byref(made)))
+    return live.value, made.value
 
 
 def bip_set_cube_memory(ctx, nbytes):

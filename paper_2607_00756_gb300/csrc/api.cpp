@@ -1,6 +1,7 @@
 // C ABI of the BiP-PRISM library: argument checks, host geometry, device
 // tables and the order of the kernels (Algorithm 5).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -94,6 +95,7 @@ struct bip_ctx {
     size_t ev_used = 0;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_rec;
     int64_t launches[BIP_N_STAGES] = {0};
+    uint64_t wait_ns = 0;               // give-up limit of the tcgen05 kernels' waits (0: 4 s)
 };
 
 namespace {
@@ -153,6 +155,11 @@ struct StageTimer {
         CUDA_TRY(c, expr);               \
     } while (0)
 
+// Device allocations of the library, counted for tests: the live ones, the
+// ones made, and an injected failure (the fail_at-th allocation from the
+// moment it is set fails as if the device were out of memory).
+std::atomic<int64_t> g_live{0}, g_made{0}, g_fail_at{0};
+
 cudaError_t ensure(DevBuf& b, size_t bytes, bool zero = false, cudaStream_t s = nullptr) {
     if (bytes == 0) bytes = 16;
     if (b.cap >= bytes) return cudaSuccess;
@@ -160,21 +167,29 @@ cudaError_t ensure(DevBuf& b, size_t bytes, bool zero = false, cudaStream_t s = 
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
         cudaFree(b.p);
+        --g_live;
         b.p = nullptr;
         b.cap = 0;
     }
+    const int64_t n = ++g_made;
+    const int64_t fail_at = g_fail_at.load();
+    if (fail_at > 0 && n == fail_at) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc(&b.p, bytes);
     if (e != cudaSuccess) {
         b.p = nullptr;
         return e;
     }
+    ++g_live;
     b.cap = bytes;
     if (zero) return cudaMemsetAsync(b.p, 0, bytes, s);
     return cudaSuccess;
 }
 
 void release(DevBuf& b) {
-    if (b.p) cudaFree(b.p);
+    if (b.p) {
+        cudaFree(b.p);
+        --g_live;
+    }
     b.p = nullptr;
     b.cap = 0;
 }
@@ -829,6 +844,7 @@ bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H,
         r.side[1].ld = Bpad;
     }
     r.err = (int*)c->errflag.p;
+    r.wait_ns = c->wait_ns;
     if (f8) {
         r.f8 = 1;
         r.inv_row[0] = (const float*)c->f8inv0.p;
@@ -1506,6 +1522,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             G1.out32_ld = K;
             G1.out32_trans = 1;
             G1.err = (int*)c->errflag.p;
+            G1.wait_ns = c->wait_ns;
             TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(G1, s));
             // Y^(n) = H_n x Psi, then a^(n)_d(rho) = sum_r S2_d(r) Y^(n)(rho, r)
             // and the |.|^2 sums over d and n into the sites' maps
@@ -1550,6 +1567,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             ct.scale = (float)det_scale(c);
             ct.mt_inner = 1;
             ct.err = (int*)c->errflag.p;
+            ct.wait_ns = c->wait_ns;
             // A: the S2 windows (opA16 holds four planes' room: 4 SB Dpad rows of K)
             if (probe_cols) {
                 // per-column sums of the batch's sites, then the channel sum
@@ -1609,6 +1627,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             A.ep_B = Bpad;
             A.ep_Dp = Dpad;
             A.err = (int*)c->errflag.p;
+            A.wait_ns = c->wait_ns;
             if (f8) {
                 // E4M3 rows of K bytes, seen by the tensor maps as K / 2 bf16
                 A.f8 = 1;
@@ -1663,6 +1682,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
                     ct.grp = (const int32_t*)c->cube_grp.p + cube_goff[bi];
                 }
                 ct.err = (int*)c->errflag.p;
+                ct.wait_ns = c->wait_ns;
                 // channels per launch: one TMEM accumulator pair (2 ctn columns)
                 // each in 512 columns
                 const int per = 512 / (2 * ctn);
@@ -1693,6 +1713,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             Gq.out32_site = (int64_t)perQ;
             Gq.out32_ld = Bpad;
             Gq.err = (int*)c->errflag.p;
+            Gq.wait_ns = c->wait_ns;
             TIMED(c, BIP_STAGE_GRAM, s, bip_tc_gemm(Gq, s));
         } else {
             // coupling M = S2^T diag(H) S1, stored transposed for the Gram step
@@ -1982,6 +2003,7 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
                 A.ep_B = Bpad;
                 A.ep_Dp = Dpb;
                 A.err = (int*)c->errflag.p;
+                A.wait_ns = c->wait_ns;
                 TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(A, s));
                 SplitArgs sa{(const float2*)c->mt32.p, 1, Dpb, (int64_t)perMt, Dpb, (int)KB, nb,
                              (uint16_t*)c->cubeA.p, (int64_t)(4 * D128 * KB), D128, (int)KB, 0, 0};
@@ -2010,6 +2032,7 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
                 ct.n_groups = cube_goff[bi + 1] - cube_goff[bi] - 1;
                 ct.grp = (const int32_t*)c->cube_grp.p + cube_goff[bi];
                 ct.err = (int*)c->errflag.p;
+                ct.wait_ns = c->wait_ns;
                 const int per = 512 / (2 * ctn);
                 for (int ch0 = 0; ch0 < nch; ch0 += per) {
                     ct.ch0 = ch0;
@@ -2084,6 +2107,25 @@ bip_status bip_cube_beams(const bip_ctx* c, int32_t* n_cube, int32_t* h) {
     if (!c || !n_cube) return BIP_ERR_INVALID_ARG;
     *n_cube = c->geo.n_cube;
     if (h) std::memcpy(h, c->geo.h_cube.data(), c->geo.h_cube.size() * sizeof(int32_t));
+    return BIP_OK;
+}
+
+bip_status bip_set_wait_limit(bip_ctx* c, int64_t ns) {
+    if (!c || ns < 0) return BIP_ERR_INVALID_ARG;
+    c->wait_ns = (uint64_t)ns;
+    return BIP_OK;
+}
+
+bip_status bip_debug_fail_alloc(int64_t k) {
+    if (k < 0) return BIP_ERR_INVALID_ARG;
+    g_made = 0;
+    g_fail_at = k;
+    return BIP_OK;
+}
+
+bip_status bip_debug_allocs(int64_t* live, int64_t* made) {
+    if (live) *live = g_live.load();
+    if (made) *made = g_made.load();
     return BIP_OK;
 }
 
@@ -2436,6 +2478,7 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
             A.ep_B = Bpad;
             A.ep_Dp = Dpad;
             A.err = (int*)c->errflag.p;
+            A.wait_ns = c->wait_ns;
             CUDA_TRY(c, bip_tc_gemm(A, s));
         } else {
             CGemmArgs A{};
@@ -2506,6 +2549,7 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
                     t.out32_site = (int64_t)perT;
                     t.out32_ld = K;
                     t.err = (int*)c->errflag.p;
+                    t.wait_ns = c->wait_ns;
                     CUDA_TRY(c, bip_tc_gemm(t, s));
                 } else {
                     CGemmGen t{};
@@ -2552,6 +2596,7 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
                 u.out32_site = (int64_t)perS2bar;
                 u.out32_ld = K;
                 u.err = (int*)c->errflag.p;
+                u.wait_ns = c->wait_ns;
                 CUDA_TRY(c, bip_tc_gemm(u, s));
             } else {
                 for (int n = 0; n < nch; ++n) {
@@ -2760,6 +2805,7 @@ bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_ou
         A.out32_ld = (int64_t)ldc;
         A.out32_trans = 1;
         A.err = (int*)c->errflag.p;
+        A.wait_ns = c->wait_ns;
         if (f8) {
             A.f8 = 1;
             A.A = TcOperand{opB.p, 2 * (int64_t)ldc, K / 2, 2 * (int64_t)ldc, (int64_t)ldc};

@@ -186,6 +186,7 @@ struct ReconArgs {
     uint16_t* out[2];               // coupling operands (2 bf16 planes each)
     ReconSide side[2];
     int* err;                       // set to 1 on a device timeout
+    uint64_t wait_ns;               // give-up limit of each wait (0: the built-in 4 s)
     // FP8 path: the operands are E4M3 bytes (out[] then holds bytes, same
     // element strides), each row scaled by inv_row[side][bs rows_pad + t];
     // H is then H_n / max_r |H_n| (F8HmaxArgs::Hs)
@@ -325,6 +326,7 @@ struct TcArgs {
     int out32_trans;
     int out32_rows;                 // A row (ch, b) -> out32[site][b][ch ep_Dp + n] (as ROWS)
     int* err;                       // device flag: set when a wait gives up
+    uint64_t wait_ns;               // give-up limit of each wait (0: the built-in 4 s)
 };
 cudaError_t bip_tc_gemm(const TcArgs& a, cudaStream_t s);
 
@@ -400,6 +402,7 @@ struct CubeTcArgs {
     // crop masks then take tn / 64 words per work item
     int tn;
     int* err;
+    uint64_t wait_ns;               // give-up limit of each wait (0: the built-in 4 s)
 };
 // a_k, b_k: row lengths of A and B (bf16 elements)
 cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int a_k, const void* B, int64_t b_rows,

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int64_t a0 = (int64_t)bs * a.a_site_rows + (int64_t)mt * 128;
                 const int64_t b0 = (int64_t)bs * a.b_site_rows + (int64_t)t * kN;
                 for (int kb = kb0; kb < kb1; ++kb) {
-                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
+                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, wait_limit(a.wait_ns))) {
                         fail();
                         ok = false;
                         break;
@@ -188,14 +188,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int i = 0; ok && unit_steps(a, blockIdx.x + i * gridDim.x, su); ++i)
             for (int w = su.w0; ok && w < su.w1; ++w)
             for (int mt = su.mt0; ok && mt < su.mt1; ++mt) {
-                if (!mbar_wait(acc_empty, aph ^ 1, abort_flag)) {
+                if (!mbar_wait(acc_empty, aph ^ 1, abort_flag, wait_limit(a.wait_ns))) {
                     fail();
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 for (int kb = kb0; kb < kb1; ++kb) {
-                    if (!mbar_wait(&full[s], ph, abort_flag)) {
+                    if (!mbar_wait(&full[s], ph, abort_flag, wait_limit(a.wait_ns))) {
                         fail();
                         ok = false;
                         break;
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int w = su.w0; ok && w < su.w1; ++w)
             for (int mt = su.mt0; mt < su.mt1; ++mt) {
                 if (et == 0) {
-                    const bool good = mbar_wait(acc_full, aph, abort_flag);
+                    const bool good = mbar_wait(acc_full, aph, abort_flag, wait_limit(a.wait_ns));
                     *ep_ok = good ? 1 : 0;
                     if (!good) fail();
                 }

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int64_t a0 = (int64_t)u.bs * p.A.site_rows + (int64_t)u.mt * 128;
                 const int64_t b0 = (int64_t)u.bs * p.B.site_rows + (int64_t)u.nt * p.N;
                 for (int kb = u.kb0; kb < p.kb; ++kb) {
-                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
+                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, wait_limit(p.wait_ns))) {
                         fail();
                         ok = false;
                         break;
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             Unit u;
             for (int i = 0; ok && it.get(i, u); ++i) {
                 if (u.skip) continue;
-                if (!mbar_wait(&acc_empty[a], aph ^ 1, abort_flag)) {
+                if (!mbar_wait(&acc_empty[a], aph ^ 1, abort_flag, wait_limit(p.wait_ns))) {
                     fail();
                     break;
                 }
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t id_ir = p.conjA ? id_neg : id_pos;   // sign of Ai*Br in Im
                 const uint32_t dr = tbase + (uint32_t)(a * 2 * N), di = dr + N;
                 for (int kb = u.kb0; kb < p.kb; ++kb) {
-                    if (!mbar_wait(&full[s], ph, abort_flag)) {
+                    if (!mbar_wait(&full[s], ph, abort_flag, wait_limit(p.wait_ns))) {
                         fail();
                         ok = false;
                         break;
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // one thread waits; all 128 take the same branch, so no warp can
             // be left alone at a named barrier
             if (et == 0) {
-                const bool ok = mbar_wait(&acc_full[a], aph, abort_flag);
+                const bool ok = mbar_wait(&acc_full[a], aph, abort_flag, wait_limit(p.wait_ns));
                 *ep_ok = ok ? 1 : 0;
                 if (!ok) fail();
             }

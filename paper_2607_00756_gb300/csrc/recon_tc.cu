@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int i = 0; ok && unit_of(a, blockIdx.x + i * gridDim.x, u); ++i) {
                 const ReconSide& sd = a.side[u.side];
                 const int ab = i & 1;
-                if (!mbar_wait(&a_empty[ab], ((i >> 1) & 1) ^ 1, abort_flag)) {
+                if (!mbar_wait(&a_empty[ab], ((i >> 1) & 1) ^ 1, abort_flag, wait_limit(a.wait_ns))) {
                     fail();
                     ok = false;
                     break;
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 a_last[ab] = i;
                 const int xrow0 = (sd.x_site0 + u.bs * 3) * a.K + u.pc * a.chunk_px;
                 for (int t = 0; t < tiles; ++t) {
-                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
+                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, wait_limit(a.wait_ns))) {
                         fail();
                         ok = false;
                         break;
@@ -215,14 +215,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             Unit u;
             for (int i = 0; ok && unit_of(a, blockIdx.x + i * gridDim.x, u); ++i) {
                 const int ab = i & 1;
-                if (!mbar_wait(&a_full[ab], (i >> 1) & 1, abort_flag)) {
+                if (!mbar_wait(&a_full[ab], (i >> 1) & 1, abort_flag, wait_limit(a.wait_ns))) {
                     fail();
                     break;
                 }
                 tc_fence_after();
                 const uint32_t abase = smem_u32(abuf + ab * kABuf);
                 for (int t = 0; t < tiles; ++t) {
-                    if (!mbar_wait(&acc_empty[acc], aph ^ 1, abort_flag) || !mbar_wait(&full[s], ph, abort_flag)) {
+                    if (!mbar_wait(&acc_empty[acc], aph ^ 1, abort_flag, wait_limit(a.wait_ns)) || !mbar_wait(&full[s], ph, abort_flag, wait_limit(a.wait_ns))) {
                         fail();
                         ok = false;
                         break;
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 int okw = 1;
                 if (lane == 0) {
-                    okw = mbar_wait(&acc_full[acc], aph, abort_flag) ? 1 : 0;
+                    okw = mbar_wait(&acc_full[acc], aph, abort_flag, wait_limit(a.wait_ns)) ? 1 : 0;
                     if (!okw) fail();
                 }
                 okw = __shfl_sync(0xffffffffu, okw, 0);

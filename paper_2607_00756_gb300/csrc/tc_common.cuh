@@ -46,15 +46,22 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait; false on timeout or when another role aborted
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+// the give-up limit of a kernel's waits: the built-in one unless the
+// context set another (a short one lets a test make a wait give up)
+__device__ __forceinline__ uint64_t wait_limit(uint64_t ns) { return ns ? ns : kTimeoutNs; }
+
+// bounded wait; false on timeout (after `limit` ns) or when another role
+// aborted.  Limits under 1 ms are checked on every poll.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
+                                          uint64_t limit = kTimeoutNs) {
     if (mbar_try(b, parity)) return true;
     const uint64_t t0 = gtimer();
+    const uint32_t every = limit < 1000000ull ? 0u : 255u;
     for (uint32_t n = 1;; ++n) {
         if (mbar_try(b, parity)) return true;
-        if ((n & 255u) == 0) {
+        if ((n & every) == 0) {
             if (*abort_flag) return false;
-            if (gtimer() - t0 > kTimeoutNs) return false;
+            if (gtimer() - t0 > limit) return false;
         }
     }
 }

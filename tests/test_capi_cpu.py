@@ -275,3 +275,28 @@ def test_geometry_many_parents_is_fast(capi):
     og = G.Geometry(cfg, ph.wavelength(cfg.e0))
     assert np.max(np.abs(g["w1"] - og.w1)) < 1e-12
     assert np.max(np.abs(g["w2"] - og.w2)) < 1e-12
+
+
+def test_injected_allocation_failure_is_oom_before_any_device_work(capi):
+    """The first device allocation of a build made to fail: both builds
+    return BIP_ERR_OOM (before anything reaches the device), nothing stays
+    allocated, and the injection is off again afterwards."""
+    cfg = synth.config1()
+    live0, _ = capi.bip_debug_allocs()
+    ctx = capi.bip_create(capi.make_config(cfg))
+    try:
+        atoms = capi.make_atoms(np.array([[5.0, 5.0, 2.0]]), np.array([3]))
+        lib = capi.lib()
+        dummy = ctypes.c_void_p(256)
+        for fn in (lib.bip_build_s1, lib.bip_build_s2):
+            capi.bip_debug_fail_alloc(1)
+            assert fn(ctx, dummy, atoms, 1, None) == 3                  # BIP_ERR_OOM
+            assert "cudaErrorMemoryAllocation" in capi.bip_last_error(ctx) or "memory" in capi.bip_last_error(ctx)
+            assert capi.bip_debug_allocs() == (live0, 1)
+        assert lib.bip_set_wait_limit(ctx, -5) == 1
+        assert lib.bip_set_wait_limit(ctx, 1000) == 0
+    finally:
+        capi.bip_debug_fail_alloc(0)
+        capi.bip_destroy(ctx)
+    assert capi.bip_debug_allocs()[0] == live0
+    assert capi.lib().bip_debug_fail_alloc(-1) == 1
