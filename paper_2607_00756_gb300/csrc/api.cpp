@@ -69,6 +69,7 @@ struct bip_ctx {
     DevBuf cubeA, cubeB, cube_work, cube_mask;   // the cube on tcgen05
     DevBuf cube_grp, pcol;              // cube-mode work groups; probe-order column sums
     DevBuf hcube, shcube, cstash, ccols; // the exact cube: basis, shifts, S2 windows, columns
+    DevBuf xopA, xopB, xm32;            // ... its coupling operands and M
     size_t cube_budget = 0;             // bytes of sweep columns + windows per detector batch (0: auto)
     DevBuf s1t, psi, ybuf;              // the probe order: S1 transposed, Psi, H_n x Psi
     DevBuf pyc, pxc;                    // conjugated propagator tables (adjoint sweeps)
@@ -589,7 +590,7 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->g_dt1, &c->g_dt2, &c->g_adj, &c->g_ckpt, &c->g_seg, &c->g_gvp, &c->pyc, &c->pxc,
                      &c->ray, &c->rax, &c->g_tA, &c->g_tB, &c->g_sA2, &c->g_sB2, &c->cubeA, &c->cubeB,
                      &c->cube_work, &c->cube_mask, &c->s1t, &c->psi, &c->ybuf, &c->cube_grp, &c->pcol,
-                     &c->hcube, &c->shcube, &c->cstash, &c->ccols};
+                     &c->hcube, &c->shcube, &c->cstash, &c->ccols, &c->xopA, &c->xopB, &c->xm32};
     for (DevBuf* b : all) release(*b);
     for (int i = 0; i < 6; ++i) {
         release(c->aw1[i]);
@@ -1848,15 +1849,13 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
                                       : (tc ? tc_batch(c) : std::min(c->n_sites, 8));
     const size_t rowsB = (size_t)nch * Bpad, perA = (size_t)Dpb * K, perB = rowsB * K;
     const size_t perMt = (size_t)Bpad * nch * Dpb, KB = (size_t)nch * Bpad;
-    if (tc) {
-        CUDA_TRY(c, ensure(c->opA16, SB * perA * 8, true, s));
-        CUDA_TRY(c, ensure(c->opB16, SB * perB * 8, true, s));
-        CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
-    } else {
-        CUDA_TRY(c, ensure(c->opA32, SB * perA * sizeof(float2), true, s));
-        CUDA_TRY(c, ensure(c->opB32, SB * perB * sizeof(float2), true, s));
-    }
-    CUDA_TRY(c, ensure(c->mt32, SB * perMt * sizeof(float2), true, s));
+    // the cube's own operand and coupling buffers: the map's keep zero
+    // padding in their own row layout, which these rows would overwrite
+    // (8 bytes per element: complex64, or up to four BF16 planes)
+    CUDA_TRY(c, ensure(c->xopA, SB * perA * 8, true, s));
+    CUDA_TRY(c, ensure(c->xopB, SB * perB * 8, true, s));
+    CUDA_TRY(c, ensure(c->xm32, SB * perMt * sizeof(float2), true, s));
+    if (tc) CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
 
     // tcgen05 per-beam contraction: c_b(rho) as split planes, and work items
     // grouped by scan tile (sites ascending), one CTA per cube tile
@@ -1945,7 +1944,7 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
             const int32_t* ids = (const int32_t*)c->seq_ids_d.p + b0;
             // aperture side H_n S1 (partitioned, rebuilt on the windows)
             if (c->prec == BIP_PREC_MIXED && c->recon_tc) {
-                bip_status st = recon_tc_batch(c, ids, nb, H, nullptr, c->opB16.p, s, false, false);
+                bip_status st = recon_tc_batch(c, ids, nb, H, nullptr, c->xopB.p, s, false, false);
                 if (st != BIP_OK) return st;
             } else {
                 GatherArgs g1 = gather_args(c, 1, ids, nb);
@@ -1953,11 +1952,11 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
                 g1.nch = nch;
                 g1.H = (const float2*)H;
                 if (tc) {
-                    g1.out_bf16 = (uint16_t*)c->opB16.p;
+                    g1.out_bf16 = (uint16_t*)c->xopB.p;
                     g1.out_planes = npl;
                     g1.site_stride = (int64_t)(npl * perB);
                 } else {
-                    g1.out_c64 = (float2*)c->opB32.p;
+                    g1.out_c64 = (float2*)c->xopB.p;
                     g1.site_stride = (int64_t)perB;
                 }
                 TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g1, s));
@@ -1975,11 +1974,11 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
             ra.ex = (const float2*)c->ex.p;
             ra.rows_pad = Dpb;
             if (tc) {
-                ra.out_bf16 = (uint16_t*)c->opA16.p;
+                ra.out_bf16 = (uint16_t*)c->xopA.p;
                 ra.out_planes = npl;
                 ra.site_stride = (int64_t)npl * perA;
             } else {
-                ra.out_c64 = (float2*)c->opA32.p;
+                ra.out_c64 = (float2*)c->xopA.p;
                 ra.site_stride = (int64_t)perA;
             }
             TIMED(c, BIP_STAGE_GATHER, s, bip_retilt(ra, s));
@@ -1990,14 +1989,14 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
                 A.N = tile_width(Dpb);
                 A.npl = npl;
                 A.out_planes = npl;
-                A.A = TcOperand{c->opB16.p, (int64_t)SB * npl * (int64_t)rowsB, K, npl * (int64_t)rowsB, (int64_t)rowsB};
-                A.B = TcOperand{c->opA16.p, (int64_t)SB * npl * (int64_t)Dpb, K, npl * (int64_t)Dpb, (int64_t)Dpb};
+                A.A = TcOperand{c->xopB.p, (int64_t)SB * npl * (int64_t)rowsB, K, npl * (int64_t)rowsB, (int64_t)rowsB};
+                A.B = TcOperand{c->xopA.p, (int64_t)SB * npl * (int64_t)Dpb, K, npl * (int64_t)Dpb, (int64_t)Dpb};
                 A.kb = K / 32;
                 A.n_sites = nb;
                 A.mt_per = (int)(rowsB / 128);
                 A.nt_per = (Dpb + A.N - 1) / A.N;
                 A.n_cols = Dpb;
-                A.out32 = (float2*)c->mt32.p;
+                A.out32 = (float2*)c->xm32.p;
                 A.out32_site = (int64_t)perMt;
                 A.out32_ld = Dpb;
                 A.ep_B = Bpad;
@@ -2005,7 +2004,7 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
                 A.err = (int*)c->errflag.p;
                 A.wait_ns = c->wait_ns;
                 TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(A, s));
-                SplitArgs sa{(const float2*)c->mt32.p, 1, Dpb, (int64_t)perMt, Dpb, (int)KB, nb,
+                SplitArgs sa{(const float2*)c->xm32.p, 1, Dpb, (int64_t)perMt, Dpb, (int)KB, nb,
                              (uint16_t*)c->cubeA.p, (int64_t)(4 * D128 * KB), D128, (int)KB, 0, 0};
                 TIMED(c, BIP_STAGE_QUADFORM, s, bip_split_planes(sa, s));
                 CubeTcArgs ct{};
@@ -2044,18 +2043,18 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
             } else {
                 CGemmArgs A{};
                 A.M = nd; A.N = (int)rowsB; A.K = K;
-                A.A = (const float2*)c->opA32.p; A.lda = K; A.strideA = (int64_t)perA;
-                A.Bm = (const float2*)c->opB32.p; A.ldb = K; A.strideB = (int64_t)perB;
+                A.A = (const float2*)c->xopA.p; A.lda = K; A.strideA = (int64_t)perA;
+                A.Bm = (const float2*)c->xopB.p; A.ldb = K; A.strideB = (int64_t)perB;
                 A.batch = nb;
                 A.epi = 1;
-                A.C = (float2*)c->mt32.p; A.ldc = (int64_t)nch * Dpb; A.strideC = (int64_t)perMt;
+                A.C = (float2*)c->xm32.p; A.ldc = (int64_t)nch * Dpb; A.strideC = (int64_t)perMt;
                 A.ep_B = Bpad; A.ep_Dp = Dpb;
                 TIMED(c, BIP_STAGE_COUPLING, s, bip_cgemm_simt(A, s));
                 CubeArgs ca = cube_args(c, ids, nb, P, cube_out + d0);
                 ca.n_det = nd;
                 ca.Dp = Dpb;
                 ca.m_ld = (int64_t)nch * Dpb;
-                ca.m32 = (const float2*)c->mt32.p;
+                ca.m32 = (const float2*)c->xm32.p;
                 ca.m_site = (int64_t)perMt;
                 ca.scale = 1.0f;
                 ca.cube_ld = n_cube;

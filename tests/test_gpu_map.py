@@ -428,3 +428,18 @@ def test_raster_and_horner_evaluations_agree(lib, which, prec):
     tol = 1e-4 if prec == "fp32" else 1e-3
     assert rel(m_r, ref.map) < tol and rel(m_h, ref.map) < tol
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16", "mixed"])
+def test_map_unchanged_after_cube_and_grad(lib, c1, prec):
+    """The cube and the reverse pass share a context with the map without
+    disturbing it: the map after both is the map before, bit for bit (the
+    workspaces' zero padding survives the other layouts)."""
+    cfg, sp, pr, ref = c1
+    ctx, m0, _, H = gpu_run(lib, cfg, sp, prec=prec)
+    V = torch.tensor(sp.V, dtype=torch.float32, device=H.device)
+    ctx.cube(V, H, sp.scans)
+    ctx.grad(H, sp.scans, torch.ones(len(sp.scans), dtype=torch.float64, device=H.device), V=V)
+    m1 = ctx.map(H, sp.scans).cpu().numpy()
+    assert np.array_equal(m1, m0)
+    ctx.close()
