@@ -67,7 +67,7 @@ struct bip_ctx {
     DevBuf g_s1bar, g_s2bar, g_ubar, g_dA, g_dt1, g_dt2, g_adj, g_ckpt, g_seg, g_gvp;
     DevBuf g_tA, g_tB, g_sA2, g_sB2;    // split-BF16 operands of the reverse-pass contractions
     DevBuf cubeA, cubeB, cube_work, cube_mask;   // the cube on tcgen05
-    DevBuf cube_grp, pcol;              // cube-mode work groups; probe-order column sums
+    DevBuf cube_grp, cube_wmap, mpart;  // cube-mode work groups; map modes' item map and column sums
     DevBuf hcube, shcube, cstash, ccols; // the exact cube: basis, shifts, S2 windows, columns
     DevBuf xopA, xopB, xm32;            // ... its coupling operands and M
     size_t cube_budget = 0;             // bytes of sweep columns + windows per detector batch (0: auto)
@@ -589,7 +589,7 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->g_gmt, &c->g_T, &c->g_D, &c->g_Dsum, &c->g_s1bar, &c->g_s2bar, &c->g_ubar, &c->g_dA,
                      &c->g_dt1, &c->g_dt2, &c->g_adj, &c->g_ckpt, &c->g_seg, &c->g_gvp, &c->pyc, &c->pxc,
                      &c->ray, &c->rax, &c->g_tA, &c->g_tB, &c->g_sA2, &c->g_sB2, &c->cubeA, &c->cubeB,
-                     &c->cube_work, &c->cube_mask, &c->s1t, &c->psi, &c->ybuf, &c->cube_grp, &c->pcol,
+                     &c->cube_work, &c->cube_mask, &c->s1t, &c->psi, &c->ybuf, &c->cube_grp, &c->cube_wmap, &c->mpart,
                      &c->hcube, &c->shcube, &c->cstash, &c->ccols, &c->xopA, &c->xopB, &c->xm32};
     for (DevBuf* b : all) release(*b);
     for (int i = 0; i < 6; ++i) {
@@ -1411,6 +1411,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     const int crow = probe ? round_up(P, 128) : round_up(P, ctn);
     const size_t KB = (size_t)nch * Bpad;
     std::vector<int> cube_off, cube_goff;
+    int n_ct_map = 0;                   // map modes: scan tiles per site (the wmap rows)
     if (cube_tc) {
         CUDA_TRY(c, ensure(c->cubeB, (size_t)4 * crow * Bpad * sizeof(uint16_t), true, s));
         if (!probe) CUDA_TRY(c, ensure(c->cubeA, (size_t)SB * 4 * D128 * KB * sizeof(uint16_t), true, s));
@@ -1435,7 +1436,8 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         // work items per batch; for the per-beam output (cube mode) ordered by
         // scan tile, then site, with one group per tile: a group's items
         // write the same cube entries, in site order, from one CTA
-        std::vector<int32_t> cw, cg;
+        std::vector<int32_t> cw, cg, wm;
+        int max_items = 0;
         for (int b0 = 0; b0 < c->n_sites; b0 += SB) {
             const int nbb = std::min(SB, c->n_sites - b0);
             cube_off.push_back((int)cw.size() / 2);
@@ -1457,20 +1459,29 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
                 }
                 cg.push_back((int)cw.size() / 2 - first);
             } else {
+                // map modes: each (site, tile)'s work item, or -1
                 for (int bs = 0; bs < nbb; ++bs)
-                    for (int t = 0; t < n_ct; ++t)
-                        if (meets(bs, t)) {
+                    for (int t = 0; t < n_ct; ++t) {
+                        const bool m = meets(bs, t);
+                        wm.push_back(m ? (int)cw.size() / 2 - first : -1);
+                        if (m) {
                             cw.push_back(bs);
                             cw.push_back(t);
                         }
+                    }
+                max_items = std::max(max_items, (int)cw.size() / 2 - first);
             }
         }
         cube_off.push_back((int)cw.size() / 2);
         cube_goff.push_back((int)cg.size());
         CUDA_TRY(c, upload(c->cube_work, cw, s));
         if (cube_out) CUDA_TRY(c, upload(c->cube_grp, cg, s));
-        if (probe_cols)
-            CUDA_TRY(c, ensure(c->pcol, (size_t)SB * round_up(P * nch, 64) * sizeof(float), false, s));
+        if (!cube_out) {
+            CUDA_TRY(c, upload(c->cube_wmap, wm, s));
+            CUDA_TRY(c, ensure(c->mpart, std::max<size_t>(1, (size_t)max_items * (D128 / 128) * tile) * sizeof(float),
+                               false, s));
+        }
+        n_ct_map = n_ct;
         CUDA_TRY(c, ensure(c->cube_mask, std::max<size_t>(1, cw.size() / 2 * (tile / 64)) * sizeof(unsigned long long),
                            false, s));
     }
@@ -1566,31 +1577,28 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             ct.site_ids = ids;
             ct.ny = g.ny; ct.nx = g.nx; ct.fy = g.fy; ct.fx = g.fx;
             ct.scale = (float)det_scale(c);
-            ct.mt_inner = 1;
+            ct.mpart = (float*)c->mpart.p;
             ct.err = (int*)c->errflag.p;
             ct.wait_ns = c->wait_ns;
+            // the per-unit column sums added to the sites' maps, in order
+            MapReduceArgs mr{(const float*)c->mpart.p, (const int32_t*)c->cube_wmap.p + (size_t)b0 * n_ct_map, nb,
+                             n_ct_map, 64, ct.mt_per, probe_cols ? nch : 1, P, ids, (float)det_scale(c), partial};
             // A: the S2 windows (opA16 holds four planes' room: 4 SB Dpad rows of K)
             if (probe_cols) {
-                // per-column sums of the batch's sites, then the channel sum
-                // of each scan in order
                 ct.ch0 = 0;
                 ct.nacc = 1;
-                ct.pcol = (float*)c->pcol.p;
-                ct.pcol_site = round_up(P * nch, 64);
-                CUDA_TRY(c, cudaMemsetAsync(c->pcol.p, 0, (size_t)nb * ct.pcol_site * sizeof(float), s));
                 TIMED(c, BIP_STAGE_QUADFORM, s,
                       bip_cube_tc(ct, c->opA16.p, (int64_t)SB * 4 * Dpad, K, c->ybuf.p, (int64_t)SB * 2 * P64 * nch,
                                   K, s));
-                TIMED(c, BIP_STAGE_QUADFORM, s,
-                      bip_cube_col_reduce((const float*)c->pcol.p, ct.pcol_site, nb, ids, P, nch, partial, s));
+                TIMED(c, BIP_STAGE_QUADFORM, s, bip_cube_map_reduce(mr, s));
             } else {
-                ct.partial = partial;
                 for (int ch0 = 0; ch0 < nch; ch0 += 4) {
                     ct.ch0 = ch0;
                     ct.nacc = std::min(4, nch - ch0);
                     TIMED(c, BIP_STAGE_QUADFORM, s,
                           bip_cube_tc(ct, c->opA16.p, (int64_t)SB * 4 * Dpad, K, c->ybuf.p, (int64_t)SB * 2 * P64,
                                       nch * K, s));
+                    TIMED(c, BIP_STAGE_QUADFORM, s, bip_cube_map_reduce(mr, s));
                 }
             }
             continue;
@@ -1673,9 +1681,11 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
                 ct.site_ids = ids;
                 ct.ny = g.ny; ct.nx = g.nx; ct.fy = g.fy; ct.fx = g.fx;
                 ct.scale = (float)det_scale(c);
+                MapReduceArgs mr{};
                 if (beam) {
-                    ct.partial = partial;
-                    ct.mt_inner = 1;
+                    ct.mpart = (float*)c->mpart.p;
+                    mr = MapReduceArgs{(const float*)c->mpart.p, (const int32_t*)c->cube_wmap.p + (size_t)b0 * n_ct_map,
+                                       nb, n_ct_map, ctn, ct.mt_per, 1, P, ids, (float)det_scale(c), partial};
                 } else {
                     ct.cube = cube_out;
                     ct.cube_ld = geo.n_det;
@@ -1693,6 +1703,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
                     TIMED(c, BIP_STAGE_QUADFORM, s,
                           bip_cube_tc(ct, c->cubeA.p, (int64_t)nb * 4 * D128, (int)KB, c->cubeB.p, (int64_t)4 * crow,
                                       Bpad, s));
+                    if (beam) TIMED(c, BIP_STAGE_QUADFORM, s, bip_cube_map_reduce(mr, s));
                 }
                 continue;
             }

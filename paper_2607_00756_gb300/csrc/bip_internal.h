@@ -377,18 +377,13 @@ struct CubeTcArgs {
     int ny, nx, fy, fx;
     float scale;                    // the detector-side factor (1 for the exact cube)
     float* cube;                    // cube mode: [P][cube_ld], rows d added to; or
-    float* partial;                 // map mode: [n_sites_total][P] per-site map, the
-                                    // detector sum taken in the epilogue; or
-    float* pcol;                    // map mode with (scan, channel) columns: [bs][pcol_site]
-                                    // column sums (bip_cube_col_reduce adds them up)
-    int64_t pcol_site;
+    float* mpart;                   // map mode: [n_work][mt_per][tn] column sums over each
+                                    // unit's 128 beams (bip_cube_map_reduce adds them up)
     int64_t cube_ld;                // cube row stride (>= n_det)
     // units: cube mode, (group g of work items grp[g] .. grp[g+1]-1 -- one
-    // scan tile, sites ascending -- x d tile); map mode (mt_inner = 1), one
-    // work item with all its d tiles
+    // scan tile, sites ascending -- x d tile); map mode, (work item, d tile)
     int n_groups;
     const int32_t* grp;
-    int mt_inner;
     // probe order: B rows per site (0: one B for every site), the channel in
     // B's columns instead of A's (A = S2 windows, B = H_n x windowed probes),
     // and operands of two BF16 planes (re, im) instead of four (split BF16)
@@ -407,8 +402,17 @@ struct CubeTcArgs {
 // a_k, b_k: row lengths of A and B (bf16 elements)
 cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int a_k, const void* B, int64_t b_rows,
                         int b_k, cudaStream_t s);
-cudaError_t bip_cube_col_reduce(const float* pcol, int64_t pcol_site, int n_sites, const int32_t* site_ids, int P,
-                                int ncol, float* partial, cudaStream_t s);
+// map mode's second stage: partial[site][rho] += scale sum over the scan's
+// columns (rho ncol + n) and the d tiles of mpart, in order
+struct MapReduceArgs {
+    const float* mpart;             // [n_work][mt_per][tn]
+    const int32_t* wmap;            // [n_sites][n_tiles]: work item of (site, tile), or -1
+    int n_sites, n_tiles, tn, mt_per, ncol, P;
+    const int32_t* site_ids;
+    float scale;
+    float* partial;                 // [n_sites_total][P]
+};
+cudaError_t bip_cube_map_reduce(const MapReduceArgs& a, cudaStream_t s);
 
 // probe.cu : the probe order of the scan contraction.  Y[site][plane][rho][n K
 // + r] = H_n(r) Psi(rho, r) as BF16 planes (re, im), from the windowed probes

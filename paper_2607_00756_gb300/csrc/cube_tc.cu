@@ -18,11 +18,12 @@
 //   cube mode: a unit is (group of work items sharing one scan tile, sites
 //     in ascending order; tile of 128 detector beams); the CTA that owns it
 //     adds each site's channel sum to the cube with a plain read-add-write.
-//   map mode: a unit is one work item with every 128-beam tile of d; the
+//   map mode: a unit is one work item and one 128-beam tile of d; the
 //     detector sum of each scan column is taken by a fixed shuffle tree per
-//     warp, then over the four epilogue warps and the d tiles in order, and
-//     added once to the site's map (or, with (scan, channel) columns,
-//     stored per column and summed over the channels by col_reduce_kernel).
+//     warp, then over the four epilogue warps in order, and stored in the
+//     unit's own slot; map_reduce_kernel then adds each scan's slots over
+//     the d tiles (and, with (scan, channel) columns, over the channels) in
+//     order to the site's map.
 // The crop mask of a work item's scans is a precomputed 64-bit word per 64
 // columns.  Persistent, one CTA per SM, 192 threads: warp 0 TMA producer,
 // warp 1 TMEM allocator and MMA issuer, warps 2-5 epilogue.  Every wait is
@@ -58,9 +59,10 @@ struct Steps {
     int w0, w1, mt0, mt1;
 };
 __device__ __forceinline__ bool unit_steps(const CubeTcArgs& a, int u, Steps& st) {
-    if (a.mt_inner) {
-        if (u >= a.n_work) return false;
-        st = Steps{u, u + 1, 0, a.mt_per};
+    if (!a.cube) {
+        // map mode: one work item and one d tile per unit
+        if (u >= a.n_work * a.mt_per) return false;
+        st = Steps{u / a.mt_per, u / a.mt_per + 1, u % a.mt_per, u % a.mt_per + 1};
     } else {
         if (u >= a.n_groups * a.mt_per) return false;
         const int g = u / a.mt_per, mt = u % a.mt_per;
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
         const int q = warp & 3;
         const int et = threadIdx.x - 64;
-        const bool map_mode = a.partial || a.pcol;
+        const bool map_mode = a.mpart != nullptr;
         uint32_t aph = 0;
         bool ok = true;
         Steps su;
@@ -326,17 +328,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             if (!ok || !map_mode || et >= kN) continue;
-            // end of a map-mode unit (one work item): its columns are written once
+            // end of a map-mode unit (one work item, one d tile): its column
+            // sums go to the unit's own slot (summed over d tiles, in order,
+            // by bip_cube_map_reduce); columns outside the crop mask are 0
             const int w = su.w0;
-            const int t = a.work[2 * w + 1];
             const bool in = (a.mask[(size_t)w * MW + (et >> 6)] >> (et & 63)) & 1ull;
-            const int col = t * kN + et;
-            if (a.pcol) {
-                if (col < a.P * a.col_nch) a.pcol[(size_t)a.work[2 * w] * a.pcol_site + col] = in ? a.scale * colacc : 0.f;
-            } else if (in) {
-                float* e = a.partial + (size_t)a.site_ids[a.work[2 * w]] * a.P + col;
-                *e += a.scale * colacc;
-            }
+            a.mpart[((size_t)w * a.mt_per + su.mt0) * kN + et] = in ? colacc : 0.f;
         }
     }
     tc_fence_before();
@@ -374,17 +371,24 @@ __global__ void crop_mask_kernel(CubeTcArgs a, int tn) {
         a.mask[sub] = part[threadIdx.x / 64][0] | (part[threadIdx.x / 64][1] << 32);
 }
 
-// (scan, channel) columns of the probe order: partial[site][rho] += the
-// site's columns rho ncol .. rho ncol + ncol - 1, in channel order.
-__global__ void col_reduce_kernel(const float* __restrict__ pcol, int64_t pcol_site, int n_sites,
-                                  const int32_t* __restrict__ site_ids, int P, int ncol, float* partial) {
+// Map mode, second stage: partial[site][rho] += scale sum_n sum_mt
+// mpart[w][mt][c] over the columns (rho ncol + n) of the site's scan,
+// w the work item of the column's tile (none: 0), in channel then d-tile
+// order -- one thread per (site, scan), so every addition order is fixed.
+__global__ void map_reduce_kernel(MapReduceArgs a) {
     const int rho = blockIdx.x * blockDim.x + threadIdx.x;
     const int bs = blockIdx.y;
-    if (rho >= P || bs >= n_sites) return;
-    const float* c = pcol + (size_t)bs * pcol_site + (size_t)rho * ncol;
+    if (rho >= a.P) return;
     float v = 0.f;
-    for (int n = 0; n < ncol; ++n) v += c[n];
-    partial[(size_t)site_ids[bs] * P + rho] += v;
+    for (int n = 0; n < a.ncol; ++n) {
+        const int col = rho * a.ncol + n;
+        const int w = a.wmap[(size_t)bs * a.n_tiles + col / a.tn];
+        if (w < 0) continue;
+        const float* m = a.mpart + (size_t)w * a.mt_per * a.tn + col % a.tn;
+        for (int mt = 0; mt < a.mt_per; ++mt) v += m[(size_t)mt * a.tn];
+    }
+    float* e = a.partial + (size_t)a.site_ids[bs] * a.P + rho;
+    *e += a.scale * v;
 }
 
 template <bool HI, int TN>
@@ -396,7 +400,7 @@ cudaError_t launch_cube(const CubeTcArgs& a, const CUtensorMap& ma, const CUtens
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int units = a.mt_inner ? a.n_work : a.n_groups * a.mt_per;
+    const int units = a.cube ? a.n_groups * a.mt_per : a.n_work * a.mt_per;
     const int grid = units < num_sms() ? units : num_sms();
     cube_tc_kernel<HI, TN><<<grid, kThreads, kSmem, s>>>(ma, mb, a);
     return cudaGetLastError();
@@ -413,13 +417,11 @@ cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int 
     if (a.nacc < 1 || a.nacc * 2 * tn > (int)kTmemCols || a.kb_ch < 1 || a.mt_per < 1 || a.ch0 < 0 || a_k % 32 ||
         b_k % 32)
         return cudaErrorInvalidValue;
-    // map mode (partial, or pcol with (scan, channel) columns): one work item
-    // per unit; cube mode: groups of items sharing a scan tile
-    const bool map_mode = a.partial || a.pcol;
-    if (map_mode != (a.mt_inner != 0) || (map_mode && a.cube) || (!map_mode && !a.cube)) return cudaErrorInvalidValue;
-    if (!map_mode && (a.n_groups < 1 || !a.grp || a.cube_ld < a.n_det)) return cudaErrorInvalidValue;
-    if (a.col_nch < 0 || (a.col_nch > 0) != (a.pcol != nullptr) || (a.col_nch > 0 && (a.nacc != 1 || a.ch0 != 0)))
-        return cudaErrorInvalidValue;
+    // map mode (mpart: per-unit column sums), or cube mode (groups of items
+    // sharing a scan tile)
+    if ((a.mpart != nullptr) == (a.cube != nullptr)) return cudaErrorInvalidValue;
+    if (a.cube && (a.n_groups < 1 || !a.grp || a.cube_ld < a.n_det)) return cudaErrorInvalidValue;
+    if (a.col_nch < 0 || (a.col_nch > 0 && (a.nacc != 1 || a.ch0 != 0 || a.cube))) return cudaErrorInvalidValue;
     // the channel range inside the operand that has channels, one channel's
     // K blocks inside the other
     const int ch_k = a.swap_ch ? b_k : a_k, one_k = a.swap_ch ? a_k : b_k;
@@ -446,11 +448,9 @@ cudaError_t bip_cube_tc(const CubeTcArgs& a, const void* A, int64_t a_rows, int 
     return tn == 128 ? launch_cube<false, 128>(a, ma, mb, s) : launch_cube<false, 64>(a, ma, mb, s);
 }
 
-cudaError_t bip_cube_col_reduce(const float* pcol, int64_t pcol_site, int n_sites, const int32_t* site_ids, int P,
-                                int ncol, float* partial, cudaStream_t s) {
-    if (n_sites < 1 || P < 1) return cudaSuccess;
-    if (ncol < 1 || pcol_site < (int64_t)P * ncol) return cudaErrorInvalidValue;
-    col_reduce_kernel<<<dim3((P + 127) / 128, n_sites), 128, 0, s>>>(pcol, pcol_site, n_sites, site_ids, P, ncol,
-                                                                   partial);
+cudaError_t bip_cube_map_reduce(const MapReduceArgs& a, cudaStream_t s) {
+    if (a.n_sites < 1 || a.P < 1) return cudaSuccess;
+    if (a.ncol < 1 || a.tn < 1 || a.mt_per < 1 || a.n_tiles * a.tn < a.P * a.ncol) return cudaErrorInvalidValue;
+    map_reduce_kernel<<<dim3((a.P + 127) / 128, a.n_sites), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
