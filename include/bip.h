@@ -117,6 +117,11 @@ typedef struct {
      * q_x needs dfx = 1 (along q_y: dfy = 1); the map's detector factor is
      * dfy dfx. */
     int32_t dfy, dfx;
+    /* the 4D cube's output basis: 0, 0 -- every beam with |q| lambda <=
+     * theta_det; else a box of cube_ky x cube_kx k-pixels centred on the
+     * zero beam, -cube_ky/2 <= h_y < cube_ky/2 (and likewise for x), at most
+     * ny x nx. */
+    int32_t cube_ky, cube_kx;
 } bip_config;
 
 /* Host geometry (Algorithm 5 build steps; Sec. 2.2.2-2.2.3, Eq. nnw):
@@ -124,7 +129,8 @@ typedef struct {
  * |q| lambda <= theta_det with h = 0 mod (dfy, dfx), hex-ring parents for
  * both and FP64 Sibson natural-neighbour weights, computed once and cached
  * in the context; and the 4D cube's complete output basis, every beam with
- * |q| lambda <= theta_det (no subsampling).  Host only: touches no GPU.
+ * |q| lambda <= theta_det (no subsampling), or the box of k-pixels the
+ * configuration names.  Host only: touches no GPU.
  * *out receives the new context. */
 bip_status bip_create(const bip_config* cfg, bip_ctx** out);
 
@@ -202,7 +208,8 @@ bip_status bip_coreloss_sites(bip_ctx* ctx, const void* H, const double* scan_px
  * keeps every output beam, so S2 is not reduced.  S1 stays partitioned (the
  * context's bip_build_s1 windows, rebuilt per site as for the map); the exit
  * side is exact on the complete basis -- every beam with |q| lambda <=
- * theta_det, unsubsampled (bip_cube_beams) -- through unpartitioned S2
+ * theta_det, unsubsampled, or the configuration's box of k-pixels
+ * (bip_cube_beams) -- through unpartitioned S2
  * columns (Eq. s2, the reciprocity form of Algorithm 3's exit multislice):
  *   cube[rho][q] = sum_sites sum_n |sum_b M^(n)_{q,b} c_b(rho)|^2,
  *   M^(n)_{q,b} = sum_{r in window} S2^q(r) H_n(r) S~1^b(r),

@@ -267,6 +267,21 @@ def sibson_weights(parent_h, query_h, ly, lx):
 # --------------------------------------------------------------------------
 # bundled geometry for a configuration
 
+def cube_basis(cfg, lam):
+    """The cube's output beams, (h_y, h_x) ascending: every beam with
+    |q| lambda <= theta_det (no subsampling), or, when the configuration
+    asks for a box of cube_ky x cube_kx k-pixels, the beams with
+    -ky/2 <= h_y < ky/2 and -kx/2 <= h_x < kx/2 (a detector of that many
+    pixels at the grid's own k-sampling)."""
+    ky, kx = int(getattr(cfg, "cube_ky", 0)), int(getattr(cfg, "cube_kx", 0))
+    if ky > 0 and kx > 0:
+        hy = np.arange(-(ky // 2), ky - ky // 2)
+        hx = np.arange(-(kx // 2), kx - kx // 2)
+        HY, HX = np.meshgrid(hy, hx, indexing="ij")
+        return np.stack([HY.ravel(), HX.ravel()], axis=1).astype(np.int64)
+    return disc_beams(cfg.ny, cfg.nx, cfg.ly, cfg.lx, lam, cfg.theta_det)
+
+
 def detector_subsampling(cfg):
     """(dfy, dfx): the subsampling of the detector beams (h = 0 mod df); a
     configuration without dfy/dfx, or with 0, takes the probe's (fy, fx)
@@ -291,8 +306,9 @@ class Geometry:
         self.dfy, self.dfx = detector_subsampling(cfg)
         self.h_det = disc_beams(ny, nx, ly, lx, lam, cfg.theta_det, self.dfy, self.dfx)
         # the 4D cube's complete output basis: every beam inside the detector
-        # disc, unsubsampled (Sec. 2.2.6: S2 cannot be reduced for the cube)
-        self.h_cube = disc_beams(ny, nx, ly, lx, lam, cfg.theta_det)
+        # disc, unsubsampled (Sec. 2.2.6: S2 cannot be reduced for the cube),
+        # or a box of k-pixels
+        self.h_cube = cube_basis(cfg, lam)
         self.psi_full = aperture_function(self.h_full, ly, lx, lam, cfg.defocus, cfg.cs)
         self.psi_beam = aperture_function(self.h_beam, ly, lx, lam, cfg.defocus, cfg.cs)
         if parents_override is None:

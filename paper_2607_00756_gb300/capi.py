@@ -31,7 +31,8 @@ class BipConfig(ctypes.Structure):
                 ("nrad1", ctypes.c_int32), ("nang1", ctypes.c_int32),
                 ("nrad2", ctypes.c_int32), ("nang2", ctypes.c_int32),
                 ("win", ctypes.c_int32), ("recon", ctypes.c_int32), ("prec", ctypes.c_int32),
-                ("dfy", ctypes.c_int32), ("dfx", ctypes.c_int32)]
+                ("dfy", ctypes.c_int32), ("dfx", ctypes.c_int32),
+                ("cube_ky", ctypes.c_int32), ("cube_kx", ctypes.c_int32)]
 
 
 class BipAtom(ctypes.Structure):
@@ -130,7 +131,8 @@ def make_config(cfg, prec=None, recon=None):
     for name, _ in BipConfig._fields_:
         if name in ("recon", "prec"):
             continue
-        setattr(c, name, getattr(cfg, name, 0) if name in ("dfy", "dfx") else getattr(cfg, name))
+        optional = ("dfy", "dfx", "cube_ky", "cube_kx")
+        setattr(c, name, getattr(cfg, name, 0) if name in optional else getattr(cfg, name))
     r = recon if recon is not None else getattr(cfg, "recon", "magnitude")
     p = prec if prec is not None else getattr(cfg, "prec", "fp32")
     c.recon = RECON[r] if isinstance(r, str) else int(r)

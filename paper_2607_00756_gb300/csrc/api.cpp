@@ -556,6 +556,8 @@ bip_status bip_create(const bip_config* cfg, bip_ctx** out) {
     if (g.fy < 1 || g.fx < 1 || g.ny % g.fy || g.nx % g.fx) return bad(BIP_ERR_SHAPE, "f");
     if (g.dfy < 0 || g.dfx < 0 || (g.dfy > 0 && g.ny % g.dfy) || (g.dfx > 0 && g.nx % g.dfx))
         return bad(BIP_ERR_SHAPE, "detector subsampling");
+    if (g.cube_ky < 0 || g.cube_kx < 0 || g.cube_ky > g.ny || g.cube_kx > g.nx || ((g.cube_ky > 0) != (g.cube_kx > 0)))
+        return bad(BIP_ERR_SHAPE, "cube box");
     if (g.win < 16 || g.win % 16 || g.win > g.ny / g.fy || g.win > g.nx / g.fx) return bad(BIP_ERR_SHAPE, "win");
     if (g.nrad1 < 0 || g.nrad2 < 0 || g.nang1 < 1 || g.nang2 < 1) return bad(BIP_ERR_INVALID_ARG, "rings");
     if (g.recon != BIP_RECON_COMPLEX && g.recon != BIP_RECON_MAGNITUDE) return bad(BIP_ERR_INVALID_ARG, "recon");

@@ -353,7 +353,17 @@ bip_status bip_build_geometry(const bip_config& c, BipGeometry& g, std::string& 
     g.dfy = c.dfy > 0 ? c.dfy : c.fy;
     g.dfx = c.dfx > 0 ? c.dfx : c.fx;
     g.h_det = disc(c, g.lambda, c.theta_det, g.dfy, g.dfx);
-    g.h_cube = disc(c, g.lambda, c.theta_det, 1, 1);
+    if (c.cube_ky > 0 && c.cube_kx > 0) {
+        // a box of k-pixels centred on the zero beam, (h_y, h_x) ascending
+        g.h_cube.clear();
+        for (int a = -(c.cube_ky / 2); a < c.cube_ky - c.cube_ky / 2; ++a)
+            for (int b = -(c.cube_kx / 2); b < c.cube_kx - c.cube_kx / 2; ++b) {
+                g.h_cube.push_back(a);
+                g.h_cube.push_back(b);
+            }
+    } else {
+        g.h_cube = disc(c, g.lambda, c.theta_det, 1, 1);
+    }
     g.B = (int)g.h_beam.size() / 2;
     g.n_det = (int)g.h_det.size() / 2;
     g.n_cube = (int)g.h_cube.size() / 2;

@@ -28,6 +28,10 @@ class Config:
     # along x wants dfx = 1, along y dfy = 1
     dfy: int = 0
     dfx: int = 0
+    # the 4D cube's output basis: 0, 0 -- every beam inside the detector
+    # disc; else a box of cube_ky x cube_kx k-pixels centred on the zero beam
+    cube_ky: int = 0
+    cube_kx: int = 0
     nrad1: int = 2
     nang1: int = 6
     nrad2: int = 2

@@ -41,7 +41,8 @@ def _cfgs():
             c1.replace(name="aniso", ny=64, nx=128, ly=6.0, lx=10.0, fy=1, fx=2, win=32),
             c1.replace(name="rings", nrad1=3, nrad2=4, nang1=5, nang2=7),
             c1.replace(name="aberrated", defocus=-35.0, cs=1e4),
-            c1.replace(name="qeels_x", dfx=1), c1.replace(name="qeels_y", dfy=1, nrad2=3)]
+            c1.replace(name="qeels_x", dfx=1), c1.replace(name="qeels_y", dfy=1, nrad2=3),
+            c1.replace(name="cube_box", cube_ky=32, cube_kx=20)]
 
 
 @pytest.mark.parametrize("cfg", _cfgs(), ids=lambda c: c.name)
@@ -82,6 +83,8 @@ def test_config2_sizes(capi):
     (dict(e0=-1.0), "BIP_ERR_INVALID_ARG"),
     (dict(nang1=0), "BIP_ERR_INVALID_ARG"),
     (dict(dfx=3), "BIP_ERR_SHAPE"),
+    (dict(cube_ky=256, cube_kx=16), "BIP_ERR_SHAPE"),
+    (dict(cube_ky=16), "BIP_ERR_SHAPE"),
     (dict(dfy=-1), "BIP_ERR_SHAPE"),
 ])
 def test_create_rejects_bad_config(capi, change, status):

@@ -243,6 +243,20 @@ def test_cube_edge_cases(lib, prec, tol):
     assert np.array_equal(_cube(ctx, sp, H), cube)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("mixed", 1e-3)])
+def test_cube_on_a_box_of_k_pixels(lib, prec, tol):
+    """A 40 x 24 box of k-pixels as the cube's basis (a pixelated detector
+    of that shape; 960 beams, beyond the 40 mrad disc along y) against the
+    oracle's cube on the same basis."""
+    cfg = synth.config1().replace(cube_ky=40, cube_kx=24)
+    sp = synth.make_specimen(cfg)
+    pr = obip.make_problem(sp)
+    ctx, m, _, H = gpu_run(lib, cfg, sp, prec=prec)
+    assert np.array_equal(ctx.cube_beams, pr.geo.h_cube) and len(pr.geo.h_cube) == 960
+    assert rel(_cube(ctx, sp, H), obip.bip_cube(pr)) < tol
+    ctx.close()
+
+
 @pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
 def test_cube_in_beam_batches(lib, c1, prec):
     """A memory limit that splits the complete basis into several backward

@@ -72,6 +72,17 @@ def test_cube_is_algorithm3_brute_force(kw):
     assert rel(cube, bip.alg3_cube(pr)) < 1e-12
 
 
+def test_cube_on_a_box_of_k_pixels():
+    """The cube's basis as a box of k-pixels (16 x 12 around the zero beam,
+    the shape of a pixelated detector) instead of the detector disc: still
+    Algorithm 3 by brute force, beam by beam."""
+    pr = problem(small_cell(cube_ky=16, cube_kx=12))
+    h = pr.geo.h_cube
+    assert h.shape == (192, 2)
+    assert h[:, 0].min() == -8 and h[:, 0].max() == 7 and h[:, 1].min() == -6 and h[:, 1].max() == 5
+    assert rel(bip.bip_cube(pr), bip.alg3_cube(pr)) < 1e-12
+
+
 def test_cube_full_parent_limit_is_exact_prism():
     """Every aperture beam its own parent: the cube is exact PRISM's
     (Algorithm 2 with the exact exit), and at f = 1 that is conventional
