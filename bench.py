@@ -594,16 +594,12 @@ def run_cube(cfg, sp, prec="mixed", reps=1):
 
 
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of
-# the same launch size (profiles/recon_coupling_tc_config2_19site_batch.md,
-# profiles/fp8_recon_coupling_gram_config2_19site_batch.md); reported only
-# while the kernel's source file is unchanged.
+# the same launch size (profiles/recon_coupling_tc_config2_19site_batch.md);
+# reported only while the kernel's source file is unchanged.
 NCU_TRAFFIC = {
-    ("mixed", "coupling"): {"bytes": 1074423000 + 139347200,
+    ("mixed", "coupling"): {"bytes": 1078868992 + 136250112,
                             "source": "paper_2607_00756_gb300/csrc/gemm_tc.cu",
-                            "sha256": "09060694c621889f4d35024e05cc13767e85ef4fd0fcfc3b7ae1831d4055e9db"},
-    ("fp8", "coupling"): {"bytes": 474455296 + 131020800,
-                          "source": "paper_2607_00756_gb300/csrc/gemm_tc.cu",
-                          "sha256": "09060694c621889f4d35024e05cc13767e85ef4fd0fcfc3b7ae1831d4055e9db"},
+                            "sha256": "4ed2dfc0c26dd6b10004674ca76ecf519e88896f79a0c1abc4d71e4fe7443c3c"},
 }
 
 
