@@ -94,7 +94,8 @@ typedef struct {
 } bip_atom;
 
 /* Simulation parameters (lengths in Angstrom, angles in rad, energy in eV).
- * Constraints checked by bip_create: ny, nx powers of two in [64, 1024];
+ * Constraints checked by bip_create: ny, nx powers of two in [64, 1024] or
+ * 3 times a power of two in [64, 256] (192, 384, 768 -- for f = 3);
  * fy | ny and fx | nx; dfy, dfx 0 or dividing ny, nx; win a multiple of
  * 16 with 16 <= win <=
  * min(ny/fy, nx/fx); nz >= 1;
@@ -318,7 +319,8 @@ bip_status bip_set_aberrations(bip_ctx* ctx, double defocus, double cs, void* st
  *   d_V [nz, ny, nx] float32 device: dL/dV_j of every slice potential,
  *         through the reconstruction (Eq. magpreserve) and both sweeps
  *         (Eq. smatrix-advance, Eq. s2); V (device, the potential the
- *         matrices were built from) is then required.  The sweeps' forward
+ *         matrices were built from) is then required; power-of-two grid
+ *         lengths only (else BIP_ERR_UNSUPPORTED).  The sweeps' forward
  *         states are recomputed from checkpoints every ceil(sqrt(n)) slices.
  * Any output may be NULL (not computed).  Steps: R_tau = f_y f_x o_tau
  * sum_{rho in crop} g c c^H; Mbar = M R; dL/dH_n(r) = 2 sum_{d,b}

@@ -142,8 +142,8 @@ __global__ void gv_reduce_kernel(const float* part, int groups, int G, float* gV
 // re-tilt phi_t(r) = exp(sign 2 pi i (h_y iy / ny + h_x ix / nx)) at window pixel r
 __device__ __forceinline__ float2 retilt(int2 h, const SiteDev& st, int r, int win, int ny, int nx, int sign) {
     const int u = r / win, vv = r - u * win;
-    const int iy = (st.oy + u) & (ny - 1), ix = (st.ox + vv) & (nx - 1);
-    const float f = (float)((h.x * iy) & (ny - 1)) / ny + (float)((h.y * ix) & (nx - 1)) / nx;
+    const int iy = wrap_n(st.oy + u, ny), ix = wrap_n(st.ox + vv, nx);
+    const float f = (float)(wrap_n(h.x * iy, ny)) / ny + (float)(wrap_n(h.y * ix, nx)) / nx;
     float s, c;
     sincospif(2.f * f, &s, &c);
     return make_float2(c, sign * s);

@@ -203,6 +203,9 @@ cudaError_t upload(DevBuf& b, const std::vector<T>& h, cudaStream_t s) {
 }
 
 bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+// grid lengths the register FFTs take: powers of two 64..1024, and 3 m for m
+// a power of two 64..256 (192, 384, 768)
+bool grid_len_ok(int n) { return pow2_in(n, 64, 1024) || (n % 3 == 0 && pow2_in(n / 3, 64, 256)); }
 
 int signed_bin(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
 
@@ -213,7 +216,23 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 // Ns = 8^p with radix R (8, or 4 / 2 for the last pass), and its entry
 // (r - 1) Ns + k holds exp(-2 pi i r k / (Ns R)), r = 1..R-1, k < Ns.
 // Evaluated in FP64, rounded to FP32; the rest of the n entries is zero.
+// For n = 3 m (m a power of two): the table of length m, then the radix-3
+// step's exp(-2 pi i j k / n) for j = 1, 2 and k < m -- n entries in all.
+std::vector<float2> fft_twiddles_pow2(int n);
 std::vector<float2> fft_twiddles(int n) {
+    if (n % 3 != 0) return fft_twiddles_pow2(n);
+    const int m = n / 3;
+    std::vector<float2> t = fft_twiddles_pow2(m);
+    t.resize(n);
+    for (int j = 1; j <= 2; ++j)
+        for (int k = 0; k < m; ++k) {
+            const double a = -2.0 * kPi * (double)j * k / (double)n;
+            t[(size_t)m + (size_t)(j - 1) * m + k] = float2{(float)std::cos(a), (float)std::sin(a)};
+        }
+    return t;
+}
+
+std::vector<float2> fft_twiddles_pow2(int n) {
     int lg = 0;
     while ((1 << lg) < n) ++lg;
     const int rl = lg % 3 == 2 ? 4 : (lg % 3 == 1 ? 2 : 8);
@@ -549,7 +568,7 @@ bip_status bip_create(const bip_config* cfg, bip_ctx** out) {
         delete c;
         return s;
     };
-    if (!pow2_in(g.ny, 64, 1024) || !pow2_in(g.nx, 64, 1024)) return bad(BIP_ERR_SHAPE, "grid");
+    if (!grid_len_ok(g.ny) || !grid_len_ok(g.nx)) return bad(BIP_ERR_SHAPE, "grid");
     if (!(g.ly > 0) || !(g.lx > 0) || g.nz < 1 || !(g.dz >= 0) || !(g.e0 > 0) || !(g.alpha > 0) ||
         !(g.theta_det > 0) || !std::isfinite(g.defocus) || !std::isfinite(g.cs))
         return bad(BIP_ERR_INVALID_ARG, "optics");
@@ -2368,6 +2387,8 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
     bip_status st = check_map_args(c, H, scan_px, P, dL_dI);
     if (st != BIP_OK) return st;
     if (d_V && !V) return fail(c, BIP_ERR_INVALID_ARG, "d_V needs the V the matrices were built from");
+    if (d_V && (!pow2_in(c->cfg.ny, 64, 1024) || !pow2_in(c->cfg.nx, 64, 1024)))
+        return fail(c, BIP_ERR_UNSUPPORTED, "dL/dV (the adjoint sweeps) needs power-of-two grid lengths");
     if ((reinterpret_cast<uintptr_t>(d_H) & 7) != 0) return fail(c, BIP_ERR_INVALID_ARG, "d_H must be 8-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     const bip_config& g = c->cfg;

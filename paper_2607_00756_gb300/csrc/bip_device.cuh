@@ -18,3 +18,10 @@ __device__ __forceinline__ bool in_crop(double ry, double rx, double ty, double 
     const double hx = 0.5 * nx / fx;
     return d >= -hx && d < hx;
 }
+
+// x mod n in [0, n) for any sign of x (grid lengths need not be powers of
+// two: 3 M lengths are allowed).
+__device__ __forceinline__ int wrap_n(int x, int n) {
+    const int r = x % n;
+    return r < 0 ? r + n : r;
+}

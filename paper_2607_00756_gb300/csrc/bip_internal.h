@@ -542,7 +542,7 @@ struct RetiltArgs {
     int n_sites;                    // sites of this batch
     const int32_t* site_ids;
     const SiteDev* sites;
-    int win, ny, nx, K;             // ny, nx powers of two
+    int win, ny, nx, K;
     int nd;                         // beams in the stash
     const float2* stash;
     const int2* h;                  // [nd] (h_y, h_x)

@@ -165,3 +165,89 @@ __device__ __forceinline__ void fft_reg(float2 (&v)[8], float2* b0, float2* b1, 
         ph ^= 1;
     }
 }
+
+// ---------------------------------------------------------------------------
+// Length N = 3 M (M a power of two, 64..256): decimation in time by 3.  The
+// three interleaved subsequences x[3 p + j] (j = 0, 1, 2) are transformed as
+// three length-M transforms on the same threads, in lockstep through one
+// exchange buffer of N entries (region j M .. j M + M - 1 for sub-transform
+// j), then combined by a radix-3 step:
+//   X[k + l M] = sum_j exp(-2 pi i j k / N) exp(-2 pi i j l / 3) Y_j[k].
+// Thread t (NT = M / 8 of them) holds x[3 (t + m NT) + j] in v[j][m] on entry
+// and X[t + m NT + l M] in v[l][m] on exit; the inverse transform (no 1/N)
+// goes the other way.  Its twiddle table holds the length-M table and then
+// exp(-2 pi i j k / N) for j = 1, 2 and k < M ([2][M]): N entries in all.
+
+// radix-3 butterfly in place: (a0, a1, a2) -> sum_j a_j W^(j l), W = exp(-+2 pi i / 3)
+template <bool INV>
+__device__ __forceinline__ void dft3(float2& a0, float2& a1, float2& a2) {
+    const float s = 0.86602540378443864676f;   // sin(pi / 3)
+    const float2 t1 = c_add(a1, a2);
+    const float2 d = c_sub(a1, a2);
+    // -i s d (forward) or +i s d (inverse)
+    const float2 t2 = INV ? make_float2(-s * d.y, s * d.x) : make_float2(s * d.y, -s * d.x);
+    const float2 m = make_float2(fmaf(-0.5f, t1.x, a0.x), fmaf(-0.5f, t1.y, a0.y));
+    a0 = c_add(a0, t1);
+    a1 = c_add(m, t2);
+    a2 = c_sub(m, t2);
+}
+
+template <int M, bool INV>
+__device__ __forceinline__ void fft3_combine(float2 (&v)[3][8], int t, const float2* tw3) {
+    constexpr int NT = M / 8;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int k = t + m * NT;
+        float2 w1 = tw3[k], w2 = tw3[M + k];
+        if (INV) {
+            w1.y = -w1.y;
+            w2.y = -w2.y;
+            dft3<true>(v[0][m], v[1][m], v[2][m]);
+            v[1][m] = c_mul(v[1][m], w1);
+            v[2][m] = c_mul(v[2][m], w2);
+        } else {
+            v[1][m] = c_mul(v[1][m], w1);
+            v[2][m] = c_mul(v[2][m], w2);
+            dft3<false>(v[0][m], v[1][m], v[2][m]);
+        }
+    }
+}
+
+template <int M, bool INV, int P>
+__device__ __forceinline__ void fft3_step(float2 (&v)[3][8], float2* buf, int t, const float2* tw) {
+    using F = FftReg<M, INV>;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) buf[j * M + FFT_SWZ(F::out_pos(P, r, t))] = v[j][r];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float2 u[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) u[e] = buf[j * M + FFT_SWZ(F::template in_pos<P>(e, t))];
+        F::template pass<P>(u, v[j], t, tw);
+    }
+}
+
+// One length-3M transform with two alternating exchange buffers of 3M
+// entries each (as fft_reg); tw: the table described above.
+template <int M, bool INV>
+__device__ __forceinline__ void fft_reg3(float2 (&v)[3][8], float2* b0, float2* b1, int& ph, int t,
+                                         const float2* tw) {
+    using F = FftReg<M, INV>;
+    if (INV) fft3_combine<M, true>(v, t, tw + M);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F::first(v[j]);
+    fft3_step<M, INV, 1>(v, ph ? b1 : b0, t, tw);
+    ph ^= 1;
+    if constexpr (F::NPASS > 2) {
+        fft3_step<M, INV, 2>(v, ph ? b1 : b0, t, tw);
+        ph ^= 1;
+    }
+    if constexpr (F::NPASS > 3) {
+        fft3_step<M, INV, 3>(v, ph ? b1 : b0, t, tw);
+        ph ^= 1;
+    }
+    if (!INV) fft3_combine<M, false>(v, t, tw + M);
+}

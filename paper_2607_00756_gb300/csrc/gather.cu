@@ -22,6 +22,7 @@
 // pairs) stores, a warp covering whole 128-byte segments.
 #include <cuda_bf16.h>
 
+#include "bip_device.cuh"
 #include "bip_internal.h"
 #include "fft_smem.cuh"
 
@@ -97,8 +98,8 @@ __global__ void __launch_bounds__(kThreads, 3) gather_kernel(GatherArgs a) {
     const int gb = blockIdx.y * (kWarps * kGroupsPerWarp);
     const int ge = min(gb + kWarps * kGroupsPerWarp, a.grp.n_groups);
 
-    float2 stp0 = __ldg(&a.ex[(a.fx * (st.ox + v)) & (a.nx - 1)]);
-    float2 stp1 = __ldg(&a.ex[(a.fx * (st.ox + v + 1)) & (a.nx - 1)]);
+    float2 stp0 = __ldg(&a.ex[wrap_n(a.fx * (st.ox + v), a.nx)]);
+    float2 stp1 = __ldg(&a.ex[wrap_n(a.fx * (st.ox + v + 1), a.nx)]);
     if (a.tilt_sign < 0) {
         stp0.y = -stp0.y;
         stp1.y = -stp1.y;
@@ -137,11 +138,11 @@ __global__ void __launch_bounds__(kThreads, 3) gather_kernel(GatherArgs a) {
                     t0 = c_mul(t0, stp0);
                     t1 = c_mul(t1, stp1);
                 } else {
-                    const float2 base = c_mul(__ldg(&a.ey[(h.x * st.oy) & (a.ny - 1)]),
-                                              __ldg(&a.ex[(h.y * st.ox) & (a.nx - 1)]));
-                    const float2 ty = __ldg(&a.ytab[(size_t)(h.x & (a.ny - 1)) * a.win + u]);
+                    const float2 base = c_mul(__ldg(&a.ey[wrap_n(h.x * st.oy, a.ny)]),
+                                              __ldg(&a.ex[wrap_n(h.y * st.ox, a.nx)]));
+                    const float2 ty = __ldg(&a.ytab[(size_t)(wrap_n(h.x, a.ny)) * a.win + u]);
                     const float4 tx =
-                        __ldg(reinterpret_cast<const float4*>(a.xtab + (size_t)(h.y & (a.nx - 1)) * a.win + v));
+                        __ldg(reinterpret_cast<const float4*>(a.xtab + (size_t)(wrap_n(h.y, a.nx)) * a.win + v));
                     const float2 by = c_mul(base, ty);
                     t0 = c_mul(by, make_float2(tx.x, tx.y));
                     t1 = c_mul(by, make_float2(tx.z, tx.w));

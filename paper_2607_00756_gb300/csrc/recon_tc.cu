@@ -36,6 +36,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "bip_device.cuh"
 #include "fft_smem.cuh"
 #include "tc_common.cuh"
 
@@ -298,14 +299,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int wu = px0 / a.win;
                 wv = px0 - wu * a.win;
                 const float2 base =
-                    c_mul(__ldg(&a.ey[(h.x * st.oy) & (a.ny - 1)]), __ldg(&a.ex[(h.y * st.ox) & (a.nx - 1)]));
-                F = c_mul(base, c_mul(__ldg(&a.ytab[(size_t)(h.x & (a.ny - 1)) * a.win + wu]),
-                                      __ldg(&a.xtab[(size_t)(h.y & (a.nx - 1)) * a.win + wv])));
-                sx1 = __ldg(&a.ex[h.y & (a.nx - 1)]);
-                sx4 = __ldg(&a.ex[(4 * h.y) & (a.nx - 1)]);
-                sx8 = __ldg(&a.ex[(8 * h.y) & (a.nx - 1)]);
-                X64 = __ldg(&a.ex[(64 * h.y) & (a.nx - 1)]);
-                Z = c_mul(__ldg(&a.ey[h.x & (a.ny - 1)]), __ldg(&a.ex[(-a.win * h.y) & (a.nx - 1)]));
+                    c_mul(__ldg(&a.ey[wrap_n(h.x * st.oy, a.ny)]), __ldg(&a.ex[wrap_n(h.y * st.ox, a.nx)]));
+                F = c_mul(base, c_mul(__ldg(&a.ytab[(size_t)(wrap_n(h.x, a.ny)) * a.win + wu]),
+                                      __ldg(&a.xtab[(size_t)(wrap_n(h.y, a.nx)) * a.win + wv])));
+                sx1 = __ldg(&a.ex[wrap_n(h.y, a.nx)]);
+                sx4 = __ldg(&a.ex[wrap_n(4 * h.y, a.nx)]);
+                sx8 = __ldg(&a.ex[wrap_n(8 * h.y, a.nx)]);
+                X64 = __ldg(&a.ex[wrap_n(64 * h.y, a.nx)]);
+                Z = c_mul(__ldg(&a.ey[wrap_n(h.x, a.ny)]), __ldg(&a.ex[wrap_n(-a.win * h.y, a.nx)]));
                 if (sd.tilt_sign < 0) {
                     F.y = -F.y;
                     sx1.y = -sx1.y;

@@ -42,7 +42,9 @@ def _cfgs():
             c1.replace(name="rings", nrad1=3, nrad2=4, nang1=5, nang2=7),
             c1.replace(name="aberrated", defocus=-35.0, cs=1e4),
             c1.replace(name="qeels_x", dfx=1), c1.replace(name="qeels_y", dfy=1, nrad2=3),
-            c1.replace(name="cube_box", cube_ky=32, cube_kx=20)]
+            c1.replace(name="cube_box", cube_ky=32, cube_kx=20),
+            c1.replace(name="f3_384", ny=384, nx=384, ly=30.0, lx=30.0, fy=3, fx=3),
+            c1.replace(name="f3_aniso", ny=768, nx=192, ly=60.0, lx=15.0, fy=3, fx=3, nrad2=3, dfx=1)]
 
 
 @pytest.mark.parametrize("cfg", _cfgs(), ids=lambda c: c.name)
@@ -74,6 +76,8 @@ def test_config2_sizes(capi):
 
 @pytest.mark.parametrize("change,status", [
     (dict(ny=96), "BIP_ERR_SHAPE"),
+    (dict(ny=1536, ly=120.0), "BIP_ERR_SHAPE"),
+    (dict(ny=320), "BIP_ERR_SHAPE"),
     (dict(nx=2048), "BIP_ERR_SHAPE"),
     (dict(win=40), "BIP_ERR_SHAPE"),
     (dict(win=128), "BIP_ERR_SHAPE"),
