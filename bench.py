@@ -369,19 +369,22 @@ def run_gpu(args, rank, world):
 # extra lines: specimens under one CUDA graph; the reverse pass
 
 def graph_specimens():
-    """Sixteen small specimens of uneven size: grids 128^2 / 256^2, 5 to 20
-    slices, f = 2 / 4, one, three or nine channels, seeds 0..15."""
+    """Sixteen small specimens of uneven size: grids 128^2, 192^2 and 256^2,
+    5 to 20 slices, f = 2, 3 and 4, one, three or nine channels, seeds
+    0..15."""
     import synth
     out = []
     for i in range(16):
-        big = i % 4 == 3
         nz = (5, 10, 20)[i % 3]
         cfg = synth.config1().replace(
             name=f"spec{i}", seed=i, nz=nz, ion_slices=(1, nz, max(1, nz // 3)),
             channels=((0,), (-1, 0, 1), tuple(range(-4, 5)))[i % 3])
-        if big:
+        if i % 4 == 3:
             cfg = cfg.replace(ny=256, nx=256, ly=20.0, lx=20.0, cells_y=8, cells_x=8, fy=4, fx=4,
                               ion_cells=(3, 5), scan_y=(100.0, 4.0, 12), scan_x=(100.0, 4.0, 12))
+        elif i % 4 == 1:
+            cfg = cfg.replace(ny=192, nx=192, ly=15.0, lx=15.0, cells_y=6, cells_x=6, fy=3, fx=3,
+                              ion_cells=(2, 4), scan_y=(68.0, 4.0, 10), scan_x=(68.0, 4.0, 10))
         out.append(cfg)
     return out
 
@@ -415,22 +418,26 @@ def run_graphs(prec="mixed", reps=20):
         eager()
     torch.cuda.synchronize()
     t_eager = (time.perf_counter() - t0) / reps
-    g = GraphedMaps(items)
-    for _ in range(3):
-        g.replay()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        g.replay()
-    torch.cuda.synchronize()
-    t_graph = (time.perf_counter() - t0) / reps
-    g.check()
+    out = {"specimens": len(items), "precision": prec, "evals_per_round": evals, "eager_ms": t_eager * 1e3,
+           "eager_evals_per_s": evals / t_eager}
+    for name, conc in (("graph", False), ("graph_concurrent", True)):
+        g = GraphedMaps(items, concurrent=conc)
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            g.replay()
+        torch.cuda.synchronize()
+        t_graph = (time.perf_counter() - t0) / reps
+        g.check()
+        out[f"{name}_ms"] = t_graph * 1e3
+        out[f"{name}_evals_per_s"] = evals / t_graph
+        del g
     for ctx, _, _ in items:
         ctx.close()
-    return {"specimens": len(items), "precision": prec, "evals_per_round": evals,
-            "eager_ms": t_eager * 1e3, "graph_ms": t_graph * 1e3,
-            "eager_evals_per_s": evals / t_eager, "graph_evals_per_s": evals / t_graph,
-            "timing": "host wall clock around 20 repetitions, synchronised"}
+    out["timing"] = "host wall clock around 20 repetitions, synchronised; graph_concurrent: one stream per specimen"
+    return out
 
 
 def run_grad(reps=3, prec="mixed"):

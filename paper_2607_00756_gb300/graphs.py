@@ -12,13 +12,18 @@ from . import capi
 
 
 class GraphedMaps:
-    def __init__(self, items):
-        """items: [(BipContext, H, scans)], each context built."""
+    def __init__(self, items, concurrent=True):
+        """items: [(BipContext, H, scans)], each context built.  concurrent:
+        each specimen's launches on a stream of its own, forked from and
+        joined back to the capturing stream, so that the graph's branches
+        (the specimens share no buffers) can run side by side and small
+        specimens fill the GPU together; otherwise one after another."""
         self.items = [(b, H, np.asarray(sc, dtype=np.float64)) for b, H, sc in items]
         if not self.items:
             raise ValueError("no specimens")
         dev = self.items[0][1].device
         self.outs = [torch.empty(len(sc), dtype=torch.float64, device=dev) for _, _, sc in self.items]
+        self.streams = [torch.cuda.Stream(device=dev) for _ in self.items] if concurrent else None
         for b, _, _ in self.items:
             capi.bip_set_capture_safe(b.ctx, True)
         side = torch.cuda.Stream(device=dev)
@@ -33,8 +38,17 @@ class GraphedMaps:
             self._run()
 
     def _run(self):
-        for (b, H, sc), o in zip(self.items, self.outs):
-            b.map(H, sc, out=o)
+        if self.streams is None:
+            for (b, H, sc), o in zip(self.items, self.outs):
+                b.map(H, sc, out=o)
+            return
+        main = torch.cuda.current_stream()
+        for (b, H, sc), o, st in zip(self.items, self.outs, self.streams):
+            st.wait_stream(main)                      # fork
+            with torch.cuda.stream(st):
+                b.map(H, sc, out=o)
+        for st in self.streams:
+            main.wait_stream(st)                      # join
 
     def replay(self):
         """Re-run every map; returns the output tensors (one per specimen)."""

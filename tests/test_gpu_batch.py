@@ -59,13 +59,14 @@ def test_graph_replay_matches_eager_and_oracle(lib):
         items.append((ctx, H, sp.scans))
         refs.append(obip.bip_map(obip.make_problem(sp)).map)
         tols.append(tol)
-    g = GraphedMaps(items)
-    for _ in range(3):
-        outs = g.replay()
-        torch.cuda.synchronize()
-        g.check()
-        for o, e in zip(outs, eager):
-            assert np.array_equal(o.cpu().numpy(), e)
+    for conc in (False, True):
+        g = GraphedMaps(items, concurrent=conc)
+        for _ in range(3):
+            outs = g.replay()
+            torch.cuda.synchronize()
+            g.check()
+            for o, e in zip(outs, eager):
+                assert np.array_equal(o.cpu().numpy(), e), conc
     for e, r, tol in zip(eager, refs, tols):
         # the FP8 context: within 3% (its E4M3 rounding), the others their bars
         assert rel(e, r) < (tol if tol is not None else 3e-2)
