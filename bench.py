@@ -237,6 +237,8 @@ def algorithmic(cfg, geo_sizes, n_sites, n_crop, nch, geo_beams=None, path="fp32
         "ms_col_bytes": 8.0 * G,
         # operand writes plus the two stashes read once
         "gather_bytes": (op_bytes * K * (n_det + nch * B) + 8.0 * K * (bp1 + bp2)) * n_sites,
+        # the slices' transmissions, once per build: V read, T written
+        "transmission_bytes": 12.0 * G * cfg.nz,
     }
 
 
@@ -661,6 +663,8 @@ def stage_roofline(cfg, path, stage, ms, n, steps, info, geo_sizes):
             per_launch = alg[stage + "_bytes"] * (bp1 + bp2) / 2.0
         elif stage == "gather":
             per_launch = alg["gather_bytes"] / (n / steps)
+        elif stage == "transmission":
+            per_launch = alg["transmission_bytes"]
         else:   # reduce: every partial read once
             per_launch = 4.0 * info["n_sites"] * info["P"] / (n / steps)
         achieved = per_launch / (ms_launch / 1e3) / 1e9
@@ -774,6 +778,8 @@ def main():
                     help="skip the CUDA-graph batch and the reverse-pass lines")
     ap.add_argument("--max-sites", type=int, default=0,
                     help="keep only the first N ionized sites (profiling case)")
+    ap.add_argument("--only", default="", choices=["", "cube"],
+                    help="analysis: run only this line on the workload (with --max-sites) and print it")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -809,6 +815,12 @@ def main():
         return
 
     import torch
+    if args.only == "cube":
+        from paper_2607_00756_gb300 import build as pbuild
+        pbuild.build()
+        cfg, sp = workload(args.workload, 0, args.max_sites, args.scan_side)
+        print(json.dumps({"cube": run_cube(cfg, sp, reps=max(1, args.steps))}))
+        return
     if world > 1:
         torch.distributed.init_process_group("nccl")
     cfg, sp, results, info = run_gpu(args, rank, world)

@@ -356,13 +356,14 @@ bip_status bip_site_coupling(bip_ctx* ctx, const void* H, int32_t site, void* m_
  * time in ms and the number of launches since profiling was (re)enabled.
  * Stages: multislice row pass, multislice column pass, window
  * reconstruction, coupling GEMM, Gram GEMM, quadratic form, illumination +
- * site sum.  ms / launches: [BIP_N_STAGES] host arrays (either may be
+ * site sum, the slices' transmissions exp(i sigma V) (once per build).  ms / launches: [BIP_N_STAGES] host arrays (either may be
  * NULL).  bip_set_profiling(ctx, on): on = 0 stops timing, on < 0 times
  * every stage, on > 0 times the stages whose bit (1 << stage) is set; the
  * launch counts cover every stage.  Each call clears earlier records. */
 enum {
     BIP_STAGE_MS_ROW = 0, BIP_STAGE_MS_COL = 1, BIP_STAGE_GATHER = 2, BIP_STAGE_COUPLING = 3,
-    BIP_STAGE_GRAM = 4, BIP_STAGE_QUADFORM = 5, BIP_STAGE_REDUCE = 6, BIP_N_STAGES = 7
+    BIP_STAGE_GRAM = 4, BIP_STAGE_QUADFORM = 5, BIP_STAGE_REDUCE = 6, BIP_STAGE_TRANSMISSION = 7,
+    BIP_N_STAGES = 8
 };
 bip_status bip_set_profiling(bip_ctx* ctx, int32_t on);
 bip_status bip_get_profile(bip_ctx* ctx, double* ms, int64_t* launches);

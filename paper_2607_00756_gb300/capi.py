@@ -400,8 +400,8 @@ def bip_coreloss_grad(ctx, H, scans, dL_dI, d_occ=None, d_H=None, aberr=False, V
     return (float(ab[0]), float(ab[1])) if aberr else None
 
 
-N_STAGES = 7
-STAGES = ["ms_row", "ms_col", "gather", "coupling", "gram", "quadform", "reduce"]
+N_STAGES = 8
+STAGES = ["ms_row", "ms_col", "gather", "coupling", "gram", "quadform", "reduce", "transmission"]
 
 
 def bip_set_profiling(ctx, on, stages=None):

@@ -70,6 +70,7 @@ struct bip_ctx {
     DevBuf cube_grp, cube_wmap, mpart;  // cube-mode work groups; map modes' item map and column sums
     DevBuf hcube, shcube, cstash, ccols; // the exact cube: basis, shifts, S2 windows, columns
     DevBuf xopA, xopB, xm32;            // ... its coupling operands and M
+    DevBuf tcache;                      // T_j = exp(i sigma V_j) of the slices a sweep crosses
     size_t cube_budget = 0;             // bytes of sweep columns + windows per detector batch (0: auto)
     DevBuf s1t, psi, ybuf;              // the probe order: S1 transposed, Psi, H_n x Psi
     DevBuf pyc, pxc;                    // conjugated propagator tables (adjoint sweeps)
@@ -611,7 +612,7 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->g_dt1, &c->g_dt2, &c->g_adj, &c->g_ckpt, &c->g_seg, &c->g_gvp, &c->pyc, &c->pxc,
                      &c->ray, &c->rax, &c->g_tA, &c->g_tB, &c->g_sA2, &c->g_sB2, &c->cubeA, &c->cubeB,
                      &c->cube_work, &c->cube_mask, &c->s1t, &c->psi, &c->ybuf, &c->cube_grp, &c->cube_wmap, &c->mpart,
-                     &c->hcube, &c->shcube, &c->cstash, &c->ccols, &c->xopA, &c->xopB, &c->xm32};
+                     &c->hcube, &c->shcube, &c->cstash, &c->ccols, &c->xopA, &c->xopB, &c->xm32, &c->tcache};
     for (DevBuf* b : all) release(*b);
     for (int i = 0; i < 6; ++i) {
         release(c->aw1[i]);
@@ -678,6 +679,9 @@ bip_status bip_build_s1(bip_ctx* c, const float* V, const bip_atom* atoms, int32
     const MsPlan plan = plan_for(c, ncol, c->shift1);
     int last = 0;
     for (auto& sd : c->sites) last = std::max(last, (int)sd.plane);
+    // the transmissions of the slices the sweep crosses, once
+    CUDA_TRY(c, ensure(c->tcache, (size_t)g.nz * G * sizeof(float2), false, s));
+    TIMED(c, BIP_STAGE_TRANSMISSION, s, bip_transmission(V, (float)c->geo.sigma, 0, last, G, (float2*)c->tcache.p, s));
     for (int j = 0; j <= last; ++j) {
         MsRowArgs a{};
         a.cols = (float2*)c->cols.p;
@@ -686,6 +690,7 @@ bip_status bip_build_s1(bip_ctx* c, const float* V, const bip_atom* atoms, int32
         a.do_ifft = j > 0;
         a.v_pre = nullptr;
         a.v_post = j < last ? V + (size_t)j * G : nullptr;
+        a.t_slice = j < last ? (const float2*)c->tcache.p + (size_t)j * G : nullptr;
         a.do_fft = j < last;
         if (c->plane_off[j + 1] > c->plane_off[j]) {
             a.row_off = (const int32_t*)c->row_off_d.p + (size_t)j * (g.ny + 1);
@@ -726,11 +731,14 @@ bip_status bip_build_s2(bip_ctx* c, const float* V, const bip_atom* atoms, int32
         TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
         TIMED(c, BIP_STAGE_MS_COL, s, bip_ms_col_pass(plan, (float2*)c->cols.p, s));
     }
+    CUDA_TRY(c, ensure(c->tcache, (size_t)g.nz * G * sizeof(float2), false, s));
+    TIMED(c, BIP_STAGE_TRANSMISSION, s, bip_transmission(V, (float)c->geo.sigma, first, g.nz, G, (float2*)c->tcache.p, s));
     for (int j = g.nz - 1; j >= first; --j) {
         MsRowArgs a{};
         a.cols = (float2*)c->cols.p;
         a.do_ifft = 1;
         a.v_pre = V + (size_t)j * G;
+        a.t_slice = (const float2*)c->tcache.p + (size_t)j * G;
         a.do_fft = j > first;
         if (c->plane_off[j + 1] > c->plane_off[j]) {
             a.row_off = (const int32_t*)c->row_off_d.p + (size_t)j * (g.ny + 1);
@@ -1939,6 +1947,8 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
 
     int first_plane = g.nz - 1;
     for (auto& sd : c->sites) first_plane = std::min(first_plane, (int)sd.plane);
+    CUDA_TRY(c, ensure(c->tcache, (size_t)g.nz * G * sizeof(float2), false, s));
+    TIMED(c, BIP_STAGE_TRANSMISSION, s, bip_transmission(V, (float)geo.sigma, first_plane, g.nz, G, (float2*)c->tcache.p, s));
     for (int d0 = 0; d0 < n_cube; d0 += nbd) {
         const int nd = std::min(nbd, n_cube - d0);
         // the batch's exact S2 columns, exit surface to the first site plane
@@ -1960,6 +1970,7 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
             a.cols = (float2*)c->ccols.p;
             a.do_ifft = 1;
             a.v_pre = V + (size_t)j * G;
+            a.t_slice = (const float2*)c->tcache.p + (size_t)j * G;
             a.do_fft = j > first_plane;
             if (c->plane_off[j + 1] > c->plane_off[j]) {
                 a.row_off = (const int32_t*)c->row_off_d.p + (size_t)j * (g.ny + 1);

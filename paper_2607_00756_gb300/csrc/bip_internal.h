@@ -85,6 +85,8 @@ struct MsRowArgs {
     const float* v_pre;             // V slice applied before the stash (or null)
     const float* v_post;            // V slice applied after the stash (or null);
                                     // at most one of the two is set
+    const float2* t_slice;          // the slice's T = exp(i sigma V) [ny][nx], when
+                                    // precomputed (else evaluated from V)
     int init;                       // 1: start from a constant field `init_val`
     float init_val;
     int do_ifft, do_fft;
@@ -98,6 +100,9 @@ struct MsRowArgs {
                                     // [ncol, ny, nx] (null: not kept)
 };
 cudaError_t bip_ms_row_pass(const MsPlan& plan, const MsRowArgs& a, cudaStream_t s);
+// T_j = exp(i sigma V_j) of slices j0 .. j1 - 1 into T [nz][ny][nx] (the same
+// slice offsets as V), once per build, for the row passes of both sweeps
+cudaError_t bip_transmission(const float* V, float sigma, int j0, int j1, size_t G, float2* T, cudaStream_t s);
 cudaError_t bip_ms_col_pass(const MsPlan& plan, float2* cols, cudaStream_t s);
 
 // gather.cu : window reconstruction into GEMM operands

@@ -17,7 +17,10 @@
 // One step of a column is two passes over global memory:
 //   row pass    [inverse FFT along x] [T_pre] [stash, save] [T_post] [FFT along x]
 //   column pass FFT along y, times the shifted propagator, inverse FFT along y
-// with T_j = exp(i sigma V_j) evaluated in-kernel from V (sincosf).
+// with T_j = exp(i sigma V_j) read from a table the build computes once per
+// slice (shared by every column and both sweeps), or evaluated in-kernel
+// from V (sincosf) where no table is kept.
+#include <algorithm>
 #include <cstdio>
 
 #include "bip_internal.h"
@@ -93,9 +96,13 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(MsPlan plan, MsRowAr
     for (int i = threadIdx.x; i < NX; i += kThreads) {
         tw[i] = __ldg(&plan.twx[i]);
         if (vsl) {
-            float sn, co;
-            sincosf(plan.sigma * __ldg(&vsl[(size_t)y * NX + i]), &sn, &co);
-            tt[i] = make_float2(co, sn);
+            if (a.t_slice) {
+                tt[i] = __ldg(&a.t_slice[(size_t)y * NX + i]);
+            } else {
+                float sn, co;
+                sincosf(plan.sigma * __ldg(&vsl[(size_t)y * NX + i]), &sn, &co);
+                tt[i] = make_float2(co, sn);
+            }
         }
     }
     __syncthreads();
@@ -267,6 +274,14 @@ __global__ void __launch_bounds__(ColShape<NY>::THREADS, ColShape<NY>::MINB) col
                 make_float4(va[q][m].x, va[q][m].y, vb[q][m].x, vb[q][m].y);
 }
 
+__global__ void transmission_kernel(const float* __restrict__ V, float sigma, size_t n, float2* __restrict__ T) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float sn, co;
+        sincosf(sigma * __ldg(&V[i]), &sn, &co);
+        T[i] = make_float2(co, sn);
+    }
+}
+
 template <int NX>
 cudaError_t launch_row(const MsPlan& p, const MsRowArgs& a, cudaStream_t s) {
     constexpr int RPB = RowShape<NX>::RPB, ROWLEN = NX;
@@ -326,4 +341,12 @@ cudaError_t bip_ms_col_pass(const MsPlan& p, float2* cols, cudaStream_t s) {
         case 768: return launch_col<768>(p, cols, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t bip_transmission(const float* V, float sigma, int j0, int j1, size_t G, float2* T, cudaStream_t s) {
+    if (j1 <= j0) return cudaSuccess;
+    const size_t n = (size_t)(j1 - j0) * G;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+    transmission_kernel<<<blocks, 256, 0, s>>>(V + (size_t)j0 * G, sigma, n, T + (size_t)j0 * G);
+    return cudaGetLastError();
 }
