@@ -780,6 +780,8 @@ def main():
                     help="keep only the first N ionized sites (profiling case)")
     ap.add_argument("--only", default="", choices=["", "cube"],
                     help="analysis: run only this line on the workload (with --max-sites) and print it")
+    ap.add_argument("--cube-box", type=int, default=0,
+                    help="analysis: the cube on a box of N x N k-pixels instead of the detector disc")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -816,9 +818,13 @@ def main():
 
     import torch
     if args.only == "cube":
+        import synth
         from paper_2607_00756_gb300 import build as pbuild
         pbuild.build()
         cfg, sp = workload(args.workload, 0, args.max_sites, args.scan_side)
+        if args.cube_box:
+            cfg = cfg.replace(cube_ky=args.cube_box, cube_kx=args.cube_box)
+            sp = synth.Specimen(cfg=cfg, atoms=sp.atoms, nch=sp.nch, V=sp.V, H=sp.H, scans=sp.scans)
         print(json.dumps({"cube": run_cube(cfg, sp, reps=max(1, args.steps))}))
         return
     if world > 1:

@@ -22,6 +22,7 @@ __device__ __forceinline__ bool in_crop(double ry, double rx, double ty, double 
 // x mod n in [0, n) for any sign of x (grid lengths need not be powers of
 // two: 3 M lengths are allowed).
 __device__ __forceinline__ int wrap_n(int x, int n) {
+    if ((n & (n - 1)) == 0) return x & (n - 1);   // a power of two: a mask (two's complement)
     const int r = x % n;
     return r < 0 ? r + n : r;
 }
