@@ -68,6 +68,7 @@ struct bip_ctx {
     DevBuf g_tA, g_tB, g_sA2, g_sB2;    // split-BF16 operands of the reverse-pass contractions
     DevBuf cubeA, cubeB, cube_work, cube_mask;   // the cube on tcgen05
     DevBuf cube_grp, cube_wmap, mpart;  // cube-mode work groups; map modes' item map and column sums
+    std::vector<int32_t> cube_work_h, cube_grp_h, cube_wmap_h;   // what the device copies hold
     DevBuf hcube, shcube, cstash, ccols; // the exact cube: basis, shifts, S2 windows, columns
     DevBuf xopA, xopB, xm32;            // ... its coupling operands and M
     DevBuf tcache;                      // T_j = exp(i sigma V_j) of the slices a sweep crosses
@@ -194,6 +195,17 @@ void release(DevBuf& b) {
     }
     b.p = nullptr;
     b.cap = 0;
+}
+
+// true while `s` is being captured into a CUDA graph (a host-to-device copy
+// from host memory that lives only during the call must not be recorded)
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return st != cudaStreamCaptureStatusNone;
 }
 
 template <class T>
@@ -761,6 +773,22 @@ bip_status bip_build_s2(bip_ctx* c, const float* V, const bip_atom* atoms, int32
 
 namespace {
 
+// Frees the map's batch-sized workspaces (operands, M, the cube kernel's
+// operands and partial sums, the probe order's buffers, FP8 scales) after
+// the stream has drained; the next map allocates what its batching needs.
+// Tables, builds, scans and work lists stay.
+void release_map_workspaces(bip_ctx* c, cudaStream_t s) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    for (DevBuf* b : {&c->opA32, &c->opB32, &c->mt32, &c->q32, &c->opA16, &c->opB16, &c->mt16, &c->q16,
+                      &c->op8A, &c->op8B, &c->gdiff, &c->cubeA, &c->cubeB, &c->cube_mask, &c->mpart,
+                      &c->s1t, &c->psi, &c->ybuf, &c->xtc, &c->f8pmax, &c->f8inv0, &c->f8inv1, &c->f8sA,
+                      &c->f8sB})
+        release(*b);
+}
+
 // Gather arguments of one side (1: S1 windows of the aperture beams,
 // 2: S2 windows of the detector beams) for sites ids[0 .. n).
 GatherArgs gather_args(const bip_ctx* c, int side, const int32_t* ids, int n) {
@@ -1285,6 +1313,9 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     const bool same_scans = c->capture_safe && c->scans_cache.size() == (size_t)P * 2 &&
                             std::equal(scans, scans + 2 * P, c->scans_cache.begin());
     if (!same_scans) {
+        if (capturing(s))
+            return fail(c, BIP_ERR_INVALID_ARG,
+                        "a captured map must repeat the scans of the capture-safe warm-up call");
         CUDA_TRY(c, ensure(c->scans_d, (size_t)P * 2 * sizeof(double), false, s));
         CUDA_TRY(c, cudaMemcpyAsync(c->scans_d.p, scans, (size_t)P * 2 * sizeof(double), cudaMemcpyHostToDevice, s));
         c->scans_cache.assign(scans, scans + 2 * P);
@@ -1419,6 +1450,8 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         }
     }
     batch_off.push_back((int)work.size() / 2);
+    if (capturing(s))
+        return fail(c, BIP_ERR_INVALID_ARG, "a captured map must repeat the arguments of the capture-safe warm-up call");
     CUDA_TRY(c, upload(c->work_d, work, s));
     c->work_key = work_key;
     }
@@ -1503,13 +1536,24 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         }
         cube_off.push_back((int)cw.size() / 2);
         cube_goff.push_back((int)cg.size());
-        CUDA_TRY(c, upload(c->cube_work, cw, s));
-        if (cube_out) CUDA_TRY(c, upload(c->cube_grp, cg, s));
-        if (!cube_out) {
-            CUDA_TRY(c, upload(c->cube_wmap, wm, s));
+        // uploaded only when they differ from the device copies (so that a
+        // capture-safe map repeated with its warm-up arguments records no copy)
+        auto sync_list = [&](DevBuf& d, std::vector<int32_t>& held, const std::vector<int32_t>& v) -> bip_status {
+            if (held == v && d.p) return BIP_OK;
+            if (capturing(s))
+                return fail(c, BIP_ERR_INVALID_ARG,
+                            "a captured map must repeat the arguments of the capture-safe warm-up call");
+            CUDA_TRY(c, upload(d, v, s));
+            held = v;
+            return BIP_OK;
+        };
+        bip_status sl = sync_list(c->cube_work, c->cube_work_h, cw);
+        if (sl == BIP_OK && cube_out) sl = sync_list(c->cube_grp, c->cube_grp_h, cg);
+        if (sl == BIP_OK && !cube_out) sl = sync_list(c->cube_wmap, c->cube_wmap_h, wm);
+        if (sl != BIP_OK) return sl;
+        if (!cube_out)
             CUDA_TRY(c, ensure(c->mpart, std::max<size_t>(1, (size_t)max_items * (D128 / 128) * tile) * sizeof(float),
                                false, s));
-        }
         n_ct_map = n_ct;
         CUDA_TRY(c, ensure(c->cube_mask, std::max<size_t>(1, cw.size() / 2 * (tile / 64)) * sizeof(unsigned long long),
                            false, s));
@@ -1941,6 +1985,8 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
         cube_goff.push_back((int)cg.size());
         CUDA_TRY(c, upload(c->cube_work, cw, s));
         CUDA_TRY(c, upload(c->cube_grp, cg, s));
+        c->cube_work_h = cw;                // what the device copies now hold
+        c->cube_grp_h = cg;
         CUDA_TRY(c, ensure(c->cube_mask, std::max<size_t>(1, cw.size() / 2 * (ctn / 64)) * sizeof(unsigned long long),
                            false, s));
     }
@@ -2305,6 +2351,11 @@ bip_status bip_autotune(bip_ctx* c, const void* H, const double* scan_px, int32_
     double best = 1e300, t = 0.0;
     for (int sb : sbs) {
         st = time_map(sb, 0, &t);
+        if (st == BIP_ERR_OOM && sb != base) {
+            release_map_workspaces(c, s);
+            st = BIP_OK;
+            continue;
+        }
         if (st != BIP_OK) break;
         if (t < best) {
             best = t;
@@ -2333,6 +2384,12 @@ bip_status bip_autotune(bip_ctx* c, const void* H, const double* scan_px, int32_
             if (o == order0 || (o == 2 && !probe_ok)) continue;
             c->order = o;
             st = time_map(best_sb, best_cw, &t);
+            if (st == BIP_ERR_OOM) {
+                // this order's workspaces do not fit: not a candidate
+                release_map_workspaces(c, s);
+                st = BIP_OK;
+                continue;
+            }
             if (st != BIP_OK) break;
             if (t < best) {
                 best = t;
@@ -2347,6 +2404,11 @@ bip_status bip_autotune(bip_ctx* c, const void* H, const double* scan_px, int32_
         for (int sb : {8, 12, 13, 14, 16, 19, 24, 27, 28, 32}) {
             if (sb == best_sb || sb > std::max(1, c->n_sites)) continue;
             st = time_map(sb, best_cw, &t);
+            if (st == BIP_ERR_OOM) {
+                release_map_workspaces(c, s);
+                st = BIP_OK;
+                continue;
+            }
             if (st != BIP_OK) break;
             if (t < best) {
                 best = t;
@@ -2359,6 +2421,9 @@ bip_status bip_autotune(bip_ctx* c, const void* H, const double* scan_px, int32_
     c->sb_override = best_sb;
     c->cw_override = best_cw;
     c->order = best_order;
+    // the trials' largest workspaces are not kept: the next map allocates
+    // what the chosen settings need
+    release_map_workspaces(c, s);
     if (st != BIP_OK) return st;
     if (sites_per_batch) *sites_per_batch = best_sb;
     if (coupling_tile) *coupling_tile = best_cw;
