@@ -442,6 +442,117 @@ def run_graphs(prec="mixed", reps=20):
     return out
 
 
+# the batched workload's ranges: grids 256^2-1024^2, 20-300 slices, f = 2,
+# 3, 4, 1-9 channels, 32-2000 sites, 64 x 64 probes
+CONFIG4 = [  # (grid, f, slices, channels, sites)
+    (256, 2, 20, 1, 32), (256, 4, 60, 3, 64), (384, 3, 40, 9, 48), (384, 3, 120, 3, 96),
+    (512, 4, 300, 3, 2000), (512, 2, 50, 1, 128), (768, 3, 80, 3, 96), (768, 3, 20, 9, 32),
+    (1024, 4, 100, 3, 128), (1024, 4, 30, 1, 64), (256, 2, 200, 3, 128), (384, 3, 160, 1, 200),
+    (512, 4, 250, 9, 160), (768, 3, 40, 3, 64), (1024, 4, 20, 3, 32), (256, 4, 100, 9, 32)]
+
+
+def config4_specimen(i, n, f, nz, nch, target):
+    """One specimen of the batched workload: the synthetic crystal at 0.078 A
+    pixels, 300 keV, 25 mrad, 40 mrad detector, n_radial = 4; about `target`
+    sites in a central square of c x c cells on every stride-th slice; 64 x 64
+    scans at 1 px around them."""
+    import synth
+    cells = n // 32
+    per = min(nz, 20)
+    c = min(cells - 2, int(math.ceil(math.sqrt(target / per))))
+    planes = max(1, min(nz, int(round(target / (c * c)))))
+    stride = max(1, nz // planes)
+    c0 = (cells - c) // 2
+    mid = (c0 + c / 2.0) * 32.0
+    ch = {1: (0,), 3: (-1, 0, 1), 9: tuple(range(-4, 5))}[nch]
+    return synth.config2().replace(
+        name=f"c4_{i}", ny=n, nx=n, ly=n / 12.8, lx=n / 12.8, cells_y=cells, cells_x=cells, nz=nz, fy=f, fx=f,
+        channels=ch, ion_cells=(c0, c0 + c), ion_slices=(nz - stride * planes, nz, stride), seed=100 + i,
+        scan_y=(mid - 32.0, 1.0, 64), scan_x=(mid - 32.0, 1.0, 64), oracle_scan_y=None, oracle_scan_x=None)
+
+
+def run_config4(prec="mixed", reps=5):
+    """The batched workload at its own scale: 16 specimens (CONFIG4), every
+    context autotuned (sites per batch, coupling tile, contraction order),
+    the maps eager one after another and as one CUDA graph with a stream per
+    specimen (matrices built once; CUDA events around the rounds); and the
+    cube of the first specimen on a 128 x 128 box of k-pixels for its 64 x 64
+    probes."""
+    import torch
+    import synth
+    from paper_2607_00756_gb300.context import BipContext
+    from paper_2607_00756_gb300.graphs import GraphedMaps
+    dev = torch.device("cuda:0")
+    items, evals, tuned, sites = [], 0, [], []
+    for i, spec in enumerate(CONFIG4):
+        cfg = config4_specimen(i, *spec)
+        sp = synth.make_specimen(cfg)
+        V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
+        ctx = BipContext(cfg, prec=prec)
+        ctx.build(V, sp.atoms, sp.nch)
+        del V
+        H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+        sb, cw, order, ms = ctx.autotune(H, sp.scans)
+        tuned.append([sb, cw, ORDERS[order], round(ms, 2)])
+        n_sites = int((sp.nch > 0).sum())
+        sites.append(n_sites)
+        evals += n_sites * len(sp.scans)
+        items.append((ctx, H, sp.scans))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def eager():
+        for ctx, H, sc in items:
+            ctx.map(H, sc)
+    eager()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        eager()
+    e1.record()
+    torch.cuda.synchronize()
+    t_eager = e0.elapsed_time(e1) / reps
+    g = GraphedMaps(items, concurrent=True)
+    g.replay()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    g.check()
+    t_graph = e0.elapsed_time(e1) / reps
+    del g
+    for ctx, _, _ in items:
+        ctx.close()
+    items.clear()
+    # the cube on config 4's pixelated detector, first specimen
+    cfg = config4_specimen(0, *CONFIG4[0]).replace(cube_ky=128, cube_kx=128)
+    sp = synth.make_specimen(cfg)
+    V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
+    H = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+    ctx = BipContext(cfg, prec=prec)
+    ctx.build_s1(V, sp.atoms, sp.nch)
+    out = torch.empty((len(sp.scans), 128 * 128), dtype=torch.float32, device=dev)
+    ctx.cube(V, H, sp.scans, out=out)
+    torch.cuda.synchronize()
+    e0.record()
+    ctx.build_s1(V, sp.atoms, sp.nch)
+    ctx.cube(V, H, sp.scans, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    t_cube = e0.elapsed_time(e1)
+    cube_sites = int((sp.nch > 0).sum())
+    ctx.close()
+    return {"specimens": len(CONFIG4), "grids": [c[0] for c in CONFIG4], "f": [c[1] for c in CONFIG4],
+            "slices": [c[2] for c in CONFIG4], "channels": [c[3] for c in CONFIG4], "sites": sites,
+            "scans": 4096, "precision": prec, "evals_per_round": evals,
+            "autotuned": "[sites per batch, coupling tile, order, ms] " + json.dumps(tuned),
+            "eager_ms": round(t_eager, 2), "graph_concurrent_ms": round(t_graph, 2),
+            "eager_evals_per_s": evals / (t_eager / 1e3), "graph_evals_per_s": evals / (t_graph / 1e3),
+            "cube_128x128_ms": round(t_cube, 1), "cube_evals_per_s": cube_sites * 4096 / (t_cube / 1e3),
+            "timing": "maps only (matrices built once), CUDA events around 5 rounds; the cube with its S1 build"}
+
+
 def run_grad(reps=3, prec="mixed"):
     """The reverse pass on the differentiation workload (config 5): forward
     map plus dL/d(occupancy, H, defocus, Cs, V), CUDA events.  A mixed
@@ -778,7 +889,7 @@ def main():
                     help="skip the CUDA-graph batch and the reverse-pass lines")
     ap.add_argument("--max-sites", type=int, default=0,
                     help="keep only the first N ionized sites (profiling case)")
-    ap.add_argument("--only", default="", choices=["", "cube"],
+    ap.add_argument("--only", default="", choices=["", "cube", "config4"],
                     help="analysis: run only this line on the workload (with --max-sites) and print it")
     ap.add_argument("--cube-box", type=int, default=0,
                     help="analysis: the cube on a box of N x N k-pixels instead of the detector disc")
@@ -817,6 +928,11 @@ def main():
         return
 
     import torch
+    if args.only == "config4":
+        from paper_2607_00756_gb300 import build as pbuild
+        pbuild.build()
+        print(json.dumps({"config4": run_config4()}))
+        return
     if args.only == "cube":
         import synth
         from paper_2607_00756_gb300 import build as pbuild
@@ -867,6 +983,7 @@ def main():
         line["accuracy"] = {f"{p}_vs_fp32_rel_l2": float(np.linalg.norm(results[p]["map"] - b) / np.linalg.norm(b))
                             for p in ok if p != "fp32"}
     if args.extras:
+        line["config4"] = run_config4()
         line["graphs"] = run_graphs()
         line["grad"] = run_grad()
         line["cube"] = run_cube(cfg, sp)
