@@ -18,9 +18,10 @@
 //     warp 0     TMA producer: the unit's W tile (128 targets x 64 parents,
 //                hi and lo) once, then X tiles (64 pixels x 64 parents, three
 //                planes) through a 4-stage ring
-//     warp 1     TMEM allocator and MMA issuer: per 64-pixel tile, 24 MMAs
-//                (M=128, N=64, K=16) into three accumulators, two TMEM
-//                buffers so the epilogue of one tile overlaps the next
+//     warp 1     TMEM allocator and MMA issuer: per 64-pixel tile, 8 MMAs
+//                (M=128, N=192: the three planes side by side, K=16) into
+//                three accumulators, two TMEM buffers so the epilogue of one
+//                tile overlaps the next
 //     warps 2-17 epilogue: thread = target row (TMEM lane), 16 pixels per
 //                warp and tile; magnitude preservation, re-tilt stepped
 //                along the window row in four independent chains, H_n
@@ -90,6 +91,22 @@ __device__ __forceinline__ void st_v4(void* p, const uint32_t (&v)[4]) {
     asm volatile("st.global.v4.b32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
                  : "memory");
 }
+
+// the hardware reciprocal square root (relative error near 2^-23; the
+// operands leave in BF16 or E4M3)
+__device__ __forceinline__ float rsqrt_hw(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Magnitude step with no branch: U = 0 must give the real A (the phase of a
+// vanishing sum is taken as 0).  Adding 2^-60 to Re U before |U| does that
+// (then U = (2^-60, 0), whose phase is 0, and |U|^2 = 2^-120 is still a
+// normal FP32 number) and moves the phase of any other U by at most
+// 2^-60 / |U|, far below the rounding of the parents' FP16 values.
+constexpr float kPhaseGuard = 8.67361737988403547e-19f;   // 2^-60
+constexpr float kTinyNormal = 1.17549435e-38f;             // 2^-126
 
 // F8: the operands are written as E4M3 bytes, row t scaled by
 // inv_row[side][t] and channel n by inv_h[n] (per-window scales)
@@ -179,11 +196,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     uint8_t* st = bbuf + s * kBStage;
                     mbar_expect_tx(&full[s], kBStage);
+                    // per K block, the three planes' 64-row tiles back to back:
+                    // one 192-row B operand
 #pragma unroll
-                    for (int pl = 0; pl < 3; ++pl)
+                    for (int kb = 0; kb < 2; ++kb)
 #pragma unroll
-                        for (int kb = 0; kb < 2; ++kb)
-                            tma_2d(st + (pl * 2 + kb) * kBPlane, &mapX, kb * 32, xrow0 + pl * a.K + t * kN, &full[s]);
+                        for (int pl = 0; pl < 3; ++pl)
+                            tma_2d(st + (kb * 3 + pl) * kBPlane, &mapX, kb * 32, xrow0 + pl * a.K + t * kN, &full[s]);
                     ++issued;
                     if (++s == kStages) {
                         s = 0;
@@ -209,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer
-            const uint32_t id = idesc_f16(128, kN, false);
+            const uint32_t id = idesc_f16(128, 3 * kN, false);   // re, im, magnitude side by side
             int s = 0, acc = 0;
             uint32_t ph = 0, aph = 0;
             bool any = false, ok = true;
@@ -238,12 +257,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const uint64_t whi = sdesc(abase + (0 * 2 + kb) * kAPlane + kk * 32);
                             const uint64_t wlo = sdesc(abase + (1 * 2 + kb) * kAPlane + kk * 32);
                             const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-#pragma unroll
-                            for (int pl = 0; pl < 3; ++pl) {
-                                const uint64_t xd = sdesc(bbase + (pl * 2 + kb) * kBPlane + kk * 32);
-                                mma(d0 + pl * kN, whi, xd, id, first);
-                                mma(d0 + pl * kN, wlo, xd, id, 1);
-                            }
+                            const uint64_t xd = sdesc(bbase + kb * 3 * kBPlane + kk * 32);
+                            mma(d0, whi, xd, id, first);
+                            mma(d0, wlo, xd, id, 1);
                         }
                     any = true;
                     mma_commit(&empty[s]);
@@ -378,10 +394,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const int k = 4 * c + j;
                             float2 v;
                             if (a.magnitude) {
-                                const float m2 = fmaf(vr[k], vr[k], vi[k] * vi[k]);
+                                const float ur = vr[k] + kPhaseGuard;
+                                const float m2 = fmaf(ur, ur, vi[k] * vi[k]);
                                 const float mk = F8 ? vm[k] * ir : vm[k];
-                                const float sc = mk * rsqrtf(fmaxf(m2, 1.17549435e-38f));
-                                v = make_float2(m2 > 0.f ? vr[k] * sc : mk, vi[k] * sc);
+                                const float sc = mk * rsqrt_hw(fmaxf(m2, kTinyNormal));
+                                v = make_float2(ur * sc, vi[k] * sc);
                             } else {
                                 v = F8 ? make_float2(vr[k] * ir, vi[k] * ir) : make_float2(vr[k], vi[k]);
                             }
