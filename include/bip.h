@@ -190,9 +190,11 @@ bip_status bip_build_s2(bip_ctx* ctx, const float* V, const bip_atom* atoms,
  * each site contributing only at scans whose minimum-image offset from it
  * lies in [-N/(2f), N/(2f)) on both axes (crop mask).  Sites are summed in
  * a fixed order in FP64 with Neumaier compensation.
- *   H        [sum nch, win, win] complex64 device: transition potentials of
- *            each site's channels sampled on its window, sites in order;
- *            16-byte aligned (else BIP_ERR_INVALID_ARG).
+ *   H        complex64 device: transition potentials of each site's
+ *            channels sampled on its window, sites in order, each channel
+ *            [w, w] (w = win, or the site's own window after
+ *            bip_set_site_windows: [sum_sites nch w^2] in all); 16-byte
+ *            aligned (else BIP_ERR_INVALID_ARG).
  *   scan_px  [P, 2] float64 host: scan positions in pixels (y, x).
  *   map_out  [P] float64 device.
  * Requires both builds on this context (else BIP_ERR_INVALID_ARG). */
@@ -307,6 +309,25 @@ bip_status bip_set_order(bip_ctx* ctx, int32_t order);
  *   the following maps (the matrices do not depend on them). */
 bip_status bip_set_occupancy(bip_ctx* ctx, const double* occ);
 bip_status bip_set_aberrations(bip_ctx* ctx, double defocus, double cs, void* stream);
+
+/* Windows of their own for the sites (Eq. coupling: the sum over the crop
+ * window Omega_tau of each site, whose size follows the support of its
+ * H_n; sites of several edges batched in one map).  win: host int32
+ * [n_sites] in the order of the built sites, each a multiple of 16 in
+ * [16, the context's win] or 0 (the context's win); NULL: every site at the
+ * context's win again.  Site k's window is the w_k x w_k block starting at
+ * floor(t + 1/2) - w_k/2 on each axis -- the central block of the window
+ * the builds stash, so the builds need not be repeated.  The map then takes
+ * its sites in batches of one window size each, every contraction of a
+ * batch over its w_k^2 pixels, and H holds each site's channels on its own
+ * window (see bip_coreloss_map).  Kept until the next build with another
+ * site list.  Only the maps in the Gram order (bip_coreloss_map,
+ * bip_coreloss_sites, bip_autotune) take such sites: the cube, qEELS, the
+ * beam and probe orders, the reverse pass, bip_site_windows and
+ * bip_site_coupling return BIP_ERR_UNSUPPORTED while a site's window is
+ * below win.  BIP_ERR_INVALID_ARG before a build, for a bad size, or when
+ * H would exceed 2^31 complex elements. */
+bip_status bip_set_site_windows(bip_ctx* ctx, const int32_t* win, void* stream);
 
 /* Reverse pass of a scalar loss L of the map: given g = dL/dI(rho) on the
  * scans, the derivatives at the context's current state (occupancies,

@@ -57,7 +57,10 @@ from .geometry import Geometry
 class Problem:
     """Inputs of one map evaluation, prepared in FP64."""
 
-    def __init__(self, cfg, atoms, nch, V, H, scans, geometry=None):
+    def __init__(self, cfg, atoms, nch, V, H, scans, geometry=None, site_win=None):
+        """site_win: the window of each ionized site (default: cfg.win for
+        all); H: [sum nch, win, win] when every site has cfg.win, else a list
+        with one [nch_k, w_k, w_k] array per ionized site."""
         self.cfg = cfg
         self.lam = ph.wavelength(cfg.e0)
         self.sigma = ph.interaction_constant(cfg.e0)
@@ -69,17 +72,28 @@ class Problem:
         self.tau_px = np.stack([atoms[self.ion, 0] / dy, atoms[self.ion, 1] / dx], axis=1)
         self.plane = atoms[self.ion, 2].astype(np.int64)
         self.nch = np.asarray(nch)[self.ion].astype(np.int64)
-        off = np.concatenate([[0], np.cumsum(self.nch)])
-        self.H = [H[off[k]:off[k + 1]] for k in range(len(self.ion))]
+        n = len(self.ion)
+        self.win = (np.full(n, cfg.win, dtype=np.int64) if site_win is None
+                    else np.asarray(site_win, dtype=np.int64).reshape(n))
+        if isinstance(H, (list, tuple)):
+            self.H = [np.asarray(h) for h in H]
+        else:
+            off = np.concatenate([[0], np.cumsum(self.nch)])
+            self.H = [H[off[k]:off[k + 1]] for k in range(n)]
+        for k in range(n):
+            w = int(self.win[k])
+            if self.H[k].shape != (self.nch[k], w, w):
+                raise ValueError(f"site {k}: H has shape {self.H[k].shape}, want {(int(self.nch[k]), w, w)}")
         self.scans = np.asarray(scans, dtype=np.float64)
 
     # ---- transmission of slice j
     def T(self, j):
         return ph.transmission(self.V[j], self.sigma)
 
-    # ---- window geometry of ionized site k
+    # ---- window geometry of ionized site k: w_k x w_k pixels from
+    # floor(tau/dx + 1/2) - w_k/2 on each axis, wrapped
     def window_index(self, k):
-        w = self.cfg.win
+        w = int(self.win[k])
         oy = int(math.floor(self.tau_px[k, 0] + 0.5)) - w // 2
         ox = int(math.floor(self.tau_px[k, 1] + 0.5)) - w // 2
         iy = np.mod(oy + np.arange(w), self.cfg.ny)
@@ -574,6 +588,8 @@ def elastic_probe_at(prob: Problem, rho, plane):
     return psi
 
 
-def make_problem(spec, geometry=None, **cfg_overrides):
+def make_problem(spec, geometry=None, site_win=None, H=None, **cfg_overrides):
+    """Problem of a synthetic specimen; site_win and H (per-site arrays)
+    replace the uniform windows and the specimen's H when given."""
     cfg = spec.cfg.replace(**cfg_overrides) if cfg_overrides else spec.cfg
-    return Problem(cfg, spec.atoms, spec.nch, spec.V, spec.H, spec.scans, geometry)
+    return Problem(cfg, spec.atoms, spec.nch, spec.V, spec.H if H is None else H, spec.scans, geometry, site_win)

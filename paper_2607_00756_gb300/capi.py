@@ -77,6 +77,7 @@ def _load():
         "bip_build_s1_noalloc": [VP, VP, P(BipAtom), I32, VP, VP],
         "bip_get_profile": [VP, VP, VP],
         "bip_set_occupancy": [VP, P(D)],
+        "bip_set_site_windows": [VP, P(I32), VP],
         "bip_set_capture_safe": [VP, I32],
         "bip_set_raster_eval": [VP, I32],
         "bip_check_errors": [VP, VP],
@@ -379,6 +380,16 @@ def bip_set_occupancy(ctx, occ):
         return
     o = np.ascontiguousarray(occ, dtype=np.float64)
     _check("bip_set_occupancy", ctx, _lib.bip_set_occupancy(ctx, o.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+
+def bip_set_site_windows(ctx, win, stream=None):
+    """Windows of their own for the built sites (None: all at the context's win)."""
+    if win is None:
+        _check("bip_set_site_windows", ctx, _lib.bip_set_site_windows(ctx, None, _stream(stream)))
+        return
+    w = np.ascontiguousarray(win, dtype=np.int32)
+    _check("bip_set_site_windows", ctx,
+           _lib.bip_set_site_windows(ctx, w.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream(stream)))
 
 
 def bip_set_aberrations(ctx, defocus, cs, stream=None):

@@ -130,6 +130,12 @@ class BipContext:
         """Per-site occupancies weighting the site sum (None: all 1)."""
         capi.bip_set_occupancy(self.ctx, None if occ is None else np.asarray(occ, dtype=np.float64))
 
+    def set_site_windows(self, win, stream=None):
+        """Per-site windows (multiples of 16 up to the context's win; 0 or None:
+        the context's win) for the following maps; H then holds each site's
+        channels on its own window, flattened in site order."""
+        capi.bip_set_site_windows(self.ctx, None if win is None else np.asarray(win, dtype=np.int32), stream)
+
     def set_aberrations(self, defocus, cs, stream=None):
         """Probe defocus and Cs (Angstrom) for the next map."""
         capi.bip_set_aberrations(self.ctx, defocus, cs, stream)

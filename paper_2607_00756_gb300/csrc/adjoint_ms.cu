@@ -223,7 +223,7 @@ __global__ void s1bar_kernel(const int32_t* ids, const SiteDev* sites, int B, in
     const SiteDev st = sites[ids[bs]];
     float sx = 0.f, sy = 0.f;
     for (int n = 0; n < st.nch; ++n) {
-        const float2 h = __ldg(&H[(size_t)(st.ch_off + n) * K + r]);
+        const float2 h = __ldg(&H[(size_t)st.h_off + (size_t)n * K + r]);
         const float2 x = T[(int64_t)bs * t_site + (int64_t)n * t_ch + (int64_t)b * K + r];
         // conj(h) x
         sx += h.x * x.x + h.y * x.y;

@@ -51,6 +51,14 @@ struct bip_ctx {
     std::vector<int32_t> plane_off;     // [nz + 1]
     DevBuf sites_d, plane_ids_d, seq_ids_d, row_off_d, row_ent_d;
     int n_sites = 0, nch_max = 0, n_ch_total = 0;
+    // per-site windows (bip_set_site_windows; empty: every site at win) and
+    // the order the maps batch the sites in: by window, descending, stable
+    // (seq_ids_d holds it)
+    std::vector<int32_t> site_w;
+    std::vector<int32_t> batch_order;
+    bool uneven = false;                // some site's window is below win
+    int64_t h_elems = 0;                // complex elements of H the sites read
+    int op_k = 0;                       // row pitch of the coupling operands' current contents
     uint64_t sig1 = 0, sig2 = 0;        // site-list signatures of the builds
     bool s1 = false, s2 = false;
 
@@ -466,6 +474,11 @@ bip_status parse_sites(bip_ctx* c, const bip_atom* atoms, int32_t n_atoms, std::
         sd.plane = a.slice;
         sd.nch = a.nch;
         sd.ch_off = off;
+        sd.w = g.win;
+        sd.wo = 0;
+        if ((int64_t)(off + a.nch) * g.win * g.win > INT32_MAX)
+            return fail(c, BIP_ERR_INVALID_ARG, "H would exceed 2^31 complex elements");
+        sd.h_off = off * g.win * g.win;
         off += a.nch;
         nmax = std::max(nmax, (int)a.nch);
         sites.push_back(sd);
@@ -509,13 +522,43 @@ void row_windows(const bip_config& g, const std::vector<SiteDev>& sites, std::ve
     }
 }
 
+// Per-site windows onto the site list: w, wo and the H offsets, the batch
+// order (sites by window, descending; ties in site order), and both to the
+// device.  site_w empty: every site at the context's win.
+bip_status apply_windows(bip_ctx* c, cudaStream_t s) {
+    const int win = c->cfg.win;
+    const int n = (int)c->sites.size();
+    int64_t h = 0;
+    c->uneven = false;
+    for (int k = 0; k < n; ++k) {
+        SiteDev& sd = c->sites[k];
+        sd.w = c->site_w.empty() ? win : c->site_w[k];
+        sd.wo = (win - sd.w) / 2;
+        sd.h_off = (int32_t)h;
+        h += (int64_t)sd.nch * sd.w * sd.w;
+        if (sd.w != win) c->uneven = true;
+    }
+    c->h_elems = h;
+    c->batch_order.resize(n);
+    std::iota(c->batch_order.begin(), c->batch_order.end(), 0);
+    std::stable_sort(c->batch_order.begin(), c->batch_order.end(),
+                     [&](int32_t a, int32_t b) { return c->sites[a].w > c->sites[b].w; });
+    c->work_key = 0;                    // the batches may have changed
+    CUDA_TRY(c, upload(c->sites_d, c->sites, s));
+    CUDA_TRY(c, upload(c->seq_ids_d, c->batch_order, s));
+    return BIP_OK;
+}
+
 bip_status set_sites(bip_ctx* c, std::vector<SiteDev>& sites, int nmax, int total, cudaStream_t s) {
     const bip_config& g = c->cfg;
     const uint64_t sig = site_signature(sites);
     if (sig != c->sig1 && sig != c->sig2) {
         c->s1 = c->s2 = false;
     }
-    if (sig != site_signature(c->sites)) c->occ_n = 0;   // occupancies belong to a site list
+    if (sig != site_signature(c->sites)) {
+        c->occ_n = 0;                   // occupancies and windows belong to a site list
+        c->site_w.clear();
+    }
     c->sites = sites;
     c->n_sites = (int)sites.size();
     c->nch_max = nmax;
@@ -526,11 +569,9 @@ bip_status set_sites(bip_ctx* c, std::vector<SiteDev>& sites, int nmax, int tota
     c->plane_ids.assign(sites.size(), 0);
     std::vector<int32_t> fill(c->plane_off.begin(), c->plane_off.end() - 1);
     for (int i = 0; i < (int)sites.size(); ++i) c->plane_ids[fill[sites[i].plane]++] = i;
-    std::vector<int32_t> seq(sites.size());
-    std::iota(seq.begin(), seq.end(), 0);
-    CUDA_TRY(c, upload(c->sites_d, c->sites, s));
+    bip_status st = apply_windows(c, s);
+    if (st != BIP_OK) return st;
     CUDA_TRY(c, upload(c->plane_ids_d, c->plane_ids, s));
-    CUDA_TRY(c, upload(c->seq_ids_d, seq, s));
     std::vector<int32_t> roff;
     std::vector<int4> rent;
     row_windows(g, c->sites, roff, rent);
@@ -791,13 +832,18 @@ void release_map_workspaces(bip_ctx* c, cudaStream_t s) {
 
 // Gather arguments of one side (1: S1 windows of the aperture beams,
 // 2: S2 windows of the detector beams) for sites ids[0 .. n).
-GatherArgs gather_args(const bip_ctx* c, int side, const int32_t* ids, int n) {
+// w: the batch's window (0: the context's win), the central w x w block of
+// the stashed windows.
+GatherArgs gather_args(const bip_ctx* c, int side, const int32_t* ids, int n, int w = 0) {
     const bip_config& g = c->cfg;
+    if (w <= 0) w = g.win;
     GatherArgs a{};
     a.n_sites = n;
     a.site_ids = ids;
     a.sites = (const SiteDev*)c->sites_d.p;
-    a.win = g.win; a.ny = g.ny; a.nx = g.nx; a.K = g.win * g.win;
+    a.win = w; a.ny = g.ny; a.nx = g.nx; a.K = w * w;
+    a.stash_win = g.win;
+    a.wo = (g.win - w) / 2;
     a.magnitude = g.recon == BIP_RECON_MAGNITUDE;
     a.ey = (const float2*)c->ey.p;
     a.ex = (const float2*)c->ex.p;
@@ -828,11 +874,13 @@ GatherArgs gather_args(const bip_ctx* c, int side, const int32_t* ids, int n) {
 // probe: the aperture side written transposed and without H_n, the probe
 // order's operand: [site][4 planes][K][Bpad], re in plane 0 and im in plane 2
 // (the split-BF16 layout with zero lo planes)
+// w: the batch's window (0: the context's win; operand rows of w^2).
 bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H, void* opA, void* opB,
-                          cudaStream_t s, bool probe = false, bool s2_side = true) {
+                          cudaStream_t s, bool probe = false, bool s2_side = true, int w = 0) {
     const bip_config& g = c->cfg;
     const BipGeometry& geo = c->geo;
-    const int K = g.win * g.win, Dpad = c->Dpad, Bpad = c->Bpad, nch = c->nch_max;
+    if (w <= 0) w = g.win;
+    const int K = w * w, Dpad = c->Dpad, Bpad = c->Bpad, nch = c->nch_max;
     const bool f8 = c->prec == BIP_PREC_FP8_TILE;
     CUDA_TRY(c, ensure(c->xtc, (size_t)2 * nb * 3 * K * 64 * sizeof(uint16_t), false, s));
     if (f8) {
@@ -847,6 +895,9 @@ bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H,
     x.n_sites = nb;
     x.site_ids = ids;
     x.K = K;
+    x.w = w;
+    x.stash_win = g.win;
+    x.wo = (g.win - w) / 2;
     x.X = (uint16_t*)c->xtc.p;
     x.side[0] = XprepSide{s2_side ? (const float2*)c->stash2.p : nullptr, s2_side ? geo.Bp2 : 0, 0};
     x.side[1] = XprepSide{(const float2*)c->stash1.p, geo.Bp1, 3 * nb};
@@ -874,8 +925,16 @@ bip_status recon_tc_batch(bip_ctx* c, const int32_t* ids, int nb, const void* H,
     r.n_sites = nb;
     r.site_ids = ids;
     r.sites = (const SiteDev*)c->sites_d.p;
-    r.K = K; r.win = g.win; r.ny = g.ny; r.nx = g.nx;
-    r.chunk_px = std::min(K, 1024);
+    r.K = K; r.win = w; r.ny = g.ny; r.nx = g.nx;
+    r.stash_win = g.win;
+    r.wo = (g.win - w) / 2;
+    // work units of the largest multiple of 64 pixels up to 1024 that divides K
+    r.chunk_px = 64;
+    for (int cp = std::min(K, 1024) / 64 * 64; cp >= 64; cp -= 64)
+        if (K % cp == 0) {
+            r.chunk_px = cp;
+            break;
+        }
     r.chunks = K / r.chunk_px;
     r.magnitude = g.recon == BIP_RECON_MAGNITUDE;
     r.ey = (const float2*)c->ey.p;
@@ -1154,9 +1213,8 @@ bip_status adjoint_s2(bip_ctx* c, const float* V, float* dV, cudaStream_t s) {
 // it, once per call
 bip_status f8_hmax(bip_ctx* c, const void* H, cudaStream_t s) {
     CUDA_TRY(c, ensure(c->f8hmax, (size_t)c->n_sites * 9 * sizeof(float), false, s));
-    const size_t K = (size_t)c->cfg.win * c->cfg.win;
-    CUDA_TRY(c, ensure(c->f8H, (size_t)c->n_ch_total * K * sizeof(float2), false, s));
-    F8HmaxArgs h{c->n_sites, (const SiteDev*)c->sites_d.p, (int)K, (const float2*)H, (float*)c->f8hmax.p,
+    CUDA_TRY(c, ensure(c->f8H, (size_t)c->h_elems * sizeof(float2), false, s));
+    F8HmaxArgs h{c->n_sites, (const SiteDev*)c->sites_d.p, (const float2*)H, (float*)c->f8hmax.p,
                  (float2*)c->f8H.p};
     TIMED(c, BIP_STAGE_GATHER, s, bip_f8_hmax(h, s));
     return BIP_OK;
@@ -1288,6 +1346,38 @@ CubeArgs cube_args(const bip_ctx* c, const int32_t* ids, int nb, int P, float* c
     return a;
 }
 
+// The coupling operands' rows past a side's targets (the padding up to
+// Dpad / Bpad) must read as zero: the Gram contraction runs over every
+// detector row.  The buffers are zeroed when allocated and every writer
+// packs target rows only, at pitch K = w^2; after a batch packed at another
+// pitch, rows that are padding at pitch K may hold values, so the buffers
+// are cleared before the pitch changes (never while every site has the
+// context's window).
+bip_status operand_layout(bip_ctx* c, int K, cudaStream_t s) {
+    if (c->op_k == K) return BIP_OK;
+    if (c->op_k != 0)
+        for (DevBuf* b : {&c->opA16, &c->opB16, &c->op8A, &c->op8B, &c->opA32, &c->opB32})
+            if (b->p) CUDA_TRY(c, cudaMemsetAsync(b->p, 0, b->cap, s));
+    c->op_k = K;
+    return BIP_OK;
+}
+
+// Batches of the map: at most SB consecutive sites of the batch order, a
+// batch never spanning two window sizes (its contractions run at K = w^2).
+// With every site at the context's window these are the sites 0..SB-1,
+// SB..2SB-1, ...
+std::vector<std::pair<int, int>> map_batches(const bip_ctx* c, int SB) {
+    std::vector<std::pair<int, int>> out;
+    for (int b0 = 0; b0 < c->n_sites;) {
+        const int w = c->sites[c->batch_order[b0]].w;
+        int nb = 1;
+        while (nb < SB && b0 + nb < c->n_sites && c->sites[c->batch_order[b0 + nb]].w == w) ++nb;
+        out.push_back({b0, nb});
+        b0 += nb;
+    }
+    return out;
+}
+
 // The map, its per-site contributions, or the 4D cube (cube_out [P][n_det]):
 // the reconstruction and the coupling are shared, then either the Gram
 // matrix and the scan polynomial or the per-beam contraction.
@@ -1330,6 +1420,8 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     if (probe && (c->prec != BIP_PREC_MIXED || !c->recon_tc))
         return fail(c, BIP_ERR_UNSUPPORTED, "the probe order needs the mixed precision and at most 64 parents per side");
     if (probe && P > kProbeMaxScans) return fail(c, BIP_ERR_UNSUPPORTED, "the probe order takes at most 2048 scans");
+    if (c->uneven && (cube_out || beam || probe))
+        return fail(c, BIP_ERR_UNSUPPORTED, "sites with windows of their own: the map in the Gram order only");
     if (cube_out || beam || probe) {
         // c_b(rho) for every scan
         CUDA_TRY(c, ensure(c->illum, (size_t)Bpad * P * sizeof(float2), false, s));
@@ -1389,6 +1481,9 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
 
     const int SB = c->sb_override > 0 ? std::min(c->n_sites, c->sb_override)
                                       : (tc ? tc_batch(c) : std::min(c->n_sites, 8));
+    const std::vector<std::pair<int, int>> batches = map_batches(c, SB);
+    // workspaces for the context's window (the largest); a batch of smaller
+    // windows uses the front of each
     const size_t rowsA = Dpad, rowsB = (size_t)nch * Bpad;
     const size_t perA = rowsA * K, perB = rowsB * K;
     const size_t perMt = (size_t)Bpad * nch * Dpad, perQ = (size_t)Bpad * Bpad;
@@ -1438,10 +1533,10 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     if (!same_work) {
     work.clear();
     batch_off.clear();
-    for (int b0 = 0; b0 < c->n_sites; b0 += SB) {
+    for (const auto& bt : batches) {
         batch_off.push_back((int)work.size() / 2);
-        for (int bs = 0; bs < std::min(SB, c->n_sites - b0); ++bs) {
-            const SiteDev& sd = c->sites[b0 + bs];
+        for (int bs = 0; bs < bt.second; ++bs) {
+            const SiteDev& sd = c->sites[c->batch_order[bt.first + bs]];
             for (int t = 0; t < n_tiles; ++t)
                 if (box_meets_crop(bb[4 * t], bb[4 * t + 1], bb[4 * t + 2], bb[4 * t + 3], sd.ty, sd.tx, g)) {
                     work.push_back(bs);
@@ -1559,14 +1654,23 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
                            false, s));
     }
 
-    int bi = 0;
-    for (int b0 = 0; b0 < c->n_sites; b0 += SB, ++bi) {
-        const int nb = std::min(SB, c->n_sites - b0);
+    for (int bi = 0; bi < (int)batches.size(); ++bi) {
+        const int b0 = batches[bi].first, nb = batches[bi].second;
         const int32_t* ids = (const int32_t*)c->seq_ids_d.p + b0;
+        // the batch's window: its contractions run over K = w^2 pixels, the
+        // operands packed at that row length (these shadow the context-wide
+        // sizes the workspaces were allocated for)
+        const int wb = c->sites[c->batch_order[b0]].w;
+        const int K = wb * wb;
+        const size_t perA = rowsA * K, perB = rowsB * K;
+        {
+            bip_status st = operand_layout(c, K, s);
+            if (st != BIP_OK) return st;
+        }
         // S2 windows -> coupling A operand, S1 windows x H_n -> B operand
-        GatherArgs g2 = gather_args(c, 2, ids, nb);
+        GatherArgs g2 = gather_args(c, 2, ids, nb, wb);
         g2.rows_pad = Dpad;
-        GatherArgs g1 = gather_args(c, 1, ids, nb);
+        GatherArgs g1 = gather_args(c, 1, ids, nb, wb);
         g1.rows_pad = Bpad;
         g1.nch = nch;
         g1.H = (const float2*)H;
@@ -1677,10 +1781,10 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             continue;
         }
         if (f8) {
-            bip_status st = recon_tc_batch(c, ids, nb, H, c->op8A.p, c->op8B.p, s);
+            bip_status st = recon_tc_batch(c, ids, nb, H, c->op8A.p, c->op8B.p, s, false, true, wb);
             if (st != BIP_OK) return st;
         } else if (c->prec == BIP_PREC_MIXED && c->recon_tc) {
-            bip_status st = recon_tc_batch(c, ids, nb, H, c->opA16.p, c->opB16.p, s);
+            bip_status st = recon_tc_batch(c, ids, nb, H, c->opA16.p, c->opB16.p, s, false, true, wb);
             if (st != BIP_OK) return st;
         } else {
             TIMED(c, BIP_STAGE_GATHER, s, bip_gather(g2, s));
@@ -2183,6 +2287,7 @@ bip_status bip_coreloss_cube(bip_ctx* c, const float* V, const void* H, const do
     if (!c) return BIP_ERR_INVALID_ARG;
     if (!c->s1 || site_signature(c->sites) != c->sig1)
         return fail(c, BIP_ERR_INVALID_ARG, "bip_build_s1 must run first (the cube's sites are its sites)");
+    if (c->uneven) return fail(c, BIP_ERR_UNSUPPORTED, "the cube takes every site at the context's window");
     if (!V || !H || !scan_px || !cube_out) return fail(c, BIP_ERR_INVALID_ARG, "null pointer argument");
     if ((reinterpret_cast<uintptr_t>(H) & 15) != 0) return fail(c, BIP_ERR_INVALID_ARG, "H must be 16-byte aligned");
     if (P < 1) return fail(c, BIP_ERR_INVALID_ARG, "P must be >= 1");
@@ -2251,6 +2356,7 @@ bip_status bip_coreloss_qeels(bip_ctx* c, const void* H, const double* scan_px, 
                               float* qeels_out, void* stream) {
     bip_status st = check_map_args(c, H, scan_px, P, qeels_out);
     if (st != BIP_OK) return st;
+    if (c->uneven) return fail(c, BIP_ERR_UNSUPPORTED, "qEELS takes every site at the context's window");
     std::vector<int32_t> bins, bin_of;
     if (!qeels_bins(c, axis, bins, bin_of)) return fail(c, BIP_ERR_INVALID_ARG, "axis must be 0 (q_y) or 1 (q_x)");
     if ((axis == 0 ? c->geo.dfy : c->geo.dfx) != 1)
@@ -2378,7 +2484,7 @@ bip_status bip_autotune(bip_ctx* c, const void* H, const double* scan_px, int32_
     // the windowed probes (mixed precision, up to kProbeMaxScans scans)
     const int order0 = c->order;
     int best_order = order0;
-    if (st == BIP_OK && tc) {
+    if (st == BIP_OK && tc && !c->uneven) {   // (sites with windows of their own: the Gram order only)
         const bool probe_ok = c->prec == BIP_PREC_MIXED && c->recon_tc && P <= kProbeMaxScans;
         for (int o : {0, 1, 2}) {
             if (o == order0 || (o == 2 && !probe_ok)) continue;
@@ -2447,6 +2553,25 @@ bip_status bip_set_occupancy(bip_ctx* c, const double* occ) {
     return BIP_OK;
 }
 
+bip_status bip_set_site_windows(bip_ctx* c, const int32_t* win, void* stream) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (c->n_sites < 1) return fail(c, BIP_ERR_INVALID_ARG, "no sites: build the matrices first");
+    std::vector<int32_t> w;
+    if (win) {
+        w.assign(win, win + c->n_sites);
+        int64_t h = 0;
+        for (int k = 0; k < c->n_sites; ++k) {
+            if (w[k] == 0) w[k] = c->cfg.win;
+            if (w[k] < 16 || w[k] % 16 || w[k] > c->cfg.win)
+                return fail(c, BIP_ERR_INVALID_ARG, "a site window must be a multiple of 16 in [16, win] (or 0)");
+            h += (int64_t)c->sites[k].nch * w[k] * w[k];
+        }
+        if (h > INT32_MAX) return fail(c, BIP_ERR_INVALID_ARG, "H would exceed 2^31 complex elements");
+    }
+    c->site_w = w;
+    return apply_windows(c, (cudaStream_t)stream);
+}
+
 bip_status bip_set_aberrations(bip_ctx* c, double defocus, double cs, void* stream) {
     if (!c) return BIP_ERR_INVALID_ARG;
     if (!std::isfinite(defocus) || !std::isfinite(cs)) return fail(c, BIP_ERR_INVALID_ARG, "aberration not finite");
@@ -2462,6 +2587,7 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
                              void* stream) {
     bip_status st = check_map_args(c, H, scan_px, P, dL_dI);
     if (st != BIP_OK) return st;
+    if (c->uneven) return fail(c, BIP_ERR_UNSUPPORTED, "the reverse pass takes every site at the context's window");
     if (d_V && !V) return fail(c, BIP_ERR_INVALID_ARG, "d_V needs the V the matrices were built from");
     if (d_V && (!pow2_in(c->cfg.ny, 64, 1024) || !pow2_in(c->cfg.nx, 64, 1024)))
         return fail(c, BIP_ERR_UNSUPPORTED, "dL/dV (the adjoint sweeps) needs power-of-two grid lengths");
@@ -2522,6 +2648,8 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
     }
     CUDA_TRY(c, ensure(c->opA32, SB * perA * sizeof(float2), true, s));
     CUDA_TRY(c, ensure(c->opB32, SB * perB * sizeof(float2), true, s));
+    st = operand_layout(c, K, s);
+    if (st != BIP_OK) return st;
     CUDA_TRY(c, ensure(c->g_s1, SB * perS1 * sizeof(float2), true, s));
     CUDA_TRY(c, ensure(c->mt32, SB * perMt * sizeof(float2), true, s));
     CUDA_TRY(c, ensure(c->q32, SB * perQ * sizeof(float2), true, s));
@@ -2799,6 +2927,7 @@ bip_status bip_site_windows(bip_ctx* c, int32_t site, void* s1_out, void* s2_out
     if (!c->s1 || !c->s2 || c->sig1 != c->sig2)
         return fail(c, BIP_ERR_INVALID_ARG, "bip_build_s1 and bip_build_s2 must run first on the same sites");
     if (site < 0 || site >= c->n_sites) return fail(c, BIP_ERR_INVALID_ARG, "site out of range");
+    if (c->uneven) return fail(c, BIP_ERR_UNSUPPORTED, "site windows are given at the context's window only");
     if (((reinterpret_cast<uintptr_t>(s1_out) | reinterpret_cast<uintptr_t>(s2_out)) & 15) != 0)
         return fail(c, BIP_ERR_INVALID_ARG, "window outputs must be 16-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
@@ -2852,6 +2981,7 @@ bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_ou
     if (!H || !m_out) return fail(c, BIP_ERR_INVALID_ARG, "null pointer argument");
     if ((reinterpret_cast<uintptr_t>(H) & 15) != 0) return fail(c, BIP_ERR_INVALID_ARG, "H must be 16-byte aligned");
     if (site < 0 || site >= c->n_sites) return fail(c, BIP_ERR_INVALID_ARG, "site out of range");
+    if (c->uneven) return fail(c, BIP_ERR_UNSUPPORTED, "the site coupling is given at the context's window only");
     cudaStream_t s = (cudaStream_t)stream;
     const bip_config& g = c->cfg;
     const BipGeometry& geo = c->geo;

@@ -46,11 +46,13 @@ void bip_sibson_weights(const std::vector<int32_t>& parents, const std::vector<i
 // device-side tables shared by several kernels
 
 struct SiteDev {            // one ionized site, as the kernels see it
-    int32_t oy, ox;         // window origin (unwrapped pixel index)
+    int32_t oy, ox;         // origin of its stashed window (the context's win; unwrapped pixel index)
     int32_t plane;          // slice index
     int32_t nch;            // channels
     int32_t ch_off;         // first channel in H
-    int32_t pad_;
+    int32_t h_off;          // first element of its channels in H (channels of w x w each)
+    int32_t w;              // its own window (<= win, a multiple of 16): the central
+    int32_t wo;             // w x w block of the stashed window, at offset wo = (win - w) / 2
     double ty, tx;          // position in pixels
 };
 
@@ -110,21 +112,23 @@ struct GatherArgs {
     int n_sites;                    // sites in this batch
     const int32_t* site_ids;        // [n_sites] global site index
     const SiteDev* sites;           // all sites
-    int win, ny, nx;
+    int win, ny, nx;                // win: the batch's window (K = win^2 pixels)
+    int stash_win, wo;              // stashed windows (and the tables' rows) of stash_win pixels;
+                                    // the batch's window starts wo pixels in on both axes
     int Bp, n_targets, rows_pad;    // parents, targets, padded rows
-    const float2* stash;            // [n_sites_total, Bp, win, win]
+    const float2* stash;            // [n_sites_total, Bp, stash_win, stash_win]
     GroupDev grp;                   // weights of the targets
     const int2* h_t;                // [n_targets] target beams (y, x)
     int tilt_sign;                  // +1 (S1) or -1 (S2)
     int magnitude;                  // 1: magnitude-preserving
     const float2* ey;               // [ny] exp(+2 pi i m / ny)
     const float2* ex;               // [nx]
-    const float2* ytab;             // [ny][win] exp(+2 pi i h u / ny), row h mod ny
-    const float2* xtab;             // [nx][win] exp(+2 pi i h v / nx), row h mod nx
+    const float2* ytab;             // [ny][stash_win] exp(+2 pi i h u / ny), row h mod ny
+    const float2* xtab;             // [nx][stash_win] exp(+2 pi i h v / nx), row h mod nx
     int fx;                         // lattice step of the targets along x
     // channel expansion (S1 side): out row (n * rows_pad + t) = H_n * S
     int nch;                        // 0: no channel product (S2 side)
-    const float2* H;                // [sum nch, win, win]
+    const float2* H;                // site channels from SiteDev::h_off, win x win each
     // outputs (one of the two layouts)
     float2* out_c64;                // [n_sites][rows_total][K] complex64
     uint16_t* out_bf16;             // [n_sites][planes][rows_total][K]: 4 planes (re_hi, re_lo,
@@ -139,14 +143,15 @@ cudaError_t bip_gather(const GatherArgs& a, cudaStream_t s);
 // X [site-plane rows][K px][64 parents] bf16: row (x_site0 + 3 bs + plane) K
 // + px, planes re, im, magnitude of the de-tilted stash.
 struct XprepSide {
-    const float2* stash;            // [n_sites_total][Bp][K]
+    const float2* stash;            // [n_sites_total][Bp][stash_win^2]
     int Bp;                         // parents (<= 64)
     int x_site0;                    // first site-plane row block of this side
 };
 struct XprepArgs {
     int n_sites;                    // sites in this batch
     const int32_t* site_ids;        // [n_sites]
-    int K;                          // window pixels
+    int K;                          // window pixels (w^2)
+    int w, stash_win, wo;           // the batch's window inside the stashed ones
     uint16_t* X;
     XprepSide side[2];              // 0: S2 (detector), 1: S1 (aperture)
     // FP8 path: largest |dt_p(r)| over the window of each parent, as float
@@ -176,14 +181,15 @@ struct ReconArgs {
     int n_sites;
     const int32_t* site_ids;
     const SiteDev* sites;
-    int K, win, ny, nx;
+    int K, win, ny, nx;             // win: the batch's window, K = win^2
+    int stash_win, wo;              // the tables' row length; offset of the batch's window
     int chunk_px, chunks;           // pixels per work unit, units per target tile
     int magnitude;
     const float2* ey;               // [ny] exp(+2 pi i m / ny)
     const float2* ex;               // [nx]
-    const float2* ytab;             // [ny][win]
-    const float2* xtab;             // [nx][win]
-    const float2* H;                // [sum nch][K], 16-byte aligned
+    const float2* ytab;             // [ny][stash_win]
+    const float2* xtab;             // [nx][stash_win]
+    const float2* H;                // site channels from SiteDev::h_off, K each; 16-byte aligned
     const uint16_t* W;              // [w_rows][64] bf16: per side hi then lo planes
     int w_rows;
     const uint16_t* Xb;             // X of XprepArgs
@@ -207,10 +213,9 @@ cudaError_t bip_recon_tc(const ReconArgs& a, cudaStream_t s);
 struct F8HmaxArgs {
     int n_sites;                    // all sites of the context
     const SiteDev* sites;
-    int K;
-    const float2* H;                // [sum nch][K]
+    const float2* H;                // site channels from SiteDev::h_off, w^2 each
     float* hmax;                    // [n_sites][9]: max_r |H_n(r)| (0 past the site's channels)
-    float2* Hs;                     // [sum nch][K]: H_n / max_r |H_n| (0 where the max is 0)
+    float2* Hs;                     // H's layout: H_n / max_r |H_n| (0 where the max is 0)
 };
 cudaError_t bip_f8_hmax(const F8HmaxArgs& a, cudaStream_t s);
 struct F8ScaleArgs {

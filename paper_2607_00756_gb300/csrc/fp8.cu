@@ -29,11 +29,12 @@ __global__ void __launch_bounds__(kThreads) f8_hmax_kernel(F8HmaxArgs a) {
     __shared__ float red[kThreads / 32];
     const int site = blockIdx.x;
     const SiteDev st = a.sites[site];
+    const int K = st.w * st.w;                 // the site's window
     for (int n = 0; n < 9; ++n) {
         float m = 0.f;
         if (n < st.nch) {
-            const float2* h = a.H + (size_t)(st.ch_off + n) * a.K;
-            for (int i = threadIdx.x; i < a.K; i += kThreads) {
+            const float2* h = a.H + (size_t)st.h_off + (size_t)n * K;
+            for (int i = threadIdx.x; i < K; i += kThreads) {
                 const float2 v = __ldg(&h[i]);
                 m = fmaxf(m, fmaf(v.x, v.x, v.y * v.y));
             }
@@ -49,9 +50,9 @@ __global__ void __launch_bounds__(kThreads) f8_hmax_kernel(F8HmaxArgs a) {
         // H_n / max|H_n| for the E4M3 rows (the reconstruction multiplies by it)
         if (n < st.nch) {
             const float inv = hm > 0.f ? 1.f / hm : 0.f;
-            const float2* h = a.H + (size_t)(st.ch_off + n) * a.K;
-            float2* o = a.Hs + (size_t)(st.ch_off + n) * a.K;
-            for (int i = threadIdx.x; i < a.K; i += kThreads) {
+            const float2* h = a.H + (size_t)st.h_off + (size_t)n * K;
+            float2* o = a.Hs + (size_t)st.h_off + (size_t)n * K;
+            for (int i = threadIdx.x; i < K; i += kThreads) {
                 const float2 v = __ldg(&h[i]);
                 o[i] = make_float2(v.x * inv, v.y * inv);
             }
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) f8_scale_kernel(F8ScaleArgs a) {
 }  // namespace
 
 cudaError_t bip_f8_hmax(const F8HmaxArgs& a, cudaStream_t s) {
-    if (a.n_sites < 1 || a.K < 1) return cudaErrorInvalidValue;
+    if (a.n_sites < 1) return cudaErrorInvalidValue;
     f8_hmax_kernel<<<a.n_sites, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }

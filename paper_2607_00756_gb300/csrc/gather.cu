@@ -65,11 +65,16 @@ __global__ void __launch_bounds__(kThreads, 3) gather_kernel(GatherArgs a) {
     const int site = a.site_ids[bs];
     const SiteDev st = a.sites[site];
     const int r0 = blockIdx.x * kPix;
-    const int K2 = a.K / 2;                    // pixel pairs per window
-    const float4* src = reinterpret_cast<const float4*>(a.stash + (size_t)site * Bp * a.K) + r0 / 2;
+    // the batch's window is the central win x win block of the stashed
+    // stash_win x stash_win windows; a lane's two pixels are adjacent in both
+    // (win, stash_win and wo even)
+    const int SK = a.stash_win * a.stash_win;
+    const float2* src = a.stash + (size_t)site * Bp * SK;
     for (int i = threadIdx.x; i < Bp * 32; i += kThreads) {
         const int p = i >> 5, l = i & 31;
-        const float4 v = __ldg(src + (size_t)p * K2 + l);
+        const int rl = r0 + 2 * l, ul = rl / a.win;
+        const int idx = (ul + a.wo) * a.stash_win + (rl - ul * a.win) + a.wo;
+        const float4 v = __ldg(reinterpret_cast<const float4*>(src + (size_t)p * SK + idx));
         sv[i] = v;
         sm[i] = make_float2(sqrtf(v.x * v.x + v.y * v.y), sqrtf(v.z * v.z + v.w * v.w));
     }
@@ -80,7 +85,7 @@ __global__ void __launch_bounds__(kThreads, 3) gather_kernel(GatherArgs a) {
     if (MAXCH > 3) {
         for (int i = threadIdx.x; i < MAXCH * 32; i += kThreads) {
             const int n = i >> 5, l = i & 31;
-            hs[i] = n < nuse ? __ldg(H4 + (size_t)(st.ch_off + n) * K2 + r0 / 2 + l) : make_float4(0.f, 0.f, 0.f, 0.f);
+            hs[i] = n < nuse ? __ldg(H4 + ((size_t)st.h_off + (size_t)n * a.K + r0) / 2 + l) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
     __syncthreads();
@@ -89,7 +94,7 @@ __global__ void __launch_bounds__(kThreads, 3) gather_kernel(GatherArgs a) {
     if (MAXCH <= 3) {
 #pragma unroll
         for (int n = 0; n < HR; ++n)
-            hr[n] = n < nuse ? __ldg(H4 + (size_t)(st.ch_off + n) * K2 + r0 / 2 + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+            hr[n] = n < nuse ? __ldg(H4 + ((size_t)st.h_off + (size_t)n * a.K + r0) / 2 + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const int rr = r0 + 2 * lane;              // the lane's first window pixel
     const int u = rr / a.win, v = rr - u * a.win;   // window row, column (v even)
@@ -98,8 +103,9 @@ __global__ void __launch_bounds__(kThreads, 3) gather_kernel(GatherArgs a) {
     const int gb = blockIdx.y * (kWarps * kGroupsPerWarp);
     const int ge = min(gb + kWarps * kGroupsPerWarp, a.grp.n_groups);
 
-    float2 stp0 = __ldg(&a.ex[wrap_n(a.fx * (st.ox + v), a.nx)]);
-    float2 stp1 = __ldg(&a.ex[wrap_n(a.fx * (st.ox + v + 1), a.nx)]);
+    const int oy = st.oy + a.wo, ox = st.ox + a.wo;   // origin of the batch's window
+    float2 stp0 = __ldg(&a.ex[wrap_n(a.fx * (ox + v), a.nx)]);
+    float2 stp1 = __ldg(&a.ex[wrap_n(a.fx * (ox + v + 1), a.nx)]);
     if (a.tilt_sign < 0) {
         stp0.y = -stp0.y;
         stp1.y = -stp1.y;
@@ -138,11 +144,11 @@ __global__ void __launch_bounds__(kThreads, 3) gather_kernel(GatherArgs a) {
                     t0 = c_mul(t0, stp0);
                     t1 = c_mul(t1, stp1);
                 } else {
-                    const float2 base = c_mul(__ldg(&a.ey[wrap_n(h.x * st.oy, a.ny)]),
-                                              __ldg(&a.ex[wrap_n(h.y * st.ox, a.nx)]));
-                    const float2 ty = __ldg(&a.ytab[(size_t)(wrap_n(h.x, a.ny)) * a.win + u]);
-                    const float4 tx =
-                        __ldg(reinterpret_cast<const float4*>(a.xtab + (size_t)(wrap_n(h.y, a.nx)) * a.win + v));
+                    const float2 base = c_mul(__ldg(&a.ey[wrap_n(h.x * oy, a.ny)]),
+                                              __ldg(&a.ex[wrap_n(h.y * ox, a.nx)]));
+                    const float2 ty = __ldg(&a.ytab[(size_t)(wrap_n(h.x, a.ny)) * a.stash_win + u]);
+                    const float4 tx = __ldg(
+                        reinterpret_cast<const float4*>(a.xtab + (size_t)(wrap_n(h.y, a.nx)) * a.stash_win + v));
                     const float2 by = c_mul(base, ty);
                     t0 = c_mul(by, make_float2(tx.x, tx.y));
                     t1 = c_mul(by, make_float2(tx.z, tx.w));
@@ -205,6 +211,8 @@ cudaError_t launch(const GatherArgs& a, cudaStream_t s) {
 
 cudaError_t bip_gather(const GatherArgs& a, cudaStream_t s) {
     if (a.K % kPix != 0 || a.win % 2 != 0 || a.nch > 9 || a.n_targets > a.grp.n_groups * kG) return cudaErrorInvalidValue;
+    if (a.K != a.win * a.win || a.stash_win % 2 || a.wo % 2 || a.wo < 0 || a.win + 2 * a.wo != a.stash_win)
+        return cudaErrorInvalidValue;
     if (a.nch > 0 && (reinterpret_cast<uintptr_t>(a.H) & 15) != 0) return cudaErrorMisalignedAddress;
     if (a.n_sites == 0 || a.grp.n_groups == 0) return cudaSuccess;
     // channel count: 1 stands for the S2 side (no channel product)

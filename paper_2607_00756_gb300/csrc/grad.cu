@@ -133,7 +133,7 @@ __global__ void hgrad_kernel(GradArgs a, const int32_t* ids, const float2* S1, i
         acc.x = fmaf(x.x, y.x, fmaf(-x.y, y.y, acc.x));
         acc.y = fmaf(x.x, y.y, fmaf(x.y, y.x, acc.y));
     }
-    dH[(size_t)(st.ch_off + n) * a.K + r] = make_float2(2.f * acc.x, 2.f * acc.y);
+    dH[(size_t)st.h_off + (size_t)n * a.K + r] = make_float2(2.f * acc.x, 2.f * acc.y);
 }
 
 // D[bs][b] = sum_b' Q[b][b'] R[b'][b]

@@ -34,7 +34,7 @@ __global__ void probe_y_kernel(ProbeYArgs a) {
     const float4* ps = reinterpret_cast<const float4*>(a.psi + ((int64_t)bs * a.psi_rows + rho) * a.K + r0);
     uint32_t re[4], im[4];
     if (n < st.nch) {
-        const float4* hp = reinterpret_cast<const float4*>(a.H + (int64_t)(st.ch_off + n) * a.K + r0);
+        const float4* hp = reinterpret_cast<const float4*>(a.H + (int64_t)st.h_off + (int64_t)n * a.K + r0);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const float4 p = __ldg(&ps[j]), h = __ldg(&hp[j]);

@@ -314,10 +314,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int px0 = u.pc * a.chunk_px + c0;
                 const int wu = px0 / a.win;
                 wv = px0 - wu * a.win;
-                const float2 base =
-                    c_mul(__ldg(&a.ey[wrap_n(h.x * st.oy, a.ny)]), __ldg(&a.ex[wrap_n(h.y * st.ox, a.nx)]));
-                F = c_mul(base, c_mul(__ldg(&a.ytab[(size_t)(wrap_n(h.x, a.ny)) * a.win + wu]),
-                                      __ldg(&a.xtab[(size_t)(wrap_n(h.y, a.nx)) * a.win + wv])));
+                // origin of the batch's window: wo pixels into the stashed one
+                const float2 base = c_mul(__ldg(&a.ey[wrap_n(h.x * (st.oy + a.wo), a.ny)]),
+                                          __ldg(&a.ex[wrap_n(h.y * (st.ox + a.wo), a.nx)]));
+                F = c_mul(base, c_mul(__ldg(&a.ytab[(size_t)(wrap_n(h.x, a.ny)) * a.stash_win + wu]),
+                                      __ldg(&a.xtab[(size_t)(wrap_n(h.y, a.nx)) * a.stash_win + wv])));
                 sx1 = __ldg(&a.ex[wrap_n(h.y, a.nx)]);
                 sx4 = __ldg(&a.ex[wrap_n(4 * h.y, a.nx)]);
                 sx8 = __ldg(&a.ex[wrap_n(8 * h.y, a.nx)]);
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             float ir = 1.f;                                    // F8: 448 / bound of this row
             if (F8 && valid) ir = __ldg(&a.inv_row[u.side][(size_t)u.bs * sd.rows_pad + t]);
             const size_t ch_stride = (size_t)sd.rows_pad * a.K;
-            const float2* Hs = a.H + (size_t)st.ch_off * a.K;
+            const float2* Hs = a.H + (size_t)st.h_off;
             const int nh = sd.nch * 16;                       // H_n values of a warp per tile
             for (int tt = 0; tt < tiles; ++tt) {
                 const int px = u.pc * a.chunk_px + tt * kN + c0;     // this warp's 16 pixels
@@ -490,8 +491,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// stash [Bp][K] complex64 of one site -> X planes [3][K][64] fp16 (re, im,
-// magnitude; parents past Bp zero).  Block: 64 pixels of one site and side.
+// stash [Bp][stash_win^2] complex64 of one site -> X planes [3][K][64] fp16
+// (re, im, magnitude; parents past Bp zero) of the batch's w x w window, the
+// central block at offset wo of the stashed one.  Block: 64 pixels of one
+// site and side.
 constexpr int kPrepThreads = 256;
 __global__ void __launch_bounds__(kPrepThreads) xprep_kernel(XprepArgs a) {
     __shared__ float2 s[64][65];
@@ -500,14 +503,19 @@ __global__ void __launch_bounds__(kPrepThreads) xprep_kernel(XprepArgs a) {
     const int bs = blockIdx.y;
     const int site = a.site_ids[bs];
     const int px0 = blockIdx.x * 64;
-    const float2* src = sd.stash + (size_t)site * sd.Bp * a.K + px0;
+    const int SK = a.stash_win * a.stash_win;
+    const float2* src = sd.stash + (size_t)site * sd.Bp * SK;
+    // stash index of this thread's pixel px0 + (threadIdx.x & 63) (the same
+    // for its 16 loads: i & 63 does not change with r)
+    const int pix = px0 + (threadIdx.x & 63), pu = pix / a.w;
+    const int sidx = (pu + a.wo) * a.stash_win + (pix - pu * a.w) + a.wo;
     // (FP8 path: the parents' window maxima are taken from the same tile)
     // 16 loads per thread in flight at once (parents p = i / 64, pixels i % 64)
     float2 v[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         const int i = threadIdx.x + r * kPrepThreads, p = i >> 6;
-        v[r] = p < sd.Bp ? __ldg(&src[(size_t)p * a.K + (i & 63)]) : make_float2(0.f, 0.f);
+        v[r] = p < sd.Bp ? __ldg(&src[(size_t)p * SK + sidx]) : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
@@ -561,12 +569,14 @@ __global__ void __launch_bounds__(kPrepThreads) xprep_kernel(XprepArgs a) {
 cudaError_t bip_xprep(const XprepArgs& a, cudaStream_t s) {
     if (a.K % 64 || a.n_sites < 1) return cudaErrorInvalidValue;
     if (a.side[0].Bp > 64 || a.side[1].Bp > 64) return cudaErrorInvalidValue;
+    if (a.K != a.w * a.w || a.wo < 0 || a.w + 2 * a.wo != a.stash_win) return cudaErrorInvalidValue;
     xprep_kernel<<<dim3(a.K / 64, a.n_sites, 2), kPrepThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t bip_recon_tc(const ReconArgs& a, cudaStream_t s) {
     if (a.K % kN || a.chunk_px % kN || a.K % a.chunk_px || a.chunk_px > kChunk || a.win % 16) return cudaErrorInvalidValue;
+    if (a.K != a.win * a.win || a.wo < 0 || a.win + 2 * a.wo != a.stash_win) return cudaErrorInvalidValue;
     if (a.n_sites < 1 || a.chunks != a.K / a.chunk_px) return cudaErrorInvalidValue;
     for (int i = 0; i < 2; ++i) {
         const ReconSide& sd = a.side[i];

@@ -9,9 +9,9 @@ crystals stand in for them with the same shape regime.
 """
 from .prng import SplitMix64
 from .configs import Config, config1, config2, config3, config5, tiny_config, CONFIGS
-from .specimen import Specimen, make_specimen, window_origin
+from .specimen import Specimen, make_specimen, window_origin, site_window_inputs
 
 __all__ = [
     "SplitMix64", "Config", "config1", "config2", "config3", "config5", "tiny_config",
-    "CONFIGS", "Specimen", "make_specimen", "window_origin",
+    "CONFIGS", "Specimen", "make_specimen", "window_origin", "site_window_inputs",
 ]

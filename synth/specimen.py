@@ -127,3 +127,26 @@ def make_specimen(cfg: Config, with_potential: bool = True) -> Specimen:
     H = _transition(cfg, atoms, nch)
     scans = scan_raster(cfg.scan_y, cfg.scan_x)
     return Specimen(cfg=cfg, atoms=atoms, nch=nch, V=V, H=H, scans=scans)
+
+
+def site_window_inputs(sp: Specimen, site_win):
+    """Transition potentials of the ionized sites on windows of their own:
+    site k keeps the central w_k x w_k block of its samples (the same sample
+    points: window_origin(t, w_k) is (win - w_k) / 2 past window_origin(t,
+    win)).  Returns (per-site arrays [nch_k, w_k, w_k], their flat
+    concatenation in site order, and H on the full windows with zeros
+    outside each site's block)."""
+    win = sp.cfg.win
+    nch = sp.nch[sp.nch > 0]
+    site_win = np.asarray(site_win, dtype=np.int64)
+    if site_win.shape != nch.shape:
+        raise ValueError("one window per ionized site")
+    off = np.concatenate([[0], np.cumsum(nch)])
+    parts, padded = [], np.zeros_like(sp.H)
+    for k, w in enumerate(site_win.tolist()):
+        o = (win - w) // 2
+        h = sp.H[off[k]:off[k + 1], o:o + w, o:o + w]
+        parts.append(h.copy())
+        padded[off[k]:off[k + 1], o:o + w, o:o + w] = h
+    flat = np.concatenate([p.reshape(-1) for p in parts]) if parts else np.zeros(0, dtype=sp.H.dtype)
+    return parts, flat, padded

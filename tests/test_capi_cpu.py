@@ -150,6 +150,11 @@ def test_model_and_launch_controls_host(capi):
         assert lib.bip_set_occupancy(ctx, occ) == 1
         assert "build" in capi.bip_last_error(ctx)
         assert lib.bip_set_occupancy(ctx, None) == 0
+        # per-site windows need built sites too
+        w = (ctypes.c_int32 * 4)(32, 64, 16, 48)
+        assert lib.bip_set_site_windows(ctx, w, None) == 1
+        assert "build" in capi.bip_last_error(ctx)
+        assert lib.bip_set_site_windows(None, w, None) == 1
         # aberrations: finite values only
         assert lib.bip_set_aberrations(ctx, D(float("nan")), D(0.0), None) == 1
         assert lib.bip_set_aberrations(ctx, D(25.0), D(1.0e5), None) == 0

@@ -1,0 +1,149 @@
+"""Sites with windows of their own (Eq. coupling summed over each site's
+crop window Omega_tau, the window following the support of its H_n: sites
+of several edges batched in one map).  Maps of config 1 and of a 12-site
+mix with windows from 16 to 64 pixels against the FP64 oracle in every
+precision; the same map as the context's windows with H zero outside each
+site's block; the windows cleared again giving the uniform map back bit
+for bit; and the paths that take only the context's window refusing."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import bip as obip
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = {"fp32": 1e-4, "split_bf16": 1e-4, "mixed": 1e-3, "fp8": 3e-2}
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2607_00756_gb300 import build
+    build.build()
+    from paper_2607_00756_gb300.context import BipContext
+    return BipContext
+
+
+def case(kind):
+    """(config, specimen, per-site windows): config 1's four sites, or
+    twelve sites on three slices with windows 64, 48, 32, 16 in turn."""
+    if kind == "config1":
+        cfg = synth.config1()
+        sp = synth.make_specimen(cfg)
+        return cfg, sp, [32, 64, 16, 48]
+    cfg = synth.config1().replace(name="mix", ion_slices=(1, 4), seed=5)
+    sp = synth.make_specimen(cfg)
+    n = int((sp.nch > 0).sum())
+    return cfg, sp, [(64, 48, 32, 16)[k % 4] for k in range(n)]
+
+
+_refs = {}
+
+
+def oracle_own(kind):
+    if kind not in _refs:
+        cfg, sp, w = case(kind)
+        parts, _, _ = synth.site_window_inputs(sp, w)
+        _refs[kind] = obip.bip_map(obip.make_problem(sp, site_win=w, H=parts))
+    return _refs[kind]
+
+
+def built(lib, cfg, sp, prec):
+    dev = torch.device("cuda:0")
+    ctx = lib(cfg, prec=prec)
+    ctx.build(torch.tensor(sp.V, dtype=torch.float32, device=dev), sp.atoms, sp.nch)
+    return ctx
+
+
+@pytest.mark.parametrize("kind", ["config1", "mix"])
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16", "mixed", "fp8"])
+def test_own_windows_map(lib, kind, prec):
+    cfg, sp, w = case(kind)
+    ref = oracle_own(kind)
+    _, flat, _ = synth.site_window_inputs(sp, w)
+    ctx = built(lib, cfg, sp, prec)
+    ctx.set_site_windows(w)
+    H = torch.tensor(flat, dtype=torch.complex64, device="cuda:0")
+    m = ctx.map(H, sp.scans).cpu().numpy()
+    assert rel(m, ref.map) < TOL[prec]
+    parts = ctx.sites(H, sp.scans).cpu().numpy()
+    assert rel(parts, ref.partials) < TOL[prec]
+    # smaller batches (never across a window size) give the same map
+    ctx.set_launch(2, 0)
+    m2 = ctx.map(H, sp.scans).cpu().numpy()
+    assert rel(m2, m) < (1e-6 if prec in ("fp32", "split_bf16") else TOL[prec])
+    # a second map is bit-identical (fixed order, no atomics)
+    assert np.array_equal(ctx.map(H, sp.scans).cpu().numpy(), m2)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_own_windows_equal_zero_padded_context_windows(lib, prec):
+    """Own windows against the context's windows with H_n zero outside each
+    site's block (the same sum, Eq. coupling), then the windows cleared."""
+    cfg, sp, w = case("mix")
+    _, flat, padded = synth.site_window_inputs(sp, w)
+    dev = torch.device("cuda:0")
+    ctx = built(lib, cfg, sp, prec)
+    H_full = torch.tensor(sp.H, dtype=torch.complex64, device=dev)
+    m_full = ctx.map(H_full, sp.scans).cpu().numpy()
+    m_pad = ctx.map(torch.tensor(padded, dtype=torch.complex64, device=dev), sp.scans).cpu().numpy()
+    ctx.set_site_windows(w)
+    m_own = ctx.map(torch.tensor(flat, dtype=torch.complex64, device=dev), sp.scans).cpu().numpy()
+    assert rel(m_own, m_pad) < (1e-5 if prec == "fp32" else 1e-3)
+    assert rel(m_own, m_full) > 1e-4          # the windows do change the map
+    ctx.set_site_windows(None)
+    assert np.array_equal(ctx.map(H_full, sp.scans).cpu().numpy(), m_full)
+    # windows equal to the context's are the uniform case
+    ctx.set_site_windows([cfg.win] * len(w))
+    assert np.array_equal(ctx.map(H_full, sp.scans).cpu().numpy(), m_full)
+    ctx.close()
+
+
+def test_own_windows_autotune_keeps_the_gram_order(lib):
+    cfg, sp, w = case("mix")
+    _, flat, _ = synth.site_window_inputs(sp, w)
+    ctx = built(lib, cfg, sp, "mixed")
+    ctx.set_site_windows(w)
+    H = torch.tensor(flat, dtype=torch.complex64, device="cuda:0")
+    m0 = ctx.map(H, sp.scans).cpu().numpy()
+    sb, cw, order, ms = ctx.autotune(H, sp.scans)
+    assert order == 0 and ms > 0.0
+    assert rel(ctx.map(H, sp.scans).cpu().numpy(), m0) < 1e-6
+    ctx.close()
+
+
+def test_own_windows_refusals(lib):
+    from paper_2607_00756_gb300.capi import BipError
+    cfg, sp, w = case("config1")
+    _, flat, _ = synth.site_window_inputs(sp, w)
+    dev = torch.device("cuda:0")
+    V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
+    ctx = built(lib, cfg, sp, "mixed")
+    for bad in ([17, 64, 16, 48], [32, 80, 16, 48], [32, 64, 0, -16]):
+        with pytest.raises(BipError):
+            ctx.set_site_windows(bad)
+    ctx.set_site_windows(w)
+    H = torch.tensor(flat, dtype=torch.complex64, device=dev)
+    with pytest.raises(BipError):
+        ctx.cube(V, H, sp.scans)
+    with pytest.raises(BipError):
+        ctx.grad(H, sp.scans, torch.ones(len(sp.scans), dtype=torch.float64, device=dev))
+    with pytest.raises(BipError):
+        ctx.windows(0)
+    for order in (1, 2):
+        ctx.set_order(order)
+        with pytest.raises(BipError):
+            ctx.map(H, sp.scans)
+    ctx.set_order(0)
+    assert np.all(np.isfinite(ctx.map(H, sp.scans).cpu().numpy()))
+    ctx.close()

@@ -249,3 +249,25 @@ def test_golden_config1_map_is_the_oracles():
     m = bip.bip_map(bip.make_problem(sp)).map
     assert stored.shape == m.shape
     assert np.max(np.abs(stored - m)) <= 1e-15 * np.max(np.abs(m))
+
+
+def test_site_windows_restrict_the_coupling_sum(c1):
+    """Eq. coupling sums over each site's own crop window Omega_tau: sites
+    whose windows are smaller than the context's (w_k x w_k from
+    floor(t + 1/2) - w_k/2) give exactly the map of the full windows with
+    H_n zero outside each site's block -- which pins the sub-window's origin
+    and the restriction of the sum -- and a visibly different map from the
+    full windows with the full H (the truncation of H matters here)."""
+    sp, pr, _ = c1
+    site_win = [32, 64, 16, 48]
+    parts, _, padded = synth.site_window_inputs(sp, site_win)
+    own = bip.bip_map(bip.make_problem(sp, site_win=site_win, H=parts))
+    pad = bip.bip_map(bip.make_problem(sp, H=padded))
+    assert rel(own.map, pad.map) < 1e-12
+    assert rel(own.partials, pad.partials) < 1e-12
+    full = bip.bip_map(pr)
+    assert rel(own.map, full.map) > 1e-4
+    # a site whose window is the context's is untouched
+    assert rel(own.partials[1], full.partials[1]) < 1e-12
+    with pytest.raises(ValueError):
+        bip.make_problem(sp, site_win=[32, 64, 16, 32], H=parts)
