@@ -405,9 +405,10 @@ bip_status bip_get_profile(bip_ctx* ctx, double* ms, int64_t* launches);
  * its host geometry (bip_create allocates no device memory); this call does
  * not touch the context's own device buffers or mark S1 as built.
  *
- * The first call on a device looks up the array's device address (once per
- * device); the driver may place the array in device memory at that moment.
- * Make that first call before any stream capture.  Requests that
+ * Each call looks up the array's address in the current device context and
+ * copies its tables and site lists from host memory that lives only during
+ * the call, so the call must not be captured into a CUDA graph: on a stream
+ * that is being captured it returns BIP_ERR_INVALID_ARG.  Requests that
  * need more than 32 MiB -- Bp1 * ny * nx * 8 bytes of parent columns plus a
  * few KB of tables and site lists -- return BIP_ERR_SHAPE with the sizes in
  * bip_last_error.  All calls share the one array and keep the last call's

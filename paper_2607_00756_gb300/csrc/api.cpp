@@ -3092,6 +3092,8 @@ extern "C" bip_status bip_build_s1_noalloc(bip_ctx* c, const float* V, const bip
     if (!V) return fail(c, BIP_ERR_INVALID_ARG, "V is null");
     if (!stash) return fail(c, BIP_ERR_INVALID_ARG, "stash is null");
     cudaStream_t s = (cudaStream_t)stream;
+    if (capturing(s))
+        return fail(c, BIP_ERR_INVALID_ARG, "bip_build_s1_noalloc copies from call-local host memory: not capturable");
     const bip_config& g = c->cfg;
     const BipGeometry& geo = c->geo;
     std::vector<SiteDev> sites;
