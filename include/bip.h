@@ -340,9 +340,9 @@ bip_status bip_set_site_windows(bip_ctx* ctx, const int32_t* win, void* stream);
  *   d_V [nz, ny, nx] float32 device: dL/dV_j of every slice potential,
  *         through the reconstruction (Eq. magpreserve) and both sweeps
  *         (Eq. smatrix-advance, Eq. s2); V (device, the potential the
- *         matrices were built from) is then required; power-of-two grid
- *         lengths only (else BIP_ERR_UNSUPPORTED).  The sweeps' forward
- *         states are recomputed from checkpoints every ceil(sqrt(n)) slices.
+ *         matrices were built from) is then required (every grid length
+ *         bip_create takes).  The sweeps' forward states are recomputed
+ *         from checkpoints every ceil(sqrt(n)) slices.
  * Any output may be NULL (not computed).  Steps: R_tau = f_y f_x o_tau
  * sum_{rho in crop} g c c^H; Mbar = M R; dL/dH_n(r) = 2 sum_{d,b}
  * Mbar_n(d,b) conj(S2_d(r) S1_b(r)); dL/dtheta = -2 sum_b chi'_b Im

@@ -28,10 +28,36 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Row layout of a length-NX row (NX = S M, S = 1 or 3 for the lengths 3 M):
+// NT = M / 8 threads per row, value (s, m) of thread t at the real-space
+// point real(s, m, t) and the frequency freq(s, m, t) -- the layouts of
+// fft_reg and fft_reg3, as the forward row pass holds them.
+template <int NX>
+struct AdjRow {
+    static constexpr bool THREE = NX % 3 == 0;
+    static constexpr int S = THREE ? 3 : 1;
+    static constexpr int M = NX / S;
+    static constexpr int NT = M / 8;
+    static constexpr int RPB = kThreads / NT;
+    __device__ __forceinline__ static int real(int s, int m, int t) {
+        return THREE ? 3 * (t + m * NT) + s : t + m * NT;
+    }
+    __device__ __forceinline__ static int freq(int s, int m, int t) { return t + m * NT + s * M; }
+};
+
+template <int NX, bool INV>
+__device__ __forceinline__ void adj_fft(float2 (&v)[AdjRow<NX>::S][8], float2* b0, float2* b1, int& ph, int t,
+                                        const float2* tw) {
+    if constexpr (AdjRow<NX>::THREE)
+        fft_reg3<AdjRow<NX>::M, INV>(v, b0, b1, ph, t, tw);
+    else
+        fft_reg<NX, INV>(v[0], b0, b1, ph, t, tw);
+}
+
 template <int NX>
 __global__ void __launch_bounds__(kThreads) adj_row_kernel(MsPlan plan, MsAdjArgs a) {
-    constexpr int NT = NX / 8;
-    constexpr int RPB = kThreads / NT;
+    using RS = AdjRow<NX>;
+    constexpr int NT = RS::NT, RPB = RS::RPB, S = RS::S;
     extern __shared__ float2 smem[];
     const int sub = threadIdx.x / NT;
     const int t = threadIdx.x % NT;
@@ -47,9 +73,15 @@ __global__ void __launch_bounds__(kThreads) adj_row_kernel(MsPlan plan, MsAdjArg
     const bool active = c < plan.ncol;
     float2* g = a.cols + ((size_t)(active ? c : 0) * plan.ny + y) * NX;
 
-    float2 v[8];
+    // the row arrives in frequency order for an inverse FFT, in real-space
+    // order otherwise, and leaves in frequency order after an FFT
+    float2 v[S][8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = (!active || a.zero_in) ? make_float2(0.f, 0.f) : g[t + m * NT];
+    for (int q = 0; q < S; ++q)
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+            v[q][m] = (!active || a.zero_in) ? make_float2(0.f, 0.f)
+                                             : g[a.do_ifft ? RS::freq(q, m, t) : RS::real(q, m, t)];
     for (int i = threadIdx.x; i < NX; i += kThreads) {
         tw[i] = __ldg(&plan.twx[i]);
         if (a.v) {
@@ -60,7 +92,7 @@ __global__ void __launch_bounds__(kThreads) adj_row_kernel(MsPlan plan, MsAdjArg
     }
     __syncthreads();
     int ph = 0;
-    if (a.do_ifft && !a.zero_in) fft_reg<NX, true>(v, b0, b1, ph, t, tw);
+    if (a.do_ifft && !a.zero_in) adj_fft<NX, true>(v, b0, b1, ph, t, tw);
     auto inject = [&]() {
         if (!active || !a.row_off) return;
         const int e1 = __ldg(&a.row_off[y + 1]);
@@ -68,15 +100,17 @@ __global__ void __launch_bounds__(kThreads) adj_row_kernel(MsPlan plan, MsAdjArg
             const int4 en = __ldg(&a.row_ent[e]);      // (site, u, ox, -)
             const float2* src = a.inj + (((size_t)en.x * plan.ncol + c) * a.win + en.y) * a.win;
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                int u = (t + m * NT - en.z) % NX;
-                if (u < 0) u += NX;
-                if (u < a.win) {
-                    const float2 d = __ldg(&src[u]);
-                    v[m].x += d.x;
-                    v[m].y += d.y;
+            for (int q = 0; q < S; ++q)
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    int u = (RS::real(q, m, t) - en.z) % NX;
+                    if (u < 0) u += NX;
+                    if (u < a.win) {
+                        const float2 d = __ldg(&src[u]);
+                        v[q][m].x += d.x;
+                        v[q][m].y += d.y;
+                    }
                 }
-            }
         }
     };
     if (a.inj_before) inject();
@@ -85,16 +119,19 @@ __global__ void __launch_bounds__(kThreads) adj_row_kernel(MsPlan plan, MsAdjArg
         // parents in order
         const float2* st = a.state + ((size_t)(active ? c : 0) * plan.ny + y) * NX;
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            float r = 0.f;
-            if (active) {
-                float2 u = st[t + m * NT];
-                if (a.state_times_T) u = c_mul(u, tt[t + m * NT]);
-                // Im(conj(v) u) = v.x u.y - v.y u.x
-                r = -2.f * plan.sigma * (v[m].x * u.y - v[m].y * u.x);
+        for (int q = 0; q < S; ++q)
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int x = RS::real(q, m, t);
+                float r = 0.f;
+                if (active) {
+                    float2 u = st[x];
+                    if (a.state_times_T) u = c_mul(u, tt[x]);
+                    // Im(conj(v) u) = v.x u.y - v.y u.x
+                    r = -2.f * plan.sigma * (v[q][m].x * u.y - v[q][m].y * u.x);
+                }
+                red[sub * NX + x] = r;
             }
-            red[sub * NX + t + m * NT] = r;
-        }
         __syncthreads();
         for (int i = threadIdx.x; i < NX; i += kThreads) {
             float s = 0.f;
@@ -104,19 +141,26 @@ __global__ void __launch_bounds__(kThreads) adj_row_kernel(MsPlan plan, MsAdjArg
     }
     if (a.v) {
 #pragma unroll
-        for (int m = 0; m < 8; ++m) v[m] = c_mul(v[m], make_float2(tt[t + m * NT].x, -tt[t + m * NT].y));
+        for (int q = 0; q < S; ++q)
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const float2 tv = tt[RS::real(q, m, t)];
+                v[q][m] = c_mul(v[q][m], make_float2(tv.x, -tv.y));
+            }
     }
     if (!a.inj_before) inject();
-    if (a.do_fft) fft_reg<NX, false>(v, b0, b1, ph, t, tw);
+    if (a.do_fft) adj_fft<NX, false>(v, b0, b1, ph, t, tw);
     if (active) {
 #pragma unroll
-        for (int m = 0; m < 8; ++m) g[t + m * NT] = v[m];
+        for (int q = 0; q < S; ++q)
+#pragma unroll
+            for (int m = 0; m < 8; ++m) g[a.do_fft ? RS::freq(q, m, t) : RS::real(q, m, t)] = v[q][m];
     }
 }
 
 template <int NX>
 cudaError_t launch_adj_row(const MsPlan& p, const MsAdjArgs& a, int* groups, cudaStream_t s) {
-    constexpr int NT = NX / 8, RPB = kThreads / NT;
+    constexpr int RPB = AdjRow<NX>::RPB;
     const int gpy = (p.ncol + RPB - 1) / RPB;
     *groups = gpy;
     const long long blocks = (long long)p.ny * gpy;
@@ -241,6 +285,9 @@ cudaError_t bip_ms_adj_row_pass(const MsPlan& p, const MsAdjArgs& a, int* groups
         case 256: return launch_adj_row<256>(p, a, groups, s);
         case 512: return launch_adj_row<512>(p, a, groups, s);
         case 1024: return launch_adj_row<1024>(p, a, groups, s);
+        case 192: return launch_adj_row<192>(p, a, groups, s);
+        case 384: return launch_adj_row<384>(p, a, groups, s);
+        case 768: return launch_adj_row<768>(p, a, groups, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -2589,8 +2589,6 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
     if (st != BIP_OK) return st;
     if (c->uneven) return fail(c, BIP_ERR_UNSUPPORTED, "the reverse pass takes every site at the context's window");
     if (d_V && !V) return fail(c, BIP_ERR_INVALID_ARG, "d_V needs the V the matrices were built from");
-    if (d_V && (!pow2_in(c->cfg.ny, 64, 1024) || !pow2_in(c->cfg.nx, 64, 1024)))
-        return fail(c, BIP_ERR_UNSUPPORTED, "dL/dV (the adjoint sweeps) needs power-of-two grid lengths");
     if ((reinterpret_cast<uintptr_t>(d_H) & 7) != 0) return fail(c, BIP_ERR_INVALID_ARG, "d_H must be 8-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     const bip_config& g = c->cfg;
