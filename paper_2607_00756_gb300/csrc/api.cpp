@@ -1348,7 +1348,7 @@ CubeArgs cube_args(const bip_ctx* c, const int32_t* ids, int nb, int P, float* c
 
 // The coupling operands' rows past a side's targets (the padding up to
 // Dpad / Bpad) must read as zero: the Gram contraction runs over every
-// detector row.  The buffers are zeroed when allocated and every writer
+// detector row (and the probe order's operands are cleared with them).  The buffers are zeroed when allocated and every writer
 // packs target rows only, at pitch K = w^2; after a batch packed at another
 // pitch, rows that are padding at pitch K may hold values, so the buffers
 // are cleared before the pitch changes (never while every site has the
@@ -1356,7 +1356,7 @@ CubeArgs cube_args(const bip_ctx* c, const int32_t* ids, int nb, int P, float* c
 bip_status operand_layout(bip_ctx* c, int K, cudaStream_t s) {
     if (c->op_k == K) return BIP_OK;
     if (c->op_k != 0)
-        for (DevBuf* b : {&c->opA16, &c->opB16, &c->op8A, &c->op8B, &c->opA32, &c->opB32})
+        for (DevBuf* b : {&c->opA16, &c->opB16, &c->op8A, &c->op8B, &c->opA32, &c->opB32, &c->s1t, &c->psi, &c->ybuf})
             if (b->p) CUDA_TRY(c, cudaMemsetAsync(b->p, 0, b->cap, s));
     c->op_k = K;
     return BIP_OK;
@@ -1420,8 +1420,6 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     if (probe && (c->prec != BIP_PREC_MIXED || !c->recon_tc))
         return fail(c, BIP_ERR_UNSUPPORTED, "the probe order needs the mixed precision and at most 64 parents per side");
     if (probe && P > kProbeMaxScans) return fail(c, BIP_ERR_UNSUPPORTED, "the probe order takes at most 2048 scans");
-    if (c->uneven && (cube_out || beam || probe))
-        return fail(c, BIP_ERR_UNSUPPORTED, "sites with windows of their own: the map in the Gram order only");
     if (cube_out || beam || probe) {
         // c_b(rho) for every scan
         CUDA_TRY(c, ensure(c->illum, (size_t)Bpad * P * sizeof(float2), false, s));
@@ -1595,13 +1593,13 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
         // write the same cube entries, in site order, from one CTA
         std::vector<int32_t> cw, cg, wm;
         int max_items = 0;
-        for (int b0 = 0; b0 < c->n_sites; b0 += SB) {
-            const int nbb = std::min(SB, c->n_sites - b0);
+        for (const auto& bt : batches) {
+            const int b0 = bt.first, nbb = bt.second;
             cube_off.push_back((int)cw.size() / 2);
             cube_goff.push_back((int)cg.size());
             const int first = (int)cw.size() / 2;
             auto meets = [&](int bs, int t) {
-                const SiteDev& sd = c->sites[b0 + bs];
+                const SiteDev& sd = c->sites[c->batch_order[b0 + bs]];
                 return box_meets_crop(bb64[4 * t], bb64[4 * t + 1], bb64[4 * t + 2], bb64[4 * t + 3], sd.ty, sd.tx, g);
             };
             if (cube_out) {
@@ -1688,7 +1686,7 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             g1.site_stride = (int64_t)perB;
         }
         if (probe) {
-            bip_status st = recon_tc_batch(c, ids, nb, H, c->opA16.p, c->s1t.p, s, true);
+            bip_status st = recon_tc_batch(c, ids, nb, H, c->opA16.p, c->s1t.p, s, true, true, wb);
             if (st != BIP_OK) return st;
             // Psi[rho][r] = sum_b c_b(rho) S1_b(r): A = S1 transposed (pixels in
             // 128-row tiles; BF16, zero lo planes), B = C^T (the scans as the
@@ -2356,7 +2354,6 @@ bip_status bip_coreloss_qeels(bip_ctx* c, const void* H, const double* scan_px, 
                               float* qeels_out, void* stream) {
     bip_status st = check_map_args(c, H, scan_px, P, qeels_out);
     if (st != BIP_OK) return st;
-    if (c->uneven) return fail(c, BIP_ERR_UNSUPPORTED, "qEELS takes every site at the context's window");
     std::vector<int32_t> bins, bin_of;
     if (!qeels_bins(c, axis, bins, bin_of)) return fail(c, BIP_ERR_INVALID_ARG, "axis must be 0 (q_y) or 1 (q_x)");
     if ((axis == 0 ? c->geo.dfy : c->geo.dfx) != 1)
@@ -2484,7 +2481,7 @@ bip_status bip_autotune(bip_ctx* c, const void* H, const double* scan_px, int32_
     // the windowed probes (mixed precision, up to kProbeMaxScans scans)
     const int order0 = c->order;
     int best_order = order0;
-    if (st == BIP_OK && tc && !c->uneven) {   // (sites with windows of their own: the Gram order only)
+    if (st == BIP_OK && tc) {
         const bool probe_ok = c->prec == BIP_PREC_MIXED && c->recon_tc && P <= kProbeMaxScans;
         for (int o : {0, 1, 2}) {
             if (o == order0 || (o == 2 && !probe_ok)) continue;
