@@ -471,6 +471,64 @@ def config4_specimen(i, n, f, nz, nch, target):
         scan_y=(mid - 32.0, 1.0, 64), scan_x=(mid - 32.0, 1.0, 64), oracle_scan_y=None, oracle_scan_x=None)
 
 
+def run_multi_edge(prec="mixed", reps=5):
+    """Two edges in one specimen (config-4 specimen 2: 384^2, f = 3, 40
+    slices): alternate sites keep the nine L-edge-like channels on the
+    64-px window, the others one K-edge-like channel (m = 0) on a 32-px
+    window of its own (the central block; bip_set_site_windows).  The map
+    timed with those windows and with every site on the 64-px window (the
+    one-channel sites' H zero outside their block: the same map), CUDA
+    events around `reps` maps; the two maps' difference is reported."""
+    import torch
+    import synth
+    from paper_2607_00756_gb300.context import BipContext
+    dev = torch.device("cuda:0")
+    cfg = config4_specimen(2, *CONFIG4[2])
+    sp = synth.make_specimen(cfg)
+    ion = np.nonzero(sp.nch > 0)[0]
+    nch = sp.nch.copy()
+    parts, full = [], []
+    for k, a in enumerate(ion.tolist()):
+        h = sp.H[9 * k:9 * (k + 1)]
+        if k % 2:
+            nch[a] = 1
+            c = (cfg.win - 32) // 2
+            parts.append(h[4:5, c:c + 32, c:c + 32])
+            z = np.zeros_like(h[4:5])
+            z[:, c:c + 32, c:c + 32] = h[4:5, c:c + 32, c:c + 32]
+            full.append(z)
+        else:
+            parts.append(h)
+            full.append(h)
+    w = [64 if k % 2 == 0 else 32 for k in range(len(ion))]
+    V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
+    ctx = BipContext(cfg, prec=prec)
+    ctx.build(V, sp.atoms, nch)
+    del V
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(H):
+        out = ctx.map(H, sp.scans)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            ctx.map(H, sp.scans, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out.cpu().numpy()
+
+    Hf = torch.tensor(np.concatenate([x.reshape(-1) for x in full]), dtype=torch.complex64, device=dev)
+    t_full, m_full = timed(Hf)
+    ctx.set_site_windows(w)
+    Ho = torch.tensor(np.concatenate([x.reshape(-1) for x in parts]), dtype=torch.complex64, device=dev)
+    t_own, m_own = timed(Ho)
+    ctx.close()
+    return {"specimen": "384^2, f = 3, 40 slices, %d sites, 64 x 64 scans" % len(ion),
+            "sites": "alternate: 9 channels on 64 px / 1 channel on its own 32 px window",
+            "context_window_ms": round(t_full, 2), "own_windows_ms": round(t_own, 2),
+            "own_vs_context_rel_l2": float(np.linalg.norm(m_own - m_full) / np.linalg.norm(m_full))}
+
+
 def run_config4(prec="mixed", reps=5):
     """The batched workload at its own scale: 16 specimens (CONFIG4), every
     context autotuned (sites per batch, coupling tile, contraction order),
@@ -550,6 +608,7 @@ def run_config4(prec="mixed", reps=5):
             "eager_ms": round(t_eager, 2), "graph_concurrent_ms": round(t_graph, 2),
             "eager_evals_per_s": evals / (t_eager / 1e3), "graph_evals_per_s": evals / (t_graph / 1e3),
             "cube_128x128_ms": round(t_cube, 1), "cube_evals_per_s": cube_sites * 4096 / (t_cube / 1e3),
+            "multi_edge": run_multi_edge(prec),
             "timing": "maps only (matrices built once), CUDA events around 5 rounds; the cube with its S1 build"}
 
 
