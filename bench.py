@@ -769,7 +769,8 @@ def run_cube(cfg, sp, prec="mixed", reps=1):
     return {"ms_per_step": ms, "evals_per_s": n_sites * len(sp.scans) / (ms / 1e3), "precision": prec,
             "n_cube": n_cube, "stage_ms": {k: round(v[0], 1) for k, v in prof.items() if v[1] > 0},
             "step": "S1 build and the cube [P, n_cube] on the complete basis (exact S2 columns swept in "
-                    "batches, per-beam contraction on tcgen05 in split BF16)"}
+                    "batches; the per-beam contraction separated over the beam lattice on the raster "
+                    "scans, FP32)"}
 
 
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of

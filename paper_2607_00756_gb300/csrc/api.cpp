@@ -80,6 +80,7 @@ struct bip_ctx {
     DevBuf hcube, shcube, cstash, ccols; // the exact cube: basis, shifts, S2 windows, columns
     DevBuf xopA, xopB, xm32;            // ... its coupling operands and M
     DevBuf tcache;                      // T_j = exp(i sigma V_j) of the slices a sweep crosses
+    DevBuf cr_ay, cr_ax, cr_cy, cr_cx, cr_T;   // the cube on a raster: phase tables, crop bits, T
     size_t cube_budget = 0;             // bytes of sweep columns + windows per detector batch (0: auto)
     DevBuf s1t, psi, ybuf;              // the probe order: S1 transposed, Psi, H_n x Psi
     DevBuf pyc, pxc;                    // conjugated propagator tables (adjoint sweeps)
@@ -665,7 +666,8 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->g_dt1, &c->g_dt2, &c->g_adj, &c->g_ckpt, &c->g_seg, &c->g_gvp, &c->pyc, &c->pxc,
                      &c->ray, &c->rax, &c->g_tA, &c->g_tB, &c->g_sA2, &c->g_sB2, &c->cubeA, &c->cubeB,
                      &c->cube_work, &c->cube_mask, &c->s1t, &c->psi, &c->ybuf, &c->cube_grp, &c->cube_wmap, &c->mpart,
-                     &c->hcube, &c->shcube, &c->cstash, &c->ccols, &c->xopA, &c->xopB, &c->xm32, &c->tcache};
+                     &c->hcube, &c->shcube, &c->cstash, &c->ccols, &c->xopA, &c->xopB, &c->xm32, &c->tcache,
+                     &c->cr_ay, &c->cr_ax, &c->cr_cy, &c->cr_cx, &c->cr_T};
     for (DevBuf* b : all) release(*b);
     for (int i = 0; i < 6; ++i) {
         release(c->aw1[i]);
@@ -2043,12 +2045,79 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
     CUDA_TRY(c, ensure(c->xm32, SB * perMt * sizeof(float2), true, s));
     if (tc) CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
 
+    // On a raster scan list the per-beam contraction separates over the
+    // aperture beams' lattice (cube_raster.cu): phase tables per scan row and
+    // column, angles reduced in FP64, and the stage-1 workspace T.
+    const Raster rr = detect_raster(scans, P);
+    const int nky = 2 * c->Ky + 1, nkx = 2 * c->Kx + 1;
+    // (stage 2 prefetches a tile of nky x 64 values with 8 per thread: nky <= 32)
+    const bool sep = rr.ok && nky <= 32 && nkx <= 128 && (size_t)nkx * (rr.Mx + 32) * 8 <= 200 * 1024;
+    CubeRasterArgs cra{};
+    if (sep) {
+        std::vector<double> ry(rr.My), rx(rr.Mx);
+        for (int my = 0; my < rr.My; ++my) ry[my] = scans[2 * (size_t)my * rr.Mx];
+        for (int mx = 0; mx < rr.Mx; ++mx) rx[mx] = scans[2 * (size_t)mx + 1];
+        std::vector<float2> ay((size_t)rr.My * nky), ax((size_t)nkx * rr.Mx);
+        for (int my = 0; my < rr.My; ++my)
+            for (int iy = 0; iy < nky; ++iy)
+                ay[(size_t)my * nky + iy] = turn_d(-(double)g.fy * (iy - c->Ky) * ry[my] / g.ny);
+        for (int ix = 0; ix < nkx; ++ix)
+            for (int mx = 0; mx < rr.Mx; ++mx)
+                ax[(size_t)ix * rr.Mx + mx] = turn_d(-(double)g.fx * (ix - c->Kx) * rx[mx] / g.nx);
+        // each site's crop per axis as bits (the FP64 test of in_crop, one
+        // axis at a time: the mask is the product of the two)
+        auto axis = [](double r, double t, int n, int f) {
+            double d = r - t;
+            d -= n * std::floor((d + 0.5 * n) / n);
+            const double h = 0.5 * n / f;
+            return d >= -h && d < h;
+        };
+        const int wy = (rr.My + 31) / 32, wx = (rr.Mx + 31) / 32;
+        std::vector<uint32_t> cy((size_t)c->n_sites * wy, 0u), cx((size_t)c->n_sites * wx, 0u);
+        for (int k = 0; k < c->n_sites; ++k) {
+            const SiteDev& sd = c->sites[k];
+            for (int my = 0; my < rr.My; ++my)
+                if (axis(ry[my], sd.ty, g.ny, g.fy)) cy[(size_t)k * wy + my / 32] |= 1u << (my % 32);
+            for (int mx = 0; mx < rr.Mx; ++mx)
+                if (axis(rx[mx], sd.tx, g.nx, g.fx)) cx[(size_t)k * wx + mx / 32] |= 1u << (mx % 32);
+        }
+        CUDA_TRY(c, upload(c->cr_cy, cy, s));
+        CUDA_TRY(c, upload(c->cr_cx, cx, s));
+        cra.crop_y = (const uint32_t*)c->cr_cy.p;
+        cra.crop_x = (const uint32_t*)c->cr_cx.p;
+        cra.wy = wy;
+        cra.wx = wx;
+        CUDA_TRY(c, upload(c->cr_ay, ay, s));
+        CUDA_TRY(c, upload(c->cr_ax, ax, s));
+        cra.nch = nch;
+        cra.nd_pad = Dpb;
+        cra.nky = nky;
+        cra.nkx = nkx;
+        cra.lat = (const int32_t*)c->lat_d.p;
+        cra.coef = (const double2*)c->coef.p;
+        cra.ay = (const float2*)c->cr_ay.p;
+        cra.ax = (const float2*)c->cr_ax.p;
+        cra.My = rr.My;
+        cra.Mx = rr.Mx;
+        cra.n_sites = SB;
+        CUDA_TRY(c, ensure(c->cr_T, bip_cube_raster_t_bytes(cra), false, s));
+        cra.T = (float2*)c->cr_T.p;
+        cra.cube_ld = n_cube;
+        cra.scale = 1.0f;
+        cra.sites = (const SiteDev*)c->sites_d.p;
+        if (tc) {   // M from the coupling as complex64 rows (ch, b), columns d
+            cra.m_site = (int64_t)perMt; cra.m_b = Dpb; cra.m_ch = (int64_t)Bpad * Dpb;
+        } else {    // Mt[b][ch Dp + d]
+            cra.m_site = (int64_t)perMt; cra.m_b = (int64_t)nch * Dpb; cra.m_ch = Dpb;
+        }
+    }
+
     // tcgen05 per-beam contraction: c_b(rho) as split planes, and work items
     // grouped by scan tile (sites ascending), one CTA per cube tile
     const int ctn = P >= 128 ? 128 : 64;
     const int crow = round_up(P, ctn), n_ct = crow / ctn;
     std::vector<int> cube_off, cube_goff;
-    if (tc) {
+    if (tc && !sep) {
         CUDA_TRY(c, ensure(c->cubeB, (size_t)4 * crow * Bpad * sizeof(uint16_t), true, s));
         CUDA_TRY(c, ensure(c->cubeA, (size_t)SB * 4 * D128 * KB * sizeof(uint16_t), true, s));
         SplitArgs sc{(const float2*)c->illum.p, 1, P, 0, P, Bpad, 1, (uint16_t*)c->cubeB.p, 0, crow, Bpad, 0, 0};
@@ -2195,6 +2264,16 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
                 A.err = (int*)c->errflag.p;
                 A.wait_ns = c->wait_ns;
                 TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(A, s));
+                if (sep) {
+                    CubeRasterArgs r = cra;
+                    r.n_sites = nb;
+                    r.site_ids = ids;
+                    r.m = (const float2*)c->xm32.p;
+                    r.nd = nd;
+                    r.cube = cube_out + d0;
+                    TIMED(c, BIP_STAGE_QUADFORM, s, bip_cube_raster(r, s));
+                    continue;
+                }
                 SplitArgs sa{(const float2*)c->xm32.p, 1, Dpb, (int64_t)perMt, Dpb, (int)KB, nb,
                              (uint16_t*)c->cubeA.p, (int64_t)(4 * D128 * KB), D128, (int)KB, 0, 0};
                 TIMED(c, BIP_STAGE_QUADFORM, s, bip_split_planes(sa, s));
@@ -2241,6 +2320,16 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
                 A.C = (float2*)c->xm32.p; A.ldc = (int64_t)nch * Dpb; A.strideC = (int64_t)perMt;
                 A.ep_B = Bpad; A.ep_Dp = Dpb;
                 TIMED(c, BIP_STAGE_COUPLING, s, bip_cgemm_simt(A, s));
+                if (sep) {
+                    CubeRasterArgs r = cra;
+                    r.n_sites = nb;
+                    r.site_ids = ids;
+                    r.m = (const float2*)c->xm32.p;
+                    r.nd = nd;
+                    r.cube = cube_out + d0;
+                    TIMED(c, BIP_STAGE_QUADFORM, s, bip_cube_raster(r, s));
+                    continue;
+                }
                 CubeArgs ca = cube_args(c, ids, nb, P, cube_out + d0);
                 ca.n_det = nd;
                 ca.Dp = Dpb;

@@ -142,6 +142,33 @@ cudaError_t bip_gather(const GatherArgs& a, cudaStream_t s);
 // recon_tc.cu : window reconstruction on the tensor cores (mixed path).
 // X [site-plane rows][K px][64 parents] bf16: row (x_site0 + 3 bs + plane) K
 // + px, planes re, im, magnitude of the de-tilted stash.
+// cube_raster.cu : the cube's per-beam contraction on a raster scan list,
+// separated over the aperture beams' lattice (two short sums, FP32)
+struct CubeRasterArgs {
+    int n_sites;                    // sites of the batch
+    const int32_t* site_ids;
+    const SiteDev* sites;
+    const float2* m;                // M(n, b, d) = m[bs m_site + b m_b + n m_ch + d], complex64
+    int64_t m_site, m_b, m_ch;
+    int nch;                        // channel slots of M (a site uses its first nch)
+    int nd, nd_pad;                 // beams d of the batch; row pitch of T (multiple of 32)
+    int nky, nkx;                   // lattice rows 2 Ky + 1 and columns 2 Kx + 1
+    const int32_t* lat;             // [nky][nkx] aperture beam at (k_y, k_x), or -1
+    const double2* coef;            // [B] c_b(rho) = coef_b exp(-2 pi i h_b.rho / N)
+    const float2* ay;               // [My][nky] exp(-2 pi i f_y k_y ry[my] / ny)
+    const float2* ax;               // [nkx][Mx] exp(-2 pi i f_x k_x rx[mx] / nx)
+    const uint32_t* crop_y;         // [all sites][wy] bit my: row my inside the site's crop (one axis)
+    const uint32_t* crop_x;         // [all sites][wx] bit mx: column mx inside it
+    int wy, wx;                     // words per site: ceil(My / 32), ceil(Mx / 32)
+    int My, Mx;                     // scan (my, mx) is scan my Mx + mx
+    float2* T;                      // workspace, bip_cube_raster_t_bytes
+    float* cube;                    // cube[(my Mx + mx) cube_ld + d] += scale sum_n |a_d|^2
+    int64_t cube_ld;
+    float scale;
+};
+size_t bip_cube_raster_t_bytes(const CubeRasterArgs& a);
+cudaError_t bip_cube_raster(const CubeRasterArgs& a, cudaStream_t s);
+
 struct XprepSide {
     const float2* stash;            // [n_sites_total][Bp][stash_win^2]
     int Bp;                         // parents (<= 64)

@@ -229,6 +229,24 @@ def test_cube_config1(lib, c1, prec, tol):
     assert np.array_equal(_cube(ctx, sp, H), cube)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("split_bf16", 1e-4), ("mixed", 1e-3)])
+def test_cube_raster_and_any_scan_order_agree(lib, c1, prec, tol):
+    """On a raster scan list the cube's per-beam contraction runs separated
+    over the beam lattice (two short sums per site, FP32); the same scans
+    shuffled are no raster and take the per-scan contraction.  Both against
+    the oracle, and row for row against each other."""
+    cfg, sp, pr, ref = c1
+    want = obip.bip_cube(pr)
+    ctx, m, _, H = gpu_run(lib, cfg, sp, prec=prec)
+    cube_r = _cube(ctx, sp, H)
+    assert rel(cube_r, want) < tol
+    perm = np.random.default_rng(3).permutation(len(sp.scans))
+    V = torch.tensor(sp.V, dtype=torch.float32, device=H.device)
+    cube_p = ctx.cube(V, H, sp.scans[perm]).cpu().numpy()
+    assert rel(cube_p, want[perm]) < tol
+    assert rel(cube_p, cube_r[perm]) < tol
+
+
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("mixed", 1e-3)])
 def test_cube_edge_cases(lib, prec, tol):
     """Sites in every plane, windows wrapping the grid, one- and
