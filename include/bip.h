@@ -322,7 +322,7 @@ bip_status bip_set_aberrations(bip_ctx* ctx, double defocus, double cs, void* st
  * batch over its w_k^2 pixels, and H holds each site's channels on its own
  * window (see bip_coreloss_map).  Kept until the next build with another
  * site list.  The maps (every contraction order, bip_coreloss_sites,
- * bip_autotune) and qEELS take such sites; the cube, the reverse pass,
+ * bip_autotune), qEELS and the cube take such sites; the reverse pass,
  * bip_site_windows and bip_site_coupling return BIP_ERR_UNSUPPORTED while a
  * site's window is below win.  BIP_ERR_INVALID_ARG before a build, for a
  * bad size, or when H would exceed 2^31 complex elements. */

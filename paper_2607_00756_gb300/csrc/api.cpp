@@ -59,6 +59,7 @@ struct bip_ctx {
     bool uneven = false;                // some site's window is below win
     int64_t h_elems = 0;                // complex elements of H the sites read
     int op_k = 0;                       // row pitch of the coupling operands' current contents
+    int xop_k = 0;                      // ... and of the cube's own operands (xopA, xopB)
     uint64_t sig1 = 0, sig2 = 0;        // site-list signatures of the builds
     bool s1 = false, s2 = false;
 
@@ -2035,6 +2036,7 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
     // site batches and their buffers (as the map's)
     const int SB = c->sb_override > 0 ? std::min(c->n_sites, c->sb_override)
                                       : (tc ? tc_batch(c) : std::min(c->n_sites, 8));
+    const std::vector<std::pair<int, int>> batches = map_batches(c, SB);   // (one window size each)
     const size_t rowsB = (size_t)nch * Bpad, perA = (size_t)Dpb * K, perB = rowsB * K;
     const size_t perMt = (size_t)Bpad * nch * Dpb, KB = (size_t)nch * Bpad;
     // the cube's own operand and coupling buffers: the map's keep zero
@@ -2134,15 +2136,15 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
             bb.insert(bb.end(), {y0, y1, x0, x1});
         }
         std::vector<int32_t> cw, cg;
-        for (int b0 = 0; b0 < c->n_sites; b0 += SB) {
-            const int nbb = std::min(SB, c->n_sites - b0);
+        for (const auto& bt : batches) {
+            const int b0 = bt.first, nbb = bt.second;
             cube_off.push_back((int)cw.size() / 2);
             cube_goff.push_back((int)cg.size());
             const int first = (int)cw.size() / 2;
             for (int t = 0; t < n_ct; ++t) {
                 const int g0 = (int)cw.size() / 2 - first;
                 for (int bs = 0; bs < nbb; ++bs) {
-                    const SiteDev& sd = c->sites[b0 + bs];
+                    const SiteDev& sd = c->sites[c->batch_order[b0 + bs]];
                     if (box_meets_crop(bb[4 * t], bb[4 * t + 1], bb[4 * t + 2], bb[4 * t + 3], sd.ty, sd.tx, g)) {
                         cw.push_back(bs);
                         cw.push_back(t);
@@ -2198,16 +2200,28 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
             TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
             if (j > first_plane) TIMED(c, BIP_STAGE_MS_COL, s, bip_ms_col_pass(plan, (float2*)c->ccols.p, s));
         }
-        int bi = 0;
-        for (int b0 = 0; b0 < c->n_sites; b0 += SB, ++bi) {
-            const int nb = std::min(SB, c->n_sites - b0);
+        for (int bi = 0; bi < (int)batches.size(); ++bi) {
+            const int b0 = batches[bi].first, nb = batches[bi].second;
             const int32_t* ids = (const int32_t*)c->seq_ids_d.p + b0;
+            // the batch's window: its operands packed at K = w^2 (shadowing the
+            // context-wide sizes the buffers were allocated for); after a
+            // batch at another pitch the operands' padding rows are cleared
+            const int wb = c->sites[c->batch_order[b0]].w;
+            const int K = wb * wb;
+            const size_t perA = (size_t)Dpb * K, perB = rowsB * K;
+            if (c->xop_k != K) {
+                if (c->xop_k != 0) {
+                    CUDA_TRY(c, cudaMemsetAsync(c->xopA.p, 0, c->xopA.cap, s));
+                    CUDA_TRY(c, cudaMemsetAsync(c->xopB.p, 0, c->xopB.cap, s));
+                }
+                c->xop_k = K;
+            }
             // aperture side H_n S1 (partitioned, rebuilt on the windows)
             if (c->prec == BIP_PREC_MIXED && c->recon_tc) {
-                bip_status st = recon_tc_batch(c, ids, nb, H, nullptr, c->xopB.p, s, false, false);
+                bip_status st = recon_tc_batch(c, ids, nb, H, nullptr, c->xopB.p, s, false, false, wb);
                 if (st != BIP_OK) return st;
             } else {
-                GatherArgs g1 = gather_args(c, 1, ids, nb);
+                GatherArgs g1 = gather_args(c, 1, ids, nb, wb);
                 g1.rows_pad = Bpad;
                 g1.nch = nch;
                 g1.H = (const float2*)H;
@@ -2226,7 +2240,9 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
             ra.n_sites = nb;
             ra.site_ids = ids;
             ra.sites = (const SiteDev*)c->sites_d.p;
-            ra.win = g.win; ra.ny = g.ny; ra.nx = g.nx; ra.K = K;
+            ra.win = wb; ra.ny = g.ny; ra.nx = g.nx; ra.K = K;
+            ra.stash_win = g.win;
+            ra.wo = (g.win - wb) / 2;
             ra.nd = nd;
             ra.stash = (const float2*)c->cstash.p;
             ra.h = (const int2*)c->hcube.p + d0;
@@ -2374,7 +2390,6 @@ bip_status bip_coreloss_cube(bip_ctx* c, const float* V, const void* H, const do
     if (!c) return BIP_ERR_INVALID_ARG;
     if (!c->s1 || site_signature(c->sites) != c->sig1)
         return fail(c, BIP_ERR_INVALID_ARG, "bip_build_s1 must run first (the cube's sites are its sites)");
-    if (c->uneven) return fail(c, BIP_ERR_UNSUPPORTED, "the cube takes every site at the context's window");
     if (!V || !H || !scan_px || !cube_out) return fail(c, BIP_ERR_INVALID_ARG, "null pointer argument");
     if ((reinterpret_cast<uintptr_t>(H) & 15) != 0) return fail(c, BIP_ERR_INVALID_ARG, "H must be 16-byte aligned");
     if (P < 1) return fail(c, BIP_ERR_INVALID_ARG, "P must be >= 1");

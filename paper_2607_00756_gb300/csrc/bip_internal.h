@@ -579,9 +579,10 @@ struct RetiltArgs {
     int n_sites;                    // sites of this batch
     const int32_t* site_ids;
     const SiteDev* sites;
-    int win, ny, nx, K;
+    int win, ny, nx, K;             // win: the batch's window, K = win^2
+    int stash_win, wo;              // the stashed windows' size; offset of the batch's
     int nd;                         // beams in the stash
-    const float2* stash;
+    const float2* stash;            // [all sites][nd][stash_win^2]
     const int2* h;                  // [nd] (h_y, h_x)
     const float2* ey;               // [ny] exp(+2 pi i m / ny)
     const float2* ex;               // [nx]

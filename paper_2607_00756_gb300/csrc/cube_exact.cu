@@ -30,13 +30,18 @@ __global__ void __launch_bounds__(kThreads) retilt_kernel(RetiltArgs a) {
     const SiteDev st = a.sites[site];
     const int px = 2 * pair;
     const int u = px / a.win, v = px - u * a.win;              // v even: v, v + 1 on one row
-    const float4 w = __ldg(reinterpret_cast<const float4*>(a.stash + ((size_t)site * a.nd + d) * a.K) + pair);
+    // the batch's window: the central win x win block (offset wo) of the
+    // stashed stash_win x stash_win one
+    const size_t sk = (size_t)a.stash_win * a.stash_win;
+    const float4 w = __ldg(reinterpret_cast<const float4*>(a.stash + ((size_t)site * a.nd + d) * sk +
+                                                           (size_t)(u + a.wo) * a.stash_win + v + a.wo));
     const int2 h = __ldg(&a.h[d]);
+    const int oy = st.oy + a.wo, ox = st.ox + a.wo;
     // exp(+2 pi i (h_y y + h_x x) / N) from the per-axis tables, the
     // products reduced modulo N (also when negative)
-    const float2 ty = __ldg(&a.ey[wrap_n(h.x * (st.oy + u), a.ny)]);
-    const float2 tx0 = __ldg(&a.ex[wrap_n(h.y * (st.ox + v), a.nx)]);
-    const float2 tx1 = __ldg(&a.ex[wrap_n(h.y * (st.ox + v + 1), a.nx)]);
+    const float2 ty = __ldg(&a.ey[wrap_n(h.x * (oy + u), a.ny)]);
+    const float2 tx0 = __ldg(&a.ex[wrap_n(h.y * (ox + v), a.nx)]);
+    const float2 tx1 = __ldg(&a.ex[wrap_n(h.y * (ox + v + 1), a.nx)]);
     float2 p0 = c_mul(ty, tx0), p1 = c_mul(ty, tx1);
     p0.y = -p0.y;                                               // the conjugate: exp(-2 pi i h.r/N)
     p1.y = -p1.y;
@@ -66,6 +71,7 @@ cudaError_t bip_retilt(const RetiltArgs& a, cudaStream_t s) {
     if (a.n_sites < 1 || a.nd < 1) return cudaSuccess;
     if (a.K % 2 || a.win % 2 || a.nd > a.rows_pad || a.nd > 65535 || a.n_sites > 65535 || a.ny < 1 || a.nx < 1)
         return cudaErrorInvalidValue;
+    if (a.K != a.win * a.win || a.wo < 0 || a.wo % 2 || a.win + 2 * a.wo != a.stash_win) return cudaErrorInvalidValue;
     if (!a.out_c64 && (!a.out_bf16 || (a.out_planes != 2 && a.out_planes != 4))) return cudaErrorInvalidValue;
     const int pairs = a.K / 2;
     retilt_kernel<<<dim3((pairs + kThreads - 1) / kThreads, a.nd, a.n_sites), kThreads, 0, s>>>(a);

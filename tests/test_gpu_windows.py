@@ -137,8 +137,6 @@ def test_own_windows_refusals(lib):
     ctx.set_site_windows(w)
     H = torch.tensor(flat, dtype=torch.complex64, device=dev)
     with pytest.raises(BipError):
-        ctx.cube(V, H, sp.scans)
-    with pytest.raises(BipError):
         ctx.grad(H, sp.scans, torch.ones(len(sp.scans), dtype=torch.float64, device=dev))
     with pytest.raises(BipError):
         ctx.windows(0)
@@ -186,4 +184,31 @@ def test_own_windows_qeels(lib, prec):
     tol = 1e-4 if prec == "fp32" else 1e-3
     assert rel(q, want) < tol
     assert rel(q.astype(np.float64).sum(axis=1), ctx.map(H, sp.scans).cpu().numpy()) < tol
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("mixed", 1e-3)])
+@pytest.mark.parametrize("order", ["raster", "shuffled"])
+def test_own_windows_cube(lib, prec, tol, order):
+    """The exact cube (Algorithm 3) with the sites' own windows: S1's side
+    rebuilt and the exact S2 windows re-tilted on each site's block, the
+    batches of one window size each -- on the raster scans (the separated
+    per-beam contraction) and shuffled (the per-scan one) -- against the
+    oracle's cube with the same windows."""
+    cfg, sp, w = case("config1")
+    parts, flat, _ = synth.site_window_inputs(sp, w)
+    pr = obip.make_problem(sp, site_win=w, H=parts)
+    want = obip.bip_cube(pr)
+    scans = sp.scans
+    if order == "shuffled":
+        perm = np.random.default_rng(4).permutation(len(scans))
+        scans, want = scans[perm], want[perm]
+    dev = torch.device("cuda:0")
+    V = torch.tensor(sp.V, dtype=torch.float32, device=dev)
+    ctx = built(lib, cfg, sp, prec)
+    ctx.set_site_windows(w)
+    H = torch.tensor(flat, dtype=torch.complex64, device=dev)
+    cube = ctx.cube(V, H, scans).cpu().numpy()
+    assert cube.shape == want.shape
+    assert rel(cube, want) < tol
     ctx.close()
