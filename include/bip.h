@@ -322,9 +322,9 @@ bip_status bip_set_aberrations(bip_ctx* ctx, double defocus, double cs, void* st
  * batch over its w_k^2 pixels, and H holds each site's channels on its own
  * window (see bip_coreloss_map).  Kept until the next build with another
  * site list.  The maps (every contraction order, bip_coreloss_sites,
- * bip_autotune), qEELS and the cube take such sites; the reverse pass,
- * bip_site_windows and bip_site_coupling return BIP_ERR_UNSUPPORTED while a
- * site's window is below win.  BIP_ERR_INVALID_ARG before a build, for a
+ * bip_autotune), qEELS, the cube and the reverse pass take such sites
+ * (d_H then has H's layout); bip_site_windows and bip_site_coupling return
+ * BIP_ERR_UNSUPPORTED while a site's window is below win.  BIP_ERR_INVALID_ARG before a build, for a
  * bad size, or when H would exceed 2^31 complex elements. */
 bip_status bip_set_site_windows(bip_ctx* ctx, const int32_t* win, void* stream);
 

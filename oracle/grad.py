@@ -221,7 +221,7 @@ def gradients(prob, params, target=None, scans=None, mode=None, dL_dI=None, want
             Hbar[n] = np.sum(np.conj(S1) * Tn, axis=0)
             S1bar += np.conj(Heff[n])[None, :] * Tn
             S2bar += np.conj(Heff[n])[None, :] * (Mbar @ np.conj(S1))
-        w = cfg.win
+        w = int(prob.win[k])                                            # the site's window
         out["amp"][k, :nch] = 2.0 * np.sum(Hbar * np.conj(Hk.reshape(nch, -1)), axis=1)
         out["H"].append((2.0 * np.conj(params.amp[k, :nch, None]) * Hbar).reshape(nch, w, w))
         if not want_V:

@@ -183,10 +183,12 @@ __global__ void gv_reduce_kernel(const float* part, int groups, int G, float* gV
     gV[i] = s;
 }
 
-// re-tilt phi_t(r) = exp(sign 2 pi i (h_y iy / ny + h_x ix / nx)) at window pixel r
-__device__ __forceinline__ float2 retilt(int2 h, const SiteDev& st, int r, int win, int ny, int nx, int sign) {
+// re-tilt phi_t(r) = exp(sign 2 pi i (h_y iy / ny + h_x ix / nx)) at pixel r
+// of the batch's window (win x win, wo pixels into the stashed one)
+__device__ __forceinline__ float2 retilt(int2 h, const SiteDev& st, int r, int win, int wo, int ny, int nx,
+                                         int sign) {
     const int u = r / win, vv = r - u * win;
-    const int iy = wrap_n(st.oy + u, ny), ix = wrap_n(st.ox + vv, nx);
+    const int iy = wrap_n(st.oy + wo + u, ny), ix = wrap_n(st.ox + wo + vv, nx);
     const float f = (float)(wrap_n(h.x * iy, ny)) / ny + (float)(wrap_n(h.y * ix, nx)) / nx;
     float s, c;
     sincospif(2.f * f, &s, &c);
@@ -200,17 +202,19 @@ __global__ void recon_adj_target_kernel(ReconAdjArgs a) {
     if (r >= a.K || t >= a.n_targets) return;
     const int site = a.site_ids[bs];
     const SiteDev st = a.sites[site];
-    const float2* dt = a.stash + (size_t)site * a.Bp * a.K + r;
+    const size_t sk = (size_t)a.stash_win * a.stash_win;
+    const int ru = r / a.win;
+    const float2* dt = a.stash + (size_t)site * a.Bp * sk + (size_t)(ru + a.wo) * a.stash_win + (r - ru * a.win) + a.wo;
     float ur = 0.f, ui = 0.f, am = 0.f;
     for (int e = __ldg(&a.w.t_off[t]); e < __ldg(&a.w.t_off[t + 1]); ++e) {
         const int p = __ldg(&a.w.t_par[e]);
         const float w = __ldg(&a.w.t_w[e]);
-        const float2 d = __ldg(&dt[(size_t)p * a.K]);
+        const float2 d = __ldg(&dt[(size_t)p * sk]);
         ur = fmaf(w, d.x, ur);
         ui = fmaf(w, d.y, ui);
         am = fmaf(w, sqrtf(d.x * d.x + d.y * d.y), am);
     }
-    const float2 phi = retilt(__ldg(&a.h_t[t]), st, r, a.win, a.ny, a.nx, a.tilt_sign);
+    const float2 phi = retilt(__ldg(&a.h_t[t]), st, r, a.win, a.wo, a.ny, a.nx, a.tilt_sign);
     const float2 sb = a.Sbar[((size_t)bs * a.sbar_rows + t) * a.K + r];
     // Ebar = Sbar conj(phi)
     const float2 eb = make_float2(sb.x * phi.x + sb.y * phi.y, sb.y * phi.x - sb.x * phi.y);
@@ -243,7 +247,10 @@ __global__ void recon_adj_parent_kernel(ReconAdjArgs a) {
     const int p = blockIdx.y, bs = blockIdx.z;
     if (r >= a.K || p >= a.Bp) return;
     const int site = a.site_ids[bs];
-    const float2 d = __ldg(&a.stash[((size_t)site * a.Bp + p) * a.K + r]);
+    const size_t sk = (size_t)a.stash_win * a.stash_win;
+    const int ru = r / a.win;
+    const size_t sidx = ((size_t)site * a.Bp + p) * sk + (size_t)(ru + a.wo) * a.stash_win + (r - ru * a.win) + a.wo;
+    const float2 d = __ldg(&a.stash[sidx]);
     const float md = sqrtf(d.x * d.x + d.y * d.y);
     const float2 unit = md > 0.f ? make_float2(d.x / md, d.y / md) : make_float2(0.f, 0.f);
     float sx = 0.f, sy = 0.f;
@@ -256,7 +263,7 @@ __global__ void recon_adj_parent_kernel(ReconAdjArgs a) {
         sx = fmaf(w, fmaf(h, unit.x, ub.x), sx);
         sy = fmaf(w, fmaf(h, unit.y, ub.y), sy);
     }
-    a.dtbar[((size_t)site * a.Bp + p) * a.K + r] = make_float2(sx, sy);
+    a.dtbar[sidx] = make_float2(sx, sy);
 }
 
 __global__ void s1bar_kernel(const int32_t* ids, const SiteDev* sites, int B, int K, const float2* H, const float2* T,
@@ -299,6 +306,7 @@ cudaError_t bip_gv_reduce(const float* part, int groups, int G, float* gV, cudaS
 
 cudaError_t bip_recon_adjoint(const ReconAdjArgs& a, cudaStream_t s) {
     if (a.n_sites < 1 || a.n_targets < 1 || a.Bp < 1 || a.K < 1) return cudaErrorInvalidValue;
+    if (a.K != a.win * a.win || a.wo < 0 || a.win + 2 * a.wo != a.stash_win) return cudaErrorInvalidValue;
     if (a.n_targets > 65535 || a.Bp > 65535 || a.n_sites > 65535) return cudaErrorInvalidValue;
     recon_adj_target_kernel<<<dim3((a.K + 255) / 256, a.n_targets, a.n_sites), 256, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();

@@ -60,6 +60,7 @@ struct bip_ctx {
     int64_t h_elems = 0;                // complex elements of H the sites read
     int op_k = 0;                       // row pitch of the coupling operands' current contents
     int xop_k = 0;                      // ... and of the cube's own operands (xopA, xopB)
+    int gop_k = 0;                      // ... and of the reverse pass's per-pixel workspaces
     uint64_t sig1 = 0, sig2 = 0;        // site-list signatures of the builds
     bool s1 = false, s2 = false;
 
@@ -2688,7 +2689,6 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
                              void* stream) {
     bip_status st = check_map_args(c, H, scan_px, P, dL_dI);
     if (st != BIP_OK) return st;
-    if (c->uneven) return fail(c, BIP_ERR_UNSUPPORTED, "the reverse pass takes every site at the context's window");
     if (d_V && !V) return fail(c, BIP_ERR_INVALID_ARG, "d_V needs the V the matrices were built from");
     if ((reinterpret_cast<uintptr_t>(d_H) & 7) != 0) return fail(c, BIP_ERR_INVALID_ARG, "d_H must be 8-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
@@ -2759,7 +2759,13 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
     CUDA_TRY(c, ensure(c->g_D, (size_t)SB * B * sizeof(double2), false, s));
     CUDA_TRY(c, ensure(c->g_Dsum, (size_t)B * sizeof(double2), false, s));
     CUDA_TRY(c, cudaMemsetAsync(c->g_Dsum.p, 0, (size_t)B * sizeof(double2), s));
-    if (d_H) CUDA_TRY(c, cudaMemsetAsync(d_H, 0, (size_t)c->n_ch_total * K * sizeof(float2), s));
+    if (d_H) CUDA_TRY(c, cudaMemsetAsync(d_H, 0, (size_t)c->h_elems * sizeof(float2), s));
+    // window adjoints of sites with smaller windows than the stash: zero
+    // outside their block (the sweeps inject the whole stashed window)
+    if (d_V && c->uneven) {
+        CUDA_TRY(c, cudaMemsetAsync(c->g_dt1.p, 0, (size_t)c->n_sites * geo.Bp1 * K * sizeof(float2), s));
+        CUDA_TRY(c, cudaMemsetAsync(c->g_dt2.p, 0, (size_t)c->n_sites * geo.Bp2 * K * sizeof(float2), s));
+    }
     GradArgs ga{};
     ga.P = P; ga.K = K; ga.B = B;
     ga.scans = (const double*)c->scans_d.p;
@@ -2768,22 +2774,40 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
     ga.sites = (const SiteDev*)c->sites_d.p;
     ga.ny = g.ny; ga.nx = g.nx; ga.fy = g.fy; ga.fx = g.fx;
     ga.scale = (double)det_scale(c);
-    for (int b0 = 0; b0 < c->n_sites; b0 += SB) {
-        const int nb = std::min(SB, c->n_sites - b0);
+    for (const auto& bt : map_batches(c, SB)) {
+        const int b0 = bt.first, nb = bt.second;
         const int32_t* ids = (const int32_t*)c->seq_ids_d.p + b0;
-        GatherArgs g2 = gather_args(c, 2, ids, nb);
+        // the batch's window (one size per batch): every per-pixel buffer at
+        // pitch K = w^2, shadowing the context-wide sizes the workspaces were
+        // allocated for; a pitch change clears them first (their padding
+        // rows must read as zero)
+        const int wb = c->sites[c->batch_order[b0]].w;
+        const int K = wb * wb;
+        const size_t perA = (size_t)Dpad * K, perB = (size_t)nch * Bpad * K, perS1 = (size_t)Bpad * K;
+        const size_t perT = (size_t)nch * Bpad * K, perS2bar = (size_t)(tcg ? D128 : Dpad) * K;
+        st = operand_layout(c, K, s);
+        if (st != BIP_OK) return st;
+        if (c->gop_k != K) {
+            if (c->gop_k != 0)
+                for (DevBuf* b : {&c->g_s1, &c->g_T, &c->g_tB, &c->g_sB2, &c->g_s1bar, &c->g_s2bar, &c->g_ubar, &c->g_dA})
+                    if (b->p) CUDA_TRY(c, cudaMemsetAsync(b->p, 0, b->cap, s));
+            c->gop_k = K;
+        }
+        GradArgs gab = ga;
+        gab.K = K;
+        GatherArgs g2 = gather_args(c, 2, ids, nb, wb);
         g2.rows_pad = Dpad;
         g2.out_c64 = (float2*)c->opA32.p;
         g2.site_stride = (int64_t)perA;
         CUDA_TRY(c, bip_gather(g2, s));
-        GatherArgs g1 = gather_args(c, 1, ids, nb);
+        GatherArgs g1 = gather_args(c, 1, ids, nb, wb);
         g1.rows_pad = Bpad;
         g1.nch = nch;
         g1.H = (const float2*)H;
         g1.out_c64 = (float2*)c->opB32.p;
         g1.site_stride = (int64_t)perB;
         CUDA_TRY(c, bip_gather(g1, s));
-        GatherArgs g0 = gather_args(c, 1, ids, nb);
+        GatherArgs g0 = gather_args(c, 1, ids, nb, wb);
         g0.rows_pad = Bpad;
         g0.out_c64 = (float2*)c->g_s1.p;
         g0.site_stride = (int64_t)perS1;
@@ -2828,7 +2852,7 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
             CUDA_TRY(c, bip_cgemm_simt(A, s));
         }
         // R_tau = f o_tau sum_{rho in crop} g c c^H
-        CUDA_TRY(c, bip_grad_crop_weights(ga, nb, ids, (float*)c->g_w.p, s));
+        CUDA_TRY(c, bip_grad_crop_weights(gab, nb, ids, (float*)c->g_w.p, s));
         CGemmGen r{};
         r.M = B; r.N = B; r.K = P; r.batch = nb;
         r.A = (const float2*)c->illum.p; r.sam = P; r.sak = 1; r.sab = 0;
@@ -2898,7 +2922,7 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
                 }
             }
             if (d_H)
-                CUDA_TRY(c, bip_grad_h(ga, nb, ids, nch, (const float2*)c->g_s1.p, (int64_t)perS1,
+                CUDA_TRY(c, bip_grad_h(gab, nb, ids, nch, (const float2*)c->g_s1.p, (int64_t)perS1,
                                        (const float2*)c->g_T.p, (int64_t)perT, (int64_t)Bpad * K, (float2*)d_H, s));
         }
         if (d_V) {
@@ -2954,7 +2978,9 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
                 ra.n_sites = nb;
                 ra.site_ids = ids;
                 ra.sites = (const SiteDev*)c->sites_d.p;
-                ra.K = K; ra.win = g.win; ra.ny = g.ny; ra.nx = g.nx;
+                ra.K = K; ra.win = wb; ra.ny = g.ny; ra.nx = g.nx;
+                ra.stash_win = g.win;
+                ra.wo = (g.win - wb) / 2;
                 ra.magnitude = g.recon == BIP_RECON_MAGNITUDE;
                 if (side == 1) {
                     ra.Bp = geo.Bp1; ra.n_targets = B; ra.tilt_sign = +1;

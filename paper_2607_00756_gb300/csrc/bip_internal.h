@@ -507,16 +507,17 @@ struct ReconAdjArgs {
     int n_sites;                    // batch
     const int32_t* site_ids;
     const SiteDev* sites;
-    int K, win, ny, nx, Bp, n_targets;
+    int K, win, ny, nx, Bp, n_targets;   // win: the batch's window, K = win^2
+    int stash_win, wo;              // the stashed windows' size; offset of the batch's window
     int magnitude, tilt_sign;
     const int2* h_t;
-    const float2* stash;            // [n_sites_total][Bp][K]
+    const float2* stash;            // [n_sites_total][Bp][stash_win^2]
     AdjWeights w;
     const float2* Sbar;             // [bs][rows][K] dL/dS*, row stride sbar_rows
     int sbar_rows;
     float2* Ubar;                   // scratch [bs][n_targets][K]
     float* dA;                      // scratch [bs][n_targets][K]
-    float2* dtbar;                  // out [n_sites_total][Bp][K] (overwritten for the batch's sites)
+    float2* dtbar;                  // out [n_sites_total][Bp][stash_win^2]: the batch's sites' blocks
 };
 cudaError_t bip_recon_adjoint(const ReconAdjArgs& a, cudaStream_t s);
 // S1bar[bs][b][r] = sum_n conj H_n(r) T[bs][n][b][r]

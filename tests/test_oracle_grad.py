@@ -136,3 +136,43 @@ def test_linear_loss_occupancy_is_partials(case):
     _, g = og.gradients(pr, par, dL_dI=gI)
     _, fw = og.forward(pr, par, keep=True)
     assert np.allclose(g["occ"], fw["partials"] @ gI, rtol=1e-13, atol=0.0)
+
+
+def test_site_windows_reverse_pass():
+    """The reverse pass with the sites' own crop windows (a 16-px window
+    inside the context's 32 px, the other site at 32 px): the slice-potential
+    and transition-potential derivatives against central differences, and
+    the H derivative shaped like each site's own window."""
+    cfg = synth.config1().replace(name="grad_win", ny=64, nx=64, ly=5.0, lx=5.0, nz=4, cells_y=2, cells_x=2,
+                                  win=32, fy=2, fx=2, ion_slices=(1, 3), ion_cells=(0, 1), defocus=30.0, cs=2.0e5,
+                                  scan_y=(10.0, 6.0, 4), scan_x=(12.0, 5.0, 4))
+    sp = synth.make_specimen(cfg)
+    site_win = [16, 32]
+    parts, _, _ = synth.site_window_inputs(sp, site_win)
+    pr = obip.make_problem(sp, site_win=site_win, H=parts)
+    rng = np.random.default_rng(21)
+    par = og.Params(pr)
+    par.occ = 1.0 + 0.2 * rng.standard_normal(len(pr.ion))
+    I0 = og.forward(pr, par)
+    target = I0 * (1.0 + 0.1 * rng.standard_normal(I0.shape))
+    _, g = og.gradients(pr, par, target)
+    assert [h.shape[1] for h in g["H"]] == site_win
+    for j in (1, 2):
+        D = np.zeros_like(par.V)
+        D[j] = cfg.atom_peak * rng.standard_normal(D[j].shape)
+
+        def s(p, d, D=D):
+            p.V += d * D
+        close(central(pr, par, target, s), float(np.sum(g["V"] * D)), 1e-6)
+    for k in range(len(pr.ion)):
+        E = rng.standard_normal(pr.H[k].shape) + 1j * rng.standard_normal(pr.H[k].shape)
+        H0 = pr.H[k].copy()
+
+        def L_at(e):
+            pr.H[k] = H0 + e * E
+            try:
+                return og.loss(pr, par, target)
+            finally:
+                pr.H[k] = H0
+        fd = (L_at(H_STEP) - L_at(-H_STEP)) / (2.0 * H_STEP)
+        close(fd, float(np.real(np.sum(np.conj(g["H"][k]) * E))), 1e-6)
