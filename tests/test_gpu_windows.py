@@ -240,3 +240,48 @@ def test_own_windows_reverse_pass(lib, prec):
     wH = np.concatenate([h.reshape(-1) for h in want["H"]])
     assert rel(got["H"].cpu().numpy(), wH) < 1e-4
     ctx.close()
+
+
+def test_own_windows_under_a_graph(lib):
+    """A context whose sites have their own windows inside a CUDA graph of
+    several specimens (one stream each): every replay equals the eager maps
+    bit for bit, and the windows' map matches the oracle."""
+    from paper_2607_00756_gb300.graphs import GraphedMaps
+    dev = torch.device("cuda:0")
+    cfg, sp, w = case("mix")
+    _, flat, _ = synth.site_window_inputs(sp, w)
+    a = built(lib, cfg, sp, "mixed")
+    a.set_site_windows(w)
+    Ha = torch.tensor(flat, dtype=torch.complex64, device=dev)
+    cfg1, sp1, _ = case("config1")
+    b = built(lib, cfg1, sp1, "fp32")
+    Hb = torch.tensor(sp1.H, dtype=torch.complex64, device=dev)
+    eager = [a.map(Ha, sp.scans).cpu().numpy(), b.map(Hb, sp1.scans).cpu().numpy()]
+    g = GraphedMaps([(a, Ha, sp.scans), (b, Hb, sp1.scans)], concurrent=True)
+    for _ in range(3):
+        outs = g.replay()
+        torch.cuda.synchronize()
+        g.check()
+        for o, e in zip(outs, eager):
+            assert np.array_equal(o.cpu().numpy(), e)
+    assert rel(eager[0], oracle_own("mix").map) < 1e-3
+    a.close()
+    b.close()
+
+
+def test_own_windows_on_a_3m_grid(lib):
+    """Own windows on a 192^2 grid at f = 3 (the radix-3 multislice and the
+    modular table indices), FP32 and mixed, against the oracle."""
+    cfg = synth.config1().replace(name="f3win", ny=192, nx=192, ly=15.0, lx=15.0, cells_y=6, cells_x=6, fy=3,
+                                  fx=3, ion_cells=(2, 4), ion_slices=(2, 3), scan_y=(90.5, 3.0, 7),
+                                  scan_x=(91.75, 3.5, 6))
+    sp = synth.make_specimen(cfg)
+    w = [48, 64, 32, 16]
+    parts, flat, _ = synth.site_window_inputs(sp, w)
+    ref = obip.bip_map(obip.make_problem(sp, site_win=w, H=parts))
+    for prec, tol in (("fp32", 1e-4), ("mixed", 1e-3)):
+        ctx = built(lib, cfg, sp, prec)
+        ctx.set_site_windows(w)
+        H = torch.tensor(flat, dtype=torch.complex64, device="cuda:0")
+        assert rel(ctx.map(H, sp.scans).cpu().numpy(), ref.map) < tol
+        ctx.close()
