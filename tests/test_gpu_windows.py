@@ -285,3 +285,33 @@ def test_own_windows_on_a_3m_grid(lib):
         H = torch.tensor(flat, dtype=torch.complex64, device="cuda:0")
         assert rel(ctx.map(H, sp.scans).cpu().numpy(), ref.map) < tol
         ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("mixed", 1e-3), ("split_bf16", 1e-4)])
+def test_two_edges_in_one_map(lib, prec, tol):
+    """Two edges in one specimen: alternate sites keep nine channels
+    (m = -4..4) on the 64-px window, the others one channel (m = 0) on a
+    32-px window of their own -- uneven channel counts and windows in the
+    same batches -- against the oracle."""
+    cfg = synth.config1().replace(name="two_edges", channels=tuple(range(-4, 5)))
+    sp = synth.make_specimen(cfg)
+    ion = np.nonzero(sp.nch > 0)[0]
+    nch = sp.nch.copy()
+    parts, w = [], []
+    for k, a in enumerate(ion.tolist()):
+        h = sp.H[9 * k:9 * (k + 1)]
+        if k % 2:
+            nch[a] = 1
+            parts.append(h[4:5, 16:48, 16:48].copy())
+            w.append(32)
+        else:
+            parts.append(h.copy())
+            w.append(64)
+    sp2 = synth.Specimen(cfg=cfg, atoms=sp.atoms, nch=nch, V=sp.V, H=sp.H, scans=sp.scans)
+    ref = obip.bip_map(obip.make_problem(sp2, site_win=w, H=parts))
+    ctx = built(lib, cfg, sp2, prec)
+    ctx.set_site_windows(w)
+    H = torch.tensor(np.concatenate([p.reshape(-1) for p in parts]), dtype=torch.complex64, device="cuda:0")
+    assert rel(ctx.map(H, sp.scans).cpu().numpy(), ref.map) < tol
+    assert rel(ctx.sites(H, sp.scans).cpu().numpy(), ref.partials) < tol
+    ctx.close()
