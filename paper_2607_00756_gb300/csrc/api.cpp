@@ -1382,6 +1382,9 @@ std::vector<std::pair<int, int>> map_batches(const bip_ctx* c, int SB) {
     return out;
 }
 
+bip_status raster_cube_setup(bip_ctx* c, const double* scans, int P, int SB, int nd_pad, int64_t m_b, int64_t m_ch,
+                             int64_t m_site, int64_t cube_ld, float scale, CubeRasterArgs& cra, bool& sep,
+                             cudaStream_t s);
 // The map, its per-site contributions, or the 4D cube (cube_out [P][n_det]):
 // the reconstruction and the coupling are shared, then either the Gram
 // matrix and the scan polynomial or the per-beam contraction.
@@ -1555,7 +1558,17 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
 
     // the cube on tcgen05: c_b(rho) as split planes [4][crow][Bpad] once, and
     // work lists of (site in batch, scan tile meeting its crop mask)
-    const bool cube_tc = (cube_out || beam || probe) && tc;
+    // the per-beam cube of qEELS on a raster scan list: the separated
+    // contraction of cube_raster.cu instead of the cube kernel
+    CubeRasterArgs cra{};
+    bool sepq = false;
+    if (cube_out) {
+        bip_status st = raster_cube_setup(c, scans, P, SB, Dpad, tc ? (int64_t)Dpad : (int64_t)nch * Dpad,
+                                          tc ? (int64_t)Bpad * Dpad : (int64_t)Dpad, (int64_t)perMt, geo.n_det,
+                                          (float)det_scale(c), cra, sepq, s);
+        if (st != BIP_OK) return st;
+    }
+    const bool cube_tc = (cube_out || beam || probe) && tc && !sepq;
     // scans per tile of the cube kernel (its MMA's N) for the cube and the
     // beam order: 128 once there are that many scans, else 64; the probe
     // order's last contraction keeps 64
@@ -1835,6 +1848,16 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
                 A.out32_ld = Dpad;
             }
             TIMED(c, BIP_STAGE_COUPLING, s, bip_tc_gemm(A, s));
+            if (sepq) {
+                CubeRasterArgs r = cra;
+                r.n_sites = nb;
+                r.site_ids = ids;
+                r.m = (const float2*)c->mt32.p;
+                r.nd = geo.n_det;
+                r.cube = cube_out;
+                TIMED(c, BIP_STAGE_QUADFORM, s, bip_cube_raster(r, s));
+                continue;
+            }
             if (cube_out || beam) {
                 // A = M transposed to rows d, K = (ch, b), as split planes; then
                 // the per-beam contraction and |.|^2 channel sum on tcgen05
@@ -1917,6 +1940,16 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
             A.C = (float2*)c->mt32.p; A.ldc = (int64_t)nch * Dpad; A.strideC = (int64_t)perMt;
             A.ep_B = Bpad; A.ep_Dp = Dpad;
             TIMED(c, BIP_STAGE_COUPLING, s, bip_cgemm_simt(A, s));
+            if (sepq) {
+                CubeRasterArgs r = cra;
+                r.n_sites = nb;
+                r.site_ids = ids;
+                r.m = (const float2*)c->mt32.p;
+                r.nd = geo.n_det;
+                r.cube = cube_out;
+                TIMED(c, BIP_STAGE_QUADFORM, s, bip_cube_raster(r, s));
+                continue;
+            }
             if (cube_out) {
                 CubeArgs ca = cube_args(c, ids, nb, P, cube_out);
                 ca.m32 = (const float2*)c->mt32.p;
@@ -1993,6 +2026,79 @@ bip_status run_map(bip_ctx* c, const void* H, const double* scans, int32_t P, fl
     return BIP_OK;
 }
 
+// Setup of the cube's separated per-beam contraction on a raster scan list
+// (cube_raster.cu): the raster test, the phase tables per scan row and
+// column (angles reduced in FP64), each site's crop per axis as bits (the
+// FP64 test of in_crop, one axis at a time), and the stage-1 workspace T
+// for batches of SB sites and nd_pad beams.  M(n, b, d) of a batch lies at
+// m[bs m_site + b m_b + n m_ch + d].  sep is false, and nothing is set up,
+// when the scans are no raster or the lattice is too large for the kernels.
+bip_status raster_cube_setup(bip_ctx* c, const double* scans, int P, int SB, int nd_pad, int64_t m_b, int64_t m_ch,
+                             int64_t m_site, int64_t cube_ld, float scale, CubeRasterArgs& cra, bool& sep,
+                             cudaStream_t s) {
+    const bip_config& g = c->cfg;
+    const Raster rr = detect_raster(scans, P);
+    const int nky = 2 * c->Ky + 1, nkx = 2 * c->Kx + 1;
+    // (stage 2 prefetches a tile of nky x 64 values with 8 per thread: nky <= 32)
+    sep = rr.ok && nky <= 32 && nkx <= 128 && (size_t)nkx * (rr.Mx + 32) * 8 <= 200 * 1024;
+    if (!sep) return BIP_OK;
+    const int nch = c->nch_max;
+    std::vector<double> ry(rr.My), rx(rr.Mx);
+    for (int my = 0; my < rr.My; ++my) ry[my] = scans[2 * (size_t)my * rr.Mx];
+    for (int mx = 0; mx < rr.Mx; ++mx) rx[mx] = scans[2 * (size_t)mx + 1];
+    std::vector<float2> ay((size_t)rr.My * nky), ax((size_t)nkx * rr.Mx);
+    for (int my = 0; my < rr.My; ++my)
+        for (int iy = 0; iy < nky; ++iy)
+            ay[(size_t)my * nky + iy] = turn_d(-(double)g.fy * (iy - c->Ky) * ry[my] / g.ny);
+    for (int ix = 0; ix < nkx; ++ix)
+        for (int mx = 0; mx < rr.Mx; ++mx)
+            ax[(size_t)ix * rr.Mx + mx] = turn_d(-(double)g.fx * (ix - c->Kx) * rx[mx] / g.nx);
+    auto axis = [](double r, double t, int n, int f) {
+        double d = r - t;
+        d -= n * std::floor((d + 0.5 * n) / n);
+        const double h = 0.5 * n / f;
+        return d >= -h && d < h;
+    };
+    const int wy = (rr.My + 31) / 32, wx = (rr.Mx + 31) / 32;
+    std::vector<uint32_t> cy((size_t)c->n_sites * wy, 0u), cx((size_t)c->n_sites * wx, 0u);
+    for (int k = 0; k < c->n_sites; ++k) {
+        const SiteDev& sd = c->sites[k];
+        for (int my = 0; my < rr.My; ++my)
+            if (axis(ry[my], sd.ty, g.ny, g.fy)) cy[(size_t)k * wy + my / 32] |= 1u << (my % 32);
+        for (int mx = 0; mx < rr.Mx; ++mx)
+            if (axis(rx[mx], sd.tx, g.nx, g.fx)) cx[(size_t)k * wx + mx / 32] |= 1u << (mx % 32);
+    }
+    CUDA_TRY(c, upload(c->cr_cy, cy, s));
+    CUDA_TRY(c, upload(c->cr_cx, cx, s));
+    CUDA_TRY(c, upload(c->cr_ay, ay, s));
+    CUDA_TRY(c, upload(c->cr_ax, ax, s));
+    cra = CubeRasterArgs{};
+    cra.crop_y = (const uint32_t*)c->cr_cy.p;
+    cra.crop_x = (const uint32_t*)c->cr_cx.p;
+    cra.wy = wy;
+    cra.wx = wx;
+    cra.nch = nch;
+    cra.nd_pad = nd_pad;
+    cra.nky = nky;
+    cra.nkx = nkx;
+    cra.lat = (const int32_t*)c->lat_d.p;
+    cra.coef = (const double2*)c->coef.p;
+    cra.ay = (const float2*)c->cr_ay.p;
+    cra.ax = (const float2*)c->cr_ax.p;
+    cra.My = rr.My;
+    cra.Mx = rr.Mx;
+    cra.n_sites = SB;
+    CUDA_TRY(c, ensure(c->cr_T, bip_cube_raster_t_bytes(cra), false, s));
+    cra.T = (float2*)c->cr_T.p;
+    cra.cube_ld = cube_ld;
+    cra.scale = scale;
+    cra.sites = (const SiteDev*)c->sites_d.p;
+    cra.m_site = m_site;
+    cra.m_b = m_b;
+    cra.m_ch = m_ch;
+    return BIP_OK;
+}
+
 // The energy-filtered 4D cube (Sec. 2.2.6, Algorithm 3): S1 partitioned
 // (the context's S1 stash, rebuilt on each window), the exit side exact on
 // the complete basis: batches of the cube's beams are taken back from the
@@ -2049,70 +2155,14 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
     if (tc) CUDA_TRY(c, cudaMemsetAsync(c->errflag.p, 0, sizeof(int), s));
 
     // On a raster scan list the per-beam contraction separates over the
-    // aperture beams' lattice (cube_raster.cu): phase tables per scan row and
-    // column, angles reduced in FP64, and the stage-1 workspace T.
-    const Raster rr = detect_raster(scans, P);
-    const int nky = 2 * c->Ky + 1, nkx = 2 * c->Kx + 1;
-    // (stage 2 prefetches a tile of nky x 64 values with 8 per thread: nky <= 32)
-    const bool sep = rr.ok && nky <= 32 && nkx <= 128 && (size_t)nkx * (rr.Mx + 32) * 8 <= 200 * 1024;
+    // aperture beams' lattice (cube_raster.cu)
     CubeRasterArgs cra{};
-    if (sep) {
-        std::vector<double> ry(rr.My), rx(rr.Mx);
-        for (int my = 0; my < rr.My; ++my) ry[my] = scans[2 * (size_t)my * rr.Mx];
-        for (int mx = 0; mx < rr.Mx; ++mx) rx[mx] = scans[2 * (size_t)mx + 1];
-        std::vector<float2> ay((size_t)rr.My * nky), ax((size_t)nkx * rr.Mx);
-        for (int my = 0; my < rr.My; ++my)
-            for (int iy = 0; iy < nky; ++iy)
-                ay[(size_t)my * nky + iy] = turn_d(-(double)g.fy * (iy - c->Ky) * ry[my] / g.ny);
-        for (int ix = 0; ix < nkx; ++ix)
-            for (int mx = 0; mx < rr.Mx; ++mx)
-                ax[(size_t)ix * rr.Mx + mx] = turn_d(-(double)g.fx * (ix - c->Kx) * rx[mx] / g.nx);
-        // each site's crop per axis as bits (the FP64 test of in_crop, one
-        // axis at a time: the mask is the product of the two)
-        auto axis = [](double r, double t, int n, int f) {
-            double d = r - t;
-            d -= n * std::floor((d + 0.5 * n) / n);
-            const double h = 0.5 * n / f;
-            return d >= -h && d < h;
-        };
-        const int wy = (rr.My + 31) / 32, wx = (rr.Mx + 31) / 32;
-        std::vector<uint32_t> cy((size_t)c->n_sites * wy, 0u), cx((size_t)c->n_sites * wx, 0u);
-        for (int k = 0; k < c->n_sites; ++k) {
-            const SiteDev& sd = c->sites[k];
-            for (int my = 0; my < rr.My; ++my)
-                if (axis(ry[my], sd.ty, g.ny, g.fy)) cy[(size_t)k * wy + my / 32] |= 1u << (my % 32);
-            for (int mx = 0; mx < rr.Mx; ++mx)
-                if (axis(rx[mx], sd.tx, g.nx, g.fx)) cx[(size_t)k * wx + mx / 32] |= 1u << (mx % 32);
-        }
-        CUDA_TRY(c, upload(c->cr_cy, cy, s));
-        CUDA_TRY(c, upload(c->cr_cx, cx, s));
-        cra.crop_y = (const uint32_t*)c->cr_cy.p;
-        cra.crop_x = (const uint32_t*)c->cr_cx.p;
-        cra.wy = wy;
-        cra.wx = wx;
-        CUDA_TRY(c, upload(c->cr_ay, ay, s));
-        CUDA_TRY(c, upload(c->cr_ax, ax, s));
-        cra.nch = nch;
-        cra.nd_pad = Dpb;
-        cra.nky = nky;
-        cra.nkx = nkx;
-        cra.lat = (const int32_t*)c->lat_d.p;
-        cra.coef = (const double2*)c->coef.p;
-        cra.ay = (const float2*)c->cr_ay.p;
-        cra.ax = (const float2*)c->cr_ax.p;
-        cra.My = rr.My;
-        cra.Mx = rr.Mx;
-        cra.n_sites = SB;
-        CUDA_TRY(c, ensure(c->cr_T, bip_cube_raster_t_bytes(cra), false, s));
-        cra.T = (float2*)c->cr_T.p;
-        cra.cube_ld = n_cube;
-        cra.scale = 1.0f;
-        cra.sites = (const SiteDev*)c->sites_d.p;
-        if (tc) {   // M from the coupling as complex64 rows (ch, b), columns d
-            cra.m_site = (int64_t)perMt; cra.m_b = Dpb; cra.m_ch = (int64_t)Bpad * Dpb;
-        } else {    // Mt[b][ch Dp + d]
-            cra.m_site = (int64_t)perMt; cra.m_b = (int64_t)nch * Dpb; cra.m_ch = Dpb;
-        }
+    bool sep = false;
+    {
+        bip_status st = raster_cube_setup(c, scans, P, SB, Dpb, tc ? (int64_t)Dpb : (int64_t)nch * Dpb,
+                                          tc ? (int64_t)Bpad * Dpb : (int64_t)Dpb, (int64_t)perMt, n_cube, 1.0f,
+                                          cra, sep, s);
+        if (st != BIP_OK) return st;
     }
 
     // tcgen05 per-beam contraction: c_b(rho) as split planes, and work items

@@ -328,6 +328,26 @@ def test_qeels_config1(lib, axis, prec):
     assert rel(m, obip.bip_map(pr).map) < tol
 
 
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_qeels_raster_and_any_scan_order_agree(lib, prec):
+    """qEELS on the raster scans (the per-beam terms by the separated
+    contraction) and on the same scans shuffled (the cube kernel): each
+    against the oracle and against each other row for row."""
+    cfg = synth.config1().replace(dfx=1)
+    sp = synth.make_specimen(cfg)
+    pr = obip.make_problem(sp)
+    _, want = obip.bip_qeels(pr, 1)
+    ctx, m, _, H = gpu_run(lib, cfg, sp, prec=prec)
+    _, q_r = ctx.qeels(H, sp.scans, 1)
+    perm = np.random.default_rng(6).permutation(len(sp.scans))
+    _, q_p = ctx.qeels(H, sp.scans[perm], 1)
+    q_r, q_p = q_r.cpu().numpy(), q_p.cpu().numpy()
+    tol = 1e-4 if prec == "fp32" else 1e-3
+    assert rel(q_r, want) < tol
+    assert rel(q_p, want[perm]) < tol
+    assert rel(q_p, q_r[perm]) < tol
+
+
 def test_qeels_refuses_a_subsampled_axis(lib, c1):
     from paper_2607_00756_gb300.capi import BipError, STATUS
     cfg, sp, pr, ref = c1
