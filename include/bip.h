@@ -227,8 +227,13 @@ bip_status bip_coreloss_sites(bip_ctx* ctx, const void* H, const double* scan_px
  *   H, scan_px as bip_coreloss_map.
  *   cube_out [P, n_cube] float32 device, overwritten; beams in the order of
  *            bip_cube_beams.
- * Precisions: FP32 (SIMT), SPLIT_BF16 and MIXED (tcgen05); FP8 contexts
- * return BIP_ERR_UNSUPPORTED.  BIP_ERR_OOM when not even 32 beams fit.
+ * Precisions: the coupling M in the context's precision -- FP32 (SIMT),
+ * SPLIT_BF16 and MIXED (tcgen05); FP8 contexts return BIP_ERR_UNSUPPORTED.
+ * The per-beam sum over b: on a raster scan list (scan p = my Mx + mx at
+ * (ry[my], rx[mx])) separated over the aperture beams' lattice, two short
+ * FP32 sums (c_b(rho) factorises over the axes); on any other list in the
+ * context's precision (tcgen05, or FP32 SIMT).  The same holds for qEELS.
+ * BIP_ERR_OOM when not even 32 beams fit.
  * bip_cube_beams: n_cube and (h, nullable host int32 [n_cube, 2]) the
  *   basis's beams (h_y, h_x), ordered by (h_y, h_x).  Host only. */
 bip_status bip_coreloss_cube(bip_ctx* ctx, const float* V, const void* H, const double* scan_px,
