@@ -21,6 +21,7 @@ workload on this machine's host cores (there is no runnable reference
 implementation of the paper).
 """
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -1050,6 +1051,10 @@ def main():
         line["orders"] = run_orders(cfg, sp)
         line["precision"] = run_precision()
     line["e2e"] = res.get("e2e")
+    live, peak = capi.bip_mem_stats()
+    line["memory"] = {"library_peak_gb": round(peak / 1e9, 3),
+                      "torch_peak_gb": round(torch.cuda.max_memory_allocated() / 1e9, 3),
+                      "scope": "high-water marks over the whole run (every path and line above)"}
     line["gpu_launches"] = res["launches"]
     line["clocks"] = res["clocks"]
     if args.cpu and world == 1:
@@ -1081,6 +1086,7 @@ def config_block(cfg, sp, order="gram"):
                         f"{len(sp.scans)} scans, 0-{cfg.theta_det * 1e3:.0f} mrad detector",
             "sites": n_sites, "scans": len(sp.scans), "grid": [cfg.ny, cfg.nx], "slices": cfg.nz,
             "window": cfg.win, "recon": cfg.recon, "order": order,
+            "hash": hashlib.sha1(repr(cfg).encode()).hexdigest()[:16],
             "l2": "256 MB buffer written between timed steps; working set (6.4 GB stash) >> L2"}
 
 

@@ -56,7 +56,9 @@ typedef enum {
     BIP_ERR_OOM = 3,           /* a device or host allocation failed          */
     BIP_ERR_CUDA = 4,          /* a CUDA call failed (text in bip_last_error) */
     BIP_ERR_TIMEOUT = 5,       /* a device-side wait gave up                  */
-    BIP_ERR_UNSUPPORTED = 6    /* valid request this build does not implement */
+    BIP_ERR_UNSUPPORTED = 6,   /* valid request this build does not implement */
+    BIP_ERR_NUMERIC = 7        /* an output holds NaN or Inf (only with
+                                  bip_set_check_finite on)                    */
 } bip_status;
 
 typedef enum {
@@ -154,6 +156,27 @@ bip_status bip_get_geometry(const bip_ctx* ctx, int32_t* h_beam, int32_t* h_det,
 
 /* Copies the configuration the context was created with to *out. */
 bip_status bip_get_config(const bip_ctx* ctx, bip_config* out);
+
+/* On-disk cache of the host geometry (the natural-neighbour weights depend
+ * only on the aperture, the detector and the rings, so, as in the paper's
+ * Sec. 2.2.3, they are computed once per such geometry): with a directory
+ * set, bip_create looks there for its geometry's file -- named by a 64-bit
+ * hash of the configuration fields the geometry reads (grid, cell, energy,
+ * angles, defocus, Cs, f, rings, detector subsampling, cube box) -- and
+ * reads it instead of recomputing, after checking its format version, the
+ * configuration fields stored in it and its checksum.  A missing file, or
+ * one that fails a check, is recomputed and written again (under a
+ * temporary name, then renamed into place).  A directory that cannot be
+ * written only costs the recomputation; bip_create's result is the same
+ * either way.
+ * bip_set_geometry_cache(dir): process-wide; NULL or "" turns the cache
+ *   off.  Until it is first called, the environment variable
+ *   BIP_GEOMETRY_CACHE (read once) names the directory.
+ * bip_geometry_cache_stats: since the process started, geometries read from
+ *   the cache (hits), computed and written with the cache on (misses), and
+ *   files that failed a check (rejected); any pointer may be NULL. */
+bip_status bip_set_geometry_cache(const char* dir);
+bip_status bip_geometry_cache_stats(int64_t* hits, int64_t* misses, int64_t* rejected);
 
 /* Chooses the contraction arithmetic for later bip_coreloss_* calls. */
 bip_status bip_set_precision(bip_ctx* ctx, int32_t prec);
@@ -374,6 +397,46 @@ bip_status bip_site_windows(bip_ctx* ctx, int32_t site, void* s1_out, void* s2_o
                             void* stream);
 bip_status bip_site_coupling(bip_ctx* ctx, const void* H, int32_t site, void* m_out,
                              void* stream);
+
+/* Saving and restoring the builds, so that maps can be rerun without the
+ * multislice: the map, the per-site and qEELS calls and the autotuner read
+ * only the window stashes, the site list, the geometry and H.
+ * bip_export_stash(ctx, which, dst, bytes): the whole stash of S1
+ *   (which = 1) or S2 (2), [n_sites, Bp, win, win] complex64 in site order
+ *   (per site the layout of bip_copy_stash), to dst -- device, pinned or
+ *   pageable host memory (the copy direction follows the pointers).  bytes
+ *   must equal the stash's size, n_sites * Bp * win * win * 8 (else
+ *   BIP_ERR_SHAPE, nothing copied).  A pageable dst is complete when the
+ *   call returns, others when the stream reaches the copy.
+ * bip_import_stash(ctx, which, atoms, n_atoms, src, bytes): the reverse.
+ *   It takes the site list from the atoms as bip_build_s<which> would,
+ *   checks bytes against that list (else BIP_ERR_SHAPE before any other
+ *   effect) and copies the stash in; afterwards the context is as after
+ *   bip_build_s<which> with those atoms.  The stash must come from a
+ *   context with the same configuration (geometry, window, grid), which the
+ *   library cannot check from the bytes: the caller keeps them together
+ *   (the Python binding stores the configuration with the stash and
+ *   compares it).  The source may be reused when the stream reaches the
+ *   copy (pageable host memory: when the call returns).
+ * Neither call may be captured into a CUDA graph (BIP_ERR_INVALID_ARG on a
+ * capturing stream). */
+bip_status bip_export_stash(bip_ctx* ctx, int32_t which, void* dst, int64_t bytes, void* stream);
+bip_status bip_import_stash(bip_ctx* ctx, int32_t which, const bip_atom* atoms, int32_t n_atoms,
+                            const void* src, int64_t bytes, void* stream);
+
+/* bip_set_check_finite(ctx, on): with on, bip_coreloss_map, _sites, _cube,
+ *   _qeels and _grad scan their outputs for NaN or infinite values once
+ *   they are computed and return BIP_ERR_NUMERIC (with the count in
+ *   bip_last_error) if any is found; the outputs are written either way.
+ *   The scan synchronises the stream, so with the check on these calls
+ *   refuse a capturing stream (BIP_ERR_INVALID_ARG).  Off by default.
+ * bip_mem_stats: bytes of device memory the library's contexts hold now
+ *   (every context's workspaces; bip_build_s1_noalloc's static array and
+ *   caller-owned buffers excluded) and the high-water mark since the
+ *   process started or the last reset (reset_peak != 0 sets it to the live
+ *   bytes after reading).  Either pointer may be NULL. */
+bip_status bip_set_check_finite(bip_ctx* ctx, int32_t on);
+bip_status bip_mem_stats(int64_t* live_bytes, int64_t* peak_bytes, int32_t reset_peak);
 
 /* Per-stage timing of the library's own kernels.  With profiling on, every
  * launch is bracketed by CUDA events recorded on the stream it runs on;

@@ -77,7 +77,7 @@ def build(verbose=False, force=False):
     objs = [o for _, o, _ in jobs]
     newest_obj = max(os.path.getmtime(o) for o in objs)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest_obj:
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB + ".tmp", *objs]
+        cmd = [nvcc, *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libbip.so")
 
 BIP_OK = 0
 STATUS = {0: "BIP_OK", 1: "BIP_ERR_INVALID_ARG", 2: "BIP_ERR_SHAPE", 3: "BIP_ERR_OOM",
-          4: "BIP_ERR_CUDA", 5: "BIP_ERR_TIMEOUT", 6: "BIP_ERR_UNSUPPORTED"}
+          4: "BIP_ERR_CUDA", 5: "BIP_ERR_TIMEOUT", 6: "BIP_ERR_UNSUPPORTED", 7: "BIP_ERR_NUMERIC"}
 PREC = {"fp32": 0, "split_bf16": 1, "mixed": 2, "fp8": 3}
 RECON = {"complex": 0, "magnitude": 1}
 
@@ -86,6 +86,12 @@ def _load():
         "bip_set_order": [VP, I32],
         "bip_set_aberrations": [VP, D, D, VP],
         "bip_coreloss_grad": [VP, VP, VP, P(D), I32, VP, VP, VP, P(D), VP, VP],
+        "bip_set_geometry_cache": [ctypes.c_char_p],
+        "bip_geometry_cache_stats": [P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)],
+        "bip_export_stash": [VP, I32, VP, ctypes.c_int64, VP],
+        "bip_import_stash": [VP, I32, P(BipAtom), I32, VP, ctypes.c_int64, VP],
+        "bip_set_check_finite": [VP, I32],
+        "bip_mem_stats": [P(ctypes.c_int64), P(ctypes.c_int64), I32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -292,6 +298,65 @@ def bip_debug_allocs():
     live, made = ctypes.c_int64(0), ctypes.c_int64(0)
     _check("bip_debug_allocs", None, _lib.bip_debug_allocs(ctypes.byref(live), ctypes.byref(made)))
     return live.value, made.value
+
+
+def bip_set_geometry_cache(directory):
+    """Directory of the on-disk geometry cache (None or "": off)."""
+    d = None if not directory else os.fsencode(directory)
+    _check("bip_set_geometry_cache", None, _lib.bip_set_geometry_cache(d))
+
+
+def bip_geometry_cache_stats():
+    """(hits, misses, rejected) of the geometry cache since the process started."""
+    v = [ctypes.c_int64(0) for _ in range(3)]
+    _check("bip_geometry_cache_stats", None, _lib.bip_geometry_cache_stats(*[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def _buffer(a, name):
+    """(pointer, bytes) of a contiguous complex64 CUDA tensor or host array."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.complex64 or not a.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous complex64 tensor")
+        return ctypes.c_void_p(a.data_ptr()), a.numel() * 8
+    if not isinstance(a, np.ndarray) or a.dtype != np.complex64 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{name} must be a C-contiguous complex64 array")
+    return a.ctypes.data_as(ctypes.c_void_p), a.nbytes
+
+
+def stash_shape(ctx, which):
+    """[n_sites, Bp, win, win] of the built stash `which` (1: S1, 2: S2)."""
+    _, _, bp1, bp2, n_sites = bip_query(ctx)
+    win = bip_get_config(ctx).win
+    return (n_sites, bp1 if which == 1 else bp2, win, win)
+
+
+def bip_export_stash(ctx, which, dst, stream=None):
+    """Whole stash of S1 (which=1) or S2 (2) into `dst` (CUDA tensor or host
+    array, complex64, exactly the stash's size)."""
+    ptr, nbytes = _buffer(dst, "dst")
+    _check("bip_export_stash", ctx, _lib.bip_export_stash(ctx, int(which), ptr, nbytes, _stream(stream)))
+    return dst
+
+
+def bip_import_stash(ctx, which, atoms_arr, src, stream=None):
+    """Restores a stash exported from a context of the same configuration,
+    for the sites of `atoms_arr`; afterwards S<which> counts as built."""
+    ptr, nbytes = _buffer(src, "src")
+    _check("bip_import_stash", ctx, _lib.bip_import_stash(ctx, int(which), atoms_arr, len(atoms_arr), ptr, nbytes,
+                                                           _stream(stream)))
+
+
+def bip_set_check_finite(ctx, on):
+    _check("bip_set_check_finite", ctx, _lib.bip_set_check_finite(ctx, 1 if on else 0))
+
+
+def bip_mem_stats(reset_peak=False):
+    """(live bytes, peak bytes) of the library's device workspaces."""
+    live, peak = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check("bip_mem_stats", None, _lib.bip_mem_stats(ctypes.byref(live), ctypes.byref(peak), 1 if reset_peak else 0))
+    return live.value, peak.value
 
 
 def bip_set_cube_memory(ctx, nbytes):

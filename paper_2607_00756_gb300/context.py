@@ -34,6 +34,38 @@ class BipContext:
         capi.bip_build_s2(self.ctx, V, self._atoms, stream)
         self.n_sites = capi.bip_query(self.ctx)[4]
 
+    def _config_values(self):
+        c = capi.bip_get_config(self.ctx)
+        return np.array([float(getattr(c, name)) for name, _ in capi.BipConfig._fields_])
+
+    def save_builds(self, path, stream=None):
+        """Writes both window stashes, the sites and the configuration to
+        `path` (.npz), for map-only reruns in another process."""
+        stashes = {}
+        for which in (1, 2):
+            host = np.empty(capi.stash_shape(self.ctx, which), dtype=np.complex64)
+            capi.bip_export_stash(self.ctx, which, host, stream)
+            stashes[f"s{which}"] = host
+        atoms = np.ctypeslib.as_array(self._atoms)
+        np.savez(path, config=self._config_values(), y=atoms["y"], x=atoms["x"], slice=atoms["slice"], nch=atoms["nch"], **stashes)
+
+    def load_builds(self, path, stream=None):
+        """Restores what save_builds wrote; the file's configuration must be
+        this context's (else ValueError, nothing restored)."""
+        with np.load(path) as f:
+            if not np.array_equal(f["config"], self._config_values()):
+                raise ValueError("the builds in this file were made with another configuration")
+            atoms = np.stack([f["y"], f["x"], f["slice"].astype(np.float64)], axis=1)
+            nch = f["nch"]
+            self._atoms = capi.make_atoms(atoms, nch)
+            self._nch_max = int(np.max(nch))
+            for which in (1, 2):
+                capi.bip_import_stash(self.ctx, which, self._atoms, np.ascontiguousarray(f[f"s{which}"]), stream)
+        self.n_sites = capi.bip_query(self.ctx)[4]
+
+    def set_check_finite(self, on):
+        capi.bip_set_check_finite(self.ctx, on)
+
     def build_s1(self, V, atoms, nch, stream=None):
         self._atoms = capi.make_atoms(atoms, nch)
         capi.bip_build_s1(self.ctx, V, self._atoms, stream)

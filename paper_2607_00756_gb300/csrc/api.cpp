@@ -5,11 +5,13 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <numeric>
 #include <string>
 
 #include <cuda_fp16.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "bip_internal.h"
 
@@ -102,6 +104,8 @@ struct bip_ctx {
     DevBuf f8pmax, f8inv0, f8inv1, f8hmax, f8H, f8sA, f8sB;   // FP8 per-window scales
     DevBuf errflag;
     std::vector<int32_t> work_h;
+    bool check_finite = false;          // scan outputs for NaN / Inf (bip_set_check_finite)
+    DevBuf nf_count;
 
     // per-stage event timing
     uint32_t prof = 0;                  // stages timed (bit s: stage s)
@@ -132,6 +136,21 @@ bip_status fail_cuda(bip_ctx* c, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return fail_cuda(c, e_, #expr); \
     } while (0)
 
+// NVTX range over a public call or a stage's launch (host side: under a
+// tracing tool the range shows what was enqueued; with no tool attached a
+// push or pop is one check of a function pointer).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define BIP_RANGE(name) NvtxRange nvtx_range_(name)
+
+const char* const kStageRange[BIP_N_STAGES] = {
+    "bip:ms_row", "bip:ms_col", "bip:reconstruct", "bip:coupling",
+    "bip:gram", "bip:quadform", "bip:reduce", "bip:transmission"};
+
 // Brackets one launch with events on its stream when profiling is on, and
 // counts it.  Returns the launch's error.
 struct StageTimer {
@@ -147,7 +166,8 @@ struct StageTimer {
         }
         return c->ev_pool[c->ev_used++];
     }
-    StageTimer(bip_ctx* c_, int st, cudaStream_t s_) : c(c_), stage(st), s(s_) {
+    NvtxRange range;
+    StageTimer(bip_ctx* c_, int st, cudaStream_t s_) : c(c_), stage(st), s(s_), range(kStageRange[st]) {
         c->launches[stage]++;
         if (c->prof >> stage & 1u) {
             e0 = take();
@@ -173,6 +193,15 @@ struct StageTimer {
 // ones made, and an injected failure (the fail_at-th allocation from the
 // moment it is set fails as if the device were out of memory).
 std::atomic<int64_t> g_live{0}, g_made{0}, g_fail_at{0};
+// bytes of the live allocations and their high-water mark
+std::atomic<int64_t> g_bytes{0}, g_peak{0};
+
+void count_bytes(int64_t delta) {
+    const int64_t now = g_bytes += delta;
+    int64_t peak = g_peak.load();
+    while (now > peak && !g_peak.compare_exchange_weak(peak, now)) {
+    }
+}
 
 cudaError_t ensure(DevBuf& b, size_t bytes, bool zero = false, cudaStream_t s = nullptr) {
     if (bytes == 0) bytes = 16;
@@ -182,6 +211,7 @@ cudaError_t ensure(DevBuf& b, size_t bytes, bool zero = false, cudaStream_t s = 
         if (e != cudaSuccess) return e;
         cudaFree(b.p);
         --g_live;
+        count_bytes(-(int64_t)b.cap);
         b.p = nullptr;
         b.cap = 0;
     }
@@ -194,6 +224,7 @@ cudaError_t ensure(DevBuf& b, size_t bytes, bool zero = false, cudaStream_t s = 
         return e;
     }
     ++g_live;
+    count_bytes((int64_t)bytes);
     b.cap = bytes;
     if (zero) return cudaMemsetAsync(b.p, 0, bytes, s);
     return cudaSuccess;
@@ -203,6 +234,7 @@ void release(DevBuf& b) {
     if (b.p) {
         cudaFree(b.p);
         --g_live;
+        count_bytes(-(int64_t)b.cap);
     }
     b.p = nullptr;
     b.cap = 0;
@@ -616,6 +648,7 @@ bip_status build_common(bip_ctx* c, const float* V, const bip_atom* atoms, int32
 extern "C" {
 
 bip_status bip_create(const bip_config* cfg, bip_ctx** out) {
+    BIP_RANGE("bip_create");
     if (!cfg || !out) return BIP_ERR_INVALID_ARG;
     *out = nullptr;
     const bip_config& g = *cfg;
@@ -643,7 +676,7 @@ bip_status bip_create(const bip_config* cfg, bip_ctx** out) {
     c->cfg = g;
     c->prec = g.prec;
     std::string err;
-    bip_status st = bip_build_geometry(g, c->geo, err);
+    bip_status st = bip_geometry_cached(g, c->geo, err);
     if (st != BIP_OK) {
         delete c;
         return st;
@@ -669,7 +702,7 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->ray, &c->rax, &c->g_tA, &c->g_tB, &c->g_sA2, &c->g_sB2, &c->cubeA, &c->cubeB,
                      &c->cube_work, &c->cube_mask, &c->s1t, &c->psi, &c->ybuf, &c->cube_grp, &c->cube_wmap, &c->mpart,
                      &c->hcube, &c->shcube, &c->cstash, &c->ccols, &c->xopA, &c->xopB, &c->xm32, &c->tcache,
-                     &c->cr_ay, &c->cr_ax, &c->cr_cy, &c->cr_cx, &c->cr_T};
+                     &c->cr_ay, &c->cr_ax, &c->cr_cy, &c->cr_cx, &c->cr_T, &c->nf_count};
     for (DevBuf* b : all) release(*b);
     for (int i = 0; i < 6; ++i) {
         release(c->aw1[i]);
@@ -724,6 +757,7 @@ const char* bip_last_error(const bip_ctx* c) {
 }
 
 bip_status bip_build_s1(bip_ctx* c, const float* V, const bip_atom* atoms, int32_t n_atoms, void* stream) {
+    BIP_RANGE("bip_build_s1");
     cudaStream_t s = (cudaStream_t)stream;
     bip_status st = build_common(c, V, atoms, n_atoms, s);
     if (st != BIP_OK) return st;
@@ -764,6 +798,7 @@ bip_status bip_build_s1(bip_ctx* c, const float* V, const bip_atom* atoms, int32
 }
 
 bip_status bip_build_s2(bip_ctx* c, const float* V, const bip_atom* atoms, int32_t n_atoms, void* stream) {
+    BIP_RANGE("bip_build_s2");
     cudaStream_t s = (cudaStream_t)stream;
     bip_status st = build_common(c, V, atoms, n_atoms, s);
     if (st != BIP_OK) return st;
@@ -2418,26 +2453,63 @@ bip_status run_cube_exact(bip_ctx* c, const float* V, const void* H, const doubl
     return BIP_OK;
 }
 
+// Optional scan of a call's outputs for NaN or infinite values
+// (bip_set_check_finite).  Synchronises the stream.
+struct OutSpan {
+    const void* p;
+    int64_t n;
+    int bytes;
+};
+
+bip_status finite_check(bip_ctx* c, std::initializer_list<OutSpan> spans, cudaStream_t s) {
+    if (!c->check_finite) return BIP_OK;
+    CUDA_TRY(c, ensure(c->nf_count, sizeof(unsigned long long), false, s));
+    CUDA_TRY(c, cudaMemsetAsync(c->nf_count.p, 0, sizeof(unsigned long long), s));
+    for (const OutSpan& o : spans)
+        if (o.p && o.n > 0)
+            CUDA_TRY(c, bip_count_nonfinite(o.p, o.n, o.bytes, (unsigned long long*)c->nf_count.p, s));
+    unsigned long long bad = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&bad, c->nf_count.p, sizeof(bad), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (bad) return fail(c, BIP_ERR_NUMERIC, std::to_string(bad) + " output values are NaN or infinite");
+    return BIP_OK;
+}
+
+bip_status refuse_check_under_capture(bip_ctx* c, cudaStream_t s) {
+    if (c && c->check_finite && capturing(s))
+        return fail(c, BIP_ERR_INVALID_ARG, "the finite check synchronises the stream: turn it off to capture");
+    return BIP_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 bip_status bip_coreloss_map(bip_ctx* c, const void* H, const double* scan_px, int32_t P, double* map_out,
                             void* stream) {
+    BIP_RANGE("bip_coreloss_map");
     bip_status st = check_map_args(c, H, scan_px, P, map_out);
+    if (st == BIP_OK) st = refuse_check_under_capture(c, (cudaStream_t)stream);
     if (st != BIP_OK) return st;
-    return run_map(c, H, scan_px, P, nullptr, map_out, nullptr, (cudaStream_t)stream);
+    st = run_map(c, H, scan_px, P, nullptr, map_out, nullptr, (cudaStream_t)stream);
+    if (st != BIP_OK) return st;
+    return finite_check(c, {{map_out, P, 8}}, (cudaStream_t)stream);
 }
 
 bip_status bip_coreloss_sites(bip_ctx* c, const void* H, const double* scan_px, int32_t P, float* partial_out,
                               void* stream) {
+    BIP_RANGE("bip_coreloss_sites");
     bip_status st = check_map_args(c, H, scan_px, P, partial_out);
+    if (st == BIP_OK) st = refuse_check_under_capture(c, (cudaStream_t)stream);
     if (st != BIP_OK) return st;
-    return run_map(c, H, scan_px, P, partial_out, nullptr, nullptr, (cudaStream_t)stream);
+    st = run_map(c, H, scan_px, P, partial_out, nullptr, nullptr, (cudaStream_t)stream);
+    if (st != BIP_OK) return st;
+    return finite_check(c, {{partial_out, (int64_t)c->n_sites * P, 4}}, (cudaStream_t)stream);
 }
 
 bip_status bip_coreloss_cube(bip_ctx* c, const float* V, const void* H, const double* scan_px, int32_t P,
                              float* cube_out, void* stream) {
+    BIP_RANGE("bip_coreloss_cube");
     if (!c) return BIP_ERR_INVALID_ARG;
     if (!c->s1 || site_signature(c->sites) != c->sig1)
         return fail(c, BIP_ERR_INVALID_ARG, "bip_build_s1 must run first (the cube's sites are its sites)");
@@ -2446,7 +2518,11 @@ bip_status bip_coreloss_cube(bip_ctx* c, const float* V, const void* H, const do
     if (P < 1) return fail(c, BIP_ERR_INVALID_ARG, "P must be >= 1");
     for (int i = 0; i < 2 * P; ++i)
         if (!std::isfinite(scan_px[i])) return fail(c, BIP_ERR_INVALID_ARG, "scan position is not finite");
-    return run_cube_exact(c, V, H, scan_px, P, cube_out, (cudaStream_t)stream);
+    bip_status st = refuse_check_under_capture(c, (cudaStream_t)stream);
+    if (st != BIP_OK) return st;
+    st = run_cube_exact(c, V, H, scan_px, P, cube_out, (cudaStream_t)stream);
+    if (st != BIP_OK) return st;
+    return finite_check(c, {{cube_out, (int64_t)P * c->geo.n_cube, 4}}, (cudaStream_t)stream);
 }
 
 bip_status bip_cube_beams(const bip_ctx* c, int32_t* n_cube, int32_t* h) {
@@ -2507,6 +2583,7 @@ bip_status bip_qeels_bins(const bip_ctx* c, int32_t axis, int32_t* n_bins, int32
 
 bip_status bip_coreloss_qeels(bip_ctx* c, const void* H, const double* scan_px, int32_t P, int32_t axis,
                               float* qeels_out, void* stream) {
+    BIP_RANGE("bip_coreloss_qeels");
     bip_status st = check_map_args(c, H, scan_px, P, qeels_out);
     if (st != BIP_OK) return st;
     std::vector<int32_t> bins, bin_of;
@@ -2516,13 +2593,15 @@ bip_status bip_coreloss_qeels(bip_ctx* c, const void* H, const double* scan_px, 
                     "qEELS needs the resolved axis sampled at f = 1: create the context with dfy = 1 (axis 0) "
                     "or dfx = 1 (axis 1)");
     cudaStream_t s = (cudaStream_t)stream;
+    st = refuse_check_under_capture(c, s);
+    if (st != BIP_OK) return st;
     CUDA_TRY(c, ensure(c->cube_scratch, (size_t)P * c->geo.n_det * sizeof(float), false, s));
     CUDA_TRY(c, upload(c->bin_of_d, bin_of, s));
     st = run_map(c, H, scan_px, P, nullptr, nullptr, (float*)c->cube_scratch.p, s);
     if (st != BIP_OK) return st;
     CUDA_TRY(c, bip_qeels_bin((const float*)c->cube_scratch.p, P, c->geo.n_det, (const int32_t*)c->bin_of_d.p,
                               (int)bins.size(), qeels_out, s));
-    return BIP_OK;
+    return finite_check(c, {{qeels_out, (int64_t)P * (int64_t)bins.size(), 4}}, s);
 }
 
 bip_status bip_set_capture_safe(bip_ctx* c, int32_t on) {
@@ -2574,6 +2653,7 @@ bip_status bip_set_launch(bip_ctx* c, int32_t sites_per_batch, int32_t coupling_
 
 bip_status bip_autotune(bip_ctx* c, const void* H, const double* scan_px, int32_t P, double* map_out, void* stream,
                         int32_t* sites_per_batch, int32_t* coupling_tile, int32_t* order, double* best_ms) {
+    BIP_RANGE("bip_autotune");
     bip_status st = check_map_args(c, H, scan_px, P, map_out);
     if (st != BIP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -2706,6 +2786,7 @@ bip_status bip_set_occupancy(bip_ctx* c, const double* occ) {
 }
 
 bip_status bip_set_site_windows(bip_ctx* c, const int32_t* win, void* stream) {
+    BIP_RANGE("bip_set_site_windows");
     if (!c) return BIP_ERR_INVALID_ARG;
     if (c->n_sites < 1) return fail(c, BIP_ERR_INVALID_ARG, "no sites: build the matrices first");
     std::vector<int32_t> w;
@@ -2725,6 +2806,7 @@ bip_status bip_set_site_windows(bip_ctx* c, const int32_t* win, void* stream) {
 }
 
 bip_status bip_set_aberrations(bip_ctx* c, double defocus, double cs, void* stream) {
+    BIP_RANGE("bip_set_aberrations");
     if (!c) return BIP_ERR_INVALID_ARG;
     if (!std::isfinite(defocus) || !std::isfinite(cs)) return fail(c, BIP_ERR_INVALID_ARG, "aberration not finite");
     c->cfg.defocus = defocus;
@@ -2734,9 +2816,9 @@ bip_status bip_set_aberrations(bip_ctx* c, double defocus, double cs, void* stre
     return BIP_OK;
 }
 
-bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const double* scan_px, int32_t P,
-                             const double* dL_dI, double* d_occ, void* d_H, double* d_aberr, float* d_V,
-                             void* stream) {
+static bip_status coreloss_grad(bip_ctx* c, const float* V, const void* H, const double* scan_px, int32_t P,
+                                const double* dL_dI, double* d_occ, void* d_H, double* d_aberr, float* d_V,
+                                void* stream) {
     bip_status st = check_map_args(c, H, scan_px, P, dL_dI);
     if (st != BIP_OK) return st;
     if (d_V && !V) return fail(c, BIP_ERR_INVALID_ARG, "d_V needs the V the matrices were built from");
@@ -3084,6 +3166,22 @@ bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const do
     return BIP_OK;
 }
 
+bip_status bip_coreloss_grad(bip_ctx* c, const float* V, const void* H, const double* scan_px, int32_t P,
+                             const double* dL_dI, double* d_occ, void* d_H, double* d_aberr, float* d_V,
+                             void* stream) {
+    BIP_RANGE("bip_coreloss_grad");
+    bip_status st = refuse_check_under_capture(c, (cudaStream_t)stream);
+    if (st != BIP_OK) return st;
+    st = coreloss_grad(c, V, H, scan_px, P, dL_dI, d_occ, d_H, d_aberr, d_V, stream);
+    if (st != BIP_OK || !c->check_finite) return st;
+    if (d_aberr && !(std::isfinite(d_aberr[0]) && std::isfinite(d_aberr[1])))
+        return fail(c, BIP_ERR_NUMERIC, "the aberration derivatives are NaN or infinite");
+    const int64_t G = (int64_t)c->cfg.ny * c->cfg.nx;
+    return finite_check(c,
+                        {{d_occ, c->n_sites, 8}, {d_H, 2 * c->h_elems, 4}, {d_V, (int64_t)c->cfg.nz * G, 4}},
+                        (cudaStream_t)stream);
+}
+
 bip_status bip_copy_stash(bip_ctx* c, int32_t which, int32_t site, void* out, void* stream) {
     if (!c) return BIP_ERR_INVALID_ARG;
     if (!out) return fail(c, BIP_ERR_INVALID_ARG, "out is null");
@@ -3097,7 +3195,74 @@ bip_status bip_copy_stash(bip_ctx* c, int32_t which, int32_t site, void* out, vo
     return BIP_OK;
 }
 
+bip_status bip_export_stash(bip_ctx* c, int32_t which, void* dst, int64_t bytes, void* stream) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (which != 1 && which != 2) return fail(c, BIP_ERR_INVALID_ARG, "which must be 1 or 2");
+    if ((which == 1 && !c->s1) || (which == 2 && !c->s2)) return fail(c, BIP_ERR_INVALID_ARG, "matrix not built");
+    if (!dst) return fail(c, BIP_ERR_INVALID_ARG, "dst is null");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (capturing(s)) return fail(c, BIP_ERR_INVALID_ARG, "bip_export_stash is not capturable");
+    const size_t need = (size_t)c->n_sites * (which == 1 ? c->geo.Bp1 : c->geo.Bp2) * c->cfg.win * c->cfg.win *
+                        sizeof(float2);
+    if (bytes < 0 || (size_t)bytes != need)
+        return fail(c, BIP_ERR_SHAPE, "the stash is " + std::to_string(need) + " bytes, not " + std::to_string(bytes));
+    const void* src = which == 1 ? c->stash1.p : c->stash2.p;
+    CUDA_TRY(c, cudaMemcpyAsync(dst, src, need, cudaMemcpyDefault, s));
+    return BIP_OK;
+}
+
+bip_status bip_import_stash(bip_ctx* c, int32_t which, const bip_atom* atoms, int32_t n_atoms, const void* src,
+                            int64_t bytes, void* stream) {
+    BIP_RANGE("bip_import_stash");
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (which != 1 && which != 2) return fail(c, BIP_ERR_INVALID_ARG, "which must be 1 or 2");
+    if (!src) return fail(c, BIP_ERR_INVALID_ARG, "src is null");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (capturing(s)) return fail(c, BIP_ERR_INVALID_ARG, "bip_import_stash is not capturable");
+    std::vector<SiteDev> sites;
+    int nmax = 0, total = 0;
+    bip_status st = parse_sites(c, atoms, n_atoms, sites, nmax, total);
+    if (st != BIP_OK) return st;
+    const int ncol = which == 1 ? c->geo.Bp1 : c->geo.Bp2;
+    const size_t need = sites.size() * ncol * c->cfg.win * c->cfg.win * sizeof(float2);
+    if (bytes < 0 || (size_t)bytes != need)
+        return fail(c, BIP_ERR_SHAPE, "a stash of these sites is " + std::to_string(need) + " bytes, not " +
+                                          std::to_string(bytes));
+    st = make_tables(c, s);
+    if (st != BIP_OK) return st;
+    st = set_sites(c, sites, nmax, total, s);
+    if (st != BIP_OK) return st;
+    DevBuf& stash = which == 1 ? c->stash1 : c->stash2;
+    const size_t G = (size_t)c->cfg.ny * c->cfg.nx;
+    CUDA_TRY(c, ensure(stash, need, false, s));
+    // the reverse pass's sweeps use the builds' column workspace
+    CUDA_TRY(c, ensure(c->cols, (size_t)std::max(c->geo.Bp1, c->geo.Bp2) * G * sizeof(float2), false, s));
+    CUDA_TRY(c, cudaMemcpyAsync(stash.p, src, need, cudaMemcpyDefault, s));
+    if (which == 1) {
+        c->s1 = true;
+        c->sig1 = site_signature(c->sites);
+    } else {
+        c->s2 = true;
+        c->sig2 = site_signature(c->sites);
+    }
+    return BIP_OK;
+}
+
+bip_status bip_set_check_finite(bip_ctx* c, int32_t on) {
+    if (!c) return BIP_ERR_INVALID_ARG;
+    c->check_finite = on != 0;
+    return BIP_OK;
+}
+
+bip_status bip_mem_stats(int64_t* live_bytes, int64_t* peak_bytes, int32_t reset_peak) {
+    if (live_bytes) *live_bytes = g_bytes.load();
+    if (peak_bytes) *peak_bytes = g_peak.load();
+    if (reset_peak) g_peak = g_bytes.load();
+    return BIP_OK;
+}
+
 bip_status bip_site_windows(bip_ctx* c, int32_t site, void* s1_out, void* s2_out, void* stream) {
+    BIP_RANGE("bip_site_windows");
     if (!c) return BIP_ERR_INVALID_ARG;
     if (!c->s1 || !c->s2 || c->sig1 != c->sig2)
         return fail(c, BIP_ERR_INVALID_ARG, "bip_build_s1 and bip_build_s2 must run first on the same sites");
@@ -3150,6 +3315,7 @@ bip_status bip_get_profile(bip_ctx* c, double* ms, int64_t* launches) {
 }
 
 bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_out, void* stream) {
+    BIP_RANGE("bip_site_coupling");
     if (!c) return BIP_ERR_INVALID_ARG;
     if (!c->s1 || !c->s2 || c->sig1 != c->sig2)
         return fail(c, BIP_ERR_INVALID_ARG, "bip_build_s1 and bip_build_s2 must run first on the same sites");
@@ -3263,6 +3429,7 @@ bip_status bip_site_coupling(bip_ctx* c, const void* H, int32_t site, void* m_ou
 
 extern "C" bip_status bip_build_s1_noalloc(bip_ctx* c, const float* V, const bip_atom* atoms, int32_t n_atoms,
                                            void* stash, void* stream) {
+    BIP_RANGE("bip_build_s1_noalloc");
     if (!c) return BIP_ERR_INVALID_ARG;
     if (!V) return fail(c, BIP_ERR_INVALID_ARG, "V is null");
     if (!stash) return fail(c, BIP_ERR_INVALID_ARG, "stash is null");

@@ -30,6 +30,8 @@ struct BipGeometry {
 };
 
 bip_status bip_build_geometry(const bip_config& cfg, BipGeometry& g, std::string& err);
+// bip_build_geometry through the on-disk cache when one is set (geom_cache.cpp)
+bip_status bip_geometry_cached(const bip_config& cfg, BipGeometry& g, std::string& err);
 // chi(q) = pi lambda df |q|^2 + (pi/2) Cs lambda^3 |q|^4 of beam h (Psi = exp(-i chi))
 // and its derivatives with respect to df and Cs (each output optional)
 void bip_aberration_phase(const bip_config& c, double lambda, int hy, int hx, double* chi, double* d_defocus,
@@ -316,6 +318,8 @@ cudaError_t bip_raster_eval(const DiffArgs& a, const RasterArgs& r, cudaStream_t
 // (already zero outside each site's crop mask), in a fixed order; scratch
 // of bip_reduce_scratch_bytes(n_sites, P) bytes.
 size_t bip_reduce_scratch_bytes(int n_sites, int P);
+// adds to *count the NaN or infinite values among n values of elem_bytes (4: float, 8: double)
+cudaError_t bip_count_nonfinite(const void* v, int64_t n, int elem_bytes, unsigned long long* count, cudaStream_t s);
 // occ (optional, [n_sites]): each site's contribution is weighted by its
 // occupancy before the sum
 cudaError_t bip_reduce_sites(const float* partial, int n_sites, int P, void* scratch, double* map_out,

@@ -5,6 +5,8 @@
 // compensation in a fixed order -- sites in chunks of kChunk in site order,
 // then the chunks in order -- so the result does not depend on how the
 // sites were batched or scheduled.
+#include <algorithm>
+
 #include "bip_internal.h"
 
 namespace {
@@ -65,5 +67,40 @@ cudaError_t bip_reduce_sites(const float* partial, int n_sites, int P, void* scr
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     reduce_final_kernel<<<(P + kThreads - 1) / kThreads, kThreads, 0, s>>>(cs, n_chunks, P, out);
+    return cudaGetLastError();
+}
+
+// Count of NaN or infinite values in an output (the optional finite check
+// of the map, cube, qEELS and gradient calls): n values of 4 or 8 bytes,
+// grid-stride, one atomic add per block of its non-zero count.
+namespace {
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) count_nonfinite_kernel(const T* __restrict__ v, int64_t n,
+                                                                   unsigned long long* __restrict__ count) {
+    __shared__ unsigned int warp_bad[kThreads / 32];
+    unsigned int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+        bad += isfinite(v[i]) ? 0u : 1u;
+    bad = __reduce_add_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) warp_bad[threadIdx.x >> 5] = bad;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = 0;
+        for (int w = 0; w < kThreads / 32; ++w) t += warp_bad[w];
+        if (t) atomicAdd(count, (unsigned long long)t);
+    }
+}
+
+}  // namespace
+
+cudaError_t bip_count_nonfinite(const void* v, int64_t n, int elem_bytes, unsigned long long* count,
+                                cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 8);
+    if (elem_bytes == 8)
+        count_nonfinite_kernel<double><<<(int)blocks, kThreads, 0, s>>>((const double*)v, n, count);
+    else
+        count_nonfinite_kernel<float><<<(int)blocks, kThreads, 0, s>>>((const float*)v, n, count);
     return cudaGetLastError();
 }
