@@ -67,6 +67,7 @@ struct bip_ctx {
     bool s1 = false, s2 = false;
 
     DevBuf stash1, stash2, cols;
+    DevBuf tw512;                       // nx = 512: the half-warp row pass's twiddles
 
     // map workspaces
     DevBuf scans_d, work_d, partial, gdiff, rsum, illum, cube_scratch, bin_of_d;
@@ -419,6 +420,13 @@ bip_status make_tables(bip_ctx* c, cudaStream_t s) {
         for (int v = 0; v < g.win; ++v) xt[(size_t)h * g.win + v] = turn((int)((int64_t)h * v % g.nx), g.nx, +1.0);
     CUDA_TRY(c, upload(c->twy, twy, s));
     CUDA_TRY(c, upload(c->twx, twx, s));
+    if (g.nx == 512) {
+        // twiddles of the half-warp row pass's second pass
+        std::vector<float2> t5(15 * 32);
+        for (int e = 1; e < 16; ++e)
+            for (int j = 0; j < 32; ++j) t5[(size_t)(e - 1) * 32 + j] = turn(e * j, 512, -1.0);
+        CUDA_TRY(c, upload(c->tw512, t5, s));
+    }
     CUDA_TRY(c, upload(c->ey, ey, s));
     CUDA_TRY(c, upload(c->ex, ex, s));
     CUDA_TRY(c, upload(c->py, py, s));
@@ -626,6 +634,7 @@ MsPlan plan_for(bip_ctx* c, int ncol, const DevBuf& shift) {
     p.py = (const float2*)c->py.p;
     p.px = (const float2*)c->px.p;
     p.shift = (const int2*)shift.p;
+    p.tw512 = c->cfg.nx == 512 ? (const float2*)c->tw512.p : nullptr;
     return p;
 }
 
@@ -702,7 +711,7 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->ray, &c->rax, &c->g_tA, &c->g_tB, &c->g_sA2, &c->g_sB2, &c->cubeA, &c->cubeB,
                      &c->cube_work, &c->cube_mask, &c->s1t, &c->psi, &c->ybuf, &c->cube_grp, &c->cube_wmap, &c->mpart,
                      &c->hcube, &c->shcube, &c->cstash, &c->ccols, &c->xopA, &c->xopB, &c->xm32, &c->tcache,
-                     &c->cr_ay, &c->cr_ax, &c->cr_cy, &c->cr_cx, &c->cr_T, &c->nf_count};
+                     &c->cr_ay, &c->cr_ax, &c->cr_cy, &c->cr_cx, &c->cr_T, &c->nf_count, &c->tw512};
     for (DevBuf* b : all) release(*b);
     for (int i = 0; i < 6; ++i) {
         release(c->aw1[i]);

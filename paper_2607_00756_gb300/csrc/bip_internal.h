@@ -82,6 +82,8 @@ struct MsPlan {
     const float2* py;               // [ny] exp(-i pi lambda dz qy^2) / ny
     const float2* px;               // [nx]
     const int2* shift;              // [ncol] propagator shift (sy, sx)
+    const float2* tw512;            // nx = 512: exp(-2 pi i e j / 512) at (e - 1) 32 + j,
+                                    // e = 1..15, j < 32 (the half-warp row pass); else null
 };
 // row pass: [inverse row FFT] -> [T_pre] -> [stash] -> [T_post] -> [row FFT]
 struct MsRowArgs {

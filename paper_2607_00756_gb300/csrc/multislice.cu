@@ -12,7 +12,9 @@
 // unnormalised forward/inverse FFT pair.
 //
 // Grid lengths: powers of two 64..1024, and 3 M (192, 384, 768) through
-// the radix-3 layer of the register FFT (fft_reg3).
+// the radix-3 layer of the register FFT (fft_reg3).  Rows of 512 points
+// (the paper-scale grids) take a two-pass form on half-warps when the plan
+// carries its twiddle table (row_pass_hw512_kernel).
 //
 // One step of a column is two passes over global memory:
 //   row pass    [inverse FFT along x] [T_pre] [stash, save] [T_post] [FFT along x]
@@ -149,6 +151,262 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(MsPlan plan, MsRowAr
 #pragma unroll
             for (int m = 0; m < 8; ++m) g[a.do_fft ? RS::freq(q, m, t) : RS::real(q, m, t)] = v[q][m];
     }
+}
+
+// ---------------------------------------------------------------------------
+// Rows of 512 points on half-warps.  512 = 32 x 16, so a transform is two
+// register passes with one exchange between them: pass 1 a DFT-32 per
+// thread over x[t + 16 m] (m = 0..31), pass 2 two DFT-16 per thread, each
+// after a twiddle by exp(-+2 pi i e j / 512).  Sixteen threads hold a row in
+// the cyclic layout x = t + 16 m in both domains, so the row never leaves
+// its half-warp: the exchange needs __syncwarp only, and against the
+// radix-8 form above it moves every value through shared memory once per
+// transform instead of twice and reads half the twiddles.  A block of 256
+// threads takes 16 parent columns at one y.
+//
+// Local DFTs of length L = 4 B (B = 8 or 4), natural order in and out:
+// with n = n1 + 4 n2 and k = B k1 + k2, a DFT-B over n2 for each n1, the
+// twiddle W_L^(n1 k2), then a DFT-4 over n1 for each k2.
+namespace hw512 {
+
+constexpr int N = 512, NT = 16, NV = 32;
+constexpr int RPB = kThreads / NT;                 // rows (parent columns) per block
+constexpr int ROWBUF = N + N / 32;                 // exchange entries per row: one pad per 32
+constexpr int NTW = 15 * 32;                       // pass-2 twiddles [e - 1][j]
+
+// exp(-2 pi i m / 32)
+__constant__ float2 kW32[32] = {
+    {1.0f, 0.0f}, {0.9807852506637573f, -0.19509032368659973f}, {0.9238795042037964f, -0.3826834261417389f},
+    {0.8314695954322815f, -0.5555702447891235f}, {0.7071067690849304f, -0.7071067690849304f},
+    {0.5555702447891235f, -0.8314695954322815f}, {0.3826834261417389f, -0.9238795042037964f},
+    {0.19509032368659973f, -0.9807852506637573f}, {0.0f, -1.0f}, {-0.19509032368659973f, -0.9807852506637573f},
+    {-0.3826834261417389f, -0.9238795042037964f}, {-0.5555702447891235f, -0.8314695954322815f},
+    {-0.7071067690849304f, -0.7071067690849304f}, {-0.8314695954322815f, -0.5555702447891235f},
+    {-0.9238795042037964f, -0.3826834261417389f}, {-0.9807852506637573f, -0.19509032368659973f}, {-1.0f, 0.0f},
+    {-0.9807852506637573f, 0.19509032368659973f}, {-0.9238795042037964f, 0.3826834261417389f},
+    {-0.8314695954322815f, 0.5555702447891235f}, {-0.7071067690849304f, 0.7071067690849304f},
+    {-0.5555702447891235f, 0.8314695954322815f}, {-0.3826834261417389f, 0.9238795042037964f},
+    {-0.19509032368659973f, 0.9807852506637573f}, {0.0f, 1.0f}, {0.19509032368659973f, 0.9807852506637573f},
+    {0.3826834261417389f, 0.9238795042037964f}, {0.5555702447891235f, 0.8314695954322815f},
+    {0.7071067690849304f, 0.7071067690849304f}, {0.8314695954322815f, 0.5555702447891235f},
+    {0.9238795042037964f, 0.3826834261417389f}, {0.9807852506637573f, 0.19509032368659973f}};
+
+// a W32^m (conjugate for the inverse); m is a constant after unrolling, so
+// the branches fold and the quarter turns cost no multiply
+template <bool INV>
+__device__ __forceinline__ float2 tw32(float2 a, int m) {
+    m &= 31;
+    if (m == 0) return a;
+    if (m == 8) return c_rot<INV>(a);
+    if (m == 16) return make_float2(-a.x, -a.y);
+    if (m == 24) return c_rot<!INV>(a);
+    float2 w = kW32[m];
+    if (INV) w.y = -w.y;
+    return c_mul(a, w);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&u)[16]) {
+    float2 b[4][4];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) b[n1][n2] = u[n1 + 4 * n2];
+        dft4<INV>(b[n1][0], b[n1][1], b[n1][2], b[n1][3]);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) b[n1][k2] = tw32<INV>(b[n1][k2], 2 * n1 * k2);
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+        dft4<INV>(b[0][k2], b[1][k2], b[2][k2], b[3][k2]);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) u[4 * k1 + k2] = b[k1][k2];
+    }
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft32(float2 (&v)[NV]) {
+    float2 b[4][8];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) b[n1][n2] = v[n1 + 4 * n2];
+        dft8<INV>(b[n1]);
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) b[n1][k2] = tw32<INV>(b[n1][k2], n1 * k2);
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+        dft4<INV>(b[0][k2], b[1][k2], b[2][k2], b[3][k2]);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) v[8 * k1 + k2] = b[k1][k2];
+    }
+}
+
+// One length-512 transform of the row held by this half-warp (thread t:
+// v[m] = x[t + 16 m] on entry, X[t + 16 m] on exit; unnormalised inverse).
+// buf: this row's exchange buffer (entry i at i + i / 32); tw2: the pass-2
+// twiddles exp(-2 pi i e j / 512) at (e - 1) 32 + j.  Every lane of the warp
+// calls it (the warp's two rows together).
+template <bool INV>
+__device__ __forceinline__ void fft512(float2 (&v)[NV], float2* buf, int t, const float2* tw2) {
+    dft32<INV>(v);
+    // pass-1 output r of butterfly t is y[32 t + r]
+#pragma unroll
+    for (int r = 0; r < 32; ++r) buf[33 * t + r] = v[r];
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int j = t + 16 * h;                  // pass-2 butterfly: y[j + 32 e], e < 16
+        float2 u[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) u[e] = buf[j + 33 * e];
+#pragma unroll
+        for (int e = 1; e < 16; ++e) {
+            float2 w = tw2[(e - 1) * 32 + j];
+            if (INV) w.y = -w.y;
+            u[e] = c_mul(u[e], w);
+        }
+        dft16<INV>(u);
+        // output r is X[j + 32 r] = X[t + 16 (2 r + h)]
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[2 * r + h] = u[r];
+    }
+    __syncwarp();                                  // reads done before the buffer is reused
+}
+
+}  // namespace hw512
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// The row pass of row_pass_kernel<512> on half-warp rows (same arguments,
+// same results up to rounding order), persistent over the grid rows: block
+// b keeps the column group b % groups and takes the rows y = b / groups,
+// + blocks / groups, ...  While a half-warp stores its row it already copies
+// its next row into its exchange buffer (idle between transforms) with
+// cp.async, and the block copies the next row's transmission into the
+// other of two T buffers, so the loads of one row overlap the work of the
+// previous one.
+__global__ void __launch_bounds__(kThreads, 2) row_pass_hw512_kernel(MsPlan plan, MsRowArgs a, int groups) {
+    using namespace hw512;
+    extern __shared__ float2 smem[];
+    const int sub = threadIdx.x / NT;
+    const int t = threadIdx.x % NT;
+    float2* buf = smem + sub * ROWBUF;
+    float2* tw2 = smem + RPB * ROWBUF;             // [15][32]
+    float2* tts = tw2 + NTW;                       // [2][512] transmission of the current / next y
+    const int cg = blockIdx.x % groups;
+    const int ystep = gridDim.x / groups;          // the launch makes gridDim.x a multiple of groups
+    const int c = cg * RPB + sub;
+    const bool active = c < plan.ncol;
+    const float* vsl = a.v_pre ? a.v_pre : a.v_post;
+    const bool table = vsl && a.t_slice;           // T copied from the build's table
+    const bool load = active && !a.init;
+    float2* gcol = a.cols + (size_t)(active ? c : 0) * plan.ny * N;
+
+    // copies of row y: this half-warp's row into buf (unpadded), the T row
+    // into tts[slot]
+    auto prefetch = [&](int y, int slot) {
+        if (load) {
+            const float2* src = gcol + (size_t)y * N;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) cp_async16(buf + 2 * (t + 16 * k), src + 2 * (t + 16 * k));
+        }
+        if (table) cp_async16(tts + slot * N + 2 * threadIdx.x, a.t_slice + (size_t)y * N + 2 * threadIdx.x);
+        cp_async_commit();
+    };
+
+    // windows crossing row y: entries row_off[y] .. row_off[y + 1] - 1 (the
+    // same for every column), read one row ahead
+    auto entries = [&](int yy, int& o0, int& o1) {
+        o0 = o1 = 0;
+        if (a.row_off && yy < plan.ny) {
+            o0 = __ldg(&a.row_off[yy]);
+            o1 = __ldg(&a.row_off[yy + 1]);
+        }
+    };
+
+    for (int i = threadIdx.x; i < NTW; i += kThreads) tw2[i] = __ldg(&plan.tw512[i]);
+    int y = blockIdx.x / groups;
+    int slot = 0;
+    int e0, e1;
+    entries(y, e0, e1);
+    if (y < plan.ny) prefetch(y, 0);
+    for (; y < plan.ny; y += ystep, slot ^= 1) {
+        float2* tt = tts + slot * N;
+        // the first 16 entries, one per lane, in flight during the inverse transform
+        int4 ent = make_int4(0, 0, 0, 0);
+        if (e0 + t < e1) ent = __ldg(&a.row_ent[e0 + t]);
+        if (vsl && !a.t_slice) {
+            for (int i = threadIdx.x; i < N; i += kThreads) {
+                float sn, co;
+                sincosf(plan.sigma * __ldg(&vsl[(size_t)y * N + i]), &sn, &co);
+                tt[i] = make_float2(co, sn);
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();                           // every copy of this row and its T is visible
+        float2 v[NV];
+#pragma unroll
+        for (int m = 0; m < NV; ++m)
+            v[m] = !active ? make_float2(0.f, 0.f) : a.init ? make_float2(a.init_val, 0.f) : buf[t + NT * m];
+        __syncwarp();                              // the row is in registers before buf is reused
+        if (a.do_ifft) fft512<true>(v, buf, t, tw2);
+        if (a.v_pre) {
+#pragma unroll
+            for (int m = 0; m < NV; ++m) v[m] = c_mul(v[m], tt[t + NT * m]);
+        }
+        if (active && a.save) {
+            float2* o = a.save + ((size_t)c * plan.ny + y) * N;
+#pragma unroll
+            for (int m = 0; m < NV; ++m) o[t + NT * m] = v[m];
+        }
+        if (e1 > e0) {
+            // the stash: the row in buf (free between the transforms), then each
+            // crossing window's segment x = ox .. ox + win - 1 (wrapped) copied
+            // from there, 16 consecutive pixels per store; entries (site, u, ox)
+            // are read one per lane and passed round the half-warp
+#pragma unroll
+            for (int m = 0; m < NV; ++m) buf[t + NT * m] = v[m];
+            __syncwarp();
+            for (int base = e0; base < e1; base += NT) {
+                if (base > e0) {
+                    ent = make_int4(0, 0, 0, 0);
+                    if (base + t < e1) ent = __ldg(&a.row_ent[base + t]);
+                }
+                const int cnt = min(NT, e1 - base);
+                for (int k = 0; k < cnt; ++k) {
+                    const int site = __shfl_sync(0xffffffffu, ent.x, k, NT);
+                    const int wu = __shfl_sync(0xffffffffu, ent.y, k, NT);
+                    const int ox = __shfl_sync(0xffffffffu, ent.z, k, NT);
+                    if (active) {
+                        float2* dst = a.stash + (((size_t)site * plan.ncol + c) * a.win + wu) * a.win;
+                        for (int u = t; u < a.win; u += NT) dst[u] = buf[(ox + u) & (N - 1)];
+                    }
+                }
+            }
+            __syncwarp();                          // buf's reads are done before the transform
+        }
+        if (a.v_post) {
+#pragma unroll
+            for (int m = 0; m < NV; ++m) v[m] = c_mul(v[m], tt[t + NT * m]);
+        }
+        if (a.do_fft) fft512<false>(v, buf, t, tw2);
+        __syncwarp();                              // buf's last reads are done
+        entries(y + ystep, e0, e1);
+        if (y + ystep < plan.ny) prefetch(y + ystep, slot ^ 1);
+        if (active) {
+            float2* g = gcol + (size_t)y * N;
+#pragma unroll
+            for (int m = 0; m < NV; ++m) g[t + NT * m] = v[m];
+        }
+    }
+    cp_async_wait_all();
 }
 
 // Column pass geometry: XB columns per block, two adjacent columns per
@@ -297,6 +555,34 @@ cudaError_t launch_row(const MsPlan& p, const MsRowArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_row_hw512(const MsPlan& p, const MsRowArgs& a, cudaStream_t s) {
+    using namespace hw512;
+    const int groups = (p.ncol + RPB - 1) / RPB;
+    const size_t sm = ((size_t)RPB * ROWBUF + NTW + 2 * N) * sizeof(float2);
+    static bool attr = false;
+    static int per_sm = 0, sms = 0;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(row_pass_hw512_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sm);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, row_pass_hw512_kernel, kThreads, sm);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        attr = true;
+    }
+    // persistent: whole rounds of the resident blocks, a multiple of the
+    // column groups, at most one block per (group, y)
+    long long blocks = (long long)sms * per_sm / groups * groups;
+    if (blocks < groups) blocks = groups;
+    if (blocks > (long long)groups * p.ny) blocks = (long long)groups * p.ny;
+    row_pass_hw512_kernel<<<(unsigned)blocks, kThreads, sm, s>>>(p, a, groups);
+    return cudaGetLastError();
+}
+
 template <int NY>
 cudaError_t launch_col(const MsPlan& p, float2* cols, cudaStream_t s) {
     using C = ColShape<NY>;
@@ -320,7 +606,7 @@ cudaError_t bip_ms_row_pass(const MsPlan& p, const MsRowArgs& a, cudaStream_t s)
         case 64: return launch_row<64>(p, a, s);
         case 128: return launch_row<128>(p, a, s);
         case 256: return launch_row<256>(p, a, s);
-        case 512: return launch_row<512>(p, a, s);
+        case 512: return p.tw512 ? launch_row_hw512(p, a, s) : launch_row<512>(p, a, s);
         case 1024: return launch_row<1024>(p, a, s);
         case 192: return launch_row<192>(p, a, s);
         case 384: return launch_row<384>(p, a, s);

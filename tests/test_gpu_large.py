@@ -1,7 +1,8 @@
 """GPU parity on the largest grids the library accepts (1024 pixels on an
-axis): the 1024-point register FFTs of the row and column passes, the
-windows and tables at that size, in FP32 and mixed precision, against the
-oracle's map on a few scans around the sites."""
+axis) and on 512-pixel rows (the half-warp row pass): the register FFTs of
+the row and column passes, the windows and tables at those sizes, in FP32
+and mixed precision, against the oracle's map on a few scans around the
+sites and, in FP32, the stashed parent windows."""
 import numpy as np
 import pytest
 
@@ -41,7 +42,8 @@ def large_case(ny, nx):
     return cfg, synth.Specimen(cfg=cfg, atoms=sp.atoms, nch=nch, V=sp.V, H=H, scans=scans)
 
 
-@pytest.mark.parametrize("shape", [(1024, 1024), (1024, 256), (256, 1024)], ids=lambda s: f"{s[0]}x{s[1]}")
+@pytest.mark.parametrize("shape", [(1024, 1024), (1024, 256), (256, 1024), (512, 512), (256, 512)],
+                         ids=lambda s: f"{s[0]}x{s[1]}")
 def test_map_on_1024_grids(shape):
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
