@@ -123,19 +123,44 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(MsPlan plan, MsRowAr
 #pragma unroll
             for (int m = 0; m < 8; ++m) o[RS::real(q, m, t)] = v[q][m];
     }
-    if (active && a.row_off) {
-        const int e1 = __ldg(&a.row_off[y + 1]);
-        for (int e = __ldg(&a.row_off[y]); e < e1; ++e) {
-            const int4 en = __ldg(&a.row_ent[e]);      // (site, u, ox, -)
-            float2* dst = a.stash + (((size_t)en.x * plan.ncol + c) * a.win + en.y) * a.win;
+    if (a.row_off) {
+        // the stash: the row staged in real-space order in an exchange
+        // buffer, then each window crossing row y -- the same entries for
+        // every row of the block -- copied from there by the row's threads,
+        // NT consecutive pixels per store.  Entries (site, u, ox) are read one
+        // per lane and passed round the warp.  The staging buffer is the one
+        // the next transform writes only after its first barrier (buffer
+        // ph ^ 1); the barrier before staging ends the inverse transform's
+        // last reads of it.
+        const int e0 = __ldg(&a.row_off[y]), e1 = __ldg(&a.row_off[y + 1]);
+        if (e1 > e0) {
+            float2* rowbuf = ph ? b0 : b1;
+            __syncthreads();
 #pragma unroll
             for (int q = 0; q < S; ++q)
 #pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    int u = (RS::real(q, m, t) - en.z) % NX;   // column of this point in the window
-                    if (u < 0) u += NX;
-                    if (u < a.win) dst[u] = v[q][m];
+                for (int m = 0; m < 8; ++m) rowbuf[RS::real(q, m, t)] = v[q][m];
+            __syncthreads();
+            const int lane = threadIdx.x & 31;
+            for (int base = e0; base < e1; base += 32) {
+                int4 ent = make_int4(0, 0, 0, 0);
+                if (base + lane < e1) ent = __ldg(&a.row_ent[base + lane]);
+                const int cnt = min(32, e1 - base);
+                for (int k = 0; k < cnt; ++k) {
+                    const int site = __shfl_sync(0xffffffffu, ent.x, k);
+                    const int wu = __shfl_sync(0xffffffffu, ent.y, k);
+                    int ox = __shfl_sync(0xffffffffu, ent.z, k) % NX;
+                    if (ox < 0) ox += NX;
+                    if (active) {
+                        float2* dst = a.stash + (((size_t)site * plan.ncol + c) * a.win + wu) * a.win;
+                        for (int u = t; u < a.win; u += NT) {
+                            int x = ox + u;
+                            if (x >= NX) x -= NX;
+                            dst[u] = rowbuf[x];
+                        }
+                    }
                 }
+            }
         }
     }
     if (a.v_post) {
