@@ -204,6 +204,20 @@ bip_status bip_build_s1(bip_ctx* ctx, const float* V, const bip_atom* atoms,
 bip_status bip_build_s2(bip_ctx* ctx, const float* V, const bip_atom* atoms,
                         int32_t n_atoms, void* stream);
 
+/* Both builds at once: the S1 and S2 sweeps of bip_build_s1 and
+ * bip_build_s2 with the same arguments, S1 on `stream` and S2 on a stream
+ * the context creates at its first use (non-blocking, on the current
+ * device), forked from and joined back into `stream` by events, so that the
+ * two sweeps' kernels share the GPU.  The stashes are bit-identical to
+ * those of the two separate calls, and the context is afterwards as after
+ * them.  S2's sweep gets its own column workspace (Bp2 x ny x nx complex64
+ * more device memory than the separate calls).  On an error the side
+ * stream's work is still joined into `stream`.  Not capturable into a CUDA
+ * graph (BIP_ERR_INVALID_ARG on a capturing stream; the builds upload host
+ * tables).  Errors as bip_build_s1. */
+bip_status bip_build(bip_ctx* ctx, const float* V, const bip_atom* atoms, int32_t n_atoms,
+                     void* stream);
+
 /* Elemental map (Algorithm 5; Eq. window-recon, magpreserve, coupling,
  * map-sum): for every site the windows of S1 and S2 are rebuilt from the
  * parents, M^{(n)} = S2^T diag(H_n) S1 is formed, and

@@ -60,6 +60,7 @@ def _load():
         "bip_set_precision": [VP, I32],
         "bip_build_s1": [VP, VP, P(BipAtom), I32, VP],
         "bip_build_s2": [VP, VP, P(BipAtom), I32, VP],
+        "bip_build": [VP, VP, P(BipAtom), I32, VP],
         "bip_coreloss_map": [VP, VP, P(D), I32, VP, VP],
         "bip_coreloss_sites": [VP, VP, P(D), I32, VP, VP],
         "bip_coreloss_cube": [VP, VP, VP, P(D), I32, VP, VP],
@@ -214,6 +215,13 @@ def bip_build_s2(ctx, V, atoms_arr, stream=None):
     import torch
     _check("bip_build_s2", ctx, _lib.bip_build_s2(ctx, _dev(V, torch.float32, "V"), atoms_arr,
                                                    len(atoms_arr), _stream(stream)))
+
+
+def bip_build(ctx, V, atoms_arr, stream=None):
+    """Both builds, the S2 sweep on the context's side stream."""
+    import torch
+    _check("bip_build", ctx, _lib.bip_build(ctx, _dev(V, torch.float32, "V"), atoms_arr, len(atoms_arr),
+                                             _stream(stream)))
 
 
 def _scans(scans):

@@ -27,11 +27,11 @@ class BipContext:
         capi.bip_set_precision(self.ctx, prec)
 
     def build(self, V, atoms, nch, stream=None):
-        """S1 and S2 builds (both window stashes) from a device V."""
+        """S1 and S2 builds (both window stashes) from a device V, the two
+        sweeps side by side (bip_build)."""
         self._atoms = capi.make_atoms(atoms, nch)
         self._nch_max = int(np.max(nch))
-        capi.bip_build_s1(self.ctx, V, self._atoms, stream)
-        capi.bip_build_s2(self.ctx, V, self._atoms, stream)
+        capi.bip_build(self.ctx, V, self._atoms, stream)
         self.n_sites = capi.bip_query(self.ctx)[4]
 
     def _config_values(self):

@@ -67,6 +67,9 @@ struct bip_ctx {
     bool s1 = false, s2 = false;
 
     DevBuf stash1, stash2, cols;
+    DevBuf cols2;                       // S2's columns while both sweeps run at once (bip_build)
+    cudaStream_t side = nullptr;        // bip_build: the stream S2's sweep runs on
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     DevBuf tw512;                       // nx = 512: the half-warp row pass's twiddles
 
     // map workspaces
@@ -650,6 +653,101 @@ bip_status build_common(bip_ctx* c, const float* V, const bip_atom* atoms, int32
     return set_sites(c, sites, nmax, total, s);
 }
 
+
+// Workspaces of the S1 build: its stash, the column set, the transmissions.
+bip_status alloc_s1(bip_ctx* c, cudaStream_t s) {
+    const bip_config& g = c->cfg;
+    const size_t win2 = (size_t)g.win * g.win, G = (size_t)g.ny * g.nx;
+    CUDA_TRY(c, ensure(c->stash1, (size_t)c->n_sites * c->geo.Bp1 * win2 * sizeof(float2), false, s));
+    CUDA_TRY(c, ensure(c->cols, (size_t)std::max(c->geo.Bp1, c->geo.Bp2) * G * sizeof(float2), false, s));
+    CUDA_TRY(c, ensure(c->tcache, (size_t)g.nz * G * sizeof(float2), false, s));
+    return BIP_OK;
+}
+
+// ... of the S2 build, its columns in `cols`.
+bip_status alloc_s2(bip_ctx* c, DevBuf& cols, cudaStream_t s) {
+    const bip_config& g = c->cfg;
+    const size_t win2 = (size_t)g.win * g.win, G = (size_t)g.ny * g.nx;
+    CUDA_TRY(c, ensure(c->stash2, (size_t)c->n_sites * c->geo.Bp2 * win2 * sizeof(float2), false, s));
+    CUDA_TRY(c, ensure(cols, (size_t)std::max(c->geo.Bp1, c->geo.Bp2) * G * sizeof(float2), false, s));
+    CUDA_TRY(c, ensure(c->tcache, (size_t)g.nz * G * sizeof(float2), false, s));
+    return BIP_OK;
+}
+
+// S1's forward sweep (Eq. smatrix-advance) on columns `cols`, stashing the
+// windows of each plane's sites; with `transmission` it first computes T_j
+// of the slices it crosses into the table.
+bip_status sweep_s1(bip_ctx* c, const float* V, float2* cols, bool transmission, cudaStream_t s) {
+    const bip_config& g = c->cfg;
+    const size_t G = (size_t)g.ny * g.nx;
+    const MsPlan plan = plan_for(c, c->geo.Bp1, c->shift1);
+    int last = 0;
+    for (auto& sd : c->sites) last = std::max(last, (int)sd.plane);
+    if (transmission)
+        TIMED(c, BIP_STAGE_TRANSMISSION, s, bip_transmission(V, (float)c->geo.sigma, 0, last, G, (float2*)c->tcache.p, s));
+    for (int j = 0; j <= last; ++j) {
+        MsRowArgs a{};
+        a.cols = cols;
+        a.init = j == 0;
+        a.init_val = 1.0f;
+        a.do_ifft = j > 0;
+        a.v_pre = nullptr;
+        a.v_post = j < last ? V + (size_t)j * G : nullptr;
+        a.t_slice = j < last ? (const float2*)c->tcache.p + (size_t)j * G : nullptr;
+        a.do_fft = j < last;
+        if (c->plane_off[j + 1] > c->plane_off[j]) {
+            a.row_off = (const int32_t*)c->row_off_d.p + (size_t)j * (g.ny + 1);
+            a.row_ent = (const int4*)c->row_ent_d.p;
+        }
+        a.win = g.win;
+        a.stash = (float2*)c->stash1.p;
+        TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
+        if (j < last) TIMED(c, BIP_STAGE_MS_COL, s, bip_ms_col_pass(plan, cols, s));
+    }
+    return BIP_OK;
+}
+
+// S2's backward sweep (Eq. s2) on columns `cols` from the exit surface to
+// the shallowest plane with a site.
+bip_status sweep_s2(bip_ctx* c, const float* V, float2* cols, bool transmission, cudaStream_t s) {
+    const bip_config& g = c->cfg;
+    const size_t G = (size_t)g.ny * g.nx;
+    const MsPlan plan = plan_for(c, c->geo.Bp2, c->shift2);
+    int first = g.nz - 1;
+    for (auto& sd : c->sites) first = std::min(first, (int)sd.plane);
+    // start: G^{-1/2} constant, forward row FFT, then the first propagator
+    {
+        MsRowArgs a{};
+        a.cols = cols;
+        a.init = 1;
+        a.init_val = (float)(1.0 / std::sqrt((double)G));
+        a.do_fft = 1;
+        a.win = g.win;
+        a.stash = (float2*)c->stash2.p;
+        TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
+        TIMED(c, BIP_STAGE_MS_COL, s, bip_ms_col_pass(plan, cols, s));
+    }
+    if (transmission)
+        TIMED(c, BIP_STAGE_TRANSMISSION, s, bip_transmission(V, (float)c->geo.sigma, first, g.nz, G, (float2*)c->tcache.p, s));
+    for (int j = g.nz - 1; j >= first; --j) {
+        MsRowArgs a{};
+        a.cols = cols;
+        a.do_ifft = 1;
+        a.v_pre = V + (size_t)j * G;
+        a.t_slice = (const float2*)c->tcache.p + (size_t)j * G;
+        a.do_fft = j > first;
+        if (c->plane_off[j + 1] > c->plane_off[j]) {
+            a.row_off = (const int32_t*)c->row_off_d.p + (size_t)j * (g.ny + 1);
+            a.row_ent = (const int4*)c->row_ent_d.p;
+        }
+        a.win = g.win;
+        a.stash = (float2*)c->stash2.p;
+        TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
+        if (j > first) TIMED(c, BIP_STAGE_MS_COL, s, bip_ms_col_pass(plan, cols, s));
+    }
+    return BIP_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -711,8 +809,11 @@ bip_status bip_destroy(bip_ctx* c) {
                      &c->ray, &c->rax, &c->g_tA, &c->g_tB, &c->g_sA2, &c->g_sB2, &c->cubeA, &c->cubeB,
                      &c->cube_work, &c->cube_mask, &c->s1t, &c->psi, &c->ybuf, &c->cube_grp, &c->cube_wmap, &c->mpart,
                      &c->hcube, &c->shcube, &c->cstash, &c->ccols, &c->xopA, &c->xopB, &c->xm32, &c->tcache,
-                     &c->cr_ay, &c->cr_ax, &c->cr_cy, &c->cr_cx, &c->cr_T, &c->nf_count, &c->tw512};
+                     &c->cr_ay, &c->cr_ax, &c->cr_cy, &c->cr_cx, &c->cr_T, &c->nf_count, &c->tw512, &c->cols2};
     for (DevBuf* b : all) release(*b);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     for (int i = 0; i < 6; ++i) {
         release(c->aw1[i]);
         release(c->aw2[i]);
@@ -770,37 +871,10 @@ bip_status bip_build_s1(bip_ctx* c, const float* V, const bip_atom* atoms, int32
     cudaStream_t s = (cudaStream_t)stream;
     bip_status st = build_common(c, V, atoms, n_atoms, s);
     if (st != BIP_OK) return st;
-    const bip_config& g = c->cfg;
-    const int ncol = c->geo.Bp1;
-    const size_t win2 = (size_t)g.win * g.win;
-    const size_t G = (size_t)g.ny * g.nx;
-    CUDA_TRY(c, ensure(c->stash1, (size_t)c->n_sites * ncol * win2 * sizeof(float2), false, s));
-    CUDA_TRY(c, ensure(c->cols, (size_t)std::max(c->geo.Bp1, c->geo.Bp2) * G * sizeof(float2), false, s));
-    const MsPlan plan = plan_for(c, ncol, c->shift1);
-    int last = 0;
-    for (auto& sd : c->sites) last = std::max(last, (int)sd.plane);
-    // the transmissions of the slices the sweep crosses, once
-    CUDA_TRY(c, ensure(c->tcache, (size_t)g.nz * G * sizeof(float2), false, s));
-    TIMED(c, BIP_STAGE_TRANSMISSION, s, bip_transmission(V, (float)c->geo.sigma, 0, last, G, (float2*)c->tcache.p, s));
-    for (int j = 0; j <= last; ++j) {
-        MsRowArgs a{};
-        a.cols = (float2*)c->cols.p;
-        a.init = j == 0;
-        a.init_val = 1.0f;
-        a.do_ifft = j > 0;
-        a.v_pre = nullptr;
-        a.v_post = j < last ? V + (size_t)j * G : nullptr;
-        a.t_slice = j < last ? (const float2*)c->tcache.p + (size_t)j * G : nullptr;
-        a.do_fft = j < last;
-        if (c->plane_off[j + 1] > c->plane_off[j]) {
-            a.row_off = (const int32_t*)c->row_off_d.p + (size_t)j * (g.ny + 1);
-            a.row_ent = (const int4*)c->row_ent_d.p;
-        }
-        a.win = g.win;
-        a.stash = (float2*)c->stash1.p;
-        TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
-        if (j < last) TIMED(c, BIP_STAGE_MS_COL, s, bip_ms_col_pass(plan, (float2*)c->cols.p, s));
-    }
+    st = alloc_s1(c, s);
+    if (st != BIP_OK) return st;
+    st = sweep_s1(c, V, (float2*)c->cols.p, true, s);
+    if (st != BIP_OK) return st;
     c->s1 = true;
     c->sig1 = site_signature(c->sites);
     return BIP_OK;
@@ -811,47 +885,46 @@ bip_status bip_build_s2(bip_ctx* c, const float* V, const bip_atom* atoms, int32
     cudaStream_t s = (cudaStream_t)stream;
     bip_status st = build_common(c, V, atoms, n_atoms, s);
     if (st != BIP_OK) return st;
-    const bip_config& g = c->cfg;
-    const int ncol = c->geo.Bp2;
-    const size_t win2 = (size_t)g.win * g.win;
-    const size_t G = (size_t)g.ny * g.nx;
-    CUDA_TRY(c, ensure(c->stash2, (size_t)c->n_sites * ncol * win2 * sizeof(float2), false, s));
-    CUDA_TRY(c, ensure(c->cols, (size_t)std::max(c->geo.Bp1, c->geo.Bp2) * G * sizeof(float2), false, s));
-    const MsPlan plan = plan_for(c, ncol, c->shift2);
-    int first = g.nz - 1;
-    for (auto& sd : c->sites) first = std::min(first, (int)sd.plane);
-    // start: G^{-1/2} constant, forward row FFT, then the first propagator
-    {
-        MsRowArgs a{};
-        a.cols = (float2*)c->cols.p;
-        a.init = 1;
-        a.init_val = (float)(1.0 / std::sqrt((double)G));
-        a.do_fft = 1;
-        a.win = g.win;
-        a.stash = (float2*)c->stash2.p;
-        TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
-        TIMED(c, BIP_STAGE_MS_COL, s, bip_ms_col_pass(plan, (float2*)c->cols.p, s));
-    }
-    CUDA_TRY(c, ensure(c->tcache, (size_t)g.nz * G * sizeof(float2), false, s));
-    TIMED(c, BIP_STAGE_TRANSMISSION, s, bip_transmission(V, (float)c->geo.sigma, first, g.nz, G, (float2*)c->tcache.p, s));
-    for (int j = g.nz - 1; j >= first; --j) {
-        MsRowArgs a{};
-        a.cols = (float2*)c->cols.p;
-        a.do_ifft = 1;
-        a.v_pre = V + (size_t)j * G;
-        a.t_slice = (const float2*)c->tcache.p + (size_t)j * G;
-        a.do_fft = j > first;
-        if (c->plane_off[j + 1] > c->plane_off[j]) {
-            a.row_off = (const int32_t*)c->row_off_d.p + (size_t)j * (g.ny + 1);
-            a.row_ent = (const int4*)c->row_ent_d.p;
-        }
-        a.win = g.win;
-        a.stash = (float2*)c->stash2.p;
-        TIMED(c, BIP_STAGE_MS_ROW, s, bip_ms_row_pass(plan, a, s));
-        if (j > first) TIMED(c, BIP_STAGE_MS_COL, s, bip_ms_col_pass(plan, (float2*)c->cols.p, s));
-    }
+    st = alloc_s2(c, c->cols, s);
+    if (st != BIP_OK) return st;
+    st = sweep_s2(c, V, (float2*)c->cols.p, true, s);
+    if (st != BIP_OK) return st;
     c->s2 = true;
     c->sig2 = site_signature(c->sites);
+    return BIP_OK;
+}
+
+bip_status bip_build(bip_ctx* c, const float* V, const bip_atom* atoms, int32_t n_atoms, void* stream) {
+    BIP_RANGE("bip_build");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c) return BIP_ERR_INVALID_ARG;
+    if (capturing(s)) return fail(c, BIP_ERR_INVALID_ARG, "bip_build is not capturable");
+    bip_status st = build_common(c, V, atoms, n_atoms, s);
+    if (st != BIP_OK) return st;
+    // everything the two sweeps write is allocated before they fork
+    st = alloc_s1(c, s);
+    if (st == BIP_OK) st = alloc_s2(c, c->cols2, s);
+    if (st != BIP_OK) return st;
+    if (!c->side) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    if (!c->ev_fork) CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    if (!c->ev_join) CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    // the transmissions of every slice, once, before the fork (both sweeps read them)
+    const size_t G = (size_t)c->cfg.ny * c->cfg.nx;
+    TIMED(c, BIP_STAGE_TRANSMISSION, s, bip_transmission(V, (float)c->geo.sigma, 0, c->cfg.nz, G,
+                                                         (float2*)c->tcache.p, s));
+    c->s1 = c->s2 = false;
+    CUDA_TRY(c, cudaEventRecord(c->ev_fork, s));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    // S1 on the caller's stream, S2 on the side stream; the caller's stream
+    // waits for S2 whatever happened, so nothing of it runs on unjoined
+    const bip_status st1 = sweep_s1(c, V, (float2*)c->cols.p, false, s);
+    const bip_status st2 = st1 == BIP_OK ? sweep_s2(c, V, (float2*)c->cols2.p, false, c->side) : st1;
+    const cudaError_t e1 = cudaEventRecord(c->ev_join, c->side);
+    const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(s, c->ev_join, 0) : e1;
+    if (st2 != BIP_OK) return st2;
+    CUDA_TRY(c, e2);
+    c->s1 = c->s2 = true;
+    c->sig1 = c->sig2 = site_signature(c->sites);
     return BIP_OK;
 }
 

@@ -200,7 +200,7 @@ def test_nvtx_stage_ranges(lib, tmp_path):
     lines = record.read_text().splitlines()
     assert nvtx_tool.nesting_ok(lines)
     names = [ln[5:] for ln in lines if ln.startswith("push ")]
-    for n in ("bip_create", "bip_build_s1", "bip_build_s2", "bip_coreloss_map", "bip:transmission",
+    for n in ("bip_create", "bip_build", "bip_coreloss_map", "bip:transmission",
               "bip:ms_row", "bip:ms_col", "bip:reconstruct", "bip:coupling", "bip:gram", "bip:quadform",
               "bip:reduce"):
         assert n in names, n
@@ -215,3 +215,46 @@ def test_nvtx_stage_ranges(lib, tmp_path):
         else:
             top.pop()
             depth -= 1
+
+
+@pytest.mark.parametrize("grid", [128, 512])
+def test_combined_build_equals_separate_builds(lib, grid):
+    """bip_build (S2's sweep on the context's side stream, beside S1's)
+    leaves stashes bit-identical to bip_build_s1 followed by bip_build_s2,
+    and the same map; a second combined build on the same context too."""
+    capi, BipContext = lib
+    if grid == 128:
+        cfg = synth.config1().replace(ion_slices=(0, 5), ion_cells=(0, 3))   # sites in every plane
+    else:
+        cfg = synth.config1().replace(name="grid512", ny=512, nx=512, ly=40.0, lx=40.0, cells_y=16, cells_x=16,
+                                      nz=6, e0=300e3, alpha=0.020, theta_det=0.030, fy=8, fx=8,
+                                      ion_slices=(1, 5), ion_cells=(7, 9))
+    sp = synth.make_specimen(cfg)
+    V, H = _inputs(cfg, sp)
+    atoms = capi.make_atoms(sp.atoms, sp.nch)
+    out = {}
+    for mode in ("separate", "combined"):
+        ctx = BipContext(cfg, prec="mixed")
+        try:
+            if mode == "separate":
+                capi.bip_build_s1(ctx.ctx, V, atoms)
+                capi.bip_build_s2(ctx.ctx, V, atoms)
+                ctx.n_sites = capi.bip_query(ctx.ctx)[4]
+                ctx._atoms = atoms
+            else:
+                ctx.build(V, sp.atoms, sp.nch)
+                ctx.build(V, sp.atoms, sp.nch)
+            st = []
+            for w in (1, 2):
+                t = torch.empty(capi.stash_shape(ctx.ctx, w), dtype=torch.complex64, device="cuda")
+                capi.bip_export_stash(ctx.ctx, w, t)
+                st.append(t)
+            m = ctx.map(H, sp.scans)
+            torch.cuda.synchronize()
+            out[mode] = (st, m.cpu().numpy())
+        finally:
+            ctx.close()
+    (s_a, m_a), (s_b, m_b) = out["separate"], out["combined"]
+    assert s_a[0].shape[0] >= 2
+    assert torch.equal(s_a[0], s_b[0]) and torch.equal(s_a[1], s_b[1])
+    assert np.array_equal(m_a, m_b)
