@@ -31,6 +31,7 @@ std::mutex g_mu;
 std::string g_dir;                       // empty: no cache
 bool g_env_read = false;
 std::atomic<int64_t> g_hits{0}, g_misses{0}, g_rejected{0};
+std::atomic<uint64_t> g_tmp_seq{0};       // temporary file names unique within the process
 
 uint64_t fnv1a(const void* p, size_t n, uint64_t h = 1469598103934665603ull) {
     const unsigned char* b = (const unsigned char*)p;
@@ -197,7 +198,10 @@ bool read_file(const std::string& path, std::vector<unsigned char>& out) {
 }
 
 void write_file(const std::string& path, const std::vector<unsigned char>& bytes) {
-    const std::string tmp = path + ".tmp." + std::to_string((long long)getpid());
+    // unique per process and write, so concurrent writers (threads or
+    // processes) never share a temporary file; the rename is atomic
+    const std::string tmp = path + ".tmp." + std::to_string((long long)getpid()) + "." +
+                            std::to_string((unsigned long long)++g_tmp_seq);
     FILE* f = std::fopen(tmp.c_str(), "wb");
     if (!f) return;                      // an unwritable cache only costs the rebuild
     const bool ok = std::fwrite(bytes.data(), 1, bytes.size(), f) == bytes.size();

@@ -209,3 +209,35 @@ def test_load_builds_refuses_another_configuration(capi, tmp_path):
     finally:
         a.close()
         b.close()
+
+
+def test_geometry_cache_concurrent_creates(capi, cache_dir):
+    """Contexts created from several threads at once (ctypes releases the
+    interpreter lock during the call) with the cache on: every geometry is
+    right, the cache ends with one valid file, no temporary file is left."""
+    import threading
+    cfg = synth.config1().replace(nrad1=3, nrad2=3)
+    capi.bip_set_geometry_cache(None)
+    want = _geometry(capi, cfg)
+    capi.bip_set_geometry_cache(str(cache_dir))
+    got, errors = [], []
+
+    def worker():
+        try:
+            for _ in range(3):
+                got.append(_geometry(capi, cfg))
+        except Exception as e:                  # noqa: BLE001 -- reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker) for _ in range(6)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors
+    assert len(got) == 18 and all(_same(g, want) for g in got)
+    files = os.listdir(cache_dir)
+    assert len(files) == 1 and files[0].endswith(".bin"), files
+    s0 = capi.bip_geometry_cache_stats()
+    assert _same(_geometry(capi, cfg), want)
+    assert _stats_since(capi, s0) == (1, 0, 0)
