@@ -56,7 +56,7 @@ typedef enum {
     BIP_ERR_OOM = 3,           /* a device or host allocation failed          */
     BIP_ERR_CUDA = 4,          /* a CUDA call failed (text in bip_last_error) */
     BIP_ERR_TIMEOUT = 5,       /* a device-side wait gave up                  */
-    BIP_ERR_UNSUPPORTED = 6,   /* valid request this build does not implement */
+    BIP_ERR_UNSUPPORTED = 6,   /* valid request the library does not implement */
     BIP_ERR_NUMERIC = 7        /* an output holds NaN or Inf (only with
                                   bip_set_check_finite on)                    */
 } bip_status;
