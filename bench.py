@@ -3,8 +3,8 @@
 
 Metric: atom x probe core-loss evaluations per second -- (ionized sites x
 scan positions) / time of one whole map evaluation (S1 build + S2 build +
-window reconstruction + coupling + Gram + quadratic form + site sum),
-inputs resident in HBM.  Workload: the 512^2 x 100-slice synthetic crystal
+window reconstruction + coupling + Gram + quadratic form + site sum; the
+two builds' sweeps side by side on two streams), inputs resident in HBM.  Workload: the 512^2 x 100-slice synthetic crystal
 with 1600 ionized sites (3 channels each) and 128 x 128 scans (config2 in
 synth/configs.py).  The mixed path (FP16 reconstruction sums, BF16
 coupling and Gram on tcgen05, FP32 accumulation) is the headline; the
@@ -13,8 +13,9 @@ compared with the FP32 map, and the line ends with that comparison.
 
 Multi-GPU (torchrun): each rank evaluates an independent frozen-phonon
 configuration (its own seeded jitter), so per-GPU work is fixed (weak
-scaling); the maps are averaged over ranks with one all-reduce per step,
-the incoherent frozen-phonon average of the method.
+scaling) and no step exchanges data; after the timed steps the maps are
+averaged over ranks with one all-reduce, the incoherent frozen-phonon
+average of the method.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload on this machine's host cores (there is no runnable reference
