@@ -165,12 +165,11 @@ cudaError_t launch_adj_row(const MsPlan& p, const MsAdjArgs& a, int* groups, cud
     *groups = gpy;
     const long long blocks = (long long)p.ny * gpy;
     const size_t sm = ((size_t)2 * RPB * NX + 2 * NX) * sizeof(float2) + (size_t)RPB * NX * sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(adj_row_kernel<NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<bool> attr{false};
+    const cudaError_t e = bip_set_once(attr, [&] {
+        return cudaFuncSetAttribute(adj_row_kernel<NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    });
+    if (e != cudaSuccess) return e;
     adj_row_kernel<NX><<<(unsigned)blocks, kThreads, sm, s>>>(p, a);
     return cudaGetLastError();
 }

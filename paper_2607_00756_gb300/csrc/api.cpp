@@ -1352,14 +1352,17 @@ int gram_planes(int prec) { return prec == BIP_PREC_SPLIT_BF16 ? 4 : 2; }
 // -- above 16 -- small enough that the batch's coupling output (which the
 // Gram re-reads several times) stays within 1.2 x the L2 cache.
 int tc_batch(const bip_ctx* c) {
-    static int sms = 0, l2 = 0;
-    if (!sms) {
-        int dev = 0;
+    // the device's SM count and L2 size, read once (thread-safe
+    // initialisation; one GPU per process)
+    static const int2 dev_info = [] {
+        int dev = 0, sms = 0, l2 = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
             sms = 148;
         if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || l2 < 1) l2 = 64 << 20;
-    }
+        return int2{sms, l2};
+    }();
+    const int sms = dev_info.x, l2 = dev_info.y;
     const int npl = gram_planes(c->prec);
     const double mt_site = 2.0 * npl * c->Bpad * (double)c->nch_max * c->Dpad;   // bytes of Mt per site
     // at least 16 sites: fewer leave the Gram (a few tiles per site) without

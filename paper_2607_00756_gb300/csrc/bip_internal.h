@@ -2,8 +2,10 @@
 // launchers of every CUDA kernel.  Host code only (no device code here).
 #pragma once
 
+#include <atomic>
 #include <complex>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -13,6 +15,35 @@
 
 // ---------------------------------------------------------------------------
 // host geometry (FP64), built once per context
+
+// Runs `set` (a kernel's launch attributes, set once per process: the
+// library serves one GPU per process) until it first succeeds, safely when
+// several host threads launch at once.
+inline std::mutex& bip_attr_mutex() {
+    static std::mutex m;
+    return m;
+}
+template <class F>
+cudaError_t bip_set_once(std::atomic<bool>& done, F&& set) {
+    if (done.load(std::memory_order_acquire)) return cudaSuccess;
+    std::lock_guard<std::mutex> lk(bip_attr_mutex());
+    if (done.load(std::memory_order_relaxed)) return cudaSuccess;
+    const cudaError_t e = set();
+    if (e == cudaSuccess) done.store(true, std::memory_order_release);
+    return e;
+}
+// Runs `set` (raising a kernel's dynamic shared-memory limit to `bytes`)
+// when `bytes` is above the largest size it succeeded for so far (`cur`),
+// safely when several host threads launch at once.
+template <class F>
+cudaError_t bip_raise_once(std::atomic<size_t>& cur, size_t bytes, F&& set) {
+    if (bytes <= cur.load(std::memory_order_acquire)) return cudaSuccess;
+    std::lock_guard<std::mutex> lk(bip_attr_mutex());
+    if (bytes <= cur.load(std::memory_order_relaxed)) return cudaSuccess;
+    const cudaError_t e = set();
+    if (e == cudaSuccess) cur.store(bytes, std::memory_order_release);
+    return e;
+}
 
 struct BipGeometry {
     double lambda = 0.0;      // electron wavelength, Angstrom

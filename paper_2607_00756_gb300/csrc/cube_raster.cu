@@ -255,19 +255,19 @@ cudaError_t bip_cube_raster(const CubeRasterArgs& a, cudaStream_t s) {
     if ((size_t)a.nky * kTileElems > (size_t)kPf * kThreads) return cudaErrorInvalidValue;
     if (sm1 > 200 * 1024 || sm2 > 200 * 1024) return cudaErrorInvalidValue;
     if (a.My > 65535 * kMy || a.Mx > 65535 * kMx) return cudaErrorInvalidValue;
-    static size_t attr1 = 0, attr2 = 0;
+    static std::atomic<size_t> attr1{0}, attr2{0};
     cudaError_t e;
-    if (sm1 > 48 * 1024 && sm1 > attr1) {
-        if ((e = cudaFuncSetAttribute(cube_raster_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1)) !=
-            cudaSuccess)
-            return e;
-        attr1 = sm1;
+    if (sm1 > 48 * 1024) {
+        e = bip_raise_once(attr1, sm1, [&] {
+            return cudaFuncSetAttribute(cube_raster_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+        });
+        if (e != cudaSuccess) return e;
     }
-    if (sm2 > 48 * 1024 && sm2 > attr2) {
-        if ((e = cudaFuncSetAttribute(cube_raster_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) !=
-            cudaSuccess)
-            return e;
-        attr2 = sm2;
+    if (sm2 > 48 * 1024) {
+        e = bip_raise_once(attr2, sm2, [&] {
+            return cudaFuncSetAttribute(cube_raster_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+        });
+        if (e != cudaSuccess) return e;
     }
     cube_raster_t_kernel<<<dim3(a.nd_pad / kD, a.nch, a.n_sites), kThreads, sm1, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

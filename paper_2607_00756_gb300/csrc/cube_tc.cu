@@ -393,13 +393,11 @@ __global__ void map_reduce_kernel(MapReduceArgs a) {
 
 template <bool HI, int TN>
 cudaError_t launch_cube(const CubeTcArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e =
-            cudaFuncSetAttribute(cube_tc_kernel<HI, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<bool> attr{false};
+    const cudaError_t e = bip_set_once(attr, [&] {
+        return cudaFuncSetAttribute(cube_tc_kernel<HI, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    });
+    if (e != cudaSuccess) return e;
     const int units = a.cube ? a.n_groups * a.mt_per : a.n_work * a.mt_per;
     const int grid = units < num_sms() ? units : num_sms();
     cube_tc_kernel<HI, TN><<<grid, kThreads, kSmem, s>>>(ma, mb, a);

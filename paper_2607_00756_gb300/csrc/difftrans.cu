@@ -212,11 +212,12 @@ cudaError_t bip_raster_eval(const DiffArgs& a, const RasterArgs& r, cudaStream_t
     const size_t nd = (size_t)(2 * a.Ky + 1) * (4 * a.Kx + 1);
     const size_t sm = (nd + (size_t)kRasterRows * (4 * a.Kx + 1)) * sizeof(float2);
     if (sm > 200 * 1024) return cudaErrorInvalidValue;
-    static size_t attr = 0;
-    if (sm > 48 * 1024 && sm > attr) {
-        cudaError_t e = cudaFuncSetAttribute(raster_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static std::atomic<size_t> attr{0};
+    if (sm > 48 * 1024) {
+        const cudaError_t e = bip_raise_once(attr, sm, [&] {
+            return cudaFuncSetAttribute(raster_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        });
         if (e != cudaSuccess) return e;
-        attr = sm;
     }
     raster_eval_kernel<<<dim3((r.My + kRasterRows - 1) / kRasterRows, a.n_sites), 128, sm, s>>>(a, r);
     return cudaGetLastError();
@@ -227,11 +228,12 @@ cudaError_t bip_diff_bin(const DiffArgs& a, cudaStream_t s) {
     const size_t sm = (size_t)a.B * (sizeof(int2) + sizeof(float2)) +
                       (size_t)(2 * a.Ky + 1) * (2 * a.Kx + 1) * sizeof(int);
     if (sm > 200 * 1024) return cudaErrorInvalidValue;
-    static size_t attr = 0;
-    if (sm > 48 * 1024 && sm > attr) {
-        cudaError_t e = cudaFuncSetAttribute(diff_bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static std::atomic<size_t> attr{0};
+    if (sm > 48 * 1024) {
+        const cudaError_t e = bip_raise_once(attr, sm, [&] {
+            return cudaFuncSetAttribute(diff_bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        });
         if (e != cudaSuccess) return e;
-        attr = sm;
     }
     dim3 grid((nd + kBinWarps - 1) / kBinWarps, a.n_sites);
     diff_bin_kernel<<<grid, kBinWarps * 32, sm, s>>>(a);
@@ -243,25 +245,31 @@ cudaError_t bip_diff_eval(const DiffArgs& a, cudaStream_t s) {
     const size_t nd = (size_t)(2 * a.Ky + 1) * (4 * a.Kx + 1);
     const size_t sm = nd * sizeof(float2);
     if (sm > 200 * 1024) return cudaErrorInvalidValue;
-    static size_t attr = 0;
-    if (sm > 48 * 1024 && sm > attr) {
-        cudaError_t e = cudaFuncSetAttribute(diff_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static std::atomic<size_t> attr{0};
+    if (sm > 48 * 1024) {
+        const cudaError_t e = bip_raise_once(attr, sm, [&] {
+            return cudaFuncSetAttribute(diff_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        });
         if (e != cudaSuccess) return e;
-        attr = sm;
     }
     // persistent grid: every resident block slot, at most one block per item
     static int per_sm = 0, sms = 0;
     static size_t sm_at = 0;
-    if (per_sm == 0 || sm_at != sm) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, diff_eval_kernel, 256, sm) != cudaSuccess ||
-            per_sm < 1)
-            per_sm = 1;
-        sm_at = sm;
+    int slots;
+    {
+        std::lock_guard<std::mutex> lk(bip_attr_mutex());
+        if (per_sm == 0 || sm_at != sm) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, diff_eval_kernel, 256, sm) != cudaSuccess ||
+                per_sm < 1)
+                per_sm = 1;
+            sm_at = sm;
+        }
+        slots = per_sm * sms;
     }
-    const int grid = a.n_work < per_sm * sms ? a.n_work : per_sm * sms;
+    const int grid = a.n_work < slots ? a.n_work : slots;
     diff_eval_kernel<<<grid, 256, sm, s>>>(a);
     return cudaGetLastError();
 }

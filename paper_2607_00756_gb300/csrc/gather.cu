@@ -197,11 +197,12 @@ cudaError_t launch(const GatherArgs& a, cudaStream_t s) {
     dim3 grid(a.K / kPix, (a.grp.n_groups + gpb - 1) / gpb, a.n_sites);
     const size_t sm = (size_t)a.Bp * 32 * (sizeof(float4) + sizeof(float2)) +
                       (MAXCH > 3 ? (size_t)MAXCH * 32 * sizeof(float4) : 0);
-    static size_t attr = 0;
-    if (sm > 48 * 1024 && sm > attr) {
-        cudaError_t e = cudaFuncSetAttribute(gather_kernel<MAXCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static std::atomic<size_t> attr{0};
+    if (sm > 48 * 1024) {
+        const cudaError_t e = bip_raise_once(attr, sm, [&] {
+            return cudaFuncSetAttribute(gather_kernel<MAXCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        });
         if (e != cudaSuccess) return e;
-        attr = sm;
     }
     gather_kernel<MAXCH><<<grid, kThreads, sm, s>>>(a);
     return cudaGetLastError();

@@ -366,13 +366,12 @@ template <int N, int EPI, int NPL, bool F8>
 cudaError_t launch(const TcArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mbt, int grid,
                    cudaStream_t s) {
     constexpr size_t smem = TcShape<N, NPL>::SMEM;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e =
-            cudaFuncSetAttribute(tc_kernel<N, EPI, NPL, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<bool> attr{false};
+    const cudaError_t e = bip_set_once(attr, [&] {
+        return cudaFuncSetAttribute(tc_kernel<N, EPI, NPL, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    });
+    if (e != cudaSuccess) return e;
     tc_kernel<N, EPI, NPL, F8><<<grid, kThreads, smem, s>>>(ma, mb, mbt, a);
     return cudaGetLastError();
 }

@@ -570,12 +570,11 @@ cudaError_t launch_row(const MsPlan& p, const MsRowArgs& a, cudaStream_t s) {
     constexpr int RPB = RowShape<NX>::RPB, ROWLEN = NX;
     const long long blocks = (long long)p.ny * ((p.ncol + RPB - 1) / RPB);
     const size_t sm = ((size_t)2 * RPB * ROWLEN + 2 * NX) * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(row_pass_kernel<NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<bool> attr{false};
+    const cudaError_t e = bip_set_once(attr, [&] {
+        return cudaFuncSetAttribute(row_pass_kernel<NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    });
+    if (e != cudaSuccess) return e;
     row_pass_kernel<NX><<<(unsigned)blocks, kThreads, sm, s>>>(p, a);
     return cudaGetLastError();
 }
@@ -584,21 +583,20 @@ cudaError_t launch_row_hw512(const MsPlan& p, const MsRowArgs& a, cudaStream_t s
     using namespace hw512;
     const int groups = (p.ncol + RPB - 1) / RPB;
     const size_t sm = ((size_t)RPB * ROWBUF + NTW + 2 * N) * sizeof(float2);
-    static bool attr = false;
-    static int per_sm = 0, sms = 0;
-    if (!attr) {
+    static std::atomic<bool> attr{false};
+    static int per_sm = 0, sms = 0;              // written once, before attr is set
+    const cudaError_t e0 = bip_set_once(attr, [&] {
         cudaError_t e = cudaFuncSetAttribute(row_pass_hw512_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sm);
-        if (e != cudaSuccess) return e;
         int dev = 0;
-        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, row_pass_hw512_kernel, kThreads, sm);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        attr = true;
-    }
+        if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+        return e;
+    });
+    if (e0 != cudaSuccess) return e0;
     // persistent: whole rounds of the resident blocks, a multiple of the
     // column groups, at most one block per (group, y)
     long long blocks = (long long)sms * per_sm / groups * groups;
@@ -613,12 +611,11 @@ cudaError_t launch_col(const MsPlan& p, float2* cols, cudaStream_t s) {
     using C = ColShape<NY>;
     if (p.nx % C::XB != 0) return cudaErrorInvalidValue;
     const size_t sm = (size_t)NY * C::XB * sizeof(float2) + NY * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(col_pass_kernel<NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<bool> attr{false};
+    const cudaError_t e = bip_set_once(attr, [&] {
+        return cudaFuncSetAttribute(col_pass_kernel<NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    });
+    if (e != cudaSuccess) return e;
     dim3 grid(p.nx / C::XB, p.ncol);
     col_pass_kernel<NY><<<grid, C::THREADS, sm, s>>>(p, cols);
     return cudaGetLastError();

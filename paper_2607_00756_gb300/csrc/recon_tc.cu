@@ -595,13 +595,14 @@ cudaError_t bip_recon_tc(const ReconArgs& a, cudaStream_t s) {
     e = make_map_2d(&mx, a.Xb, a.x_rows, 64, kN);
     if (e != cudaSuccess) return e;
     if (a.f8 && (!a.inv_row[0] || !a.inv_row[1])) return cudaErrorInvalidValue;
-    static bool attr[2] = {false, false};
-    if (!attr[a.f8 ? 1 : 0]) {
-        e = a.f8 ? cudaFuncSetAttribute(recon_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem)
-                 : cudaFuncSetAttribute(recon_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-        if (e != cudaSuccess) return e;
-        attr[a.f8 ? 1 : 0] = true;
-    }
+    static std::atomic<bool> attr[2];
+    e = bip_set_once(attr[a.f8 ? 1 : 0], [&] {
+        return a.f8 ? cudaFuncSetAttribute(recon_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kSmem)
+                    : cudaFuncSetAttribute(recon_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kSmem);
+    });
+    if (e != cudaSuccess) return e;
     const int units = a.n_sites * (a.side[0].mt_tiles + a.side[1].mt_tiles) * a.chunks;
     const int grid = units < num_sms() ? units : num_sms();
     if (a.f8)

@@ -202,13 +202,13 @@ cudaError_t make_map_2d(CUtensorMap* m, const void* base, int64_t rows, int k, i
 }
 
 int num_sms() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
+    // thread-safe one-time initialisation (one GPU per process)
+    static const int n = [] {
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 148;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 148;
+    }();
     return n;
 }
 
