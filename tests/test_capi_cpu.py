@@ -115,6 +115,15 @@ def test_calls_out_of_order_return_errors(capi):
         assert "slice" in capi.bip_last_error(ctx)
         atoms = capi.make_atoms(np.array([[1.0, 1.0, 0.0]]), np.array([0]))
         assert lib.bip_build_s1(ctx, dummy, atoms, 1, None) == 1      # nothing ionized
+        # the combined build checks the same arguments before any device work
+        assert lib.bip_build(None, dummy, atoms, 1, None) == 1
+        assert lib.bip_build(ctx, None, atoms, 1, None) == 1          # V is null
+        assert lib.bip_build(ctx, dummy, atoms, 1, None) == 1         # nothing ionized
+        assert "ionized" in capi.bip_last_error(ctx)
+        atoms = capi.make_atoms(np.array([[1.0, 1.0, 9.0]]), np.array([3]))
+        assert lib.bip_build(ctx, dummy, atoms, 1, None) == 1         # slice 9 >= nz
+        assert "slice" in capi.bip_last_error(ctx)
+        assert capi.bip_query(ctx)[4] == 0                            # nothing built
     finally:
         capi.bip_destroy(ctx)
     assert capi.lib().bip_last_error(None) == b"null context"
