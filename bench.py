@@ -82,8 +82,10 @@ def phonon_mean(out, world):
 # workload
 
 def workload(name, rank, max_sites=0, scan_side=0):
+    """The named workload (config2 ...) or one given as a JSON file of a
+    synth.Config (synth.config_to_json writes one)."""
     import synth
-    cfg = synth.CONFIGS[name]()
+    cfg = synth.load_config(name)
     if rank:
         cfg = cfg.replace(seed=rank)          # another frozen-phonon configuration
     sp = synth.make_specimen(cfg)
@@ -953,7 +955,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config2")
+    ap.add_argument("--workload", default="config2",
+                    help="a named workload (config1, config2, config3, config5) or a synth.Config JSON file")
     ap.add_argument("--order", default="gram", choices=ORDERS,
                     help="scan contraction of the map (analysis; the headline runs the Gram route)")
     ap.add_argument("--scan-side", type=int, default=0,

@@ -8,10 +8,11 @@ hydrogenic transition potentials) are not available; these Gaussian-atom
 crystals stand in for them with the same shape regime.
 """
 from .prng import SplitMix64
-from .configs import Config, config1, config2, config3, config5, tiny_config, CONFIGS
+from .configs import (Config, config1, config2, config3, config5, tiny_config, CONFIGS, config_to_json,
+                      config_from_json, load_config)
 from .specimen import Specimen, make_specimen, window_origin, site_window_inputs
 
 __all__ = [
     "SplitMix64", "Config", "config1", "config2", "config3", "config5", "tiny_config",
-    "CONFIGS", "Specimen", "make_specimen", "window_origin", "site_window_inputs",
+    "CONFIGS", "config_to_json", "config_from_json", "load_config", "Specimen", "make_specimen", "window_origin", "site_window_inputs",
 ]

@@ -3,7 +3,8 @@
 Lengths in Angstrom, angles in rad, energies in eV, potentials in V*Angstrom.
 Slices are indexed from 0; "the third slice" of a five-slice cell is index 2.
 """
-from dataclasses import dataclass, field, replace
+import json
+from dataclasses import asdict, dataclass, field, fields, replace
 from typing import Tuple
 
 
@@ -128,3 +129,30 @@ def tiny_config(**kw) -> Config:
 
 
 CONFIGS = {"config1": config1, "config2": config2, "config3": config3, "config5": config5}
+
+
+def config_to_json(cfg: Config) -> str:
+    """The configuration as JSON (every field; tuples as lists)."""
+    return json.dumps(asdict(cfg), indent=1, sort_keys=True)
+
+
+def config_from_json(text: str) -> Config:
+    """A configuration from JSON: the fields config_to_json writes; missing
+    optional fields take their defaults, unknown ones are refused."""
+    d = json.loads(text)
+    known = {f.name: f for f in fields(Config)}
+    unknown = sorted(set(d) - set(known))
+    if unknown:
+        raise ValueError(f"unknown configuration fields: {unknown}")
+    for k, v in list(d.items()):
+        if isinstance(v, list):
+            d[k] = tuple(v)
+    return Config(**d)
+
+
+def load_config(name_or_path: str) -> Config:
+    """A named workload (config1, config2, config3, config5) or a JSON file."""
+    if name_or_path.endswith(".json"):
+        with open(name_or_path) as f:
+            return config_from_json(f.read())
+    return CONFIGS[name_or_path]()

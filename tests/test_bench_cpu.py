@@ -73,3 +73,25 @@ def test_crop_counts_bound_the_pairs():
     n = bench.crop_counts(cfg, sp)
     assert n_sites <= n <= n_sites * len(sp.scans)
     assert synth.config1().name == cfg.name
+
+
+@pytest.mark.parametrize("name", sorted(synth.CONFIGS))
+def test_config_json_round_trip(name):
+    cfg = synth.CONFIGS[name]()
+    assert synth.config_from_json(synth.config_to_json(cfg)) == cfg
+
+
+def test_workload_from_a_json_file(tmp_path):
+    """A workload given as a JSON file is the named workload's specimen,
+    bit for bit; unknown fields are refused."""
+    path = tmp_path / "c1.json"
+    path.write_text(synth.config_to_json(synth.config1()))
+    cfg_a, a = bench.workload("config1", 0)
+    cfg_b, b = bench.workload(str(path), 0)
+    assert cfg_a == cfg_b
+    for k in ("V", "H", "atoms", "nch", "scans"):
+        np.testing.assert_array_equal(getattr(a, k), getattr(b, k))
+    bad = tmp_path / "bad.json"
+    bad.write_text(synth.config_to_json(synth.config1())[:-2] + ', "grid": 3}')
+    with pytest.raises(ValueError, match="unknown configuration fields"):
+        synth.load_config(str(bad))
